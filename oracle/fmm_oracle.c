@@ -1,0 +1,796 @@
+/*
+ * FP64 CPU oracle of the replacement-based fast multipole method of
+ * Y. Kajima, "Notes on the Fast Multipole Method" (arXiv:2212.13080).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the CPU
+ * baseline leg of the benchmark are the only callers.  The product library
+ * never links, loads or calls this file, and this file shares no source,
+ * header, table or constant generator with the CUDA library.
+ *
+ * Every routine is a plain, slow transcription of the paper's definitions in
+ * double precision, in the order the paper gives them.  No blocking, fusion or
+ * reordering beyond what a definition states; loops over independent outputs
+ * may run on several OpenMP threads, which does not change any output's
+ * summation order.
+ *
+ * Coordinates.  The box [x0, x0+L)^3 is mapped onto the unit cube: the
+ * canonical single-precision map u = fl32(fl32(x - x0) / fl32(L)) is the one
+ * place where single precision is used, so that leaf membership (integer work)
+ * is decided on exactly the same numbers as the GPU path.  Everything after it
+ * runs in FP64 on the widened values.  Potentials and forces come out in
+ * unit-cube units; the Python driver scales them by 1/L and 1/L^2.
+ *
+ * Index conventions.
+ *   grid vector of a cell:   index (k*n + j)*n + i  for node (i, j, k), x fastest
+ *   cell of level l:         natural index (cz*S + cy)*S + cx, S = 2^l
+ *   leaf key:                Morton interleave, bit b of cx -> 3b, cy -> 3b+1,
+ *                            cz -> 3b+2
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXN 12
+
+#define ORC_ERR_OUT_OF_BOX 1
+#define ORC_ERR_NONFINITE 2
+
+/* ------------------------------------------------------------------------ */
+/* §2.1.1-§2.1.2: n-division points and the Lagrange basis                  */
+/* ------------------------------------------------------------------------ */
+
+/* §2.1.2: the n-division points of a segment are equally spaced and include
+ * both end points; on the unit segment they are a_i = i/(n-1). */
+static double tau(int n, int i) { return (double)i / (double)(n - 1); }
+
+/* §2.1.1, eq. (Lag1): g_i(x) = prod_{k!=i} (x - a_k) / prod_{k!=i} (a_i - a_k). */
+void orc_lagrange(int n, double x, double *g)
+{
+    for (int i = 0; i < n; i++) {
+        double num = 1.0, den = 1.0;
+        for (int k = 0; k < n; k++) {
+            if (k == i) continue;
+            num *= x - tau(n, k);
+            den *= tau(n, i) - tau(n, k);
+        }
+        g[i] = num / den;
+    }
+}
+
+/* d g_i / dx of eq. (Lag1), by the product rule.  The far-field force at the
+ * end of §2.2 uses v'_a = -q d/da g_{ijk}. */
+void orc_lagrange_deriv(int n, double x, double *dg)
+{
+    for (int i = 0; i < n; i++) {
+        double den = 1.0;
+        for (int k = 0; k < n; k++)
+            if (k != i) den *= tau(n, i) - tau(n, k);
+        double sum = 0.0;
+        for (int m = 0; m < n; m++) {
+            if (m == i) continue;
+            double prod = 1.0;
+            for (int k = 0; k < n; k++)
+                if (k != i && k != m) prod *= x - tau(n, k);
+            sum += prod;
+        }
+        dg[i] = sum / den;
+    }
+}
+
+/* §2.1.6, eq. (trans): the shift from a child segment to its parent has
+ * (j,i) entry g~_j(a_i): the parent's basis evaluated at the child's nodes.
+ * In parent-local coordinates the child h (0 = lower half, 1 = upper half)
+ * has nodes (h + a_i)/2.  G[J*n + i]. */
+void orc_shift_matrix(int n, int h, double *G)
+{
+    double g[ORC_MAXN];
+    for (int i = 0; i < n; i++) {
+        orc_lagrange(n, 0.5 * ((double)h + tau(n, i)), g);
+        for (int J = 0; J < n; J++) G[J * n + i] = g[J];
+    }
+}
+
+/* §2.1.7, eqs. (newer), (bilinear): F(P(a), P(a~)) = 1/|a - a~| between the
+ * n-division points a of the unit cell at the origin and a~ of the unit cell
+ * displaced by the integer vector o.  K[a*n^3 + b]. */
+void orc_m2l_kernel(int n, int ox, int oy, int oz, double *K)
+{
+    int n3 = n * n * n;
+    for (int a = 0; a < n3; a++) {
+        double ax = tau(n, a % n), ay = tau(n, (a / n) % n), az = tau(n, a / (n * n));
+        for (int b = 0; b < n3; b++) {
+            double bx = ox + tau(n, b % n), by = oy + tau(n, (b / n) % n),
+                   bz = oz + tau(n, b / (n * n));
+            double dx = ax - bx, dy = ay - by, dz = az - bz;
+            K[(int64_t)a * n3 + b] = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* §4.2: periodic boundary by Ewald summation (unit cubic box, tin-foil)     */
+/* ------------------------------------------------------------------------ */
+
+/* Ewald splitting constants for the unit box: real-space images |m|_inf <= 5
+ * and reciprocal vectors |h|_inf <= 6 with alpha = 2.5 leave truncation terms
+ * below 1e-40 and 1e-16 for every r in [-1,1]^3. */
+#define EW_ALPHA 2.5
+#define EW_RMAX 5
+#define EW_KMAX 6
+
+/* Lattice kernel of the level-0 cell (the box) with all of its periodic
+ * images that are not among its 26 nearest:
+ *   psi(r) = sum_{m not in {-1,0,1}^3} 1/|r + m|   (Ewald-regularised),
+ * written as the Ewald pair potential minus the 27 nearest image terms.  The
+ * real-space terms of the nearest images become -erf(alpha s)/s, whose limit
+ * at s = 0 is -2 alpha/sqrt(pi).  The neutralising-background constant
+ * -pi/alpha^2 is kept; it cancels for neutral systems because replacement
+ * conserves the total charge (eq. (Lag2) with j = 0). */
+double orc_lattice_psi(double rx, double ry, double rz)
+{
+    const double al = EW_ALPHA;
+    double s = 0.0;
+    for (int mz = -EW_RMAX; mz <= EW_RMAX; mz++)
+        for (int my = -EW_RMAX; my <= EW_RMAX; my++)
+            for (int mx = -EW_RMAX; mx <= EW_RMAX; mx++) {
+                double dx = rx + mx, dy = ry + my, dz = rz + mz;
+                double d = sqrt(dx * dx + dy * dy + dz * dz);
+                int nearest = (abs(mx) <= 1 && abs(my) <= 1 && abs(mz) <= 1);
+                if (nearest) {
+                    if (d == 0.0) s -= 2.0 * al / sqrt(M_PI);
+                    else s -= erf(al * d) / d;
+                } else {
+                    s += erfc(al * d) / d;
+                }
+            }
+    for (int hz = -EW_KMAX; hz <= EW_KMAX; hz++)
+        for (int hy = -EW_KMAX; hy <= EW_KMAX; hy++)
+            for (int hx = -EW_KMAX; hx <= EW_KMAX; hx++) {
+                if (hx == 0 && hy == 0 && hz == 0) continue;
+                double h2 = (double)(hx * hx + hy * hy + hz * hz);
+                double A = exp(-M_PI * M_PI * h2 / (al * al)) / h2;
+                s += A / M_PI * cos(2.0 * M_PI * (hx * rx + hy * ry + hz * rz));
+            }
+    s -= M_PI / (al * al);
+    return s;
+}
+
+/* K_lat[a*n^3 + b] = psi(a - b) for the n-division points of the unit box.
+ * psi depends on a - b only, which takes (2n-1)^3 distinct values; each is
+ * evaluated once. */
+void orc_lattice_kernel(int n, double *K)
+{
+    int n3 = n * n * n, m = 2 * n - 1;
+    double *tab = (double *)malloc(sizeof(double) * (size_t)m * m * m);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int e = 0; e < m * m * m; e++) {
+        int dx = e % m - (n - 1), dy = (e / m) % m - (n - 1), dz = e / (m * m) - (n - 1);
+        double rx = tau(n, dx > 0 ? dx : 0) - tau(n, dx < 0 ? -dx : 0);
+        double ry = tau(n, dy > 0 ? dy : 0) - tau(n, dy < 0 ? -dy : 0);
+        double rz = tau(n, dz > 0 ? dz : 0) - tau(n, dz < 0 ? -dz : 0);
+        tab[e] = orc_lattice_psi(rx, ry, rz);
+    }
+    for (int a = 0; a < n3; a++)
+        for (int b = 0; b < n3; b++) {
+            int dx = a % n - b % n + n - 1;
+            int dy = (a / n) % n - (b / n) % n + n - 1;
+            int dz = a / (n * n) - b / (n * n) + n - 1;
+            K[(int64_t)a * n3 + b] = tab[(dz * m + dy) * m + dx];
+        }
+    free(tab);
+}
+
+/* Plain Ewald sum (tin-foil boundary, neutralising background) of the
+ * potential and field at particles tgt[] of a periodic unit box; the truth for
+ * the periodic form of §4.2.  x is 3N unit-cube coordinates.  phi[t] is the
+ * potential per unit charge at particle tgt[t] from all other charges and all
+ * images (its own images included); F[3t..] = q_i * field. */
+void orc_ewald_direct(int64_t N, const double *x, const double *q, int64_t nt,
+                      const int64_t *tgt, double *phi, double *F)
+{
+    const double al = EW_ALPHA;
+    const int RM = 4; /* after minimum-image wrap, |r+m| >= 4.1 beyond this */
+    double qtot = 0.0;
+    for (int64_t j = 0; j < N; j++) qtot += q[j];
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = tgt[t];
+        double p = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+        for (int64_t j = 0; j < N; j++) {
+            double r0[3];
+            for (int a = 0; a < 3; a++) {
+                double d = x[3 * i + a] - x[3 * j + a];
+                r0[a] = d - floor(d + 0.5);
+            }
+            for (int mz = -RM; mz <= RM; mz++)
+                for (int my = -RM; my <= RM; my++)
+                    for (int mx = -RM; mx <= RM; mx++) {
+                        double dx = r0[0] + mx, dy = r0[1] + my, dz = r0[2] + mz;
+                        double s2 = dx * dx + dy * dy + dz * dz;
+                        if (j == i && mx == 0 && my == 0 && mz == 0) continue;
+                        if (s2 == 0.0) continue;
+                        double s = sqrt(s2);
+                        double ec = erfc(al * s) / s;
+                        p += q[j] * ec;
+                        double g = (ec + 2.0 * al / sqrt(M_PI) * exp(-al * al * s2)) / s2;
+                        fx += q[j] * g * dx;
+                        fy += q[j] * g * dy;
+                        fz += q[j] * g * dz;
+                    }
+        }
+        for (int hz = -EW_KMAX; hz <= EW_KMAX; hz++)
+            for (int hy = -EW_KMAX; hy <= EW_KMAX; hy++)
+                for (int hx = -EW_KMAX; hx <= EW_KMAX; hx++) {
+                    if (hx == 0 && hy == 0 && hz == 0) continue;
+                    double h2 = (double)(hx * hx + hy * hy + hz * hz);
+                    double A = exp(-M_PI * M_PI * h2 / (al * al)) / h2;
+                    double c = 0.0, sn = 0.0;
+                    for (int64_t j = 0; j < N; j++) {
+                        double arg = 2.0 * M_PI * (hx * (x[3 * i] - x[3 * j]) +
+                                                   hy * (x[3 * i + 1] - x[3 * j + 1]) +
+                                                   hz * (x[3 * i + 2] - x[3 * j + 2]));
+                        c += q[j] * cos(arg);
+                        sn += q[j] * sin(arg);
+                    }
+                    p += A / M_PI * c;
+                    fx += 2.0 * A * hx * sn;
+                    fy += 2.0 * A * hy * sn;
+                    fz += 2.0 * A * hz * sn;
+                }
+        p -= 2.0 * al / sqrt(M_PI) * q[i];
+        p -= M_PI / (al * al) * qtot;
+        phi[t] = p;
+        F[3 * t] = q[i] * fx;
+        F[3 * t + 1] = q[i] * fy;
+        F[3 * t + 2] = q[i] * fz;
+    }
+}
+
+/* Plain O(N^2) Coulomb sum, open boundary: phi_i = sum_{j != i} q_j/|x_i - x_j|
+ * and F_i = q_i sum_{j != i} q_j (x_i - x_j)/|x_i - x_j|^3, at particles tgt[].
+ * Coincident pairs are skipped. */
+void orc_direct_open(int64_t N, const double *x, const double *q, int64_t nt,
+                     const int64_t *tgt, double *phi, double *F)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = tgt[t];
+        double p = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+        for (int64_t j = 0; j < N; j++) {
+            if (j == i) continue;
+            double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1],
+                   dz = x[3 * i + 2] - x[3 * j + 2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2);
+            p += q[j] / r;
+            double c = q[j] / (r2 * r);
+            fx += c * dx;
+            fy += c * dy;
+            fz += c * dz;
+        }
+        phi[t] = p;
+        F[3 * t] = q[i] * fx;
+        F[3 * t + 1] = q[i] * fy;
+        F[3 * t + 2] = q[i] * fz;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* §2.2 step 1: divide the simulation box                                    */
+/* ------------------------------------------------------------------------ */
+
+static uint32_t morton3(int x, int y, int z, int depth)
+{
+    uint32_t k = 0;
+    for (int b = 0; b < depth; b++) {
+        k |= (uint32_t)((x >> b) & 1) << (3 * b);
+        k |= (uint32_t)((y >> b) & 1) << (3 * b + 1);
+        k |= (uint32_t)((z >> b) & 1) << (3 * b + 2);
+    }
+    return k;
+}
+
+static void demorton3(uint32_t k, int depth, int *x, int *y, int *z)
+{
+    *x = *y = *z = 0;
+    for (int b = 0; b < depth; b++) {
+        *x |= (int)((k >> (3 * b)) & 1u) << b;
+        *y |= (int)((k >> (3 * b + 1)) & 1u) << b;
+        *z |= (int)((k >> (3 * b + 2)) & 1u) << b;
+    }
+}
+
+uint32_t orc_morton(int x, int y, int z, int depth) { return morton3(x, y, z, depth); }
+
+/* Step 1 of §2.2 divides the box into 8^depth finest cells.  The map from a
+ * position to its finest cell is not spelled out in the paper; it is taken
+ * here as the canonical single-precision map
+ *   u = fl32(fl32(x - x0) / fl32(L)),  c = min(floor(u 2^depth), 2^depth - 1),
+ *   t = u 2^depth - c   (exact: 2^depth is a power of two),
+ * with u wrapped into [0,1) in the periodic form (§4.2) and rejected outside
+ * [0,1) in the open form.  A particle exactly on a plane belongs to the upper
+ * cell.  Returns a bit set of ORC_ERR_* flags. */
+int orc_bin(int64_t N, const float *pos, const double *box, int depth, int periodic,
+            float *u_out, float *t_out, int32_t *cell_out, uint32_t *key_out)
+{
+    const float x0[3] = {(float)box[0], (float)box[1], (float)box[2]};
+    const float Lf = (float)box[3];
+    const int S = 1 << depth;
+    const float Sf = (float)S;
+    int err = 0;
+    for (int64_t i = 0; i < N; i++) {
+        int c[3];
+        for (int a = 0; a < 3; a++) {
+            float d = pos[3 * i + a] - x0[a];
+            float u = d / Lf;
+            if (!isfinite(u)) {
+                err |= ORC_ERR_NONFINITE;
+                u = 0.0f;
+            }
+            if (periodic) {
+                u = u - floorf(u);
+                if (u >= 1.0f) u = 0.0f;
+            } else if (!(u >= 0.0f && u < 1.0f)) {
+                err |= ORC_ERR_OUT_OF_BOX;
+                u = 0.0f;
+            }
+            float v = u * Sf;
+            int ci = (int)floorf(v);
+            if (ci > S - 1) ci = S - 1;
+            u_out[3 * i + a] = u;
+            t_out[3 * i + a] = v - (float)ci;
+            cell_out[3 * i + a] = ci;
+            c[a] = ci;
+        }
+        key_out[i] = morton3(c[0], c[1], c[2], depth);
+    }
+    return err;
+}
+
+/* ------------------------------------------------------------------------ */
+/* §2.3: split of particles that lie closer than d to a plane of the finest  */
+/* cells (continuous form); §4.2 adds the walls of the periodic box.         */
+/* ------------------------------------------------------------------------ */
+
+/* One axis of the split of one particle: up to n+1 entries of
+ * (cell, local coordinate, weight, d weight / du). */
+typedef struct {
+    int m;
+    int cell[ORC_MAXN + 1];
+    double t[ORC_MAXN + 1];
+    double w[ORC_MAXN + 1];
+    double dw[ORC_MAXN + 1];
+} axis_split;
+
+/* §2.3: a particle within distance d (< d, strict) of a plane is replaced by n
+ * charges on a segment of length 2d perpendicular to the plane, centred on
+ * it, with weights given by the one-dimensional replacement (§2.1.3) onto the
+ * segment's n-division points.  dt = d / (leaf width) in leaf units.  Planes
+ * are the interior planes of the finest cells; the periodic form also splits
+ * at the box walls, identifying the points outside with their images inside
+ * (§4.2).  Odd n: the middle point lies on the plane and is divided into two
+ * half charges, one in each adjacent cell (first option of §2.3). */
+static void split_axis(int n, int depth, int periodic, int continuous, float dtf, int c,
+                       float t, axis_split *s)
+{
+    const int S = 1 << depth;
+    const float hi = 1.0f - dtf;
+    int lower = continuous && (periodic || c > 0) && t < dtf;
+    int upper = continuous && (periodic || c < S - 1) && t > hi;
+    if (!lower && !upper) {
+        s->m = 1;
+        s->cell[0] = c;
+        s->t[0] = (double)t;
+        s->w[0] = 1.0;
+        s->dw[0] = 0.0;
+        return;
+    }
+    const double dt = (double)dtf;
+    int cl, cu;        /* cells below and above the plane */
+    double sigma;      /* signed distance from the plane in units of d */
+    if (lower) {
+        cl = c - 1;
+        cu = c;
+        sigma = (double)t / dt;
+    } else {
+        cl = c;
+        cu = c + 1;
+        sigma = ((double)t - 1.0) / dt;
+    }
+    if (periodic) {
+        cl = (cl + S) % S;
+        cu = cu % S;
+    }
+    double g[ORC_MAXN], dg[ORC_MAXN];
+    double x = 0.5 * (sigma + 1.0); /* segment nodes -1 + 2k/(n-1) <-> tau_k */
+    orc_lagrange(n, x, g);
+    orc_lagrange_deriv(n, x, dg);
+    /* d x / d u = (1/2) * (1/dt) * 2^depth */
+    const double dxdu = 0.5 / dt * (double)S;
+    int m = 0;
+    for (int k = 0; k < n; k++) {
+        double sk = -1.0 + 2.0 * (double)k / (double)(n - 1);
+        if (2 * k == n - 1) {
+            s->cell[m] = cl; s->t[m] = 1.0; s->w[m] = 0.5 * g[k]; s->dw[m] = 0.5 * dg[k] * dxdu; m++;
+            s->cell[m] = cu; s->t[m] = 0.0; s->w[m] = 0.5 * g[k]; s->dw[m] = 0.5 * dg[k] * dxdu; m++;
+        } else if (2 * k < n - 1) {
+            s->cell[m] = cl; s->t[m] = 1.0 + sk * dt; s->w[m] = g[k]; s->dw[m] = dg[k] * dxdu; m++;
+        } else {
+            s->cell[m] = cu; s->t[m] = sk * dt; s->w[m] = g[k]; s->dw[m] = dg[k] * dxdu; m++;
+        }
+    }
+    s->m = m;
+}
+
+/* Number of charges each particle becomes: the product over the three axes
+ * (1, n, or n+1 for odd n); the paper's n, n^2, n^3 cases of §2.3.
+ * axes[3i+a] = 1 where particle i is split along axis a. */
+void orc_split_count(int64_t N, const float *t, const int32_t *cell, int n, int depth,
+                     int periodic, int continuous, float dtf, int32_t *count, int8_t *axes)
+{
+    for (int64_t i = 0; i < N; i++) {
+        int c = 1;
+        for (int a = 0; a < 3; a++) {
+            axis_split s;
+            split_axis(n, depth, periodic, continuous, dtf, cell[3 * i + a], t[3 * i + a], &s);
+            c *= s.m;
+            axes[3 * i + a] = (int8_t)(s.m > 1);
+        }
+        count[i] = c;
+    }
+}
+
+/* Emits the charges of every particle, particle after particle, each as the
+ * tensor product of its three axes with x fastest (§2.3: n^2 and n^3 near
+ * edges and corners).  offset[i] = first output slot of particle i. */
+void orc_split_emit(int64_t N, const float *t, const int32_t *cell, const float *q, int n,
+                    int depth, int periodic, int continuous, float dtf, const int64_t *offset,
+                    double *pt_t, int32_t *pt_cell, uint32_t *pt_key, double *pt_q,
+                    double *pt_w, double *pt_dw, int64_t *pt_origin)
+{
+    for (int64_t i = 0; i < N; i++) {
+        axis_split s[3];
+        for (int a = 0; a < 3; a++)
+            split_axis(n, depth, periodic, continuous, dtf, cell[3 * i + a], t[3 * i + a], &s[a]);
+        int64_t o = offset[i];
+        for (int kz = 0; kz < s[2].m; kz++)
+            for (int ky = 0; ky < s[1].m; ky++)
+                for (int kx = 0; kx < s[0].m; kx++) {
+                    double W = s[0].w[kx] * s[1].w[ky] * s[2].w[kz];
+                    pt_t[3 * o] = s[0].t[kx];
+                    pt_t[3 * o + 1] = s[1].t[ky];
+                    pt_t[3 * o + 2] = s[2].t[kz];
+                    pt_cell[3 * o] = s[0].cell[kx];
+                    pt_cell[3 * o + 1] = s[1].cell[ky];
+                    pt_cell[3 * o + 2] = s[2].cell[kz];
+                    pt_key[o] = morton3(s[0].cell[kx], s[1].cell[ky], s[2].cell[kz], depth);
+                    pt_w[o] = W;
+                    pt_q[o] = (double)q[i] * W;
+                    pt_dw[3 * o] = s[0].dw[kx] * s[1].w[ky] * s[2].w[kz];
+                    pt_dw[3 * o + 1] = s[0].w[kx] * s[1].dw[ky] * s[2].w[kz];
+                    pt_dw[3 * o + 2] = s[0].w[kx] * s[1].w[ky] * s[2].dw[kz];
+                    pt_origin[o] = i;
+                    o++;
+                }
+    }
+}
+
+/* Stable counting sort of the charges by finest-cell key: perm[s] = emitted
+ * index of sorted slot s, start[key] = first slot of the cell.  Ties keep
+ * their emitted order. */
+void orc_sort(int64_t npts, const uint32_t *key, int depth, int64_t *perm, int64_t *start)
+{
+    int64_t ncell = (int64_t)1 << (3 * depth);
+    for (int64_t c = 0; c <= ncell; c++) start[c] = 0;
+    for (int64_t e = 0; e < npts; e++) start[key[e] + 1]++;
+    for (int64_t c = 0; c < ncell; c++) start[c + 1] += start[c];
+    int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncell);
+    for (int64_t c = 0; c < ncell; c++) cur[c] = start[c];
+    for (int64_t e = 0; e < npts; e++) perm[cur[key[e]]++] = e;
+    free(cur);
+}
+
+/* ------------------------------------------------------------------------ */
+/* §2.2 step 2: upward pass (replacement at the leaves, then shift upward)   */
+/* ------------------------------------------------------------------------ */
+
+static int64_t level_offset(int n, int l)
+{
+    int64_t n3 = (int64_t)n * n * n, cells = 0;
+    for (int k = 0; k < l; k++) cells += (int64_t)1 << (3 * k);
+    return cells * n3;
+}
+
+int64_t orc_level_offset(int n, int l) { return level_offset(n, l); }
+
+/* §2.1.5, eq. (ex66): replacement of the charges of each finest cell with
+ * respect to that cell, Phi[i,j,k] = sum_l q_l g_i(x_l) g_j(y_l) g_k(z_l),
+ * x_l in cell-local coordinates.  Sorted charges (t, q) and cell starts by
+ * Morton key.  Writes level `depth` of Phi. */
+void orc_p2m(int n, int depth, const double *st, const double *sq, const int64_t *start,
+             double *Phi)
+{
+    const int64_t ncell = (int64_t)1 << (3 * depth);
+    const int n3 = n * n * n, S = 1 << depth;
+    double *P = Phi + level_offset(n, depth);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t key = 0; key < ncell; key++) {
+        int cx, cy, cz;
+        demorton3((uint32_t)key, depth, &cx, &cy, &cz);
+        double *v = P + (((int64_t)cz * S + cy) * S + cx) * n3;
+        for (int a = 0; a < n3; a++) v[a] = 0.0;
+        for (int64_t s = start[key]; s < start[key + 1]; s++) {
+            double gx[ORC_MAXN], gy[ORC_MAXN], gz[ORC_MAXN];
+            orc_lagrange(n, st[3 * s], gx);
+            orc_lagrange(n, st[3 * s + 1], gy);
+            orc_lagrange(n, st[3 * s + 2], gz);
+            for (int k = 0; k < n; k++)
+                for (int j = 0; j < n; j++)
+                    for (int i = 0; i < n; i++)
+                        v[(k * n + j) * n + i] += sq[s] * gx[i] * gy[j] * gz[k];
+        }
+    }
+}
+
+/* One-dimensional shift along `axis` (eq. (threethree)): out = G (x) in on
+ * every line of the n^3 vector parallel to the axis. */
+static void shift_axis(int n, const double *G, int axis, const double *in, double *out)
+{
+    for (int k = 0; k < n; k++)
+        for (int j = 0; j < n; j++)
+            for (int i = 0; i < n; i++) {
+                int idx[3] = {i, j, k};
+                double s = 0.0;
+                for (int m = 0; m < n; m++) {
+                    int src[3] = {i, j, k};
+                    src[axis] = m;
+                    s += G[idx[axis] * n + m] * in[(src[2] * n + src[1]) * n + src[0]];
+                }
+                out[(k * n + j) * n + i] = s;
+            }
+}
+
+/* §2.2 step 2: shift every cell's vector to its parent with the three
+ * successive one-dimensional shifts of eq. (threethree) (x, then y, then z)
+ * and sum the eight children; repeat from level `depth` up to level `lmin`. */
+void orc_m2m(int n, int depth, int lmin, double *Phi)
+{
+    const int n3 = n * n * n;
+    double G[2][ORC_MAXN * ORC_MAXN];
+    orc_shift_matrix(n, 0, G[0]);
+    orc_shift_matrix(n, 1, G[1]);
+    for (int l = depth; l > lmin; l--) {
+        const int S = 1 << l, Sp = S >> 1;
+        const double *C = Phi + level_offset(n, l);
+        double *P = Phi + level_offset(n, l - 1);
+#pragma omp parallel for schedule(static)
+        for (int64_t pc = 0; pc < (int64_t)Sp * Sp * Sp; pc++) {
+            int px = (int)(pc % Sp), py = (int)((pc / Sp) % Sp), pz = (int)(pc / ((int64_t)Sp * Sp));
+            double *v = P + pc * n3;
+            double a[ORC_MAXN * ORC_MAXN * ORC_MAXN], b[ORC_MAXN * ORC_MAXN * ORC_MAXN];
+            for (int e = 0; e < n3; e++) v[e] = 0.0;
+            for (int hz = 0; hz < 2; hz++)
+                for (int hy = 0; hy < 2; hy++)
+                    for (int hx = 0; hx < 2; hx++) {
+                        int cx = 2 * px + hx, cy = 2 * py + hy, cz = 2 * pz + hz;
+                        const double *w = C + (((int64_t)cz * S + cy) * S + cx) * n3;
+                        shift_axis(n, G[hx], 0, w, a);
+                        shift_axis(n, G[hy], 1, a, b);
+                        shift_axis(n, G[hz], 2, b, a);
+                        for (int e = 0; e < n3; e++) v[e] += a[e];
+                    }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* §2.2 step 3: downward pass                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Transpose of the one-dimensional shift along `axis`: out = G^T (x) in. */
+static void shift_axis_t(int n, const double *G, int axis, const double *in, double *out)
+{
+    for (int k = 0; k < n; k++)
+        for (int j = 0; j < n; j++)
+            for (int i = 0; i < n; i++) {
+                int idx[3] = {i, j, k};
+                double s = 0.0;
+                for (int m = 0; m < n; m++) {
+                    int src[3] = {i, j, k};
+                    src[axis] = m;
+                    s += G[m * n + idx[axis]] * in[(src[2] * n + src[1]) * n + src[0]];
+                }
+                out[(k * n + j) * n + i] = s;
+            }
+}
+
+/* The linear functional Psi_C(v) of §2.2 step 3 is stored as the vector L_C
+ * with Psi_C(v) = L_C . v.
+ *
+ *  - Psi is zero at levels 0 and 1 (open form).  The periodic form (§4.2)
+ *    starts at level 0 with the interaction of the box with its images beyond
+ *    the 26 nearest (Ewald lattice kernel), and adds interaction lists from
+ *    level 1 on, whose cells are the periodic images.
+ *  - Psi_child(v) = Psi_parent(shift_{child->parent}(v)), i.e.
+ *    L_child = shift^T L_parent.
+ *  - B^n_{C,C~}(v, Phi_C~) is added for every C~ in the interaction list of C
+ *    (eq. (bilinear)): L_C[a] += sum_b F(a, b~) Phi_C~[b], with
+ *    F = 2^l / |a - b~| in unit-box units for cells of level l.
+ *  - The interaction list (Greengard-Rokhlin, cited in §2.2): children of the
+ *    parent's 26 neighbours and the parent itself that are not adjacent to C.
+ *
+ * need[l] (optional, natural index) marks the cells whose L is required;
+ * the others are skipped.  Klat: the n^3 x n^3 lattice kernel (periodic). */
+void orc_downward(int n, int depth, int periodic, const double *Phi, double *L,
+                  const uint8_t *const *need, const double *Klat)
+{
+    const int n3 = n * n * n;
+    double G[2][ORC_MAXN * ORC_MAXN];
+    orc_shift_matrix(n, 0, G[0]);
+    orc_shift_matrix(n, 1, G[1]);
+    /* unit kernels K_o for the 7^3 offsets |o|_inf <= 3, stored transposed
+     * (KT[b*n3 + a]) so that the accumulation below runs over b in order */
+    double *KT = (double *)malloc(sizeof(double) * 343 * (size_t)n3 * n3);
+    double *K = (double *)malloc(sizeof(double) * (size_t)n3 * n3);
+    for (int oz = -3; oz <= 3; oz++)
+        for (int oy = -3; oy <= 3; oy++)
+            for (int ox = -3; ox <= 3; ox++) {
+                int oi = ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3);
+                orc_m2l_kernel(n, ox, oy, oz, K);
+                for (int a = 0; a < n3; a++)
+                    for (int b = 0; b < n3; b++)
+                        KT[(int64_t)oi * n3 * n3 + (int64_t)b * n3 + a] = K[(int64_t)a * n3 + b];
+            }
+    free(K);
+
+    if (periodic) {
+        /* level 0: the box against its far images */
+        double *L0 = L + level_offset(n, 0);
+        const double *P0 = Phi + level_offset(n, 0);
+        for (int a = 0; a < n3; a++) {
+            double s = 0.0;
+            for (int b = 0; b < n3; b++) s += Klat[(int64_t)a * n3 + b] * P0[b];
+            L0[a] = s;
+        }
+    } else {
+        for (int e = 0; e < n3; e++) L[level_offset(n, 0) + e] = 0.0;
+    }
+    for (int l = 1; l <= depth; l++) {
+        const int S = 1 << l, Sp = S >> 1;
+        const double scale = (double)S;
+        const double *Pl = Phi + level_offset(n, l);
+        double *Ll = L + level_offset(n, l);
+        const double *Lp = L + level_offset(n, l - 1);
+        const int do_m2l = periodic ? (l >= 1) : (l >= 2);
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t c = 0; c < (int64_t)S * S * S; c++) {
+            if (need && need[l] && !need[l][c]) continue;
+            int cx = (int)(c % S), cy = (int)((c / S) % S), cz = (int)(c / ((int64_t)S * S));
+            double *v = Ll + c * n3;
+            /* Psi_child(v) = Psi_parent(shift(v)) */
+            double a[ORC_MAXN * ORC_MAXN * ORC_MAXN], b[ORC_MAXN * ORC_MAXN * ORC_MAXN];
+            int px = cx >> 1, py = cy >> 1, pz = cz >> 1;
+            const double *w = Lp + (((int64_t)pz * Sp + py) * Sp + px) * n3;
+            shift_axis_t(n, G[cz & 1], 2, w, a);
+            shift_axis_t(n, G[cy & 1], 1, a, b);
+            shift_axis_t(n, G[cx & 1], 0, b, a);
+            for (int e = 0; e < n3; e++) v[e] = a[e];
+            if (!do_m2l) continue;
+            /* interaction list */
+            for (int sz = 2 * (pz - 1); sz <= 2 * (pz + 1) + 1; sz++)
+                for (int sy = 2 * (py - 1); sy <= 2 * (py + 1) + 1; sy++)
+                    for (int sx = 2 * (px - 1); sx <= 2 * (px + 1) + 1; sx++) {
+                        int ox = sx - cx, oy = sy - cy, oz = sz - cz;
+                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+                        int wx = sx, wy = sy, wz = sz;
+                        if (periodic) {
+                            wx = ((sx % S) + S) % S;
+                            wy = ((sy % S) + S) % S;
+                            wz = ((sz % S) + S) % S;
+                        } else if (sx < 0 || sy < 0 || sz < 0 || sx >= S || sy >= S || sz >= S) {
+                            continue;
+                        }
+                        int oi = ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3);
+                        const double *kt = KT + (int64_t)oi * n3 * n3;
+                        const double *src = Pl + (((int64_t)wz * S + wy) * S + wx) * n3;
+                        for (int bb = 0; bb < n3; bb++) {
+                            double f = scale * src[bb];
+                            const double *row = kt + (int64_t)bb * n3;
+                            for (int aa = 0; aa < n3; aa++) v[aa] += row[aa] * f;
+                        }
+                    }
+        }
+    }
+    free(KT);
+}
+
+/* ------------------------------------------------------------------------ */
+/* §2.2 steps 4-5 and the forces: far field at each charge, plus the near    */
+/* field over the cell itself and its 26 neighbours                          */
+/* ------------------------------------------------------------------------ */
+
+/* For every sorted charge s (or those with mask[s] set):
+ *   far:  phi_far = Psi_leaf(g(x_s)) = sum_ijk g_ijk(x_s) L_leaf[ijk]
+ *         (step 4 per unit charge), and the force Psi_leaf(v'_a) with
+ *         v'_a = -q d g / d a (end of §2.2);
+ *   near: the direct sum over the charges of the same cell and of its 26
+ *         neighbours (step 5; no second neighbours, §1), skipping charges of
+ *         the same original particle (the split charges of one particle do
+ *         not interact with each other).  Coincident charges of different
+ *         particles contribute nothing and are counted in *ncoinc.
+ * Outputs per charge (unit-box units): phi[s] per unit charge, F[3s..] force. */
+void orc_evaluate(int n, int depth, int periodic, int64_t npts, const double *st,
+                  const int32_t *scell, const double *sq, const int64_t *sorigin,
+                  const int64_t *start, const double *L, const uint8_t *mask, double *phi,
+                  double *F, int64_t *ncoinc)
+{
+    const int n3 = n * n * n, S = 1 << depth;
+    const double w = 1.0 / (double)S;
+    const double *Ll = L + level_offset(n, depth);
+    int64_t coinc = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : coinc)
+    for (int64_t s = 0; s < npts; s++) {
+        if (mask && !mask[s]) continue;
+        int cx = scell[3 * s], cy = scell[3 * s + 1], cz = scell[3 * s + 2];
+        const double *v = Ll + (((int64_t)cz * S + cy) * S + cx) * n3;
+        double gx[ORC_MAXN], gy[ORC_MAXN], gz[ORC_MAXN];
+        double dx_[ORC_MAXN], dy_[ORC_MAXN], dz_[ORC_MAXN];
+        orc_lagrange(n, st[3 * s], gx);
+        orc_lagrange(n, st[3 * s + 1], gy);
+        orc_lagrange(n, st[3 * s + 2], gz);
+        orc_lagrange_deriv(n, st[3 * s], dx_);
+        orc_lagrange_deriv(n, st[3 * s + 1], dy_);
+        orc_lagrange_deriv(n, st[3 * s + 2], dz_);
+        double pf = 0.0, gfx = 0.0, gfy = 0.0, gfz = 0.0;
+        for (int k = 0; k < n; k++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) {
+                    double Lv = v[(k * n + j) * n + i];
+                    pf += gx[i] * gy[j] * gz[k] * Lv;
+                    gfx += dx_[i] * gy[j] * gz[k] * Lv;
+                    gfy += gx[i] * dy_[j] * gz[k] * Lv;
+                    gfz += gx[i] * gy[j] * dz_[k] * Lv;
+                }
+        /* d/du = 2^depth d/dt */
+        double fx = -sq[s] * gfx * S, fy = -sq[s] * gfy * S, fz = -sq[s] * gfz * S;
+        double pn = 0.0, nfx = 0.0, nfy = 0.0, nfz = 0.0;
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int nx = cx + dx, ny = cy + dy, nz = cz + dz;
+                    if (periodic) {
+                        nx = (nx + S) % S;
+                        ny = (ny + S) % S;
+                        nz = (nz + S) % S;
+                    } else if (nx < 0 || ny < 0 || nz < 0 || nx >= S || ny >= S || nz >= S) {
+                        continue;
+                    }
+                    uint32_t key = morton3(nx, ny, nz, depth);
+                    for (int64_t r = start[key]; r < start[key + 1]; r++) {
+                        if (sorigin[r] == sorigin[s]) continue;
+                        /* separation in unit-box units, neighbour cell at offset (dx,dy,dz) */
+                        double rx = (st[3 * s] - st[3 * r] - dx) * w;
+                        double ry = (st[3 * s + 1] - st[3 * r + 1] - dy) * w;
+                        double rz = (st[3 * s + 2] - st[3 * r + 2] - dz) * w;
+                        double r2 = rx * rx + ry * ry + rz * rz;
+                        if (r2 == 0.0) {
+                            coinc++;
+                            continue;
+                        }
+                        double rr = sqrt(r2);
+                        pn += sq[r] / rr;
+                        double c = sq[s] * sq[r] / (r2 * rr);
+                        nfx += c * rx;
+                        nfy += c * ry;
+                        nfz += c * rz;
+                    }
+                }
+        phi[s] = pf + pn;
+        F[3 * s] = fx + nfx;
+        F[3 * s + 1] = fy + nfy;
+        F[3 * s + 2] = fz + nfz;
+    }
+    if (ncoinc) *ncoinc = coinc;
+}

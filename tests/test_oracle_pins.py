@@ -1,0 +1,389 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: an identity
+of the paper, a value the paper prints (tests/golden), a closed form, an
+exactness special case, or a brute-force sum.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import read_golden
+from paper_2212_13080_gb300 import inputs
+
+
+# --- §2.1.1: Lagrange basis --------------------------------------------------
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7, 8])
+def test_lagrange_identity_lag2(n):
+    """eq. (Lag2): sum_i a_i^j g_i(x) = x^j for j < n, and g_i(a_j) = delta_ij."""
+    x = np.linspace(-0.7, 1.9, 37)
+    g = oracle.lagrange(n, x)
+    a = oracle.nodes(n)
+    leb = np.abs(g).sum(axis=1)  # Lebesgue function: rounding scale of the sum
+    for j in range(n):
+        assert np.all(np.abs(g @ a ** j - x ** j) <= 1e-14 * leb * np.maximum(1, np.abs(x) ** j))
+    np.testing.assert_allclose(oracle.lagrange(n, a), np.eye(n), atol=1e-15)
+    # j = n is NOT reproduced (the first neglected term of eq. (error))
+    assert np.max(np.abs(g @ a ** n - x ** n)) > 1e-3
+
+
+@pytest.mark.parametrize("n", [2, 4, 5, 7])
+def test_lagrange_derivative(n):
+    """d/dx of eq. (Lag2): sum_i a_i^j g_i'(x) = j x^(j-1); and central differences."""
+    x = np.linspace(-0.3, 1.3, 23)
+    dg = oracle.lagrange_deriv(n, x)
+    a = oracle.nodes(n)
+    for j in range(1, n):
+        np.testing.assert_allclose(dg @ a ** j, j * x ** (j - 1), rtol=1e-11, atol=1e-11)
+    h = 1e-6
+    fd = (oracle.lagrange(n, x + h) - oracle.lagrange(n, x - h)) / (2 * h)
+    np.testing.assert_allclose(dg, fd, rtol=1e-6, atol=1e-6)
+
+
+# --- §2.1.5-2.1.6: replacement, shift, invariance ------------------------------
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6])
+def test_replacement_conserves_moments(n):
+    """Replacement reproduces every moment sum q x^a y^b z^c with a, b, c < n
+    (eq. (Lag2) per axis, eq. (ex66))."""
+    rng = np.random.default_rng(n)
+    t = rng.random((50, 3))
+    q = rng.uniform(-1, 1, 50)
+    v = oracle.replace(n, t, q).reshape(n, n, n)  # [k, j, i]
+    a = oracle.nodes(n)
+    for al in range(n):
+        for be in range(n):
+            for ga in range(n):
+                lhs = np.einsum("kji,i,j,k->", v, a ** al, a ** be, a ** ga)
+                rhs = np.sum(q * t[:, 0] ** al * t[:, 1] ** be * t[:, 2] ** ga)
+                assert abs(lhs - rhs) <= 1e-12 * max(1.0, np.sum(np.abs(q)))
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_shift_round_trip_identity(n):
+    """shift_{parent->child} o shift_{child->parent} = I on the child's vectors
+    (Appendix A.2 uses shift_{S->C} o shift_{C->S} = id).  The parent->child
+    shift has entries g_child_j(parent node I) = g_j(2 a_I - h)."""
+    a = oracle.nodes(n)
+    for h in (0, 1):
+        G = oracle.shift_matrix(n, h)
+        H = oracle.lagrange(n, 2 * a - h)  # H[I, j] = g_j(2 a_I - h)
+        np.testing.assert_allclose(H.T @ G, np.eye(n), atol=1e-11)
+
+
+@pytest.mark.parametrize("n,periodic", [(4, False), (5, False), (4, True)])
+def test_invariance_through_levels(n, periodic):
+    """Eq. (onediminv) in 3-D: the upward pass's Phi at every level equals the
+    direct replacement of the cell's charges with respect to that cell."""
+    pos, q, box = inputs.uniform_pm1(300, 21)
+    r = oracle.fmm(pos, q, box, depth=3, n=n, periodic=periodic)
+    u = r["u"].astype(np.float64)
+    lmin = 0 if periodic else 2
+    for l in range(lmin, 4):
+        S = 1 << l
+        c = np.minimum(np.floor(u * S).astype(int), S - 1)
+        Phi_l = oracle.level_view(r["Phi"], n, l)
+        for cell in sorted({0, min(5, S ** 3 - 1), (S ** 3) // 2, S ** 3 - 1}):
+            cz, cy, cx = cell // (S * S), (cell // S) % S, cell % S
+            m = (c[:, 0] == cx) & (c[:, 1] == cy) & (c[:, 2] == cz)
+            tl = u[m] * S - np.array([cx, cy, cz])
+            ref = oracle.replace(n, tl, q[m])
+            np.testing.assert_allclose(Phi_l[cell], ref, rtol=1e-11, atol=1e-11)
+
+
+# --- Appendix A.1: Table 2 -----------------------------------------------------
+
+def _weights(n, P):
+    gx, gy, gz = (oracle.lagrange(n, P[:, a]) for a in range(3))
+    return np.einsum("pk,pj,pi->pkji", gz, gy, gx).reshape(len(P), -1)
+
+
+@pytest.mark.parametrize("row", read_golden("table2_errors.txt"))
+def test_table2_pairwise_errors(row):
+    """Table 2: max relative error of eq. (newer) between a unit cube and the
+    unit cube one gap directly above it (the case the paper reports as the
+    maximum), 26^3 x 26^3 positions at step 0.04.  E1: both sides replaced;
+    E2: source side only.  Within 10% of the printed values.  The target
+    points are reduced by the cube's symmetries x<->1-x, y<->1-y, x<->y."""
+    n, E1p, E2p = int(row[0]), row[1], row[2]
+    g = np.arange(26) * 0.04
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    Pr = P[(P[:, 0] < 0.5) & (P[:, 1] < 0.5) & (P[:, 1] <= P[:, 0])]
+    Pt = P + np.array([0.0, 0.0, 2.0])
+    WP, WT = _weights(n, Pr), _weights(n, P)
+    K = oracle.m2l_kernel(n, (0, 0, 2))
+    a = oracle.nodes(n)
+    idx = np.arange(n ** 3)
+    nodes_src = np.stack([a[idx % n], a[(idx // n) % n], a[idx // (n * n)]], 1) + [0, 0, 2.0]
+    A = WP @ K
+    e1 = e2 = 0.0
+    for s in range(0, len(Pr), 400):
+        pr = Pr[s:s + 400]
+        F = 1.0 / np.linalg.norm(pr[:, None, :] - Pt[None, :, :], axis=2)
+        e1 = max(e1, np.max(np.abs(F - A[s:s + 400] @ WT.T) / F))
+        Fn = 1.0 / np.linalg.norm(pr[:, None, :] - nodes_src[None, :, :], axis=2)
+        e2 = max(e2, np.max(np.abs(F - Fn @ WT.T) / F))
+    assert abs(e1 / E1p - 1) < 0.10, (n, e1, E1p)
+    assert abs(e2 / E2p - 1) < 0.10, (n, e2, E2p)
+
+
+def test_error_bound_appendix():
+    """Appendix A.1: |sum q q~ F - B(Phi, Phi~)| <= E1 (sum|q|)(sum|q~|) max F,
+    with E1 from Table 2, for charges in a cube and the cube directly above."""
+    rng = np.random.default_rng(5)
+    for row in read_golden("table2_errors.txt"):
+        n, E1 = int(row[0]), row[1]
+        t1 = rng.random((40, 3))
+        t2 = rng.random((40, 3))
+        q1 = rng.uniform(-1, 1, 40)
+        q2 = rng.uniform(-1, 1, 40)
+        exact = np.sum(q1[:, None] * q2[None, :] /
+                       np.linalg.norm(t1[:, None, :] - (t2[None, :, :] + [0, 0, 2]), axis=2))
+        approx = oracle.replace(n, t1, q1) @ oracle.m2l_kernel(n, (0, 0, 2)) @ oracle.replace(n, t2, q2)
+        assert abs(exact - approx) <= E1 * np.sum(np.abs(q1)) * np.sum(np.abs(q2)) * 1.0
+
+
+# --- §2.2: the whole FMM -------------------------------------------------------
+
+def _node_lattice(nsites_axis, count, seed):
+    """count distinct points of the lattice k/nsites_axis, k = 0..nsites-1."""
+    rng = np.random.default_rng(seed)
+    sites = rng.choice(nsites_axis ** 3, size=count, replace=False)
+    ijk = np.stack([sites % nsites_axis, (sites // nsites_axis) % nsites_axis,
+                    sites // nsites_axis ** 2], 1)
+    pos = (ijk / nsites_axis).astype(np.float32)
+    q = np.where(rng.random(count) < 0.5, 1.0, -1.0).astype(np.float32)
+    return pos, q
+
+
+@pytest.mark.parametrize("depth,periodic", [(2, False), (3, False), (4, False), (2, True), (3, True)])
+def test_exact_on_node_lattice(depth, periodic):
+    """Exactness special case: with n = 5 every point of the lattice k/16 is a
+    node of every cell of level >= 2 (k/4: of every level >= 0), so every
+    replacement, shift and interpolation the open (periodic) form uses is exact
+    (one-hot weights, eq. (Lag1) at the nodes) and the FMM potential equals the
+    direct (open) or Ewald (periodic) sum to rounding."""
+    if periodic:
+        pos, q = _node_lattice(4, 40, depth * 10 + 1)
+    else:
+        pos, q = _node_lattice(16, 700, depth * 10)
+    box = (0.0, 0.0, 0.0, 1.0)
+    r = oracle.fmm(pos, q, box, depth=depth, n=5, periodic=periodic)
+    pd, _ = oracle.direct(pos, q, box, periodic=periodic)
+    tol = 1e-10 if periodic else 1e-12
+    np.testing.assert_allclose(r["phi"], pd, rtol=0, atol=tol * np.max(np.abs(pd)))
+    assert abs(r["E"] - 0.5 * np.dot(q.astype(np.float64), pd)) < tol * np.sum(np.abs(pd))
+
+
+def test_table1_error_magnitudes():
+    """Table 1: Error1 / Error2 (mean relative errors against the direct sum,
+    §3.1 definitions) for 23040 random +-1 charges in 8^3 finest cells.  Both
+    statistics are heavy-tailed (a particle whose exact potential or force
+    component is near zero dominates the mean), so the median over 5 seeded
+    configurations is compared with the printed values, within a factor 2.5;
+    successive orders differ by a factor 5-10."""
+    rows = read_golden("table1_errors.txt")
+    e1 = {int(r[0]): [] for r in rows}
+    e2 = {int(r[0]): [] for r in rows}
+    for seed in range(11, 16):
+        pos, q, box = inputs.uniform_pm1(23040, seed)
+        pd, Fd = oracle.direct(pos, q, box)
+        for r in rows:
+            n = int(r[0])
+            o = oracle.fmm(pos, q, box, depth=3, n=n, keep=False)
+            e1[n].append(np.mean(np.abs((o["phi"] - pd) / pd)))
+            e2[n].append(np.mean(np.abs((o["F"] - Fd) / Fd)))
+    for r in rows:
+        n = int(r[0])
+        m1, m2 = np.median(e1[n]), np.median(e2[n])
+        assert r[1] / 2.5 < m1 < r[1] * 2.5, (n, m1, r[1])
+        assert r[2] / 2.5 < m2 < r[2] * 2.5, (n, m2, r[2])
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_convergence_to_direct(periodic):
+    """The FMM converges to the direct / Ewald sum as the order grows."""
+    pos, q, box = inputs.uniform_pm1(500, 31)
+    pd, Fd = oracle.direct(pos, q, box, periodic=periodic)
+    errs = []
+    for n in (3, 4, 5, 6):
+        r = oracle.fmm(pos, q, box, depth=2, n=n, periodic=periodic)
+        errs.append(np.linalg.norm(r["phi"] - pd) / np.linalg.norm(pd))
+    assert errs[-1] < 1e-4
+    assert all(errs[k + 1] < errs[k] for k in range(len(errs) - 1)), errs
+
+
+def test_ewald_madelung_nacl_cscl():
+    """Closed forms: Madelung constants of rock salt (1.7475645946) and caesium
+    chloride (1.7626747731) pin the Ewald sum used for the periodic form."""
+    x = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0],
+                  [.5, 0, 0], [0, .5, 0], [0, 0, .5], [.5, .5, .5]])
+    q = np.array([1, 1, 1, 1, -1, -1, -1, -1.0])
+    phi, F = oracle.ewald_unit(x, q)
+    np.testing.assert_allclose(-phi * q * 0.5, 1.747564594633182, rtol=1e-12)
+    assert np.max(np.abs(F)) < 1e-12
+    x = np.array([[0.1, 0.2, 0.3], [0.6, 0.7, 0.8]])
+    q = np.array([1.0, -1.0])
+    phi, _ = oracle.ewald_unit(x, q)
+    np.testing.assert_allclose(-phi * q * (np.sqrt(3) / 2), 1.762674773070988, rtol=1e-12)
+
+
+def test_lattice_kernel_simple_cubic_constant():
+    """psi(0) = (simple-cubic lattice sum over m != 0 with neutralising
+    background, -2.837297479480620) minus the 26 nearest images."""
+    near = 6 + 12 / np.sqrt(2) + 8 / np.sqrt(3)
+    assert abs(oracle.lattice_psi((0, 0, 0)) - (-2.837297479480620 - near)) < 1e-12
+    K = oracle.lattice_kernel(4)
+    np.testing.assert_allclose(K, K.T, atol=1e-12)
+
+
+def test_energy_is_half_sum():
+    pos, q, box = inputs.uniform_pm1(400, 41)
+    r = oracle.fmm(pos, q, box, depth=3, n=4)
+    assert abs(r["E"] - 0.5 * np.dot(q.astype(np.float64), r["phi"])) < 1e-9 * abs(r["E"])
+
+
+# --- integer work ------------------------------------------------------------
+
+def test_binning_sort_and_ranges():
+    pos, q, box = inputs.uniform_pm1(5000, 51)
+    r = oracle.fmm(pos, q, box, depth=4, n=3)
+    cell = np.floor(pos.astype(np.float64) * 16).astype(int)
+    np.testing.assert_array_equal(r["cell"], cell)
+    # Morton key: children of one parent are 8 consecutive keys
+    for c in range(3):
+        assert np.all((r["key"] >> 3) == (r["pt_key"][: len(pos)] >> 3))
+    bits = np.zeros(len(pos), np.int64)
+    for b in range(4):
+        for a in range(3):
+            bits |= ((cell[:, a] >> b) & 1) << (3 * b + a)
+    np.testing.assert_array_equal(r["key"], bits)
+    np.testing.assert_array_equal(r["perm"], np.argsort(r["pt_key"], kind="stable"))
+    counts = np.bincount(r["pt_key"], minlength=16 ** 3)
+    np.testing.assert_array_equal(np.diff(r["start"]), counts)
+
+
+def test_binning_edges():
+    """A particle on a plane belongs to the upper cell; periodic positions wrap;
+    open positions outside [0,1) are rejected."""
+    pos = np.array([[0.5, 0.25, 0.0], [0.999999, 0.125, 0.75]], np.float32)
+    q = np.array([1, -1], np.float32)
+    r = oracle.fmm(pos, q, (0, 0, 0, 1), depth=2, n=3)
+    np.testing.assert_array_equal(r["cell"], [[2, 1, 0], [3, 0, 3]])
+    pos2 = np.array([[1.5, -0.25, 2.0], [0.25, 0.5, 0.75]], np.float32)
+    r2 = oracle.fmm(pos2, q, (0, 0, 0, 1), depth=2, n=3, periodic=True)
+    np.testing.assert_array_equal(r2["cell"], [[2, 3, 0], [1, 2, 3]])
+    with pytest.raises(ValueError):
+        oracle.fmm(pos2, q, (0, 0, 0, 1), depth=2, n=3, periodic=False)
+
+
+# --- §2.3 split ----------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_split_conserves_charge_and_position(n):
+    """Each particle's split charges carry its charge and its position as
+    first moment (eq. (Lag2), j = 0, 1), sit on a segment of length 2d centred
+    on the plane, and odd n halves the middle point into both cells."""
+    pos, q, box = inputs.uniform_pm1(20000, 61)
+    dt = 1.0 / 16
+    r = oracle.fmm(pos, q, box, depth=3, n=n, continuous=True, dt=dt)
+    org = r["pt_origin"]
+    W = r["pt_w"]
+    u = r["u"].astype(np.float64)
+    np.testing.assert_allclose(np.bincount(org, weights=W), 1.0, atol=1e-12)
+    xu = (r["pt_cell"] + r["pt_t"]) / 8.0
+    for a in range(3):
+        np.testing.assert_allclose(np.bincount(org, weights=W * xu[:, a]), u[:, a], atol=1e-12)
+    split = r["count"] > 1
+    assert split.any()
+    per_axis = n + (n % 2)
+    assert set(np.unique(r["count"])) <= {1, per_axis, per_axis ** 2, per_axis ** 3}
+    # split points stay within d of a plane, in the cell they are assigned to
+    sp = r["count"][org] > 1
+    tt = r["pt_t"][sp]
+    moved = r["axes"][org[sp]].astype(bool)
+    dist = np.minimum(tt, 1 - tt)
+    assert np.all(dist[moved] <= dt + 1e-12)
+
+
+def test_split_count_matches_paper_run():
+    """§3.2: 475 of 23040 charges were split with 2d = 1/1024 in 8^3 cells.
+    Splitting at the 7 interior planes per axis predicts
+    23040 (1 - (1 - 7/1024)^3) = 469 +- 22; splitting at the walls too would
+    predict 536."""
+    counts = []
+    for seed in range(11, 16):
+        pos, q, box = inputs.uniform_pm1(23040, seed)
+        r = oracle.fmm(pos, q, box, depth=3, n=4, continuous=True, keep=True)
+        counts.append(int(np.sum(r["count"] > 1)))
+    m = np.mean(counts)
+    assert abs(m - 469.4) < 3 * 22 / np.sqrt(len(counts)) + 5, counts
+    assert abs(475 - 469.4) < 3 * 22
+
+
+@pytest.mark.parametrize("n,periodic", [(4, False), (5, False), (4, True), (5, True)])
+def test_continuity_across_planes(n, periodic):
+    """§3.2 / Fig. 6: with the split, the energy is continuous when a particle
+    crosses a plane of the finest cells (and the periodic wall, §4.2);
+    without it the energy jumps there."""
+    pos, q, box = inputs.uniform_pm1(1500, 71)
+    planes = [np.float32(0.5), np.float32(0.25)] + ([np.float32(0.0)] if periodic else [])
+    for plane in planes:
+        below = np.nextafter(plane, np.float32(-1)) if plane > 0 else np.float32(1) - np.float32(2 ** -24)
+        jumps, slope = {}, {}
+        for cont in (False, True):
+            Es, Fs = [], []
+            for x in (below, plane):
+                p = pos.copy()
+                p[0, 0] = x
+                o = oracle.fmm(p, q, box, depth=3, n=n, periodic=periodic, continuous=cont,
+                               keep=False)
+                Es.append(o["E"])
+                Fs.append(abs(o["F"][0, 0]))
+            jumps[cont] = abs(Es[1] - Es[0])
+            # a smooth energy changes by about |F| dx over the move
+            dx = float(plane) - float(below) if plane > 0 else 2.0 ** -24
+            slope[cont] = max(Fs) * dx
+        assert jumps[True] < 3 * slope[True] + 1e-12 * abs(Es[0]), (plane, jumps, slope)
+        assert jumps[False] > 20 * slope[False], (plane, jumps, slope)
+
+
+@pytest.mark.parametrize("continuous,periodic,n", [(False, False, 4), (True, False, 4),
+                                                   (True, False, 5), (True, True, 4)])
+def test_forces_are_minus_energy_gradient(continuous, periodic, n):
+    """The adjoint force is -dE/dx of the FMM energy (far part: the paper's
+    Psi(v'_a) of §2.2; split axes: the weight derivative).  Central
+    differences with a power-of-two step, particles away from the split-band
+    edges."""
+    pos, q, box = inputs.uniform_pm1(600, 81)
+    pos = (pos * np.float32(0.5) + np.float32(0.25)).astype(np.float32)  # exact in fp32
+    h = np.float32(2.0 ** -14)
+    dt = 1.0 / 8
+    r = oracle.fmm(pos, q, box, depth=3, n=n, periodic=periodic, continuous=continuous, dt=dt)
+    t = r["t"]
+    edge = np.minimum(np.abs(t - dt), np.abs(1 - t - dt)).min(axis=1) * 8
+    cand = np.where(edge > 4 * h)[0]
+    if continuous:
+        cand = cand[r["count"][cand] > 1][:6].tolist() + cand[r["count"][cand] == 1][:3].tolist()
+    else:
+        cand = cand[:8].tolist()
+    for i in cand:
+        for a in range(3):
+            Ep = []
+            for s in (1, -1):
+                p = pos.copy()
+                p[i, a] = p[i, a] + s * h
+                Ep.append(oracle.fmm(p, q, box, depth=3, n=n, periodic=periodic,
+                                     continuous=continuous, dt=dt, keep=False)["E"])
+            fd = -(Ep[0] - Ep[1]) / (2 * float(h))
+            assert abs(fd - r["F"][i, a]) < 2e-4 * max(1.0, np.abs(r["F"][i]).max()), (i, a, fd, r["F"][i, a])
+
+
+def test_sampled_mode_matches_full():
+    pos, q, box = inputs.uniform_pm1(3000, 91)
+    full = oracle.fmm(pos, q, box, depth=3, n=4, continuous=True, periodic=True)
+    s = np.array([0, 17, 999, 2999])
+    part = oracle.fmm(pos, q, box, depth=3, n=4, continuous=True, periodic=True, sample=s)
+    np.testing.assert_allclose(part["phi"], full["phi"][s], rtol=1e-14)
+    np.testing.assert_allclose(part["F"], full["F"][s], rtol=1e-13, atol=1e-13)
