@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the replacement-based FMM (energy + potentials + forces).
+
+Workload (default "uniform1m"): 1,048,576 particles uniform in the unit cube,
+charges uniform in [-1, 1] shifted to zero net charge, open boundary,
+continuous (split) form with 2d = w/128, octree depth 5, p = 4, FP32.
+
+One step = one full evaluation: binning, split, sort, upward pass, downward
+pass, far and near field, recombination, FP64 energy.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on the host cores, on the same workload.  Multi-GPU (torchrun): every rank
+evaluates its own replica of the workload (weak scaling, no collective on the
+data path); the value is the particles of all ranks over the slowest rank.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM energy+forces Mparticles/s"
+UNIT = "Mparticles/s"
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+P2P_FLOPS_PER_PAIR = 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def m2l_cell_pairs(depth, periodic):
+    """Cell pairs of the interaction lists over all levels (189 per interior cell)."""
+    total = 0
+    for l in range(1 if periodic else 2, depth + 1):
+        S = 1 << l
+        for par in range(8):
+            b = [(par >> a) & 1 for a in range(3)]
+            for oz in range(-2 - b[2], 4 - b[2]):
+                for oy in range(-2 - b[1], 4 - b[1]):
+                    for ox in range(-2 - b[0], 4 - b[0]):
+                        if max(abs(ox), abs(oy), abs(oz)) <= 1:
+                            continue
+                        c = 1
+                        for a, o in enumerate((ox, oy, oz)):
+                            cs = range(b[a], S, 2)
+                            c *= len(cs) if periodic else sum(1 for x in cs if 0 <= x + o < S)
+                        total += c
+    return total
+
+
+def p2p_pairs(plan, depth, periodic):
+    """Ordered charge pairs of the near field (27 cells, same-particle pairs excluded)."""
+    import numpy as np
+    start = plan.dump("start").astype(np.int64)
+    origin = plan.dump("origin")
+    S = 1 << depth
+    cnt = np.diff(start)
+    # Morton key -> (x, y, z)
+    keys = np.arange(S ** 3, dtype=np.int64)
+    xyz = np.zeros((S ** 3, 3), np.int64)
+    for bit in range(depth):
+        for a in range(3):
+            xyz[:, a] |= ((keys >> (3 * bit + a)) & 1) << bit
+    grid = np.zeros((S, S, S), np.int64)
+    grid[xyz[:, 2], xyz[:, 1], xyz[:, 0]] = cnt
+    nb = np.zeros_like(grid)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if periodic:
+                    nb += np.roll(grid, shift=(-dz, -dy, -dx), axis=(0, 1, 2))
+                else:
+                    g = np.zeros((S + 2, S + 2, S + 2), np.int64)
+                    g[1:-1, 1:-1, 1:-1] = grid
+                    nb += g[1 + dz:S + 1 + dz, 1 + dy:S + 1 + dy, 1 + dx:S + 1 + dx]
+    m = np.bincount(origin)
+    return int(np.sum(grid * nb) - np.sum(m.astype(np.int64) ** 2))
+
+
+def run_reference(args, workload, world, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2212_13080_gb300 import inputs
+    w = inputs.workload(workload)
+    pos, q, box = w["pos"], w["q"], w["box"]
+    n = len(q)
+    kw = dict(depth=w["depth"], n=w["p"], periodic=w["periodic"], continuous=w["continuous"],
+              keep=False)
+    for _ in range(args.warmup):
+        oracle.fmm(pos, q, box, **kw)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.fmm(pos, q, box, **kw)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.mean(ts)
+    cores = os.cpu_count()
+    v = n / t / 1e6
+    sample = "whole workload (%d particles) per step, oracle.fmm FP64, OpenMP" % n
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload, "n": n, "depth": w["depth"],
+                                        "p": w["p"], "periodic": w["periodic"],
+                                        "continuous": w["continuous"]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(workload):
+    import oracle
+    from paper_2212_13080_gb300 import inputs
+    w = inputs.workload(workload)
+    n = len(w["q"])
+    t0 = time.perf_counter()
+    oracle.fmm(w["pos"], w["q"], w["box"], depth=w["depth"], n=w["p"], periodic=w["periodic"],
+               continuous=w["continuous"], keep=False)
+    t = time.perf_counter() - t0
+    return {"value": n / t / 1e6, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "whole workload (%d particles), one oracle.fmm run (FP64, OpenMP), %.1f s"
+                      % (n, t)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uniform1m")
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, args.workload, world, rank)
+        return
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2212_13080_gb300 import FMM, inputs
+    w = inputs.workload(args.workload)
+    pos_h, q_h, box = w["pos"], w["q"], w["box"]
+    n = len(q_h)
+    dev = torch.device("cuda", local)
+    pos = torch.from_numpy(pos_h).to(dev)
+    q = torch.from_numpy(q_h).to(dev)
+    mk = dict(periodic=w["periodic"], continuous=w["continuous"], precision=args.precision,
+              max_n=n)
+    plan = FMM(box, w["depth"], w["p"], sync=False, **mk)
+    plan.set_timing(True)
+    ws = plan.workspace(n)
+    out = {"potential": torch.empty(n, device=dev), "energy": torch.empty(1, dtype=torch.float64, device=dev),
+           "forces": torch.empty((n, 3), device=dev)}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.eval(pos, q, workspace=ws, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    rc = plan_status(plan, ws)
+    if rc:
+        raise SystemExit("evaluation failed: status %d" % rc)
+
+    # algorithmic work of one step
+    pairs = p2p_pairs(plan, w["depth"], w["periodic"])
+    cellpairs = m2l_cell_pairs(w["depth"], w["periodic"])
+    m2l_flops = 2.0 * (w["p"] ** 6) * cellpairs
+    p2p_flops = float(P2P_FLOPS_PER_PAIR) * pairs
+
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    stage_tot = {}
+    launches = 0
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+        st = plan.stats()
+        launches += st["launches"]
+        for k, v in st["stage_ms"].items():
+            stage_tot[k] = stage_tot.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    rc = plan_status(plan, ws)
+    if rc:
+        raise SystemExit("evaluation failed: status %d" % rc)
+    t_step = statistics.mean(ms)
+    if dist is not None:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = world * n / (t_step * 1e-3) / 1e6
+    stage_ms = {k: v / args.steps for k, v in stage_tot.items()}
+
+    # end to end through the public API with host buffers (pinned)
+    plan_e2e = FMM(box, w["depth"], w["p"], sync=True, **mk)
+    pos_p = torch.from_numpy(pos_h).pin_memory()
+    q_p = torch.from_numpy(q_h).pin_memory()
+    for _ in range(2):
+        plan_e2e.eval(pos_p, q_p)
+    torch.cuda.synchronize()
+    te = []
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        r = plan_e2e.eval(pos_p, q_p)
+        te.append(time.perf_counter() - t0)
+    e2e_v = world * n / statistics.mean(te) / 1e6
+    h2d = pos_p.numel() * 4 + q_p.numel() * 4
+    d2h = r["potential"].numel() * 4 + r["forces"].numel() * 4 + 8
+
+    # roofline of the dominant kernel stage
+    hbm, peak_kind = _peaks()
+    dom = max(("m2l", "p2p"), key=lambda k: stage_ms.get(k, 0.0))
+    if dom == "p2p":
+        ach = p2p_flops / (stage_ms["p2p"] * 1e-3) / 1e12
+        roof = {"kernel": "k_p2p", "bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                "algorithmic": "%d ordered pairs x %d flop" % (pairs, P2P_FLOPS_PER_PAIR),
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
+    else:
+        ach = m2l_flops / (stage_ms["m2l"] * 1e-3) / 1e12
+        roof = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": ach,
+                "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_ALU_PEAK_TFLOPS,
+                "traffic": None,
+                "algorithmic": "%d cell pairs x 2 p^6 flop (all levels per step)" % cellpairs,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
+    roof["hbm_peak_gbs"] = hbm
+    roof["hbm_peak_source"] = peak_kind
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "depth": w["depth"], "p": w["p"],
+                   "periodic": w["periodic"], "continuous": w["continuous"],
+                   "split_2d_over_w": 1 / 128, "outputs": "potential+energy+forces",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "stage_ms": stage_ms,
+        "pairs_per_s": pairs / (t_step * 1e-3),
+        "p2p_tflops": p2p_flops / (stage_ms.get("p2p", 1e9) * 1e-3) / 1e12,
+        "m2l_tflops": m2l_flops / (stage_ms.get("m2l", 1e9) * 1e-3) / 1e12,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    plan.close()
+    plan_e2e.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def plan_status(plan, ws):
+    from paper_2212_13080_gb300 import _binding as B
+    import ctypes
+    import torch
+    ws_al = plan._aligned(ws)
+    return B.fmm_status(plan._h, ctypes.c_void_p(ws_al.data_ptr()),
+                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+if __name__ == "__main__":
+    main()

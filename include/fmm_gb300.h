@@ -1,0 +1,228 @@
+/*
+ * fmm_gb300.h — C ABI of the GB300 (sm_103a) replacement-based fast multipole
+ * method of Y. Kajima, "Notes on the Fast Multipole Method" (arXiv:2212.13080).
+ *
+ * The method (§2.2) computes, for N point charges in a cubic box, the Coulomb
+ * potential of every charge, the total energy and the forces:
+ *   - the box is divided into an octree of depth `depth` (§2.2 step 1);
+ *   - the charges of every finest cell are replaced by p^3 charges on the
+ *     cell's p-division points (replacement, eq. ex66), shifted up the tree
+ *     (shift, eq. threethree);
+ *   - well-separated cells interact through the p^3 x p^3 bilinear form of the
+ *     grid charges (eq. bilinear), passed down the tree as linear functionals
+ *     (§2.2 step 3) and evaluated at the charges (step 4, and the far-field
+ *     force at the end of §2.2);
+ *   - the near field is summed directly over each finest cell's 27-cell
+ *     neighbourhood (step 5).
+ * The continuous form (§2.3) first splits every charge that lies closer than
+ * d to a plane of the finest cells into p (p^2, p^3) charges on a segment of
+ * length 2d across the plane; the periodic form (§4.2) also splits at the box
+ * walls and adds the lattice sum of the box's far images (Ewald, tin-foil).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: FMM_OK (0) or one FMM_ERR_* code.
+ *     No C++ exception crosses this boundary.  fmm_strerror() names a code.
+ *   - Device pointers are CUDA device (or managed) memory of the current
+ *     device; the caller owns them.  Host pointers are marked "host".
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     All device work of a call is queued on it, in order.
+ *   - Positions are float32, row-major (n, 3): x0 y0 z0 x1 y1 z1 ...
+ *     Charges are float32 (n).  Output arrays are float32, or float64 when
+ *     the plan's precision is FMM_PREC_FP64.
+ *   - Units: potential phi_i = sum_{j != i} q_j / r_ij (per unit charge),
+ *     energy E = 1/2 sum_i q_i phi_i, force F_i = -dE/dx_i, in the units of
+ *     the positions and charges (Coulomb constant 1, §3.1).
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define FMM_OK 0
+#define FMM_ERR_ARG 1            /* invalid argument (depth, p, box, sizes, null) */
+#define FMM_ERR_OOM 2            /* device allocation failed, or plan too large */
+#define FMM_ERR_OUT_OF_BOX 3     /* open form: a position outside [x0, x0+L) */
+#define FMM_ERR_NONFINITE 4      /* a position is NaN or infinite */
+#define FMM_ERR_SPLIT_OVERFLOW 5 /* continuous form: more split charges than the
+                                    workspace was sized for (fmm_opts_t.split_capacity) */
+#define FMM_ERR_TIMEOUT 6        /* a bounded device-side wait gave up */
+#define FMM_ERR_CUDA 7           /* a CUDA runtime call failed */
+#define FMM_ERR_STATE 8          /* fmm_backward without a matching fmm_eval */
+#define FMM_ERR_WORKSPACE 9      /* workspace pointer null, misaligned or too small */
+#define FMM_ERR_UNSUPPORTED 10   /* combination not built (e.g. tensor-core M2L for this p) */
+
+/* ---- precision of the far-field contraction (and of everything else) ----- */
+#define FMM_PREC_FP32 0   /* FP32 everywhere (SIMT bilinear forms) */
+#define FMM_PREC_FP64 1   /* FP64 everywhere; outputs are float64 */
+#define FMM_PREC_TF32X3 2 /* bilinear forms on tcgen05 tensor cores, 3-pass split TF32,
+                             FP32 accumulate; rest FP32 */
+
+/* ---- flags of fmm_eval ---------------------------------------------------- */
+#define FMM_FORCE_ADJOINT 0 /* forces = -dE/dx of the FMM energy (default) */
+#define FMM_FORCE_PAPER 1   /* split axes: sum of the forces the split charges feel (§2.3) */
+
+typedef struct fmm_plan_s *fmm_plan_t;
+
+typedef struct {
+    int continuous;        /* 1: split near the planes of the finest cells (§2.3, §4.2) */
+    double split_ratio;    /* d / finest-cell width, in (0, 0.5); <= 0 selects 1/256
+                              (2d = w/128; §3.2 uses 2d = 1/1024 with w = 1/8) */
+    double split_capacity; /* workspace holds split_capacity * n charges after the split;
+                              <= 0 selects 2.0 (continuous) */
+    int precision;         /* FMM_PREC_* */
+    int force_mode;        /* FMM_FORCE_ADJOINT or FMM_FORCE_PAPER */
+    int sync;              /* 1 (default when opts is NULL): fmm_eval waits for the device
+                              and returns device-side errors; 0: fmm_eval returns after
+                              queueing, fmm_status() reports them later */
+} fmm_opts_t;
+
+/* Fills *opts with the defaults (continuous 0, split_ratio 1/256, split_capacity 2,
+ * precision FP32, adjoint forces, sync 1). */
+void fmm_opts_default(fmm_opts_t *opts);
+
+/*
+ * fmm_plan_create — build the tables of one (box, depth, p, form) (§2.1, §2.2).
+ *   box     host, 4 doubles: x0, y0, z0 (lower corner) and edge length L > 0.
+ *   depth   octree depth l_f, 2 <= depth <= 8 (§2.2 step 1 needs l_f >= 2).
+ *   p       points per cell edge (the paper's order n), 2 <= p <= 8.
+ *   periodic 0: open boundary; 1: periodic box (§4.2).
+ *   opts    host, nullable (defaults).
+ *   max_n   largest particle count fmm_eval will be given with this plan.
+ * Builds in FP64 on the host: the p-division points and Lagrange coefficients,
+ * the two child->parent shift matrices (eq. trans), the 316 unit-cell
+ * bilinear-form kernels 1/|a - (o + b)| for |o|_inf <= 3 (eq. bilinear), and
+ * (periodic) the Ewald lattice kernel of the box's far images; uploads them to
+ * the current device.  The plan owns those tables (device memory freed by
+ * fmm_plan_destroy).  Errors: FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA.
+ */
+int fmm_plan_create(fmm_plan_t *plan, const double box[4], int depth, int p, int periodic,
+                    const fmm_opts_t *opts, int64_t max_n);
+
+/* Frees the plan's device tables.  NULL is accepted. */
+void fmm_plan_destroy(fmm_plan_t plan);
+
+/*
+ * fmm_workspace_size — bytes of device workspace fmm_eval needs for n
+ * particles (n <= max_n).  The workspace holds the sorted charges, the grid
+ * charges Phi and functionals L of every level, and the status word; it is
+ * the caller's memory (any 256-byte aligned device allocation) and it is the
+ * state fmm_backward reuses.  Errors: FMM_ERR_ARG.
+ */
+int fmm_workspace_size(fmm_plan_t plan, int64_t n, size_t *bytes);
+
+/*
+ * fmm_eval — one evaluation of §2.2 (+ §2.3 split, §4.2 periodic).
+ *   n          number of particles, 0 <= n <= max_n (n = 0: energy 0).
+ *   pos        device, float32 (n,3).  Open form: every position must lie in
+ *              [x0, x0+L)^3 (else FMM_ERR_OUT_OF_BOX); periodic: wrapped.
+ *   q          device, float32 (n).
+ *   potential  device, (n) float32 (float64 for FP64 plans), nullable.
+ *   energy     device, 1 double, nullable.
+ *   forces     device, (n,3) float32 (float64 for FP64 plans), nullable.
+ *   workspace  device, >= fmm_workspace_size(plan, n) bytes, 256-byte aligned.
+ *   stream     cudaStream_t as void*.
+ * With opts.sync = 1 the call waits for the device and returns the device
+ * status (FMM_ERR_OUT_OF_BOX, FMM_ERR_NONFINITE, FMM_ERR_SPLIT_OVERFLOW);
+ * outputs are then undefined if the status is not FMM_OK.
+ */
+int fmm_eval(fmm_plan_t plan, int64_t n, const float *pos, const float *q, void *potential,
+             double *energy, void *forces, void *workspace, size_t workspace_bytes,
+             void *stream);
+
+/*
+ * fmm_backward — adjoint of the energy (end of §2.2; forces as -dE/dx):
+ * grad_pos = -F * grad_energy, grad_q = phi * grad_energy, recomputing only the
+ * per-charge far-field gradients and near-field forces from the tree, grid
+ * charges and functionals that the last fmm_eval on this workspace left in it
+ * (no binning, sort, upward or downward pass).
+ *   grad_energy  device, 1 double (dLoss/dE).
+ *   grad_pos     device, (n,3) float32 (float64 for FP64 plans), nullable.
+ *   grad_q       device, (n) float32 (float64 for FP64 plans), nullable.
+ * pos and q must be the arrays the last fmm_eval was given.  Errors:
+ * FMM_ERR_STATE if the workspace holds no evaluation of this plan and n.
+ */
+int fmm_backward(fmm_plan_t plan, int64_t n, const float *pos, const float *q,
+                 const double *grad_energy, void *grad_pos, void *grad_q, void *workspace,
+                 size_t workspace_bytes, void *stream);
+
+/*
+ * fmm_status — device-side status of the last fmm_eval/fmm_backward on this
+ * workspace (waits on `stream`).  For opts.sync = 0.
+ */
+int fmm_status(fmm_plan_t plan, const void *workspace, void *stream);
+
+/*
+ * fmm_debug_dump — copies one intermediate of the last evaluation on
+ * `workspace` to host memory `dst` (host, `bytes` long), after waiting on
+ * `stream`.  Layouts:
+ *   FMM_DUMP_COUNTS   int32 [4]: n, number of charges after the split, number of
+ *                     finest cells, number of coincident pairs skipped
+ *   FMM_DUMP_KEYS     uint32 [n_eff]: Morton key of each charge, emitted order
+ *   FMM_DUMP_ORIGIN   int32 [n_eff]: particle of each charge, sorted order
+ *   FMM_DUMP_PERM     int32 [n_eff]: emitted index of each sorted slot
+ *   FMM_DUMP_START    int32 [cells+1]: first sorted slot of each finest cell (Morton)
+ *   FMM_DUMP_POINTS   real [n_eff][4]: (t_x, t_y, t_z, q_eff) per sorted slot,
+ *                     t in finest-cell units (real = float, double for FP64 plans)
+ *   FMM_DUMP_PHI      real [level][8^level][p^3]: grid charges, natural cell
+ *                     order (cz*S + cy)*S + cx, levels 0..depth
+ *   FMM_DUMP_LOCAL    real, same layout: functionals L (Psi_C(v) = L_C . v)
+ * Errors: FMM_ERR_ARG (unknown item or dst too small).
+ */
+#define FMM_DUMP_COUNTS 0
+#define FMM_DUMP_KEYS 1
+#define FMM_DUMP_ORIGIN 2
+#define FMM_DUMP_PERM 3
+#define FMM_DUMP_START 4
+#define FMM_DUMP_POINTS 5
+#define FMM_DUMP_PHI 6
+#define FMM_DUMP_LOCAL 7
+int fmm_debug_dump(fmm_plan_t plan, int what, const void *workspace, void *dst, size_t bytes,
+                   void *stream);
+
+/* Bytes fmm_debug_dump needs for `what` after the last evaluation on
+ * `workspace` (waits on `stream`). */
+int fmm_debug_size(fmm_plan_t plan, int what, const void *workspace, size_t *bytes,
+                   void *stream);
+
+/*
+ * Stage timing and launch accounting (tracing).
+ * fmm_set_timing(plan, 1) makes every later fmm_eval/fmm_backward of the plan
+ * bracket each stage's kernels with CUDA events on the call's stream;
+ * fmm_get_stats() waits for them and reports the device time per stage (ms)
+ * of the last call, and the number of kernels that call launched (counted
+ * whether or not timing is on).  Stage ids: FMM_STAGE_*.
+ */
+#define FMM_STAGE_BIN 0      /* binning and split (§2.2 step 1, §2.3) */
+#define FMM_STAGE_SORT 1     /* finest-cell ranges and stable sort */
+#define FMM_STAGE_P2M 2      /* replacement at the finest cells (eq. ex66) */
+#define FMM_STAGE_M2M 3      /* shifts upward (eq. threethree) and halo */
+#define FMM_STAGE_M2L 4      /* bilinear forms of the interaction lists, lattice term */
+#define FMM_STAGE_L2L 5      /* shift transposes downward */
+#define FMM_STAGE_L2P 6      /* far field at the charges */
+#define FMM_STAGE_P2P 7      /* near field over 27 cells */
+#define FMM_STAGE_UNSPLIT 8  /* recombination, outputs, FP64 energy */
+#define FMM_NSTAGES 9
+typedef struct {
+    int launches;                    /* kernels launched by the last call */
+    int timed;                       /* 1 if stage_ms is valid */
+    double stage_ms[FMM_NSTAGES];    /* device time per stage of the last call */
+} fmm_stats_t;
+int fmm_set_timing(fmm_plan_t plan, int on);
+int fmm_get_stats(fmm_plan_t plan, fmm_stats_t *stats);
+
+/* Static string naming a status code. */
+const char *fmm_strerror(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int fmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM_GB300_H */

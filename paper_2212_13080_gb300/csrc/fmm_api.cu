@@ -1,0 +1,601 @@
+// C ABI of the GB300 replacement-FMM library: plans, tables, workspace layout
+// and the order of the stages of one evaluation.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+void far_set_attributes();
+}
+
+using namespace fmm;
+
+struct fmm_plan_s {
+    int depth, p, periodic;
+    fmm_opts_t opts;
+    double box[4];
+    int64_t max_n;
+    int device;
+    bool fp64;
+    void *Kunit;  // [343][p^3][p^3] unit-cell bilinear-form kernels, plan real type
+    void *Klat;   // [p^3][p^3] lattice kernel (periodic form)
+    Coef<float> cf;
+    Coef<double> cd;
+    Geom geom;
+    const void *last_ws;
+    int64_t last_n;
+    int *h_hdr;  // pinned copy of the workspace header
+    bool timing;
+    cudaEvent_t ev[512];
+    int nev_created;
+    Tracer last;  // launches and stage events of the last call
+};
+
+static int g_plan_counter = 0;
+
+// ---------------------------------------------------------------------------
+// FP64 tables (host)
+// ---------------------------------------------------------------------------
+namespace {
+
+double node(int p, int i) { return (double)i / (double)(p - 1); }
+
+// §2.1.1: Lagrange basis g_i(x) on the p-division points of [0,1]
+double lagrange(int p, int i, double x) {
+    double v = 1.0;
+    for (int k = 0; k < p; k++)
+        if (k != i) v *= (x - node(p, k)) / (node(p, i) - node(p, k));
+    return v;
+}
+
+// Ewald-regularised sum over the lattice vectors m outside {-1,0,1}^3 of
+// 1/|r + m| for r in [-1,1]^3 (unit cubic box, tin-foil boundary, neutralising
+// background constant -pi/alpha^2): the Ewald pair potential of the unit box
+// minus its 27 nearest image terms (§4.2, periodic form, level 0).
+double far_image_sum(double rx, double ry, double rz) {
+    const double alpha = 2.0;
+    const int RM = 7, HM = 7;
+    const double spi = std::sqrt(M_PI);
+    double real_part = 0.0;
+    for (int mz = -RM; mz <= RM; mz++)
+        for (int my = -RM; my <= RM; my++)
+            for (int mx = -RM; mx <= RM; mx++) {
+                double x = rx + mx, y = ry + my, z = rz + mz;
+                double s = std::sqrt(x * x + y * y + z * z);
+                bool near = std::abs(mx) <= 1 && std::abs(my) <= 1 && std::abs(mz) <= 1;
+                if (near) {
+                    // erfc(as)/s - 1/s = -erf(as)/s, -> -2a/sqrt(pi) at s = 0
+                    real_part += (s > 0.0) ? -std::erf(alpha * s) / s : -2.0 * alpha / spi;
+                } else {
+                    real_part += std::erfc(alpha * s) / s;
+                }
+            }
+    double recip = 0.0;
+    for (int hz = 0; hz <= HM; hz++)
+        for (int hy = -HM; hy <= HM; hy++)
+            for (int hx = -HM; hx <= HM; hx++) {
+                // half space hz > 0, plus hz == 0 with (hy, hx) > 0; pairs +-h
+                if (hz == 0 && (hy < 0 || (hy == 0 && hx <= 0))) continue;
+                double h2 = (double)(hx * hx + hy * hy + hz * hz);
+                double w = std::exp(-M_PI * M_PI * h2 / (alpha * alpha)) / (M_PI * h2);
+                recip += 2.0 * w * std::cos(2.0 * M_PI * (hx * rx + hy * ry + hz * rz));
+            }
+    return real_part + recip - M_PI / (alpha * alpha);
+}
+
+template <typename real>
+void fill_coef(int p, Coef<real> &C) {
+    memset(&C, 0, sizeof(C));
+    for (int i = 0; i < p; i++) {
+        C.tau[i] = (real)node(p, i);
+        double den = 1.0;
+        for (int k = 0; k < p; k++)
+            if (k != i) den *= node(p, i) - node(p, k);
+        C.cinv[i] = (real)(1.0 / den);
+    }
+    // eq. (trans): (J,i) entry = parent basis g_J at the child node (h + tau_i)/2
+    for (int h = 0; h < 2; h++)
+        for (int J = 0; J < p; J++)
+            for (int i = 0; i < p; i++) C.G[h][J * p + i] = (real)lagrange(p, J, 0.5 * (h + node(p, i)));
+}
+
+template <typename real>
+int upload_tables(fmm_plan_t P) {
+    const int p = P->p, p3 = p * p * p;
+    const size_t nk = (size_t)343 * p3 * p3;
+    std::vector<real> K(nk, (real)0);
+    for (int oz = -3; oz <= 3; oz++)
+        for (int oy = -3; oy <= 3; oy++)
+            for (int ox = -3; ox <= 3; ox++) {
+                if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
+                size_t base = (size_t)(((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3)) * p3 * p3;
+                for (int a = 0; a < p3; a++) {
+                    double ax = node(p, a % p), ay = node(p, (a / p) % p), az = node(p, a / (p * p));
+                    for (int b = 0; b < p3; b++) {
+                        double dx = ax - (ox + node(p, b % p));
+                        double dy = ay - (oy + node(p, (b / p) % p));
+                        double dz = az - (oz + node(p, b / (p * p)));
+                        K[base + (size_t)a * p3 + b] = (real)(1.0 / std::sqrt(dx * dx + dy * dy + dz * dz));
+                    }
+                }
+            }
+    if (cudaMalloc(&P->Kunit, nk * sizeof(real)) != cudaSuccess) return FMM_ERR_OOM;
+    if (cudaMemcpy(P->Kunit, K.data(), nk * sizeof(real), cudaMemcpyHostToDevice) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    if (P->periodic) {
+        // psi depends on a - b only: (2p-1)^3 distinct arguments
+        const int m = 2 * p - 1;
+        std::vector<double> tab((size_t)m * m * m);
+        for (int dz = 0; dz < m; dz++)
+            for (int dy = 0; dy < m; dy++)
+                for (int dx = 0; dx < m; dx++)
+                    tab[((size_t)dz * m + dy) * m + dx] =
+                        far_image_sum((dx - (p - 1)) / (double)(p - 1), (dy - (p - 1)) / (double)(p - 1),
+                                      (dz - (p - 1)) / (double)(p - 1));
+        std::vector<real> Kl((size_t)p3 * p3);
+        for (int a = 0; a < p3; a++)
+            for (int b = 0; b < p3; b++) {
+                int dx = a % p - b % p + p - 1, dy = (a / p) % p - (b / p) % p + p - 1,
+                    dz = a / (p * p) - b / (p * p) + p - 1;
+                Kl[(size_t)a * p3 + b] = (real)tab[((size_t)dz * m + dy) * m + dx];
+            }
+        if (cudaMalloc(&P->Klat, Kl.size() * sizeof(real)) != cudaSuccess) return FMM_ERR_OOM;
+        if (cudaMemcpy(P->Klat, Kl.data(), Kl.size() * sizeof(real), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return FMM_ERR_CUDA;
+    }
+    return FMM_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+WsLayout make_layout(const fmm_plan_t P, int64_t n) {
+    WsLayout W;
+    memset(&W, 0, sizeof(W));
+    const size_t rs = P->fp64 ? 8 : 4;
+    const int p3 = P->p * P->p * P->p;
+    const bool cont = P->opts.continuous != 0;
+    W.ncell = (int64_t)1 << (3 * P->depth);
+    if (cont) {
+        double f = P->opts.split_capacity > 0 ? P->opts.split_capacity : 2.0;
+        W.cap = (int64_t)std::ceil(f * (double)n) + 64;
+        if (W.cap < n) W.cap = n;
+    } else {
+        W.cap = n;
+    }
+    if (W.cap < 1) W.cap = 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o += align256(bytes);
+        return r;
+    };
+    W.hdr = take(256);
+    W.count = take(cont ? n * 4 : 0);
+    W.offset = take(cont ? (n + 1) * 4 : 0);
+    W.axes = take(cont ? n : 0);
+    W.e_key = take(W.cap * 4);
+    W.e_pt = take(W.cap * 4 * rs);
+    W.e_wd = take(cont ? W.cap * 4 * rs : 0);
+    W.e_origin = take(W.cap * 4);
+    W.leaf_count = take(W.ncell * 4);
+    W.leaf_start = take((W.ncell + 1) * 4);
+    W.cursor = take(W.ncell * 4);
+    W.tmp = take(W.cap * 4);
+    W.perm = take(W.cap * 4);
+    W.inv = take(W.cap * 4);
+    W.s_pt = take(W.cap * 4 * rs);
+    W.s_origin = take(W.cap * 4);
+    W.out_pt = take(W.cap * 4 * rs);
+    int64_t ph = 0, lc = 0;
+    for (int l = 0; l <= P->depth; l++) {
+        W.phi_level[l] = ph * p3;
+        W.loc_level[l] = lc * p3;
+        ph += phi_level_cells(l);
+        lc += loc_level_cells(l);
+    }
+    W.phi_level[P->depth + 1] = ph * p3;
+    W.loc_level[P->depth + 1] = lc * p3;
+    W.phi = take((size_t)ph * p3 * rs);
+    W.loc = take((size_t)lc * p3 * rs);
+    int64_t mx = n > W.ncell ? n : W.ncell;
+    W.scan_blocks = (int)(mx / 2048 + 2);
+    W.scan_tmp = take((size_t)(W.scan_blocks + 1) * 4);
+    W.epart = take((size_t)((n + 255) / 256 + 1) * 8);
+    W.total = o;
+    return W;
+}
+
+template <typename real>
+Ptrs<real> make_ptrs(const WsLayout &W, void *ws) {
+    char *b = (char *)ws;
+    Ptrs<real> P;
+    typedef typename Vec4<real>::T R4;
+    P.hdr = (WsHeader *)(b + W.hdr);
+    P.count = (int *)(b + W.count);
+    P.offset = (int *)(b + W.offset);
+    P.axes = (unsigned char *)(b + W.axes);
+    P.e_key = (uint32_t *)(b + W.e_key);
+    P.e_pt = (R4 *)(b + W.e_pt);
+    P.e_wd = (R4 *)(b + W.e_wd);
+    P.e_origin = (int *)(b + W.e_origin);
+    P.leaf_count = (int *)(b + W.leaf_count);
+    P.leaf_start = (int *)(b + W.leaf_start);
+    P.cursor = (int *)(b + W.cursor);
+    P.tmp = (int *)(b + W.tmp);
+    P.perm = (int *)(b + W.perm);
+    P.inv = (int *)(b + W.inv);
+    P.s_pt = (R4 *)(b + W.s_pt);
+    P.s_origin = (int *)(b + W.s_origin);
+    P.out_pt = (R4 *)(b + W.out_pt);
+    P.phi = (real *)(b + W.phi);
+    P.loc = (real *)(b + W.loc);
+    P.scan_tmp = (int *)(b + W.scan_tmp);
+    P.epart = (double *)(b + W.epart);
+    return P;
+}
+
+int status_to_error(int st) {
+    if (st & ST_NONFINITE) return FMM_ERR_NONFINITE;
+    if (st & ST_OUT_OF_BOX) return FMM_ERR_OUT_OF_BOX;
+    if (st & ST_SPLIT_OVERFLOW) return FMM_ERR_SPLIT_OVERFLOW;
+    return FMM_OK;
+}
+
+__global__ void k_mark_valid(WsHeader *hdr, long long tag) {
+    hdr->valid = 1;
+    hdr->tag = tag;
+}
+
+int check_ws(const fmm_plan_t P, int64_t n, const void *ws, size_t bytes) {
+    if (!ws) return FMM_ERR_WORKSPACE;
+    if (((uintptr_t)ws) & 255) return FMM_ERR_WORKSPACE;
+    WsLayout W = make_layout(P, n);
+    if (bytes < W.total) return FMM_ERR_WORKSPACE;
+    return FMM_OK;
+}
+
+int finish(fmm_plan_t P, const WsHeader *hdr, cudaStream_t st, bool sync) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return FMM_ERR_CUDA;
+    if (!sync) return FMM_OK;
+    if (cudaMemcpyAsync(P->h_hdr, hdr, sizeof(WsHeader), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_ERR_CUDA;
+    return status_to_error(P->h_hdr[0]);
+}
+
+template <typename real>
+int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *potential,
+              double *energy, real *forces, void *ws, cudaStream_t st, Tracer &tr) {
+    WsLayout W = make_layout(P, n);
+    Ptrs<real> ptr = make_ptrs<real>(W, ws);
+    const Coef<real> &C = *reinterpret_cast<const Coef<real> *>(P->fp64 ? (const void *)&P->cd
+                                                                        : (const void *)&P->cf);
+    Geom g = P->geom;
+    cudaMemsetAsync(ptr.hdr, 0, 256, st);
+    if (n == 0) {
+        launch_unsplit<real>(g, ptr, W, 0, q, potential, energy, forces, nullptr, nullptr, false, st,
+                             tr);
+        return FMM_OK;
+    }
+    cudaMemsetAsync(ptr.leaf_count, 0, W.ncell * 4, st);
+    cudaMemsetAsync(ptr.cursor, 0, W.ncell * 4, st);
+    launch_bin_emit<real>(g, C, ptr, W, (int)n, pos, q, st, tr);
+    launch_sort<real>(g, ptr, W, (int)n, st, tr);
+    launch_upward<real>(g, C, ptr, W, st, tr);
+    launch_downward<real>(g, C, ptr, W, (const real *)P->Kunit, (const real *)P->Klat, st, tr);
+    launch_evaluate<real>(g, C, ptr, W, forces != nullptr, st, tr);
+    launch_unsplit<real>(g, ptr, W, (int)n, q, potential, energy, forces, nullptr, nullptr, false,
+                         st, tr);
+    k_mark_valid<<<1, 1, 0, st>>>(ptr.hdr, (long long)n);
+    tr.count();
+    return FMM_OK;
+}
+
+template <typename real>
+int backward_impl(fmm_plan_t P, int64_t n, const float *q, const double *gE, real *grad_pos,
+                  real *grad_q, void *ws, cudaStream_t st, Tracer &tr) {
+    WsLayout W = make_layout(P, n);
+    Ptrs<real> ptr = make_ptrs<real>(W, ws);
+    const Coef<real> &C = *reinterpret_cast<const Coef<real> *>(P->fp64 ? (const void *)&P->cd
+                                                                        : (const void *)&P->cf);
+    Geom g = P->geom;
+    if (n == 0) return FMM_OK;
+    launch_evaluate<real>(g, C, ptr, W, true, st, tr);
+    launch_unsplit<real>(g, ptr, W, (int)n, q, nullptr, nullptr, grad_pos, gE, grad_q, true, st, tr);
+    return FMM_OK;
+}
+
+Tracer make_tracer(fmm_plan_t P, cudaStream_t st) {
+    Tracer tr;
+    tr.st = st;
+    tr.on = P->timing;
+    tr.ev = P->ev;
+    tr.cap = P->nev_created;
+    return tr;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void fmm_opts_default(fmm_opts_t *o) {
+    if (!o) return;
+    o->continuous = 0;
+    o->split_ratio = 1.0 / 256.0;
+    o->split_capacity = 2.0;
+    o->precision = FMM_PREC_FP32;
+    o->force_mode = FMM_FORCE_ADJOINT;
+    o->sync = 1;
+}
+
+const char *fmm_strerror(int s) {
+    switch (s) {
+    case FMM_OK: return "ok";
+    case FMM_ERR_ARG: return "invalid argument";
+    case FMM_ERR_OOM: return "out of device memory";
+    case FMM_ERR_OUT_OF_BOX: return "position outside the box (open form)";
+    case FMM_ERR_NONFINITE: return "non-finite position";
+    case FMM_ERR_SPLIT_OVERFLOW: return "more split charges than the workspace holds";
+    case FMM_ERR_TIMEOUT: return "device wait timed out";
+    case FMM_ERR_CUDA: return "CUDA runtime error";
+    case FMM_ERR_STATE: return "no evaluation to differentiate";
+    case FMM_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case FMM_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+    }
+}
+
+int fmm_version(void) { return 100; }
+
+int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int periodic,
+                    const fmm_opts_t *opts, int64_t max_n) {
+    if (!out || !box) return FMM_ERR_ARG;
+    *out = nullptr;
+    if (depth < 2 || depth > FMM_MAXDEPTH || p < 2 || p > FMM_MAXP) return FMM_ERR_ARG;
+    if (!(box[3] > 0.0) || !std::isfinite(box[0]) || !std::isfinite(box[1]) ||
+        !std::isfinite(box[2]) || !std::isfinite(box[3]))
+        return FMM_ERR_ARG;
+    if (max_n < 0 || max_n > (int64_t)1 << 30) return FMM_ERR_ARG;
+    fmm_opts_t o;
+    fmm_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.split_ratio <= 0) o.split_ratio = 1.0 / 256.0;
+    if (o.continuous && !(o.split_ratio < 0.5)) return FMM_ERR_ARG;
+    if (o.precision != FMM_PREC_FP32 && o.precision != FMM_PREC_FP64) return FMM_ERR_UNSUPPORTED;
+    fmm_plan_s *P = new (std::nothrow) fmm_plan_s();
+    if (!P) return FMM_ERR_OOM;
+    P->depth = depth;
+    P->p = p;
+    P->periodic = periodic ? 1 : 0;
+    P->opts = o;
+    memcpy(P->box, box, sizeof(double) * 4);
+    P->max_n = max_n;
+    P->fp64 = o.precision == FMM_PREC_FP64;
+    cudaGetDevice(&P->device);
+    fill_coef<float>(p, P->cf);
+    fill_coef<double>(p, P->cd);
+    Geom &g = P->geom;
+    g.p = p;
+    g.p3 = p * p * p;
+    g.depth = depth;
+    g.periodic = P->periodic;
+    g.continuous = o.continuous ? 1 : 0;
+    g.force_mode = o.force_mode;
+    g.S = 1 << depth;
+    for (int a = 0; a < 3; a++) g.x0[a] = (float)box[a];
+    g.Lf = (float)box[3];
+    g.dtf = (float)o.split_ratio;
+    g.dthi = 1.0f - g.dtf;
+    g.L = box[3];
+    if (cudaMallocHost(&P->h_hdr, 256) != cudaSuccess) {
+        delete P;
+        return FMM_ERR_OOM;
+    }
+    fmm::far_set_attributes();
+    int rc = P->fp64 ? upload_tables<double>(P) : upload_tables<float>(P);
+    if (rc != FMM_OK) {
+        fmm_plan_destroy(P);
+        return rc;
+    }
+    *out = P;
+    return FMM_OK;
+}
+
+void fmm_plan_destroy(fmm_plan_t P) {
+    if (!P) return;
+    for (int i = 0; i < P->nev_created; i++) cudaEventDestroy(P->ev[i]);
+    if (P->Kunit) cudaFree(P->Kunit);
+    if (P->Klat) cudaFree(P->Klat);
+    if (P->h_hdr) cudaFreeHost(P->h_hdr);
+    delete P;
+}
+
+int fmm_workspace_size(fmm_plan_t P, int64_t n, size_t *bytes) {
+    if (!P || !bytes || n < 0 || n > P->max_n) return FMM_ERR_ARG;
+    *bytes = make_layout(P, n).total;
+    return FMM_OK;
+}
+
+int fmm_eval(fmm_plan_t P, int64_t n, const float *pos, const float *q, void *potential,
+             double *energy, void *forces, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!P || n < 0 || n > P->max_n) return FMM_ERR_ARG;
+    if (n > 0 && (!pos || !q)) return FMM_ERR_ARG;
+    int rc = check_ws(P, n, workspace, workspace_bytes);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaGetLastError();
+    Tracer tr = make_tracer(P, st);
+    if (P->fp64)
+        rc = eval_impl<double>(P, n, pos, q, (double *)potential, energy, (double *)forces, workspace, st, tr);
+    else
+        rc = eval_impl<float>(P, n, pos, q, (float *)potential, energy, (float *)forces, workspace, st, tr);
+    P->last = tr;
+    if (rc) return rc;
+    P->last_ws = workspace;
+    P->last_n = n;
+    WsLayout W = make_layout(P, n);
+    return finish(P, (const WsHeader *)((char *)workspace + W.hdr), st, P->opts.sync != 0);
+}
+
+int fmm_backward(fmm_plan_t P, int64_t n, const float *pos, const float *q,
+                 const double *grad_energy, void *grad_pos, void *grad_q, void *workspace,
+                 size_t workspace_bytes, void *stream) {
+    (void)pos;
+    if (!P || n < 0 || n > P->max_n || !grad_energy) return FMM_ERR_ARG;
+    if (n > 0 && !q) return FMM_ERR_ARG;
+    int rc = check_ws(P, n, workspace, workspace_bytes);
+    if (rc) return rc;
+    if (P->last_ws != workspace || P->last_n != n) return FMM_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaGetLastError();
+    Tracer tr = make_tracer(P, st);
+    if (P->fp64)
+        rc = backward_impl<double>(P, n, q, grad_energy, (double *)grad_pos, (double *)grad_q, workspace, st, tr);
+    else
+        rc = backward_impl<float>(P, n, q, grad_energy, (float *)grad_pos, (float *)grad_q, workspace, st, tr);
+    P->last = tr;
+    if (rc) return rc;
+    WsLayout W = make_layout(P, n);
+    return finish(P, (const WsHeader *)((char *)workspace + W.hdr), st, P->opts.sync != 0);
+}
+
+int fmm_set_timing(fmm_plan_t P, int on) {
+    if (!P) return FMM_ERR_ARG;
+    if (on && P->nev_created == 0) {
+        for (int i = 0; i < 512; i++) {
+            if (cudaEventCreate(&P->ev[i]) != cudaSuccess) return FMM_ERR_CUDA;
+            P->nev_created = i + 1;
+        }
+    }
+    P->timing = on != 0;
+    return FMM_OK;
+}
+
+int fmm_get_stats(fmm_plan_t P, fmm_stats_t *out) {
+    if (!P || !out) return FMM_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    const Tracer &tr = P->last;
+    out->launches = tr.launches;
+    if (tr.on && tr.n >= 2) {
+        if (cudaEventSynchronize(tr.ev[tr.n - 1]) != cudaSuccess) return FMM_ERR_CUDA;
+        for (int k = 0; k + 1 < tr.n; k += 2) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, tr.ev[k], tr.ev[k + 1]) != cudaSuccess) return FMM_ERR_CUDA;
+            int s = tr.stage[k / 2];
+            if (s >= 0 && s < FMM_NSTAGES) out->stage_ms[s] += ms;
+        }
+        out->timed = 1;
+    }
+    return FMM_OK;
+}
+
+int fmm_status(fmm_plan_t P, const void *workspace, void *stream) {
+    if (!P || !workspace) return FMM_ERR_ARG;
+    return finish(P, (const WsHeader *)((const char *)workspace), (cudaStream_t)stream, true);
+}
+
+static int dump_bytes(fmm_plan_t P, int what, int n_eff, size_t *bytes) {
+    const size_t rs = P->fp64 ? 8 : 4;
+    const int64_t ncell = (int64_t)1 << (3 * P->depth);
+    const int p3 = P->p * P->p * P->p;
+    int64_t cells = 0;
+    for (int l = 0; l <= P->depth; l++) cells += (int64_t)1 << (3 * l);
+    switch (what) {
+    case FMM_DUMP_COUNTS: *bytes = 16; break;
+    case FMM_DUMP_KEYS:
+    case FMM_DUMP_ORIGIN:
+    case FMM_DUMP_PERM: *bytes = (size_t)n_eff * 4; break;
+    case FMM_DUMP_START: *bytes = (size_t)(ncell + 1) * 4; break;
+    case FMM_DUMP_POINTS: *bytes = (size_t)n_eff * 4 * rs; break;
+    case FMM_DUMP_PHI:
+    case FMM_DUMP_LOCAL: *bytes = (size_t)cells * p3 * rs; break;
+    default: return FMM_ERR_ARG;
+    }
+    return FMM_OK;
+}
+
+int fmm_debug_size(fmm_plan_t P, int what, const void *workspace, size_t *bytes, void *stream) {
+    if (!P || !workspace || !bytes) return FMM_ERR_ARG;
+    if (P->last_ws != workspace) return FMM_ERR_STATE;
+    WsLayout W = make_layout(P, P->last_n);
+    WsHeader h;
+    if (cudaMemcpyAsync(&h, (const char *)workspace + W.hdr, sizeof(h), cudaMemcpyDeviceToHost,
+                        (cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    return dump_bytes(P, what, h.n_eff, bytes);
+}
+
+int fmm_debug_dump(fmm_plan_t P, int what, const void *workspace, void *dst, size_t bytes,
+                   void *stream) {
+    if (!P || !workspace || !dst) return FMM_ERR_ARG;
+    if (P->last_ws != workspace) return FMM_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = P->last_n;
+    WsLayout W = make_layout(P, n);
+    const char *b = (const char *)workspace;
+    WsHeader h;
+    if (cudaMemcpyAsync(&h, b + W.hdr, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    size_t need;
+    if (dump_bytes(P, what, h.n_eff, &need) || bytes < need) return FMM_ERR_ARG;
+    const size_t rs = P->fp64 ? 8 : 4;
+    const int p = P->p, p3 = p * p * p;
+    auto copy = [&](size_t off, size_t nb) {
+        if (nb == 0) return FMM_OK;
+        if (cudaMemcpyAsync(dst, b + off, nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        return FMM_OK;
+    };
+    switch (what) {
+    case FMM_DUMP_COUNTS: {
+        int32_t c[4] = {(int32_t)n, h.n_eff, (int32_t)W.ncell, h.n_coinc};
+        memcpy(dst, c, 16);
+        return FMM_OK;
+    }
+    case FMM_DUMP_KEYS: return copy(W.e_key, need);
+    case FMM_DUMP_ORIGIN: return copy(W.s_origin, need);
+    case FMM_DUMP_PERM: return copy(W.perm, need);
+    case FMM_DUMP_START: return copy(W.leaf_start, need);
+    case FMM_DUMP_POINTS: return copy(W.s_pt, need);
+    case FMM_DUMP_PHI:
+    case FMM_DUMP_LOCAL: {
+        const bool isphi = what == FMM_DUMP_PHI;
+        size_t off = isphi ? W.phi : W.loc;
+        int64_t total = isphi ? W.phi_level[P->depth + 1] : W.loc_level[P->depth + 1];
+        std::vector<char> raw((size_t)total * rs);
+        if (cudaMemcpyAsync(raw.data(), b + off, raw.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        char *d = (char *)dst;
+        size_t o = 0;
+        for (int l = 0; l <= P->depth; l++) {
+            int S = 1 << l;
+            int64_t lvl = isphi ? W.phi_level[l] : W.loc_level[l];
+            for (int cz = 0; cz < S; cz++)
+                for (int cy = 0; cy < S; cy++)
+                    for (int cx = 0; cx < S; cx++) {
+                        int64_t c = isphi ? phi_cell(l, cx, cy, cz) : loc_cell(l, cx, cy, cz);
+                        memcpy(d + o, raw.data() + (size_t)(lvl + c * p3) * rs, (size_t)p3 * rs);
+                        o += (size_t)p3 * rs;
+                    }
+        }
+        return FMM_OK;
+    }
+    default: return FMM_ERR_ARG;
+    }
+}
+
+}  // extern "C"

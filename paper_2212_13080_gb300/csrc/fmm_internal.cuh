@@ -1,0 +1,185 @@
+// Internal declarations of the GB300 replacement-FMM library (not part of the C ABI).
+//
+// Data layout in device memory (all indices int32 unless noted):
+//   charges after binning/split, sorted by finest cell (Morton order):
+//     s_pt[slot]     real4 (t_x, t_y, t_z, q_eff): t in finest-cell units, [0,1]
+//     s_origin[slot] particle the charge came from
+//   grid charges Phi of level l >= 1: 8 parity blocks of (H+2)^3 coarse cells
+//     (H = 2^(l-1); one halo cell per side, zero in the open form, the periodic
+//     image in the periodic form), each cell a contiguous p^3 vector with node
+//     (i,j,k) at (k*p + j)*p + i.  Level 0 is a single cell.
+//   functionals L of level l >= 1: 8 parity blocks of H^3 cells (no halo).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fmm_gb300.h"
+
+#define FMM_MAXP 8
+#define FMM_MAXDEPTH 8
+
+namespace fmm {
+
+// Coefficients of the p-division points of the unit segment (§2.1.2) and of the
+// child->parent shift (eq. trans), in the plan's real type.  Passed by value.
+template <typename real>
+struct Coef {
+    real tau[FMM_MAXP];                    // nodes i/(p-1)
+    real cinv[FMM_MAXP];                   // 1 / prod_{k != i} (tau_i - tau_k)
+    real G[2][FMM_MAXP * FMM_MAXP];        // G_h[J*p + i] = g_J((h + tau_i)/2)
+};
+
+// Per-evaluation scalars.
+struct Geom {
+    int p, p3, depth, periodic, continuous, force_mode;
+    int S;            // 2^depth
+    float x0[3];      // float32 box corner
+    float Lf;         // float32 box edge
+    float dtf, dthi;  // split half-width in finest-cell units and 1 - dtf (float32)
+    double L;         // box edge (FP64) for output scaling
+};
+
+// Workspace header (first 256 bytes of the workspace).
+struct WsHeader {
+    int status;       // FMM_ERR_* bits from the device (see status codes below)
+    int n_eff;        // charges after the split
+    int n_coinc;      // coincident pairs skipped in the near field
+    int valid;        // 0 until an evaluation completed
+    long long tag;    // plan id and n of the last evaluation
+};
+
+// device-side status bits
+#define ST_OUT_OF_BOX 1
+#define ST_NONFINITE 2
+#define ST_SPLIT_OVERFLOW 4
+
+// Workspace carving (byte offsets), computed on the host for (plan, n).
+struct WsLayout {
+    size_t hdr;
+    size_t count, offset, axes;           // per particle (continuous form)
+    size_t e_key, e_pt, e_wd, e_origin;   // per emitted charge
+    size_t leaf_count, leaf_start, cursor;
+    size_t tmp, perm, inv;
+    size_t s_pt, s_origin, out_pt;
+    size_t phi, loc;                      // all levels
+    size_t scan_tmp, epart;
+    size_t total;
+    int64_t cap;                          // charge capacity
+    int64_t ncell;                        // 8^depth
+    int64_t phi_level[FMM_MAXDEPTH + 2];  // element offset of each level in Phi
+    int64_t loc_level[FMM_MAXDEPTH + 2];  // element offset of each level in L
+    int scan_blocks;
+};
+
+// ---- index helpers -----------------------------------------------------------
+__host__ __device__ inline uint32_t morton_encode(uint32_t x, uint32_t y, uint32_t z) {
+    uint32_t k = 0;
+#pragma unroll
+    for (int b = 0; b < 10; b++) {
+        k |= ((x >> b) & 1u) << (3 * b);
+        k |= ((y >> b) & 1u) << (3 * b + 1);
+        k |= ((z >> b) & 1u) << (3 * b + 2);
+    }
+    return k;
+}
+__host__ __device__ inline void morton_decode(uint32_t k, int &x, int &y, int &z) {
+    x = y = z = 0;
+#pragma unroll
+    for (int b = 0; b < 10; b++) {
+        x |= (int)((k >> (3 * b)) & 1u) << b;
+        y |= (int)((k >> (3 * b + 1)) & 1u) << b;
+        z |= (int)((k >> (3 * b + 2)) & 1u) << b;
+    }
+}
+// cell (cx,cy,cz) of level l >= 1 in the padded Phi layout
+__host__ __device__ inline int64_t phi_cell(int l, int cx, int cy, int cz) {
+    if (l == 0) return 0;
+    int64_t H = (int64_t)1 << (l - 1), P = H + 2;
+    int par = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+    return ((par * P + (cz >> 1) + 1) * P + (cy >> 1) + 1) * P + (cx >> 1) + 1;
+}
+__host__ __device__ inline int64_t phi_level_cells(int l) {
+    if (l == 0) return 1;
+    int64_t P = ((int64_t)1 << (l - 1)) + 2;
+    return 8 * P * P * P;
+}
+// cell of level l >= 1 in the unpadded L layout
+__host__ __device__ inline int64_t loc_cell(int l, int cx, int cy, int cz) {
+    if (l == 0) return 0;
+    int64_t H = (int64_t)1 << (l - 1);
+    int par = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+    return ((par * H + (cz >> 1)) * H + (cy >> 1)) * H + (cx >> 1);
+}
+__host__ __device__ inline int64_t loc_level_cells(int l) { return (int64_t)1 << (3 * l); }
+
+template <typename real> struct Vec4;
+template <> struct Vec4<float> { typedef float4 T; };
+template <> struct Vec4<double> { typedef double4 T; };
+
+// Stage tracer: counts kernel launches and, when on, brackets each stage's
+// kernels with CUDA events on the stream (FMM_STAGE_* ids).
+struct Tracer {
+    bool on = false;
+    cudaStream_t st = 0;
+    int launches = 0;
+    cudaEvent_t *ev = nullptr;
+    int cap = 0, n = 0;
+    int stage[512];
+    void begin(int s) {
+        if (on && n + 2 <= cap) {
+            stage[n / 2] = s;
+            cudaEventRecord(ev[n++], st);
+        }
+    }
+    void end() {
+        if (on && (n & 1)) cudaEventRecord(ev[n++], st);
+    }
+    void count(int k = 1) { launches += k; }
+};
+
+// ---- kernels launch wrappers (defined in the .cu files) -------------------
+template <typename real>
+struct Ptrs {
+    WsHeader *hdr;
+    int *count, *offset;
+    unsigned char *axes;
+    uint32_t *e_key;
+    typename Vec4<real>::T *e_pt, *e_wd;
+    int *e_origin;
+    int *leaf_count, *leaf_start, *cursor;
+    int *tmp, *perm, *inv;
+    typename Vec4<real>::T *s_pt;
+    int *s_origin;
+    typename Vec4<real>::T *out_pt;
+    real *phi, *loc;
+    int *scan_tmp;
+    double *epart;
+};
+
+// tree / bookkeeping stage (kernels_tree.cu)
+template <typename real>
+void launch_bin_emit(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
+                     int n, const float *pos, const float *q, cudaStream_t st, Tracer &tr);
+template <typename real>
+void launch_sort(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, cudaStream_t st,
+                 Tracer &tr);
+template <typename real>
+void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, const float *q,
+                    real *potential, double *energy, real *forces, const double *grad_energy,
+                    real *grad_q, bool backward, cudaStream_t st, Tracer &tr);
+int launch_scan(const int *in, int *out, int m, int *tmp, cudaStream_t st);
+
+// far field (kernels_far.cu)
+template <typename real>
+void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
+                   cudaStream_t st, Tracer &tr);
+template <typename real>
+void launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
+                     const real *Kunit, const real *Klat, cudaStream_t st, Tracer &tr);
+
+// near field + far-field evaluation at the charges (kernels_p2p.cu)
+template <typename real>
+void launch_evaluate(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
+                     bool forces, cudaStream_t st, Tracer &tr);
+
+}  // namespace fmm

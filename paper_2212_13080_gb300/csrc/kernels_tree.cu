@@ -1,0 +1,565 @@
+// Binning, split, stable sort by finest cell, recombination of split charges
+// and the FP64 energy reduction.
+#include "fmm_internal.cuh"
+#include "lagrange.cuh"
+
+namespace fmm {
+
+// ---------------------------------------------------------------------------
+// §2.2 step 1: the canonical single-precision map of a coordinate to its
+// finest cell.  u = fl32(fl32(x - x0) / fl32(L)) (wrapped in the periodic form),
+// c = min(floor(u 2^depth), 2^depth - 1), t = u 2^depth - c (exact).
+// Every operation is an explicitly rounded intrinsic: no contraction.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bin_axis(const Geom &g, float x, int a, float &t, int &c,
+                                         int &st) {
+    float u = __fdiv_rn(__fsub_rn(x, g.x0[a]), g.Lf);
+    if (!isfinite(u)) {
+        st |= ST_NONFINITE;
+        u = 0.0f;
+    }
+    if (g.periodic) {
+        u = __fsub_rn(u, floorf(u));
+        if (u >= 1.0f) u = 0.0f;
+    } else if (!(u >= 0.0f && u < 1.0f)) {
+        st |= ST_OUT_OF_BOX;
+        u = 0.0f;
+    }
+    float v = __fmul_rn(u, (float)g.S);
+    int ci = (int)floorf(v);
+    if (ci > g.S - 1) ci = g.S - 1;
+    t = __fsub_rn(v, (float)ci);
+    c = ci;
+}
+
+// Split decision of one axis (§2.3; walls too in the periodic form, §4.2).
+// mode 0: not split (1 entry); 1: split below the cell (plane between c-1 and
+// c); 2: split above (plane between c and c+1).
+struct AxisInfo {
+    int mode, cl, cu, m;
+    float t;
+};
+
+__device__ __forceinline__ AxisInfo split_axis_info(const Geom &g, int c, float t) {
+    AxisInfo A;
+    A.t = t;
+    A.mode = 0;
+    A.cl = A.cu = c;
+    A.m = 1;
+    if (!g.continuous) return A;
+    bool lower = (g.periodic || c > 0) && t < g.dtf;
+    bool upper = (g.periodic || c < g.S - 1) && t > g.dthi;
+    if (lower) {
+        A.mode = 1;
+        A.cl = c - 1;
+        A.cu = c;
+    } else if (upper) {
+        A.mode = 2;
+        A.cl = c;
+        A.cu = c + 1;
+    } else {
+        return A;
+    }
+    if (g.periodic) {
+        A.cl = (A.cl + g.S) % g.S;
+        A.cu = A.cu % g.S;
+    }
+    A.m = g.p + (g.p & 1);  // odd p: the middle node becomes two half charges
+    return A;
+}
+
+// Entry e of a split axis: cell, local coordinate, weight, d weight / du.
+// Segment nodes s_k = -1 + 2k/(p-1) (length 2d centred on the plane); the
+// weights are the one-dimensional replacement onto them, g_k((sigma+1)/2),
+// sigma = signed distance from the plane in units of d.
+template <typename real>
+__device__ __forceinline__ void split_entry(const Geom &g, const Coef<real> &C, const AxisInfo &A,
+                                            int e, int &cell, real &t, real &w, real &dw) {
+    if (A.mode == 0) {
+        cell = A.cl;
+        t = (real)A.t;
+        w = 1;
+        dw = 0;
+        return;
+    }
+    const int p = g.p;
+    const real dt = (real)g.dtf;
+    real sigma = (A.mode == 1) ? (real)A.t / dt : ((real)A.t - real(1)) / dt;
+    real x = (sigma + real(1)) * real(0.5);
+    int k, side;  // side 0: lower cell, 1: upper cell
+    real half = 1;
+    if (p & 1) {
+        int mid = (p - 1) / 2;
+        if (e < mid) {
+            k = e;
+            side = 0;
+        } else if (e == mid) {
+            k = mid;
+            side = 0;
+            half = real(0.5);
+        } else if (e == mid + 1) {
+            k = mid;
+            side = 1;
+            half = real(0.5);
+        } else {
+            k = e - 1;
+            side = 1;
+        }
+    } else {
+        k = e;
+        side = (2 * k < p - 1) ? 0 : 1;
+    }
+    real gk, dgk;
+    lag_one(C, p, k, x, gk, dgk);
+    w = half * gk;
+    dw = half * dgk * (real(0.5) / dt) * (real)g.S;
+    real s = (real)(2 * k) / (real)(p - 1) - real(1);
+    if (half != real(1)) {
+        t = side ? real(0) : real(1);
+    } else {
+        t = side ? s * dt : real(1) + s * dt;
+    }
+    cell = side ? A.cu : A.cl;
+}
+
+// number of charges per particle (continuous form only)
+__global__ void k_split_count(Geom g, int n, const float *__restrict__ pos, int *__restrict__ count,
+                              unsigned char *__restrict__ axes, WsHeader *hdr) {
+    int st = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int m = 1;
+        unsigned char ax = 0;
+        for (int a = 0; a < 3; a++) {
+            float t;
+            int c;
+            bin_axis(g, pos[3 * i + a], a, t, c, st);
+            AxisInfo A = split_axis_info(g, c, t);
+            m *= A.m;
+            if (A.mode) ax |= (unsigned char)(1 << a);
+        }
+        count[i] = m;
+        axes[i] = ax;
+    }
+    if (st) atomicOr(&hdr->status, st);
+}
+
+// Emits every particle's charges (particle order; per particle the tensor
+// product of its axes with x fastest), with Morton key, (t, q_eff), (W, dW/du)
+// and origin, and counts the charges of every finest cell.
+template <typename real>
+__global__ void k_emit(Geom g, Coef<real> C, int n, const float *__restrict__ pos,
+                       const float *__restrict__ q, const int *__restrict__ offset, int cap,
+                       uint32_t *__restrict__ e_key, typename Vec4<real>::T *__restrict__ e_pt,
+                       typename Vec4<real>::T *__restrict__ e_wd, int *__restrict__ e_origin,
+                       int *__restrict__ leaf_count, WsHeader *hdr) {
+    int st = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        AxisInfo A[3];
+        for (int a = 0; a < 3; a++) {
+            float t;
+            int c;
+            bin_axis(g, pos[3 * i + a], a, t, c, st);
+            A[a] = split_axis_info(g, c, t);
+        }
+        const real qi = (real)q[i];
+        int e = offset ? offset[i] : i;
+        if (offset && e + A[0].m * A[1].m * A[2].m > cap) {
+            st |= ST_SPLIT_OVERFLOW;
+            continue;
+        }
+        for (int ez = 0; ez < A[2].m; ez++) {
+            int cz;
+            real tz, wz, dwz;
+            split_entry(g, C, A[2], ez, cz, tz, wz, dwz);
+            for (int ey = 0; ey < A[1].m; ey++) {
+                int cy;
+                real ty, wy, dwy;
+                split_entry(g, C, A[1], ey, cy, ty, wy, dwy);
+                for (int ex = 0; ex < A[0].m; ex++) {
+                    int cx;
+                    real tx, wx, dwx;
+                    split_entry(g, C, A[0], ex, cx, tx, wx, dwx);
+                    real W = wx * wy * wz;
+                    uint32_t key = morton_encode(cx, cy, cz);
+                    e_key[e] = key;
+                    typename Vec4<real>::T v;
+                    v.x = tx;
+                    v.y = ty;
+                    v.z = tz;
+                    v.w = qi * W;
+                    e_pt[e] = v;
+                    if (e_wd) {
+                        typename Vec4<real>::T d;
+                        d.x = W;
+                        d.y = dwx * wy * wz;
+                        d.z = wx * dwy * wz;
+                        d.w = wx * wy * dwz;
+                        e_wd[e] = d;
+                    }
+                    e_origin[e] = i;
+                    atomicAdd(&leaf_count[key], 1);
+                    e++;
+                }
+            }
+        }
+    }
+    if (st) atomicOr(&hdr->status, st);
+}
+
+// n_eff = charges of the particles that were emitted in full: the particles
+// with offset[i+1] <= cap form a prefix (offsets increase), found by bisection.
+__global__ void k_set_neff(const int *offset, int n, WsHeader *hdr, int cap) {
+    if (!offset) {
+        hdr->n_eff = n;
+        return;
+    }
+    if (offset[n] <= cap) {
+        hdr->n_eff = offset[n];
+        return;
+    }
+    int lo = 0, hi = n;  // number of particles fully emitted is in [lo, hi)
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (offset[mid] <= cap) lo = mid; else hi = mid;
+    }
+    // offset[lo] <= cap < offset[lo+1]: particle lo was not emitted
+    hdr->n_eff = offset[lo];
+    atomicOr(&hdr->status, ST_SPLIT_OVERFLOW);
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int32 (three passes: block sums, scan of block sums,
+// block-local scan plus prefix); out has m+1 entries, out[m] = total.
+// ---------------------------------------------------------------------------
+#define SCAN_BS 256
+#define SCAN_IPT 8
+#define SCAN_TILE (SCAN_BS * SCAN_IPT)
+
+__device__ __forceinline__ int block_excl_scan(int v, int *sh, int &total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    total = sh[(blockDim.x >> 5) - 1];
+    int pre = (wid > 0 ? sh[wid - 1] : 0) + x - v;
+    __syncthreads();
+    return pre;
+}
+
+__global__ void k_scan_reduce(const int *__restrict__ in, int m, int *__restrict__ bsum) {
+    __shared__ int sh[32];
+    int base = blockIdx.x * SCAN_TILE;
+    int s = 0;
+    for (int k = 0; k < SCAN_IPT; k++) {
+        int i = base + k * SCAN_BS + threadIdx.x;
+        if (i < m) s += in[i];
+    }
+    int tot;
+    block_excl_scan(s, sh, tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_blocks(int *bsum, int nb) {
+    __shared__ int sh[32];
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+        int i = b0 + threadIdx.x;
+        int v = i < nb ? bsum[i] : 0;
+        int tot;
+        int pre = block_excl_scan(v, sh, tot);
+        if (i < nb) bsum[i] = carry + pre;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void k_scan_apply(const int *__restrict__ in, int m, const int *__restrict__ bsum,
+                             int *__restrict__ out) {
+    __shared__ int sh[32];
+    int base = blockIdx.x * SCAN_TILE;
+    int vals[SCAN_IPT];
+    int s = 0;
+    // thread owns SCAN_IPT consecutive elements
+    for (int k = 0; k < SCAN_IPT; k++) {
+        int i = base + threadIdx.x * SCAN_IPT + k;
+        vals[k] = i < m ? in[i] : 0;
+        s += vals[k];
+    }
+    int tot;
+    int pre = block_excl_scan(s, sh, tot) + bsum[blockIdx.x];
+    for (int k = 0; k < SCAN_IPT; k++) {
+        int i = base + threadIdx.x * SCAN_IPT + k;
+        if (i < m) out[i] = pre;
+        pre += vals[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[m] = bsum[gridDim.x];
+}
+
+int launch_scan(const int *in, int *out, int m, int *tmp, cudaStream_t st) {
+    int nb = (m + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 0) nb = 1;
+    k_scan_reduce<<<nb, SCAN_BS, 0, st>>>(in, m, tmp);
+    k_scan_blocks<<<1, 1024, 0, st>>>(tmp, nb);
+    k_scan_apply<<<nb, SCAN_BS, 0, st>>>(in, m, tmp, out);
+    return 3;
+}
+
+template <typename real>
+void launch_bin_emit(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
+                     int n, const float *pos, const float *q, cudaStream_t st, Tracer &tr) {
+    int nb = (n + 255) / 256;
+    if (nb < 1) nb = 1;
+    if (nb > 152 * 64) nb = 152 * 64;
+    const int *offset = nullptr;
+    tr.begin(FMM_STAGE_BIN);
+    if (g.continuous) {
+        k_split_count<<<nb, 256, 0, st>>>(g, n, pos, P.count, P.axes, P.hdr);
+        tr.count(1 + launch_scan(P.count, P.offset, n, P.scan_tmp, st));
+        offset = P.offset;
+    }
+    k_emit<real><<<nb, 256, 0, st>>>(g, C, n, pos, q, offset, (int)W.cap, P.e_key, P.e_pt,
+                                     g.continuous ? P.e_wd : nullptr, P.e_origin, P.leaf_count,
+                                     P.hdr);
+    k_set_neff<<<1, 1, 0, st>>>(offset, n, P.hdr, (int)W.cap);
+    tr.count(2);
+    tr.end();
+}
+
+// ---------------------------------------------------------------------------
+// stable counting sort by finest cell: scatter with per-cell cursors, then
+// order each cell's segment by emitted index (= particle order), then gather.
+// ---------------------------------------------------------------------------
+__global__ void k_scatter(const WsHeader *hdr, const uint32_t *__restrict__ e_key,
+                          const int *__restrict__ leaf_start, int *__restrict__ cursor,
+                          int *__restrict__ tmp) {
+    int ne = hdr->n_eff;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+        uint32_t k = e_key[e];
+        int slot = leaf_start[k] + atomicAdd(&cursor[k], 1);
+        tmp[slot] = e;
+    }
+}
+
+// one warp per finest cell: rank every element of the cell's segment among
+// the segment (all values distinct) and place it
+__global__ void k_leaf_order(int ncell, const int *__restrict__ leaf_start,
+                             const int *__restrict__ tmp, int *__restrict__ perm) {
+    int lane = threadIdx.x & 31;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = warp; c < ncell; c += nwarps) {
+        int s0 = leaf_start[c], s1 = leaf_start[c + 1];
+        int cnt = s1 - s0;
+        if (cnt == 0) continue;
+        if (cnt <= 32) {
+            int v = lane < cnt ? tmp[s0 + lane] : 0x7fffffff;
+            int r = 0;
+            for (int j = 0; j < cnt; j++) {
+                int w = __shfl_sync(0xffffffffu, v, j);
+                r += (w < v);
+            }
+            if (lane < cnt) perm[s0 + r] = v;
+        } else {
+            for (int i = lane; i < cnt; i += 32) {
+                int v = tmp[s0 + i];
+                int r = 0;
+                for (int j = 0; j < cnt; j++) r += (tmp[s0 + j] < v);
+                perm[s0 + r] = v;
+            }
+        }
+    }
+}
+
+template <typename real>
+__global__ void k_gather(const WsHeader *hdr, const int *__restrict__ perm,
+                         const typename Vec4<real>::T *__restrict__ e_pt,
+                         const int *__restrict__ e_origin, typename Vec4<real>::T *__restrict__ s_pt,
+                         int *__restrict__ s_origin, int *__restrict__ inv) {
+    int ne = hdr->n_eff;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ne; s += gridDim.x * blockDim.x) {
+        int e = perm[s];
+        s_pt[s] = e_pt[e];
+        s_origin[s] = e_origin[e];
+        inv[e] = s;
+    }
+}
+
+template <typename real>
+void launch_sort(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, cudaStream_t st,
+                 Tracer &tr) {
+    int ncell = (int)W.ncell;
+    tr.begin(FMM_STAGE_SORT);
+    tr.count(launch_scan(P.leaf_count, P.leaf_start, ncell, P.scan_tmp, st));
+    int nbp = (int)((W.cap + 255) / 256);
+    if (nbp < 1) nbp = 1;
+    if (nbp > 152 * 64) nbp = 152 * 64;
+    k_scatter<<<nbp, 256, 0, st>>>(P.hdr, P.e_key, P.leaf_start, P.cursor, P.tmp);
+    int nbl = (ncell * 32 + 255) / 256;
+    if (nbl > 152 * 64) nbl = 152 * 64;
+    k_leaf_order<<<nbl, 256, 0, st>>>(ncell, P.leaf_start, P.tmp, P.perm);
+    k_gather<real><<<nbp, 256, 0, st>>>(P.hdr, P.perm, P.e_pt, P.e_origin, P.s_pt, P.s_origin,
+                                        P.inv);
+    tr.count(3);
+    tr.end();
+}
+
+// ---------------------------------------------------------------------------
+// recombination of the split charges into their particles (§2.3), scaling to
+// physical units, and the FP64 energy E = 1/2 sum_i q_i phi_i.
+//   phi_i = sum_k W_k phi(s_k)
+//   adjoint force, axis not split: sum_k F(s_k); split axis: -q_i sum_k dW_k/du phi(s_k)
+//   paper force: sum_k F(s_k) on every axis
+// out_pt holds (phi, F) per sorted charge in unit-box units.
+// backward: grad_pos = -F * gE, grad_q = phi * gE.
+// ---------------------------------------------------------------------------
+#define UNSPLIT_BS 256
+
+template <typename real>
+__global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__restrict__ q,
+                          const int *__restrict__ offset,
+                          const int *__restrict__ count, const unsigned char *__restrict__ axes,
+                          const int *__restrict__ inv, const typename Vec4<real>::T *__restrict__ e_wd,
+                          const typename Vec4<real>::T *__restrict__ out_pt, real *__restrict__ potential,
+                          real *__restrict__ forces, double *__restrict__ epart,
+                          const double *__restrict__ grad_energy, real *__restrict__ grad_q,
+                          int backward) {
+    __shared__ double sh[UNSPLIT_BS / 32];
+    const double invL = 1.0 / g.L;
+    const real sphi = (real)invL, sF = (real)(invL * invL);
+    double gE = backward ? *grad_energy : 0.0;
+    double eacc = 0.0;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        real phi, Fx, Fy, Fz;
+        if (!offset) {
+            typename Vec4<real>::T o = out_pt[inv[i]];
+            phi = o.x;
+            Fx = o.y;
+            Fy = o.z;
+            Fz = o.w;
+        } else {
+            int e0 = offset[i], m = count[i];
+            if (e0 + m > hdr->n_eff) m = 0;  // not emitted (split overflow; status is set)
+            phi = 0;
+            real Sx = 0, Sy = 0, Sz = 0, Nx = 0, Ny = 0, Nz = 0;
+            for (int e = e0; e < e0 + m; e++) {
+                typename Vec4<real>::T o = out_pt[inv[e]];
+                typename Vec4<real>::T d = e_wd[e];
+                phi += d.x * o.x;
+                Sx += o.y;
+                Sy += o.z;
+                Sz += o.w;
+                Nx += d.y * o.x;
+                Ny += d.z * o.x;
+                Nz += d.w * o.x;
+            }
+            unsigned ax = g.force_mode == FMM_FORCE_PAPER ? 0u : axes[i];
+            real qi = (real)q[i];
+            Fx = (ax & 1) ? -qi * Nx : Sx;
+            Fy = (ax & 2) ? -qi * Ny : Sy;
+            Fz = (ax & 4) ? -qi * Nz : Sz;
+        }
+        phi *= sphi;
+        Fx *= sF;
+        Fy *= sF;
+        Fz *= sF;
+        if (!backward) {
+            if (potential) potential[i] = phi;
+            if (forces) {
+                forces[3 * i] = Fx;
+                forces[3 * i + 1] = Fy;
+                forces[3 * i + 2] = Fz;
+            }
+            eacc = 0.5 * (double)q[i] * (double)phi;
+        } else {
+            if (forces) {
+                forces[3 * i] = (real)(-(double)Fx * gE);
+                forces[3 * i + 1] = (real)(-(double)Fy * gE);
+                forces[3 * i + 2] = (real)(-(double)Fz * gE);
+            }
+            if (grad_q) grad_q[i] = (real)((double)phi * gE);
+        }
+    }
+    if (epart) {
+        // deterministic block reduction
+        for (int o = 16; o > 0; o >>= 1) eacc += __shfl_down_sync(0xffffffffu, eacc, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = eacc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0;
+            for (int w = 0; w < UNSPLIT_BS / 32; w++) s += sh[w];
+            epart[blockIdx.x] = s;
+        }
+    }
+}
+
+__global__ void k_energy_final(const double *__restrict__ epart, int nb, double *energy) {
+    __shared__ double sh[1024];
+    double s = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += epart[b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *energy = sh[0];
+}
+
+__global__ void k_zero_energy(double *energy) { *energy = 0.0; }
+
+template <typename real>
+void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, const float *q,
+                    real *potential, double *energy, real *forces, const double *grad_energy,
+                    real *grad_q, bool backward, cudaStream_t st, Tracer &tr) {
+    tr.begin(FMM_STAGE_UNSPLIT);
+    if (n == 0) {
+        if (energy && !backward) {
+            k_zero_energy<<<1, 1, 0, st>>>(energy);
+            tr.count();
+        }
+        tr.end();
+        return;
+    }
+    int nb = (n + UNSPLIT_BS - 1) / UNSPLIT_BS;
+    double *ep = (!backward && energy) ? P.epart : nullptr;
+    k_unsplit<real><<<nb, UNSPLIT_BS, 0, st>>>(
+        g, P.hdr, n, q, g.continuous ? P.offset : nullptr, P.count, P.axes, P.inv,
+        g.continuous ? P.e_wd : nullptr, P.out_pt, potential, forces, ep, grad_energy, grad_q,
+        backward ? 1 : 0);
+    tr.count();
+    if (ep) {
+        k_energy_final<<<1, 1024, 0, st>>>(P.epart, nb, energy);
+        tr.count();
+    }
+    tr.end();
+}
+
+#define INST(real)                                                                               \
+    template void launch_bin_emit<real>(const Geom &, const Coef<real> &, const Ptrs<real> &,     \
+                                        const WsLayout &, int, const float *, const float *,      \
+                                        cudaStream_t, Tracer &);                                  \
+    template void launch_sort<real>(const Geom &, const Ptrs<real> &, const WsLayout &, int,      \
+                                    cudaStream_t, Tracer &);                                      \
+    template void launch_unsplit<real>(const Geom &, const Ptrs<real> &, const WsLayout &, int,   \
+                                       const float *, real *, double *, real *, const double *,   \
+                                       real *, bool, cudaStream_t, Tracer &);
+INST(float)
+INST(double)
+
+}  // namespace fmm

@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads, and exports every symbol the header declares
+(no compute: this runs without a GPU)."""
+import os
+import re
+import subprocess
+
+from conftest import ROOT
+
+
+def _declared():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"\b(fmm_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_builds_and_exports_header_symbols():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2212_13080_gb300 import _binding
+    lib = _binding.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (fmm_[a-z_0-9]+)", out))
+    declared = _declared()
+    assert declared, "no declarations found"
+    missing = [d for d in declared if d not in exported]
+    assert not missing, missing
+    assert sorted(declared) == sorted(_binding.EXPORTED)
+
+
+def test_host_only_entry_points():
+    from paper_2212_13080_gb300 import _binding as B
+    assert B.fmm_version() >= 100
+    assert B.fmm_strerror(B.FMM_ERR_OUT_OF_BOX) == "position outside the box (open form)"
+    assert B.fmm_strerror(12345) == "unknown status"
+    o = B.fmm_opts_default()
+    assert o.continuous == 0 and abs(o.split_ratio - 1 / 256) < 1e-15 and o.sync == 1
+
+
+def test_plan_argument_checks():
+    """Invalid arguments are rejected before any device call."""
+    import ctypes
+    from paper_2212_13080_gb300 import _binding as B
+    L = B.lib()
+    h = ctypes.c_void_p()
+    box = (ctypes.c_double * 4)(0, 0, 0, 1)
+    for depth, p, max_n in [(1, 4, 10), (9, 4, 10), (3, 1, 10), (3, 9, 10), (3, 4, -1)]:
+        assert L.fmm_plan_create(ctypes.byref(h), box, depth, p, 0, None, max_n) == B.FMM_ERR_ARG
+    bad = (ctypes.c_double * 4)(0, 0, 0, 0)
+    assert L.fmm_plan_create(ctypes.byref(h), bad, 3, 4, 0, None, 10) == B.FMM_ERR_ARG
+    o = B.fmm_opts_default()
+    o.continuous = 1
+    o.split_ratio = 0.6
+    assert L.fmm_plan_create(ctypes.byref(h), box, 3, 4, 0, ctypes.byref(o), 10) == B.FMM_ERR_ARG
+    assert L.fmm_eval(None, 1, None, None, None, None, None, None, 0, None) == B.FMM_ERR_ARG

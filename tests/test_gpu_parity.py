@@ -1,0 +1,238 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the
+same seeded inputs.
+
+Integer work (Morton keys, split charges and their particles, the sort
+permutation, finest-cell ranges) must be bit-exact.  Floating point:
+  FP64 plans: relative error <= 1e-11 (rounding order only);
+  FP32 plans: relative L2 error <= 1e-6 on potentials and forces and
+              relative energy error <= 1e-6, on top of the method's own error
+              (the oracle runs the same method in FP64).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2212_13080_gb300 import FMM, FmmError, inputs  # noqa: E402
+
+TOL_FP32 = 1e-6
+TOL_FP64 = 1e-11
+
+
+def _gpu(pos, q, box, depth, p, periodic=False, continuous=False, dt=None, precision="fp32",
+         forces=True, force_mode="adjoint"):
+    plan = FMM(box, depth, p, periodic=periodic, continuous=continuous, split_ratio=dt,
+               precision=precision, max_n=max(len(q), 1), force_mode=force_mode)
+    r = plan.eval(torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda(), forces=forces)
+    torch.cuda.synchronize()
+    out = {k: (v.cpu().numpy().astype(np.float64) if v is not None else None) for k, v in r.items()}
+    return plan, out
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _check_integer_work(plan, ref):
+    cnt = plan.dump("counts")
+    n_eff = int(cnt[1])
+    assert n_eff == ref["n_points"]
+    np.testing.assert_array_equal(plan.dump("keys"), ref["pt_key"])
+    np.testing.assert_array_equal(plan.dump("perm"), ref["perm"])
+    np.testing.assert_array_equal(plan.dump("start"), ref["start"])
+    np.testing.assert_array_equal(plan.dump("origin"), ref["pt_origin"][ref["perm"]])
+
+
+def _check_levels(plan, ref, p, depth, periodic, tol):
+    Phi = plan.dump("phi").reshape(-1).astype(np.float64)
+    Lv = plan.dump("local").reshape(-1).astype(np.float64)
+    lmin_phi = 0 if periodic else 2
+    for l in range(lmin_phi, depth + 1):
+        a, b = oracle.level_offset(p, l), oracle.level_offset(p, l + 1)
+        e = _rel_l2(Phi[a:b], ref["Phi"][a:b])
+        assert e < tol, ("Phi", l, e)
+        e = _rel_l2(Lv[a:b], ref["L"][a:b])
+        assert e < tol, ("L", l, e)
+
+
+CASES = [
+    # name, generator, depth, p, periodic, continuous, dt
+    ("uniform4k-open-plain", lambda: inputs.uniform_pm1(4096, 1), 3, 4, False, False, None),
+    ("uniform20k-open-cont", lambda: inputs.uniform_cont(20000, 5), 4, 4, False, True, 1 / 32),
+    ("uniform9k-open-cont-p5", lambda: inputs.uniform_cont(9001, 6), 3, 5, False, True, 1 / 16),
+    ("water3k-periodic-cont-p5", lambda: inputs.water(1001, 3), 3, 5, True, True, 1 / 16),
+    ("uniform5k-periodic-plain-p3", lambda: inputs.uniform_pm1(5000, 9), 3, 3, True, False, None),
+    ("uniform3k-open-cont-p6-d2", lambda: inputs.uniform_cont(3001, 8), 2, 6, False, True, 1 / 8),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_parity_small(case, precision):
+    name, gen, depth, p, periodic, cont, dt = case
+    pos, q, box = gen()
+    ref = oracle.fmm(pos, q, box, depth=depth, n=p, periodic=periodic, continuous=cont, dt=dt)
+    plan, out = _gpu(pos, q, box, depth, p, periodic, cont, dt, precision)
+    _check_integer_work(plan, ref)
+    tol = TOL_FP64 if precision == "fp64" else TOL_FP32
+    # sorted charges: unsplit charges carry the exact binned coordinate
+    pts = plan.dump("points").astype(np.float64)
+    st = ref["pt_t"][ref["perm"]]
+    sq = ref["pt_q"][ref["perm"]]
+    unsplit = ref["count"][ref["pt_origin"][ref["perm"]]] == 1
+    np.testing.assert_array_equal(pts[unsplit, :3], st[unsplit])
+    assert np.max(np.abs(pts[:, :3] - st)) < (1e-15 if precision == "fp64" else 1e-7)
+    assert _rel_l2(pts[:, 3], sq) < (1e-15 if precision == "fp64" else 1e-7)
+    _check_levels(plan, ref, p, depth, periodic, tol * 10 if precision == "fp64" else tol)
+    e_phi = _rel_l2(out["potential"], ref["phi"])
+    e_F = _rel_l2(out["forces"], ref["F"])
+    e_E = abs(out["energy"][0] - ref["E"]) / abs(ref["E"])
+    assert e_phi < tol and e_F < tol and e_E < tol, (e_phi, e_F, e_E)
+    plan.close()
+
+
+def test_paper_force_mode():
+    pos, q, box = inputs.uniform_cont(8000, 12)
+    ref = oracle.fmm(pos, q, box, depth=3, n=4, continuous=True, dt=1 / 16)
+    plan, out = _gpu(pos, q, box, 3, 4, False, True, 1 / 16, "fp64", force_mode="paper")
+    assert _rel_l2(out["forces"], ref["F_paper"]) < TOL_FP64
+    plan.close()
+
+
+def test_energy_only_and_potential_only():
+    pos, q, box = inputs.uniform_pm1(3000, 13)
+    ref = oracle.fmm(pos, q, box, depth=3, n=4)
+    plan, out = _gpu(pos, q, box, 3, 4, precision="fp64", forces=False)
+    assert out["forces"] is None
+    assert _rel_l2(out["potential"], ref["phi"]) < TOL_FP64
+    assert abs(out["energy"][0] - ref["E"]) < TOL_FP64 * abs(ref["E"])
+    plan.close()
+
+
+def test_deterministic():
+    pos, q, box = inputs.uniform_cont(30000, 14)
+    plan = FMM(box, 4, 4, continuous=True, max_n=len(q))
+    P, Q = torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda()
+    a = plan.eval(P, Q)
+    a = {k: v.clone() for k, v in a.items()}
+    b = plan.eval(P, Q)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    plan.close()
+
+
+def test_edge_cases():
+    box = (0.0, 0.0, 0.0, 1.0)
+    # n = 0
+    plan = FMM(box, 3, 4, max_n=16)
+    r = plan.eval(torch.zeros((0, 3), device="cuda"), torch.zeros(0, device="cuda"))
+    assert r["energy"].item() == 0.0
+    # one particle: no interaction at all
+    r = plan.eval(torch.tensor([[0.3, 0.6, 0.1]], device="cuda"), torch.tensor([1.0], device="cuda"))
+    assert r["energy"].item() == 0.0 and r["potential"].item() == 0.0
+    # all particles in one finest cell; particles exactly on planes
+    pos = np.array([[0.5, 0.5, 0.5], [0.55, 0.52, 0.51], [0.25, 0.5, 0.75], [0.125, 0.0, 0.999],
+                    [0.0, 0.0, 0.0], [0.5, 0.125, 0.625]], np.float32)
+    q = np.array([1, -1, 1, -1, 1, -1], np.float32)
+    for cont in (False, True):
+        ref = oracle.fmm(pos, q, box, depth=3, n=4, continuous=cont, dt=1 / 8)
+        plan2, out = _gpu(pos, q, box, 3, 4, False, cont, 1 / 8, "fp64")
+        _check_integer_work(plan2, ref)
+        assert _rel_l2(out["potential"], ref["phi"]) < TOL_FP64
+        plan2.close()
+    # open form: a position outside the box is an error, not a wrong answer
+    with pytest.raises(FmmError) as e:
+        plan.eval(torch.tensor([[1.5, 0.5, 0.5]], device="cuda"), torch.tensor([1.0], device="cuda"))
+    assert e.value.code == 3
+    with pytest.raises(FmmError) as e:
+        plan.eval(torch.tensor([[float("nan"), 0.5, 0.5]], device="cuda"),
+                  torch.tensor([1.0], device="cuda"))
+    assert e.value.code == 4
+    plan.close()
+
+
+def test_split_overflow_is_reported():
+    # every particle near a corner: 64 charges each, capacity 2 per particle
+    rng = np.random.default_rng(3)
+    c = rng.integers(1, 7, size=(500, 3))
+    pos = ((c + rng.uniform(-1, 1, size=(500, 3)) * 0.01) / 8).astype(np.float32)
+    q = np.ones(500, np.float32)
+    plan = FMM((0, 0, 0, 1), 3, 4, continuous=True, split_ratio=1 / 16, max_n=500)
+    with pytest.raises(FmmError) as e:
+        plan.eval(torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda())
+    assert e.value.code == 5
+    # with room for the split it evaluates and matches the oracle
+    plan2 = FMM((0, 0, 0, 1), 3, 4, continuous=True, split_ratio=1 / 16, max_n=500,
+                split_capacity=70, precision="fp64")
+    r = plan2.eval(torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda())
+    ref = oracle.fmm(pos, q, (0, 0, 0, 1), depth=3, n=4, continuous=True, dt=1 / 16)
+    assert _rel_l2(r["potential"].cpu().numpy(), ref["phi"]) < TOL_FP64
+    plan.close()
+    plan2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_backward_matches_forces_and_potential(precision):
+    pos, q, box = inputs.water(800, 17)
+    ref = oracle.fmm(pos, q, box, depth=3, n=5, periodic=True, continuous=True, dt=1 / 16)
+    plan = FMM(box, 3, 5, periodic=True, continuous=True, split_ratio=1 / 16, precision=precision,
+               max_n=len(q))
+    from paper_2212_13080_gb300 import fmm_energy
+    P = torch.from_numpy(pos).cuda().requires_grad_(True)
+    Q = torch.from_numpy(q).cuda().requires_grad_(True)
+    E = fmm_energy(plan, P, Q)
+    (2.0 * E).backward()
+    tol = TOL_FP64 if precision == "fp64" else TOL_FP32
+    assert abs(E.item() - ref["E"]) < tol * abs(ref["E"])
+    assert _rel_l2(P.grad.cpu().numpy().astype(np.float64), -2.0 * ref["F"]) < tol
+    assert _rel_l2(Q.grad.cpu().numpy().astype(np.float64), 2.0 * ref["phi"]) < tol
+    plan.close()
+
+
+def test_forces_central_differences_fp64():
+    """Forces are -dE/dx of the GPU's own energy (central differences, h = 2^-14,
+    particles away from the split-band edges)."""
+    pos, q, box = inputs.uniform_pm1(700, 19)
+    pos = (pos * np.float32(0.5) + np.float32(0.25)).astype(np.float32)
+    dt = 1 / 8
+    plan = FMM(box, 3, 4, continuous=True, split_ratio=dt, precision="fp64", max_n=len(q))
+    P, Q = torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda()
+    F = plan.eval(P, Q)["forces"].cpu().numpy()
+    h = np.float32(2.0 ** -14)
+    ref = oracle.fmm(pos, q, box, depth=3, n=4, continuous=True, dt=dt)
+    t = ref["t"]
+    edge = np.minimum(np.abs(t - dt), np.abs(1 - t - dt)).min(axis=1) * 8
+    idx = np.where(edge > 4 * h)[0][:12]
+    for i in idx:
+        for a in range(3):
+            Es = []
+            for s in (1, -1):
+                pp = pos.copy()
+                pp[i, a] += s * h
+                Es.append(plan.eval(torch.from_numpy(pp).cuda(), Q)["energy"].item())
+            fd = -(Es[0] - Es[1]) / (2 * float(h))
+            assert abs(fd - F[i, a]) < 2e-4 * max(1.0, np.abs(F[i]).max()), (i, a, fd, F[i, a])
+    plan.close()
+
+
+@pytest.mark.parametrize("name,sample", [("uniform1m", 512), ("water2m", 256)])
+def test_parity_full_size_sampled(name, sample):
+    """Full-size workloads in the benchmark's launch configuration: integer work
+    on every charge, outputs on sampled particles (the oracle computes those one
+    by one from its full upward pass)."""
+    w = inputs.workload(name)
+    pos, q, box = w["pos"], w["q"], w["box"]
+    rng = np.random.default_rng(0)
+    s = np.sort(rng.choice(len(q), sample, replace=False))
+    ref = oracle.fmm(pos, q, box, depth=w["depth"], n=w["p"], periodic=w["periodic"],
+                     continuous=w["continuous"], sample=s)
+    plan, out = _gpu(pos, q, box, w["depth"], w["p"], w["periodic"], w["continuous"], None, "fp32")
+    _check_integer_work(plan, ref)
+    assert _rel_l2(out["potential"][s], ref["phi"]) < TOL_FP32
+    assert _rel_l2(out["forces"][s], ref["F"]) < TOL_FP32
+    # energy: the sum is a property at any size; E = 1/2 sum q phi of the GPU's own phi
+    E_from_phi = 0.5 * np.dot(q.astype(np.float64), out["potential"])
+    assert abs(out["energy"][0] - E_from_phi) < 1e-9 * np.sum(np.abs(q * out["potential"]))
+    plan.close()
