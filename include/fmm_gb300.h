@@ -74,7 +74,8 @@ typedef struct {
     double split_ratio;    /* d / finest-cell width, in (0, 0.5); <= 0 selects 1/256
                               (2d = w/128; §3.2 uses 2d = 1/1024 with w = 1/8) */
     double split_capacity; /* workspace holds split_capacity * n charges after the split;
-                              <= 0 selects 2.0 (continuous) */
+                              <= 0 selects max(2, 1.5 (1 + 2 (d/w)(m-1))^3), m = p
+                              (even p) or p+1 (odd p): 1.5x the uniform-density mean */
     int precision;         /* FMM_PREC_* */
     int force_mode;        /* FMM_FORCE_ADJOINT or FMM_FORCE_PAPER */
     int sync;              /* 1 (default when opts is NULL): fmm_eval waits for the device
@@ -82,8 +83,8 @@ typedef struct {
                               queueing, fmm_status() reports them later */
 } fmm_opts_t;
 
-/* Fills *opts with the defaults (continuous 0, split_ratio 1/256, split_capacity 2,
- * precision FP32, adjoint forces, sync 1). */
+/* Fills *opts with the defaults (continuous 0, split_ratio 1/256, split_capacity 0
+ * (automatic), precision FP32, adjoint forces, sync 1). */
 void fmm_opts_default(fmm_opts_t *opts);
 
 /*
@@ -172,6 +173,8 @@ int fmm_status(fmm_plan_t plan, const void *workspace, void *stream);
  *   FMM_DUMP_PHI      real [level][8^level][p^3]: grid charges, natural cell
  *                     order (cz*S + cy)*S + cx, levels 0..depth
  *   FMM_DUMP_LOCAL    real, same layout: functionals L (Psi_C(v) = L_C . v)
+ *   FMM_DUMP_OUT      real [n_eff][4]: (phi, F_x, F_y, F_z) per sorted charge in
+ *                     unit-box units (phi per unit charge, F with the charge)
  * Errors: FMM_ERR_ARG (unknown item or dst too small).
  */
 #define FMM_DUMP_COUNTS 0
@@ -182,6 +185,7 @@ int fmm_status(fmm_plan_t plan, const void *workspace, void *stream);
 #define FMM_DUMP_POINTS 5
 #define FMM_DUMP_PHI 6
 #define FMM_DUMP_LOCAL 7
+#define FMM_DUMP_OUT 8
 int fmm_debug_dump(fmm_plan_t plan, int what, const void *workspace, void *dst, size_t bytes,
                    void *stream);
 

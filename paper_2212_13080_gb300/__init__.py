@@ -165,7 +165,7 @@ class FMM:
             return buf.view(np.int32)
         if what == "keys":
             return buf.view(np.uint32)
-        if what == "points":
+        if what in ("points", "out"):
             return buf.view(real).reshape(-1, 4)
         return buf.view(real).reshape(-1, self.p ** 3)
 

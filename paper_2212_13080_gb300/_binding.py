@@ -37,6 +37,7 @@ FMM_DUMP_START = 4
 FMM_DUMP_POINTS = 5
 FMM_DUMP_PHI = 6
 FMM_DUMP_LOCAL = 7
+FMM_DUMP_OUT = 8
 
 # every symbol include/fmm_gb300.h declares
 EXPORTED = ["fmm_opts_default", "fmm_plan_create", "fmm_plan_destroy", "fmm_workspace_size",

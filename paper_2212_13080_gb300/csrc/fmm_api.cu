@@ -22,8 +22,10 @@ struct fmm_plan_s {
     int64_t max_n;
     int device;
     bool fp64;
-    void *Kunit;  // [343][p^3][p^3] unit-cell bilinear-form kernels, plan real type
-    void *Klat;   // [p^3][p^3] lattice kernel (periodic form)
+    void *Kunit;  // [343][p^3][p^3] Kt_o transposed ([o][b][a]), plan real type
+    void *Kbar;   // [343][p^3] row means of the unit-cell kernels
+    void *Klat;   // [p^3][p^3] lattice kernel minus its row mean (periodic form)
+    void *Klbar;  // [p^3] row means of the lattice kernel
     Coef<float> cf;
     Coef<double> cd;
     Geom geom;
@@ -105,28 +107,45 @@ void fill_coef(int p, Coef<real> &C) {
 }
 
 template <typename real>
+int upload(void **dst, const std::vector<real> &v) {
+    if (cudaMalloc(dst, v.size() * sizeof(real)) != cudaSuccess) return FMM_ERR_OOM;
+    if (cudaMemcpy(*dst, v.data(), v.size() * sizeof(real), cudaMemcpyHostToDevice) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    return FMM_OK;
+}
+
+// Unit-cell kernels of eq. (bilinear), K_o[a,b] = 1/|a - (o + b)| for the 316
+// offsets 2 <= |o|_inf <= 3, split into row mean and remainder (FP64, then
+// rounded to the plan's type).
+template <typename real>
 int upload_tables(fmm_plan_t P) {
     const int p = P->p, p3 = p * p * p;
     const size_t nk = (size_t)343 * p3 * p3;
-    std::vector<real> K(nk, (real)0);
+    std::vector<real> KtT(nk, (real)0), Kbar((size_t)343 * p3, (real)0);
+    std::vector<double> row(p3);
     for (int oz = -3; oz <= 3; oz++)
         for (int oy = -3; oy <= 3; oy++)
             for (int ox = -3; ox <= 3; ox++) {
                 if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
-                size_t base = (size_t)(((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3)) * p3 * p3;
+                size_t oi = (size_t)(((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3));
                 for (int a = 0; a < p3; a++) {
                     double ax = node(p, a % p), ay = node(p, (a / p) % p), az = node(p, a / (p * p));
+                    double mean = 0.0;
                     for (int b = 0; b < p3; b++) {
                         double dx = ax - (ox + node(p, b % p));
                         double dy = ay - (oy + node(p, (b / p) % p));
                         double dz = az - (oz + node(p, b / (p * p)));
-                        K[base + (size_t)a * p3 + b] = (real)(1.0 / std::sqrt(dx * dx + dy * dy + dz * dz));
+                        row[b] = 1.0 / std::sqrt(dx * dx + dy * dy + dz * dz);
+                        mean += row[b];
                     }
+                    mean /= p3;
+                    Kbar[oi * p3 + a] = (real)mean;
+                    for (int b = 0; b < p3; b++) KtT[(oi * p3 + b) * p3 + a] = (real)(row[b] - mean);
                 }
             }
-    if (cudaMalloc(&P->Kunit, nk * sizeof(real)) != cudaSuccess) return FMM_ERR_OOM;
-    if (cudaMemcpy(P->Kunit, K.data(), nk * sizeof(real), cudaMemcpyHostToDevice) != cudaSuccess)
-        return FMM_ERR_CUDA;
+    int rc = upload(&P->Kunit, KtT);
+    if (!rc) rc = upload(&P->Kbar, Kbar);
+    if (rc) return rc;
     if (P->periodic) {
         // psi depends on a - b only: (2p-1)^3 distinct arguments
         const int m = 2 * p - 1;
@@ -137,17 +156,22 @@ int upload_tables(fmm_plan_t P) {
                     tab[((size_t)dz * m + dy) * m + dx] =
                         far_image_sum((dx - (p - 1)) / (double)(p - 1), (dy - (p - 1)) / (double)(p - 1),
                                       (dz - (p - 1)) / (double)(p - 1));
-        std::vector<real> Kl((size_t)p3 * p3);
-        for (int a = 0; a < p3; a++)
+        std::vector<real> Kl((size_t)p3 * p3), Klb(p3);
+        for (int a = 0; a < p3; a++) {
+            double mean = 0.0;
             for (int b = 0; b < p3; b++) {
                 int dx = a % p - b % p + p - 1, dy = (a / p) % p - (b / p) % p + p - 1,
                     dz = a / (p * p) - b / (p * p) + p - 1;
-                Kl[(size_t)a * p3 + b] = (real)tab[((size_t)dz * m + dy) * m + dx];
+                row[b] = tab[((size_t)dz * m + dy) * m + dx];
+                mean += row[b];
             }
-        if (cudaMalloc(&P->Klat, Kl.size() * sizeof(real)) != cudaSuccess) return FMM_ERR_OOM;
-        if (cudaMemcpy(P->Klat, Kl.data(), Kl.size() * sizeof(real), cudaMemcpyHostToDevice) !=
-            cudaSuccess)
-            return FMM_ERR_CUDA;
+            mean /= p3;
+            Klb[a] = (real)mean;
+            for (int b = 0; b < p3; b++) Kl[(size_t)a * p3 + b] = (real)(row[b] - mean);
+        }
+        rc = upload(&P->Klat, Kl);
+        if (!rc) rc = upload(&P->Klbar, Klb);
+        if (rc) return rc;
     }
     return FMM_OK;
 }
@@ -162,7 +186,13 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     const bool cont = P->opts.continuous != 0;
     W.ncell = (int64_t)1 << (3 * P->depth);
     if (cont) {
-        double f = P->opts.split_capacity > 0 ? P->opts.split_capacity : 2.0;
+        // default: 1.5x the expected charges per particle for uniform density,
+        // (1 + 2 d/w (m - 1))^3 with m charges per split axis, and at least 2
+        const int m = P->p + (P->p & 1);
+        double e1 = 1.0 + 2.0 * P->opts.split_ratio * (m - 1);
+        double fdef = 1.5 * e1 * e1 * e1;
+        if (fdef < 2.0) fdef = 2.0;
+        double f = P->opts.split_capacity > 0 ? P->opts.split_capacity : fdef;
         W.cap = (int64_t)std::ceil(f * (double)n) + 64;
         if (W.cap < n) W.cap = n;
     } else {
@@ -203,6 +233,13 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     W.loc_level[P->depth + 1] = lc * p3;
     W.phi = take((size_t)ph * p3 * rs);
     W.loc = take((size_t)lc * p3 * rs);
+    int64_t qc = 0;
+    for (int l = 0; l <= P->depth; l++) {
+        W.q_level[l] = qc;
+        qc += phi_level_cells(l);
+    }
+    W.q_level[P->depth + 1] = qc;
+    W.qlev = take((size_t)qc * rs);
     int64_t mx = n > W.ncell ? n : W.ncell;
     W.scan_blocks = (int)(mx / 2048 + 2);
     W.scan_tmp = take((size_t)(W.scan_blocks + 1) * 4);
@@ -235,6 +272,7 @@ Ptrs<real> make_ptrs(const WsLayout &W, void *ws) {
     P.out_pt = (R4 *)(b + W.out_pt);
     P.phi = (real *)(b + W.phi);
     P.loc = (real *)(b + W.loc);
+    P.qlev = (real *)(b + W.qlev);
     P.scan_tmp = (int *)(b + W.scan_tmp);
     P.epart = (double *)(b + W.epart);
     return P;
@@ -289,7 +327,12 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     launch_bin_emit<real>(g, C, ptr, W, (int)n, pos, q, st, tr);
     launch_sort<real>(g, ptr, W, (int)n, st, tr);
     launch_upward<real>(g, C, ptr, W, st, tr);
-    launch_downward<real>(g, C, ptr, W, (const real *)P->Kunit, (const real *)P->Klat, st, tr);
+    DevTables<real> T;
+    T.KtT = (const real *)P->Kunit;
+    T.Kbar = (const real *)P->Kbar;
+    T.Klt = (const real *)P->Klat;
+    T.Klbar = (const real *)P->Klbar;
+    launch_downward<real>(g, C, ptr, W, T, st, tr);
     launch_evaluate<real>(g, C, ptr, W, forces != nullptr, st, tr);
     launch_unsplit<real>(g, ptr, W, (int)n, q, potential, energy, forces, nullptr, nullptr, false,
                          st, tr);
@@ -332,7 +375,7 @@ void fmm_opts_default(fmm_opts_t *o) {
     if (!o) return;
     o->continuous = 0;
     o->split_ratio = 1.0 / 256.0;
-    o->split_capacity = 2.0;
+    o->split_capacity = 0.0;
     o->precision = FMM_PREC_FP32;
     o->force_mode = FMM_FORCE_ADJOINT;
     o->sync = 1;
@@ -415,7 +458,9 @@ void fmm_plan_destroy(fmm_plan_t P) {
     if (!P) return;
     for (int i = 0; i < P->nev_created; i++) cudaEventDestroy(P->ev[i]);
     if (P->Kunit) cudaFree(P->Kunit);
+    if (P->Kbar) cudaFree(P->Kbar);
     if (P->Klat) cudaFree(P->Klat);
+    if (P->Klbar) cudaFree(P->Klbar);
     if (P->h_hdr) cudaFreeHost(P->h_hdr);
     delete P;
 }
@@ -516,7 +561,8 @@ static int dump_bytes(fmm_plan_t P, int what, int n_eff, size_t *bytes) {
     case FMM_DUMP_ORIGIN:
     case FMM_DUMP_PERM: *bytes = (size_t)n_eff * 4; break;
     case FMM_DUMP_START: *bytes = (size_t)(ncell + 1) * 4; break;
-    case FMM_DUMP_POINTS: *bytes = (size_t)n_eff * 4 * rs; break;
+    case FMM_DUMP_POINTS:
+    case FMM_DUMP_OUT: *bytes = (size_t)n_eff * 4 * rs; break;
     case FMM_DUMP_PHI:
     case FMM_DUMP_LOCAL: *bytes = (size_t)cells * p3 * rs; break;
     default: return FMM_ERR_ARG;
@@ -570,6 +616,7 @@ int fmm_debug_dump(fmm_plan_t P, int what, const void *workspace, void *dst, siz
     case FMM_DUMP_PERM: return copy(W.perm, need);
     case FMM_DUMP_START: return copy(W.leaf_start, need);
     case FMM_DUMP_POINTS: return copy(W.s_pt, need);
+    case FMM_DUMP_OUT: return copy(W.out_pt, need);
     case FMM_DUMP_PHI:
     case FMM_DUMP_LOCAL: {
         const bool isphi = what == FMM_DUMP_PHI;

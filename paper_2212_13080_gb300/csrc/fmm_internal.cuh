@@ -62,12 +62,14 @@ struct WsLayout {
     size_t tmp, perm, inv;
     size_t s_pt, s_origin, out_pt;
     size_t phi, loc;                      // all levels
+    size_t qlev;                          // total charge of every cell, padded Phi layout
     size_t scan_tmp, epart;
     size_t total;
     int64_t cap;                          // charge capacity
     int64_t ncell;                        // 8^depth
     int64_t phi_level[FMM_MAXDEPTH + 2];  // element offset of each level in Phi
     int64_t loc_level[FMM_MAXDEPTH + 2];  // element offset of each level in L
+    int64_t q_level[FMM_MAXDEPTH + 2];    // cell offset of each level in qlev
     int scan_blocks;
 };
 
@@ -152,8 +154,22 @@ struct Ptrs {
     int *s_origin;
     typename Vec4<real>::T *out_pt;
     real *phi, *loc;
+    real *qlev;
     int *scan_tmp;
     double *epart;
+};
+
+// Bilinear-form tables on the device.  K_o = Kbar_o[a] + Kt_o[a,b] with
+// Kbar_o[a] = mean_b K_o[a,b]: the contraction sum_b K_o[a,b] Phi[b] is evaluated
+// as sum_b Kt_o[a,b] Phi[b] + Kbar_o[a] Q with Q = sum_b Phi[b] the cell's total
+// charge (replacement conserves charge), which removes the cancellation of the
+// nearly constant kernel against grid charges of both signs.
+template <typename real>
+struct DevTables {
+    const real *KtT;    // [343][b][a] = Kt_o[a,b] (transposed, SIMT contraction)
+    const real *Kbar;   // [343][a]
+    const real *Klt;    // [a][b] lattice kernel minus its row mean (periodic form)
+    const real *Klbar;  // [a]
 };
 
 // tree / bookkeeping stage (kernels_tree.cu)
@@ -175,7 +191,7 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
                    cudaStream_t st, Tracer &tr);
 template <typename real>
 void launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
-                     const real *Kunit, const real *Klat, cudaStream_t st, Tracer &tr);
+                     const DevTables<real> &T, cudaStream_t st, Tracer &tr);
 
 // near field + far-field evaluation at the charges (kernels_p2p.cu)
 template <typename real>

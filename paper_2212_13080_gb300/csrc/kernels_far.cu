@@ -17,7 +17,7 @@ namespace fmm {
 template <typename real, int P>
 __global__ void __launch_bounds__(P2M_BS) k_p2m(Coef<real> C, int depth, const int *__restrict__ leaf_start,
                                                 const typename Vec4<real>::T *__restrict__ s_pt,
-                                                real *__restrict__ phi_leaf) {
+                                                real *__restrict__ phi_leaf, real *__restrict__ q_leaf) {
     constexpr int P3 = P * P * P;
     __shared__ real wx[P2M_CH][P], wy[P2M_CH][P], wz[P2M_CH][P], wq[P2M_CH];
     const uint32_t key = blockIdx.x;
@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(Coef<real> C, int depth, const i
     real acc[NO];
 #pragma unroll
     for (int r = 0; r < NO; r++) acc[r] = 0;
+    real Q = 0, Qc = 0;  // total charge of the cell (Kahan), thread 0
     for (int c0 = s0; c0 < s1; c0 += P2M_CH) {
         int m = min(P2M_CH, s1 - c0);
         if (threadIdx.x < m) {
@@ -45,6 +46,12 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(Coef<real> C, int depth, const i
             wq[threadIdx.x] = v.w;
         }
         __syncthreads();
+        if (threadIdx.x == 0)
+            for (int t = 0; t < m; t++) {
+                real y = wq[t] - Qc, tt = Q + y;
+                Qc = (tt - Q) - y;
+                Q = tt;
+            }
 #pragma unroll
         for (int r = 0; r < NO; r++) {
             int o = threadIdx.x + r * P2M_BS;
@@ -57,12 +64,14 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(Coef<real> C, int depth, const i
         }
         __syncthreads();
     }
-    real *out = phi_leaf + phi_cell(depth, cx, cy, cz) * P3;
+    const int64_t cell = phi_cell(depth, cx, cy, cz);
+    real *out = phi_leaf + cell * P3;
 #pragma unroll
     for (int r = 0; r < NO; r++) {
         int o = threadIdx.x + r * P2M_BS;
         if (o < P3) out[o] = acc[r];
     }
+    if (threadIdx.x == 0) q_leaf[cell] = Q;
 }
 
 // ---------------------------------------------------------------------------
@@ -74,7 +83,9 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(Coef<real> C, int depth, const i
 
 template <typename real>
 __global__ void __launch_bounds__(M2M_BS) k_m2m(Coef<real> C, int p, int l, const real *__restrict__ phi_child,
-                                                real *__restrict__ phi_parent) {
+                                                real *__restrict__ phi_parent,
+                                                const real *__restrict__ q_child,
+                                                real *__restrict__ q_parent) {
     extern __shared__ unsigned char smraw[];
     real *A = reinterpret_cast<real *>(smraw);
     const int p3 = p * p * p;
@@ -117,12 +128,18 @@ __global__ void __launch_bounds__(M2M_BS) k_m2m(Coef<real> C, int p, int l, cons
         }
         out[o] = s;
     }
+    if (threadIdx.x == 0) {
+        real Q = 0;
+        for (int h = 0; h < 8; h++)
+            Q += q_child[phi_cell(l, 2 * px + (h & 1), 2 * py + ((h >> 1) & 1), 2 * pz + (h >> 2))];
+        q_parent[phi_cell(l - 1, px, py, pz)] = Q;
+    }
 }
 
 // Halo of the padded Phi layout of level l >= 1: open form zeros; periodic form
 // the periodic image (coarse coordinate wrapped within the same parity block).
 template <typename real>
-__global__ void k_halo(int p3, int l, int periodic, real *__restrict__ phi_l) {
+__global__ void k_halo(int p3, int l, int periodic, real *__restrict__ phi_l, real *__restrict__ q_l) {
     const int H = 1 << (l - 1), P = H + 2;
     const int64_t ncells = 8LL * P * P * P;
     for (int64_t c = blockIdx.x; c < ncells; c += gridDim.x) {
@@ -133,12 +150,15 @@ __global__ void k_halo(int p3, int l, int periodic, real *__restrict__ phi_l) {
         real *dst = phi_l + c * p3;
         if (!periodic) {
             for (int o = threadIdx.x; o < p3; o += blockDim.x) dst[o] = 0;
+            if (threadIdx.x == 0) q_l[c] = 0;
         } else {
             int Xs = X == 0 ? H : (X == P - 1 ? 1 : X);
             int Ys = Y == 0 ? H : (Y == P - 1 ? 1 : Y);
             int Zs = Z == 0 ? H : (Z == P - 1 ? 1 : Z);
-            const real *src = phi_l + (((int64_t)par * P + Zs) * P + Ys) * P * (int64_t)p3 + (int64_t)Xs * p3;
+            const int64_t sc = (((int64_t)par * P + Zs) * P + Ys) * P + Xs;
+            const real *src = phi_l + sc * p3;
             for (int o = threadIdx.x; o < p3; o += blockDim.x) dst[o] = src[o];
+            if (threadIdx.x == 0) q_l[c] = q_l[sc];
         }
     }
 }
@@ -160,12 +180,16 @@ __global__ void k_halo(int p3, int l, int periodic, real *__restrict__ phi_l) {
 
 template <typename real>
 __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *__restrict__ phi_l,
+                                                     const real *__restrict__ q_l,
                                                      real *__restrict__ loc_l,
-                                                     const real *__restrict__ Kunit, int accumulate) {
+                                                     const real *__restrict__ KtT,
+                                                     const real *__restrict__ Kbar, int accumulate) {
     typedef typename Vec4<real>::T real4;
     extern __shared__ __align__(16) unsigned char smraw[];
     real *Ps = reinterpret_cast<real *>(smraw);  // [64 b][64 cells]
     real *Ks = Ps + M2L_T * M2L_T;               // [64 b][64 a]
+    real *Qs = Ks + M2L_T * M2L_T;               // [64 cells] source total charges
+    real *Kb = Qs + M2L_T;                       // [64 a] row means
     const int p3 = p * p * p;
     const int H = 1 << (l - 1), P = H + 2;
     const int T = H < 4 ? H : 4;  // tile edge in coarse cells
@@ -175,21 +199,46 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
     const int bx = par & 1, by = (par >> 1) & 1, bz = (par >> 2) & 1;
     const int ncell = T * T * T;
     const int cg = threadIdx.x / 16, ag = threadIdx.x % 16;
-    real acc[4][4];
+    // per-offset partial sums (64 terms) are added into the totals with Kahan
+    // compensation: one FP32 accumulator over all 189 x 64 terms would lose
+    // ~sqrt(12096/2) ulps
+    real acc[4][4], tot[4][4], cmp[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0;
+        for (int j = 0; j < 4; j++) tot[i][j] = cmp[i][j] = 0;
 
     for (int oz = -2 - bz; oz <= 3 - bz; oz++)
         for (int oy = -2 - by; oy <= 3 - by; oy++)
             for (int ox = -2 - bx; ox <= 3 - bx; ox++) {
                 if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[i][j] = 0;
                 // source parity and coarse shift
                 const int sx = bx + ox, sy = by + oy, sz = bz + oz;
                 const int spar = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
                 const int dX = sx >> 1, dY = sy >> 1, dZ = sz >> 1;
-                const real *Kt = Kunit + (int64_t)(((3 - oz) * 7 + (3 - oy)) * 7 + (3 - ox)) * p3 * p3;
+                const int oi = ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3);
+                const real *Kt = KtT + (int64_t)oi * p3 * p3;
+                // monopole part: Kbar_o[a] * Q_source (the previous offset's
+                // readers of Qs/Kb must be done first)
+                __syncthreads();
+                if (threadIdx.x < M2L_T) {
+                    int ci = threadIdx.x;
+                    real v = 0;
+                    if (ci < ncell) {
+                        int tx = ci % T, ty = (ci / T) % T, tz = ci / (T * T);
+                        int64_t cell = (((int64_t)spar * P + TZ + tz + 1 + dZ) * P + TY + ty + 1 + dY) * P +
+                                       TX + tx + 1 + dX;
+                        v = q_l[cell];
+                    }
+                    Qs[ci] = v;
+                } else if (threadIdx.x < 2 * M2L_T) {
+                    int a = threadIdx.x - M2L_T;
+                    Kb[a] = (a0 + a < p3) ? Kbar[(int64_t)oi * p3 + a0 + a] : real(0);
+                }
                 for (int b0 = 0; b0 < p3; b0 += M2L_T) {
                     // stage sources: Ps[b][ci]
                     for (int e = threadIdx.x; e < M2L_T * M2L_T; e += M2L_BS) {
@@ -203,7 +252,7 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
                         }
                         Ps[b * M2L_T + ci] = v;
                     }
-                    // stage K_o^T: Ks[b][a] = K_{-o}[b0+b][a0+a]
+                    // stage Kt_o^T: Ks[b][a] = Kt_o[a0+a][b0+b]
                     for (int e = threadIdx.x; e < M2L_T * M2L_T; e += M2L_BS) {
                         int a = e % M2L_T, b = e / M2L_T;
                         real v = 0;
@@ -224,6 +273,16 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
                     }
                     __syncthreads();
                 }
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        acc[i][j] += Kb[ag * 4 + j] * Qs[cg * 4 + i];
+                        real y = acc[i][j] - cmp[i][j];
+                        real t = tot[i][j] + y;
+                        cmp[i][j] = (t - tot[i][j]) - y;
+                        tot[i][j] = t;
+                    }
             }
     const real scale = (real)(1 << l);
 #pragma unroll
@@ -237,7 +296,7 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
         for (int j = 0; j < 4; j++) {
             int a = a0 + ag * 4 + j;
             if (a < p3) {
-                real v = scale * acc[i][j];
+                real v = scale * tot[i][j];
                 out[a] = accumulate ? out[a] + v : v;
             }
         }
@@ -247,12 +306,13 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
 // §4.2 (periodic form): the box against its images beyond the 26 nearest,
 // L_0 = K_lat Phi_0 (level 0, unit box).
 template <typename real>
-__global__ void k_lattice(int p3, const real *__restrict__ Klat, const real *__restrict__ phi0,
+__global__ void k_lattice(int p3, const real *__restrict__ Klt, const real *__restrict__ Klbar,
+                          const real *__restrict__ phi0, const real *__restrict__ q0,
                           real *__restrict__ loc0) {
     for (int a = threadIdx.x; a < p3; a += blockDim.x) {
         real s = 0;
-        for (int b = 0; b < p3; b++) s += Klat[(int64_t)a * p3 + b] * phi0[b];
-        loc0[a] = s;
+        for (int b = 0; b < p3; b++) s += Klt[(int64_t)a * p3 + b] * phi0[b];
+        loc0[a] = s + Klbar[a] * q0[0];
     }
 }
 
@@ -269,7 +329,7 @@ __global__ void __launch_bounds__(M2M_BS) k_l2l(Coef<real> C, int p, int l, cons
     const int p3 = p * p * p;
     real *A = Lp + p3;       // [hz][k][J][I]      2 p3
     real *B = A + 2 * p3;    // [hz][hy][k][j][I]  4 p3
-    const int Hp = l >= 2 ? 1 << (l - 2) : 1;
+    const int Hp = 1 << (l - 1);  // parents per axis (level l-1)
     const int pid = blockIdx.x;
     const int px = pid % Hp, py = (pid / Hp) % Hp, pz = pid / (Hp * Hp);
     const real *src = loc_parent + loc_cell(l - 1, px, py, pz) * p3;
@@ -314,7 +374,10 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
     tr.begin(FMM_STAGE_P2M);
     switch (p) {
 #define CASE(PP) \
-    case PP: k_p2m<real, PP><<<ncell, P2M_BS, 0, st>>>(C, depth, P.leaf_start, P.s_pt, phi_leaf); break;
+    case PP:                                                                                     \
+        k_p2m<real, PP><<<ncell, P2M_BS, 0, st>>>(C, depth, P.leaf_start, P.s_pt, phi_leaf,      \
+                                                  P.qlev + W.q_level[depth]);                    \
+        break;
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
     }
@@ -324,13 +387,15 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
     const int lmin = g.periodic ? 0 : 2;
     for (int l = depth; l >= 1; l--) {
         int blocks = (int)(phi_level_cells(l) < 4096 ? phi_level_cells(l) : 4096);
-        k_halo<real><<<blocks, 64, 0, st>>>(p3, l, g.periodic, P.phi + W.phi_level[l]);
+        k_halo<real><<<blocks, 64, 0, st>>>(p3, l, g.periodic, P.phi + W.phi_level[l],
+                                            P.qlev + W.q_level[l]);
         tr.count();
         if (l - 1 >= lmin) {
             int nparent = 1 << (3 * (l - 1));
             size_t sm = sizeof(real) * 16 * p3;
             k_m2m<real><<<nparent, M2M_BS, sm, st>>>(C, p, l, P.phi + W.phi_level[l],
-                                                     P.phi + W.phi_level[l - 1]);
+                                                     P.phi + W.phi_level[l - 1],
+                                                     P.qlev + W.q_level[l], P.qlev + W.q_level[l - 1]);
             tr.count();
         }
     }
@@ -339,15 +404,16 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
 
 template <typename real>
 void launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
-                     const real *Kunit, const real *Klat, cudaStream_t st, Tracer &tr) {
+                     const DevTables<real> &T, cudaStream_t st, Tracer &tr) {
     const int p = g.p, p3 = g.p3, depth = g.depth;
     const int achunks = (p3 + M2L_T - 1) / M2L_T;
-    const size_t sm_m2l = sizeof(real) * 2 * M2L_T * M2L_T;
+    const size_t sm_m2l = sizeof(real) * (2 * M2L_T * M2L_T + 2 * M2L_T);
     const size_t sm_l2l = sizeof(real) * 7 * p3;
     int lstart;
     if (g.periodic) {
         tr.begin(FMM_STAGE_M2L);
-        k_lattice<real><<<1, 256, 0, st>>>(p3, Klat, P.phi + W.phi_level[0], P.loc + W.loc_level[0]);
+        k_lattice<real><<<1, 256, 0, st>>>(p3, T.Klt, T.Klbar, P.phi + W.phi_level[0],
+                                           P.qlev + W.q_level[0], P.loc + W.loc_level[0]);
         tr.count();
         tr.end();
         lstart = 1;
@@ -365,12 +431,13 @@ void launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, co
             tr.end();
         }
         const int H = 1 << (l - 1);
-        const int T = H < 4 ? H : 4;
-        const int ntiles = (H / T) * (H / T) * (H / T);
+        const int Tt = H < 4 ? H : 4;
+        const int ntiles = (H / Tt) * (H / Tt) * (H / Tt);
         dim3 grid(ntiles, 8, achunks);
         tr.begin(FMM_STAGE_M2L);
         k_m2l_simt<real><<<grid, M2L_BS, sm_m2l, st>>>(p, l, P.phi + W.phi_level[l],
-                                                       P.loc + W.loc_level[l], Kunit,
+                                                       P.qlev + W.q_level[l],
+                                                       P.loc + W.loc_level[l], T.KtT, T.Kbar,
                                                        have_parent ? 1 : 0);
         tr.count();
         tr.end();
@@ -378,7 +445,7 @@ void launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, co
 }
 
 void far_set_attributes() {
-    cudaFuncSetAttribute(k_m2l_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_m2l_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 66 * 1024);
     cudaFuncSetAttribute(k_m2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * 512 * 8);
     cudaFuncSetAttribute(k_m2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * 512 * 4);
     cudaFuncSetAttribute(k_l2l<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * 512 * 8);
@@ -390,10 +457,10 @@ template void launch_upward<float>(const Geom &, const Coef<float> &, const Ptrs
 template void launch_upward<double>(const Geom &, const Coef<double> &, const Ptrs<double> &,
                                     const WsLayout &, cudaStream_t, Tracer &);
 template void launch_downward<float>(const Geom &, const Coef<float> &, const Ptrs<float> &,
-                                     const WsLayout &, const float *, const float *, cudaStream_t,
+                                     const WsLayout &, const DevTables<float> &, cudaStream_t,
                                      Tracer &);
 template void launch_downward<double>(const Geom &, const Coef<double> &, const Ptrs<double> &,
-                                      const WsLayout &, const double *, const double *,
-                                      cudaStream_t, Tracer &);
+                                      const WsLayout &, const DevTables<double> &, cudaStream_t,
+                                      Tracer &);
 
 }  // namespace fmm

@@ -91,6 +91,14 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, const i
 // G-th source; the G partial sums are added in a fixed order.  Pairs of charges
 // of the same particle (split charges) and coincident pairs are skipped.
 // ---------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ void kahan_add(real &sum, real &c, real x) {
+    real y = x - c;
+    real t = sum + y;
+    c = (t - sum) - y;
+    sum = t;
+}
+
 #define P2P_BS 128
 #define P2P_CHUNK 1024
 
@@ -169,7 +177,10 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p(int depth, int periodic, const i
         } else {
             tv.x = tv.y = tv.z = tv.w = 0;
         }
+        // totals with Kahan compensation; each block of up to 32 sources is
+        // first summed into a short partial
         real phi = 0, fx = 0, fy = 0, fz = 0;
+        real cphi = 0, cfx = 0, cfy = 0, cfz = 0;
         for (int c0 = 0; c0 < Ns; c0 += P2P_CHUNK) {
             const int cn = min(P2P_CHUNK, Ns - c0);
             if (!(single_chunk && staged)) {
@@ -190,19 +201,29 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p(int depth, int periodic, const i
                 staged = true;
             }
             if (active) {
-                for (int s = grp; s < cn; s += G) {
-                    real4 sv = src[s];
-                    real dx = tv.x - sv.x, dy = tv.y - sv.y, dz = tv.z - sv.z;
-                    real r2 = dx * dx + dy * dy + dz * dz;
-                    bool ok = (r2 > real(0)) && (srco[s] != to);
-                    real ri = ok ? rsqrt_r<real>(r2) : real(0);
-                    real qr = sv.w * ri;
-                    phi += qr;
+                for (int sb = grp; sb < cn; sb += 32 * G) {
+                    const int se = min(cn, sb + 32 * G);
+                    real pp = 0, px = 0, py = 0, pz = 0;
+                    for (int s = sb; s < se; s += G) {
+                        real4 sv = src[s];
+                        real dx = tv.x - sv.x, dy = tv.y - sv.y, dz = tv.z - sv.z;
+                        real r2 = dx * dx + dy * dy + dz * dz;
+                        bool ok = (r2 > real(0)) && (srco[s] != to);
+                        real ri = ok ? rsqrt_r<real>(r2) : real(0);
+                        real qr = sv.w * ri;
+                        pp += qr;
+                        if (FORCES) {
+                            real qr3 = qr * ri * ri;
+                            px += qr3 * dx;
+                            py += qr3 * dy;
+                            pz += qr3 * dz;
+                        }
+                    }
+                    kahan_add(phi, cphi, pp);
                     if (FORCES) {
-                        real qr3 = qr * ri * ri;
-                        fx += qr3 * dx;
-                        fy += qr3 * dy;
-                        fz += qr3 * dz;
+                        kahan_add(fx, cfx, px);
+                        kahan_add(fy, cfy, py);
+                        kahan_add(fz, cfz, pz);
                     }
                 }
             }
