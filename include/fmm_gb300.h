@@ -220,6 +220,31 @@ typedef struct {
 int fmm_set_timing(fmm_plan_t plan, int on);
 int fmm_get_stats(fmm_plan_t plan, fmm_stats_t *stats);
 
+/*
+ * fmm_eval_static — fmm_eval without a workspace argument.  The paper has no
+ * counterpart: this entry point is for callers that cannot allocate device
+ * memory at the time they evaluate (code running inside another framework's
+ * stream capture, real-time time-step loops that forbid allocation, hosts
+ * whose device memory is all owned by a pool they cannot draw from).
+ *   Scratch: a static device array of FMM_STATIC_WORKSPACE_BYTES (32 MiB),
+ *   which every GPU that loads the library holds until the process exits.
+ *   Limit: (plan, n) whose fmm_workspace_size exceeds it are rejected with
+ *   FMM_ERR_WORKSPACE before any device work.
+ *   Allocation: none (no cudaMalloc/cudaFree, no allocating library call);
+ *   the plan, created beforehand, owns its tables.
+ *   Set-up: the first call on a device, with that device current, looks up
+ *   the array's device address (cudaGetSymbolAddress); make that first call
+ *   before any stream capture.
+ *   Sharing: every call uses the same array and leaves the last call's
+ *   contents in it (the call clears what must start at zero itself); calls
+ *   that overlap on the GPU (other streams, other host threads) race and
+ *   must be serialised by the caller.
+ * Arguments and results as fmm_eval.
+ */
+#define FMM_STATIC_WORKSPACE_BYTES (32u << 20)
+int fmm_eval_static(fmm_plan_t plan, int64_t n, const float *pos, const float *q,
+                    void *potential, double *energy, void *forces, void *stream);
+
 /* Static string naming a status code. */
 const char *fmm_strerror(int status);
 

@@ -42,7 +42,10 @@ FMM_DUMP_OUT = 8
 # every symbol include/fmm_gb300.h declares
 EXPORTED = ["fmm_opts_default", "fmm_plan_create", "fmm_plan_destroy", "fmm_workspace_size",
             "fmm_eval", "fmm_backward", "fmm_status", "fmm_debug_dump", "fmm_debug_size",
-            "fmm_set_timing", "fmm_get_stats", "fmm_strerror", "fmm_version"]
+            "fmm_set_timing", "fmm_get_stats", "fmm_strerror", "fmm_version",
+            "fmm_eval_static"]
+
+FMM_STATIC_WORKSPACE_BYTES = 32 << 20
 
 STAGES = ["bin", "sort", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "unsplit"]
 
@@ -92,6 +95,7 @@ def lib():
         L.fmm_strerror.argtypes = [i32]
         L.fmm_strerror.restype = ctypes.c_char_p
         L.fmm_version.argtypes = []
+        L.fmm_eval_static.argtypes = [P, i64, P, P, P, P, P, P]
         _lib = L
     return _lib
 
