@@ -39,7 +39,10 @@ class FMM:
     eval(pos, q) -> dict(potential, energy, forces) for device tensors
     (float32 positions (n,3), charges (n,)); outputs are float32, or float64
     for precision="fp64".  Host tensors are copied to the device and the
-    results back (the end-to-end path).
+    results back (the end-to-end path); host results are views of pinned
+    buffers the plan keeps and overwrites on its next host call (clone to keep).
+    precision: "fp32" (SIMT contraction), "fp64", "tf32x3" (contraction of
+    levels >= 4 on the tcgen05 tensor cores, 3-pass split TF32; p = 4).
     """
 
     def __init__(self, box, depth, p, periodic=False, continuous=False, split_ratio=None,
@@ -125,8 +128,30 @@ class FMM:
         res = {"potential": phi if potential else None, "energy": E if energy else None,
                "forces": F if forces else None}
         if host:
-            res = {k: (v.to("cpu") if v is not None else None) for k, v in res.items()}
+            # results into pinned host buffers (kept by the plan), one wait at the end
+            hb = self._host_out(n)
+            stream_t = torch.cuda.current_stream() if stream is None else stream
+            out_h = {}
+            for k, v in res.items():
+                if v is None:
+                    out_h[k] = None
+                    continue
+                h = hb[k][: v.numel()].view(v.shape)
+                h.copy_(v, non_blocking=True)
+                out_h[k] = h
+            stream_t.synchronize()
+            res = out_h
         return res
+
+    def _host_out(self, n):
+        hb = getattr(self, "_hbuf", None)
+        if hb is None or hb["n"] < n:
+            hb = {"n": n,
+                  "potential": torch.empty(n, dtype=self.out_dtype).pin_memory(),
+                  "energy": torch.empty(1, dtype=torch.float64).pin_memory(),
+                  "forces": torch.empty(3 * n, dtype=self.out_dtype).pin_memory()}
+            self._hbuf = hb
+        return hb
 
     def backward(self, grad_energy, stream=None):
         """dLoss/dpos = -F * gE and dLoss/dq = phi * gE from the last eval's state."""

@@ -26,6 +26,9 @@ struct fmm_plan_s {
     void *Kbar;   // [343][p^3] row means of the unit-cell kernels
     void *Klat;   // [p^3][p^3] lattice kernel minus its row mean (periodic form)
     void *Klbar;  // [p^3] row means of the lattice kernel
+    void *Ktc_hi, *Ktc_lo;  // [343][a][b] TF32 split of the unit-cell kernels (TF32X3 plans)
+    alignas(64) unsigned char khi_map[128], klo_map[128];  // their TMA tensor maps
+    bool tc;                // bilinear forms of levels >= 4 on tensor cores
     Coef<float> cf;
     Coef<double> cd;
     Geom geom;
@@ -146,6 +149,45 @@ int upload_tables(fmm_plan_t P) {
     int rc = upload(&P->Kunit, KtT);
     if (!rc) rc = upload(&P->Kbar, Kbar);
     if (rc) return rc;
+    if (P->tc) {
+        // Kt_o[a][b] = K_o[a][b] - Kbar_o[a] (natural layout), split as hi =
+        // Kt with its 13 low mantissa bits cleared, lo = Kt - hi (from the FP64
+        // value): hi exact in TF32
+        std::vector<float> Khi(nk, 0.0f), Klo(nk, 0.0f);
+        for (int oi = 0; oi < 343; oi++) {
+            int ox = oi % 7 - 3, oy = (oi / 7) % 7 - 3, oz = oi / 49 - 3;
+            if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
+            for (int a = 0; a < p3; a++) {
+                double ax = node(p, a % p), ay = node(p, (a / p) % p), az = node(p, a / (p * p));
+                double mean = 0.0;
+                for (int b = 0; b < p3; b++) {
+                    double dx = ax - (ox + node(p, b % p));
+                    double dy = ay - (oy + node(p, (b / p) % p));
+                    double dz = az - (oz + node(p, b / (p * p)));
+                    row[b] = 1.0 / std::sqrt(dx * dx + dy * dy + dz * dz);
+                    mean += row[b];
+                }
+                mean /= p3;
+                for (int b = 0; b < p3; b++) {
+                    double k = row[b] - mean;
+                    float f = (float)k;
+                    uint32_t u;
+                    memcpy(&u, &f, 4);
+                    u &= 0xFFFFE000u;
+                    float hi;
+                    memcpy(&hi, &u, 4);
+                    size_t idx = ((size_t)oi * p3 + a) * p3 + b;
+                    Khi[idx] = hi;
+                    Klo[idx] = (float)(k - (double)hi);
+                }
+            }
+        }
+        rc = upload(&P->Ktc_hi, Khi);
+        if (!rc) rc = upload(&P->Ktc_lo, Klo);
+        if (!rc) rc = tc_encode_kernel_map(P->khi_map, (const float *)P->Ktc_hi);
+        if (!rc) rc = tc_encode_kernel_map(P->klo_map, (const float *)P->Ktc_lo);
+        if (rc) return rc;
+    }
     if (P->periodic) {
         // psi depends on a - b only: (2p-1)^3 distinct arguments
         const int m = 2 * p - 1;
@@ -240,6 +282,22 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     }
     W.q_level[P->depth + 1] = qc;
     W.qlev = take((size_t)qc * rs);
+    size_t part = 0;
+    for (int l = 2; l <= P->depth; l++) {
+        int G = m2l_groups(l, p3);
+        if (G > 1) {
+            size_t need = (size_t)G * ((size_t)1 << (3 * l)) * p3;
+            if (need > part) part = need;
+        }
+    }
+    if (P->periodic) {
+        int G = m2l_groups(1, p3);
+        size_t need = (size_t)G * 8 * p3;
+        if (G > 1 && need > part) part = need;
+    }
+    W.m2l_part = take(part * rs);
+    W.phihi = take(P->tc ? (size_t)ph * p3 * rs : 0);
+    W.philo = take(P->tc ? (size_t)ph * p3 * rs : 0);
     int64_t mx = n > W.ncell ? n : W.ncell;
     W.scan_blocks = (int)(mx / 2048 + 2);
     W.scan_tmp = take((size_t)(W.scan_blocks + 1) * 4);
@@ -273,12 +331,16 @@ Ptrs<real> make_ptrs(const WsLayout &W, void *ws) {
     P.phi = (real *)(b + W.phi);
     P.loc = (real *)(b + W.loc);
     P.qlev = (real *)(b + W.qlev);
+    P.m2l_part = (real *)(b + W.m2l_part);
+    P.phihi = (real *)(b + W.phihi);
+    P.philo = (real *)(b + W.philo);
     P.scan_tmp = (int *)(b + W.scan_tmp);
     P.epart = (double *)(b + W.epart);
     return P;
 }
 
 int status_to_error(int st) {
+    if (st & ST_TIMEOUT) return FMM_ERR_TIMEOUT;
     if (st & ST_NONFINITE) return FMM_ERR_NONFINITE;
     if (st & ST_OUT_OF_BOX) return FMM_ERR_OUT_OF_BOX;
     if (st & ST_SPLIT_OVERFLOW) return FMM_ERR_SPLIT_OVERFLOW;
@@ -332,7 +394,11 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     T.Kbar = (const real *)P->Kbar;
     T.Klt = (const real *)P->Klat;
     T.Klbar = (const real *)P->Klbar;
-    launch_downward<real>(g, C, ptr, W, T, st, tr);
+    T.tc_lmin = P->tc ? 4 : 0;
+    T.tc_khi_map = P->khi_map;
+    T.tc_klo_map = P->klo_map;
+    int rc = launch_downward<real>(g, C, ptr, W, T, st, tr);
+    if (rc) return rc;
     launch_evaluate<real>(g, C, ptr, W, forces != nullptr, st, tr);
     launch_unsplit<real>(g, ptr, W, (int)n, q, potential, energy, forces, nullptr, nullptr, false,
                          st, tr);
@@ -414,7 +480,10 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     if (opts) o = *opts;
     if (o.split_ratio <= 0) o.split_ratio = 1.0 / 256.0;
     if (o.continuous && !(o.split_ratio < 0.5)) return FMM_ERR_ARG;
-    if (o.precision != FMM_PREC_FP32 && o.precision != FMM_PREC_FP64) return FMM_ERR_UNSUPPORTED;
+    if (o.precision != FMM_PREC_FP32 && o.precision != FMM_PREC_FP64 &&
+        o.precision != FMM_PREC_TF32X3)
+        return FMM_ERR_UNSUPPORTED;
+    if (o.precision == FMM_PREC_TF32X3 && p != 4) return FMM_ERR_UNSUPPORTED;
     fmm_plan_s *P = new (std::nothrow) fmm_plan_s();
     if (!P) return FMM_ERR_OOM;
     P->depth = depth;
@@ -424,6 +493,7 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     memcpy(P->box, box, sizeof(double) * 4);
     P->max_n = max_n;
     P->fp64 = o.precision == FMM_PREC_FP64;
+    P->tc = o.precision == FMM_PREC_TF32X3;
     cudaGetDevice(&P->device);
     fill_coef<float>(p, P->cf);
     fill_coef<double>(p, P->cd);
@@ -461,6 +531,8 @@ void fmm_plan_destroy(fmm_plan_t P) {
     if (P->Kbar) cudaFree(P->Kbar);
     if (P->Klat) cudaFree(P->Klat);
     if (P->Klbar) cudaFree(P->Klbar);
+    if (P->Ktc_hi) cudaFree(P->Ktc_hi);
+    if (P->Ktc_lo) cudaFree(P->Ktc_lo);
     if (P->h_hdr) cudaFreeHost(P->h_hdr);
     delete P;
 }

@@ -52,6 +52,7 @@ struct WsHeader {
 #define ST_OUT_OF_BOX 1
 #define ST_NONFINITE 2
 #define ST_SPLIT_OVERFLOW 4
+#define ST_TIMEOUT 8
 
 // Workspace carving (byte offsets), computed on the host for (plan, n).
 struct WsLayout {
@@ -63,6 +64,8 @@ struct WsLayout {
     size_t s_pt, s_origin, out_pt;
     size_t phi, loc;                      // all levels
     size_t qlev;                          // total charge of every cell, padded Phi layout
+    size_t phihi, philo;                  // TF32 split of Phi (tensor-core plans)
+    size_t m2l_part;                      // per-offset-group partials of the SIMT contraction
     size_t scan_tmp, epart;
     size_t total;
     int64_t cap;                          // charge capacity
@@ -155,6 +158,8 @@ struct Ptrs {
     typename Vec4<real>::T *out_pt;
     real *phi, *loc;
     real *qlev;
+    real *phihi, *philo;
+    real *m2l_part;
     int *scan_tmp;
     double *epart;
 };
@@ -170,7 +175,20 @@ struct DevTables {
     const real *Kbar;   // [343][a]
     const real *Klt;    // [a][b] lattice kernel minus its row mean (periodic form)
     const real *Klbar;  // [a]
+    // tensor-core contraction (TF32X3 plans): levels >= tc_lmin, 0 = none
+    int tc_lmin;
+    const void *tc_khi_map, *tc_klo_map;  // CUtensorMap of the split unit-cell kernels
 };
+
+// Offset groups of the SIMT contraction at level l: the 189 offsets of a
+// target tile are split over G CTAs when a level has too few tiles to fill
+// the GPU; each CTA writes a partial, summed afterwards in a fixed order.
+__host__ __device__ inline int m2l_groups(int l, int p3) {
+    int H = 1 << (l - 1), T = H < 4 ? H : 4;
+    int ctas = (H / T) * (H / T) * (H / T) * 8 * ((p3 + 63) / 64);
+    int G = (2 * 152 + ctas - 1) / ctas;
+    return G < 1 ? 1 : (G > 27 ? 27 : G);
+}
 
 // tree / bookkeeping stage (kernels_tree.cu)
 template <typename real>
@@ -190,8 +208,14 @@ template <typename real>
 void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
                    cudaStream_t st, Tracer &tr);
 template <typename real>
-void launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
-                     const DevTables<real> &T, cudaStream_t st, Tracer &tr);
+int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
+                    const DevTables<real> &T, cudaStream_t st, Tracer &tr);
+
+// tensor-core contraction (m2l_tc.cu)
+int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
+                  const void *k_lo_map, const float *kbar, int lmin, cudaStream_t st, Tracer &tr);
+int tc_encode_kernel_map(void *map, const float *base);
+size_t tc_map_bytes();
 
 // near field + far-field evaluation at the charges (kernels_p2p.cu)
 template <typename real>

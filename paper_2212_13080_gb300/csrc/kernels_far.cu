@@ -1,6 +1,8 @@
 // Far field: replacement at the finest cells (P2M), shift up (M2M), the
 // grid-to-grid bilinear forms of the interaction lists (M2L), the periodic
 // lattice term, and the shift-transpose down (L2L).
+#include <type_traits>
+
 #include "fmm_internal.cuh"
 #include "lagrange.cuh"
 
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
                                                      const real *__restrict__ q_l,
                                                      real *__restrict__ loc_l,
                                                      const real *__restrict__ KtT,
-                                                     const real *__restrict__ Kbar, int accumulate) {
+                                                     const real *__restrict__ Kbar, int ngroups) {
     typedef typename Vec4<real>::T real4;
     extern __shared__ __align__(16) unsigned char smraw[];
     real *Ps = reinterpret_cast<real *>(smraw);  // [64 b][64 cells]
@@ -194,7 +196,11 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
     const int H = 1 << (l - 1), P = H + 2;
     const int T = H < 4 ? H : 4;  // tile edge in coarse cells
     const int ntx = H / T;
-    const int tile = blockIdx.x, par = blockIdx.y, a0 = blockIdx.z * M2L_T;
+    const int tile = blockIdx.x, par = blockIdx.y;
+    const int a0 = (blockIdx.z / ngroups) * M2L_T, grp = blockIdx.z % ngroups;
+    const int per = (189 + ngroups - 1) / ngroups;
+    const int off_lo = grp * per, off_hi = off_lo + per;  // this CTA's offsets
+    int off_idx = -1;
     const int TX = (tile % ntx) * T, TY = ((tile / ntx) % ntx) * T, TZ = (tile / (ntx * ntx)) * T;
     const int bx = par & 1, by = (par >> 1) & 1, bz = (par >> 2) & 1;
     const int ncell = T * T * T;
@@ -212,6 +218,8 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
         for (int oy = -2 - by; oy <= 3 - by; oy++)
             for (int ox = -2 - bx; ox <= 3 - bx; ox++) {
                 if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+                off_idx++;
+                if (off_idx < off_lo || off_idx >= off_hi) continue;
 #pragma unroll
                 for (int i = 0; i < 4; i++)
 #pragma unroll
@@ -284,22 +292,33 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
                         tot[i][j] = t;
                     }
             }
+    // ngroups > 1: loc_l is the partial buffer of this group (level layout)
     const real scale = (real)(1 << l);
+    real *dst = loc_l + (int64_t)grp * ((int64_t)1 << (3 * l)) * p3;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         int ci = cg * 4 + i;
         if (ci >= ncell) continue;
         int tx = ci % T, ty = (ci / T) % T, tz = ci / (T * T);
         int cx = 2 * (TX + tx) + bx, cy = 2 * (TY + ty) + by, cz = 2 * (TZ + tz) + bz;
-        real *out = loc_l + loc_cell(l, cx, cy, cz) * p3;
+        real *out = dst + loc_cell(l, cx, cy, cz) * p3;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             int a = a0 + ag * 4 + j;
-            if (a < p3) {
-                real v = scale * tot[i][j];
-                out[a] = accumulate ? out[a] + v : v;
-            }
+            if (a < p3) out[a] = scale * tot[i][j];
         }
+    }
+}
+
+// sum of the offset-group partials, in group order
+template <typename real>
+__global__ void k_m2l_reduce(int ngroups, int64_t n, const real *__restrict__ part,
+                             real *__restrict__ loc_l) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        real s = 0;
+        for (int g = 0; g < ngroups; g++) s += part[(int64_t)g * n + i];
+        loc_l[i] = s;
     }
 }
 
@@ -318,8 +337,9 @@ __global__ void k_lattice(int p3, const real *__restrict__ Klt, const real *__re
 
 // ---------------------------------------------------------------------------
 // §2.2 step 3: Psi_child(v) = Psi_parent(shift_{child->parent}(v)), i.e.
-// L_child_h = (G_hx (x) G_hy (x) G_hz)^T L_parent, as three passes (z, y, x).
-// One CTA per parent of level l-1; writes the 8 children of level l.
+// L_child_h += (G_hx (x) G_hy (x) G_hz)^T L_parent, as three passes (z, y, x).
+// One CTA per parent of level l-1; adds to the 8 children of level l (which
+// already hold their own interaction-list contributions).
 // ---------------------------------------------------------------------------
 template <typename real>
 __global__ void __launch_bounds__(M2M_BS) k_l2l(Coef<real> C, int p, int l, const real *__restrict__ loc_parent,
@@ -360,7 +380,7 @@ __global__ void __launch_bounds__(M2M_BS) k_l2l(Coef<real> C, int p, int l, cons
         real s = 0;
         for (int I = 0; I < p; I++) s += G[I * p + i] * b[I];
         int cx = 2 * px + hx, cy = 2 * py + hy, cz = 2 * pz + hz;
-        loc_child[loc_cell(l, cx, cy, cz) * p3 + o] = s;
+        loc_child[loc_cell(l, cx, cy, cz) * p3 + o] += s;
     }
 }
 
@@ -403,45 +423,60 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
 }
 
 template <typename real>
-void launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
-                     const DevTables<real> &T, cudaStream_t st, Tracer &tr) {
+int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
+                    const DevTables<real> &T, cudaStream_t st, Tracer &tr) {
     const int p = g.p, p3 = g.p3, depth = g.depth;
     const int achunks = (p3 + M2L_T - 1) / M2L_T;
     const size_t sm_m2l = sizeof(real) * (2 * M2L_T * M2L_T + 2 * M2L_T);
     const size_t sm_l2l = sizeof(real) * 7 * p3;
-    int lstart;
+    // 1. every level's own interaction-list contributions (they only need Phi):
+    //    L_0 = lattice term (periodic), L_l = sum over the interaction list
+    const int lstart = g.periodic ? 1 : 2;
     if (g.periodic) {
         tr.begin(FMM_STAGE_M2L);
         k_lattice<real><<<1, 256, 0, st>>>(p3, T.Klt, T.Klbar, P.phi + W.phi_level[0],
                                            P.qlev + W.q_level[0], P.loc + W.loc_level[0]);
         tr.count();
         tr.end();
-        lstart = 1;
-    } else {
-        lstart = 2;
     }
-    for (int l = lstart; l <= depth; l++) {
-        const bool have_parent = g.periodic || l >= 3;
-        if (have_parent) {
-            int nparent = 1 << (3 * (l - 1));
-            tr.begin(FMM_STAGE_L2L);
-            k_l2l<real><<<nparent, M2M_BS, sm_l2l, st>>>(C, p, l, P.loc + W.loc_level[l - 1],
-                                                         P.loc + W.loc_level[l]);
-            tr.count();
-            tr.end();
-        }
+    int lsimt_end = depth;
+    if (T.tc_lmin > 0 && depth >= T.tc_lmin) lsimt_end = T.tc_lmin - 1;
+    for (int l = lstart; l <= lsimt_end; l++) {
         const int H = 1 << (l - 1);
         const int Tt = H < 4 ? H : 4;
         const int ntiles = (H / Tt) * (H / Tt) * (H / Tt);
-        dim3 grid(ntiles, 8, achunks);
+        const int G = m2l_groups(l, p3);
+        dim3 grid(ntiles, 8, achunks * G);
+        real *dst = G > 1 ? P.m2l_part : P.loc + W.loc_level[l];
         tr.begin(FMM_STAGE_M2L);
         k_m2l_simt<real><<<grid, M2L_BS, sm_m2l, st>>>(p, l, P.phi + W.phi_level[l],
-                                                       P.qlev + W.q_level[l],
-                                                       P.loc + W.loc_level[l], T.KtT, T.Kbar,
-                                                       have_parent ? 1 : 0);
+                                                       P.qlev + W.q_level[l], dst, T.KtT, T.Kbar, G);
+        tr.count();
+        if (G > 1) {
+            const int64_t n = ((int64_t)1 << (3 * l)) * p3;
+            int nb = (int)((n + 255) / 256);
+            if (nb > 152 * 16) nb = 152 * 16;
+            k_m2l_reduce<real><<<nb, 256, 0, st>>>(G, n, P.m2l_part, P.loc + W.loc_level[l]);
+            tr.count();
+        }
+        tr.end();
+    }
+    if constexpr (std::is_same<real, float>::value) {
+        if (T.tc_lmin > 0 && depth >= T.tc_lmin) {
+            int rc = launch_m2l_tc(g, P, W, T.tc_khi_map, T.tc_klo_map, T.Kbar, T.tc_lmin, st, tr);
+            if (rc) return rc;
+        }
+    }
+    // 2. downward: Psi_child = Psi_parent o shift, added level by level
+    for (int l = g.periodic ? 1 : 3; l <= depth; l++) {
+        int nparent = 1 << (3 * (l - 1));
+        tr.begin(FMM_STAGE_L2L);
+        k_l2l<real><<<nparent, M2M_BS, sm_l2l, st>>>(C, p, l, P.loc + W.loc_level[l - 1],
+                                                     P.loc + W.loc_level[l]);
         tr.count();
         tr.end();
     }
+    return FMM_OK;
 }
 
 void far_set_attributes() {
@@ -456,10 +491,10 @@ template void launch_upward<float>(const Geom &, const Coef<float> &, const Ptrs
                                    const WsLayout &, cudaStream_t, Tracer &);
 template void launch_upward<double>(const Geom &, const Coef<double> &, const Ptrs<double> &,
                                     const WsLayout &, cudaStream_t, Tracer &);
-template void launch_downward<float>(const Geom &, const Coef<float> &, const Ptrs<float> &,
+template int launch_downward<float>(const Geom &, const Coef<float> &, const Ptrs<float> &,
                                      const WsLayout &, const DevTables<float> &, cudaStream_t,
                                      Tracer &);
-template void launch_downward<double>(const Geom &, const Coef<double> &, const Ptrs<double> &,
+template int launch_downward<double>(const Geom &, const Coef<double> &, const Ptrs<double> &,
                                       const WsLayout &, const DevTables<double> &, cudaStream_t,
                                       Tracer &);
 

@@ -7,10 +7,10 @@
 
 namespace fmm {
 
-template <typename real> __device__ __forceinline__ real rsqrt_r(real x);
-// single precision: the hardware reciprocal square root (2 ulp)
-template <> __device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
-template <> __device__ __forceinline__ double rsqrt_r<double>(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float4 make_vec4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+__device__ __forceinline__ double4 make_vec4(double a, double b, double c, double d) {
+    return make_double4(a, b, c, d);
+}
 
 // ---------------------------------------------------------------------------
 // far field: phi_far = sum_ijk g_i(t_x) g_j(t_y) g_k(t_z) L_leaf[ijk] and
@@ -86,10 +86,13 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, const i
 // ---------------------------------------------------------------------------
 // near field.  One CTA of 128 threads per target cell.  The charges of the 27
 // neighbour cells are staged in shared memory, shifted into the target cell's
-// frame (source t + neighbour offset), in chunks.  With T targets the CTA
-// runs G = 128 / T thread groups over the same targets, each taking every
-// G-th source; the G partial sums are added in a fixed order.  Pairs of charges
-// of the same particle (split charges) and coincident pairs are skipped.
+// frame (source t + neighbour offset), in chunks.  Every thread owns two
+// targets (one shared-memory source load serves two pairs); with T targets the
+// CTA runs G = 128 / ceil(T/2) thread groups over the same targets, each taking
+// every G-th source; the G partial sums are added in a fixed order.  Pairs of
+// charges of the same particle (split charges) and coincident pairs are
+// skipped.  Sums: blocks of up to 32 sources into a short partial, partials
+// into the total with Kahan compensation.
 // ---------------------------------------------------------------------------
 template <typename real>
 __device__ __forceinline__ void kahan_add(real &sum, real &c, real x) {
@@ -98,6 +101,38 @@ __device__ __forceinline__ void kahan_add(real &sum, real &c, real x) {
     c = (t - sum) - y;
     sum = t;
 }
+
+// 1/sqrt(r2): single precision uses the SFU reciprocal square root directly
+// (r2 is never subnormal here: it is 0 or a squared distance of FP32 charges
+// inside a few cells); double precision the correctly rounded form.
+template <typename real> __device__ __forceinline__ real rsqrt_pair(real x);
+template <> __device__ __forceinline__ float rsqrt_pair<float>(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+template <> __device__ __forceinline__ double rsqrt_pair<double>(double x) { return 1.0 / sqrt(x); }
+
+template <typename real, bool FORCES>
+struct PairAcc {
+    real p, x, y, z;
+    __device__ __forceinline__ void zero() { p = x = y = z = 0; }
+    __device__ __forceinline__ void add(real tx, real ty, real tz, int to, const typename Vec4<real>::T &sv,
+                                        int so) {
+        real dx = tx - sv.x, dy = ty - sv.y, dz = tz - sv.z;
+        real r2 = dx * dx + dy * dy + dz * dz;
+        real ri = rsqrt_pair<real>(r2);
+        ri = (r2 > real(0) && so != to) ? ri : real(0);
+        real qr = sv.w * ri;
+        p += qr;
+        if (FORCES) {
+            real qr3 = qr * (ri * ri);
+            x += qr3 * dx;
+            y += qr3 * dy;
+            z += qr3 * dz;
+        }
+    }
+};
 
 #define P2P_BS 128
 #define P2P_CHUNK 1024
@@ -111,8 +146,7 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p(int depth, int periodic, const i
     __shared__ real4 src[P2P_CHUNK];
     __shared__ int srco[P2P_CHUNK];
     __shared__ int nb_start[27], nb_off[28];
-    __shared__ real nb_d[27][3];
-    __shared__ real4 part[P2P_BS];
+    __shared__ real4 part[2 * P2P_BS];
 
     const uint32_t key = blockIdx.x;
     const int t0 = leaf_start[key], t1 = leaf_start[key + 1];
@@ -141,9 +175,6 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p(int depth, int periodic, const i
         }
         nb_start[d] = st;
         nb_off[d + 1] = cnt;
-        nb_d[d][0] = (real)dx;
-        nb_d[d][1] = (real)dy;
-        nb_d[d][2] = (real)dz;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -152,109 +183,115 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p(int depth, int periodic, const i
     }
     __syncthreads();
     const int Ns = nb_off[27];
-    int G, TPP;
-    if (T >= P2P_BS) {
-        G = 1;
+    // thread -> (slot, group); a slot owns targets tb + slot and tb + TPP + slot
+    int TPP, G;
+    if (T >= 2 * P2P_BS) {
         TPP = P2P_BS;
+        G = 1;
     } else {
-        G = P2P_BS / T;
-        TPP = T;
+        TPP = (T + 1) / 2;
+        G = P2P_BS / TPP;
     }
     const int slot = threadIdx.x % TPP, grp = threadIdx.x / TPP;
     const bool grp_ok = grp < G;
     const bool single_chunk = Ns <= P2P_CHUNK;
     bool staged = false;
     const real S_r = (real)S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    for (int tb = 0; tb < T; tb += TPP) {
-        const int tgt = tb + slot;
-        const bool active = grp_ok && tgt < T;
-        real4 tv;
-        int to = -1;
-        if (active) {
-            tv = s_pt[t0 + tgt];
-            to = s_origin[t0 + tgt];
-        } else {
-            tv.x = tv.y = tv.z = tv.w = 0;
+    for (int tb = 0; tb < T; tb += 2 * TPP) {
+        const int ta = tb + slot, tbb = tb + TPP + slot;
+        const bool act_a = grp_ok && ta < T, act_b = grp_ok && tbb < T;
+        real4 va, vb;
+        int oa = -1, ob = -1;
+        va.x = va.y = va.z = va.w = 0;
+        vb = va;
+        if (act_a) {
+            va = s_pt[t0 + ta];
+            oa = s_origin[t0 + ta];
         }
-        // totals with Kahan compensation; each block of up to 32 sources is
-        // first summed into a short partial
-        real phi = 0, fx = 0, fy = 0, fz = 0;
-        real cphi = 0, cfx = 0, cfy = 0, cfz = 0;
+        if (act_b) {
+            vb = s_pt[t0 + tbb];
+            ob = s_origin[t0 + tbb];
+        }
+        PairAcc<real, FORCES> A, Bq, ca, cb;  // totals and Kahan compensations
+        A.zero();
+        Bq.zero();
+        ca.zero();
+        cb.zero();
         for (int c0 = 0; c0 < Ns; c0 += P2P_CHUNK) {
             const int cn = min(P2P_CHUNK, Ns - c0);
             if (!(single_chunk && staged)) {
                 __syncthreads();
-                for (int f = threadIdx.x; f < cn; f += P2P_BS) {
-                    int ff = c0 + f;
-                    int d = 0;
-                    while (nb_off[d + 1] <= ff) d++;
-                    int sidx = nb_start[d] + ff - nb_off[d];
-                    real4 v = s_pt[sidx];
-                    v.x += nb_d[d][0];
-                    v.y += nb_d[d][1];
-                    v.z += nb_d[d][2];
-                    src[f] = v;
-                    srco[f] = s_origin[sidx];
+                // neighbour by neighbour, one warp per neighbour cell
+                for (int d = warp; d < 27; d += P2P_BS / 32) {
+                    const int lo = max(nb_off[d], c0), hi = min(nb_off[d + 1], c0 + cn);
+                    const real ox = (real)(d % 3 - 1), oy = (real)((d / 3) % 3 - 1), oz = (real)(d / 9 - 1);
+                    for (int f = lo + lane; f < hi; f += 32) {
+                        const int sidx = nb_start[d] + f - nb_off[d];
+                        real4 v = s_pt[sidx];
+                        v.x += ox;
+                        v.y += oy;
+                        v.z += oz;
+                        src[f - c0] = v;
+                        srco[f - c0] = s_origin[sidx];
+                    }
                 }
                 __syncthreads();
                 staged = true;
             }
-            if (active) {
+            if (act_a) {
                 for (int sb = grp; sb < cn; sb += 32 * G) {
                     const int se = min(cn, sb + 32 * G);
-                    real pp = 0, px = 0, py = 0, pz = 0;
+                    PairAcc<real, FORCES> pa, pb;
+                    pa.zero();
+                    pb.zero();
+#pragma unroll 4
                     for (int s = sb; s < se; s += G) {
-                        real4 sv = src[s];
-                        real dx = tv.x - sv.x, dy = tv.y - sv.y, dz = tv.z - sv.z;
-                        real r2 = dx * dx + dy * dy + dz * dz;
-                        bool ok = (r2 > real(0)) && (srco[s] != to);
-                        real ri = ok ? rsqrt_r<real>(r2) : real(0);
-                        real qr = sv.w * ri;
-                        pp += qr;
-                        if (FORCES) {
-                            real qr3 = qr * ri * ri;
-                            px += qr3 * dx;
-                            py += qr3 * dy;
-                            pz += qr3 * dz;
-                        }
+                        const real4 sv = src[s];
+                        const int so = srco[s];
+                        pa.add(va.x, va.y, va.z, oa, sv, so);
+                        pb.add(vb.x, vb.y, vb.z, ob, sv, so);
                     }
-                    kahan_add(phi, cphi, pp);
+                    kahan_add(A.p, ca.p, pa.p);
+                    kahan_add(Bq.p, cb.p, pb.p);
                     if (FORCES) {
-                        kahan_add(fx, cfx, px);
-                        kahan_add(fy, cfy, py);
-                        kahan_add(fz, cfz, pz);
+                        kahan_add(A.x, ca.x, pa.x);
+                        kahan_add(A.y, ca.y, pa.y);
+                        kahan_add(A.z, ca.z, pa.z);
+                        kahan_add(Bq.x, cb.x, pb.x);
+                        kahan_add(Bq.y, cb.y, pb.y);
+                        kahan_add(Bq.z, cb.z, pb.z);
                     }
                 }
             }
         }
         // fixed-order sum over the groups, then add to the far field
-        real4 pv;
-        pv.x = phi;
-        pv.y = fx;
-        pv.z = fy;
-        pv.w = fz;
         __syncthreads();
-        part[threadIdx.x] = pv;
+        part[threadIdx.x] = make_vec4(A.p, A.x, A.y, A.z);
+        part[P2P_BS + threadIdx.x] = make_vec4(Bq.p, Bq.x, Bq.y, Bq.z);
         __syncthreads();
-        if (threadIdx.x < TPP && tb + threadIdx.x < T) {
-            real4 s = part[threadIdx.x];
+        for (int k = threadIdx.x; k < 2 * TPP; k += P2P_BS) {
+            const int half = k / TPP, sl = k % TPP;
+            const int tgt = tb + half * TPP + sl;
+            if (tgt >= T) continue;
+            real4 sum = part[half * P2P_BS + sl];
             for (int g2 = 1; g2 < G; g2++) {
-                real4 o = part[threadIdx.x + g2 * TPP];
-                s.x += o.x;
-                s.y += o.y;
-                s.z += o.z;
-                s.w += o.w;
+                real4 o = part[half * P2P_BS + sl + g2 * TPP];
+                sum.x += o.x;
+                sum.y += o.y;
+                sum.z += o.z;
+                sum.w += o.w;
             }
             // unit-box units: 1/r_u = S / r_t, (x/r^3)_u = S^2 (x/r^3)_t
-            const int sl = t0 + tb + threadIdx.x;
-            real4 out = out_pt[sl];
-            const real qt = s_pt[sl].w;
-            out.x += S_r * s.x;
-            out.y += qt * S_r * S_r * s.y;
-            out.z += qt * S_r * S_r * s.z;
-            out.w += qt * S_r * S_r * s.w;
-            out_pt[sl] = out;
+            const int si = t0 + tgt;
+            real4 out = out_pt[si];
+            const real qt = s_pt[si].w;
+            out.x += S_r * sum.x;
+            out.y += qt * S_r * S_r * sum.y;
+            out.z += qt * S_r * S_r * sum.z;
+            out.w += qt * S_r * S_r * sum.w;
+            out_pt[si] = out;
         }
     }
 }

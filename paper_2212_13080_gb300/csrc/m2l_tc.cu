@@ -1,0 +1,350 @@
+// Bilinear forms of the interaction lists (§2.2 step 3, eq. bilinear) on the
+// 5th-generation tensor cores (tcgen05), 3-pass split TF32.
+//
+// For one level, one target parity and one box of 8x4x4 coarse cells (128
+// target cells = the MMA's M), every one of the 189 interaction-list offsets o
+// contributes L[cell][a] += sum_b Phi[cell + o][b] K_o[a][b]: a 128 x 64 x 64
+// GEMM whose A operand (the 128 source vectors) is one rectangular box of the
+// padded parity-major Phi layout and whose B operand is the unit-cell kernel.
+// Both arrive by TMA, in two 128-byte K halves, into a 2-stage ring; one
+// thread issues the MMAs.
+//
+// Accuracy.  Split precision: x = hi + lo with hi = x with its 13 low mantissa
+// bits cleared (exact in TF32); D = Ahi Bhi + Ahi Blo + Alo Bhi.  The kernel
+// is split as K_o = Kbar_o[a] + Kt_o[a,b] (row mean): the tensor cores contract
+// Kt_o, the CUDA cores add Kbar_o[a] Q (Q = the source cell's total charge).
+// Each offset accumulates into a fresh TMEM region (two regions, alternating):
+// the four epilogue warps read it out and add the 189 partials in FP32
+// registers, so no FP32 accumulator in TMEM sees more than 24 MMAs (the
+// tensor cores' accumulation is not round-to-nearest; over 1512 MMAs it
+// drifted by ~1e-4).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "fmm_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fmm {
+
+#define TC_M 128
+#define TC_N 64
+#define TC_STAGES 2
+#define TC_ABYTES (TC_M * 128)                      // 128 rows x 32 fp32
+#define TC_BBYTES (TC_N * 128)                      // 64 rows x 32 fp32
+#define TC_STAGE (2 * TC_ABYTES + 2 * TC_BBYTES)    // Ahi, Alo, Bhi, Blo
+#define TC_THREADS 192
+#define TC_SMEM (TC_STAGES * TC_STAGE + 1024 + 128)
+#define TC_WAIT_CYCLES (4LL << 30)                  // about 2 s of SM clock
+#define TC_NOFF 189
+
+struct TcParams {
+    CUtensorMap phi_hi[FMM_MAXDEPTH + 1];
+    CUtensorMap phi_lo[FMM_MAXDEPTH + 1];
+    CUtensorMap k_hi, k_lo;
+    int first_block[FMM_MAXDEPTH + 2];
+    int lmin, lmax;
+    long long loc_off[FMM_MAXDEPTH + 1];
+    long long q_off[FMM_MAXDEPTH + 1];
+    float *loc;
+    const float *qlev;
+    const float *kbar;  // [343][64]
+    int *status;
+};
+
+// The i-th offset of the interaction list of parity (bx, by, bz), in the
+// order shared by the producer and the epilogue.
+struct Off {
+    int oi, spar, dX, dY, dZ;
+};
+__device__ __forceinline__ bool next_offset(int bx, int by, int bz, int &ox, int &oy, int &oz) {
+    do {
+        if (++ox > 3 - bx) {
+            ox = -2 - bx;
+            if (++oy > 3 - by) {
+                oy = -2 - by;
+                if (++oz > 3 - bz) return false;
+            }
+        }
+    } while (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1);
+    return true;
+}
+__device__ __forceinline__ Off make_off(int bx, int by, int bz, int ox, int oy, int oz) {
+    Off f;
+    const int sx = bx + ox, sy = by + oy, sz = bz + oz;
+    f.spar = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
+    f.dX = sx >> 1;
+    f.dY = sy >> 1;
+    f.dZ = sz >> 1;
+    f.oi = ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3);
+    return f;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(const __grid_constant__ TcParams prm) {
+    extern __shared__ unsigned char smraw[];
+    const uint32_t raw = tc::smem_u32(smraw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    const uint32_t bars = sbase + TC_STAGES * TC_STAGE;
+    const uint32_t full0 = bars, empty0 = bars + 16, rfull0 = bars + 32, rfree0 = bars + 48;
+    const uint32_t done = bars + 64;  // every MMA of this CTA has completed
+    const uint32_t tslot = bars + 72;
+    volatile uint32_t *tslot_ptr = reinterpret_cast<volatile uint32_t *>(smraw + (tslot - raw));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // block -> level, target parity, tile of 8x4x4 coarse cells
+    int l = prm.lmin;
+    while (l < prm.lmax && (int)blockIdx.x >= prm.first_block[l + 1]) l++;
+    const int rel = blockIdx.x - prm.first_block[l];
+    const int H = 1 << (l - 1), P = H + 2;
+    const int ntx = H / 8, nty = H / 4, ntz = H / 4;
+    const int ntiles = ntx * nty * ntz;
+    const int par = rel / ntiles, tile = rel % ntiles;
+    const int X0 = (tile % ntx) * 8, Y0 = ((tile / ntx) % nty) * 4, Z0 = (tile / (ntx * nty)) * 4;
+    const int bx = par & 1, by = (par >> 1) & 1, bz = par >> 2;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; s++) {
+            tc::mbar_init(full0 + 8 * s, 1);
+            tc::mbar_init(empty0 + 8 * s, 1);
+            tc::mbar_init(rfull0 + 8 * s, 1);
+            tc::mbar_init(rfree0 + 8 * s, 128);
+        }
+        tc::mbar_init(done, 1);
+        tc::fence_barrier_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 2 * TC_N);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot_ptr;
+
+    if (warp == 4 && lane == 0) {
+        // ---- TMA producer: (offset, K half) stages ----
+        bool failed = false;
+        int last_phase[TC_STAGES] = {-1, -1};
+        int ox = -2 - bx - 1, oy = -2 - by, oz = -2 - bz, it = 0;
+        while (!failed && next_offset(bx, by, bz, ox, oy, oz)) {
+            const Off f = make_off(bx, by, bz, ox, oy, oz);
+            const int cX = X0 + 1 + f.dX, cY = Y0 + 1 + f.dY, cZ = Z0 + 1 + f.dZ;
+            for (int kh = 0; kh < 2; kh++, it++) {
+                const int s = it % TC_STAGES;
+                const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+                if (!tc::mbar_wait(empty0 + 8 * s, ph ^ 1u, TC_WAIT_CYCLES)) {
+                    failed = true;
+                    break;
+                }
+                const uint32_t st = sbase + s * TC_STAGE;
+                const uint32_t fb = full0 + 8 * s;
+                tc::mbar_expect_tx(fb, TC_STAGE);
+                tc::tma_load_5d(st, &prm.phi_hi[l], fb, kh * 32, cX, cY, cZ, f.spar);
+                tc::tma_load_5d(st + TC_ABYTES, &prm.phi_lo[l], fb, kh * 32, cX, cY, cZ, f.spar);
+                tc::tma_load_3d(st + 2 * TC_ABYTES, &prm.k_hi, fb, kh * 32, 0, f.oi);
+                tc::tma_load_3d(st + 2 * TC_ABYTES + TC_BBYTES, &prm.k_lo, fb, kh * 32, 0, f.oi);
+                last_phase[s] = (int)ph;
+            }
+        }
+        if (failed) {
+            atomicOr(prm.status, ST_TIMEOUT);
+            // let the copies already issued land before the CTA can exit
+            for (int s = 0; s < TC_STAGES; s++)
+                if (last_phase[s] >= 0) tc::mbar_wait(full0 + 8 * s, (uint32_t)last_phase[s], TC_WAIT_CYCLES);
+        }
+    } else if (warp == 5 && lane == 0) {
+        // ---- MMA issuer: offset i accumulates into TMEM region i & 1 ----
+        const uint32_t idesc = tc::idesc_tf32(TC_M, TC_N);
+        bool failed = false;
+        for (int i = 0; i < TC_NOFF && !failed; i++) {
+            const int r = i & 1;
+            const uint32_t u = (uint32_t)(i >> 1) & 1u;
+            if (!tc::mbar_wait(rfree0 + 8 * r, u ^ 1u, TC_WAIT_CYCLES)) {
+                failed = true;
+                break;
+            }
+            const uint32_t d = tmem + (uint32_t)(r * TC_N);
+            for (int kh = 0; kh < 2; kh++) {
+                const int it = 2 * i + kh;
+                const int s = it % TC_STAGES;
+                const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+                if (!tc::mbar_wait(full0 + 8 * s, ph, TC_WAIT_CYCLES)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t st = sbase + s * TC_STAGE;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {  // K = 8 tf32 = 32 bytes per MMA
+                    const uint64_t ah = tc::desc_sw128(st + 32 * k);
+                    const uint64_t al = tc::desc_sw128(st + TC_ABYTES + 32 * k);
+                    const uint64_t bh = tc::desc_sw128(st + 2 * TC_ABYTES + 32 * k);
+                    const uint64_t bl = tc::desc_sw128(st + 2 * TC_ABYTES + TC_BBYTES + 32 * k);
+                    tc::mma_tf32(d, ah, bh, idesc, (kh | k) != 0);
+                    tc::mma_tf32(d, ah, bl, idesc, 1u);
+                    tc::mma_tf32(d, al, bh, idesc, 1u);
+                }
+                tc::mma_commit(empty0 + 8 * s);
+            }
+            if (!failed) tc::mma_commit(rfull0 + 8 * r);
+        }
+        if (failed) atomicOr(prm.status, ST_TIMEOUT);
+        tc::mma_commit(done);  // always: the deallocation waits on it
+    } else if (warp < 4) {
+        // ---- epilogue: TMEM lane = target cell; sum the per-offset partials ----
+        const int row = warp * 32 + lane;
+        const int tx = row & 7, ty = (row >> 3) & 3, tz = row >> 5;
+        const float *q = prm.qlev + prm.q_off[l];
+        float tot[TC_N];
+#pragma unroll
+        for (int j = 0; j < TC_N; j++) tot[j] = 0.0f;
+        bool ok = true;
+        int ox = -2 - bx - 1, oy = -2 - by, oz = -2 - bz;
+        for (int i = 0; i < TC_NOFF; i++) {
+            next_offset(bx, by, bz, ox, oy, oz);
+            const Off f = make_off(bx, by, bz, ox, oy, oz);
+            const float Qs = q[(((int64_t)f.spar * P + Z0 + tz + 1 + f.dZ) * P + Y0 + ty + 1 + f.dY) * P +
+                               X0 + tx + 1 + f.dX];
+            const float4 *kb = reinterpret_cast<const float4 *>(prm.kbar + (int64_t)f.oi * TC_N);
+            const int r = i & 1;
+            const uint32_t u = (uint32_t)(i >> 1) & 1u;
+            if (ok && !tc::mbar_wait(rfull0 + 8 * r, u, TC_WAIT_CYCLES)) ok = false;
+            tc::fence_after_sync();
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(r * TC_N);
+#pragma unroll
+            for (int c = 0; c < TC_N / 16; c++) {
+                uint32_t v[16];
+                tc::tmem_ld16(taddr + c * 16, v);
+#pragma unroll
+                for (int j = 0; j < 16; j += 4) {
+                    const float4 m = kb[(c * 16 + j) >> 2];
+                    tot[c * 16 + j] += __uint_as_float(v[j]) + m.x * Qs;
+                    tot[c * 16 + j + 1] += __uint_as_float(v[j + 1]) + m.y * Qs;
+                    tot[c * 16 + j + 2] += __uint_as_float(v[j + 2]) + m.z * Qs;
+                    tot[c * 16 + j + 3] += __uint_as_float(v[j + 3]) + m.w * Qs;
+                }
+            }
+            tc::fence_before_sync();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rfree0 + 8 * r) : "memory");
+        }
+        const int cx = 2 * (X0 + tx) + bx, cy = 2 * (Y0 + ty) + by, cz = 2 * (Z0 + tz) + bz;
+        float *out = prm.loc + prm.loc_off[l] + loc_cell(l, cx, cy, cz) * TC_N;
+        const float scale = (float)(1 << l);
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < TC_N; j += 4)
+                *reinterpret_cast<float4 *>(out + j) =
+                    make_float4(scale * tot[j], scale * tot[j + 1], scale * tot[j + 2], scale * tot[j + 3]);
+        } else if (lane == 0) {
+            atomicOr(prm.status, ST_TIMEOUT);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::mbar_wait(done, 0, TC_WAIT_CYCLES);
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 2 * TC_N);
+    }
+}
+
+// hi = x with the 13 low mantissa bits cleared (exact in TF32), lo = x - hi
+__global__ void k_split_tf32(const float *__restrict__ x, float *__restrict__ hi,
+                             float *__restrict__ lo, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float v = x[i];
+        float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        hi[i] = h;
+        lo[i] = v - h;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// Grid-charge box map of level l: dims (64 b, P x, P y, P z, 8 parity), box (32, 8, 4, 4, 1).
+static int encode_phi_map(CUtensorMap *m, const float *base, int l) {
+    auto enc = encode_fn();
+    if (!enc) return FMM_ERR_CUDA;
+    const cuuint64_t P = ((cuuint64_t)1 << (l - 1)) + 2;
+    cuuint64_t dims[5] = {64, P, P, P, 8};
+    cuuint64_t strides[4] = {64 * 4, 64 * 4 * P, 64 * 4 * P * P, 64 * 4 * P * P * P};
+    cuuint32_t box[5] = {32, 8, 4, 4, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void *)base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? FMM_OK : FMM_ERR_CUDA;
+}
+
+// Kernel-table map: dims (64 b, 64 a, 343 offsets), box (32, 64, 1).
+int tc_encode_kernel_map(void *map, const float *base) {
+    auto enc = encode_fn();
+    if (!enc) return FMM_ERR_CUDA;
+    cuuint64_t dims[3] = {64, 64, 343};
+    cuuint64_t strides[2] = {64 * 4, 64 * 64 * 4};
+    cuuint32_t box[3] = {32, 64, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc((CUtensorMap *)map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims,
+                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? FMM_OK : FMM_ERR_CUDA;
+}
+
+size_t tc_map_bytes() { return sizeof(CUtensorMap); }
+
+int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
+                  const void *k_lo_map, const float *kbar, int lmin, cudaStream_t st, Tracer &tr) {
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) !=
+            cudaSuccess)
+            return FMM_ERR_CUDA;
+        attr = true;
+    }
+    const int depth = g.depth;
+    // split the grid charges of levels lmin..depth into TF32 hi / lo parts
+    const int64_t a = W.phi_level[lmin], b = W.phi_level[depth + 1];
+    tr.begin(FMM_STAGE_M2L);
+    k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi + a, P.phihi + a, P.philo + a, b - a);
+    tr.count();
+    TcParams prm;
+    memset(&prm, 0, sizeof(prm));
+    int blocks = 0;
+    for (int l = lmin; l <= depth; l++) {
+        int rc = encode_phi_map(&prm.phi_hi[l], P.phihi + W.phi_level[l], l);
+        if (!rc) rc = encode_phi_map(&prm.phi_lo[l], P.philo + W.phi_level[l], l);
+        if (rc) return rc;
+        prm.first_block[l] = blocks;
+        const int H = 1 << (l - 1);
+        blocks += 8 * (H / 8) * (H / 4) * (H / 4);
+        prm.loc_off[l] = W.loc_level[l];
+        prm.q_off[l] = W.q_level[l];
+    }
+    prm.first_block[depth + 1] = blocks;
+    memcpy(&prm.k_hi, k_hi_map, sizeof(CUtensorMap));
+    memcpy(&prm.k_lo, k_lo_map, sizeof(CUtensorMap));
+    prm.lmin = lmin;
+    prm.lmax = depth;
+    prm.loc = P.loc;
+    prm.qlev = P.qlev;
+    prm.kbar = kbar;
+    prm.status = &P.hdr->status;
+    k_m2l_tc<<<blocks, TC_THREADS, TC_SMEM, st>>>(prm);
+    tr.count();
+    tr.end();
+    return FMM_OK;
+}
+
+}  // namespace fmm

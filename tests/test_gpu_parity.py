@@ -107,6 +107,24 @@ def test_parity_small(case, precision):
     plan.close()
 
 
+TOL_TF32X3 = 1e-5  # reduced-precision far field (3-pass split TF32 on tensor cores)
+
+
+@pytest.mark.parametrize("name,n,depth,seed", [("uniform", 40000, 4, 31), ("uniform", 300000, 5, 32)])
+def test_parity_tf32x3(name, n, depth, seed):
+    """Far-field contraction of levels >= 4 on the tcgen05 tensor cores (3-pass
+    split TF32, per-offset accumulators); potentials, energy and forces within
+    the reduced-precision tolerance of the FP64 oracle."""
+    pos, q, box = inputs.uniform_cont(n, seed)
+    s = np.arange(0, n, max(1, n // 2000))
+    ref = oracle.fmm(pos, q, box, depth=depth, n=4, continuous=True, sample=s)
+    plan, out = _gpu(pos, q, box, depth, 4, False, True, None, "tf32x3")
+    _check_integer_work(plan, ref)
+    assert _rel_l2(out["potential"][s], ref["phi"]) < TOL_TF32X3
+    assert _rel_l2(out["forces"][s], ref["F"]) < TOL_TF32X3
+    plan.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_paper_force_mode(precision):
     """The paper's force for split particles (sum of the forces their split
