@@ -35,6 +35,8 @@ struct fmm_plan_s {
     const void *last_ws;
     int64_t last_n;
     int *h_hdr;  // pinned copy of the workspace header
+    cudaStream_t s_near, s_coarse;  // auxiliary streams of an evaluation
+    cudaEvent_t e_sorted, e_near, e_fork, e_coarse;
     bool timing;
     cudaEvent_t ev[512];
     int nev_created;
@@ -388,6 +390,13 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     cudaMemsetAsync(ptr.cursor, 0, W.ncell * 4, st);
     launch_bin_emit<real>(g, C, ptr, W, (int)n, pos, q, st, tr);
     launch_sort<real>(g, ptr, W, (int)n, st, tr);
+    // the near field needs only the sorted charges: it runs on its own stream
+    // beside the whole far field and joins before the far field is added
+    Streams S = {st, P->s_near, P->s_coarse, P->e_sorted, P->e_near, P->e_fork, P->e_coarse};
+    cudaEventRecord(S.sorted, st);
+    cudaStreamWaitEvent(S.near, S.sorted, 0);
+    launch_p2p<real>(g, ptr, W, forces != nullptr, S.near, tr);
+    cudaEventRecord(S.near_done, S.near);
     launch_upward<real>(g, C, ptr, W, st, tr);
     DevTables<real> T;
     T.KtT = (const real *)P->Kunit;
@@ -397,9 +406,10 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     T.tc_lmin = P->tc ? 4 : 0;
     T.tc_khi_map = P->khi_map;
     T.tc_klo_map = P->klo_map;
-    int rc = launch_downward<real>(g, C, ptr, W, T, st, tr);
+    int rc = launch_downward<real>(g, C, ptr, W, T, S, tr);
     if (rc) return rc;
-    launch_evaluate<real>(g, C, ptr, W, forces != nullptr, st, tr);
+    cudaStreamWaitEvent(st, S.near_done, 0);
+    launch_l2p<real>(g, C, ptr, W, forces != nullptr, st, tr);
     launch_unsplit<real>(g, ptr, W, (int)n, q, potential, energy, forces, nullptr, nullptr, false,
                          st, tr);
     k_mark_valid<<<1, 1, 0, st>>>(ptr.hdr, (long long)n);
@@ -416,7 +426,8 @@ int backward_impl(fmm_plan_t P, int64_t n, const float *q, const double *gE, rea
                                                                         : (const void *)&P->cf);
     Geom g = P->geom;
     if (n == 0) return FMM_OK;
-    launch_evaluate<real>(g, C, ptr, W, true, st, tr);
+    launch_p2p<real>(g, ptr, W, true, st, tr);
+    launch_l2p<real>(g, C, ptr, W, true, st, tr);
     launch_unsplit<real>(g, ptr, W, (int)n, q, nullptr, nullptr, grad_pos, gE, grad_q, true, st, tr);
     return FMM_OK;
 }
@@ -514,6 +525,20 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
         delete P;
         return FMM_ERR_OOM;
     }
+    {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        // near field: lowest priority (it fills the GPU); coarse levels: highest
+        if (cudaStreamCreateWithPriority(&P->s_near, cudaStreamNonBlocking, lo) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&P->s_coarse, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->e_sorted, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->e_near, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->e_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->e_coarse, cudaEventDisableTiming) != cudaSuccess) {
+            fmm_plan_destroy(P);
+            return FMM_ERR_CUDA;
+        }
+    }
     fmm::far_set_attributes();
     int rc = P->fp64 ? upload_tables<double>(P) : upload_tables<float>(P);
     if (rc != FMM_OK) {
@@ -526,6 +551,12 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
 
 void fmm_plan_destroy(fmm_plan_t P) {
     if (!P) return;
+    if (P->s_near) cudaStreamDestroy(P->s_near);
+    if (P->s_coarse) cudaStreamDestroy(P->s_coarse);
+    if (P->e_sorted) cudaEventDestroy(P->e_sorted);
+    if (P->e_near) cudaEventDestroy(P->e_near);
+    if (P->e_fork) cudaEventDestroy(P->e_fork);
+    if (P->e_coarse) cudaEventDestroy(P->e_coarse);
     for (int i = 0; i < P->nev_created; i++) cudaEventDestroy(P->ev[i]);
     if (P->Kunit) cudaFree(P->Kunit);
     if (P->Kbar) cudaFree(P->Kbar);

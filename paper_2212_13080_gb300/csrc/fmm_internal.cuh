@@ -130,14 +130,17 @@ struct Tracer {
     cudaEvent_t *ev = nullptr;
     int cap = 0, n = 0;
     int stage[512];
-    void begin(int s) {
+    cudaStream_t cur = 0;
+    // stage events on `stream` (default: the call's stream)
+    void begin(int s, cudaStream_t stream = nullptr) {
+        cur = stream ? stream : st;
         if (on && n + 2 <= cap) {
             stage[n / 2] = s;
-            cudaEventRecord(ev[n++], st);
+            cudaEventRecord(ev[n++], cur);
         }
     }
     void end() {
-        if (on && (n & 1)) cudaEventRecord(ev[n++], st);
+        if (on && (n & 1)) cudaEventRecord(ev[n++], cur);
     }
     void count(int k = 1) { launches += k; }
 };
@@ -207,9 +210,16 @@ int launch_scan(const int *in, int *out, int m, int *tmp, cudaStream_t st);
 template <typename real>
 void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
                    cudaStream_t st, Tracer &tr);
+// Streams of one evaluation: the caller's stream, two plan-owned auxiliary
+// streams and the events that fork work onto them and join it back.
+struct Streams {
+    cudaStream_t main, near, coarse;
+    cudaEvent_t sorted, near_done, fork, coarse_done;
+};
+
 template <typename real>
 int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
-                    const DevTables<real> &T, cudaStream_t st, Tracer &tr);
+                    const DevTables<real> &T, const Streams &S, Tracer &tr);
 
 // tensor-core contraction (m2l_tc.cu)
 int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
@@ -218,8 +228,12 @@ int tc_encode_kernel_map(void *map, const float *base);
 size_t tc_map_bytes();
 
 // near field + far-field evaluation at the charges (kernels_p2p.cu)
+// near field: writes out_pt (assigns); far field at the charges: adds to it
 template <typename real>
-void launch_evaluate(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
-                     bool forces, cudaStream_t st, Tracer &tr);
+void launch_p2p(const Geom &g, const Ptrs<real> &P, const WsLayout &W, bool forces,
+                cudaStream_t st, Tracer &tr);
+template <typename real>
+void launch_l2p(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
+                bool forces, cudaStream_t st, Tracer &tr);
 
 }  // namespace fmm

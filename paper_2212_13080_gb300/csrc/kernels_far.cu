@@ -424,7 +424,8 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
 
 template <typename real>
 int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
-                    const DevTables<real> &T, cudaStream_t st, Tracer &tr) {
+                    const DevTables<real> &T, const Streams &S, Tracer &tr) {
+    cudaStream_t st = S.main;
     const int p = g.p, p3 = g.p3, depth = g.depth;
     const int achunks = (p3 + M2L_T - 1) / M2L_T;
     const size_t sm_m2l = sizeof(real) * (2 * M2L_T * M2L_T + 2 * M2L_T);
@@ -441,6 +442,9 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
     }
     int lsimt_end = depth;
     if (T.tc_lmin > 0 && depth >= T.tc_lmin) lsimt_end = T.tc_lmin - 1;
+    // the SIMT levels run on the coarse stream, beside the tensor-core levels
+    cudaEventRecord(S.fork, st);
+    cudaStreamWaitEvent(S.coarse, S.fork, 0);
     for (int l = lstart; l <= lsimt_end; l++) {
         const int H = 1 << (l - 1);
         const int Tt = H < 4 ? H : 4;
@@ -448,25 +452,28 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
         const int G = m2l_groups(l, p3);
         dim3 grid(ntiles, 8, achunks * G);
         real *dst = G > 1 ? P.m2l_part : P.loc + W.loc_level[l];
-        tr.begin(FMM_STAGE_M2L);
-        k_m2l_simt<real><<<grid, M2L_BS, sm_m2l, st>>>(p, l, P.phi + W.phi_level[l],
-                                                       P.qlev + W.q_level[l], dst, T.KtT, T.Kbar, G);
+        tr.begin(FMM_STAGE_M2L, S.coarse);
+        k_m2l_simt<real><<<grid, M2L_BS, sm_m2l, S.coarse>>>(p, l, P.phi + W.phi_level[l],
+                                                             P.qlev + W.q_level[l], dst, T.KtT,
+                                                             T.Kbar, G);
         tr.count();
         if (G > 1) {
             const int64_t n = ((int64_t)1 << (3 * l)) * p3;
             int nb = (int)((n + 255) / 256);
             if (nb > 152 * 16) nb = 152 * 16;
-            k_m2l_reduce<real><<<nb, 256, 0, st>>>(G, n, P.m2l_part, P.loc + W.loc_level[l]);
+            k_m2l_reduce<real><<<nb, 256, 0, S.coarse>>>(G, n, P.m2l_part, P.loc + W.loc_level[l]);
             tr.count();
         }
         tr.end();
     }
+    cudaEventRecord(S.coarse_done, S.coarse);
     if constexpr (std::is_same<real, float>::value) {
         if (T.tc_lmin > 0 && depth >= T.tc_lmin) {
             int rc = launch_m2l_tc(g, P, W, T.tc_khi_map, T.tc_klo_map, T.Kbar, T.tc_lmin, st, tr);
             if (rc) return rc;
         }
     }
+    cudaStreamWaitEvent(st, S.coarse_done, 0);
     // 2. downward: Psi_child = Psi_parent o shift, added level by level
     for (int l = g.periodic ? 1 : 3; l <= depth; l++) {
         int nparent = 1 << (3 * (l - 1));
@@ -492,10 +499,10 @@ template void launch_upward<float>(const Geom &, const Coef<float> &, const Ptrs
 template void launch_upward<double>(const Geom &, const Coef<double> &, const Ptrs<double> &,
                                     const WsLayout &, cudaStream_t, Tracer &);
 template int launch_downward<float>(const Geom &, const Coef<float> &, const Ptrs<float> &,
-                                     const WsLayout &, const DevTables<float> &, cudaStream_t,
-                                     Tracer &);
+                                    const WsLayout &, const DevTables<float> &, const Streams &,
+                                    Tracer &);
 template int launch_downward<double>(const Geom &, const Coef<double> &, const Ptrs<double> &,
-                                      const WsLayout &, const DevTables<double> &, cudaStream_t,
-                                      Tracer &);
+                                     const WsLayout &, const DevTables<double> &, const Streams &,
+                                     Tracer &);
 
 }  // namespace fmm

@@ -1,7 +1,9 @@
-// Evaluation at the charges: far field (§2.2 step 4 and the far-field force at
-// the end of §2.2) and near field (step 5: direct sum over the finest cell and
-// its 26 neighbours).  Results per sorted charge, unit-box units:
+// Evaluation at the charges: near field (step 5: direct sum over the finest
+// cell and its 26 neighbours) and far field (§2.2 step 4 and the far-field force
+// at the end of §2.2).  Results per sorted charge, unit-box units:
 //   out_pt[slot] = (phi, F_x, F_y, F_z), phi per unit charge, F with the charge.
+// The near-field kernel writes out_pt, the far-field kernel adds to it: the
+// near field needs only the sorted charges and can run beside the far field.
 #include "fmm_internal.cuh"
 #include "lagrange.cuh"
 
@@ -74,11 +76,11 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, const i
                 fz += dz[k] * aw;
             }
         }
-        typename Vec4<real>::T o;
-        o.x = phi;
-        o.y = -v.w * S * fx;
-        o.z = -v.w * S * fy;
-        o.w = -v.w * S * fz;
+        typename Vec4<real>::T o = out_pt[s];  // the near field is already there
+        o.x += phi;
+        o.y += -v.w * S * fx;
+        o.z += -v.w * S * fy;
+        o.w += -v.w * S * fz;
         out_pt[s] = o;
     }
 }
@@ -285,23 +287,19 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p(int depth, int periodic, const i
             }
             // unit-box units: 1/r_u = S / r_t, (x/r^3)_u = S^2 (x/r^3)_t
             const int si = t0 + tgt;
-            real4 out = out_pt[si];
             const real qt = s_pt[si].w;
-            out.x += S_r * sum.x;
-            out.y += qt * S_r * S_r * sum.y;
-            out.z += qt * S_r * S_r * sum.z;
-            out.w += qt * S_r * S_r * sum.w;
-            out_pt[si] = out;
+            out_pt[si] = make_vec4(S_r * sum.x, qt * S_r * S_r * sum.y, qt * S_r * S_r * sum.z,
+                                   qt * S_r * S_r * sum.w);
         }
     }
 }
 
 template <typename real>
-void launch_evaluate(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
-                     bool forces, cudaStream_t st, Tracer &tr) {
+void launch_l2p(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
+                bool forces, cudaStream_t st, Tracer &tr) {
     const int ncell = (int)W.ncell, depth = g.depth;
     const real *loc_leaf = P.loc + W.loc_level[depth];
-    tr.begin(FMM_STAGE_L2P);
+    tr.begin(FMM_STAGE_L2P, st);
     switch (g.p) {
 #define CASE(PP)                                                                                 \
     case PP:                                                                                     \
@@ -317,7 +315,13 @@ void launch_evaluate(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, co
     }
     tr.count();
     tr.end();
-    tr.begin(FMM_STAGE_P2P);
+}
+
+template <typename real>
+void launch_p2p(const Geom &g, const Ptrs<real> &P, const WsLayout &W, bool forces,
+                cudaStream_t st, Tracer &tr) {
+    const int ncell = (int)W.ncell, depth = g.depth;
+    tr.begin(FMM_STAGE_P2P, st);
     if (forces)
         k_p2p<real, true><<<ncell, P2P_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt,
                                                     P.s_origin, P.out_pt);
@@ -328,9 +332,13 @@ void launch_evaluate(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, co
     tr.end();
 }
 
-template void launch_evaluate<float>(const Geom &, const Coef<float> &, const Ptrs<float> &,
-                                     const WsLayout &, bool, cudaStream_t, Tracer &);
-template void launch_evaluate<double>(const Geom &, const Coef<double> &, const Ptrs<double> &,
-                                      const WsLayout &, bool, cudaStream_t, Tracer &);
+template void launch_l2p<float>(const Geom &, const Coef<float> &, const Ptrs<float> &,
+                                const WsLayout &, bool, cudaStream_t, Tracer &);
+template void launch_l2p<double>(const Geom &, const Coef<double> &, const Ptrs<double> &,
+                                 const WsLayout &, bool, cudaStream_t, Tracer &);
+template void launch_p2p<float>(const Geom &, const Ptrs<float> &, const WsLayout &, bool,
+                                cudaStream_t, Tracer &);
+template void launch_p2p<double>(const Geom &, const Ptrs<double> &, const WsLayout &, bool,
+                                 cudaStream_t, Tracer &);
 
 }  // namespace fmm
