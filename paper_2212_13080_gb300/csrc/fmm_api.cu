@@ -26,7 +26,8 @@ struct fmm_plan_s {
     void *Kbar;   // [343][p^3] row means of the unit-cell kernels
     void *Klat;   // [p^3][p^3] lattice kernel minus its row mean (periodic form)
     void *Klbar;  // [p^3] row means of the lattice kernel
-    void *Ktc_hi, *Ktc_lo;  // [343][a][b] TF32 split of the unit-cell kernels (TF32X3 plans)
+    void *Ktc_hi, *Ktc_lo;  // [343][a][b] TF32 split of Kt, padded to 32 (TF32X3 plans)
+    void *Kbar_tc;          // [343][a] row means, padded to 32
     alignas(64) unsigned char khi_map[128], klo_map[128];  // their TMA tensor maps
     bool tc;                // bilinear forms of levels >= 4 on tensor cores
     Coef<float> cf;
@@ -152,10 +153,12 @@ int upload_tables(fmm_plan_t P) {
     if (!rc) rc = upload(&P->Kbar, Kbar);
     if (rc) return rc;
     if (P->tc) {
-        // Kt_o[a][b] = K_o[a][b] - Kbar_o[a] (natural layout), split as hi =
-        // Kt with its 13 low mantissa bits cleared, lo = Kt - hi (from the FP64
-        // value): hi exact in TF32
-        std::vector<float> Khi(nk, 0.0f), Klo(nk, 0.0f);
+        // Kt_o[a][b] = K_o[a][b] - Kbar_o[a] (natural layout, rows and columns
+        // zero-padded to p3s = p^3 rounded up to 32), split as hi = Kt with its
+        // 13 low mantissa bits cleared, lo = Kt - hi (from the FP64 value)
+        const int p3s = tc_padded(p3);
+        const size_t nt = (size_t)343 * p3s * p3s;
+        std::vector<float> Khi(nt, 0.0f), Klo(nt, 0.0f), Kb((size_t)343 * p3s, 0.0f);
         for (int oi = 0; oi < 343; oi++) {
             int ox = oi % 7 - 3, oy = (oi / 7) % 7 - 3, oz = oi / 49 - 3;
             if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
@@ -170,6 +173,7 @@ int upload_tables(fmm_plan_t P) {
                     mean += row[b];
                 }
                 mean /= p3;
+                Kb[(size_t)oi * p3s + a] = (float)mean;
                 for (int b = 0; b < p3; b++) {
                     double k = row[b] - mean;
                     float f = (float)k;
@@ -178,7 +182,7 @@ int upload_tables(fmm_plan_t P) {
                     u &= 0xFFFFE000u;
                     float hi;
                     memcpy(&hi, &u, 4);
-                    size_t idx = ((size_t)oi * p3 + a) * p3 + b;
+                    size_t idx = ((size_t)oi * p3s + a) * p3s + b;
                     Khi[idx] = hi;
                     Klo[idx] = (float)(k - (double)hi);
                 }
@@ -186,8 +190,9 @@ int upload_tables(fmm_plan_t P) {
         }
         rc = upload(&P->Ktc_hi, Khi);
         if (!rc) rc = upload(&P->Ktc_lo, Klo);
-        if (!rc) rc = tc_encode_kernel_map(P->khi_map, (const float *)P->Ktc_hi);
-        if (!rc) rc = tc_encode_kernel_map(P->klo_map, (const float *)P->Ktc_lo);
+        if (!rc) rc = upload(&P->Kbar_tc, Kb);
+        if (!rc) rc = tc_encode_kernel_map(P->khi_map, (const float *)P->Ktc_hi, p3s);
+        if (!rc) rc = tc_encode_kernel_map(P->klo_map, (const float *)P->Ktc_lo, p3s);
         if (rc) return rc;
     }
     if (P->periodic) {
@@ -298,8 +303,9 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
         if (G > 1 && need > part) part = need;
     }
     W.m2l_part = take(part * rs);
-    W.phihi = take(P->tc ? (size_t)ph * p3 * rs : 0);
-    W.philo = take(P->tc ? (size_t)ph * p3 * rs : 0);
+    const size_t p3s = (size_t)tc_padded(p3);
+    W.phihi = take(P->tc ? (size_t)ph * p3s * rs : 0);
+    W.philo = take(P->tc ? (size_t)ph * p3s * rs : 0);
     int64_t mx = n > W.ncell ? n : W.ncell;
     W.scan_blocks = (int)(mx / 2048 + 2);
     W.scan_tmp = take((size_t)(W.scan_blocks + 1) * 4);
@@ -406,6 +412,7 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     T.tc_lmin = P->tc ? 4 : 0;
     T.tc_khi_map = P->khi_map;
     T.tc_klo_map = P->klo_map;
+    T.tc_kbar = (const float *)P->Kbar_tc;
     int rc = launch_downward<real>(g, C, ptr, W, T, S, tr);
     if (rc) return rc;
     cudaStreamWaitEvent(st, S.near_done, 0);
@@ -494,7 +501,7 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     if (o.precision != FMM_PREC_FP32 && o.precision != FMM_PREC_FP64 &&
         o.precision != FMM_PREC_TF32X3)
         return FMM_ERR_UNSUPPORTED;
-    if (o.precision == FMM_PREC_TF32X3 && p != 4) return FMM_ERR_UNSUPPORTED;
+    if (o.precision == FMM_PREC_TF32X3 && (p < 3 || p > 6)) return FMM_ERR_UNSUPPORTED;
     fmm_plan_s *P = new (std::nothrow) fmm_plan_s();
     if (!P) return FMM_ERR_OOM;
     P->depth = depth;
@@ -564,6 +571,7 @@ void fmm_plan_destroy(fmm_plan_t P) {
     if (P->Klbar) cudaFree(P->Klbar);
     if (P->Ktc_hi) cudaFree(P->Ktc_hi);
     if (P->Ktc_lo) cudaFree(P->Ktc_lo);
+    if (P->Kbar_tc) cudaFree(P->Kbar_tc);
     if (P->h_hdr) cudaFreeHost(P->h_hdr);
     delete P;
 }

@@ -181,6 +181,7 @@ struct DevTables {
     // tensor-core contraction (TF32X3 plans): levels >= tc_lmin, 0 = none
     int tc_lmin;
     const void *tc_khi_map, *tc_klo_map;  // CUtensorMap of the split unit-cell kernels
+    const float *tc_kbar;                 // [343][p3 padded to 32] row means
 };
 
 // Offset groups of the SIMT contraction at level l: the 189 offsets of a
@@ -224,7 +225,8 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
 // tensor-core contraction (m2l_tc.cu)
 int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
                   const void *k_lo_map, const float *kbar, int lmin, cudaStream_t st, Tracer &tr);
-int tc_encode_kernel_map(void *map, const float *base);
+int tc_encode_kernel_map(void *map, const float *base, int p3s);
+int tc_padded(int p3);
 size_t tc_map_bytes();
 
 // near field + far-field evaluation at the charges (kernels_p2p.cu)

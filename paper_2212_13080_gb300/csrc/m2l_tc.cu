@@ -3,21 +3,21 @@
 //
 // For one level, one target parity and one box of 8x4x4 coarse cells (128
 // target cells = the MMA's M), every one of the 189 interaction-list offsets o
-// contributes L[cell][a] += sum_b Phi[cell + o][b] K_o[a][b]: a 128 x 64 x 64
-// GEMM whose A operand (the 128 source vectors) is one rectangular box of the
-// padded parity-major Phi layout and whose B operand is the unit-cell kernel.
-// Both arrive by TMA, in two 128-byte K halves, into a 2-stage ring; one
-// thread issues the MMAs.
+// contributes L[cell][a] += sum_b Phi[cell + o][b] K_o[a][b]: a 128 x N x K
+// GEMM (N = K = p^3 padded to a multiple of 32) whose A operand (the 128
+// source vectors) is one rectangular box of the padded parity-major grid-charge
+// layout and whose B operand is the unit-cell kernel.  Both arrive by TMA, in
+// 128-byte K chunks, into a 2-stage ring; one thread issues the MMAs.
 //
 // Accuracy.  Split precision: x = hi + lo with hi = x with its 13 low mantissa
 // bits cleared (exact in TF32); D = Ahi Bhi + Ahi Blo + Alo Bhi.  The kernel
 // is split as K_o = Kbar_o[a] + Kt_o[a,b] (row mean): the tensor cores contract
 // Kt_o, the CUDA cores add Kbar_o[a] Q (Q = the source cell's total charge).
 // Each offset accumulates into a fresh TMEM region (two regions, alternating):
-// the four epilogue warps read it out and add the 189 partials in FP32
-// registers, so no FP32 accumulator in TMEM sees more than 24 MMAs (the
-// tensor cores' accumulation is not round-to-nearest; over 1512 MMAs it
-// drifted by ~1e-4).
+// the epilogue warps read it out and add the 189 partials in FP32 registers,
+// so no FP32 accumulator in TMEM sees more than 3 * K / 8 MMAs (the tensor
+// cores' accumulation is not round-to-nearest; over 1512 MMAs it drifted by
+// ~1e-4).  For N > 64 the epilogue splits the columns over two warp groups.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -27,14 +27,9 @@
 namespace fmm {
 
 #define TC_M 128
-#define TC_N 64
 #define TC_STAGES 2
-#define TC_ABYTES (TC_M * 128)                      // 128 rows x 32 fp32
-#define TC_BBYTES (TC_N * 128)                      // 64 rows x 32 fp32
-#define TC_STAGE (2 * TC_ABYTES + 2 * TC_BBYTES)    // Ahi, Alo, Bhi, Blo
-#define TC_THREADS 192
-#define TC_SMEM (TC_STAGES * TC_STAGE + 1024 + 128)
-#define TC_WAIT_CYCLES (4LL << 30)                  // about 2 s of SM clock
+#define TC_ABYTES (TC_M * 128)      // 128 rows x 32 fp32 (one K chunk)
+#define TC_WAIT_CYCLES (4LL << 30)  // about 2 s of SM clock
 #define TC_NOFF 189
 
 struct TcParams {
@@ -42,12 +37,12 @@ struct TcParams {
     CUtensorMap phi_lo[FMM_MAXDEPTH + 1];
     CUtensorMap k_hi, k_lo;
     int first_block[FMM_MAXDEPTH + 2];
-    int lmin, lmax;
+    int lmin, lmax, p3;
     long long loc_off[FMM_MAXDEPTH + 1];
     long long q_off[FMM_MAXDEPTH + 1];
     float *loc;
     const float *qlev;
-    const float *kbar;  // [343][64]
+    const float *kbar;  // [343][N], zero padded
     int *status;
 };
 
@@ -79,11 +74,28 @@ __device__ __forceinline__ Off make_off(int bx, int by, int bz, int ox, int oy, 
     return f;
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(const __grid_constant__ TcParams prm) {
+template <int N>
+struct TcShape {
+    static constexpr int CH = N > 64 ? 2 : 1;           // epilogue column groups
+    static constexpr int EPI = 4 * CH;                  // epilogue warps
+    static constexpr int THREADS = 32 * (EPI + 2);      // + producer + MMA issuer
+    static constexpr int KC = N / 32;                   // 128-byte K chunks
+    static constexpr int BBYTES = N * 128;
+    static constexpr int STAGE = 2 * TC_ABYTES + 2 * BBYTES;
+    static constexpr int SMEM = TC_STAGES * STAGE + 1024 + 128;
+    static constexpr int TCOLS = 2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : (2 * N <= 256 ? 256 : 512));
+    static constexpr int MINB = N <= 64 ? 2 : 1;
+    static constexpr int COLS = N / CH;                 // columns per epilogue thread
+};
+
+template <int N>
+__global__ void __launch_bounds__(TcShape<N>::THREADS, TcShape<N>::MINB)
+    k_m2l_tc(const __grid_constant__ TcParams prm) {
+    typedef TcShape<N> Sh;
     extern __shared__ unsigned char smraw[];
     const uint32_t raw = tc::smem_u32(smraw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
-    const uint32_t bars = sbase + TC_STAGES * TC_STAGE;
+    const uint32_t bars = sbase + TC_STAGES * Sh::STAGE;
     const uint32_t full0 = bars, empty0 = bars + 16, rfull0 = bars + 32, rfree0 = bars + 48;
     const uint32_t done = bars + 64;  // every MMA of this CTA has completed
     const uint32_t tslot = bars + 72;
@@ -107,39 +119,39 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(const __grid_constant_
             tc::mbar_init(full0 + 8 * s, 1);
             tc::mbar_init(empty0 + 8 * s, 1);
             tc::mbar_init(rfull0 + 8 * s, 1);
-            tc::mbar_init(rfree0 + 8 * s, 128);
+            tc::mbar_init(rfree0 + 8 * s, 32 * Sh::EPI);
         }
         tc::mbar_init(done, 1);
         tc::fence_barrier_init();
     }
-    if (warp == 0) tc::tmem_alloc(tslot, 2 * TC_N);
+    if (warp == 0) tc::tmem_alloc(tslot, Sh::TCOLS);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot_ptr;
 
-    if (warp == 4 && lane == 0) {
-        // ---- TMA producer: (offset, K half) stages ----
+    if (warp == Sh::EPI && lane == 0) {
+        // ---- TMA producer: (offset, K chunk) stages ----
         bool failed = false;
         int last_phase[TC_STAGES] = {-1, -1};
         int ox = -2 - bx - 1, oy = -2 - by, oz = -2 - bz, it = 0;
         while (!failed && next_offset(bx, by, bz, ox, oy, oz)) {
             const Off f = make_off(bx, by, bz, ox, oy, oz);
             const int cX = X0 + 1 + f.dX, cY = Y0 + 1 + f.dY, cZ = Z0 + 1 + f.dZ;
-            for (int kh = 0; kh < 2; kh++, it++) {
+            for (int kc = 0; kc < Sh::KC; kc++, it++) {
                 const int s = it % TC_STAGES;
                 const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
                 if (!tc::mbar_wait(empty0 + 8 * s, ph ^ 1u, TC_WAIT_CYCLES)) {
                     failed = true;
                     break;
                 }
-                const uint32_t st = sbase + s * TC_STAGE;
+                const uint32_t st = sbase + s * Sh::STAGE;
                 const uint32_t fb = full0 + 8 * s;
-                tc::mbar_expect_tx(fb, TC_STAGE);
-                tc::tma_load_5d(st, &prm.phi_hi[l], fb, kh * 32, cX, cY, cZ, f.spar);
-                tc::tma_load_5d(st + TC_ABYTES, &prm.phi_lo[l], fb, kh * 32, cX, cY, cZ, f.spar);
-                tc::tma_load_3d(st + 2 * TC_ABYTES, &prm.k_hi, fb, kh * 32, 0, f.oi);
-                tc::tma_load_3d(st + 2 * TC_ABYTES + TC_BBYTES, &prm.k_lo, fb, kh * 32, 0, f.oi);
+                tc::mbar_expect_tx(fb, Sh::STAGE);
+                tc::tma_load_5d(st, &prm.phi_hi[l], fb, kc * 32, cX, cY, cZ, f.spar);
+                tc::tma_load_5d(st + TC_ABYTES, &prm.phi_lo[l], fb, kc * 32, cX, cY, cZ, f.spar);
+                tc::tma_load_3d(st + 2 * TC_ABYTES, &prm.k_hi, fb, kc * 32, 0, f.oi);
+                tc::tma_load_3d(st + 2 * TC_ABYTES + Sh::BBYTES, &prm.k_lo, fb, kc * 32, 0, f.oi);
                 last_phase[s] = (int)ph;
             }
         }
@@ -149,9 +161,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(const __grid_constant_
             for (int s = 0; s < TC_STAGES; s++)
                 if (last_phase[s] >= 0) tc::mbar_wait(full0 + 8 * s, (uint32_t)last_phase[s], TC_WAIT_CYCLES);
         }
-    } else if (warp == 5 && lane == 0) {
+    } else if (warp == Sh::EPI + 1 && lane == 0) {
         // ---- MMA issuer: offset i accumulates into TMEM region i & 1 ----
-        const uint32_t idesc = tc::idesc_tf32(TC_M, TC_N);
+        const uint32_t idesc = tc::idesc_tf32(TC_M, N);
         bool failed = false;
         for (int i = 0; i < TC_NOFF && !failed; i++) {
             const int r = i & 1;
@@ -160,9 +172,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(const __grid_constant_
                 failed = true;
                 break;
             }
-            const uint32_t d = tmem + (uint32_t)(r * TC_N);
-            for (int kh = 0; kh < 2; kh++) {
-                const int it = 2 * i + kh;
+            const uint32_t d = tmem + (uint32_t)(r * N);
+            for (int kc = 0; kc < Sh::KC; kc++) {
+                const int it = Sh::KC * i + kc;
                 const int s = it % TC_STAGES;
                 const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
                 if (!tc::mbar_wait(full0 + 8 * s, ph, TC_WAIT_CYCLES)) {
@@ -170,14 +182,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(const __grid_constant_
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t st = sbase + s * TC_STAGE;
+                const uint32_t st = sbase + s * Sh::STAGE;
 #pragma unroll
                 for (int k = 0; k < 4; k++) {  // K = 8 tf32 = 32 bytes per MMA
                     const uint64_t ah = tc::desc_sw128(st + 32 * k);
                     const uint64_t al = tc::desc_sw128(st + TC_ABYTES + 32 * k);
                     const uint64_t bh = tc::desc_sw128(st + 2 * TC_ABYTES + 32 * k);
-                    const uint64_t bl = tc::desc_sw128(st + 2 * TC_ABYTES + TC_BBYTES + 32 * k);
-                    tc::mma_tf32(d, ah, bh, idesc, (kh | k) != 0);
+                    const uint64_t bl = tc::desc_sw128(st + 2 * TC_ABYTES + Sh::BBYTES + 32 * k);
+                    tc::mma_tf32(d, ah, bh, idesc, (kc | k) != 0);
                     tc::mma_tf32(d, ah, bl, idesc, 1u);
                     tc::mma_tf32(d, al, bh, idesc, 1u);
                 }
@@ -187,14 +199,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(const __grid_constant_
         }
         if (failed) atomicOr(prm.status, ST_TIMEOUT);
         tc::mma_commit(done);  // always: the deallocation waits on it
-    } else if (warp < 4) {
-        // ---- epilogue: TMEM lane = target cell; sum the per-offset partials ----
-        const int row = warp * 32 + lane;
+    } else if (warp < Sh::EPI) {
+        // ---- epilogue: TMEM lane = target cell; columns [c0, c0 + COLS) ----
+        const int sub = warp & 3, cgrp = warp >> 2;
+        const int c0 = cgrp * Sh::COLS;
+        const int row = sub * 32 + lane;
         const int tx = row & 7, ty = (row >> 3) & 3, tz = row >> 5;
         const float *q = prm.qlev + prm.q_off[l];
-        float tot[TC_N];
+        float tot[Sh::COLS];
 #pragma unroll
-        for (int j = 0; j < TC_N; j++) tot[j] = 0.0f;
+        for (int j = 0; j < Sh::COLS; j++) tot[j] = 0.0f;
         bool ok = true;
         int ox = -2 - bx - 1, oy = -2 - by, oz = -2 - bz;
         for (int i = 0; i < TC_NOFF; i++) {
@@ -202,14 +216,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(const __grid_constant_
             const Off f = make_off(bx, by, bz, ox, oy, oz);
             const float Qs = q[(((int64_t)f.spar * P + Z0 + tz + 1 + f.dZ) * P + Y0 + ty + 1 + f.dY) * P +
                                X0 + tx + 1 + f.dX];
-            const float4 *kb = reinterpret_cast<const float4 *>(prm.kbar + (int64_t)f.oi * TC_N);
+            const float4 *kb = reinterpret_cast<const float4 *>(prm.kbar + (int64_t)f.oi * N + c0);
             const int r = i & 1;
             const uint32_t u = (uint32_t)(i >> 1) & 1u;
             if (ok && !tc::mbar_wait(rfull0 + 8 * r, u, TC_WAIT_CYCLES)) ok = false;
             tc::fence_after_sync();
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(r * TC_N);
+            const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(r * N + c0);
 #pragma unroll
-            for (int c = 0; c < TC_N / 16; c++) {
+            for (int c = 0; c < Sh::COLS / 16; c++) {
                 uint32_t v[16];
                 tc::tmem_ld16(taddr + c * 16, v);
 #pragma unroll
@@ -225,13 +239,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(const __grid_constant_
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rfree0 + 8 * r) : "memory");
         }
         const int cx = 2 * (X0 + tx) + bx, cy = 2 * (Y0 + ty) + by, cz = 2 * (Z0 + tz) + bz;
-        float *out = prm.loc + prm.loc_off[l] + loc_cell(l, cx, cy, cz) * TC_N;
+        const int p3 = prm.p3;
+        float *out = prm.loc + prm.loc_off[l] + loc_cell(l, cx, cy, cz) * p3 + c0;
         const float scale = (float)(1 << l);
         if (ok) {
 #pragma unroll
-            for (int j = 0; j < TC_N; j += 4)
-                *reinterpret_cast<float4 *>(out + j) =
-                    make_float4(scale * tot[j], scale * tot[j + 1], scale * tot[j + 2], scale * tot[j + 3]);
+            for (int j = 0; j < Sh::COLS; j++)
+                if (c0 + j < p3) out[j] = scale * tot[j];
         } else if (lane == 0) {
             atomicOr(prm.status, ST_TIMEOUT);
         }
@@ -241,16 +255,20 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(const __grid_constant_
     if (warp == 0) {
         tc::mbar_wait(done, 0, TC_WAIT_CYCLES);
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, 2 * TC_N);
+        tc::tmem_dealloc(tmem, Sh::TCOLS);
     }
 }
 
-// hi = x with the 13 low mantissa bits cleared (exact in TF32), lo = x - hi
+// hi = x with the 13 low mantissa bits cleared (exact in TF32), lo = x - hi,
+// from cell vectors of p3 values to cell vectors of p3s (zero padded)
 __global__ void k_split_tf32(const float *__restrict__ x, float *__restrict__ hi,
-                             float *__restrict__ lo, int64_t n) {
+                             float *__restrict__ lo, int64_t ncells, int p3, int p3s) {
+    const int64_t n = ncells * p3s;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float v = x[i];
+        const int64_t c = i / p3s;
+        const int b = (int)(i - c * p3s);
+        float v = b < p3 ? x[c * p3 + b] : 0.0f;
         float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
         hi[i] = h;
         lo[i] = v - h;
@@ -273,13 +291,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// Grid-charge box map of level l: dims (64 b, P x, P y, P z, 8 parity), box (32, 8, 4, 4, 1).
-static int encode_phi_map(CUtensorMap *m, const float *base, int l) {
+int tc_padded(int p3) { return (p3 + 31) / 32 * 32; }
+
+// Grid-charge box map of level l: dims (p3s b, P x, P y, P z, 8 parity), box (32, 8, 4, 4, 1).
+static int encode_phi_map(CUtensorMap *m, const float *base, int l, int p3s) {
     auto enc = encode_fn();
     if (!enc) return FMM_ERR_CUDA;
-    const cuuint64_t P = ((cuuint64_t)1 << (l - 1)) + 2;
-    cuuint64_t dims[5] = {64, P, P, P, 8};
-    cuuint64_t strides[4] = {64 * 4, 64 * 4 * P, 64 * 4 * P * P, 64 * 4 * P * P * P};
+    const cuuint64_t P = ((cuuint64_t)1 << (l - 1)) + 2, rb = (cuuint64_t)p3s * 4;
+    cuuint64_t dims[5] = {(cuuint64_t)p3s, P, P, P, 8};
+    cuuint64_t strides[4] = {rb, rb * P, rb * P * P, rb * P * P * P};
     cuuint32_t box[5] = {32, 8, 4, 4, 1};
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void *)base, dims, strides, box, es,
@@ -288,13 +308,14 @@ static int encode_phi_map(CUtensorMap *m, const float *base, int l) {
     return r == CUDA_SUCCESS ? FMM_OK : FMM_ERR_CUDA;
 }
 
-// Kernel-table map: dims (64 b, 64 a, 343 offsets), box (32, 64, 1).
-int tc_encode_kernel_map(void *map, const float *base) {
+// Kernel-table map: dims (p3s b, p3s a, 343 offsets), box (32, p3s, 1).
+int tc_encode_kernel_map(void *map, const float *base, int p3s) {
     auto enc = encode_fn();
     if (!enc) return FMM_ERR_CUDA;
-    cuuint64_t dims[3] = {64, 64, 343};
-    cuuint64_t strides[2] = {64 * 4, 64 * 64 * 4};
-    cuuint32_t box[3] = {32, 64, 1};
+    const cuuint64_t n = (cuuint64_t)p3s;
+    cuuint64_t dims[3] = {n, n, 343};
+    cuuint64_t strides[2] = {n * 4, n * n * 4};
+    cuuint32_t box[3] = {32, (cuuint32_t)p3s, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc((CUtensorMap *)map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims,
                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -304,27 +325,36 @@ int tc_encode_kernel_map(void *map, const float *base) {
 
 size_t tc_map_bytes() { return sizeof(CUtensorMap); }
 
-int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
-                  const void *k_lo_map, const float *kbar, int lmin, cudaStream_t st, Tracer &tr) {
+template <int N>
+static int launch_tc_kernel(const TcParams &prm, int blocks, cudaStream_t st) {
+    typedef TcShape<N> Sh;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) !=
+        if (cudaFuncSetAttribute(k_m2l_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM) !=
             cudaSuccess)
             return FMM_ERR_CUDA;
         attr = true;
     }
-    const int depth = g.depth;
-    // split the grid charges of levels lmin..depth into TF32 hi / lo parts
-    const int64_t a = W.phi_level[lmin], b = W.phi_level[depth + 1];
+    k_m2l_tc<N><<<blocks, Sh::THREADS, Sh::SMEM, st>>>(prm);
+    return FMM_OK;
+}
+
+int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
+                  const void *k_lo_map, const float *kbar, int lmin, cudaStream_t st, Tracer &tr) {
+    const int depth = g.depth, p3 = g.p3, p3s = tc_padded(p3);
+    // split the grid charges of levels lmin..depth into padded TF32 hi / lo parts
+    const int64_t c0 = W.phi_level[lmin] / p3, c1 = W.phi_level[depth + 1] / p3;
     tr.begin(FMM_STAGE_M2L);
-    k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi + a, P.phihi + a, P.philo + a, b - a);
+    k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi + W.phi_level[lmin], P.phihi + c0 * p3s,
+                                          P.philo + c0 * p3s, c1 - c0, p3, p3s);
     tr.count();
     TcParams prm;
     memset(&prm, 0, sizeof(prm));
     int blocks = 0;
     for (int l = lmin; l <= depth; l++) {
-        int rc = encode_phi_map(&prm.phi_hi[l], P.phihi + W.phi_level[l], l);
-        if (!rc) rc = encode_phi_map(&prm.phi_lo[l], P.philo + W.phi_level[l], l);
+        const int64_t cl = W.phi_level[l] / p3;  // first cell of level l
+        int rc = encode_phi_map(&prm.phi_hi[l], P.phihi + cl * p3s, l, p3s);
+        if (!rc) rc = encode_phi_map(&prm.phi_lo[l], P.philo + cl * p3s, l, p3s);
         if (rc) return rc;
         prm.first_block[l] = blocks;
         const int H = 1 << (l - 1);
@@ -337,14 +367,22 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
     memcpy(&prm.k_lo, k_lo_map, sizeof(CUtensorMap));
     prm.lmin = lmin;
     prm.lmax = depth;
+    prm.p3 = p3;
     prm.loc = P.loc;
     prm.qlev = P.qlev;
     prm.kbar = kbar;
     prm.status = &P.hdr->status;
-    k_m2l_tc<<<blocks, TC_THREADS, TC_SMEM, st>>>(prm);
+    int rc;
+    switch (p3s) {
+    case 32: rc = launch_tc_kernel<32>(prm, blocks, st); break;
+    case 64: rc = launch_tc_kernel<64>(prm, blocks, st); break;
+    case 128: rc = launch_tc_kernel<128>(prm, blocks, st); break;
+    case 224: rc = launch_tc_kernel<224>(prm, blocks, st); break;
+    default: rc = FMM_ERR_UNSUPPORTED;
+    }
     tr.count();
     tr.end();
-    return FMM_OK;
+    return rc;
 }
 
 }  // namespace fmm

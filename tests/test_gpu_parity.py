@@ -110,15 +110,29 @@ def test_parity_small(case, precision):
 TOL_TF32X3 = 1e-5  # reduced-precision far field (3-pass split TF32 on tensor cores)
 
 
-@pytest.mark.parametrize("name,n,depth,seed", [("uniform", 40000, 4, 31), ("uniform", 300000, 5, 32)])
-def test_parity_tf32x3(name, n, depth, seed):
+TF32_CASES = [
+    # name, generator, depth, p, periodic, continuous
+    ("uniform40k-d4-p4-cont", lambda: inputs.uniform_cont(40000, 31), 4, 4, False, True),
+    ("uniform300k-d5-p4-cont", lambda: inputs.uniform_cont(300000, 32), 5, 4, False, True),
+    ("water45k-d4-p5-periodic-cont", lambda: inputs.water(15000, 33), 4, 5, True, True),
+    ("uniform60k-d4-p6-open", lambda: inputs.uniform_pm1(60000, 34), 4, 6, False, False),
+    ("uniform30k-d4-p3-open", lambda: inputs.uniform_pm1(30000, 35), 4, 3, False, False),
+    ("uniform200k-d5-p3-periodic", lambda: inputs.uniform_pm1(200000, 36), 5, 3, True, False),
+]
+
+
+@pytest.mark.parametrize("case", TF32_CASES, ids=[c[0] for c in TF32_CASES])
+def test_parity_tf32x3(case):
     """Far-field contraction of levels >= 4 on the tcgen05 tensor cores (3-pass
-    split TF32, per-offset accumulators); potentials, energy and forces within
-    the reduced-precision tolerance of the FP64 oracle."""
-    pos, q, box = inputs.uniform_cont(n, seed)
-    s = np.arange(0, n, max(1, n // 2000))
-    ref = oracle.fmm(pos, q, box, depth=depth, n=4, continuous=True, sample=s)
-    plan, out = _gpu(pos, q, box, depth, 4, False, True, None, "tf32x3")
+    split TF32, per-offset accumulators, p^3 padded to a multiple of 32);
+    potentials, energy and forces within the reduced-precision tolerance of
+    the FP64 oracle (sampled outputs)."""
+    name, gen, depth, p, periodic, cont = case
+    pos, q, box = gen()
+    n = len(q)
+    s = np.arange(0, n, max(1, n // 1500))
+    ref = oracle.fmm(pos, q, box, depth=depth, n=p, periodic=periodic, continuous=cont, sample=s)
+    plan, out = _gpu(pos, q, box, depth, p, periodic, cont, None, "tf32x3")
     _check_integer_work(plan, ref)
     assert _rel_l2(out["potential"][s], ref["phi"]) < TOL_TF32X3
     assert _rel_l2(out["forces"][s], ref["F"]) < TOL_TF32X3
@@ -259,8 +273,10 @@ def test_forces_central_differences_fp64():
     plan.close()
 
 
-@pytest.mark.parametrize("name,sample", [("uniform1m", 512), ("water2m", 256)])
-def test_parity_full_size_sampled(name, sample):
+@pytest.mark.parametrize("name,sample,precision", [("uniform1m", 512, "fp32"), ("water2m", 256, "fp32"),
+                                                    ("uniform1m", 512, "tf32x3"),
+                                                    ("water2m", 256, "tf32x3")])
+def test_parity_full_size_sampled(name, sample, precision):
     """Full-size workloads in the benchmark's launch configuration: integer work
     on every charge, outputs on sampled particles (the oracle computes those one
     by one from its full upward pass)."""
@@ -270,10 +286,12 @@ def test_parity_full_size_sampled(name, sample):
     s = np.sort(rng.choice(len(q), sample, replace=False))
     ref = oracle.fmm(pos, q, box, depth=w["depth"], n=w["p"], periodic=w["periodic"],
                      continuous=w["continuous"], sample=s)
-    plan, out = _gpu(pos, q, box, w["depth"], w["p"], w["periodic"], w["continuous"], None, "fp32")
+    plan, out = _gpu(pos, q, box, w["depth"], w["p"], w["periodic"], w["continuous"], None, precision)
     _check_integer_work(plan, ref)
-    assert _rel_l2(out["potential"][s], ref["phi"]) < TOL_FP32
-    assert _rel_l2(out["forces"][s], ref["F"]) < (TOL_FP32_SPLIT_ADJOINT if w["continuous"] else TOL_FP32)
+    tol = TOL_FP32 if precision == "fp32" else TOL_TF32X3
+    assert _rel_l2(out["potential"][s], ref["phi"]) < tol
+    tol_F = max(tol, TOL_FP32_SPLIT_ADJOINT) if w["continuous"] else tol
+    assert _rel_l2(out["forces"][s], ref["F"]) < tol_F
     # energy: the sum is a property at any size; E = 1/2 sum q phi of the GPU's own phi
     E_from_phi = 0.5 * np.dot(q.astype(np.float64), out["potential"])
     assert abs(out["energy"][0] - E_from_phi) < 1e-9 * np.sum(np.abs(q * out["potential"]))
