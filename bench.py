@@ -197,6 +197,62 @@ def cpu_baseline(workload):
                       % (n, t)}
 
 
+def run_batch(args, world, rank, local):
+    """512 independent periodic systems (continuous form, p = 4), N per system
+    log-uniform in [1024, 65536], depth = clamp(round(log8(N/32)), 3, 5):
+    one CUDA-graph launch per step."""
+    import numpy as np
+    import torch
+    from paper_2212_13080_gb300 import FMMBatch, inputs
+    torch.cuda.set_device(local)
+    pos_h, q_h, offs, boxes, counts = inputs.batch_systems(512, 5)
+    depths = np.clip(np.rint(np.log(counts / 32.0) / np.log(8.0)), 3, 5).astype(int)
+    dev = torch.device("cuda", local)
+    pos = torch.from_numpy(pos_h).to(dev)
+    q = torch.from_numpy(q_h).to(dev)
+    bt = FMMBatch(boxes, depths, 4, periodic=True, continuous=True, precision=args.precision,
+                  max_n=counts, sync=False)
+    out = {"potential": torch.empty(len(q_h), device=dev),
+           "energy": torch.empty(512, dtype=torch.float64, device=dev),
+           "forces": torch.empty((len(q_h), 3), device=dev)}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bt.eval(pos, q, offs, out=out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bt.eval(pos, q, offs, out=out)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    clocks = sampler.stop()
+    st = bt.stats()
+    t = statistics.mean(ms)
+    n = int(offs[-1])
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": world * n / (t * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "precision": args.precision, "data": "synthetic",
+            "config": {"workload": "batch512", "systems": 512, "n_total": n,
+                       "n_min": int(counts.min()), "n_max": int(counts.max()),
+                       "depths": {str(d): int((depths == d).sum()) for d in sorted(set(depths))},
+                       "p": 4, "periodic": True, "continuous": True,
+                       "outputs": "potential+energy+forces per system",
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "gpu_launches": st["launches"] * args.steps, "graph_launches_per_step": 1,
+            "lanes": st["lanes"], "tune_ms": st["tune_ms"], "clocks": clocks}), flush=True)
+    bt.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,7 +273,15 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
+        if args.workload == "batch512":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable":
+                                  "the oracle reference arm covers the single-system workload"}))
+            return
         run_reference(args, args.workload, world, rank)
+        return
+    if args.workload == "batch512":
+        run_batch(args, world, rank, local)
         return
 
     import numpy as np

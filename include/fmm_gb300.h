@@ -221,6 +221,52 @@ int fmm_set_timing(fmm_plan_t plan, int on);
 int fmm_get_stats(fmm_plan_t plan, fmm_stats_t *stats);
 
 /*
+ * Batched evaluation of many independent systems (each its own box, depth
+ * and particle count; one p, form and precision for all), for ensembles of
+ * small systems whose separate evaluations would be launch-bound.  Each
+ * system is §2.2 (+ §2.3, §4.2) exactly as fmm_eval computes it.
+ *
+ * fmm_batch_create — nsys systems: boxes (host, nsys x 4: x0, y0, z0, L),
+ *   depths (host, nsys), max_n (host, nsys); p, periodic and opts as
+ *   fmm_plan_create (opts.sync is honoured; opts applies to every system).
+ *   Systems of the same depth share one set of tables.  Errors as
+ *   fmm_plan_create.
+ */
+typedef struct fmm_batch_s *fmm_batch_t;
+int fmm_batch_create(fmm_batch_t *batch, int nsys, const double *boxes, const int *depths, int p,
+                     int periodic, const fmm_opts_t *opts, const int64_t *max_n);
+void fmm_batch_destroy(fmm_batch_t batch);
+
+/* Bytes of device workspace for particle counts n (host, nsys). */
+int fmm_batch_workspace_size(fmm_batch_t batch, const int64_t *n, size_t *bytes);
+
+/*
+ * fmm_batch_eval — evaluates every system.  Particles of system i are rows
+ * offsets[i] .. offsets[i+1]-1 (offsets: host, nsys + 1, CSR) of pos (device,
+ * float32 (N,3)), q, potential and forces (as fmm_eval); energy: device,
+ * nsys doubles (nullable).  The systems are spread over several stream lanes
+ * forked from and joined back to `stream`; the whole launch sequence is
+ * captured once into a CUDA graph and replayed by later calls with the same
+ * pointers and counts (one graph launch per call).  The number of lanes is
+ * chosen by timing candidates on the first call (fmm_batch_get_stats reports
+ * it).  Returns the first device-side error of any system (opts.sync = 1).
+ */
+int fmm_batch_eval(fmm_batch_t batch, const int64_t *offsets, const float *pos, const float *q,
+                   void *potential, double *energy, void *forces, void *workspace,
+                   size_t workspace_bytes, void *stream);
+
+/* launches: kernels launched by the last fmm_batch_eval (inside its graph);
+ * lanes: stream lanes chosen by the autotuner; graph: 1 if the last call
+ * replayed a captured graph. */
+typedef struct {
+    int launches;
+    int lanes;
+    int graph;
+    double tune_ms[8];  /* measured ms per call of lanes = 2, 4, 8, 16, 32 (first call) */
+} fmm_batch_stats_t;
+int fmm_batch_get_stats(fmm_batch_t batch, fmm_batch_stats_t *stats);
+
+/*
  * fmm_eval_static — fmm_eval without a workspace argument.  The paper has no
  * counterpart: this entry point is for callers that cannot allocate device
  * memory at the time they evaluate (code running inside another framework's

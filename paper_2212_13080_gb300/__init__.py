@@ -18,7 +18,7 @@ import torch
 from . import _binding as B
 from ._binding import FmmError  # noqa: F401
 
-__all__ = ["FMM", "FmmError", "fmm_energy"]
+__all__ = ["FMM", "FMMBatch", "FmmError", "fmm_energy"]
 
 _PREC = {"fp32": B.FMM_PREC_FP32, "fp64": B.FMM_PREC_FP64, "tf32x3": B.FMM_PREC_TF32X3}
 _FORCE = {"adjoint": B.FMM_FORCE_ADJOINT, "paper": B.FMM_FORCE_PAPER}
@@ -193,6 +193,78 @@ class FMM:
         if what in ("points", "out"):
             return buf.view(real).reshape(-1, 4)
         return buf.view(real).reshape(-1, self.p ** 3)
+
+
+class FMMBatch:
+    """Many independent systems (own box, depth, particle count; one p, form
+    and precision) evaluated together: one CUDA-graph launch per call after
+    the first (which also picks the number of stream lanes by timing).
+
+    eval(pos, q, offsets) with pos (N,3) / q (N,) device tensors holding the
+    systems' particles back to back and offsets (nsys+1) the CSR boundaries
+    -> dict(potential (N,), energy (nsys,), forces (N,3)).
+    """
+
+    def __init__(self, boxes, depths, p, periodic=False, continuous=False, split_ratio=None,
+                 precision="fp32", force_mode="adjoint", max_n=None, split_capacity=None,
+                 sync=True, device=None):
+        import numpy as np
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self.nsys = len(depths)
+        o = B.fmm_opts_default()
+        o.continuous = int(bool(continuous))
+        if split_ratio is not None:
+            o.split_ratio = float(split_ratio)
+        if split_capacity is not None:
+            o.split_capacity = float(split_capacity)
+        o.precision = _PREC[precision]
+        o.force_mode = _FORCE[force_mode]
+        o.sync = int(bool(sync))
+        self.out_dtype = torch.float64 if precision == "fp64" else torch.float32
+        with torch.cuda.device(self.device):
+            self._h = B.fmm_batch_create(np.asarray(boxes, np.float64).reshape(-1, 4),
+                                         np.asarray(depths), p, periodic, o,
+                                         np.asarray(max_n, np.int64))
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.fmm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eval(self, pos, q, offsets, potential=True, energy=True, forces=True, stream=None,
+             out=None):
+        import numpy as np
+        offs = np.asarray(offsets, np.int64)
+        counts = np.diff(offs)
+        need = B.fmm_batch_workspace_size(self._h, counts)
+        if self._ws is None or self._ws.numel() < need + 256:
+            self._ws = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
+        ws = FMM._aligned(self._ws)
+        n = int(offs[-1])
+        o = out if out is not None else {}
+        phi = o.get("potential") if potential else None
+        if potential and phi is None:
+            phi = torch.empty(n, dtype=self.out_dtype, device=self.device)
+        E = o.get("energy") if energy else None
+        if energy and E is None:
+            E = torch.empty(self.nsys, dtype=torch.float64, device=self.device)
+        F = o.get("forces") if forces else None
+        if forces and F is None:
+            F = torch.empty((n, 3), dtype=self.out_dtype, device=self.device)
+        B.fmm_batch_eval(self._h, offs, _ptr(pos.contiguous()), _ptr(q.contiguous()), _ptr(phi),
+                         _ptr(E), _ptr(F), _ptr(ws), ws.numel(), _stream(stream))
+        return {"potential": phi, "energy": E, "forces": F}
+
+    def stats(self):
+        return B.fmm_batch_get_stats(self._h)
 
 
 class _Energy(torch.autograd.Function):

@@ -43,7 +43,8 @@ FMM_DUMP_OUT = 8
 EXPORTED = ["fmm_opts_default", "fmm_plan_create", "fmm_plan_destroy", "fmm_workspace_size",
             "fmm_eval", "fmm_backward", "fmm_status", "fmm_debug_dump", "fmm_debug_size",
             "fmm_set_timing", "fmm_get_stats", "fmm_strerror", "fmm_version",
-            "fmm_eval_static"]
+            "fmm_eval_static", "fmm_batch_create", "fmm_batch_destroy",
+            "fmm_batch_workspace_size", "fmm_batch_eval", "fmm_batch_get_stats"]
 
 FMM_STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -59,6 +60,11 @@ class fmm_opts_t(ctypes.Structure):
 class fmm_stats_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int), ("timed", ctypes.c_int),
                 ("stage_ms", ctypes.c_double * 9)]
+
+
+class fmm_batch_stats_t(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int), ("lanes", ctypes.c_int), ("graph", ctypes.c_int),
+                ("tune_ms", ctypes.c_double * 8)]
 
 
 class FmmError(RuntimeError):
@@ -96,6 +102,13 @@ def lib():
         L.fmm_strerror.restype = ctypes.c_char_p
         L.fmm_version.argtypes = []
         L.fmm_eval_static.argtypes = [P, i64, P, P, P, P, P, P]
+        L.fmm_batch_create.argtypes = [ctypes.POINTER(P), i32, P, P, i32, i32,
+                                       ctypes.POINTER(fmm_opts_t), P]
+        L.fmm_batch_destroy.argtypes = [P]
+        L.fmm_batch_destroy.restype = None
+        L.fmm_batch_workspace_size.argtypes = [P, P, ctypes.POINTER(sz)]
+        L.fmm_batch_eval.argtypes = [P, P, P, P, P, P, P, P, sz, P]
+        L.fmm_batch_get_stats.argtypes = [P, ctypes.POINTER(fmm_batch_stats_t)]
         _lib = L
     return _lib
 
@@ -173,3 +186,44 @@ def fmm_get_stats(h):
     _check(lib().fmm_get_stats(h, ctypes.byref(st)), "fmm_get_stats")
     return {"launches": st.launches, "timed": bool(st.timed),
             "stage_ms": dict(zip(STAGES, list(st.stage_ms)))}
+
+
+def fmm_batch_create(boxes, depths, p, periodic, opts, max_n):
+    import numpy as np
+    h = ctypes.c_void_p()
+    b = np.ascontiguousarray(boxes, dtype=np.float64)
+    d = np.ascontiguousarray(depths, dtype=np.int32)
+    m = np.ascontiguousarray(max_n, dtype=np.int64)
+    _check(lib().fmm_batch_create(ctypes.byref(h), len(d), b.ctypes.data_as(ctypes.c_void_p),
+                                  d.ctypes.data_as(ctypes.c_void_p), int(p), int(bool(periodic)),
+                                  ctypes.byref(opts) if opts is not None else None,
+                                  m.ctypes.data_as(ctypes.c_void_p)), "fmm_batch_create")
+    return h
+
+
+def fmm_batch_destroy(h):
+    if h:
+        lib().fmm_batch_destroy(h)
+
+
+def fmm_batch_workspace_size(h, n):
+    import numpy as np
+    a = np.ascontiguousarray(n, dtype=np.int64)
+    s = ctypes.c_size_t()
+    _check(lib().fmm_batch_workspace_size(h, a.ctypes.data_as(ctypes.c_void_p), ctypes.byref(s)),
+           "fmm_batch_workspace_size")
+    return s.value
+
+
+def fmm_batch_eval(h, offsets, pos, q, potential, energy, forces, workspace, ws_bytes, stream):
+    import numpy as np
+    o = np.ascontiguousarray(offsets, dtype=np.int64)
+    _check(lib().fmm_batch_eval(h, o.ctypes.data_as(ctypes.c_void_p), pos, q, potential, energy,
+                                forces, workspace, ws_bytes, stream), "fmm_batch_eval")
+
+
+def fmm_batch_get_stats(h):
+    st = fmm_batch_stats_t()
+    _check(lib().fmm_batch_get_stats(h, ctypes.byref(st)), "fmm_batch_get_stats")
+    return {"launches": st.launches, "lanes": st.lanes, "graph": bool(st.graph),
+            "tune_ms": dict(zip([2, 4, 8, 16, 32], list(st.tune_ms)[:5]))}

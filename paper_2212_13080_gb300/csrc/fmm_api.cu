@@ -30,6 +30,7 @@ struct fmm_plan_s {
     void *Kbar_tc;          // [343][a] row means, padded to 32
     alignas(64) unsigned char khi_map[128], klo_map[128];  // their TMA tensor maps
     bool tc;                // bilinear forms of levels >= 4 on tensor cores
+    bool shared;            // tables belong to another plan (batched systems)
     Coef<float> cf;
     Coef<double> cd;
     Geom geom;
@@ -380,7 +381,8 @@ int finish(fmm_plan_t P, const WsHeader *hdr, cudaStream_t st, bool sync) {
 
 template <typename real>
 int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *potential,
-              double *energy, real *forces, void *ws, cudaStream_t st, Tracer &tr) {
+              double *energy, real *forces, void *ws, const Streams &S, Tracer &tr) {
+    cudaStream_t st = S.main;
     WsLayout W = make_layout(P, n);
     Ptrs<real> ptr = make_ptrs<real>(W, ws);
     const Coef<real> &C = *reinterpret_cast<const Coef<real> *>(P->fp64 ? (const void *)&P->cd
@@ -398,7 +400,6 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     launch_sort<real>(g, ptr, W, (int)n, st, tr);
     // the near field needs only the sorted charges: it runs on its own stream
     // beside the whole far field and joins before the far field is added
-    Streams S = {st, P->s_near, P->s_coarse, P->e_sorted, P->e_near, P->e_fork, P->e_coarse};
     cudaEventRecord(S.sorted, st);
     cudaStreamWaitEvent(S.near, S.sorted, 0);
     launch_p2p<real>(g, ptr, W, forces != nullptr, S.near, tr);
@@ -558,6 +559,10 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
 
 void fmm_plan_destroy(fmm_plan_t P) {
     if (!P) return;
+    if (P->shared) {
+        delete P;
+        return;
+    }
     if (P->s_near) cudaStreamDestroy(P->s_near);
     if (P->s_coarse) cudaStreamDestroy(P->s_coarse);
     if (P->e_sorted) cudaEventDestroy(P->e_sorted);
@@ -591,10 +596,11 @@ int fmm_eval(fmm_plan_t P, int64_t n, const float *pos, const float *q, void *po
     cudaStream_t st = (cudaStream_t)stream;
     cudaGetLastError();
     Tracer tr = make_tracer(P, st);
+    Streams S = {st, P->s_near, P->s_coarse, P->e_sorted, P->e_near, P->e_fork, P->e_coarse};
     if (P->fp64)
-        rc = eval_impl<double>(P, n, pos, q, (double *)potential, energy, (double *)forces, workspace, st, tr);
+        rc = eval_impl<double>(P, n, pos, q, (double *)potential, energy, (double *)forces, workspace, S, tr);
     else
-        rc = eval_impl<float>(P, n, pos, q, (float *)potential, energy, (float *)forces, workspace, st, tr);
+        rc = eval_impl<float>(P, n, pos, q, (float *)potential, energy, (float *)forces, workspace, S, tr);
     P->last = tr;
     if (rc) return rc;
     P->last_ws = workspace;
@@ -754,6 +760,348 @@ int fmm_debug_dump(fmm_plan_t P, int what, const void *workspace, void *dst, siz
     }
     default: return FMM_ERR_ARG;
     }
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batched evaluation
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Lane {
+    cudaStream_t main, near, coarse;
+    cudaEvent_t sorted, near_done, fork, coarse_done, join;
+};
+
+const int kMaxLanes = 32;
+const int kLaneChoices[5] = {2, 4, 8, 16, 32};
+
+// OR of the status words of every system's workspace header
+__global__ void k_batch_status(const char *ws, const long long *off, int nsys, int *out) {
+    __shared__ int acc;
+    if (threadIdx.x == 0) acc = 0;
+    __syncthreads();
+    int st = 0;
+    for (int i = threadIdx.x; i < nsys; i += blockDim.x)
+        st |= reinterpret_cast<const WsHeader *>(ws + off[i])->status;
+    atomicOr(&acc, st);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = acc;
+}
+
+}  // namespace
+
+struct fmm_batch_s {
+    int nsys, p, periodic;
+    fmm_opts_t opts;
+    std::vector<fmm_plan_t> masters;  // one per distinct depth (owns the tables)
+    std::vector<fmm_plan_t> sys;      // per system (shares its master's tables)
+    std::vector<int64_t> max_n;
+    Lane lane[kMaxLanes];
+    int nlanes_made;
+    cudaEvent_t fork;
+    cudaStream_t cap;            // the graph is captured on and launched from this stream
+    cudaEvent_t in_ev, out_ev;   // caller's stream -> cap -> caller's stream
+    int *d_status, *h_status;
+    long long *d_off;
+    // captured graph and what it was captured for
+    cudaGraphExec_t gexec;
+    int glanes;
+    std::vector<int64_t> key;
+    int lanes;        // chosen by the autotuner (0: not yet tuned)
+    double tune_ms[8];
+    int launches;
+    bool last_graph;
+};
+
+namespace {
+
+fmm_plan_t clone_plan(const fmm_plan_s *m, const double *box, int64_t max_n) {
+    fmm_plan_s *P = new (std::nothrow) fmm_plan_s(*m);
+    if (!P) return nullptr;
+    P->shared = true;
+    P->s_near = P->s_coarse = nullptr;
+    P->e_sorted = P->e_near = P->e_fork = P->e_coarse = nullptr;
+    P->h_hdr = nullptr;
+    P->timing = false;
+    P->nev_created = 0;
+    P->max_n = max_n;
+    memcpy(P->box, box, sizeof(double) * 4);
+    for (int a = 0; a < 3; a++) P->geom.x0[a] = (float)box[a];
+    P->geom.Lf = (float)box[3];
+    P->geom.L = box[3];
+    return P;
+}
+
+int capture_batch(fmm_batch_t B, int lanes, const std::vector<int64_t> &n,
+                  const std::vector<int64_t> &pofs, const std::vector<size_t> &wofs, const float *pos,
+                  const float *q, void *potential, double *energy, void *forces, char *ws,
+                  cudaStream_t st, cudaGraphExec_t *out, int *launches) {
+    const size_t rs = B->opts.precision == FMM_PREC_FP64 ? 8 : 4;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return FMM_ERR_CUDA;
+    cudaEventRecord(B->fork, st);
+    for (int k = 0; k < lanes; k++) cudaStreamWaitEvent(B->lane[k].main, B->fork, 0);
+    int rc = FMM_OK, total = 0;
+    for (int i = 0; i < B->nsys && rc == FMM_OK; i++) {
+        const Lane &L = B->lane[i % lanes];
+        Streams S = {L.main, L.near, L.coarse, L.sorted, L.near_done, L.fork, L.coarse_done};
+        Tracer tr;
+        tr.st = L.main;
+        fmm_plan_t P = B->sys[i];
+        const int64_t o = pofs[i];
+        char *pot = potential ? (char *)potential + o * rs : nullptr;
+        char *frc = forces ? (char *)forces + 3 * o * rs : nullptr;
+        double *en = energy ? energy + i : nullptr;
+        if (P->fp64)
+            rc = eval_impl<double>(P, n[i], pos + 3 * o, q + o, (double *)pot, en, (double *)frc,
+                                   ws + wofs[i], S, tr);
+        else
+            rc = eval_impl<float>(P, n[i], pos + 3 * o, q + o, (float *)pot, en, (float *)frc,
+                                  ws + wofs[i], S, tr);
+        total += tr.launches;
+    }
+    for (int k = 0; k < lanes; k++) {
+        cudaEventRecord(B->lane[k].join, B->lane[k].main);
+        cudaStreamWaitEvent(st, B->lane[k].join, 0);
+    }
+    k_batch_status<<<1, 256, 0, st>>>(ws, B->d_off, B->nsys, B->d_status);
+    total++;
+    cudaMemcpyAsync(B->h_status, B->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (rc != FMM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess || !graph) return FMM_ERR_CUDA;
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return FMM_ERR_CUDA;
+    *launches = total;
+    return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fmm_batch_create(fmm_batch_t *out, int nsys, const double *boxes, const int *depths, int p,
+                     int periodic, const fmm_opts_t *opts, const int64_t *max_n) {
+    if (!out || nsys <= 0 || !boxes || !depths || !max_n) return FMM_ERR_ARG;
+    *out = nullptr;
+    fmm_batch_s *B = new (std::nothrow) fmm_batch_s();
+    if (!B) return FMM_ERR_OOM;
+    B->nsys = nsys;
+    B->p = p;
+    B->periodic = periodic ? 1 : 0;
+    fmm_opts_default(&B->opts);
+    if (opts) B->opts = *opts;
+    B->max_n.assign(max_n, max_n + nsys);
+    B->masters.assign(FMM_MAXDEPTH + 1, nullptr);
+    int rc = FMM_OK;
+    for (int i = 0; i < nsys && rc == FMM_OK; i++) {
+        const int d = depths[i];
+        if (d < 2 || d > FMM_MAXDEPTH) {
+            rc = FMM_ERR_ARG;
+            break;
+        }
+        if (!B->masters[d]) {
+            int64_t mx = 0;
+            for (int j = 0; j < nsys; j++)
+                if (depths[j] == d && max_n[j] > mx) mx = max_n[j];
+            rc = fmm_plan_create(&B->masters[d], boxes + 4 * i, d, p, periodic, &B->opts, mx);
+            if (rc) break;
+        }
+        if (!(boxes[4 * i + 3] > 0.0) || max_n[i] < 0) {
+            rc = FMM_ERR_ARG;
+            break;
+        }
+        fmm_plan_t c = clone_plan(B->masters[d], boxes + 4 * i, max_n[i]);
+        if (!c) {
+            rc = FMM_ERR_OOM;
+            break;
+        }
+        B->sys.push_back(c);
+    }
+    if (rc == FMM_OK) {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        for (int k = 0; k < kMaxLanes && rc == FMM_OK; k++) {
+            Lane &L = B->lane[k];
+            if (cudaStreamCreateWithFlags(&L.main, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithPriority(&L.near, cudaStreamNonBlocking, lo) != cudaSuccess ||
+                cudaStreamCreateWithPriority(&L.coarse, cudaStreamNonBlocking, hi) != cudaSuccess ||
+                cudaEventCreateWithFlags(&L.sorted, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&L.near_done, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&L.coarse_done, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming) != cudaSuccess)
+                rc = FMM_ERR_CUDA;
+            B->nlanes_made = k + 1;
+        }
+    }
+    if (rc == FMM_OK) {
+        if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->in_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->out_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&B->d_status, sizeof(int)) != cudaSuccess ||
+            cudaMallocHost(&B->h_status, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&B->d_off, sizeof(long long) * nsys) != cudaSuccess)
+            rc = FMM_ERR_OOM;
+    }
+    if (rc != FMM_OK) {
+        fmm_batch_destroy(B);
+        return rc;
+    }
+    *out = B;
+    return FMM_OK;
+}
+
+void fmm_batch_destroy(fmm_batch_t B) {
+    if (!B) return;
+    if (B->gexec) cudaGraphExecDestroy(B->gexec);
+    for (fmm_plan_t c : B->sys) delete c;
+    for (fmm_plan_t m : B->masters)
+        if (m) fmm_plan_destroy(m);
+    for (int k = 0; k < B->nlanes_made; k++) {
+        Lane &L = B->lane[k];
+        if (L.main) cudaStreamDestroy(L.main);
+        if (L.near) cudaStreamDestroy(L.near);
+        if (L.coarse) cudaStreamDestroy(L.coarse);
+        if (L.sorted) cudaEventDestroy(L.sorted);
+        if (L.near_done) cudaEventDestroy(L.near_done);
+        if (L.fork) cudaEventDestroy(L.fork);
+        if (L.coarse_done) cudaEventDestroy(L.coarse_done);
+        if (L.join) cudaEventDestroy(L.join);
+    }
+    if (B->fork) cudaEventDestroy(B->fork);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    if (B->in_ev) cudaEventDestroy(B->in_ev);
+    if (B->out_ev) cudaEventDestroy(B->out_ev);
+    if (B->d_status) cudaFree(B->d_status);
+    if (B->h_status) cudaFreeHost(B->h_status);
+    if (B->d_off) cudaFree(B->d_off);
+    delete B;
+}
+
+static int batch_layout(fmm_batch_t B, const int64_t *n, std::vector<size_t> &wofs, size_t *total) {
+    wofs.resize(B->nsys);
+    size_t o = 0;
+    for (int i = 0; i < B->nsys; i++) {
+        if (n[i] < 0 || n[i] > B->max_n[i]) return FMM_ERR_ARG;
+        wofs[i] = o;
+        o += align256(make_layout(B->sys[i], n[i]).total);
+    }
+    *total = o;
+    return FMM_OK;
+}
+
+int fmm_batch_workspace_size(fmm_batch_t B, const int64_t *n, size_t *bytes) {
+    if (!B || !n || !bytes) return FMM_ERR_ARG;
+    std::vector<size_t> w;
+    return batch_layout(B, n, w, bytes);
+}
+
+int fmm_batch_eval(fmm_batch_t B, const int64_t *offsets, const float *pos, const float *q,
+                   void *potential, double *energy, void *forces, void *workspace,
+                   size_t workspace_bytes, void *stream) {
+    if (!B || !offsets) return FMM_ERR_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255)) return FMM_ERR_WORKSPACE;
+    std::vector<int64_t> n(B->nsys), pofs(B->nsys);
+    for (int i = 0; i < B->nsys; i++) {
+        pofs[i] = offsets[i];
+        n[i] = offsets[i + 1] - offsets[i];
+    }
+    if (offsets[B->nsys] > 0 && (!pos || !q)) return FMM_ERR_ARG;
+    std::vector<size_t> wofs;
+    size_t total = 0;
+    int rc = batch_layout(B, n.data(), wofs, &total);
+    if (rc) return rc;
+    if (workspace_bytes < total) return FMM_ERR_WORKSPACE;
+    cudaStream_t caller = (cudaStream_t)stream;
+    // capture and launch on the batch's own stream (the caller's may be the
+    // legacy default stream, which cannot be captured), ordered after the
+    // caller's earlier work and before its later work by events
+    cudaStream_t st = B->cap;
+    cudaEventRecord(B->in_ev, caller);
+    cudaStreamWaitEvent(st, B->in_ev, 0);
+    char *ws = (char *)workspace;
+    // what a captured graph is valid for: pointers and counts
+    std::vector<int64_t> key = {(int64_t)(uintptr_t)pos, (int64_t)(uintptr_t)q,
+                                (int64_t)(uintptr_t)potential, (int64_t)(uintptr_t)energy,
+                                (int64_t)(uintptr_t)forces, (int64_t)(uintptr_t)workspace};
+    key.insert(key.end(), n.begin(), n.end());
+    cudaGetLastError();
+    B->last_graph = true;
+    if (!B->gexec || key != B->key || (B->lanes && B->glanes != B->lanes)) {
+        std::vector<long long> off(B->nsys);
+        for (int i = 0; i < B->nsys; i++) off[i] = (long long)wofs[i];
+        if (cudaMemcpy(B->d_off, off.data(), sizeof(long long) * B->nsys, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return FMM_ERR_CUDA;
+        if (B->gexec) {
+            cudaGraphExecDestroy(B->gexec);
+            B->gexec = nullptr;
+        }
+        if (!B->lanes) {
+            // autotune the number of stream lanes: time each candidate's graph
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            double best = 1e30;
+            int best_l = 2;
+            for (int c = 0; c < 5; c++) {
+                const int l = kLaneChoices[c] < B->nsys ? kLaneChoices[c] : B->nsys;
+                cudaGraphExec_t ex = nullptr;
+                int launches = 0;
+                rc = capture_batch(B, l, n, pofs, wofs, pos, q, potential, energy, forces, ws, st, &ex,
+                                   &launches);
+                if (rc) break;
+                cudaGraphLaunch(ex, st);  // warm-up
+                cudaEventRecord(a, st);
+                for (int r = 0; r < 3; r++) cudaGraphLaunch(ex, st);
+                cudaEventRecord(b, st);
+                cudaEventSynchronize(b);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, b);
+                B->tune_ms[c] = ms / 3.0;
+                if (ms < best) {
+                    best = ms;
+                    best_l = l;
+                }
+                cudaGraphExecDestroy(ex);
+                if (kLaneChoices[c] >= B->nsys) break;
+            }
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            if (rc) return rc;
+            B->lanes = best_l;
+        }
+        rc = capture_batch(B, B->lanes, n, pofs, wofs, pos, q, potential, energy, forces, ws, st,
+                           &B->gexec, &B->launches);
+        if (rc) return rc;
+        B->glanes = B->lanes;
+        B->key = key;
+    }
+    if (cudaGraphLaunch(B->gexec, st) != cudaSuccess) return FMM_ERR_CUDA;
+    cudaEventRecord(B->out_ev, st);
+    cudaStreamWaitEvent(caller, B->out_ev, 0);
+    if (cudaGetLastError() != cudaSuccess) return FMM_ERR_CUDA;
+    if (!B->opts.sync) return FMM_OK;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_ERR_CUDA;
+    return status_to_error(*B->h_status);
+}
+
+int fmm_batch_get_stats(fmm_batch_t B, fmm_batch_stats_t *out) {
+    if (!B || !out) return FMM_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    out->launches = B->launches;
+    out->lanes = B->lanes;
+    out->graph = B->last_graph ? 1 : 0;
+    for (int c = 0; c < 5; c++) out->tune_ms[c] = B->tune_ms[c];
+    return FMM_OK;
 }
 
 }  // extern "C"

@@ -105,6 +105,21 @@ def batched_sizes(nsys, seed, lo=1024, hi=65536):
     return n - (n % 2)
 
 
+def batch_systems(nsys, seed, lo=1024, hi=65536):
+    """nsys independent unit-box systems: N log-uniform in [lo, hi] (even),
+    uniform positions, +-1 charges with zero net charge per system.  Returns
+    (pos (sum N, 3) float32, q float32, offsets (nsys+1) int64, boxes (nsys,4),
+    counts)."""
+    counts = batched_sizes(nsys, seed, lo, hi)
+    rng = _rng(seed + 1)
+    pos = rng.random((int(counts.sum()), 3), dtype=np.float32)
+    q = np.concatenate([_pm1(rng, int(c)) for c in counts])
+    offsets = np.zeros(nsys + 1, np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    boxes = np.tile(np.array([0.0, 0.0, 0.0, 1.0]), (nsys, 1))
+    return pos, q, offsets, boxes, counts
+
+
 # ---- the named workloads -------------------------------------------------
 
 def workload(name, seed=None, n=None):

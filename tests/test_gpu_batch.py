@@ -1,0 +1,58 @@
+"""Batched evaluation of many independent systems (own box, depth, count):
+every system must equal its own single-system evaluation (same kernels, same
+inputs), and the single-system path is pinned to the oracle elsewhere; a few
+systems are also checked against the oracle directly."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2212_13080_gb300 import FMM, FMMBatch, inputs  # noqa: E402
+
+
+def _depths(counts):
+    return np.clip(np.rint(np.log(counts / 32.0) / np.log(8.0)), 3, 5).astype(int)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_matches_single_system(precision):
+    pos, q, offs, boxes, counts = inputs.batch_systems(12, 7, lo=1024, hi=20000)
+    boxes[3] = (0.25, -1.0, 2.0, 1.5)  # one system in another box
+    pos[offs[3]:offs[4]] = (pos[offs[3]:offs[4]] * np.float32(1.5) +
+                            np.array([0.25, -1.0, 2.0], np.float32)).astype(np.float32)
+    depths = _depths(counts)
+    bt = FMMBatch(boxes, depths, 4, periodic=True, continuous=True, precision=precision,
+                  max_n=counts)
+    P, Q = torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda()
+    for call in range(2):  # first call tunes and captures, second replays the graph
+        r = bt.eval(P, Q, offs)
+        torch.cuda.synchronize()
+        st = bt.stats()
+        assert st["lanes"] in (2, 4, 8, 12, 16, 32) and st["launches"] > 12
+        for i in range(len(counts)):
+            a, b = offs[i], offs[i + 1]
+            plan = FMM(boxes[i], int(depths[i]), 4, periodic=True, continuous=True,
+                       precision=precision, max_n=int(counts[i]))
+            s = plan.eval(P[a:b].contiguous(), Q[a:b].contiguous())
+            assert torch.equal(r["potential"][a:b], s["potential"]), (call, i)
+            assert torch.equal(r["forces"][a:b], s["forces"]), (call, i)
+            assert r["energy"][i].item() == s["energy"].item(), (call, i)
+            plan.close()
+    bt.close()
+
+
+def test_batch_against_oracle():
+    pos, q, offs, boxes, counts = inputs.batch_systems(6, 11, lo=1024, hi=8000)
+    depths = _depths(counts)
+    bt = FMMBatch(boxes, depths, 4, periodic=True, continuous=True, precision="fp64", max_n=counts)
+    r = bt.eval(torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda(), offs)
+    for i in (0, 5):
+        a, b = offs[i], offs[i + 1]
+        ref = oracle.fmm(pos[a:b], q[a:b], boxes[i], depth=int(depths[i]), n=4, periodic=True,
+                         continuous=True)
+        phi = r["potential"][a:b].cpu().numpy()
+        assert np.linalg.norm(phi - ref["phi"]) < 1e-11 * np.linalg.norm(ref["phi"])
+        assert abs(r["energy"][i].item() - ref["E"]) < 1e-11 * abs(ref["E"])
+    bt.close()
