@@ -37,8 +37,8 @@ struct fmm_plan_s {
     const void *last_ws;
     int64_t last_n;
     int *h_hdr;  // pinned copy of the workspace header
-    cudaStream_t s_near, s_coarse;  // auxiliary streams of an evaluation
-    cudaEvent_t e_sorted, e_near, e_fork, e_coarse;
+    cudaStream_t s_near, s_coarse, s_far;  // auxiliary streams of an evaluation
+    cudaEvent_t e_sorted, e_near, e_fork, e_coarse, e_far;
     bool timing;
     cudaEvent_t ev[512];
     int nev_created;
@@ -404,7 +404,14 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     cudaStreamWaitEvent(S.near, S.sorted, 0);
     launch_p2p<real>(g, ptr, W, forces != nullptr, S.near, tr);
     cudaEventRecord(S.near_done, S.near);
-    launch_upward<real>(g, C, ptr, W, st, tr);
+    // the far field runs on a high-priority stream when one is given, so that
+    // its CTAs are dispatched ahead of the near field's as SMs free up
+    Streams F = S;
+    if (S.far) {
+        cudaStreamWaitEvent(S.far, S.sorted, 0);
+        F.main = S.far;
+    }
+    launch_upward<real>(g, C, ptr, W, F.main, tr);
     DevTables<real> T;
     T.KtT = (const real *)P->Kunit;
     T.Kbar = (const real *)P->Kbar;
@@ -414,8 +421,12 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     T.tc_khi_map = P->khi_map;
     T.tc_klo_map = P->klo_map;
     T.tc_kbar = (const float *)P->Kbar_tc;
-    int rc = launch_downward<real>(g, C, ptr, W, T, S, tr);
+    int rc = launch_downward<real>(g, C, ptr, W, T, F, tr);
     if (rc) return rc;
+    if (S.far) {
+        cudaEventRecord(S.far_done, S.far);
+        cudaStreamWaitEvent(st, S.far_done, 0);
+    }
     cudaStreamWaitEvent(st, S.near_done, 0);
     launch_l2p<real>(g, C, ptr, W, forces != nullptr, st, tr);
     launch_unsplit<real>(g, ptr, W, (int)n, q, potential, energy, forces, nullptr, nullptr, false,
@@ -539,6 +550,8 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
         // near field: lowest priority (it fills the GPU); coarse levels: highest
         if (cudaStreamCreateWithPriority(&P->s_near, cudaStreamNonBlocking, lo) != cudaSuccess ||
             cudaStreamCreateWithPriority(&P->s_coarse, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&P->s_far, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->e_far, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&P->e_sorted, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&P->e_near, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&P->e_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -565,6 +578,8 @@ void fmm_plan_destroy(fmm_plan_t P) {
     }
     if (P->s_near) cudaStreamDestroy(P->s_near);
     if (P->s_coarse) cudaStreamDestroy(P->s_coarse);
+    if (P->s_far) cudaStreamDestroy(P->s_far);
+    if (P->e_far) cudaEventDestroy(P->e_far);
     if (P->e_sorted) cudaEventDestroy(P->e_sorted);
     if (P->e_near) cudaEventDestroy(P->e_near);
     if (P->e_fork) cudaEventDestroy(P->e_fork);
@@ -596,7 +611,8 @@ int fmm_eval(fmm_plan_t P, int64_t n, const float *pos, const float *q, void *po
     cudaStream_t st = (cudaStream_t)stream;
     cudaGetLastError();
     Tracer tr = make_tracer(P, st);
-    Streams S = {st, P->s_near, P->s_coarse, P->e_sorted, P->e_near, P->e_fork, P->e_coarse};
+    Streams S = {st, P->s_near, P->s_coarse, P->e_sorted, P->e_near, P->e_fork, P->e_coarse,
+                 P->s_far, P->e_far};
     if (P->fp64)
         rc = eval_impl<double>(P, n, pos, q, (double *)potential, energy, (double *)forces, workspace, S, tr);
     else
@@ -821,8 +837,8 @@ fmm_plan_t clone_plan(const fmm_plan_s *m, const double *box, int64_t max_n) {
     fmm_plan_s *P = new (std::nothrow) fmm_plan_s(*m);
     if (!P) return nullptr;
     P->shared = true;
-    P->s_near = P->s_coarse = nullptr;
-    P->e_sorted = P->e_near = P->e_fork = P->e_coarse = nullptr;
+    P->s_near = P->s_coarse = P->s_far = nullptr;
+    P->e_sorted = P->e_near = P->e_fork = P->e_coarse = P->e_far = nullptr;
     P->h_hdr = nullptr;
     P->timing = false;
     P->nev_created = 0;
@@ -846,7 +862,8 @@ int capture_batch(fmm_batch_t B, int lanes, const std::vector<int64_t> &n,
     int rc = FMM_OK, total = 0;
     for (int i = 0; i < B->nsys && rc == FMM_OK; i++) {
         const Lane &L = B->lane[i % lanes];
-        Streams S = {L.main, L.near, L.coarse, L.sorted, L.near_done, L.fork, L.coarse_done};
+        Streams S = {L.main, L.near, L.coarse, L.sorted, L.near_done, L.fork, L.coarse_done,
+                     nullptr, nullptr};
         Tracer tr;
         tr.st = L.main;
         fmm_plan_t P = B->sys[i];

@@ -216,6 +216,8 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
 struct Streams {
     cudaStream_t main, near, coarse;
     cudaEvent_t sorted, near_done, fork, coarse_done;
+    cudaStream_t far;     // optional: the far-field chain's stream
+    cudaEvent_t far_done;
 };
 
 template <typename real>

@@ -275,7 +275,8 @@ def test_forces_central_differences_fp64():
 
 @pytest.mark.parametrize("name,sample,precision", [("uniform1m", 512, "fp32"), ("water2m", 256, "fp32"),
                                                     ("uniform1m", 512, "tf32x3"),
-                                                    ("water2m", 256, "tf32x3")])
+                                                    ("water2m", 256, "tf32x3"),
+                                                    ("plummer8m", 256, "tf32x3")])
 def test_parity_full_size_sampled(name, sample, precision):
     """Full-size workloads in the benchmark's launch configuration: integer work
     on every charge, outputs on sampled particles (the oracle computes those one
