@@ -159,8 +159,9 @@ def run_reference(args, workload, world, rank):
     w = inputs.workload(workload)
     pos, q, box = w["pos"], w["q"], w["box"]
     n = len(q)
+    idx = _oracle_targets(n)
     kw = dict(depth=w["depth"], n=w["p"], periodic=w["periodic"], continuous=w["continuous"],
-              keep=False)
+              sample=idx, keep=False)
     for _ in range(args.warmup):
         oracle.fmm(pos, q, box, **kw)
     ts = []
@@ -170,8 +171,12 @@ def run_reference(args, workload, world, rank):
         ts.append(time.perf_counter() - t0)
     t = statistics.mean(ts)
     cores = os.cpu_count()
-    v = n / t / 1e6
-    sample = "whole workload (%d particles) per step, oracle.fmm FP64, OpenMP" % n
+    m = n if idx is None else len(idx)
+    v = m / t / 1e6
+    sample = ("whole workload (%d particles) per step, oracle.fmm FP64, OpenMP" % n
+              if idx is None else
+              "outputs of %d sampled particles of %d per step (full upward pass), oracle.fmm "
+              "FP64, OpenMP" % (m, n))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
@@ -185,18 +190,69 @@ def run_reference(args, workload, world, rank):
     }), flush=True)
 
 
-def cpu_baseline(workload):
+WHOLE_ORACLE_MAX_N = 1 << 21   # above this the oracle runs on a bounded sample of targets
+ORACLE_SAMPLE = 512
+
+
+def _oracle_targets(n):
+    import numpy as np
+    if n <= WHOLE_ORACLE_MAX_N:
+        return None
+    return np.sort(np.random.default_rng(12345).choice(n, ORACLE_SAMPLE, replace=False))
+
+
+def cpu_baseline(workload, gpu_outputs=None):
+    """The FP64 oracle on the host cores (whole workload up to 2M particles, else the
+    outputs of 512 sampled particles) and, from the same run, the relative L2 error of
+    the GPU results against it; for the open form also the method's own error (the
+    oracle against the direct O(N) sum at the sampled particles)."""
+    import numpy as np
     import oracle
     from paper_2212_13080_gb300 import inputs
     w = inputs.workload(workload)
     n = len(w["q"])
+    idx = _oracle_targets(n)
     t0 = time.perf_counter()
-    oracle.fmm(w["pos"], w["q"], w["box"], depth=w["depth"], n=w["p"], periodic=w["periodic"],
-               continuous=w["continuous"], keep=False)
+    r = oracle.fmm(w["pos"], w["q"], w["box"], depth=w["depth"], n=w["p"],
+                   periodic=w["periodic"], continuous=w["continuous"], sample=idx, keep=False)
     t = time.perf_counter() - t0
-    return {"value": n / t / 1e6, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "whole workload (%d particles), one oracle.fmm run (FP64, OpenMP), %.1f s"
-                      % (n, t)}
+    m = n if idx is None else len(idx)
+    base = {"value": m / t / 1e6, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": ("whole workload (%d particles), one oracle.fmm run (FP64, OpenMP), %.1f s"
+                       % (n, t)) if idx is None else
+                      ("outputs of %d sampled particles of %d (full upward pass, downward pass "
+                       "where they need it), one oracle.fmm run (FP64, OpenMP), %.1f s"
+                       % (m, n, t))}
+    err = None
+    if gpu_outputs:
+        sel = np.arange(n) if idx is None else idx
+        phi_o = np.asarray(r["phi"], np.float64)
+        F_o = np.asarray(r["F"], np.float64).reshape(-1, 3)
+        if idx is not None and phi_o.shape[0] == n:
+            phi_o, F_o = phi_o[idx], F_o[idx]
+
+        def rel(a, b):
+            return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+        err = {"particles": int(len(sel)), "reference": "oracle (FP64, same method and p)"}
+        for name, (phi_g, F_g, E_g) in gpu_outputs.items():
+            e = {"potential_rel_l2": rel(phi_g[sel].astype(np.float64), phi_o),
+                 "forces_rel_l2": rel(F_g[sel].astype(np.float64), F_o)}
+            if idx is None and r.get("E") is not None:
+                e["energy_rel"] = abs(E_g - r["E"]) / abs(r["E"])
+            err[name] = e
+        if not w["periodic"]:
+            tg = idx if idx is not None else np.sort(
+                np.random.default_rng(12345).choice(n, ORACLE_SAMPLE, replace=False))
+            phi_d, F_d = oracle.direct(w["pos"], w["q"], w["box"], targets=tg)
+            phi_m = np.asarray(r["phi"], np.float64)
+            F_m = np.asarray(r["F"], np.float64).reshape(-1, 3)
+            if phi_m.shape[0] == n:
+                phi_m, F_m = phi_m[tg], F_m[tg]
+            err["method_error_vs_direct"] = {"particles": int(len(tg)),
+                                             "potential_rel_l2": rel(phi_m, phi_d),
+                                             "forces_rel_l2": rel(F_m, F_d)}
+    return base, err
 
 
 def run_batch(args, world, rank, local):
@@ -368,6 +424,23 @@ def main():
     value = world * n / (t_step * 1e-3) / 1e6
     stage_ms = {k: v / args.steps for k, v in stage_tot.items()}
 
+    # the same steps with every stage on one stream: each stage's own duration
+    plan.set_timing(True, serial=True)
+    iso_tot, n_iso = {}, max(3, args.steps // 4)
+    for _ in range(n_iso):
+        flush.zero_()
+        step()
+        for k, v in plan.stats()["stage_ms"].items():
+            iso_tot[k] = iso_tot.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    stage_ms_iso = {k: v / n_iso for k, v in iso_tot.items()}
+
+    def host_outputs():
+        return (out["potential"].cpu().numpy(), out["forces"].cpu().numpy(),
+                float(out["energy"].item()))
+    gpu_outputs = {args.precision: host_outputs()}
+
     # the plain FP32 form (SIMT contraction), same timing protocol, fewer steps
     plain = None
     if args.precision != "fp32":
@@ -384,6 +457,7 @@ def main():
             b.record(stream)
             b.synchronize()
             t32.append(a.elapsed_time(b))
+        gpu_outputs["fp32"] = host_outputs()
         plain = {"precision": "fp32", "ms_per_step": statistics.mean(t32),
                  "value": n / (statistics.mean(t32) * 1e-3) / 1e6, "unit": UNIT}
         plan32.close()
@@ -423,24 +497,32 @@ def main():
                   "peak_source": tf32_src}
     if dom == "p2p":
         ach = p2p_flops / (stage_ms["p2p"] * 1e-3) / 1e12
+        ach_iso = p2p_flops / (stage_ms_iso["p2p"] * 1e-3) / 1e12
         roof = {"kernel": "k_p2p", "bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
                 "algorithmic": "%d ordered pairs x %d flop" % (pairs, P2P_FLOPS_PER_PAIR),
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                "note": "achieved: in-step duration, overlapped with the far field; "
+                        "achieved_isolated: the same kernel with every stage on one stream",
+                "achieved_isolated": ach_iso, "frac_isolated": ach_iso / FP32_ALU_PEAK_TFLOPS}
     else:
         ach = m2l_flops / (stage_ms["m2l"] * 1e-3) / 1e12
+        ach_iso = m2l_flops / (stage_ms_iso["m2l"] * 1e-3) / 1e12
         if args.precision == "tf32x3":
             roof = {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": ach, "peak": tf32_peak,
                     "unit": "TFLOP/s", "frac": ach / tf32_peak, "traffic": None,
                     "algorithmic": "%d cell pairs x 2 p^6 flop (all levels per step; the 3-pass "
                                    "split executes 3x)" % cellpairs,
-                    "peak_source": tf32_src}
+                    "peak_source": tf32_src,
+                    "achieved_isolated": ach_iso, "frac_isolated": ach_iso / tf32_peak}
         else:
             roof = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": ach,
                     "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
                     "algorithmic": "%d cell pairs x 2 p^6 flop (all levels per step)" % cellpairs,
-                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
+                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                    "achieved_isolated": ach_iso,
+                    "frac_isolated": ach_iso / FP32_ALU_PEAK_TFLOPS}
     roof["hbm_peak_gbs"] = hbm
     roof["hbm_peak_source"] = peak_kind
 
@@ -459,7 +541,7 @@ def main():
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
-        "stage_ms": stage_ms,
+        "stage_ms": stage_ms, "stage_ms_isolated": stage_ms_iso,
         "pairs_per_s": pairs / (t_step * 1e-3),
         "p2p_tflops": p2p_flops / (stage_ms.get("p2p", 1e9) * 1e-3) / 1e12,
         "m2l_tflops": m2l_flops / (stage_ms.get("m2l", 1e9) * 1e-3) / 1e12,
@@ -468,7 +550,7 @@ def main():
         "plain_fp32": plain,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(args.workload)
+        res["cpu_baseline"], res["error_vs_fp64_oracle"] = cpu_baseline(args.workload, gpu_outputs)
     if rank == 0:
         print(json.dumps(res), flush=True)
     plan.close()

@@ -62,6 +62,10 @@ extern "C" {
 #define FMM_PREC_FP64 1   /* FP64 everywhere; outputs are float64 */
 #define FMM_PREC_TF32X3 2 /* bilinear forms on tcgen05 tensor cores, 3-pass split TF32,
                              FP32 accumulate; rest FP32 */
+#define FMM_PREC_TF32X1 3 /* tensor cores, one TF32 pass (10-bit mantissa operands),
+                             FP32 accumulate; rest FP32 */
+#define FMM_PREC_BF16X3 4 /* tensor cores, 3-pass split BF16 (hi = bf16(x),
+                             lo = bf16(x - hi)), FP32 accumulate; rest FP32 */
 
 /* ---- flags of fmm_eval ---------------------------------------------------- */
 #define FMM_FORCE_ADJOINT 0 /* forces = -dE/dx of the FMM energy (default) */
@@ -201,6 +205,10 @@ int fmm_debug_size(fmm_plan_t plan, int what, const void *workspace, size_t *byt
  * fmm_get_stats() waits for them and reports the device time per stage (ms)
  * of the last call, and the number of kernels that call launched (counted
  * whether or not timing is on).  Stage ids: FMM_STAGE_*.
+ * on = 2 also runs every stage on the call's stream (the near field and the
+ * coarse levels are otherwise overlapped with the far field on plan-owned
+ * streams), so that each stage's time is its kernels' own duration; results
+ * are identical.  on = 0 switches timing off.
  */
 #define FMM_STAGE_BIN 0      /* binning and split (§2.2 step 1, §2.3) */
 #define FMM_STAGE_SORT 1     /* finest-cell ranges and stable sort */

@@ -20,7 +20,8 @@ from ._binding import FmmError  # noqa: F401
 
 __all__ = ["FMM", "FMMBatch", "FmmError", "fmm_energy"]
 
-_PREC = {"fp32": B.FMM_PREC_FP32, "fp64": B.FMM_PREC_FP64, "tf32x3": B.FMM_PREC_TF32X3}
+_PREC = {"fp32": B.FMM_PREC_FP32, "fp64": B.FMM_PREC_FP64, "tf32x3": B.FMM_PREC_TF32X3,
+         "tf32x1": B.FMM_PREC_TF32X1, "bf16x3": B.FMM_PREC_BF16X3}
 _FORCE = {"adjoint": B.FMM_FORCE_ADJOINT, "paper": B.FMM_FORCE_PAPER}
 
 
@@ -165,9 +166,12 @@ class FMM:
                        _ptr(ws), ws.numel(), _stream(stream))
         return gpos, gq
 
-    def set_timing(self, on=True):
-        """Bracket every stage of later calls with CUDA events (see stats())."""
-        B.fmm_set_timing(self._h, on)
+    def set_timing(self, on=True, serial=False):
+        """Bracket every stage of later calls with CUDA events (see stats()).
+
+        serial=True runs every stage on the call's stream (no near/far overlap), so
+        that each stage time is its kernels' own duration."""
+        B.fmm_set_timing(self._h, (2 if serial else 1) if on else 0)
 
     def stats(self):
         """Launch count and per-stage device time (ms) of the last call."""

@@ -25,6 +25,8 @@ FMM_ERR_UNSUPPORTED = 10
 FMM_PREC_FP32 = 0
 FMM_PREC_FP64 = 1
 FMM_PREC_TF32X3 = 2
+FMM_PREC_TF32X1 = 3
+FMM_PREC_BF16X3 = 4
 
 FMM_FORCE_ADJOINT = 0
 FMM_FORCE_PAPER = 1
@@ -178,7 +180,7 @@ def fmm_debug_dump(h, what, workspace, dst, nbytes, stream):
 
 
 def fmm_set_timing(h, on):
-    _check(lib().fmm_set_timing(h, int(bool(on))), "fmm_set_timing")
+    _check(lib().fmm_set_timing(h, int(on)), "fmm_set_timing")
 
 
 def fmm_get_stats(h):

@@ -30,6 +30,7 @@ struct fmm_plan_s {
     void *Kbar_tc;          // [343][a] row means, padded to 32
     alignas(64) unsigned char khi_map[128], klo_map[128];  // their TMA tensor maps
     bool tc;                // bilinear forms of levels >= 4 on tensor cores
+    int tc_mode;            // FMM_TC_*: split TF32 x3, TF32 x1, split BF16 x3
     bool shared;            // tables belong to another plan (batched systems)
     Coef<float> cf;
     Coef<double> cd;
@@ -40,6 +41,7 @@ struct fmm_plan_s {
     cudaStream_t s_near, s_coarse, s_far;  // auxiliary streams of an evaluation
     cudaEvent_t e_sorted, e_near, e_fork, e_coarse, e_far;
     bool timing;
+    bool serial;  // timing mode 2: every stage on the call's stream
     cudaEvent_t ev[512];
     int nev_created;
     Tracer last;  // launches and stage events of the last call
@@ -121,6 +123,21 @@ int upload(void **dst, const std::vector<real> &v) {
     return FMM_OK;
 }
 
+// bfloat16 = the upper 16 bits of an IEEE binary32; round to nearest, ties to
+// even, on the discarded 16 bits (finite inputs only)
+static uint16_t bf16_rne(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+static float bf16_value(uint16_t h) {
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
 // Unit-cell kernels of eq. (bilinear), K_o[a,b] = 1/|a - (o + b)| for the 316
 // offsets 2 <= |o|_inf <= 3, split into row mean and remainder (FP64, then
 // rounded to the plan's type).
@@ -154,12 +171,16 @@ int upload_tables(fmm_plan_t P) {
     if (!rc) rc = upload(&P->Kbar, Kbar);
     if (rc) return rc;
     if (P->tc) {
-        // Kt_o[a][b] = K_o[a][b] - Kbar_o[a] (natural layout, rows and columns
-        // zero-padded to p3s = p^3 rounded up to 32), split as hi = Kt with its
-        // 13 low mantissa bits cleared, lo = Kt - hi (from the FP64 value)
-        const int p3s = tc_padded(p3);
-        const size_t nt = (size_t)343 * p3s * p3s;
+        // Kt_o[a][b] = K_o[a][b] - Kbar_o[a] (natural layout, rows zero-padded to
+        // p3s = p^3 rounded up to 32, columns to pk), split from the FP64 value:
+        // TF32: hi = Kt with its 13 low mantissa bits cleared (rounded to nearest
+        // for the 1-pass form), lo = Kt - hi;
+        // BF16: hi = bf16(Kt), lo = bf16(Kt - hi), rounded to nearest even
+        const int p3s = tc_padded(p3), pk = tc_padded_k(p3, P->tc_mode);
+        const bool bf16 = P->tc_mode == FMM_TC_BF16X3;
+        const size_t nt = (size_t)343 * p3s * pk;
         std::vector<float> Khi(nt, 0.0f), Klo(nt, 0.0f), Kb((size_t)343 * p3s, 0.0f);
+        std::vector<uint16_t> Khi16(bf16 ? nt : 0, 0), Klo16(bf16 ? nt : 0, 0);
         for (int oi = 0; oi < 343; oi++) {
             int ox = oi % 7 - 3, oy = (oi / 7) % 7 - 3, oz = oi / 49 - 3;
             if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
@@ -177,23 +198,30 @@ int upload_tables(fmm_plan_t P) {
                 Kb[(size_t)oi * p3s + a] = (float)mean;
                 for (int b = 0; b < p3; b++) {
                     double k = row[b] - mean;
+                    size_t idx = ((size_t)oi * p3s + a) * pk + b;
+                    if (bf16) {
+                        uint16_t h = bf16_rne((float)k);
+                        Khi16[idx] = h;
+                        Klo16[idx] = bf16_rne((float)(k - (double)bf16_value(h)));
+                        continue;
+                    }
                     float f = (float)k;
                     uint32_t u;
                     memcpy(&u, &f, 4);
+                    if (P->tc_mode == FMM_TC_TF32X1) u += 0x1000u;  // nearest (no lo pass)
                     u &= 0xFFFFE000u;
                     float hi;
                     memcpy(&hi, &u, 4);
-                    size_t idx = ((size_t)oi * p3s + a) * p3s + b;
                     Khi[idx] = hi;
                     Klo[idx] = (float)(k - (double)hi);
                 }
             }
         }
-        rc = upload(&P->Ktc_hi, Khi);
-        if (!rc) rc = upload(&P->Ktc_lo, Klo);
+        rc = bf16 ? upload(&P->Ktc_hi, Khi16) : upload(&P->Ktc_hi, Khi);
+        if (!rc) rc = bf16 ? upload(&P->Ktc_lo, Klo16) : upload(&P->Ktc_lo, Klo);
         if (!rc) rc = upload(&P->Kbar_tc, Kb);
-        if (!rc) rc = tc_encode_kernel_map(P->khi_map, (const float *)P->Ktc_hi, p3s);
-        if (!rc) rc = tc_encode_kernel_map(P->klo_map, (const float *)P->Ktc_lo, p3s);
+        if (!rc) rc = tc_encode_kernel_map(P->khi_map, P->Ktc_hi, p3s, pk, P->tc_mode);
+        if (!rc) rc = tc_encode_kernel_map(P->klo_map, P->Ktc_lo, p3s, pk, P->tc_mode);
         if (rc) return rc;
     }
     if (P->periodic) {
@@ -418,6 +446,7 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     T.Klt = (const real *)P->Klat;
     T.Klbar = (const real *)P->Klbar;
     T.tc_lmin = P->tc ? 4 : 0;
+    T.tc_mode = P->tc_mode;
     T.tc_khi_map = P->khi_map;
     T.tc_klo_map = P->klo_map;
     T.tc_kbar = (const float *)P->Kbar_tc;
@@ -510,10 +539,11 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     if (opts) o = *opts;
     if (o.split_ratio <= 0) o.split_ratio = 1.0 / 256.0;
     if (o.continuous && !(o.split_ratio < 0.5)) return FMM_ERR_ARG;
-    if (o.precision != FMM_PREC_FP32 && o.precision != FMM_PREC_FP64 &&
-        o.precision != FMM_PREC_TF32X3)
+    const bool tc_prec = o.precision == FMM_PREC_TF32X3 || o.precision == FMM_PREC_TF32X1 ||
+                         o.precision == FMM_PREC_BF16X3;
+    if (o.precision != FMM_PREC_FP32 && o.precision != FMM_PREC_FP64 && !tc_prec)
         return FMM_ERR_UNSUPPORTED;
-    if (o.precision == FMM_PREC_TF32X3 && (p < 3 || p > 6)) return FMM_ERR_UNSUPPORTED;
+    if (tc_prec && (p < 3 || p > 6)) return FMM_ERR_UNSUPPORTED;
     fmm_plan_s *P = new (std::nothrow) fmm_plan_s();
     if (!P) return FMM_ERR_OOM;
     P->depth = depth;
@@ -523,7 +553,10 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     memcpy(P->box, box, sizeof(double) * 4);
     P->max_n = max_n;
     P->fp64 = o.precision == FMM_PREC_FP64;
-    P->tc = o.precision == FMM_PREC_TF32X3;
+    P->tc = tc_prec;
+    P->tc_mode = o.precision == FMM_PREC_BF16X3   ? FMM_TC_BF16X3
+                 : o.precision == FMM_PREC_TF32X1 ? FMM_TC_TF32X1
+                                                  : FMM_TC_TF32X3;
     cudaGetDevice(&P->device);
     fill_coef<float>(p, P->cf);
     fill_coef<double>(p, P->cd);
@@ -613,6 +646,7 @@ int fmm_eval(fmm_plan_t P, int64_t n, const float *pos, const float *q, void *po
     Tracer tr = make_tracer(P, st);
     Streams S = {st, P->s_near, P->s_coarse, P->e_sorted, P->e_near, P->e_fork, P->e_coarse,
                  P->s_far, P->e_far};
+    if (P->serial) S.near = S.coarse = st, S.far = nullptr;  // isolated stage times
     if (P->fp64)
         rc = eval_impl<double>(P, n, pos, q, (double *)potential, energy, (double *)forces, workspace, S, tr);
     else
@@ -656,6 +690,7 @@ int fmm_set_timing(fmm_plan_t P, int on) {
         }
     }
     P->timing = on != 0;
+    P->serial = on == 2;
     return FMM_OK;
 }
 
@@ -841,6 +876,7 @@ fmm_plan_t clone_plan(const fmm_plan_s *m, const double *box, int64_t max_n) {
     P->e_sorted = P->e_near = P->e_fork = P->e_coarse = P->e_far = nullptr;
     P->h_hdr = nullptr;
     P->timing = false;
+    P->serial = false;
     P->nev_created = 0;
     P->max_n = max_n;
     memcpy(P->box, box, sizeof(double) * 4);

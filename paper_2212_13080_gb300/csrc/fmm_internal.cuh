@@ -178,8 +178,9 @@ struct DevTables {
     const real *Kbar;   // [343][a]
     const real *Klt;    // [a][b] lattice kernel minus its row mean (periodic form)
     const real *Klbar;  // [a]
-    // tensor-core contraction (TF32X3 plans): levels >= tc_lmin, 0 = none
+    // tensor-core contraction (TF32X3 / TF32X1 / BF16X3 plans): levels >= tc_lmin, 0 = none
     int tc_lmin;
+    int tc_mode;                          // FMM_TC_*
     const void *tc_khi_map, *tc_klo_map;  // CUtensorMap of the split unit-cell kernels
     const float *tc_kbar;                 // [343][p3 padded to 32] row means
 };
@@ -225,10 +226,16 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
                     const DevTables<real> &T, const Streams &S, Tracer &tr);
 
 // tensor-core contraction (m2l_tc.cu)
+#define FMM_TC_TF32X3 0  // 3-pass split TF32
+#define FMM_TC_TF32X1 1  // 1-pass TF32
+#define FMM_TC_BF16X3 2  // 3-pass split BF16
 int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
-                  const void *k_lo_map, const float *kbar, int lmin, cudaStream_t st, Tracer &tr);
-int tc_encode_kernel_map(void *map, const float *base, int p3s);
-int tc_padded(int p3);
+                  const void *k_lo_map, const float *kbar, int lmin, int mode, cudaStream_t st,
+                  Tracer &tr);
+// map of a [343][p3s][pk] kernel table: fp32 (pk = p3s) or bf16 (pk = tc_padded_k)
+int tc_encode_kernel_map(void *map, const void *base, int p3s, int pk, int mode);
+int tc_padded(int p3);            // p^3 rounded up to 32 (MMA N, fp32 K)
+int tc_padded_k(int p3, int mode);  // K extent of a cell vector: 32 (fp32) or 64 (bf16) multiple
 size_t tc_map_bytes();
 
 // near field + far-field evaluation at the charges (kernels_p2p.cu)

@@ -1,5 +1,6 @@
 // Bilinear forms of the interaction lists (§2.2 step 3, eq. bilinear) on the
-// 5th-generation tensor cores (tcgen05), 3-pass split TF32.
+// 5th-generation tensor cores (tcgen05): 3-pass split TF32, 1-pass TF32 or
+// 3-pass split BF16, FP32 accumulation.
 //
 // For one level, one target parity and one box of 8x4x4 coarse cells (128
 // target cells = the MMA's M), every one of the 189 interaction-list offsets o
@@ -10,7 +11,11 @@
 // 128-byte K chunks, into a 2-stage ring; one thread issues the MMAs.
 //
 // Accuracy.  Split precision: x = hi + lo with hi = x with its 13 low mantissa
-// bits cleared (exact in TF32); D = Ahi Bhi + Ahi Blo + Alo Bhi.  The kernel
+// bits cleared (exact in TF32); D = Ahi Bhi + Ahi Blo + Alo Bhi.  The BF16
+// form splits x = hi + lo with hi = bf16(x), lo = bf16(x - hi) (both round to
+// nearest, 8 + 8 significant bits) and takes the same three products with
+// kind::f16 MMAs (K = 16 per MMA, 64 per 128-byte chunk).  The 1-pass TF32
+// form takes Ahi Bhi alone.  The kernel
 // is split as K_o = Kbar_o[a] + Kt_o[a,b] (row mean): the tensor cores contract
 // Kt_o, the CUDA cores add Kbar_o[a] Q (Q = the source cell's total charge).
 // Each offset accumulates into a fresh TMEM region (two regions, alternating):
@@ -20,6 +25,7 @@
 // ~1e-4).  For N > 64 the epilogue splits the columns over two warp groups.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 
 #include "fmm_internal.cuh"
 #include "tc_ptx.cuh"
@@ -74,12 +80,18 @@ __device__ __forceinline__ Off make_off(int bx, int by, int bz, int ox, int oy, 
     return f;
 }
 
-template <int N>
+#define TC_TF32X3 0
+#define TC_TF32X1 1
+#define TC_BF16X3 2
+
+template <int N, int MODE>
 struct TcShape {
     static constexpr int CH = N > 64 ? 2 : 1;           // epilogue column groups
     static constexpr int EPI = 4 * CH;                  // epilogue warps
     static constexpr int THREADS = 32 * (EPI + 2);      // + producer + MMA issuer
-    static constexpr int KC = N / 32;                   // 128-byte K chunks
+    static constexpr int KE = MODE == TC_BF16X3 ? 64 : 32;  // K elements per 128-byte chunk
+    static constexpr int KC = (N + KE - 1) / KE;        // 128-byte K chunks
+    static constexpr bool LO = MODE != TC_TF32X1;       // lo parts loaded and used
     static constexpr int BBYTES = N * 128;
     static constexpr int STAGE = 2 * TC_ABYTES + 2 * BBYTES;
     static constexpr int SMEM = TC_STAGES * STAGE + 1024 + 128;
@@ -88,10 +100,10 @@ struct TcShape {
     static constexpr int COLS = N / CH;                 // columns per epilogue thread
 };
 
-template <int N>
-__global__ void __launch_bounds__(TcShape<N>::THREADS, TcShape<N>::MINB)
+template <int N, int MODE>
+__global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::MINB)
     k_m2l_tc(const __grid_constant__ TcParams prm) {
-    typedef TcShape<N> Sh;
+    typedef TcShape<N, MODE> Sh;
     extern __shared__ unsigned char smraw[];
     const uint32_t raw = tc::smem_u32(smraw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -147,11 +159,14 @@ __global__ void __launch_bounds__(TcShape<N>::THREADS, TcShape<N>::MINB)
                 }
                 const uint32_t st = sbase + s * Sh::STAGE;
                 const uint32_t fb = full0 + 8 * s;
-                tc::mbar_expect_tx(fb, Sh::STAGE);
-                tc::tma_load_5d(st, &prm.phi_hi[l], fb, kc * 32, cX, cY, cZ, f.spar);
-                tc::tma_load_5d(st + TC_ABYTES, &prm.phi_lo[l], fb, kc * 32, cX, cY, cZ, f.spar);
-                tc::tma_load_3d(st + 2 * TC_ABYTES, &prm.k_hi, fb, kc * 32, 0, f.oi);
-                tc::tma_load_3d(st + 2 * TC_ABYTES + Sh::BBYTES, &prm.k_lo, fb, kc * 32, 0, f.oi);
+                const int kx = kc * Sh::KE;
+                tc::mbar_expect_tx(fb, Sh::LO ? Sh::STAGE : TC_ABYTES + Sh::BBYTES);
+                tc::tma_load_5d(st, &prm.phi_hi[l], fb, kx, cX, cY, cZ, f.spar);
+                tc::tma_load_3d(st + 2 * TC_ABYTES, &prm.k_hi, fb, kx, 0, f.oi);
+                if (Sh::LO) {
+                    tc::tma_load_5d(st + TC_ABYTES, &prm.phi_lo[l], fb, kx, cX, cY, cZ, f.spar);
+                    tc::tma_load_3d(st + 2 * TC_ABYTES + Sh::BBYTES, &prm.k_lo, fb, kx, 0, f.oi);
+                }
                 last_phase[s] = (int)ph;
             }
         }
@@ -163,7 +178,7 @@ __global__ void __launch_bounds__(TcShape<N>::THREADS, TcShape<N>::MINB)
         }
     } else if (warp == Sh::EPI + 1 && lane == 0) {
         // ---- MMA issuer: offset i accumulates into TMEM region i & 1 ----
-        const uint32_t idesc = tc::idesc_tf32(TC_M, N);
+        const uint32_t idesc = MODE == TC_BF16X3 ? tc::idesc_bf16(TC_M, N) : tc::idesc_tf32(TC_M, N);
         bool failed = false;
         for (int i = 0; i < TC_NOFF && !failed; i++) {
             const int r = i & 1;
@@ -184,14 +199,22 @@ __global__ void __launch_bounds__(TcShape<N>::THREADS, TcShape<N>::MINB)
                 tc::fence_after_sync();
                 const uint32_t st = sbase + s * Sh::STAGE;
 #pragma unroll
-                for (int k = 0; k < 4; k++) {  // K = 8 tf32 = 32 bytes per MMA
+                for (int k = 0; k < 4; k++) {  // 32 bytes of K per MMA (8 tf32 or 16 bf16)
                     const uint64_t ah = tc::desc_sw128(st + 32 * k);
                     const uint64_t al = tc::desc_sw128(st + TC_ABYTES + 32 * k);
                     const uint64_t bh = tc::desc_sw128(st + 2 * TC_ABYTES + 32 * k);
                     const uint64_t bl = tc::desc_sw128(st + 2 * TC_ABYTES + Sh::BBYTES + 32 * k);
-                    tc::mma_tf32(d, ah, bh, idesc, (kc | k) != 0);
-                    tc::mma_tf32(d, ah, bl, idesc, 1u);
-                    tc::mma_tf32(d, al, bh, idesc, 1u);
+                    if (MODE == TC_BF16X3) {
+                        tc::mma_bf16(d, ah, bh, idesc, (kc | k) != 0);
+                        tc::mma_bf16(d, ah, bl, idesc, 1u);
+                        tc::mma_bf16(d, al, bh, idesc, 1u);
+                    } else {
+                        tc::mma_tf32(d, ah, bh, idesc, (kc | k) != 0);
+                        if (MODE == TC_TF32X3) {
+                            tc::mma_tf32(d, ah, bl, idesc, 1u);
+                            tc::mma_tf32(d, al, bh, idesc, 1u);
+                        }
+                    }
                 }
                 tc::mma_commit(empty0 + 8 * s);
             }
@@ -260,18 +283,37 @@ __global__ void __launch_bounds__(TcShape<N>::THREADS, TcShape<N>::MINB)
 }
 
 // hi = x with the 13 low mantissa bits cleared (exact in TF32), lo = x - hi,
-// from cell vectors of p3 values to cell vectors of p3s (zero padded)
+// from cell vectors of p3 values to cell vectors of p3s (zero padded).  With
+// `nearest` (the 1-pass form, which has no lo term) hi is x rounded to the
+// nearest TF32 value (ties away from zero) instead of truncated.
 __global__ void k_split_tf32(const float *__restrict__ x, float *__restrict__ hi,
-                             float *__restrict__ lo, int64_t ncells, int p3, int p3s) {
+                             float *__restrict__ lo, int64_t ncells, int p3, int p3s, int nearest) {
     const int64_t n = ncells * p3s;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = i / p3s;
         const int b = (int)(i - c * p3s);
         float v = b < p3 ? x[c * p3 + b] : 0.0f;
-        float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        const uint32_t u = __float_as_uint(v) + (nearest ? 0x1000u : 0u);
+        float h = __uint_as_float(u & 0xFFFFE000u);
         hi[i] = h;
         lo[i] = v - h;
+    }
+}
+
+// hi = bf16(x), lo = bf16(x - hi), both rounded to nearest even; cell vectors
+// of p3 values to cell vectors of p3k bf16 values (zero padded, p3k % 64 == 0)
+__global__ void k_split_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ hi,
+                             __nv_bfloat16 *__restrict__ lo, int64_t ncells, int p3, int p3k) {
+    const int64_t n = ncells * p3k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / p3k;
+        const int b = (int)(i - c * p3k);
+        float v = b < p3 ? x[c * p3 + b] : 0.0f;
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[i] = h;
+        lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
 }
 
@@ -292,69 +334,102 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 int tc_padded(int p3) { return (p3 + 31) / 32 * 32; }
+int tc_padded_k(int p3, int mode) {
+    return mode == FMM_TC_BF16X3 ? (p3 + 63) / 64 * 64 : tc_padded(p3);
+}
 
-// Grid-charge box map of level l: dims (p3s b, P x, P y, P z, 8 parity), box (32, 8, 4, 4, 1).
-static int encode_phi_map(CUtensorMap *m, const float *base, int l, int p3s) {
+// Grid-charge box map of level l: dims (pk b, P x, P y, P z, 8 parity), box (one
+// 128-byte chunk of b, 8, 4, 4, 1); fp32 (pk = p3s) or bf16 (pk = p3k) elements.
+static int encode_phi_map(CUtensorMap *m, const void *base, int l, int pk, bool bf16) {
     auto enc = encode_fn();
     if (!enc) return FMM_ERR_CUDA;
-    const cuuint64_t P = ((cuuint64_t)1 << (l - 1)) + 2, rb = (cuuint64_t)p3s * 4;
-    cuuint64_t dims[5] = {(cuuint64_t)p3s, P, P, P, 8};
+    const cuuint64_t es_b = bf16 ? 2 : 4;
+    const cuuint64_t P = ((cuuint64_t)1 << (l - 1)) + 2, rb = (cuuint64_t)pk * es_b;
+    cuuint64_t dims[5] = {(cuuint64_t)pk, P, P, P, 8};
     cuuint64_t strides[4] = {rb, rb * P, rb * P * P, rb * P * P * P};
-    cuuint32_t box[5] = {32, 8, 4, 4, 1};
+    cuuint32_t box[5] = {(cuuint32_t)(128 / es_b), 8, 4, 4, 1};
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void *)base, dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5,
+                     (void *)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? FMM_OK : FMM_ERR_CUDA;
 }
 
-// Kernel-table map: dims (p3s b, p3s a, 343 offsets), box (32, p3s, 1).
-int tc_encode_kernel_map(void *map, const float *base, int p3s) {
+// Kernel-table map: dims (pk b, p3s a, 343 offsets), box (one 128-byte chunk of b,
+// p3s, 1); fp32 tables have pk = p3s, bf16 tables pk = p3k.
+int tc_encode_kernel_map(void *map, const void *base, int p3s, int pk, int mode) {
     auto enc = encode_fn();
     if (!enc) return FMM_ERR_CUDA;
-    const cuuint64_t n = (cuuint64_t)p3s;
-    cuuint64_t dims[3] = {n, n, 343};
-    cuuint64_t strides[2] = {n * 4, n * n * 4};
-    cuuint32_t box[3] = {32, (cuuint32_t)p3s, 1};
+    const bool bf16 = mode == FMM_TC_BF16X3;
+    const cuuint64_t es_b = bf16 ? 2 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)pk, (cuuint64_t)p3s, 343};
+    cuuint64_t strides[2] = {(cuuint64_t)pk * es_b, (cuuint64_t)pk * p3s * es_b};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / es_b), (cuuint32_t)p3s, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc((CUtensorMap *)map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims,
-                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc((CUtensorMap *)map,
+                     bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                     (void *)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? FMM_OK : FMM_ERR_CUDA;
 }
 
 size_t tc_map_bytes() { return sizeof(CUtensorMap); }
 
-template <int N>
+template <int N, int MODE>
 static int launch_tc_kernel(const TcParams &prm, int blocks, cudaStream_t st) {
-    typedef TcShape<N> Sh;
+    typedef TcShape<N, MODE> Sh;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_m2l_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(k_m2l_tc<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Sh::SMEM) != cudaSuccess)
             return FMM_ERR_CUDA;
         attr = true;
     }
-    k_m2l_tc<N><<<blocks, Sh::THREADS, Sh::SMEM, st>>>(prm);
+    k_m2l_tc<N, MODE><<<blocks, Sh::THREADS, Sh::SMEM, st>>>(prm);
     return FMM_OK;
 }
 
+template <int MODE>
+static int launch_tc_mode(int p3s, const TcParams &prm, int blocks, cudaStream_t st) {
+    switch (p3s) {
+    case 32: return launch_tc_kernel<32, MODE>(prm, blocks, st);
+    case 64: return launch_tc_kernel<64, MODE>(prm, blocks, st);
+    case 128: return launch_tc_kernel<128, MODE>(prm, blocks, st);
+    case 224: return launch_tc_kernel<224, MODE>(prm, blocks, st);
+    default: return FMM_ERR_UNSUPPORTED;
+    }
+}
+
 int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
-                  const void *k_lo_map, const float *kbar, int lmin, cudaStream_t st, Tracer &tr) {
-    const int depth = g.depth, p3 = g.p3, p3s = tc_padded(p3);
-    // split the grid charges of levels lmin..depth into padded TF32 hi / lo parts
+                  const void *k_lo_map, const float *kbar, int lmin, int mode, cudaStream_t st,
+                  Tracer &tr) {
+    const int depth = g.depth, p3 = g.p3, p3s = tc_padded(p3), pk = tc_padded_k(p3, mode);
+    const bool bf16 = mode == FMM_TC_BF16X3;
+    // split the grid charges of levels lmin..depth into padded hi / lo parts
+    // (the bf16 parts are stored in the same buffers, pk <= 2 p3s)
     const int64_t c0 = W.phi_level[lmin] / p3, c1 = W.phi_level[depth + 1] / p3;
     tr.begin(FMM_STAGE_M2L);
-    k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi + W.phi_level[lmin], P.phihi + c0 * p3s,
-                                          P.philo + c0 * p3s, c1 - c0, p3, p3s);
+    __nv_bfloat16 *hi16 = reinterpret_cast<__nv_bfloat16 *>(P.phihi);
+    __nv_bfloat16 *lo16 = reinterpret_cast<__nv_bfloat16 *>(P.philo);
+    if (bf16)
+        k_split_bf16<<<152 * 8, 256, 0, st>>>(P.phi + W.phi_level[lmin], hi16 + c0 * pk, lo16 + c0 * pk,
+                                              c1 - c0, p3, pk);
+    else
+        k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi + W.phi_level[lmin], P.phihi + c0 * p3s,
+                                              P.philo + c0 * p3s, c1 - c0, p3, p3s,
+                                              mode == FMM_TC_TF32X1);
     tr.count();
     TcParams prm;
     memset(&prm, 0, sizeof(prm));
     int blocks = 0;
     for (int l = lmin; l <= depth; l++) {
         const int64_t cl = W.phi_level[l] / p3;  // first cell of level l
-        int rc = encode_phi_map(&prm.phi_hi[l], P.phihi + cl * p3s, l, p3s);
-        if (!rc) rc = encode_phi_map(&prm.phi_lo[l], P.philo + cl * p3s, l, p3s);
+        const void *bh = bf16 ? (const void *)(hi16 + cl * pk) : (const void *)(P.phihi + cl * p3s);
+        const void *bl = bf16 ? (const void *)(lo16 + cl * pk) : (const void *)(P.philo + cl * p3s);
+        int rc = encode_phi_map(&prm.phi_hi[l], bh, l, pk, bf16);
+        if (!rc) rc = encode_phi_map(&prm.phi_lo[l], bl, l, pk, bf16);
         if (rc) return rc;
         prm.first_block[l] = blocks;
         const int H = 1 << (l - 1);
@@ -372,14 +447,9 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
     prm.qlev = P.qlev;
     prm.kbar = kbar;
     prm.status = &P.hdr->status;
-    int rc;
-    switch (p3s) {
-    case 32: rc = launch_tc_kernel<32>(prm, blocks, st); break;
-    case 64: rc = launch_tc_kernel<64>(prm, blocks, st); break;
-    case 128: rc = launch_tc_kernel<128>(prm, blocks, st); break;
-    case 224: rc = launch_tc_kernel<224>(prm, blocks, st); break;
-    default: rc = FMM_ERR_UNSUPPORTED;
-    }
+    int rc = mode == FMM_TC_BF16X3   ? launch_tc_mode<TC_BF16X3>(p3s, prm, blocks, st)
+             : mode == FMM_TC_TF32X1 ? launch_tc_mode<TC_TF32X1>(p3s, prm, blocks, st)
+                                     : launch_tc_mode<TC_TF32X3>(p3s, prm, blocks, st);
     tr.count();
     tr.end();
     return rc;

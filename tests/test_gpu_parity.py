@@ -139,6 +139,32 @@ def test_parity_tf32x3(case):
     plan.close()
 
 
+# Other tensor-core forms.  The split BF16 form keeps 16 significant bits of
+# each operand (8 + 8); the dropped lo*lo product and the residual of the lo
+# parts bound each product's relative error by about 3 * 2^-17.  The 1-pass
+# TF32 form keeps 11 significant bits (round to nearest): about 2 * 2^-12 per
+# product, so it states its error rather than meeting the 1e-5 bar.
+TOL_TC_MODE = {"bf16x3": 1e-5, "tf32x1": 1e-3}
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x1"])
+@pytest.mark.parametrize("case", TF32_CASES, ids=[c[0] for c in TF32_CASES])
+def test_parity_tc_modes(case, precision):
+    """Far-field contraction on the tensor cores in split BF16 (kind::f16) and
+    1-pass TF32 forms against the FP64 oracle (sampled outputs)."""
+    name, gen, depth, p, periodic, cont = case
+    pos, q, box = gen()
+    n = len(q)
+    s = np.arange(0, n, max(1, n // 1500))
+    ref = oracle.fmm(pos, q, box, depth=depth, n=p, periodic=periodic, continuous=cont, sample=s)
+    plan, out = _gpu(pos, q, box, depth, p, periodic, cont, None, precision)
+    _check_integer_work(plan, ref)
+    tol = TOL_TC_MODE[precision]
+    assert _rel_l2(out["potential"][s], ref["phi"]) < tol
+    assert _rel_l2(out["forces"][s], ref["F"]) < tol
+    plan.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_paper_force_mode(precision):
     """The paper's force for split particles (sum of the forces their split
@@ -276,7 +302,8 @@ def test_forces_central_differences_fp64():
 @pytest.mark.parametrize("name,sample,precision", [("uniform1m", 512, "fp32"), ("water2m", 256, "fp32"),
                                                     ("uniform1m", 512, "tf32x3"),
                                                     ("water2m", 256, "tf32x3"),
-                                                    ("plummer8m", 256, "tf32x3")])
+                                                    ("plummer8m", 256, "tf32x3"),
+                                                    ("plummer8m", 256, "bf16x3")])
 def test_parity_full_size_sampled(name, sample, precision):
     """Full-size workloads in the benchmark's launch configuration: integer work
     on every charge, outputs on sampled particles (the oracle computes those one
@@ -289,7 +316,7 @@ def test_parity_full_size_sampled(name, sample, precision):
                      continuous=w["continuous"], sample=s)
     plan, out = _gpu(pos, q, box, w["depth"], w["p"], w["periodic"], w["continuous"], None, precision)
     _check_integer_work(plan, ref)
-    tol = TOL_FP32 if precision == "fp32" else TOL_TF32X3
+    tol = {"fp32": TOL_FP32, "tf32x3": TOL_TF32X3}.get(precision) or TOL_TC_MODE[precision]
     assert _rel_l2(out["potential"][s], ref["phi"]) < tol
     tol_F = max(tol, TOL_FP32_SPLIT_ADJOINT) if w["continuous"] else tol
     assert _rel_l2(out["forces"][s], ref["F"]) < tol_F
