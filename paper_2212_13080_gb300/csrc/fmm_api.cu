@@ -300,6 +300,7 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     W.s_pt = take(W.cap * 4 * rs);
     W.s_origin = take(W.cap * 4);
     W.out_pt = take(W.cap * 4 * rs);
+    W.react = take(13 * W.cap * 4 * rs);
     int64_t ph = 0, lc = 0;
     for (int l = 0; l <= P->depth; l++) {
         W.phi_level[l] = ph * p3;
@@ -365,6 +366,7 @@ Ptrs<real> make_ptrs(const WsLayout &W, void *ws) {
     P.s_pt = (R4 *)(b + W.s_pt);
     P.s_origin = (int *)(b + W.s_origin);
     P.out_pt = (R4 *)(b + W.out_pt);
+    P.react = (R4 *)(b + W.react);
     P.phi = (real *)(b + W.phi);
     P.loc = (real *)(b + W.loc);
     P.qlev = (real *)(b + W.qlev);

@@ -62,6 +62,7 @@ struct WsLayout {
     size_t leaf_count, leaf_start, cursor;
     size_t tmp, perm, inv;
     size_t s_pt, s_origin, out_pt;
+    size_t react;  // [13][cap] near-field reactions per forward direction (mutual near field)
     size_t phi, loc;                      // all levels
     size_t qlev;                          // total charge of every cell, padded Phi layout
     size_t phihi, philo;                  // TF32 split of Phi (tensor-core plans)
@@ -159,6 +160,7 @@ struct Ptrs {
     typename Vec4<real>::T *s_pt;
     int *s_origin;
     typename Vec4<real>::T *out_pt;
+    typename Vec4<real>::T *react;
     real *phi, *loc;
     real *qlev;
     real *phihi, *philo;

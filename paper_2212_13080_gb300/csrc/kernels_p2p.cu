@@ -2,8 +2,11 @@
 // cell and its 26 neighbours) and far field (§2.2 step 4 and the far-field force
 // at the end of §2.2).  Results per sorted charge, unit-box units:
 //   out_pt[slot] = (phi, F_x, F_y, F_z), phi per unit charge, F with the charge.
-// The near-field kernel writes out_pt, the far-field kernel adds to it: the
-// near field needs only the sorted charges and can run beside the far field.
+// The near-field kernel evaluates every pair of neighbouring cells once for
+// both partners (mutual form): it writes the target cell's own sums to out_pt
+// and the partners' reactions to one slot per direction; the far-field kernel
+// adds the slots in a fixed order and the far field.  The near field needs only
+// the sorted charges and runs beside the far field.
 #include "fmm_internal.cuh"
 #include "lagrange.cuh"
 
@@ -14,6 +17,32 @@ __device__ __forceinline__ double4 make_vec4(double a, double b, double c, doubl
     return make_double4(a, b, c, d);
 }
 
+// Near-field directions: index 13 + d of the 3x3x3 block (x fastest) for
+// d = 0..13, i.e. the cell itself (d = 0) and the 13 neighbours that come
+// after it in (z, y, x) order.  Every unordered pair of neighbouring cells
+// {A, A + delta_d} is evaluated once, by the CTA of A.
+#define NF_SEGS 14
+__host__ __device__ __forceinline__ void nf_delta(int d, int &dx, int &dy, int &dz) {
+    const int i = 13 + d;
+    dx = i % 3 - 1;
+    dy = (i / 3) % 3 - 1;
+    dz = i / 9 - 1;
+}
+// Cell reached from (cx, cy, cz) by (dx, dy, dz), wrapped (periodic) or -1
+// outside the box (open).
+__device__ __forceinline__ int64_t nf_cell(int cx, int cy, int cz, int dx, int dy, int dz, int S,
+                                           int periodic) {
+    int nx = cx + dx, ny = cy + dy, nz = cz + dz;
+    if (periodic) {
+        nx = (nx + S) % S;
+        ny = (ny + S) % S;
+        nz = (nz + S) % S;
+    } else if (nx < 0 || ny < 0 || nz < 0 || nx >= S || ny >= S || nz >= S) {
+        return -1;
+    }
+    return (int64_t)morton_encode(nx, ny, nz);
+}
+
 // ---------------------------------------------------------------------------
 // far field: phi_far = sum_ijk g_i(t_x) g_j(t_y) g_k(t_z) L_leaf[ijk] and
 // F_far = -q * 2^depth * grad_t phi_far.  One CTA per finest cell, L_leaf in
@@ -22,12 +51,17 @@ __device__ __forceinline__ double4 make_vec4(double a, double b, double c, doubl
 #define L2P_BS 64
 
 template <typename real, int P, bool FORCES>
-__global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, const int *__restrict__ leaf_start,
+__global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int periodic,
+                                                const int *__restrict__ leaf_start,
                                                 const typename Vec4<real>::T *__restrict__ s_pt,
                                                 const real *__restrict__ loc_leaf,
+                                                const typename Vec4<real>::T *__restrict__ react,
+                                                int64_t rstride,
                                                 typename Vec4<real>::T *__restrict__ out_pt) {
+    typedef typename Vec4<real>::T real4;
     constexpr int P3 = P * P * P;
     __shared__ real Ls[P3];
+    __shared__ int slot_ok[NF_SEGS - 1];
     const uint32_t key = blockIdx.x;
     const int s0 = leaf_start[key], s1 = leaf_start[key + 1];
     if (s0 == s1) return;
@@ -35,6 +69,14 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, const i
     morton_decode(key, cx, cy, cz);
     const real *src = loc_leaf + loc_cell(depth, cx, cy, cz) * P3;
     for (int o = threadIdx.x; o < P3; o += blockDim.x) Ls[o] = src[o];
+    // slot d - 1 of this cell's charges was written by the cell (this cell -
+    // delta_d), d = 1..13, if it exists and holds charges
+    if (threadIdx.x < NF_SEGS - 1) {
+        int dx, dy, dz;
+        nf_delta(threadIdx.x + 1, dx, dy, dz);
+        const int64_t a = nf_cell(cx, cy, cz, -dx, -dy, -dz, 1 << depth, periodic);
+        slot_ok[threadIdx.x] = a >= 0 && leaf_start[a + 1] > leaf_start[a];
+    }
     __syncthreads();
     const real S = (real)(1 << depth);
     for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
@@ -76,7 +118,17 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, const i
                 fz += dz[k] * aw;
             }
         }
-        typename Vec4<real>::T o = out_pt[s];  // the near field is already there
+        // near field: own sums, then the reactions of the 13 slots in order
+        real4 o = out_pt[s];
+#pragma unroll
+        for (int d = 0; d < NF_SEGS - 1; d++) {
+            if (!slot_ok[d]) continue;
+            const real4 r = react[d * rstride + s];
+            o.x += r.x;
+            o.y += r.y;
+            o.z += r.z;
+            o.w += r.w;
+        }
         o.x += phi;
         o.y += -v.w * S * fx;
         o.z += -v.w * S * fy;
@@ -86,23 +138,33 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, const i
 }
 
 // ---------------------------------------------------------------------------
-// near field.  One CTA of 128 threads per target cell.  The charges of the 27
-// neighbour cells are staged in shared memory, shifted into the target cell's
-// frame (source t + neighbour offset), in chunks.  Every thread owns two
-// targets (one shared-memory source load serves two pairs); with T targets the
-// CTA runs G = 128 / ceil(T/2) thread groups over the same targets, each taking
-// every G-th source; the G partial sums are added in a fixed order.  Pairs of
-// charges of the same particle (split charges) and coincident pairs are
-// skipped.  Sums: blocks of up to 32 sources into a short partial, partials
-// into the total with Kahan compensation.
+// near field, mutual form.  One CTA of 128 threads per cell A.
+//
+// Forward phase: the source list is the charges of the 13 forward neighbours
+// A + delta_d (d = 1..13), shifted into A's frame (source t + delta_d).  Each
+// thread holds NF_KS sources in registers, with their reaction sums; A's
+// charges (targets) are read from shared memory by all threads at once.  Every
+// (target, source) pair is evaluated once and feeds both the target's sum
+// (per group of targets: transposed through shared memory and summed over the
+// warp's lanes in order, then over the four warps in order) and the source's
+// reaction.  Charges of different cells coincide only in the continuous form
+// with odd p, whose middle split charges sit on the cell plane (local
+// coordinate 1 below it, 0 above); otherwise the frame coordinates differ by
+// at least one ulp along an axis of delta_d.  So the pairs to skip are charges
+// of the same particle (split charges) and, with GUARD, coincident charges.
+//
+// Own phase: the pairs inside A, one-sided (each target against all of A's
+// charges), skipping charges of the same particle and coincident charges.
+//
+// Outputs: out_pt[A's charges] = A's own sums (assigned); react[d-1][j] = the
+// reaction on charge j of A + delta_d, written by this CTA alone; the far-field
+// kernel adds the 13 slots in order.  Large cells: sources in passes of
+// 128 * NF_KS (the target sums accumulate in out_pt between passes), targets in
+// blocks of TB (256 in single precision, 64 in double: static shared memory).
 // ---------------------------------------------------------------------------
-template <typename real>
-__device__ __forceinline__ void kahan_add(real &sum, real &c, real x) {
-    real y = x - c;
-    real t = sum + y;
-    c = (t - sum) - y;
-    sum = t;
-}
+#define NF_BS 128
+#define NF_KS 4
+#define NF_TP 36  // row stride (words) of the per-warp transpose buffer
 
 // 1/sqrt(r2): single precision uses the SFU reciprocal square root directly
 // (r2 is never subnormal here: it is 0 or a squared distance of FP32 charges
@@ -115,182 +177,260 @@ template <> __device__ __forceinline__ float rsqrt_pair<float>(float x) {
 }
 template <> __device__ __forceinline__ double rsqrt_pair<double>(double x) { return 1.0 / sqrt(x); }
 
-template <typename real, bool FORCES>
-struct PairAcc {
-    real p, x, y, z;
-    __device__ __forceinline__ void zero() { p = x = y = z = 0; }
-    __device__ __forceinline__ void add(real tx, real ty, real tz, int to, const typename Vec4<real>::T &sv,
-                                        int so) {
-        real dx = tx - sv.x, dy = ty - sv.y, dz = tz - sv.z;
-        real r2 = dx * dx + dy * dy + dz * dz;
-        real ri = rsqrt_pair<real>(r2);
-        ri = (r2 > real(0) && so != to) ? ri : real(0);
-        real qr = sv.w * ri;
-        p += qr;
-        if (FORCES) {
-            real qr3 = qr * (ri * ri);
-            x += qr3 * dx;
-            y += qr3 * dy;
-            z += qr3 * dz;
+// One (target, source) pair of the forward phase: target sums (p, x, y, z) in
+// a, the source's reaction in r.  FIRST assigns a instead of adding.
+template <typename real, bool FORCES, bool GUARD, bool FIRST>
+__device__ __forceinline__ void nf_pair(const typename Vec4<real>::T &tv, int to, real sx, real sy, real sz,
+                                        real sq, int so, real *a, real &rp, real &rx, real &ry, real &rz) {
+    const real dx = tv.x - sx, dy = tv.y - sy, dz = tv.z - sz;
+    const real r2 = dx * dx + dy * dy + dz * dz;
+    real ri = rsqrt_pair<real>(r2);
+    ri = (so != to && (!GUARD || r2 > real(0))) ? ri : real(0);
+    if (FIRST) a[0] = sq * ri; else a[0] += sq * ri;
+    rp += tv.w * ri;
+    if (FORCES) {
+        const real ri3 = ri * ri * ri;
+        const real as = sq * ri3, bt = tv.w * ri3;
+        if (FIRST) {
+            a[1] = as * dx;
+            a[2] = as * dy;
+            a[3] = as * dz;
+        } else {
+            a[1] += as * dx;
+            a[2] += as * dy;
+            a[3] += as * dz;
         }
+        rx -= bt * dx;
+        ry -= bt * dy;
+        rz -= bt * dz;
     }
-};
+}
 
-#define P2P_BS 128
-#define P2P_CHUNK 1024
-
-template <typename real, bool FORCES>
-__global__ void __launch_bounds__(P2P_BS) k_p2p(int depth, int periodic, const int *__restrict__ leaf_start,
-                                                const typename Vec4<real>::T *__restrict__ s_pt,
-                                                const int *__restrict__ s_origin,
-                                                typename Vec4<real>::T *__restrict__ out_pt) {
+template <typename real, bool FORCES, bool GUARD>
+__global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const int *__restrict__ leaf_start,
+                                               const typename Vec4<real>::T *__restrict__ s_pt,
+                                               const int *__restrict__ s_origin,
+                                               typename Vec4<real>::T *__restrict__ out_pt,
+                                               typename Vec4<real>::T *__restrict__ react,
+                                               int64_t rstride) {
     typedef typename Vec4<real>::T real4;
-    __shared__ real4 src[P2P_CHUNK];
-    __shared__ int srco[P2P_CHUNK];
-    __shared__ int nb_start[27], nb_off[28];
-    __shared__ real4 part[2 * P2P_BS];
+    constexpr int NC = FORCES ? 4 : 1;     // components per target
+    constexpr int TG = 32 / NC;            // targets per transposed group
+    constexpr int NW = NF_BS / 32;
+    constexpr int NF_TB = sizeof(real) == 8 ? 64 : 256;
+    __shared__ real4 tpos[NF_TB];
+    __shared__ int tori[NF_TB];
+    constexpr int WP = NF_TB * NC > 128 ? NF_TB * NC : 128;  // the own phase uses 128 per warp
+    __shared__ real wpart[NW][WP];
+    __shared__ __align__(16) real tbuf[NW][32 * NF_TP];
+    __shared__ int seg_start[NF_SEGS], seg_off[NF_SEGS];
 
     const uint32_t key = blockIdx.x;
-    const int t0 = leaf_start[key], t1 = leaf_start[key + 1];
-    const int T = t1 - t0;
+    const int t0 = leaf_start[key], T = leaf_start[key + 1] - t0;
     if (T == 0) return;
     const int S = 1 << depth;
     int cx, cy, cz;
     morton_decode(key, cx, cy, cz);
-    if (threadIdx.x < 27) {
-        int d = threadIdx.x;
-        int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-        int nx = cx + dx, ny = cy + dy, nz = cz + dz;
-        bool ok = true;
-        if (periodic) {
-            nx = (nx + S) % S;
-            ny = (ny + S) % S;
-            nz = (nz + S) % S;
-        } else {
-            ok = nx >= 0 && ny >= 0 && nz >= 0 && nx < S && ny < S && nz < S;
-        }
+    // forward segments d = 1..13 at [d - 1]
+    if (threadIdx.x < NF_SEGS - 1) {
+        int dx, dy, dz;
+        nf_delta(threadIdx.x + 1, dx, dy, dz);
+        const int64_t b = nf_cell(cx, cy, cz, dx, dy, dz, S, periodic);
         int st = 0, cnt = 0;
-        if (ok) {
-            uint32_t nk = morton_encode(nx, ny, nz);
-            st = leaf_start[nk];
-            cnt = leaf_start[nk + 1] - st;
+        if (b >= 0) {
+            st = leaf_start[b];
+            cnt = leaf_start[b + 1] - st;
         }
-        nb_start[d] = st;
-        nb_off[d + 1] = cnt;
+        seg_start[threadIdx.x] = st;
+        seg_off[threadIdx.x + 1] = cnt;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        nb_off[0] = 0;
-        for (int d = 0; d < 27; d++) nb_off[d + 1] += nb_off[d];
+        seg_off[0] = 0;
+        for (int d = 0; d < NF_SEGS - 1; d++) seg_off[d + 1] += seg_off[d];
     }
     __syncthreads();
-    const int Ns = nb_off[27];
-    // thread -> (slot, group); a slot owns targets tb + slot and tb + TPP + slot
-    int TPP, G;
-    if (T >= 2 * P2P_BS) {
-        TPP = P2P_BS;
-        G = 1;
-    } else {
-        TPP = (T + 1) / 2;
-        G = P2P_BS / TPP;
-    }
-    const int slot = threadIdx.x % TPP, grp = threadIdx.x / TPP;
-    const bool grp_ok = grp < G;
-    const bool single_chunk = Ns <= P2P_CHUNK;
-    bool staged = false;
-    const real S_r = (real)S;
+    const int Ns = seg_off[NF_SEGS - 1];
+    const int npass = (Ns + NF_BS * NF_KS - 1) / (NF_BS * NF_KS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const real Sr = (real)S;
+    real *tb_w = tbuf[warp];
 
-    for (int tb = 0; tb < T; tb += 2 * TPP) {
-        const int ta = tb + slot, tbb = tb + TPP + slot;
-        const bool act_a = grp_ok && ta < T, act_b = grp_ok && tbb < T;
-        real4 va, vb;
-        int oa = -1, ob = -1;
-        va.x = va.y = va.z = va.w = 0;
-        vb = va;
-        if (act_a) {
-            va = s_pt[t0 + ta];
-            oa = s_origin[t0 + ta];
+    // ---- forward phase (mutual) ----
+    for (int pass = 0; pass < npass; pass++) {
+        real sx[NF_KS], sy[NF_KS], sz[NF_KS], sq[NF_KS];
+        int so[NF_KS], sidx[NF_KS], sseg[NF_KS];
+        real rp[NF_KS], rx[NF_KS], ry[NF_KS], rz[NF_KS];
+#pragma unroll
+        for (int k = 0; k < NF_KS; k++) {
+            const int f = pass * NF_BS * NF_KS + k * NF_BS + threadIdx.x;
+            // an empty slot: far away, no charge, origin that matches no target
+            sx[k] = sy[k] = sz[k] = (real)(4 * S + 16);
+            sq[k] = 0;
+            so[k] = -1;
+            sidx[k] = -1;
+            sseg[k] = 0;
+            rp[k] = rx[k] = ry[k] = rz[k] = 0;
+            if (f < Ns) {
+                int d = 0;
+                while (f >= seg_off[d + 1]) d++;
+                const int j = seg_start[d] + (f - seg_off[d]);
+                int dx, dy, dz;
+                nf_delta(d + 1, dx, dy, dz);
+                const real4 v = s_pt[j];
+                sx[k] = v.x + (real)dx;
+                sy[k] = v.y + (real)dy;
+                sz[k] = v.z + (real)dz;
+                sq[k] = v.w;
+                so[k] = s_origin[j];
+                sidx[k] = j;
+                sseg[k] = d;
+            }
         }
-        if (act_b) {
-            vb = s_pt[t0 + tbb];
-            ob = s_origin[t0 + tbb];
+        for (int tb = 0; tb < T; tb += NF_TB) {
+            const int nt = min(NF_TB, T - tb);
+            __syncthreads();  // previous block's shared data consumed
+            // targets padded to a whole group with inert ones: far from every
+            // source, no charge, an origin no source has
+            const int ntp = (nt + TG - 1) / TG * TG;
+            for (int i = threadIdx.x; i < ntp; i += NF_BS) {
+                if (i < nt) {
+                    tpos[i] = s_pt[t0 + tb + i];
+                    tori[i] = s_origin[t0 + tb + i];
+                } else {
+                    const real far = -(real)(4 * S + 16);
+                    tpos[i] = make_vec4(far, far, far, real(0));
+                    tori[i] = -2;
+                }
+            }
+            __syncthreads();
+            for (int g0 = 0; g0 < nt; g0 += TG) {
+                real acc[32];
+#pragma unroll
+                for (int u = 0; u < TG; u++) {
+                    const real4 tv = tpos[g0 + u];
+                    const int to = tori[g0 + u];
+                    nf_pair<real, FORCES, GUARD, true>(tv, to, sx[0], sy[0], sz[0], sq[0], so[0], acc + u * NC,
+                                                       rp[0], rx[0], ry[0], rz[0]);
+#pragma unroll
+                    for (int k = 1; k < NF_KS; k++)
+                        nf_pair<real, FORCES, GUARD, false>(tv, to, sx[k], sy[k], sz[k], sq[k], so[k],
+                                                            acc + u * NC, rp[k], rx[k], ry[k], rz[k]);
+                }
+                // transpose through shared memory: lane l sums value l over the lanes in order
+                __syncwarp();
+#pragma unroll
+                for (int v = 0; v < 32; v += 4)
+                    *reinterpret_cast<real4 *>(tb_w + lane * NF_TP + v) = make_vec4(acc[v], acc[v + 1], acc[v + 2], acc[v + 3]);
+                __syncwarp();
+                real tot = tb_w[lane];
+#pragma unroll
+                for (int r = 1; r < 32; r++) tot += tb_w[r * NF_TP + lane];
+                if (g0 + lane / NC < nt) wpart[warp][(g0 + lane / NC) * NC + lane % NC] = tot;
+            }
+            __syncthreads();
+            // target sums: the warps in order, then accumulated over passes
+            for (int i = threadIdx.x; i < nt; i += NF_BS) {
+                real v[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int c = 0; c < NC; c++) {
+                    real t = wpart[0][i * NC + c];
+#pragma unroll
+                    for (int w = 1; w < NW; w++) t += wpart[w][i * NC + c];
+                    v[c] = t;
+                }
+                real4 &o = out_pt[t0 + tb + i];
+                if (pass > 0) {
+                    const real4 prev = o;
+                    v[0] += prev.x;
+                    v[1] += prev.y;
+                    v[2] += prev.z;
+                    v[3] += prev.w;
+                }
+                o = make_vec4(v[0], v[1], v[2], v[3]);
+            }
         }
-        PairAcc<real, FORCES> A, Bq, ca, cb;  // totals and Kahan compensations
-        A.zero();
-        Bq.zero();
-        ca.zero();
-        cb.zero();
-        for (int c0 = 0; c0 < Ns; c0 += P2P_CHUNK) {
-            const int cn = min(P2P_CHUNK, Ns - c0);
-            if (!(single_chunk && staged)) {
+        // reactions of this pass's sources, complete after all target blocks;
+        // unit-box units: 1/r_u = S/r_t, (x/r^3)_u = S^2 (x/r^3)_t
+#pragma unroll
+        for (int k = 0; k < NF_KS; k++) {
+            if (sidx[k] >= 0) {
+                const real qs = sq[k] * Sr * Sr;
+                react[sseg[k] * rstride + sidx[k]] = make_vec4(Sr * rp[k], qs * rx[k], qs * ry[k], qs * rz[k]);
+            }
+        }
+    }
+
+    // ---- own phase: pairs inside A, one-sided; a lane per target (chunks of
+    // 32), the warps take every fourth source; warp partials summed in order ----
+    real4 *spos = reinterpret_cast<real4 *>(&tbuf[0][0]);  // free after the forward phase
+    int *sori = reinterpret_cast<int *>(&tori[0]);
+    const bool once = T <= NF_TB;
+    for (int c0 = 0; c0 < T; c0 += 32) {
+        const int ti = c0 + lane;
+        const bool act = ti < T;
+        real4 tv = make_vec4(real(0), real(0), real(0), real(0));
+        int to = -3;
+        if (act) {
+            tv = s_pt[t0 + ti];
+            to = s_origin[t0 + ti];
+        }
+        real pa = 0, xa = 0, ya = 0, za = 0;
+        for (int sb = 0; sb < T; sb += NF_TB) {
+            const int ns = min(NF_TB, T - sb);
+            if (!(once && c0 > 0)) {
                 __syncthreads();
-                // neighbour by neighbour, one warp per neighbour cell
-                for (int d = warp; d < 27; d += P2P_BS / 32) {
-                    const int lo = max(nb_off[d], c0), hi = min(nb_off[d + 1], c0 + cn);
-                    const real ox = (real)(d % 3 - 1), oy = (real)((d / 3) % 3 - 1), oz = (real)(d / 9 - 1);
-                    for (int f = lo + lane; f < hi; f += 32) {
-                        const int sidx = nb_start[d] + f - nb_off[d];
-                        real4 v = s_pt[sidx];
-                        v.x += ox;
-                        v.y += oy;
-                        v.z += oz;
-                        src[f - c0] = v;
-                        srco[f - c0] = s_origin[sidx];
-                    }
+                for (int i = threadIdx.x; i < ns; i += NF_BS) {
+                    spos[i] = s_pt[t0 + sb + i];
+                    sori[i] = s_origin[t0 + sb + i];
                 }
                 __syncthreads();
-                staged = true;
             }
-            if (act_a) {
-                for (int sb = grp; sb < cn; sb += 32 * G) {
-                    const int se = min(cn, sb + 32 * G);
-                    PairAcc<real, FORCES> pa, pb;
-                    pa.zero();
-                    pb.zero();
+            if (act) {
 #pragma unroll 4
-                    for (int s = sb; s < se; s += G) {
-                        const real4 sv = src[s];
-                        const int so = srco[s];
-                        pa.add(va.x, va.y, va.z, oa, sv, so);
-                        pb.add(vb.x, vb.y, vb.z, ob, sv, so);
-                    }
-                    kahan_add(A.p, ca.p, pa.p);
-                    kahan_add(Bq.p, cb.p, pb.p);
+                for (int j = warp; j < ns; j += NW) {
+                    const real4 sv = spos[j];
+                    const real dx = tv.x - sv.x, dy = tv.y - sv.y, dz = tv.z - sv.z;
+                    const real r2 = dx * dx + dy * dy + dz * dz;
+                    real ri = rsqrt_pair<real>(r2);
+                    ri = (r2 > real(0) && sori[j] != to) ? ri : real(0);
+                    pa += sv.w * ri;
                     if (FORCES) {
-                        kahan_add(A.x, ca.x, pa.x);
-                        kahan_add(A.y, ca.y, pa.y);
-                        kahan_add(A.z, ca.z, pa.z);
-                        kahan_add(Bq.x, cb.x, pb.x);
-                        kahan_add(Bq.y, cb.y, pb.y);
-                        kahan_add(Bq.z, cb.z, pb.z);
+                        const real q3 = sv.w * ri * ri * ri;
+                        xa += q3 * dx;
+                        ya += q3 * dy;
+                        za += q3 * dz;
                     }
                 }
             }
         }
-        // fixed-order sum over the groups, then add to the far field
+        wpart[warp][lane * 4 + 0] = pa;
+        wpart[warp][lane * 4 + 1] = xa;
+        wpart[warp][lane * 4 + 2] = ya;
+        wpart[warp][lane * 4 + 3] = za;
         __syncthreads();
-        part[threadIdx.x] = make_vec4(A.p, A.x, A.y, A.z);
-        part[P2P_BS + threadIdx.x] = make_vec4(Bq.p, Bq.x, Bq.y, Bq.z);
-        __syncthreads();
-        for (int k = threadIdx.x; k < 2 * TPP; k += P2P_BS) {
-            const int half = k / TPP, sl = k % TPP;
-            const int tgt = tb + half * TPP + sl;
-            if (tgt >= T) continue;
-            real4 sum = part[half * P2P_BS + sl];
-            for (int g2 = 1; g2 < G; g2++) {
-                real4 o = part[half * P2P_BS + sl + g2 * TPP];
-                sum.x += o.x;
-                sum.y += o.y;
-                sum.z += o.z;
-                sum.w += o.w;
+        // A's own sums (forward phase + own pairs), scaled to unit-box units
+        if (threadIdx.x < 32 && act) {
+            real v[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                real t = wpart[0][lane * 4 + c];
+#pragma unroll
+                for (int w = 1; w < NW; w++) t += wpart[w][lane * 4 + c];
+                v[c] = t;
             }
-            // unit-box units: 1/r_u = S / r_t, (x/r^3)_u = S^2 (x/r^3)_t
-            const int si = t0 + tgt;
-            const real qt = s_pt[si].w;
-            out_pt[si] = make_vec4(S_r * sum.x, qt * S_r * S_r * sum.y, qt * S_r * S_r * sum.z,
-                                   qt * S_r * S_r * sum.w);
+            real4 &o = out_pt[t0 + ti];
+            if (npass > 0) {
+                const real4 prev = o;
+                v[0] += prev.x;
+                v[1] += prev.y;
+                v[2] += prev.z;
+                v[3] += prev.w;
+            }
+            const real qs = tv.w * Sr * Sr;
+            o = make_vec4(Sr * v[0], qs * v[1], qs * v[2], qs * v[3]);
         }
+        __syncthreads();
     }
 }
 
@@ -304,11 +444,13 @@ void launch_l2p(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const W
 #define CASE(PP)                                                                                 \
     case PP:                                                                                     \
         if (forces)                                                                              \
-            k_l2p<real, PP, true><<<ncell, L2P_BS, 0, st>>>(C, depth, P.leaf_start, P.s_pt,     \
-                                                           loc_leaf, P.out_pt);                 \
+            k_l2p<real, PP, true><<<ncell, L2P_BS, 0, st>>>(C, depth, g.periodic, P.leaf_start,  \
+                                                           P.s_pt, loc_leaf, P.react, W.cap,    \
+                                                           P.out_pt);                           \
         else                                                                                     \
-            k_l2p<real, PP, false><<<ncell, L2P_BS, 0, st>>>(C, depth, P.leaf_start, P.s_pt,    \
-                                                            loc_leaf, P.out_pt);                \
+            k_l2p<real, PP, false><<<ncell, L2P_BS, 0, st>>>(C, depth, g.periodic, P.leaf_start, \
+                                                            P.s_pt, loc_leaf, P.react, W.cap,   \
+                                                            P.out_pt);                          \
         break;
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
@@ -322,12 +464,19 @@ void launch_p2p(const Geom &g, const Ptrs<real> &P, const WsLayout &W, bool forc
                 cudaStream_t st, Tracer &tr) {
     const int ncell = (int)W.ncell, depth = g.depth;
     tr.begin(FMM_STAGE_P2P, st);
-    if (forces)
-        k_p2p<real, true><<<ncell, P2P_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt,
-                                                    P.s_origin, P.out_pt);
-    else
-        k_p2p<real, false><<<ncell, P2P_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt,
-                                                     P.s_origin, P.out_pt);
+    // charges of different cells can coincide only on split planes with odd p
+    const bool guard = g.continuous && (g.p & 1);
+#define LAUNCH(F, G)                                                                               \
+    k_p2p<real, F, G><<<ncell, NF_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt, P.s_origin, \
+                                               P.out_pt, P.react, W.cap)
+    if (forces) {
+        if (guard) LAUNCH(true, true);
+        else LAUNCH(true, false);
+    } else {
+        if (guard) LAUNCH(false, true);
+        else LAUNCH(false, false);
+    }
+#undef LAUNCH
     tr.count();
     tr.end();
 }

@@ -232,6 +232,32 @@ def test_edge_cases():
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_coincident_split_charges_across_cells(precision):
+    """Odd p, continuous form: the middle split charges of a particle sit on the
+    cell plane (local coordinate 1 in the lower cell, 0 in the upper one), so two
+    particles on either side of a plane with the same transverse coordinates
+    have coincident charges in different cells.  Those pairs are skipped like
+    every coincident pair (the oracle's rule); nothing may become infinite."""
+    rng = np.random.default_rng(23)
+    pos = rng.random((3000, 3)).astype(np.float32)
+    extra = np.array([[0.5 - 0.001, 0.3, 0.7], [0.5 + 0.002, 0.3, 0.7],
+                      [0.25 + 0.003, 0.61, 0.33], [0.25 - 0.001, 0.61, 0.33],
+                      [0.9, 0.375 - 0.002, 0.1], [0.9, 0.375 + 0.001, 0.1]], np.float32)
+    pos = np.concatenate([pos, extra])
+    q = rng.uniform(-1, 1, len(pos)).astype(np.float32)
+    box = (0.0, 0.0, 0.0, 1.0)
+    ref = oracle.fmm(pos, q, box, depth=3, n=5, continuous=True, dt=1 / 8)
+    plan, out = _gpu(pos, q, box, 3, 5, False, True, 1 / 8, precision)
+    _check_integer_work(plan, ref)
+    assert np.isfinite(out["potential"]).all() and np.isfinite(out["forces"]).all()
+    tol = TOL_FP64 if precision == "fp64" else TOL_FP32
+    tol_F = TOL_FP64 if precision == "fp64" else TOL_FP32_SPLIT_ADJOINT
+    assert _rel_l2(out["potential"], ref["phi"]) < tol
+    assert _rel_l2(out["forces"], ref["F"]) < tol_F
+    plan.close()
+
+
 def test_split_overflow_is_reported():
     # every particle near a corner: 64 charges each, capacity 2 per particle
     rng = np.random.default_rng(3)
