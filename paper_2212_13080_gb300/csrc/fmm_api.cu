@@ -29,7 +29,7 @@ struct fmm_plan_s {
     void *Ktc_hi, *Ktc_lo;  // [343][a][b] TF32 split of Kt, padded to 32 (TF32X3 plans)
     void *Kbar_tc;          // [343][a] row means, padded to 32
     alignas(64) unsigned char khi_map[128], klo_map[128];  // their TMA tensor maps
-    bool tc;                // bilinear forms of levels >= 4 on tensor cores
+    bool tc;                // bilinear forms of every level on tensor cores
     int tc_mode;            // FMM_TC_*: split TF32 x3, TF32 x1, split BF16 x3
     bool shared;            // tables belong to another plan (batched systems)
     Coef<float> cf;
@@ -334,8 +334,9 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     }
     W.m2l_part = take(part * rs);
     const size_t p3s = (size_t)tc_padded(p3);
-    W.phihi = take(P->tc ? (size_t)ph * p3s * rs : 0);
-    W.philo = take(P->tc ? (size_t)ph * p3s * rs : 0);
+    const size_t pht = (size_t)tc_level_first(P->depth + 1);  // cells of the operand layout
+    W.phihi = take(P->tc ? pht * p3s * rs : 0);
+    W.philo = take(P->tc ? pht * p3s * rs : 0);
     int64_t mx = n > W.ncell ? n : W.ncell;
     W.scan_blocks = (int)(mx / 2048 + 2);
     W.scan_tmp = take((size_t)(W.scan_blocks + 1) * 4);
@@ -447,7 +448,7 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     T.Kbar = (const real *)P->Kbar;
     T.Klt = (const real *)P->Klat;
     T.Klbar = (const real *)P->Klbar;
-    T.tc_lmin = P->tc ? 4 : 0;
+    T.tc_lmin = P->tc ? (P->periodic ? 1 : 2) : 0;  // every level on the tensor cores
     T.tc_mode = P->tc_mode;
     T.tc_khi_map = P->khi_map;
     T.tc_klo_map = P->klo_map;

@@ -46,6 +46,9 @@ struct WsHeader {
     int n_coinc;      // coincident pairs skipped in the near field
     int valid;        // 0 until an evaluation completed
     long long tag;    // plan id and n of the last evaluation
+    // first bounded wait that gave up: site (1 producer slot, 2 MMA region,
+    // 3 MMA operands, 4 epilogue region), block, level, iteration
+    int wait_site, wait_block, wait_level, wait_iter;
 };
 
 // device-side status bits
@@ -109,6 +112,25 @@ __host__ __device__ inline int64_t phi_level_cells(int l) {
     int64_t P = ((int64_t)1 << (l - 1)) + 2;
     return 8 * P * P * P;
 }
+// Tensor-core operand layout of the grid charges (split hi / lo copies): the
+// padded parity-major layout with at least 10 cells per axis, so that every
+// 8 x 4 x 4 box the contraction loads (starting at coarse coordinate 0..2)
+// lies inside the grid; cells beyond the padded layout hold zeros.
+__host__ __device__ inline int64_t tc_level_extent(int l) {
+    int64_t P = ((int64_t)1 << (l - 1)) + 2;
+    return P < 10 ? 10 : P;
+}
+__host__ __device__ inline int64_t tc_level_cells(int l) {
+    if (l == 0) return 1;
+    int64_t Pt = tc_level_extent(l);
+    return 8 * Pt * Pt * Pt;
+}
+__host__ __device__ inline int64_t tc_level_first(int l) {  // cells before level l
+    int64_t c = 0;
+    for (int k = 0; k < l; k++) c += tc_level_cells(k);
+    return c;
+}
+
 // cell of level l >= 1 in the unpadded L layout
 __host__ __device__ inline int64_t loc_cell(int l, int cx, int cy, int cz) {
     if (l == 0) return 0;

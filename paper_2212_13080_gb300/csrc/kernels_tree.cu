@@ -143,17 +143,34 @@ __global__ void k_split_count(Geom g, int n, const float *__restrict__ pos, int 
     if (st) atomicOr(&hdr->status, st);
 }
 
-// Emits every particle's charges (particle order; per particle the tensor
-// product of its axes with x fastest), with Morton key, (t, q_eff), (W, dW/du)
-// and origin, and counts the charges of every finest cell.
+// Marks every charge of a fully emitted particle with the particle's index
+// (continuous form).  The charges of particle i are [offset[i], offset[i] +
+// count[i]); the emitted particles are the prefix with offset[i+1] <= n_eff.
+__global__ void k_mark(int n, const int *__restrict__ offset, const int *__restrict__ count,
+                       const WsHeader *hdr, int *__restrict__ e_origin) {
+    const int ne = hdr->n_eff;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int e0 = offset[i], m = count[i];
+        if (e0 + m > ne) continue;
+        for (int k = 0; k < m; k++) e_origin[e0 + k] = i;
+    }
+}
+
+// Emits the charges, one thread per charge (no divergence on split
+// particles): charge e is entry k = e - offset[i] of particle i, the tensor
+// product of its axes with x fastest.  Writes the Morton key, (t, q_eff),
+// (W, dW/du) and origin, and counts the charges of every finest cell.
 template <typename real>
 __global__ void k_emit(Geom g, Coef<real> C, int n, const float *__restrict__ pos,
-                       const float *__restrict__ q, const int *__restrict__ offset, int cap,
+                       const float *__restrict__ q, const int *__restrict__ offset,
                        uint32_t *__restrict__ e_key, typename Vec4<real>::T *__restrict__ e_pt,
                        typename Vec4<real>::T *__restrict__ e_wd, int *__restrict__ e_origin,
                        int *__restrict__ leaf_count, WsHeader *hdr) {
     int st = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int ne = offset ? hdr->n_eff : n;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+        const int i = offset ? e_origin[e] : e;
+        int k = offset ? e - offset[i] : 0;
         AxisInfo A[3];
         for (int a = 0; a < 3; a++) {
             float t;
@@ -161,47 +178,33 @@ __global__ void k_emit(Geom g, Coef<real> C, int n, const float *__restrict__ po
             bin_axis(g, pos[3 * i + a], a, t, c, st);
             A[a] = split_axis_info(g, c, t);
         }
-        const real qi = (real)q[i];
-        int e = offset ? offset[i] : i;
-        if (offset && e + A[0].m * A[1].m * A[2].m > cap) {
-            st |= ST_SPLIT_OVERFLOW;
-            continue;
+        const int ex = k % A[0].m;
+        k /= A[0].m;
+        const int ey = k % A[1].m, ez = k / A[1].m;
+        int cx, cy, cz;
+        real tx, ty, tz, wx, wy, wz, dwx, dwy, dwz;
+        split_entry(g, C, A[0], ex, cx, tx, wx, dwx);
+        split_entry(g, C, A[1], ey, cy, ty, wy, dwy);
+        split_entry(g, C, A[2], ez, cz, tz, wz, dwz);
+        const real W = wx * wy * wz;
+        const uint32_t key = morton_encode(cx, cy, cz);
+        e_key[e] = key;
+        typename Vec4<real>::T v;
+        v.x = tx;
+        v.y = ty;
+        v.z = tz;
+        v.w = (real)q[i] * W;
+        e_pt[e] = v;
+        if (e_wd) {
+            typename Vec4<real>::T d;
+            d.x = W;
+            d.y = dwx * wy * wz;
+            d.z = wx * dwy * wz;
+            d.w = wx * wy * dwz;
+            e_wd[e] = d;
         }
-        for (int ez = 0; ez < A[2].m; ez++) {
-            int cz;
-            real tz, wz, dwz;
-            split_entry(g, C, A[2], ez, cz, tz, wz, dwz);
-            for (int ey = 0; ey < A[1].m; ey++) {
-                int cy;
-                real ty, wy, dwy;
-                split_entry(g, C, A[1], ey, cy, ty, wy, dwy);
-                for (int ex = 0; ex < A[0].m; ex++) {
-                    int cx;
-                    real tx, wx, dwx;
-                    split_entry(g, C, A[0], ex, cx, tx, wx, dwx);
-                    real W = wx * wy * wz;
-                    uint32_t key = morton_encode(cx, cy, cz);
-                    e_key[e] = key;
-                    typename Vec4<real>::T v;
-                    v.x = tx;
-                    v.y = ty;
-                    v.z = tz;
-                    v.w = qi * W;
-                    e_pt[e] = v;
-                    if (e_wd) {
-                        typename Vec4<real>::T d;
-                        d.x = W;
-                        d.y = dwx * wy * wz;
-                        d.z = wx * dwy * wz;
-                        d.w = wx * wy * dwz;
-                        e_wd[e] = d;
-                    }
-                    e_origin[e] = i;
-                    atomicAdd(&leaf_count[key], 1);
-                    e++;
-                }
-            }
-        }
+        if (!offset) e_origin[e] = i;
+        atomicAdd(&leaf_count[key], 1);
     }
     if (st) atomicOr(&hdr->status, st);
 }
@@ -332,11 +335,20 @@ void launch_bin_emit(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, co
         tr.count(1 + launch_scan(P.count, P.offset, n, P.scan_tmp, st));
         offset = P.offset;
     }
-    k_emit<real><<<nb, 256, 0, st>>>(g, C, n, pos, q, offset, (int)W.cap, P.e_key, P.e_pt,
-                                     g.continuous ? P.e_wd : nullptr, P.e_origin, P.leaf_count,
-                                     P.hdr);
     k_set_neff<<<1, 1, 0, st>>>(offset, n, P.hdr, (int)W.cap);
-    tr.count(2);
+    tr.count();
+    if (offset) {
+        k_mark<<<nb, 256, 0, st>>>(n, offset, P.count, P.hdr, P.e_origin);
+        tr.count();
+    }
+    int64_t ne_max = offset ? W.cap : n;
+    int nbe = (int)((ne_max + 255) / 256);
+    if (nbe < 1) nbe = 1;
+    if (nbe > 152 * 64) nbe = 152 * 64;
+    k_emit<real><<<nbe, 256, 0, st>>>(g, C, n, pos, q, offset, P.e_key, P.e_pt,
+                                      g.continuous ? P.e_wd : nullptr, P.e_origin, P.leaf_count,
+                                      P.hdr);
+    tr.count();
     tr.end();
 }
 

@@ -3,7 +3,8 @@
 // 3-pass split BF16, FP32 accumulation.
 //
 // For one level, one target parity and one box of 8x4x4 coarse cells (128
-// target cells = the MMA's M), every one of the 189 interaction-list offsets o
+// target cells = the MMA's M; the coarsest levels take one box partly outside
+// the grid), every one of the 189 interaction-list offsets o
 // contributes L[cell][a] += sum_b Phi[cell + o][b] K_o[a][b]: a 128 x N x K
 // GEMM (N = K = p^3 padded to a multiple of 32) whose A operand (the 128
 // source vectors) is one rectangular box of the padded parity-major grid-charge
@@ -37,6 +38,17 @@ namespace fmm {
 #define TC_ABYTES (TC_M * 128)      // 128 rows x 32 fp32 (one K chunk)
 #define TC_WAIT_CYCLES (4LL << 30)  // about 2 s of SM clock
 #define TC_NOFF 189
+
+struct TcParams;
+// records the first wait of the launch that gave up (diagnostics in the header)
+__device__ __forceinline__ void tc_wait_failed(int *status, int site, int level, int iter) {
+    WsHeader *h = reinterpret_cast<WsHeader *>(status);
+    if (atomicCAS(&h->wait_site, 0, site) == 0) {
+        h->wait_block = blockIdx.x;
+        h->wait_level = level;
+        h->wait_iter = iter;
+    }
+}
 
 struct TcParams {
     CUtensorMap phi_hi[FMM_MAXDEPTH + 1];
@@ -120,7 +132,9 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
     while (l < prm.lmax && (int)blockIdx.x >= prm.first_block[l + 1]) l++;
     const int rel = blockIdx.x - prm.first_block[l];
     const int H = 1 << (l - 1), P = H + 2;
-    const int ntx = H / 8, nty = H / 4, ntz = H / 4;
+    // levels with fewer than 8 x 4 x 4 coarse cells per parity take one tile,
+    // partly outside the grid (those rows read the TMA fill and are not stored)
+    const int ntx = (H + 7) / 8, nty = (H + 3) / 4, ntz = (H + 3) / 4;
     const int ntiles = ntx * nty * ntz;
     const int par = rel / ntiles, tile = rel % ntiles;
     const int X0 = (tile % ntx) * 8, Y0 = ((tile / ntx) % nty) * 4, Z0 = (tile / (ntx * nty)) * 4;
@@ -154,6 +168,7 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
                 const int s = it % TC_STAGES;
                 const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
                 if (!tc::mbar_wait(empty0 + 8 * s, ph ^ 1u, TC_WAIT_CYCLES)) {
+                    tc_wait_failed(prm.status, 1, l, it);
                     failed = true;
                     break;
                 }
@@ -184,6 +199,7 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
             const int r = i & 1;
             const uint32_t u = (uint32_t)(i >> 1) & 1u;
             if (!tc::mbar_wait(rfree0 + 8 * r, u ^ 1u, TC_WAIT_CYCLES)) {
+                tc_wait_failed(prm.status, 2, l, i);
                 failed = true;
                 break;
             }
@@ -193,6 +209,7 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
                 const int s = it % TC_STAGES;
                 const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
                 if (!tc::mbar_wait(full0 + 8 * s, ph, TC_WAIT_CYCLES)) {
+                    tc_wait_failed(prm.status, 3, l, it);
                     failed = true;
                     break;
                 }
@@ -228,6 +245,7 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
         const int c0 = cgrp * Sh::COLS;
         const int row = sub * 32 + lane;
         const int tx = row & 7, ty = (row >> 3) & 3, tz = row >> 5;
+        const bool valid = X0 + tx < H && Y0 + ty < H && Z0 + tz < H;
         const float *q = prm.qlev + prm.q_off[l];
         float tot[Sh::COLS];
 #pragma unroll
@@ -237,12 +255,16 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
         for (int i = 0; i < TC_NOFF; i++) {
             next_offset(bx, by, bz, ox, oy, oz);
             const Off f = make_off(bx, by, bz, ox, oy, oz);
-            const float Qs = q[(((int64_t)f.spar * P + Z0 + tz + 1 + f.dZ) * P + Y0 + ty + 1 + f.dY) * P +
-                               X0 + tx + 1 + f.dX];
+            const float Qs = valid ? q[(((int64_t)f.spar * P + Z0 + tz + 1 + f.dZ) * P + Y0 + ty + 1 + f.dY) * P +
+                                       X0 + tx + 1 + f.dX]
+                                   : 0.0f;
             const float4 *kb = reinterpret_cast<const float4 *>(prm.kbar + (int64_t)f.oi * N + c0);
             const int r = i & 1;
             const uint32_t u = (uint32_t)(i >> 1) & 1u;
-            if (ok && !tc::mbar_wait(rfull0 + 8 * r, u, TC_WAIT_CYCLES)) ok = false;
+            if (ok && !tc::mbar_wait(rfull0 + 8 * r, u, TC_WAIT_CYCLES)) {
+                if (lane == 0) tc_wait_failed(prm.status, 4, l, i);
+                ok = false;
+            }
             tc::fence_after_sync();
             const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(r * N + c0);
 #pragma unroll
@@ -263,12 +285,14 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
         }
         const int cx = 2 * (X0 + tx) + bx, cy = 2 * (Y0 + ty) + by, cz = 2 * (Z0 + tz) + bz;
         const int p3 = prm.p3;
-        float *out = prm.loc + prm.loc_off[l] + loc_cell(l, cx, cy, cz) * p3 + c0;
+        float *out = prm.loc + prm.loc_off[l] + (valid ? loc_cell(l, cx, cy, cz) : 0) * p3 + c0;
         const float scale = (float)(1 << l);
         if (ok) {
+            if (valid) {
 #pragma unroll
-            for (int j = 0; j < Sh::COLS; j++)
-                if (c0 + j < p3) out[j] = scale * tot[j];
+                for (int j = 0; j < Sh::COLS; j++)
+                    if (c0 + j < p3) out[j] = scale * tot[j];
+            }
         } else if (lane == 0) {
             atomicOr(prm.status, ST_TIMEOUT);
         }
@@ -282,38 +306,63 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
     }
 }
 
-// hi = x with the 13 low mantissa bits cleared (exact in TF32), lo = x - hi,
-// from cell vectors of p3 values to cell vectors of p3s (zero padded).  With
-// `nearest` (the 1-pass form, which has no lo term) hi is x rounded to the
+// Levels lmin..lmax of the grid charges, remapped from the padded layout (P =
+// H + 2 per axis) into the operand layout (tc_level_extent per axis, zeros
+// outside) and split into hi / lo parts.  One element = one (cell, b) of the
+// operand layout.
+struct SplitLevels {
+    int lmin, lmax;
+    long long src[FMM_MAXDEPTH + 2];  // first value of level l in the padded layout
+    long long dst[FMM_MAXDEPTH + 2];  // first cell of level l in the operand layout
+};
+__device__ __forceinline__ bool split_source(const SplitLevels &L, int64_t c, int &l, int64_t &src_cell) {
+    l = L.lmin;
+    while (l < L.lmax && c >= L.dst[l + 1]) l++;
+    const int64_t r = c - L.dst[l];
+    const int64_t Pt = tc_level_extent(l), P = ((int64_t)1 << (l - 1)) + 2;
+    const int64_t x = r % Pt, y = (r / Pt) % Pt, z = (r / (Pt * Pt)) % Pt, par = r / (Pt * Pt * Pt);
+    if (x >= P || y >= P || z >= P) return false;
+    src_cell = ((par * P + z) * P + y) * P + x;
+    return true;
+}
+
+// TF32: hi = x with the 13 low mantissa bits cleared (exact in TF32), lo = x - hi;
+// with `nearest` (the 1-pass form, which has no lo term) hi is x rounded to the
 // nearest TF32 value (ties away from zero) instead of truncated.
-__global__ void k_split_tf32(const float *__restrict__ x, float *__restrict__ hi,
-                             float *__restrict__ lo, int64_t ncells, int p3, int p3s, int nearest) {
-    const int64_t n = ncells * p3s;
+__global__ void k_split_tf32(const float *__restrict__ phi, SplitLevels L, float *__restrict__ hi,
+                             float *__restrict__ lo, int p3, int p3s, int nearest) {
+    const int64_t c0 = L.dst[L.lmin], n = (L.dst[L.lmax + 1] - c0) * p3s;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = i / p3s;
-        const int b = (int)(i - c * p3s);
-        float v = b < p3 ? x[c * p3 + b] : 0.0f;
+        const int64_t c = c0 + i / p3s;
+        const int b = (int)(i % p3s);
+        int l;
+        int64_t sc;
+        float v = 0.0f;
+        if (b < p3 && split_source(L, c, l, sc)) v = phi[L.src[l] + sc * p3 + b];
         const uint32_t u = __float_as_uint(v) + (nearest ? 0x1000u : 0u);
         float h = __uint_as_float(u & 0xFFFFE000u);
-        hi[i] = h;
-        lo[i] = v - h;
+        hi[c * p3s + b] = h;
+        lo[c * p3s + b] = v - h;
     }
 }
 
-// hi = bf16(x), lo = bf16(x - hi), both rounded to nearest even; cell vectors
-// of p3 values to cell vectors of p3k bf16 values (zero padded, p3k % 64 == 0)
-__global__ void k_split_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ hi,
-                             __nv_bfloat16 *__restrict__ lo, int64_t ncells, int p3, int p3k) {
-    const int64_t n = ncells * p3k;
+// BF16: hi = bf16(x), lo = bf16(x - hi), both rounded to nearest even; cell
+// vectors of p3k values (zero padded, p3k % 64 == 0)
+__global__ void k_split_bf16(const float *__restrict__ phi, SplitLevels L, __nv_bfloat16 *__restrict__ hi,
+                             __nv_bfloat16 *__restrict__ lo, int p3, int p3k) {
+    const int64_t c0 = L.dst[L.lmin], n = (L.dst[L.lmax + 1] - c0) * p3k;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = i / p3k;
-        const int b = (int)(i - c * p3k);
-        float v = b < p3 ? x[c * p3 + b] : 0.0f;
+        const int64_t c = c0 + i / p3k;
+        const int b = (int)(i % p3k);
+        int l;
+        int64_t sc;
+        float v = 0.0f;
+        if (b < p3 && split_source(L, c, l, sc)) v = phi[L.src[l] + sc * p3 + b];
         __nv_bfloat16 h = __float2bfloat16_rn(v);
-        hi[i] = h;
-        lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+        hi[c * p3k + b] = h;
+        lo[c * p3k + b] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
 }
 
@@ -338,13 +387,14 @@ int tc_padded_k(int p3, int mode) {
     return mode == FMM_TC_BF16X3 ? (p3 + 63) / 64 * 64 : tc_padded(p3);
 }
 
-// Grid-charge box map of level l: dims (pk b, P x, P y, P z, 8 parity), box (one
-// 128-byte chunk of b, 8, 4, 4, 1); fp32 (pk = p3s) or bf16 (pk = p3k) elements.
+// Grid-charge box map of level l (operand layout): dims (pk b, Pt x, Pt y, Pt z,
+// 8 parity), box (one 128-byte chunk of b, 8, 4, 4, 1); fp32 (pk = p3s) or bf16
+// (pk = p3k) elements.  Every box the kernel loads lies inside the map.
 static int encode_phi_map(CUtensorMap *m, const void *base, int l, int pk, bool bf16) {
     auto enc = encode_fn();
     if (!enc) return FMM_ERR_CUDA;
     const cuuint64_t es_b = bf16 ? 2 : 4;
-    const cuuint64_t P = ((cuuint64_t)1 << (l - 1)) + 2, rb = (cuuint64_t)pk * es_b;
+    const cuuint64_t P = (cuuint64_t)tc_level_extent(l), rb = (cuuint64_t)pk * es_b;
     cuuint64_t dims[5] = {(cuuint64_t)pk, P, P, P, 8};
     cuuint64_t strides[4] = {rb, rb * P, rb * P * P, rb * P * P * P};
     cuuint32_t box[5] = {(cuuint32_t)(128 / es_b), 8, 4, 4, 1};
@@ -407,25 +457,29 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
                   Tracer &tr) {
     const int depth = g.depth, p3 = g.p3, p3s = tc_padded(p3), pk = tc_padded_k(p3, mode);
     const bool bf16 = mode == FMM_TC_BF16X3;
-    // split the grid charges of levels lmin..depth into padded hi / lo parts
-    // (the bf16 parts are stored in the same buffers, pk <= 2 p3s)
-    const int64_t c0 = W.phi_level[lmin] / p3, c1 = W.phi_level[depth + 1] / p3;
+    // the grid charges of levels lmin..depth in the operand layout, split into
+    // hi / lo parts (the bf16 parts are stored in the same buffers, pk <= 2 p3s)
+    SplitLevels SL;
+    memset(&SL, 0, sizeof(SL));
+    SL.lmin = lmin;
+    SL.lmax = depth;
+    for (int l = 0; l <= depth + 1; l++) {
+        SL.src[l] = l <= depth ? W.phi_level[l] : 0;
+        SL.dst[l] = tc_level_first(l);
+    }
     tr.begin(FMM_STAGE_M2L);
     __nv_bfloat16 *hi16 = reinterpret_cast<__nv_bfloat16 *>(P.phihi);
     __nv_bfloat16 *lo16 = reinterpret_cast<__nv_bfloat16 *>(P.philo);
     if (bf16)
-        k_split_bf16<<<152 * 8, 256, 0, st>>>(P.phi + W.phi_level[lmin], hi16 + c0 * pk, lo16 + c0 * pk,
-                                              c1 - c0, p3, pk);
+        k_split_bf16<<<152 * 8, 256, 0, st>>>(P.phi, SL, hi16, lo16, p3, pk);
     else
-        k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi + W.phi_level[lmin], P.phihi + c0 * p3s,
-                                              P.philo + c0 * p3s, c1 - c0, p3, p3s,
-                                              mode == FMM_TC_TF32X1);
+        k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi, SL, P.phihi, P.philo, p3, p3s, mode == FMM_TC_TF32X1);
     tr.count();
     TcParams prm;
     memset(&prm, 0, sizeof(prm));
     int blocks = 0;
     for (int l = lmin; l <= depth; l++) {
-        const int64_t cl = W.phi_level[l] / p3;  // first cell of level l
+        const int64_t cl = tc_level_first(l);  // first cell of level l (operand layout)
         const void *bh = bf16 ? (const void *)(hi16 + cl * pk) : (const void *)(P.phihi + cl * p3s);
         const void *bl = bf16 ? (const void *)(lo16 + cl * pk) : (const void *)(P.philo + cl * p3s);
         int rc = encode_phi_map(&prm.phi_hi[l], bh, l, pk, bf16);
@@ -433,7 +487,7 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
         if (rc) return rc;
         prm.first_block[l] = blocks;
         const int H = 1 << (l - 1);
-        blocks += 8 * (H / 8) * (H / 4) * (H / 4);
+        blocks += 8 * ((H + 7) / 8) * ((H + 3) / 4) * ((H + 3) / 4);
         prm.loc_off[l] = W.loc_level[l];
         prm.q_off[l] = W.q_level[l];
     }
