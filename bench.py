@@ -480,7 +480,8 @@ def main():
 
     # roofline of the dominant kernel stage
     hbm, bf16_burst, bf16_sust, peak_kind = _peaks()
-    dom = max(("m2l", "p2p"), key=lambda k: stage_ms.get(k, 0.0))
+    # the dominant kernel by its own (isolated) duration: in-step times overlap
+    dom = max(("m2l", "p2p"), key=lambda k: stage_ms_iso.get(k, 0.0))
     # TF32 dense = 1/2 of the bf16 rate (nominal 1.1 vs 2.25 PF/s); the burst figure
     # for millisecond steps, the sustained one once a step runs for 100 ms or more
     long_step = t_step >= 100.0

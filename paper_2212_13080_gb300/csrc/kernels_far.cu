@@ -11,7 +11,10 @@ namespace fmm {
 // ---------------------------------------------------------------------------
 // §2.2 step 2, eq. (ex66): Phi_leaf[i,j,k] = sum_l q_l g_i(t_x) g_j(t_y) g_k(t_z).
 // One CTA per finest cell.  A chunk of charges gets its 3p weights computed
-// into shared memory, then every thread accumulates its grid nodes.
+// into shared memory (x weights times the charge), then every thread
+// accumulates its grid nodes; with p^3 < 128 the CTA runs 128 / p^3 thread
+// groups over every G-th charge and adds their partials in a fixed order.  The
+// cell's total charge: a warp tree per chunk, chunks added with compensation.
 // ---------------------------------------------------------------------------
 #define P2M_BS 128
 #define P2M_CH 64
@@ -21,24 +24,27 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(Coef<real> C, int depth, const i
                                                 const typename Vec4<real>::T *__restrict__ s_pt,
                                                 real *__restrict__ phi_leaf, real *__restrict__ q_leaf) {
     constexpr int P3 = P * P * P;
+    constexpr int G = P3 >= P2M_BS ? 1 : P2M_BS / P3;  // thread groups over the charges
+    constexpr int NO = (P3 + P2M_BS - 1) / P2M_BS;     // nodes per thread (G == 1)
     __shared__ real wx[P2M_CH][P], wy[P2M_CH][P], wz[P2M_CH][P], wq[P2M_CH];
+    __shared__ real part[G > 1 ? P2M_BS : 1];
     const uint32_t key = blockIdx.x;
     int cx, cy, cz;
     morton_decode(key, cx, cy, cz);
     const int s0 = leaf_start[key], s1 = leaf_start[key + 1];
-    constexpr int NO = (P3 + P2M_BS - 1) / P2M_BS;
+    const int grp = G > 1 ? threadIdx.x / P3 : 0, node = G > 1 ? threadIdx.x % P3 : threadIdx.x;
     real acc[NO];
 #pragma unroll
     for (int r = 0; r < NO; r++) acc[r] = 0;
-    real Q = 0, Qc = 0;  // total charge of the cell (Kahan), thread 0
+    real Q = 0, Qc = 0;  // total charge of the cell (thread 0)
     for (int c0 = s0; c0 < s1; c0 += P2M_CH) {
-        int m = min(P2M_CH, s1 - c0);
+        const int m = min(P2M_CH, s1 - c0);
         if (threadIdx.x < m) {
             typename Vec4<real>::T v = s_pt[c0 + threadIdx.x];
             real g[FMM_MAXP];
             lag_weights(C, P, v.x, g);
 #pragma unroll
-            for (int i = 0; i < P; i++) wx[threadIdx.x][i] = g[i];
+            for (int i = 0; i < P; i++) wx[threadIdx.x][i] = v.w * g[i];
             lag_weights(C, P, v.y, g);
 #pragma unroll
             for (int i = 0; i < P; i++) wy[threadIdx.x][i] = g[i];
@@ -48,121 +54,183 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(Coef<real> C, int depth, const i
             wq[threadIdx.x] = v.w;
         }
         __syncthreads();
-        if (threadIdx.x == 0)
-            for (int t = 0; t < m; t++) {
-                real y = wq[t] - Qc, tt = Q + y;
+        if (threadIdx.x < 32) {
+            const int t = threadIdx.x;
+            real v = (t < m ? wq[t] : real(0)) + (t + 32 < m ? wq[t + 32] : real(0));
+            for (int o = 16; o >= 1; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (t == 0) {
+                real y = v - Qc, tt = Q + y;
                 Qc = (tt - Q) - y;
                 Q = tt;
             }
+        }
+        if (grp < G) {
 #pragma unroll
-        for (int r = 0; r < NO; r++) {
-            int o = threadIdx.x + r * P2M_BS;
-            if (o < P3) {
-                int i = o % P, j = (o / P) % P, k = o / (P * P);
-                real s = acc[r];
-                for (int t = 0; t < m; t++) s += wq[t] * wx[t][i] * wy[t][j] * wz[t][k];
-                acc[r] = s;
+            for (int r = 0; r < NO; r++) {
+                const int o = node + r * P2M_BS;
+                if (o < P3) {
+                    const int i = o % P, j = (o / P) % P, k = o / (P * P);
+                    real s = acc[r];
+                    for (int t = grp; t < m; t += G) s += wx[t][i] * wy[t][j] * wz[t][k];
+                    acc[r] = s;
+                }
             }
         }
         __syncthreads();
     }
     const int64_t cell = phi_cell(depth, cx, cy, cz);
     real *out = phi_leaf + cell * P3;
+    if (G > 1) {
+        part[threadIdx.x] = grp < G ? acc[0] : real(0);
+        __syncthreads();
+        if (threadIdx.x < P3) {
+            real s = part[threadIdx.x];
 #pragma unroll
-    for (int r = 0; r < NO; r++) {
-        int o = threadIdx.x + r * P2M_BS;
-        if (o < P3) out[o] = acc[r];
+            for (int gi = 1; gi < G; gi++) s += part[gi * P3 + threadIdx.x];
+            out[threadIdx.x] = s;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < NO; r++) {
+            const int o = node + r * P2M_BS;
+            if (o < P3) out[o] = acc[r];
+        }
     }
     if (threadIdx.x == 0) q_leaf[cell] = Q;
 }
 
 // ---------------------------------------------------------------------------
 // §2.2 step 2, eq. (threethree): Phi_parent = sum_h (G_hx (x) G_hy (x) G_hz) Phi_child_h
-// as three one-dimensional passes (x, y, z) over the 8 children in shared memory.
-// One CTA per parent; children of level l, parent of level l-1.
+// in the factored order: the x shift summed over the two x siblings (4 arrays),
+// then the y shift summed over y (2 arrays), then z (1): 14 p^4 multiply-adds.
+// One CTA per parent; children of level l, parent of level l-1.  p is a
+// compile-time constant; the shift matrices are staged in shared memory.
 // ---------------------------------------------------------------------------
 #define M2M_BS 128
 
-template <typename real>
-__global__ void __launch_bounds__(M2M_BS) k_m2m(Coef<real> C, int p, int l, const real *__restrict__ phi_child,
+template <typename real, int P>
+__global__ void __launch_bounds__(M2M_BS) k_m2m(Coef<real> C, int l, const real *__restrict__ phi_child,
                                                 real *__restrict__ phi_parent,
                                                 const real *__restrict__ q_child,
                                                 real *__restrict__ q_parent) {
+    constexpr int P3 = P * P * P, PP = P * P;
     extern __shared__ unsigned char smraw[];
-    real *A = reinterpret_cast<real *>(smraw);
-    const int p3 = p * p * p;
-    real *B = A + 8 * p3;
-    const int Hp = 1 << (l - 1);  // parents per axis
+    real *A = reinterpret_cast<real *>(smraw);  // [h][k][j][i]          8 p^3
+    real *B = A + 8 * P3;                       // [hz][hy][k][j][I]     4 p^3
+    real *D = B + 4 * P3;                       // [hz][k][J][I]         2 p^3
+    real *Gs = D + 2 * P3;                      // [h][J][i]             2 p^2
+    const int Hp = 1 << (l - 1);                // parents per axis
     const int pid = blockIdx.x;
     const int px = pid % Hp, py = (pid / Hp) % Hp, pz = pid / (Hp * Hp);
-    for (int e = threadIdx.x; e < 8 * p3; e += blockDim.x) {
-        int h = e / p3, o = e % p3;
-        int cx = 2 * px + (h & 1), cy = 2 * py + ((h >> 1) & 1), cz = 2 * pz + (h >> 2);
-        A[e] = phi_child[phi_cell(l, cx, cy, cz) * p3 + o];
+    for (int e = threadIdx.x; e < 2 * PP; e += M2M_BS) Gs[e] = C.G[e / PP][e % PP];
+    for (int e = threadIdx.x; e < 8 * P3; e += M2M_BS) {
+        const int h = e / P3, o = e % P3;
+        const int cx = 2 * px + (h & 1), cy = 2 * py + ((h >> 1) & 1), cz = 2 * pz + (h >> 2);
+        A[e] = phi_child[phi_cell(l, cx, cy, cz) * P3 + o];
     }
     __syncthreads();
-    // x pass: B[h][k][j][I] = sum_i G_hx[I][i] A[h][k][j][i]
-    for (int e = threadIdx.x; e < 8 * p3; e += blockDim.x) {
-        int h = e / p3, o = e % p3, I = o % p, row = o - I;
-        const real *G = C.G[h & 1];
+    for (int e = threadIdx.x; e < 4 * P3; e += M2M_BS) {
+        const int hyz = e / P3, o = e % P3, I = o % P, row = o - I;
         real s = 0;
-        for (int i = 0; i < p; i++) s += G[I * p + i] * A[h * p3 + row + i];
+#pragma unroll
+        for (int hx = 0; hx < 2; hx++) {
+            const real *a = A + (hx + 2 * hyz) * P3 + row;
+            const real *g = Gs + hx * PP + I * P;
+#pragma unroll
+            for (int i = 0; i < P; i++) s += g[i] * a[i];
+        }
         B[e] = s;
     }
     __syncthreads();
-    // y pass: A[h][k][J][I] = sum_j G_hy[J][j] B[h][k][j][I]
-    for (int e = threadIdx.x; e < 8 * p3; e += blockDim.x) {
-        int h = e / p3, o = e % p3, I = o % p, J = (o / p) % p, k = o / (p * p);
-        const real *G = C.G[(h >> 1) & 1];
+    for (int e = threadIdx.x; e < 2 * P3; e += M2M_BS) {
+        const int hz = e / P3, o = e % P3, I = o % P, J = (o / P) % P, k = o / PP;
         real s = 0;
-        for (int j = 0; j < p; j++) s += G[J * p + j] * B[h * p3 + (k * p + j) * p + I];
-        A[e] = s;
+#pragma unroll
+        for (int hy = 0; hy < 2; hy++) {
+            const real *b = B + (hy + 2 * hz) * P3 + k * PP + I;
+            const real *g = Gs + hy * PP + J * P;
+#pragma unroll
+            for (int j = 0; j < P; j++) s += g[j] * b[j * P];
+        }
+        D[e] = s;
     }
     __syncthreads();
-    // z pass and sum over the children
-    real *out = phi_parent + phi_cell(l - 1, px, py, pz) * p3;
-    for (int o = threadIdx.x; o < p3; o += blockDim.x) {
-        int IJ = o % (p * p), K = o / (p * p);
+    real *out = phi_parent + phi_cell(l - 1, px, py, pz) * P3;
+    for (int o = threadIdx.x; o < P3; o += M2M_BS) {
+        const int K = o / PP, IJ = o % PP;
         real s = 0;
-        for (int h = 0; h < 8; h++) {
-            const real *G = C.G[h >> 2];
-            for (int k = 0; k < p; k++) s += G[K * p + k] * A[h * p3 + k * p * p + IJ];
+#pragma unroll
+        for (int hz = 0; hz < 2; hz++) {
+            const real *d = D + hz * P3 + IJ;
+            const real *g = Gs + hz * PP + K * P;
+#pragma unroll
+            for (int k = 0; k < P; k++) s += g[k] * d[k * PP];
         }
         out[o] = s;
     }
-    if (threadIdx.x == 0) {
-        real Q = 0;
-        for (int h = 0; h < 8; h++)
-            Q += q_child[phi_cell(l, 2 * px + (h & 1), 2 * py + ((h >> 1) & 1), 2 * pz + (h >> 2))];
-        q_parent[phi_cell(l - 1, px, py, pz)] = Q;
+    if (threadIdx.x < 32) {  // total charge: the eight children, tree order
+        real v = 0;
+        if (threadIdx.x < 8) {
+            const int h = threadIdx.x;
+            v = q_child[phi_cell(l, 2 * px + (h & 1), 2 * py + ((h >> 1) & 1), 2 * pz + (h >> 2))];
+        }
+        for (int m = 4; m >= 1; m >>= 1) v += __shfl_down_sync(0xffffffffu, v, m);
+        if (threadIdx.x == 0) q_parent[phi_cell(l - 1, px, py, pz)] = v;
     }
+}
+
+template <typename real, int P>
+constexpr size_t m2m_smem() {
+    return sizeof(real) * (14 * P * P * P + 2 * P * P);
 }
 
 // Halo of the padded Phi layout of level l >= 1: open form zeros; periodic form
 // the periodic image (coarse coordinate wrapped within the same parity block).
-template <typename real>
-__global__ void k_halo(int p3, int l, int periodic, real *__restrict__ phi_l, real *__restrict__ q_l) {
+// One warp per (parity, Z, Y) row of the padded grid: a row on the y/z shell is
+// all halo, any other row has its two x ends.
+__global__ void k_halo_rows(int p3, int l, int periodic, float *__restrict__ phi_f, double *__restrict__ phi_d,
+                            float *__restrict__ q_f, double *__restrict__ q_d) {
     const int H = 1 << (l - 1), P = H + 2;
-    const int64_t ncells = 8LL * P * P * P;
-    for (int64_t c = blockIdx.x; c < ncells; c += gridDim.x) {
-        int X = (int)(c % P), Y = (int)((c / P) % P), Z = (int)((c / ((int64_t)P * P)) % P);
-        int par = (int)(c / ((int64_t)P * P * P));
-        bool shell = X == 0 || Y == 0 || Z == 0 || X == P - 1 || Y == P - 1 || Z == P - 1;
-        if (!shell) continue;
-        real *dst = phi_l + c * p3;
-        if (!periodic) {
-            for (int o = threadIdx.x; o < p3; o += blockDim.x) dst[o] = 0;
-            if (threadIdx.x == 0) q_l[c] = 0;
-        } else {
-            int Xs = X == 0 ? H : (X == P - 1 ? 1 : X);
-            int Ys = Y == 0 ? H : (Y == P - 1 ? 1 : Y);
-            int Zs = Z == 0 ? H : (Z == P - 1 ? 1 : Z);
-            const int64_t sc = (((int64_t)par * P + Zs) * P + Ys) * P + Xs;
-            const real *src = phi_l + sc * p3;
-            for (int o = threadIdx.x; o < p3; o += blockDim.x) dst[o] = src[o];
-            if (threadIdx.x == 0) q_l[c] = q_l[sc];
+    const int64_t nrows = 8LL * P * P;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = w0; row < nrows; row += nw) {
+        const int Y = (int)(row % P), Z = (int)((row / P) % P);
+        const int par = (int)(row / ((int64_t)P * P));
+        const bool full = Y == 0 || Z == 0 || Y == P - 1 || Z == P - 1;
+        const int ncell = full ? P : 2;
+        for (int c = 0; c < ncell; c++) {
+            const int X = full ? c : (c == 0 ? 0 : P - 1);
+            const int64_t cell = ((int64_t)(par * P + Z) * P + Y) * P + X;
+            int64_t sc = -1;
+            if (periodic) {
+                const int Xs = X == 0 ? H : (X == P - 1 ? 1 : X);
+                const int Ys = Y == 0 ? H : (Y == P - 1 ? 1 : Y);
+                const int Zs = Z == 0 ? H : (Z == P - 1 ? 1 : Z);
+                sc = ((int64_t)(par * P + Zs) * P + Ys) * P + Xs;
+            }
+            if (phi_f) {
+                for (int o = lane; o < p3; o += 32) phi_f[cell * p3 + o] = sc >= 0 ? phi_f[sc * p3 + o] : 0.0f;
+                if (lane == 0) q_f[cell] = sc >= 0 ? q_f[sc] : 0.0f;
+            } else {
+                for (int o = lane; o < p3; o += 32) phi_d[cell * p3 + o] = sc >= 0 ? phi_d[sc * p3 + o] : 0.0;
+                if (lane == 0) q_d[cell] = sc >= 0 ? q_d[sc] : 0.0;
+            }
         }
     }
+}
+
+template <typename real>
+void launch_halo(int p3, int l, int periodic, real *phi_l, real *q_l, cudaStream_t st) {
+    const int P = (1 << (l - 1)) + 2;
+    const int64_t nrows = 8LL * P * P;
+    int blocks = (int)((nrows * 32 + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (std::is_same<real, float>::value)
+        k_halo_rows<<<blocks, 256, 0, st>>>(p3, l, periodic, (float *)phi_l, nullptr, (float *)q_l, nullptr);
+    else
+        k_halo_rows<<<blocks, 256, 0, st>>>(p3, l, periodic, nullptr, (double *)phi_l, nullptr, (double *)q_l);
 }
 
 // ---------------------------------------------------------------------------
@@ -341,47 +409,58 @@ __global__ void k_lattice(int p3, const real *__restrict__ Klt, const real *__re
 // One CTA per parent of level l-1; adds to the 8 children of level l (which
 // already hold their own interaction-list contributions).
 // ---------------------------------------------------------------------------
-template <typename real>
-__global__ void __launch_bounds__(M2M_BS) k_l2l(Coef<real> C, int p, int l, const real *__restrict__ loc_parent,
+template <typename real, int P>
+__global__ void __launch_bounds__(M2M_BS) k_l2l(Coef<real> C, int l, const real *__restrict__ loc_parent,
                                                 real *__restrict__ loc_child) {
+    constexpr int P3 = P * P * P, PP = P * P;
     extern __shared__ unsigned char smraw[];
-    real *Lp = reinterpret_cast<real *>(smraw);
-    const int p3 = p * p * p;
-    real *A = Lp + p3;       // [hz][k][J][I]      2 p3
-    real *B = A + 2 * p3;    // [hz][hy][k][j][I]  4 p3
+    real *Lp = reinterpret_cast<real *>(smraw);  // [K][J][I]             p^3
+    real *A = Lp + P3;                           // [hz][k][J][I]       2 p^3
+    real *B = A + 2 * P3;                        // [hz][hy][k][j][I]   4 p^3
+    real *Gs = B + 4 * P3;                       // [h][J][i]           2 p^2
     const int Hp = 1 << (l - 1);  // parents per axis (level l-1)
     const int pid = blockIdx.x;
     const int px = pid % Hp, py = (pid / Hp) % Hp, pz = pid / (Hp * Hp);
-    const real *src = loc_parent + loc_cell(l - 1, px, py, pz) * p3;
-    for (int o = threadIdx.x; o < p3; o += blockDim.x) Lp[o] = src[o];
+    const real *src = loc_parent + loc_cell(l - 1, px, py, pz) * P3;
+    for (int e = threadIdx.x; e < 2 * PP; e += M2M_BS) Gs[e] = C.G[e / PP][e % PP];
+    for (int o = threadIdx.x; o < P3; o += M2M_BS) Lp[o] = src[o];
     __syncthreads();
-    for (int e = threadIdx.x; e < 2 * p3; e += blockDim.x) {
-        int hz = e / p3, o = e % p3, IJ = o % (p * p), k = o / (p * p);
-        const real *G = C.G[hz];
+    for (int e = threadIdx.x; e < 2 * P3; e += M2M_BS) {
+        const int hz = e / P3, o = e % P3, IJ = o % PP, k = o / PP;
+        const real *g = Gs + hz * PP + k;
         real s = 0;
-        for (int K = 0; K < p; K++) s += G[K * p + k] * Lp[K * p * p + IJ];
+#pragma unroll
+        for (int K = 0; K < P; K++) s += g[K * P] * Lp[K * PP + IJ];
         A[e] = s;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 4 * p3; e += blockDim.x) {
-        int hh = e / p3, o = e % p3, I = o % p, j = (o / p) % p, k = o / (p * p);
-        int hz = hh >> 1, hy = hh & 1;
-        const real *G = C.G[hy];
+    for (int e = threadIdx.x; e < 4 * P3; e += M2M_BS) {
+        const int hh = e / P3, o = e % P3, I = o % P, j = (o / P) % P, k = o / PP;
+        const int hz = hh >> 1, hy = hh & 1;
+        const real *g = Gs + hy * PP + j;
+        const real *a = A + hz * P3 + k * PP + I;
         real s = 0;
-        for (int J = 0; J < p; J++) s += G[J * p + j] * A[hz * p3 + (k * p + J) * p + I];
+#pragma unroll
+        for (int J = 0; J < P; J++) s += g[J * P] * a[J * P];
         B[e] = s;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 8 * p3; e += blockDim.x) {
-        int h = e / p3, o = e % p3, i = o % p, row = o - i;
-        int hx = h & 1, hy = (h >> 1) & 1, hz = h >> 2;
-        const real *G = C.G[hx];
-        const real *b = B + ((hz << 1) | hy) * p3 + row;
+    for (int e = threadIdx.x; e < 8 * P3; e += M2M_BS) {
+        const int h = e / P3, o = e % P3, i = o % P, row = o - i;
+        const int hx = h & 1, hy = (h >> 1) & 1, hz = h >> 2;
+        const real *g = Gs + hx * PP + i;
+        const real *b = B + ((hz << 1) | hy) * P3 + row;
         real s = 0;
-        for (int I = 0; I < p; I++) s += G[I * p + i] * b[I];
-        int cx = 2 * px + hx, cy = 2 * py + hy, cz = 2 * pz + hz;
-        loc_child[loc_cell(l, cx, cy, cz) * p3 + o] += s;
+#pragma unroll
+        for (int I = 0; I < P; I++) s += g[I * P] * b[I];
+        const int cx = 2 * px + hx, cy = 2 * py + hy, cz = 2 * pz + hz;
+        loc_child[loc_cell(l, cx, cy, cz) * P3 + o] += s;
     }
+}
+
+template <typename real, int P>
+constexpr size_t l2l_smem() {
+    return sizeof(real) * (7 * P * P * P + 2 * P * P);
 }
 
 // ---------------------------------------------------------------------------
@@ -391,7 +470,7 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
     const int p = g.p, p3 = g.p3, depth = g.depth;
     real *phi_leaf = P.phi + W.phi_level[depth];
     const int ncell = (int)W.ncell;
-    tr.begin(FMM_STAGE_P2M);
+    tr.begin(FMM_STAGE_P2M, st);
     switch (p) {
 #define CASE(PP) \
     case PP:                                                                                     \
@@ -403,19 +482,23 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
     }
     tr.count();
     tr.end();
-    tr.begin(FMM_STAGE_M2M);
+    tr.begin(FMM_STAGE_M2M, st);
     const int lmin = g.periodic ? 0 : 2;
     for (int l = depth; l >= 1; l--) {
-        int blocks = (int)(phi_level_cells(l) < 4096 ? phi_level_cells(l) : 4096);
-        k_halo<real><<<blocks, 64, 0, st>>>(p3, l, g.periodic, P.phi + W.phi_level[l],
-                                            P.qlev + W.q_level[l]);
+        launch_halo<real>(p3, l, g.periodic, P.phi + W.phi_level[l], P.qlev + W.q_level[l], st);
         tr.count();
         if (l - 1 >= lmin) {
             int nparent = 1 << (3 * (l - 1));
-            size_t sm = sizeof(real) * 16 * p3;
-            k_m2m<real><<<nparent, M2M_BS, sm, st>>>(C, p, l, P.phi + W.phi_level[l],
-                                                     P.phi + W.phi_level[l - 1],
-                                                     P.qlev + W.q_level[l], P.qlev + W.q_level[l - 1]);
+            switch (p) {
+#define CASE(PP)                                                                                   \
+    case PP:                                                                                       \
+        k_m2m<real, PP><<<nparent, M2M_BS, m2m_smem<real, PP>(), st>>>(                            \
+            C, l, P.phi + W.phi_level[l], P.phi + W.phi_level[l - 1], P.qlev + W.q_level[l],       \
+            P.qlev + W.q_level[l - 1]);                                                            \
+        break;
+                CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+            }
             tr.count();
         }
     }
@@ -429,12 +512,11 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
     const int p = g.p, p3 = g.p3, depth = g.depth;
     const int achunks = (p3 + M2L_T - 1) / M2L_T;
     const size_t sm_m2l = sizeof(real) * (2 * M2L_T * M2L_T + 2 * M2L_T);
-    const size_t sm_l2l = sizeof(real) * 7 * p3;
     // 1. every level's own interaction-list contributions (they only need Phi):
     //    L_0 = lattice term (periodic), L_l = sum over the interaction list
     const int lstart = g.periodic ? 1 : 2;
     if (g.periodic) {
-        tr.begin(FMM_STAGE_M2L);
+        tr.begin(FMM_STAGE_M2L, st);
         k_lattice<real><<<1, 256, 0, st>>>(p3, T.Klt, T.Klbar, P.phi + W.phi_level[0],
                                            P.qlev + W.q_level[0], P.loc + W.loc_level[0]);
         tr.count();
@@ -478,9 +560,16 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
     // 2. downward: Psi_child = Psi_parent o shift, added level by level
     for (int l = g.periodic ? 1 : 3; l <= depth; l++) {
         int nparent = 1 << (3 * (l - 1));
-        tr.begin(FMM_STAGE_L2L);
-        k_l2l<real><<<nparent, M2M_BS, sm_l2l, st>>>(C, p, l, P.loc + W.loc_level[l - 1],
-                                                     P.loc + W.loc_level[l]);
+        tr.begin(FMM_STAGE_L2L, st);
+        switch (p) {
+#define CASE(PP)                                                                                   \
+    case PP:                                                                                       \
+        k_l2l<real, PP><<<nparent, M2M_BS, l2l_smem<real, PP>(), st>>>(                            \
+            C, l, P.loc + W.loc_level[l - 1], P.loc + W.loc_level[l]);                             \
+        break;
+            CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+        }
         tr.count();
         tr.end();
     }
@@ -489,10 +578,15 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
 
 void far_set_attributes() {
     cudaFuncSetAttribute(k_m2l_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 66 * 1024);
-    cudaFuncSetAttribute(k_m2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * 512 * 8);
-    cudaFuncSetAttribute(k_m2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * 512 * 4);
-    cudaFuncSetAttribute(k_l2l<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * 512 * 8);
-    cudaFuncSetAttribute(k_l2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * 512 * 4);
+#define ATTR(real, PP)                                                                             \
+    cudaFuncSetAttribute(k_m2m<real, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                         (int)m2m_smem<real, PP>());                                              \
+    cudaFuncSetAttribute(k_l2l<real, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                         (int)l2l_smem<real, PP>());
+    ATTR(float, 2) ATTR(float, 3) ATTR(float, 4) ATTR(float, 5) ATTR(float, 6) ATTR(float, 7)
+    ATTR(float, 8) ATTR(double, 2) ATTR(double, 3) ATTR(double, 4) ATTR(double, 5)
+    ATTR(double, 6) ATTR(double, 7) ATTR(double, 8)
+#undef ATTR
 }
 
 template void launch_upward<float>(const Geom &, const Coef<float> &, const Ptrs<float> &,

@@ -329,7 +329,7 @@ void launch_bin_emit(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, co
     if (nb < 1) nb = 1;
     if (nb > 152 * 64) nb = 152 * 64;
     const int *offset = nullptr;
-    tr.begin(FMM_STAGE_BIN);
+    tr.begin(FMM_STAGE_BIN, st);
     if (g.continuous) {
         k_split_count<<<nb, 256, 0, st>>>(g, n, pos, P.count, P.axes, P.hdr);
         tr.count(1 + launch_scan(P.count, P.offset, n, P.scan_tmp, st));
@@ -415,7 +415,7 @@ template <typename real>
 void launch_sort(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, cudaStream_t st,
                  Tracer &tr) {
     int ncell = (int)W.ncell;
-    tr.begin(FMM_STAGE_SORT);
+    tr.begin(FMM_STAGE_SORT, st);
     tr.count(launch_scan(P.leaf_count, P.leaf_start, ncell, P.scan_tmp, st));
     int nbp = (int)((W.cap + 255) / 256);
     if (nbp < 1) nbp = 1;
@@ -539,7 +539,7 @@ template <typename real>
 void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, const float *q,
                     real *potential, double *energy, real *forces, const double *grad_energy,
                     real *grad_q, bool backward, cudaStream_t st, Tracer &tr) {
-    tr.begin(FMM_STAGE_UNSPLIT);
+    tr.begin(FMM_STAGE_UNSPLIT, st);
     if (n == 0) {
         if (energy && !backward) {
             k_zero_energy<<<1, 1, 0, st>>>(energy);

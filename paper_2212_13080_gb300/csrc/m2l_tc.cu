@@ -318,51 +318,70 @@ struct SplitLevels {
 __device__ __forceinline__ bool split_source(const SplitLevels &L, int64_t c, int &l, int64_t &src_cell) {
     l = L.lmin;
     while (l < L.lmax && c >= L.dst[l + 1]) l++;
-    const int64_t r = c - L.dst[l];
-    const int64_t Pt = tc_level_extent(l), P = ((int64_t)1 << (l - 1)) + 2;
-    const int64_t x = r % Pt, y = (r / Pt) % Pt, z = (r / (Pt * Pt)) % Pt, par = r / (Pt * Pt * Pt);
+    const int r = (int)(c - L.dst[l]);  // < 8 * 130^3
+    const int Pt = (int)tc_level_extent(l), P = (1 << (l - 1)) + 2;
+    if (Pt == P) {  // levels with at least 8 coarse cells per axis: same layout
+        src_cell = r;
+        return true;
+    }
+    const int x = r % Pt, y = (r / Pt) % Pt, z = (r / (Pt * Pt)) % Pt, par = r / (Pt * Pt * Pt);
     if (x >= P || y >= P || z >= P) return false;
-    src_cell = ((par * P + z) * P + y) * P + x;
+    src_cell = ((int64_t)(par * P + z) * P + y) * P + x;
     return true;
 }
 
 // TF32: hi = x with the 13 low mantissa bits cleared (exact in TF32), lo = x - hi;
 // with `nearest` (the 1-pass form, which has no lo term) hi is x rounded to the
-// nearest TF32 value (ties away from zero) instead of truncated.
+// nearest TF32 value (ties away from zero) instead of truncated.  One thread per
+// 4 consecutive values of a cell (p3s % 32 == 0).
 __global__ void k_split_tf32(const float *__restrict__ phi, SplitLevels L, float *__restrict__ hi,
                              float *__restrict__ lo, int p3, int p3s, int nearest) {
-    const int64_t c0 = L.dst[L.lmin], n = (L.dst[L.lmax + 1] - c0) * p3s;
+    const int q4 = p3s / 4;
+    const int64_t c0 = L.dst[L.lmin], n = (L.dst[L.lmax + 1] - c0) * q4;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = c0 + i / p3s;
-        const int b = (int)(i % p3s);
+        const int64_t c = c0 + i / q4;
+        const int b0 = (int)(i % q4) * 4;
         int l;
         int64_t sc;
-        float v = 0.0f;
-        if (b < p3 && split_source(L, c, l, sc)) v = phi[L.src[l] + sc * p3 + b];
-        const uint32_t u = __float_as_uint(v) + (nearest ? 0x1000u : 0u);
-        float h = __uint_as_float(u & 0xFFFFE000u);
-        hi[c * p3s + b] = h;
-        lo[c * p3s + b] = v - h;
+        const bool in = split_source(L, c, l, sc);
+        const float *src = phi + L.src[l] + sc * p3;
+        float v[4], h[4], w[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            v[j] = (in && b0 + j < p3) ? src[b0 + j] : 0.0f;
+            const uint32_t u = __float_as_uint(v[j]) + (nearest ? 0x1000u : 0u);
+            h[j] = __uint_as_float(u & 0xFFFFE000u);
+            w[j] = v[j] - h[j];
+        }
+        *reinterpret_cast<float4 *>(hi + c * p3s + b0) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(lo + c * p3s + b0) = make_float4(w[0], w[1], w[2], w[3]);
     }
 }
 
 // BF16: hi = bf16(x), lo = bf16(x - hi), both rounded to nearest even; cell
-// vectors of p3k values (zero padded, p3k % 64 == 0)
+// vectors of p3k values (zero padded, p3k % 64 == 0).  One thread per 4 values.
 __global__ void k_split_bf16(const float *__restrict__ phi, SplitLevels L, __nv_bfloat16 *__restrict__ hi,
                              __nv_bfloat16 *__restrict__ lo, int p3, int p3k) {
-    const int64_t c0 = L.dst[L.lmin], n = (L.dst[L.lmax + 1] - c0) * p3k;
+    const int q4 = p3k / 4;
+    const int64_t c0 = L.dst[L.lmin], n = (L.dst[L.lmax + 1] - c0) * q4;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = c0 + i / p3k;
-        const int b = (int)(i % p3k);
+        const int64_t c = c0 + i / q4;
+        const int b0 = (int)(i % q4) * 4;
         int l;
         int64_t sc;
-        float v = 0.0f;
-        if (b < p3 && split_source(L, c, l, sc)) v = phi[L.src[l] + sc * p3 + b];
-        __nv_bfloat16 h = __float2bfloat16_rn(v);
-        hi[c * p3k + b] = h;
-        lo[c * p3k + b] = __float2bfloat16_rn(v - __bfloat162float(h));
+        const bool in = split_source(L, c, l, sc);
+        const float *src = phi + L.src[l] + sc * p3;
+        __nv_bfloat16 h[4], w[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float v = (in && b0 + j < p3) ? src[b0 + j] : 0.0f;
+            h[j] = __float2bfloat16_rn(v);
+            w[j] = __float2bfloat16_rn(v - __bfloat162float(h[j]));
+        }
+        *reinterpret_cast<uint2 *>(hi + c * p3k + b0) = *reinterpret_cast<const uint2 *>(h);
+        *reinterpret_cast<uint2 *>(lo + c * p3k + b0) = *reinterpret_cast<const uint2 *>(w);
     }
 }
 
@@ -467,7 +486,7 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
         SL.src[l] = l <= depth ? W.phi_level[l] : 0;
         SL.dst[l] = tc_level_first(l);
     }
-    tr.begin(FMM_STAGE_M2L);
+    tr.begin(FMM_STAGE_M2L, st);
     __nv_bfloat16 *hi16 = reinterpret_cast<__nv_bfloat16 *>(P.phihi);
     __nv_bfloat16 *lo16 = reinterpret_cast<__nv_bfloat16 *>(P.philo);
     if (bf16)
