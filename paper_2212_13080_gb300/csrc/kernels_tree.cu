@@ -368,9 +368,13 @@ __global__ void k_scatter(const WsHeader *hdr, const uint32_t *__restrict__ e_ke
 }
 
 // one warp per finest cell: rank every element of the cell's segment among
-// the segment (all values distinct) and place it
-__global__ void k_leaf_order(int ncell, const int *__restrict__ leaf_start,
-                             const int *__restrict__ tmp, int *__restrict__ perm) {
+// the segment (emission indices, all distinct), and move it to its sorted
+// slot: charge, origin, perm (slot -> emitted index) and inv (emitted -> slot)
+template <typename real>
+__global__ void k_leaf_gather(int ncell, const int *__restrict__ leaf_start, const int *__restrict__ tmp,
+                              const typename Vec4<real>::T *__restrict__ e_pt,
+                              const int *__restrict__ e_origin, typename Vec4<real>::T *__restrict__ s_pt,
+                              int *__restrict__ s_origin, int *__restrict__ perm, int *__restrict__ inv) {
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -385,29 +389,25 @@ __global__ void k_leaf_order(int ncell, const int *__restrict__ leaf_start,
                 int w = __shfl_sync(0xffffffffu, v, j);
                 r += (w < v);
             }
-            if (lane < cnt) perm[s0 + r] = v;
+            if (lane < cnt) {
+                const int slot = s0 + r;
+                perm[slot] = v;
+                inv[v] = slot;
+                s_pt[slot] = e_pt[v];
+                s_origin[slot] = e_origin[v];
+            }
         } else {
             for (int i = lane; i < cnt; i += 32) {
                 int v = tmp[s0 + i];
                 int r = 0;
                 for (int j = 0; j < cnt; j++) r += (tmp[s0 + j] < v);
-                perm[s0 + r] = v;
+                const int slot = s0 + r;
+                perm[slot] = v;
+                inv[v] = slot;
+                s_pt[slot] = e_pt[v];
+                s_origin[slot] = e_origin[v];
             }
         }
-    }
-}
-
-template <typename real>
-__global__ void k_gather(const WsHeader *hdr, const int *__restrict__ perm,
-                         const typename Vec4<real>::T *__restrict__ e_pt,
-                         const int *__restrict__ e_origin, typename Vec4<real>::T *__restrict__ s_pt,
-                         int *__restrict__ s_origin, int *__restrict__ inv) {
-    int ne = hdr->n_eff;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ne; s += gridDim.x * blockDim.x) {
-        int e = perm[s];
-        s_pt[s] = e_pt[e];
-        s_origin[s] = e_origin[e];
-        inv[e] = s;
     }
 }
 
@@ -423,10 +423,9 @@ void launch_sort(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, c
     k_scatter<<<nbp, 256, 0, st>>>(P.hdr, P.e_key, P.leaf_start, P.cursor, P.tmp);
     int nbl = (ncell * 32 + 255) / 256;
     if (nbl > 152 * 64) nbl = 152 * 64;
-    k_leaf_order<<<nbl, 256, 0, st>>>(ncell, P.leaf_start, P.tmp, P.perm);
-    k_gather<real><<<nbp, 256, 0, st>>>(P.hdr, P.perm, P.e_pt, P.e_origin, P.s_pt, P.s_origin,
-                                        P.inv);
-    tr.count(3);
+    k_leaf_gather<real><<<nbl, 256, 0, st>>>(ncell, P.leaf_start, P.tmp, P.e_pt, P.e_origin, P.s_pt,
+                                             P.s_origin, P.perm, P.inv);
+    tr.count(2);
     tr.end();
 }
 
@@ -441,6 +440,22 @@ void launch_sort(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, c
 // ---------------------------------------------------------------------------
 #define UNSPLIT_BS 256
 
+// Error-free transformations (Dekker, Knuth): a*b = p + fma_exact_err(a, b, p)
+// exactly; pair_add adds (bh, bl) to the pair (ah, al) with the rounding error
+// of the high parts carried in the low part.  In double precision these are
+// ordinary double operations.
+__device__ __forceinline__ float fma_exact_err(float a, float b, float p) { return fmaf(a, b, -p); }
+__device__ __forceinline__ double fma_exact_err(double a, double b, double p) { return fma(a, b, -p); }
+template <typename real>
+__device__ __forceinline__ void pair_add(real &ah, real &al, real bh, real bl) {
+    const real s = ah + bh;
+    const real v = s - ah;
+    const real e = (ah - (s - v)) + (bh - v);
+    const real t = e + al + bl;
+    ah = s + t;
+    al = t - (ah - s);
+}
+
 template <typename real>
 __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__restrict__ q,
                           const int *__restrict__ offset,
@@ -449,12 +464,11 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
                           const typename Vec4<real>::T *__restrict__ out_pt, real *__restrict__ potential,
                           real *__restrict__ forces, double *__restrict__ epart,
                           const double *__restrict__ grad_energy, real *__restrict__ grad_q,
-                          int backward) {
+                          int backward, real sphi, real sF) {
+    // sphi = 1/L and sF = 1/L^2 come from the host: no FP64 arithmetic per thread
     __shared__ double sh[UNSPLIT_BS / 32];
-    const double invL = 1.0 / g.L;
-    const real sphi = (real)invL, sF = (real)(invL * invL);
     double gE = backward ? *grad_energy : 0.0;
-    double eacc = 0.0;
+    real ehi = 0, elo = 0;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         real phi, Fx, Fy, Fz;
@@ -497,7 +511,8 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
                 forces[3 * i + 1] = Fy;
                 forces[3 * i + 2] = Fz;
             }
-            eacc = 0.5 * (double)q[i] * (double)phi;
+            ehi = (real)q[i] * phi;  // q phi exactly as ehi + elo (single precision)
+            elo = fma_exact_err((real)q[i], phi, ehi);
         } else {
             if (forces) {
                 forces[3 * i] = (real)(-(double)Fx * gE);
@@ -508,14 +523,19 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
         }
     }
     if (epart) {
-        // deterministic block reduction
-        for (int o = 16; o > 0; o >>= 1) eacc += __shfl_down_sync(0xffffffffu, eacc, o);
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = eacc;
+        // deterministic block reduction of sum q phi: exact products, then
+        // compensated pair sums over the warp (no FP64 arithmetic per particle)
+        for (int o = 16; o > 0; o >>= 1) {
+            const real bh = __shfl_down_sync(0xffffffffu, ehi, o);
+            const real bl = __shfl_down_sync(0xffffffffu, elo, o);
+            pair_add(ehi, elo, bh, bl);
+        }
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)ehi + (double)elo;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0;
             for (int w = 0; w < UNSPLIT_BS / 32; w++) s += sh[w];
-            epart[blockIdx.x] = s;
+            epart[blockIdx.x] = 0.5 * s;
         }
     }
 }
@@ -553,7 +573,7 @@ void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n
     k_unsplit<real><<<nb, UNSPLIT_BS, 0, st>>>(
         g, P.hdr, n, q, g.continuous ? P.offset : nullptr, P.count, P.axes, P.inv,
         g.continuous ? P.e_wd : nullptr, P.out_pt, potential, forces, ep, grad_energy, grad_q,
-        backward ? 1 : 0);
+        backward ? 1 : 0, (real)(1.0 / g.L), (real)((1.0 / g.L) * (1.0 / g.L)));
     tr.count();
     if (ep) {
         k_energy_final<<<1, 1024, 0, st>>>(P.epart, nb, energy);
