@@ -325,27 +325,33 @@ def test_forces_central_differences_fp64():
     plan.close()
 
 
-@pytest.mark.parametrize("name,sample,precision", [("uniform1m", 512, "fp32"), ("water2m", 256, "fp32"),
-                                                    ("uniform1m", 512, "tf32x3"),
+@pytest.mark.parametrize("name,sample,precision", [("uniform1m", None, "fp32"), ("water2m", 256, "fp32"),
+                                                    ("uniform1m", None, "tf32x3"),
                                                     ("water2m", 256, "tf32x3"),
                                                     ("plummer8m", 256, "tf32x3"),
                                                     ("plummer8m", 256, "bf16x3")])
 def test_parity_full_size_sampled(name, sample, precision):
     """Full-size workloads in the benchmark's launch configuration: integer work
-    on every charge, outputs on sampled particles (the oracle computes those one
-    by one from its full upward pass)."""
+    on every charge; outputs on every particle (uniform1m: the oracle runs the
+    whole workload in about a second) or on sampled particles (the oracle
+    computes those one by one from its full upward pass).  Adjoint forces of
+    split particles carry most of the force error (a difference of potentials
+    across 2d, §2.3), so a small sample's error is dominated by its few split
+    particles; the whole-workload comparison is the stronger check."""
     w = inputs.workload(name)
     pos, q, box = w["pos"], w["q"], w["box"]
     rng = np.random.default_rng(0)
-    s = np.sort(rng.choice(len(q), sample, replace=False))
+    s = np.arange(len(q)) if sample is None else np.sort(rng.choice(len(q), sample, replace=False))
     ref = oracle.fmm(pos, q, box, depth=w["depth"], n=w["p"], periodic=w["periodic"],
-                     continuous=w["continuous"], sample=s)
+                     continuous=w["continuous"], sample=None if sample is None else s)
     plan, out = _gpu(pos, q, box, w["depth"], w["p"], w["periodic"], w["continuous"], None, precision)
     _check_integer_work(plan, ref)
     tol = {"fp32": TOL_FP32, "tf32x3": TOL_TF32X3}.get(precision) or TOL_TC_MODE[precision]
     assert _rel_l2(out["potential"][s], ref["phi"]) < tol
     tol_F = max(tol, TOL_FP32_SPLIT_ADJOINT) if w["continuous"] else tol
     assert _rel_l2(out["forces"][s], ref["F"]) < tol_F
+    if sample is None:
+        assert abs(out["energy"][0] - ref["E"]) / abs(ref["E"]) < tol
     # energy: the sum is a property at any size; E = 1/2 sum q phi of the GPU's own phi
     E_from_phi = 0.5 * np.dot(q.astype(np.float64), out["potential"])
     assert abs(out["energy"][0] - E_from_phi) < 1e-9 * np.sum(np.abs(q * out["potential"]))
