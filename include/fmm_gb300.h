@@ -190,6 +190,7 @@ int fmm_status(fmm_plan_t plan, const void *workspace, void *stream);
 #define FMM_DUMP_PHI 6
 #define FMM_DUMP_LOCAL 7
 #define FMM_DUMP_OUT 8
+#define FMM_DUMP_WAIT 9
 int fmm_debug_dump(fmm_plan_t plan, int what, const void *workspace, void *dst, size_t bytes,
                    void *stream);
 
@@ -197,6 +198,25 @@ int fmm_debug_dump(fmm_plan_t plan, int what, const void *workspace, void *dst, 
  * `workspace` (waits on `stream`). */
 int fmm_debug_size(fmm_plan_t plan, int what, const void *workspace, size_t *bytes,
                    void *stream);
+
+/*
+ * Failure-detection test hook (the paper has no counterpart).  With
+ * FMM_INJECT_TC_STALL the next fmm_eval of the plan runs its tensor-core
+ * contraction with the producer arming the first stage's barrier without
+ * issuing that stage's copies: the barrier's transaction count is never met,
+ * the consumer's bounded wait (about 2 s of SM clock) expires, the kernel
+ * records the wait site in the workspace header, waits for its own copies and
+ * MMAs, frees its tensor memory and returns, and the call returns
+ * FMM_ERR_TIMEOUT.  No fault, trap or unbounded wait: the context stays usable.
+ * The hook disarms itself after one evaluation; FMM_INJECT_NONE disarms it.
+ * Plans without tensor-core contraction (FP32, FP64) return FMM_ERR_UNSUPPORTED.
+ * The wait site: fmm_debug_dump(FMM_DUMP_WAIT) = int[4] (site: 1 producer slot,
+ * 2 MMA region, 3 MMA operands, 4 epilogue region, 0 none; block; level;
+ * iteration).
+ */
+#define FMM_INJECT_NONE 0
+#define FMM_INJECT_TC_STALL 1
+int fmm_debug_inject(fmm_plan_t plan, int what);
 
 /*
  * Stage timing and launch accounting (tracing).

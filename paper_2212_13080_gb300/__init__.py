@@ -122,10 +122,11 @@ class FMM:
         F = o.get("forces")
         if forces and F is None:
             F = torch.empty((n, 3), dtype=self.out_dtype, device=self.device)
+        # recorded first: a failed call's workspace still holds its status and wait site
+        self._last = (ws, n, pos_d, q_d)
         B.fmm_eval(self._h, n, _ptr(pos_d), _ptr(q_d), _ptr(phi) if potential else None,
                    _ptr(E) if energy else None, _ptr(F) if forces else None, _ptr(ws),
                    ws.numel(), _stream(stream))
-        self._last = (ws, n, pos_d, q_d)
         res = {"potential": phi if potential else None, "energy": E if energy else None,
                "forces": F if forces else None}
         if host:
@@ -166,6 +167,12 @@ class FMM:
                        _ptr(ws), ws.numel(), _stream(stream))
         return gpos, gq
 
+    def inject(self, what="tc_stall"):
+        """Failure-detection test hook: the next evaluation's tensor-core
+        contraction withholds one stage's copies, its bounded wait expires and
+        the call raises FMM_ERR_TIMEOUT ("none" disarms)."""
+        B.fmm_debug_inject(self._h, {"none": B.FMM_INJECT_NONE, "tc_stall": B.FMM_INJECT_TC_STALL}[what])
+
     def set_timing(self, on=True, serial=False):
         """Bracket every stage of later calls with CUDA events (see stats()).
 
@@ -190,7 +197,7 @@ class FMM:
                          _stream(stream))
         buf = buf[:nb]
         real = np.float64 if self.precision == "fp64" else np.float32
-        if what in ("counts", "origin", "perm", "start"):
+        if what in ("counts", "origin", "perm", "start", "wait"):
             return buf.view(np.int32)
         if what == "keys":
             return buf.view(np.uint32)

@@ -40,13 +40,17 @@ FMM_DUMP_POINTS = 5
 FMM_DUMP_PHI = 6
 FMM_DUMP_LOCAL = 7
 FMM_DUMP_OUT = 8
+FMM_DUMP_WAIT = 9
+FMM_INJECT_NONE = 0
+FMM_INJECT_TC_STALL = 1
 
 # every symbol include/fmm_gb300.h declares
 EXPORTED = ["fmm_opts_default", "fmm_plan_create", "fmm_plan_destroy", "fmm_workspace_size",
             "fmm_eval", "fmm_backward", "fmm_status", "fmm_debug_dump", "fmm_debug_size",
             "fmm_set_timing", "fmm_get_stats", "fmm_strerror", "fmm_version",
             "fmm_eval_static", "fmm_batch_create", "fmm_batch_destroy",
-            "fmm_batch_workspace_size", "fmm_batch_eval", "fmm_batch_get_stats"]
+            "fmm_batch_workspace_size", "fmm_batch_eval", "fmm_batch_get_stats",
+            "fmm_debug_inject"]
 
 FMM_STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -99,6 +103,7 @@ def lib():
         L.fmm_debug_dump.argtypes = [P, i32, P, P, sz, P]
         L.fmm_debug_size.argtypes = [P, i32, P, ctypes.POINTER(sz), P]
         L.fmm_set_timing.argtypes = [P, i32]
+        L.fmm_debug_inject.argtypes = [P, i32]
         L.fmm_get_stats.argtypes = [P, ctypes.POINTER(fmm_stats_t)]
         L.fmm_strerror.argtypes = [i32]
         L.fmm_strerror.restype = ctypes.c_char_p
@@ -181,6 +186,10 @@ def fmm_debug_dump(h, what, workspace, dst, nbytes, stream):
 
 def fmm_set_timing(h, on):
     _check(lib().fmm_set_timing(h, int(on)), "fmm_set_timing")
+
+
+def fmm_debug_inject(h, what):
+    _check(lib().fmm_debug_inject(h, int(what)), "fmm_debug_inject")
 
 
 def fmm_get_stats(h):

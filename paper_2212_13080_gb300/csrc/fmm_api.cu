@@ -31,6 +31,7 @@ struct fmm_plan_s {
     alignas(64) unsigned char khi_map[128], klo_map[128];  // their TMA tensor maps
     bool tc;                // bilinear forms of every level on tensor cores
     int tc_mode;            // FMM_TC_*: split TF32 x3, TF32 x1, split BF16 x3
+    int inject;             // FMM_INJECT_* for the next evaluation (test hook)
     bool shared;            // tables belong to another plan (batched systems)
     Coef<float> cf;
     Coef<double> cd;
@@ -450,6 +451,8 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     T.Klbar = (const real *)P->Klbar;
     T.tc_lmin = P->tc ? (P->periodic ? 1 : 2) : 0;  // every level on the tensor cores
     T.tc_mode = P->tc_mode;
+    T.tc_inject = P->inject;
+    P->inject = FMM_INJECT_NONE;  // one evaluation only
     T.tc_khi_map = P->khi_map;
     T.tc_klo_map = P->klo_map;
     T.tc_kbar = (const float *)P->Kbar_tc;
@@ -734,10 +737,19 @@ static int dump_bytes(fmm_plan_t P, int what, int n_eff, size_t *bytes) {
     case FMM_DUMP_START: *bytes = (size_t)(ncell + 1) * 4; break;
     case FMM_DUMP_POINTS:
     case FMM_DUMP_OUT: *bytes = (size_t)n_eff * 4 * rs; break;
+    case FMM_DUMP_WAIT: *bytes = 16; break;
     case FMM_DUMP_PHI:
     case FMM_DUMP_LOCAL: *bytes = (size_t)cells * p3 * rs; break;
     default: return FMM_ERR_ARG;
     }
+    return FMM_OK;
+}
+
+int fmm_debug_inject(fmm_plan_t P, int what) {
+    if (!P) return FMM_ERR_ARG;
+    if (what != FMM_INJECT_NONE && what != FMM_INJECT_TC_STALL) return FMM_ERR_ARG;
+    if (what == FMM_INJECT_TC_STALL && !P->tc) return FMM_ERR_UNSUPPORTED;
+    P->inject = what;
     return FMM_OK;
 }
 
@@ -788,6 +800,11 @@ int fmm_debug_dump(fmm_plan_t P, int what, const void *workspace, void *dst, siz
     case FMM_DUMP_START: return copy(W.leaf_start, need);
     case FMM_DUMP_POINTS: return copy(W.s_pt, need);
     case FMM_DUMP_OUT: return copy(W.out_pt, need);
+    case FMM_DUMP_WAIT: {
+        int32_t c[4] = {h.wait_site, h.wait_block, h.wait_level, h.wait_iter};
+        memcpy(dst, c, 16);
+        return FMM_OK;
+    }
     case FMM_DUMP_PHI:
     case FMM_DUMP_LOCAL: {
         const bool isphi = what == FMM_DUMP_PHI;
@@ -880,6 +897,7 @@ fmm_plan_t clone_plan(const fmm_plan_s *m, const double *box, int64_t max_n) {
     P->h_hdr = nullptr;
     P->timing = false;
     P->serial = false;
+    P->inject = FMM_INJECT_NONE;
     P->nev_created = 0;
     P->max_n = max_n;
     memcpy(P->box, box, sizeof(double) * 4);

@@ -205,6 +205,7 @@ struct DevTables {
     // tensor-core contraction (TF32X3 / TF32X1 / BF16X3 plans): levels >= tc_lmin, 0 = none
     int tc_lmin;
     int tc_mode;                          // FMM_TC_*
+    int tc_inject;                        // FMM_INJECT_* test hook for this evaluation
     const void *tc_khi_map, *tc_klo_map;  // CUtensorMap of the split unit-cell kernels
     const float *tc_kbar;                 // [343][p3 padded to 32] row means
 };
@@ -254,8 +255,8 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
 #define FMM_TC_TF32X1 1  // 1-pass TF32
 #define FMM_TC_BF16X3 2  // 3-pass split BF16
 int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
-                  const void *k_lo_map, const float *kbar, int lmin, int mode, cudaStream_t st,
-                  Tracer &tr);
+                  const void *k_lo_map, const float *kbar, int lmin, int mode, int inject,
+                  cudaStream_t st, Tracer &tr);
 // map of a [343][p3s][pk] kernel table: fp32 (pk = p3s) or bf16 (pk = tc_padded_k)
 int tc_encode_kernel_map(void *map, const void *base, int p3s, int pk, int mode);
 int tc_padded(int p3);            // p^3 rounded up to 32 (MMA N, fp32 K)

@@ -552,7 +552,7 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
     if constexpr (std::is_same<real, float>::value) {
         if (T.tc_lmin > 0 && depth >= T.tc_lmin) {
             int rc = launch_m2l_tc(g, P, W, T.tc_khi_map, T.tc_klo_map, T.tc_kbar, T.tc_lmin,
-                                   T.tc_mode, st, tr);
+                                   T.tc_mode, T.tc_inject, st, tr);
             if (rc) return rc;
         }
     }

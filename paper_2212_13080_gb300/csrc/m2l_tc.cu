@@ -62,6 +62,7 @@ struct TcParams {
     const float *qlev;
     const float *kbar;  // [343][N], zero padded
     int *status;
+    int inject_stall;   // test hook: the first stage's copies are withheld
 };
 
 // The i-th offset of the interaction list of parity (bx, by, bz), in the
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
                 const uint32_t fb = full0 + 8 * s;
                 const int kx = kc * Sh::KE;
                 tc::mbar_expect_tx(fb, Sh::LO ? Sh::STAGE : TC_ABYTES + Sh::BBYTES);
+                if (prm.inject_stall && it == 0) continue;  // armed, never filled (test hook)
                 tc::tma_load_5d(st, &prm.phi_hi[l], fb, kx, cX, cY, cZ, f.spar);
                 tc::tma_load_3d(st + 2 * TC_ABYTES, &prm.k_hi, fb, kx, 0, f.oi);
                 if (Sh::LO) {
@@ -472,8 +474,8 @@ static int launch_tc_mode(int p3s, const TcParams &prm, int blocks, cudaStream_t
 }
 
 int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
-                  const void *k_lo_map, const float *kbar, int lmin, int mode, cudaStream_t st,
-                  Tracer &tr) {
+                  const void *k_lo_map, const float *kbar, int lmin, int mode, int inject,
+                  cudaStream_t st, Tracer &tr) {
     const int depth = g.depth, p3 = g.p3, p3s = tc_padded(p3), pk = tc_padded_k(p3, mode);
     const bool bf16 = mode == FMM_TC_BF16X3;
     // the grid charges of levels lmin..depth in the operand layout, split into
@@ -520,6 +522,7 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
     prm.qlev = P.qlev;
     prm.kbar = kbar;
     prm.status = &P.hdr->status;
+    prm.inject_stall = inject == FMM_INJECT_TC_STALL;
     int rc = mode == FMM_TC_BF16X3   ? launch_tc_mode<TC_BF16X3>(p3s, prm, blocks, st)
              : mode == FMM_TC_TF32X1 ? launch_tc_mode<TC_TF32X1>(p3s, prm, blocks, st)
                                      : launch_tc_mode<TC_TF32X3>(p3s, prm, blocks, st);

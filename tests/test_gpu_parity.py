@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from paper_2212_13080_gb300 import FMM, FmmError, inputs  # noqa: E402
+from paper_2212_13080_gb300 import _binding as B  # noqa: E402
 
 TOL_FP32 = 1e-6
 TOL_FP64 = 1e-11
@@ -256,6 +257,35 @@ def test_coincident_split_charges_across_cells(precision):
     assert _rel_l2(out["potential"], ref["phi"]) < tol
     assert _rel_l2(out["forces"], ref["F"]) < tol_F
     plan.close()
+
+
+def test_wait_timeout_is_reported_and_context_survives():
+    """Failure detection without a fault: the tensor-core contraction's producer
+    arms one stage's barrier without issuing its copies (a flag nothing sets);
+    the consumer's bounded wait expires, the kernel records where, frees its
+    tensor memory and returns; the call reports FMM_ERR_TIMEOUT and the next
+    evaluation on the same context is correct."""
+    pos, q, box = inputs.uniform_cont(20000, 41)
+    n = len(q)
+    plan = FMM(box, 4, 4, continuous=True, precision="tf32x3", max_n=n)
+    P, Q = torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda()
+    plan.inject("tc_stall")
+    with pytest.raises(FmmError) as e:
+        plan.eval(P, Q)
+    assert e.value.code == B.FMM_ERR_TIMEOUT
+    site, block, level, it = [int(v) for v in plan.dump("wait")]
+    assert site in (1, 2, 3, 4) and 2 <= level <= 4 and block >= 0
+    r = plan.eval(P, Q)  # the hook disarmed itself; same context, same plan
+    ref = oracle.fmm(pos, q, box, depth=4, n=4, continuous=True, keep=False)
+    assert _rel_l2(r["potential"].cpu().numpy().astype(np.float64), ref["phi"]) < TOL_TF32X3
+    assert int(plan.dump("wait")[0]) == 0
+    plan.close()
+    # plans without the tensor-core contraction have nothing to stall
+    plan32 = FMM(box, 4, 4, precision="fp32", max_n=n)
+    with pytest.raises(FmmError) as e:
+        plan32.inject("tc_stall")
+    assert e.value.code == B.FMM_ERR_UNSUPPORTED
+    plan32.close()
 
 
 def test_split_overflow_is_reported():
