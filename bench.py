@@ -294,8 +294,33 @@ def run_batch(args, world, rank, local):
     st = bt.stats()
     t = statistics.mean(ms)
     n = int(offs[-1])
+    outs = {args.precision: {k: v.cpu().numpy() for k, v in out.items()}}
+    bt.close()
+
+    # the plain FP32 batched form, same protocol, fewer steps
+    plain = None
+    if args.precision != "fp32":
+        b32 = FMMBatch(boxes, depths, 4, periodic=True, continuous=True, precision="fp32",
+                       max_n=counts, sync=False)
+        for _ in range(2):
+            b32.eval(pos, q, offs, out=out)
+        t32 = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            b32.eval(pos, q, offs, out=out)
+            b.record(stream)
+            b.synchronize()
+            t32.append(a.elapsed_time(b))
+        outs["fp32"] = {k: v.cpu().numpy() for k, v in out.items()}
+        plain = {"precision": "fp32", "ms_per_step": statistics.mean(t32),
+                 "value": world * n / (statistics.mean(t32) * 1e-3) / 1e6, "unit": UNIT,
+                 "lanes": b32.stats()["lanes"]}
+        b32.close()
+    res = None
     if rank == 0:
-        print(json.dumps({
+        res = {
             "metric": METRIC, "value": world * n / (t * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -307,8 +332,48 @@ def run_batch(args, world, rank, local):
                        "outputs": "potential+energy+forces per system",
                        "l2": "flushed (256 MB write) before every timed step"},
             "gpu_launches": st["launches"] * args.steps, "graph_launches_per_step": 1,
-            "lanes": st["lanes"], "tune_ms": st["tune_ms"], "clocks": clocks}), flush=True)
-    bt.close()
+            "lanes": st["lanes"], "tune_ms": st["tune_ms"], "clocks": clocks,
+            "plain_fp32": plain}
+        if world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"], res["error_vs_fp64_oracle"] = batch_cpu_baseline(
+                pos_h, q_h, offs, boxes, counts, depths, outs)
+        print(json.dumps(res), flush=True)
+
+
+def batch_cpu_baseline(pos_h, q_h, offs, boxes, counts, depths, outs):
+    """The oracle on 16 whole systems of the batch (the smallest, the largest and
+    14 seeded picks): its throughput on that sample, and the relative L2 error
+    of the GPU's batched outputs against it for those systems."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(55)
+    pick = sorted(set([int(np.argmin(counts)), int(np.argmax(counts))] +
+                      [int(v) for v in rng.choice(len(counts), 14, replace=False)]))
+    t_tot, m_tot = 0.0, 0
+    err = {name: {"potential_rel_l2": [], "forces_rel_l2": [], "energy_rel": []} for name in outs}
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    for i in pick:
+        a, b = int(offs[i]), int(offs[i + 1])
+        t0 = time.perf_counter()
+        r = oracle.fmm(pos_h[a:b], q_h[a:b], boxes[i], depth=int(depths[i]), n=4, periodic=True,
+                       continuous=True, keep=False)
+        t_tot += time.perf_counter() - t0
+        m_tot += b - a
+        for name, o in outs.items():
+            err[name]["potential_rel_l2"].append(rel(o["potential"][a:b].astype(np.float64), r["phi"]))
+            err[name]["forces_rel_l2"].append(rel(o["forces"][a:b].astype(np.float64),
+                                                  np.asarray(r["F"]).reshape(-1, 3)))
+            err[name]["energy_rel"].append(abs(float(o["energy"][i]) - r["E"]) / abs(r["E"]))
+    base = {"value": m_tot / t_tot / 1e6, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d whole systems of the batch (%d particles; the smallest, the largest and "
+                      "seeded picks), oracle.fmm FP64, OpenMP, %.1f s" % (len(pick), m_tot, t_tot)}
+    summary = {"systems": pick, "reference": "oracle (FP64, same method and p)"}
+    for name, e in err.items():
+        summary[name] = {k: {"max": max(v), "mean": float(np.mean(v))} for k, v in e.items()}
+    return base, summary
 
 
 def main():
