@@ -48,6 +48,42 @@ def _peaks():
         return 6800.0, 1900.0, 1700.0, "fallback"
 
 
+def job_step_ms(t_ms, dist, device):
+    """The slowest rank's mean step time: every rank runs the same replica and
+    the job is as fast as its slowest rank."""
+    if dist is None:
+        return t_ms
+    import torch
+    tt = torch.tensor([t_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(world, n_per_rank, t_ms):
+    """Whole-job throughput in Mparticles/s: all ranks' particles over the
+    slowest rank's step time (weak scaling, one replica per rank)."""
+    return world * n_per_rank / (t_ms * 1e-3) / 1e6
+
+
+def fence(dist, cuda=True):
+    """Barrier across ranks and device synchronisation (both sides of a timed region)."""
+    if dist is not None:
+        dist.barrier()
+    if cuda:
+        import torch
+        torch.cuda.synchronize()
+
+
+def init_ranks(world, local):
+    import torch
+    torch.cuda.set_device(local)
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group("nccl")
+    return dist
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -255,14 +291,13 @@ def cpu_baseline(workload, gpu_outputs=None):
     return base, err
 
 
-def run_batch(args, world, rank, local):
+def run_batch(args, world, rank, local, dist=None):
     """512 independent periodic systems (continuous form, p = 4), N per system
     log-uniform in [1024, 65536], depth = clamp(round(log8(N/32)), 3, 5):
     one CUDA-graph launch per step."""
     import numpy as np
     import torch
     from paper_2212_13080_gb300 import FMMBatch, inputs
-    torch.cuda.set_device(local)
     pos_h, q_h, offs, boxes, counts = inputs.batch_systems(512, 5)
     depths = np.clip(np.rint(np.log(counts / 32.0) / np.log(8.0)), 3, 5).astype(int)
     dev = torch.device("cuda", local)
@@ -279,6 +314,7 @@ def run_batch(args, world, rank, local):
         bt.eval(pos, q, offs, out=out)
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
+    fence(dist)
     sampler.start()
     time.sleep(0.3)
     ms = []
@@ -290,9 +326,10 @@ def run_batch(args, world, rank, local):
         b.record(stream)
         b.synchronize()
         ms.append(a.elapsed_time(b))
+    fence(dist)
     clocks = sampler.stop()
     st = bt.stats()
-    t = statistics.mean(ms)
+    t = job_step_ms(statistics.mean(ms), dist, dev)
     n = int(offs[-1])
     outs = {args.precision: {k: v.cpu().numpy() for k, v in out.items()}}
     bt.close()
@@ -321,7 +358,7 @@ def run_batch(args, world, rank, local):
     res = None
     if rank == 0:
         res = {
-            "metric": METRIC, "value": world * n / (t * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": job_value(world, n, t), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "precision": args.precision, "data": "synthetic",
@@ -403,17 +440,14 @@ def main():
             return
         run_reference(args, args.workload, world, rank)
         return
-    if args.workload == "batch512":
-        run_batch(args, world, rank, local)
-        return
-
     import numpy as np
     import torch
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    dist = init_ranks(world, local)
+    if args.workload == "batch512":
+        run_batch(args, world, rank, local, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     from paper_2212_13080_gb300 import FMM, inputs
     w = inputs.workload(args.workload)
@@ -457,9 +491,7 @@ def main():
     p2p_flops = float(P2P_FLOPS_PER_PAIR) * pairs
 
     sampler = ClockSampler(local)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
+    fence(dist)
     sampler.start()
     time.sleep(0.3)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -475,18 +507,14 @@ def main():
         launches += st["launches"]
         for k, v in st["stage_ms"].items():
             stage_tot[k] = stage_tot.get(k, 0.0) + v
-    torch.cuda.synchronize()
+    fence(dist)
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in evs]
     rc = plan_status(plan, ws)
     if rc:
         raise SystemExit("evaluation failed: status %d" % rc)
-    t_step = statistics.mean(ms)
-    if dist is not None:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = world * n / (t_step * 1e-3) / 1e6
+    t_step = job_step_ms(statistics.mean(ms), dist, dev)
+    value = job_value(world, n, t_step)
     stage_ms = {k: v / args.steps for k, v in stage_tot.items()}
 
     # the same steps with every stage on one stream: each stage's own duration

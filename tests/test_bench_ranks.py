@@ -1,0 +1,58 @@
+"""Multi-rank bench logic on CPU (gloo, world size 2): every rank runs the same
+replica; the job's step time is the slowest rank's, its value all ranks'
+particles over that time; only rank 0 runs the reference arm."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    bench.fence(dist, cuda=False)
+    t = bench.job_step_ms(1.0 + 0.5 * rank, dist, "cpu")  # rank 1 is the slower one
+    v = bench.job_value(world, 1000, t)
+    bench.fence(dist, cuda=False)
+    q.put((rank, t, v))
+    dist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    world, port = 2, _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [1.5, 1.5]
+    expect = 2 * 1000 / 1.5e-3 / 1e6
+    assert all(abs(r[2] - expect) < 1e-12 * expect for r in res)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.run_reference(None, "uniform1m", 2, 1) is None  # returns before any work
