@@ -85,6 +85,11 @@ typedef struct {
     int sync;              /* 1 (default when opts is NULL): fmm_eval waits for the device
                               and returns device-side errors; 0: fmm_eval returns after
                               queueing, fmm_status() reports them later */
+    double grid_scale;     /* spacing of the p-division points in units of the standard
+                              arrangement i/(p-1), about the cell centre (§4.1: the
+                              "reduced" arrangement, e.g. 1/1.2); (0, 1]; <= 0 selects 1;
+                              plain form only (continuous with a scale != 1:
+                              FMM_ERR_UNSUPPORTED) */
 } fmm_opts_t;
 
 /* Fills *opts with the defaults (continuous 0, split_ratio 1/256, split_capacity 0

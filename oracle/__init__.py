@@ -48,6 +48,7 @@ def lib():
                               ctypes.c_void_p)
         P = ctypes.c_void_p
         L.orc_lagrange.argtypes = [i32, d, P]
+        L.orc_set_grid_scale.argtypes = [d]
         L.orc_lagrange_deriv.argtypes = [i32, d, P]
         L.orc_shift_matrix.argtypes = [i32, i32, P]
         L.orc_m2l_kernel.argtypes = [i32, i32, i32, i32, P]
@@ -206,7 +207,22 @@ def level_offset(n, l):
 
 
 def fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sample=None,
-        keep=True):
+        keep=True, grid_scale=1.0):
+    """Runs the oracle FMM; grid_scale < 1 takes the reduced arrangement of the
+    n-division points (§4.1: spacing times grid_scale about the cell centre).
+    See _fmm for the other arguments."""
+    if continuous and grid_scale != 1.0:
+        raise ValueError("the reduced arrangement is defined for the plain form")
+    L_ = lib()
+    L_.orc_set_grid_scale(float(grid_scale))
+    try:
+        return _fmm(pos, q, box, depth, n, periodic, continuous, dt, sample, keep)
+    finally:
+        L_.orc_set_grid_scale(1.0)
+
+
+def _fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sample=None,
+         keep=True):
     """Runs the oracle FMM.
 
     pos: (N,3) float32 positions, q: (N,) float32 charges, box = (x0,y0,z0,L).

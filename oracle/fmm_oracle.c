@@ -41,8 +41,12 @@
 /* ------------------------------------------------------------------------ */
 
 /* §2.1.2: the n-division points of a segment are equally spaced and include
- * both end points; on the unit segment they are a_i = i/(n-1). */
-static double tau(int n, int i) { return (double)i / (double)(n - 1); }
+ * both end points; on the unit segment they are a_i = i/(n-1).  §4.1 (the
+ * "reduced" arrangement) moves them toward the centre of the cell: their
+ * spacing is multiplied by a factor s <= 1, a_i = 1/2 + s (i/(n-1) - 1/2). */
+static double g_grid_scale = 1.0;
+void orc_set_grid_scale(double s) { g_grid_scale = s; }
+static double tau(int n, int i) { return 0.5 + g_grid_scale * ((double)i / (double)(n - 1) - 0.5); }
 
 /* §2.1.1, eq. (Lag1): g_i(x) = prod_{k!=i} (x - a_k) / prod_{k!=i} (a_i - a_k). */
 void orc_lagrange(int n, double x, double *g)

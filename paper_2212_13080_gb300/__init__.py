@@ -48,7 +48,7 @@ class FMM:
 
     def __init__(self, box, depth, p, periodic=False, continuous=False, split_ratio=None,
                  precision="fp32", force_mode="adjoint", max_n=1 << 20, split_capacity=None,
-                 sync=True, device=None):
+                 sync=True, device=None, grid_scale=1.0):
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         self.box = tuple(float(x) for x in box)
@@ -64,6 +64,7 @@ class FMM:
         o.precision = _PREC[precision]
         o.force_mode = _FORCE[force_mode]
         o.sync = int(bool(sync))
+        o.grid_scale = float(grid_scale)
         with torch.cuda.device(self.device):
             self._h = B.fmm_plan_create(self.box, self.depth, self.p, self.periodic, o, self.max_n)
         self.out_dtype = torch.float64 if precision == "fp64" else torch.float32

@@ -60,7 +60,8 @@ STAGES = ["bin", "sort", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "unsplit"]
 class fmm_opts_t(ctypes.Structure):
     _fields_ = [("continuous", ctypes.c_int), ("split_ratio", ctypes.c_double),
                 ("split_capacity", ctypes.c_double), ("precision", ctypes.c_int),
-                ("force_mode", ctypes.c_int), ("sync", ctypes.c_int)]
+                ("force_mode", ctypes.c_int), ("sync", ctypes.c_int),
+                ("grid_scale", ctypes.c_double)]
 
 
 class fmm_stats_t(ctypes.Structure):

@@ -55,13 +55,15 @@ static int g_plan_counter = 0;
 // ---------------------------------------------------------------------------
 namespace {
 
-double node(int p, int i) { return (double)i / (double)(p - 1); }
+// §2.1.2: the p-division points of [0,1], i/(p-1); §4.1's reduced arrangement
+// multiplies their spacing by gs <= 1 about the centre of the cell
+double node(int p, double gs, int i) { return 0.5 + gs * ((double)i / (double)(p - 1) - 0.5); }
 
 // §2.1.1: Lagrange basis g_i(x) on the p-division points of [0,1]
-double lagrange(int p, int i, double x) {
+double lagrange(int p, double gs, int i, double x) {
     double v = 1.0;
     for (int k = 0; k < p; k++)
-        if (k != i) v *= (x - node(p, k)) / (node(p, i) - node(p, k));
+        if (k != i) v *= (x - node(p, gs, k)) / (node(p, gs, i) - node(p, gs, k));
     return v;
 }
 
@@ -101,19 +103,19 @@ double far_image_sum(double rx, double ry, double rz) {
 }
 
 template <typename real>
-void fill_coef(int p, Coef<real> &C) {
+void fill_coef(int p, double gs, Coef<real> &C) {
     memset(&C, 0, sizeof(C));
     for (int i = 0; i < p; i++) {
-        C.tau[i] = (real)node(p, i);
+        C.tau[i] = (real)node(p, gs, i);
         double den = 1.0;
         for (int k = 0; k < p; k++)
-            if (k != i) den *= node(p, i) - node(p, k);
+            if (k != i) den *= node(p, gs, i) - node(p, gs, k);
         C.cinv[i] = (real)(1.0 / den);
     }
     // eq. (trans): (J,i) entry = parent basis g_J at the child node (h + tau_i)/2
     for (int h = 0; h < 2; h++)
         for (int J = 0; J < p; J++)
-            for (int i = 0; i < p; i++) C.G[h][J * p + i] = (real)lagrange(p, J, 0.5 * (h + node(p, i)));
+            for (int i = 0; i < p; i++) C.G[h][J * p + i] = (real)lagrange(p, gs, J, 0.5 * (h + node(p, gs, i)));
 }
 
 template <typename real>
@@ -145,6 +147,7 @@ static float bf16_value(uint16_t h) {
 template <typename real>
 int upload_tables(fmm_plan_t P) {
     const int p = P->p, p3 = p * p * p;
+    const double gs = P->opts.grid_scale;
     const size_t nk = (size_t)343 * p3 * p3;
     std::vector<real> KtT(nk, (real)0), Kbar((size_t)343 * p3, (real)0);
     std::vector<double> row(p3);
@@ -154,12 +157,12 @@ int upload_tables(fmm_plan_t P) {
                 if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
                 size_t oi = (size_t)(((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3));
                 for (int a = 0; a < p3; a++) {
-                    double ax = node(p, a % p), ay = node(p, (a / p) % p), az = node(p, a / (p * p));
+                    double ax = node(p, gs, a % p), ay = node(p, gs, (a / p) % p), az = node(p, gs, a / (p * p));
                     double mean = 0.0;
                     for (int b = 0; b < p3; b++) {
-                        double dx = ax - (ox + node(p, b % p));
-                        double dy = ay - (oy + node(p, (b / p) % p));
-                        double dz = az - (oz + node(p, b / (p * p)));
+                        double dx = ax - (ox + node(p, gs, b % p));
+                        double dy = ay - (oy + node(p, gs, (b / p) % p));
+                        double dz = az - (oz + node(p, gs, b / (p * p)));
                         row[b] = 1.0 / std::sqrt(dx * dx + dy * dy + dz * dz);
                         mean += row[b];
                     }
@@ -186,12 +189,12 @@ int upload_tables(fmm_plan_t P) {
             int ox = oi % 7 - 3, oy = (oi / 7) % 7 - 3, oz = oi / 49 - 3;
             if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
             for (int a = 0; a < p3; a++) {
-                double ax = node(p, a % p), ay = node(p, (a / p) % p), az = node(p, a / (p * p));
+                double ax = node(p, gs, a % p), ay = node(p, gs, (a / p) % p), az = node(p, gs, a / (p * p));
                 double mean = 0.0;
                 for (int b = 0; b < p3; b++) {
-                    double dx = ax - (ox + node(p, b % p));
-                    double dy = ay - (oy + node(p, (b / p) % p));
-                    double dz = az - (oz + node(p, b / (p * p)));
+                    double dx = ax - (ox + node(p, gs, b % p));
+                    double dy = ay - (oy + node(p, gs, (b / p) % p));
+                    double dz = az - (oz + node(p, gs, b / (p * p)));
                     row[b] = 1.0 / std::sqrt(dx * dx + dy * dy + dz * dz);
                     mean += row[b];
                 }
@@ -233,8 +236,8 @@ int upload_tables(fmm_plan_t P) {
             for (int dy = 0; dy < m; dy++)
                 for (int dx = 0; dx < m; dx++)
                     tab[((size_t)dz * m + dy) * m + dx] =
-                        far_image_sum((dx - (p - 1)) / (double)(p - 1), (dy - (p - 1)) / (double)(p - 1),
-                                      (dz - (p - 1)) / (double)(p - 1));
+                        far_image_sum(gs * (dx - (p - 1)) / (double)(p - 1), gs * (dy - (p - 1)) / (double)(p - 1),
+                                      gs * (dz - (p - 1)) / (double)(p - 1));
         std::vector<real> Kl((size_t)p3 * p3), Klb(p3);
         for (int a = 0; a < p3; a++) {
             double mean = 0.0;
@@ -510,6 +513,7 @@ void fmm_opts_default(fmm_opts_t *o) {
     o->precision = FMM_PREC_FP32;
     o->force_mode = FMM_FORCE_ADJOINT;
     o->sync = 1;
+    o->grid_scale = 1.0;
 }
 
 const char *fmm_strerror(int s) {
@@ -544,6 +548,11 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     fmm_opts_default(&o);
     if (opts) o = *opts;
     if (o.split_ratio <= 0) o.split_ratio = 1.0 / 256.0;
+    if (o.grid_scale <= 0) o.grid_scale = 1.0;
+    if (!(o.grid_scale <= 1.0)) return FMM_ERR_ARG;
+    // the split weights (§2.3) are Lagrange weights on equally spaced segment
+    // nodes: the reduced arrangement is for the plain form
+    if (o.continuous && o.grid_scale != 1.0) return FMM_ERR_UNSUPPORTED;
     if (o.continuous && !(o.split_ratio < 0.5)) return FMM_ERR_ARG;
     const bool tc_prec = o.precision == FMM_PREC_TF32X3 || o.precision == FMM_PREC_TF32X1 ||
                          o.precision == FMM_PREC_BF16X3;
@@ -564,8 +573,8 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
                  : o.precision == FMM_PREC_TF32X1 ? FMM_TC_TF32X1
                                                   : FMM_TC_TF32X3;
     cudaGetDevice(&P->device);
-    fill_coef<float>(p, P->cf);
-    fill_coef<double>(p, P->cd);
+    fill_coef<float>(p, o.grid_scale, P->cf);
+    fill_coef<double>(p, o.grid_scale, P->cd);
     Geom &g = P->geom;
     g.p = p;
     g.p3 = p * p * p;

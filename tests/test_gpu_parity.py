@@ -488,3 +488,41 @@ def test_drag_energy_curve_fig6():
     # scale of the energy's FP32 error is the L2 norm of its terms
     scale = 0.5 * np.linalg.norm(terms)
     assert np.max(np.abs(curves["fp32"] - curves["fp64"])) < 1e-6 * scale
+
+
+def _lebesgue(p, s):
+    """max over [0,1] of sum_i |g_i(t)| for the points 1/2 + s (i/(p-1) - 1/2)."""
+    tau = 0.5 + s * (np.arange(p) / (p - 1) - 0.5)
+    t = np.linspace(0.0, 1.0, 4001)
+    total = np.zeros_like(t)
+    for i in range(p):
+        g = np.ones_like(t)
+        for k in range(p):
+            if k != i:
+                g *= (t - tau[k]) / (tau[i] - tau[k])
+        total += np.abs(g)
+    return total.max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("periodic,p", [(False, 4), (True, 5)])
+def test_parity_reduced_arrangement(precision, periodic, p):
+    """§4.1's reduced arrangement of the p-division points (spacing x 1/1.2
+    about the cell centre), plain form: the GPU path with its tables built on
+    the moved points matches the oracle on the same points."""
+    pos, q, box = inputs.uniform_pm1(30000, 57)
+    s = 1 / 1.2
+    ref = oracle.fmm(pos, q, box, depth=4, n=p, periodic=periodic, grid_scale=s)
+    plan = FMM(box, 4, p, periodic=periodic, precision=precision, max_n=len(q), grid_scale=s)
+    r = plan.eval(torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda())
+    tol = {"fp64": TOL_FP64, "fp32": TOL_FP32, "tf32x3": TOL_TF32X3}[precision]
+    if precision != "fp64":
+        # near the faces the moved points extrapolate: rounding in replacement and
+        # evaluation grows with the tensor-product Lebesgue constant (1-D cubed)
+        tol *= (_lebesgue(p, s) / _lebesgue(p, 1.0)) ** 3
+    assert _rel_l2(r["potential"].cpu().numpy().astype(np.float64), ref["phi"]) < tol
+    assert _rel_l2(r["forces"].cpu().numpy().astype(np.float64), ref["F"]) < tol
+    plan.close()
+    with pytest.raises(FmmError) as e:
+        FMM(box, 4, p, continuous=True, max_n=len(q), grid_scale=s)
+    assert e.value.code == B.FMM_ERR_UNSUPPORTED

@@ -387,3 +387,35 @@ def test_sampled_mode_matches_full():
     part = oracle.fmm(pos, q, box, depth=3, n=4, continuous=True, periodic=True, sample=s)
     np.testing.assert_allclose(part["phi"], full["phi"][s], rtol=1e-14)
     np.testing.assert_allclose(part["F"], full["F"][s], rtol=1e-13, atol=1e-13)
+
+
+def test_reduced_arrangement_trend():
+    """§4.1: with the n-division points moved inside the cell (spacing x 1/1.2
+    about the centre) the potential error falls at order 4, and the gain is
+    gone from order 6 on.  Relative L2 error of the potentials against the
+    direct sum (the paper's Error1, a mean of relative errors, is dominated by
+    particles whose exact potential is near zero), 23040 random +-1 charges in
+    8^3 finest cells, two seeds."""
+    ratios = {4: [], 6: []}
+    for seed in (11, 12):
+        pos, q, box = inputs.uniform_pm1(23040, seed)
+        pd, _ = oracle.direct(pos, q, box)
+        for n in ratios:
+            e = [np.linalg.norm(oracle.fmm(pos, q, box, depth=3, n=n, keep=False, grid_scale=s)["phi"] - pd)
+                 for s in (1.0, 1 / 1.2)]
+            ratios[n].append(e[1] / e[0])
+    assert max(ratios[4]) < 0.9, ratios
+    assert min(ratios[6]) > 0.9, ratios
+
+
+def test_reduced_arrangement_is_still_a_replacement():
+    """The reduced points are still n-division points of a (smaller) segment:
+    replacement keeps the charge and the moments below degree n (eq. Lag2), so
+    the FMM still converges to the direct sum as the order grows."""
+    pos, q, box = inputs.uniform_pm1(400, 33)
+    pd, _ = oracle.direct(pos, q, box)
+    errs = [np.linalg.norm(oracle.fmm(pos, q, box, depth=2, n=n, grid_scale=1 / 1.2)["phi"] - pd)
+            / np.linalg.norm(pd) for n in (3, 4, 5, 6)]
+    assert errs[-1] < 1e-3 and all(errs[k + 1] < errs[k] for k in range(3)), errs
+    with pytest.raises(ValueError):
+        oracle.fmm(pos, q, box, depth=2, n=4, continuous=True, grid_scale=1 / 1.2)
