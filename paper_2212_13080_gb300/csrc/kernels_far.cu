@@ -99,6 +99,79 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(Coef<real> C, int depth, const i
     if (threadIdx.x == 0) q_leaf[cell] = Q;
 }
 
+// Warp-per-cell form for p^3 <= 128: four finest cells per CTA, one warp each,
+// no block barriers.  Lane t computes the weights of the chunk's t-th charge
+// into the warp's shared-memory rows; every lane then accumulates its grid
+// nodes (lane, lane + 32, ...) over the chunk.  The cell's total charge: a warp
+// tree per chunk, chunks added with compensation.
+#define P2M_WARPS 4
+
+template <typename real, int P>
+__global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_warp(Coef<real> C, int depth, int ncell,
+                                                            const int *__restrict__ leaf_start,
+                                                            const typename Vec4<real>::T *__restrict__ s_pt,
+                                                            real *__restrict__ phi_leaf,
+                                                            real *__restrict__ q_leaf) {
+    constexpr int P3 = P * P * P;
+    constexpr int NO = (P3 + 31) / 32;
+    __shared__ real w[P2M_WARPS][32][3 * P + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int key = blockIdx.x * P2M_WARPS + warp;
+    if (key >= ncell) return;
+    int cx, cy, cz;
+    morton_decode((uint32_t)key, cx, cy, cz);
+    const int s0 = leaf_start[key], s1 = leaf_start[key + 1];
+    real (*ws)[3 * P + 1] = w[warp];
+    real acc[NO];
+#pragma unroll
+    for (int r = 0; r < NO; r++) acc[r] = 0;
+    real Q = 0, Qc = 0;
+    for (int c0 = s0; c0 < s1; c0 += 32) {
+        const int m = min(32, s1 - c0);
+        real qv = 0;
+        if (lane < m) {
+            typename Vec4<real>::T v = s_pt[c0 + lane];
+            real g[FMM_MAXP];
+            lag_weights(C, P, v.x, g);
+#pragma unroll
+            for (int i = 0; i < P; i++) ws[lane][i] = v.w * g[i];
+            lag_weights(C, P, v.y, g);
+#pragma unroll
+            for (int i = 0; i < P; i++) ws[lane][P + i] = g[i];
+            lag_weights(C, P, v.z, g);
+#pragma unroll
+            for (int i = 0; i < P; i++) ws[lane][2 * P + i] = g[i];
+            qv = v.w;
+        }
+        for (int o = 16; o >= 1; o >>= 1) qv += __shfl_down_sync(0xffffffffu, qv, o);
+        if (lane == 0) {
+            real y = qv - Qc, tt = Q + y;
+            Qc = (tt - Q) - y;
+            Q = tt;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < NO; r++) {
+            const int o = lane + 32 * r;
+            if (o < P3) {
+                const int i = o % P, j = (o / P) % P, k = o / (P * P);
+                real sum = acc[r];
+                for (int t = 0; t < m; t++) sum += ws[t][i] * ws[t][P + j] * ws[t][2 * P + k];
+                acc[r] = sum;
+            }
+        }
+        __syncwarp();
+    }
+    const int64_t cell = phi_cell(depth, cx, cy, cz);
+    real *out = phi_leaf + cell * P3;
+#pragma unroll
+    for (int r = 0; r < NO; r++) {
+        const int o = lane + 32 * r;
+        if (o < P3) out[o] = acc[r];
+    }
+    if (lane == 0) q_leaf[cell] = Q;
+}
+
 // ---------------------------------------------------------------------------
 // §2.2 step 2, eq. (threethree): Phi_parent = sum_h (G_hx (x) G_hy (x) G_hz) Phi_child_h
 // in the factored order: the x shift summed over the two x siblings (4 arrays),
@@ -472,13 +545,19 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
     const int ncell = (int)W.ncell;
     tr.begin(FMM_STAGE_P2M, st);
     switch (p) {
-#define CASE(PP) \
+#define WCASE(PP)                                                                                \
+    case PP:                                                                                     \
+        k_p2m_warp<real, PP><<<(ncell + P2M_WARPS - 1) / P2M_WARPS, 32 * P2M_WARPS, 0, st>>>(     \
+            C, depth, ncell, P.leaf_start, P.s_pt, phi_leaf, P.qlev + W.q_level[depth]);          \
+        break;
+#define CASE(PP)                                                                                 \
     case PP:                                                                                     \
         k_p2m<real, PP><<<ncell, P2M_BS, 0, st>>>(C, depth, P.leaf_start, P.s_pt, phi_leaf,      \
                                                   P.qlev + W.q_level[depth]);                    \
         break;
-        CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+        WCASE(2) WCASE(3) WCASE(4) WCASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
+#undef WCASE
     }
     tr.count();
     tr.end();

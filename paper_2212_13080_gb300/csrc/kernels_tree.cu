@@ -540,17 +540,20 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
     }
 }
 
+// total energy from the block partials: strided per-thread sums, warp trees,
+// then the warps' sums in order (fixed order: deterministic)
 __global__ void k_energy_final(const double *__restrict__ epart, int nb, double *energy) {
-    __shared__ double sh[1024];
+    __shared__ double sh[32];
     double s = 0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) s += epart[b];
-    sh[threadIdx.x] = s;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+        *energy = t;
     }
-    if (threadIdx.x == 0) *energy = sh[0];
 }
 
 __global__ void k_zero_energy(double *energy) { *energy = 0.0; }
