@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
     typedef typename Vec4<real>::T real4;
     constexpr int NC = FORCES ? 4 : 1;     // components per target
     constexpr int TG = 32 / NC;            // targets per transposed group
+    constexpr int TR = FORCES ? 2 : 8;     // targets per remainder group
     constexpr int NW = NF_BS / 32;
     constexpr int NF_TB = sizeof(real) == 8 ? 64 : 256;
     __shared__ real4 tpos[NF_TB];
@@ -292,7 +293,8 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
             __syncthreads();  // previous block's shared data consumed
             // targets padded to a whole group with inert ones: far from every
             // source, no charge, an origin no source has
-            const int ntp = (nt + TG - 1) / TG * TG;
+            // whole groups of TG, then the rest in groups of TR: pad to TR only
+            const int ntp = (nt + TR - 1) / TR * TR;
             for (int i = threadIdx.x; i < ntp; i += NF_BS) {
                 if (i < nt) {
                     tpos[i] = s_pt[t0 + tb + i];
@@ -304,7 +306,8 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
                 }
             }
             __syncthreads();
-            for (int g0 = 0; g0 < nt; g0 += TG) {
+            int g0 = 0;
+            for (; g0 + TG <= nt; g0 += TG) {
                 real acc[32];
 #pragma unroll
                 for (int u = 0; u < TG; u++) {
@@ -327,6 +330,30 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
 #pragma unroll
                 for (int r = 1; r < 32; r++) tot += tb_w[r * NF_TP + lane];
                 if (g0 + lane / NC < nt) wpart[warp][(g0 + lane / NC) * NC + lane % NC] = tot;
+            }
+            for (; g0 < nt; g0 += TR) {  // the remaining targets, TR at a time
+                real acc[TR * NC];
+#pragma unroll
+                for (int u = 0; u < TR; u++) {
+                    const real4 tv = tpos[g0 + u];
+                    const int to = tori[g0 + u];
+                    nf_pair<real, FORCES, GUARD, true>(tv, to, sx[0], sy[0], sz[0], sq[0], so[0], acc + u * NC,
+                                                       rp[0], rx[0], ry[0], rz[0]);
+#pragma unroll
+                    for (int k = 1; k < NF_KS; k++)
+                        nf_pair<real, FORCES, GUARD, false>(tv, to, sx[k], sy[k], sz[k], sq[k], so[k],
+                                                            acc + u * NC, rp[k], rx[k], ry[k], rz[k]);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int v = 0; v < TR * NC; v++) tb_w[lane * NF_TP + v] = acc[v];
+                __syncwarp();
+                if (lane < TR * NC) {
+                    real tot = tb_w[lane];
+#pragma unroll
+                    for (int r = 1; r < 32; r++) tot += tb_w[r * NF_TP + lane];
+                    if (g0 + lane / NC < nt) wpart[warp][(g0 + lane / NC) * NC + lane % NC] = tot;
+                }
             }
             __syncthreads();
             // target sums: the warps in order, then accumulated over passes
