@@ -63,7 +63,11 @@ class FMM:
             o.split_capacity = float(split_capacity)
         o.precision = _PREC[precision]
         o.force_mode = _FORCE[force_mode]
-        o.sync = int(bool(sync))
+        # the library call never waits here: with sync=True the status is read
+        # after the call (device inputs) or after the output copies (host inputs),
+        # one wait per call either way
+        self.sync = bool(sync)
+        o.sync = 0
         o.grid_scale = float(grid_scale)
         with torch.cuda.device(self.device):
             self._h = B.fmm_plan_create(self.box, self.depth, self.p, self.periodic, o, self.max_n)
@@ -130,6 +134,8 @@ class FMM:
                    ws.numel(), _stream(stream))
         res = {"potential": phi if potential else None, "energy": E if energy else None,
                "forces": F if forces else None}
+        if self.sync and not host:
+            self._check_status(ws, stream)
         if host:
             # results into pinned host buffers (kept by the plan), one wait at the end
             hb = self._host_out(n)
@@ -143,8 +149,14 @@ class FMM:
                 h.copy_(v, non_blocking=True)
                 out_h[k] = h
             stream_t.synchronize()
+            self._check_status(ws, stream)  # the stream is idle: a short read
             res = out_h
         return res
+
+    def _check_status(self, ws, stream):
+        rc = B.fmm_status(self._h, _ptr(ws), _stream(stream))
+        if rc:
+            raise FmmError(rc, "fmm_eval")
 
     def _host_out(self, n):
         hb = getattr(self, "_hbuf", None)
