@@ -45,13 +45,15 @@ __device__ __forceinline__ int64_t nf_cell(int cx, int cy, int cz, int dx, int d
 
 // ---------------------------------------------------------------------------
 // far field: phi_far = sum_ijk g_i(t_x) g_j(t_y) g_k(t_z) L_leaf[ijk] and
-// F_far = -q * 2^depth * grad_t phi_far.  One CTA per finest cell, L_leaf in
-// shared memory, one thread per charge.
+// F_far = -q * 2^depth * grad_t phi_far.  One CTA per four consecutive finest
+// cells (their charges are one contiguous range), L_leaf in shared memory, one
+// thread per charge.
 // ---------------------------------------------------------------------------
-#define L2P_BS 64
+#define L2P_BS 128
+#define L2P_LPC 4  // finest cells per CTA (consecutive keys: one contiguous charge range)
 
 template <typename real, int P, bool FORCES>
-__global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int periodic,
+__global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int periodic, int ncell,
                                                 const int *__restrict__ leaf_start,
                                                 const typename Vec4<real>::T *__restrict__ s_pt,
                                                 const real *__restrict__ loc_leaf,
@@ -60,26 +62,35 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
                                                 typename Vec4<real>::T *__restrict__ out_pt) {
     typedef typename Vec4<real>::T real4;
     constexpr int P3 = P * P * P;
-    __shared__ real Ls[P3];
-    __shared__ int slot_ok[NF_SEGS - 1];
-    const uint32_t key = blockIdx.x;
-    const int s0 = leaf_start[key], s1 = leaf_start[key + 1];
-    if (s0 == s1) return;
-    int cx, cy, cz;
-    morton_decode(key, cx, cy, cz);
-    const real *src = loc_leaf + loc_cell(depth, cx, cy, cz) * P3;
-    for (int o = threadIdx.x; o < P3; o += blockDim.x) Ls[o] = src[o];
-    // slot d - 1 of this cell's charges was written by the cell (this cell -
+    __shared__ real Ls[L2P_LPC][P3];
+    __shared__ int slot_ok[L2P_LPC][NF_SEGS - 1];
+    __shared__ int lst[L2P_LPC + 1];
+    const int k0 = blockIdx.x * L2P_LPC;
+    const int nleaf = min(L2P_LPC, ncell - k0);
+    if (threadIdx.x <= L2P_LPC) lst[threadIdx.x] = leaf_start[min(k0 + (int)threadIdx.x, ncell)];
+    for (int e = threadIdx.x; e < nleaf * P3; e += blockDim.x) {
+        const int j = e / P3, o = e % P3;
+        int cx, cy, cz;
+        morton_decode((uint32_t)(k0 + j), cx, cy, cz);
+        Ls[j][o] = loc_leaf[loc_cell(depth, cx, cy, cz) * P3 + o];
+    }
+    // slot d - 1 of a cell's charges was written by the cell (that cell -
     // delta_d), d = 1..13, if it exists and holds charges
-    if (threadIdx.x < NF_SEGS - 1) {
-        int dx, dy, dz;
-        nf_delta(threadIdx.x + 1, dx, dy, dz);
+    if (threadIdx.x < nleaf * (NF_SEGS - 1)) {
+        const int j = threadIdx.x / (NF_SEGS - 1), d = threadIdx.x % (NF_SEGS - 1);
+        int cx, cy, cz, dx, dy, dz;
+        morton_decode((uint32_t)(k0 + j), cx, cy, cz);
+        nf_delta(d + 1, dx, dy, dz);
         const int64_t a = nf_cell(cx, cy, cz, -dx, -dy, -dz, 1 << depth, periodic);
-        slot_ok[threadIdx.x] = a >= 0 && leaf_start[a + 1] > leaf_start[a];
+        slot_ok[j][d] = a >= 0 && leaf_start[a + 1] > leaf_start[a];
     }
     __syncthreads();
     const real S = (real)(1 << depth);
-    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    for (int s = lst[0] + threadIdx.x; s < lst[nleaf]; s += blockDim.x) {
+        int lf = 0;  // which of the CTA's cells holds charge s
+        while (s >= lst[lf + 1]) lf++;
+        const real *Lc = Ls[lf];
+        const int *okc = slot_ok[lf];
         typename Vec4<real>::T v = s_pt[s];
         real gx[FMM_MAXP], gy[FMM_MAXP], gz[FMM_MAXP], dx[FMM_MAXP], dy[FMM_MAXP], dz[FMM_MAXP];
         if (FORCES) {
@@ -100,7 +111,7 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
                 real rx = 0, rdx = 0;
 #pragma unroll
                 for (int i = 0; i < P; i++) {
-                    real Lv = Ls[(k * P + j) * P + i];
+                    real Lv = Lc[(k * P + j) * P + i];
                     rx += gx[i] * Lv;
                     if (FORCES) rdx += dx[i] * Lv;
                 }
@@ -122,7 +133,7 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
         real4 o = out_pt[s];
 #pragma unroll
         for (int d = 0; d < NF_SEGS - 1; d++) {
-            if (!slot_ok[d]) continue;
+            if (!okc[d]) continue;
             const real4 r = react[d * rstride + s];
             o.x += r.x;
             o.y += r.y;
@@ -471,11 +482,11 @@ void launch_l2p(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const W
 #define CASE(PP)                                                                                 \
     case PP:                                                                                     \
         if (forces)                                                                              \
-            k_l2p<real, PP, true><<<ncell, L2P_BS, 0, st>>>(C, depth, g.periodic, P.leaf_start,  \
+            k_l2p<real, PP, true><<<(ncell + L2P_LPC - 1) / L2P_LPC, L2P_BS, 0, st>>>(C, depth, g.periodic, ncell, P.leaf_start,  \
                                                            P.s_pt, loc_leaf, P.react, W.cap,    \
                                                            P.out_pt);                           \
         else                                                                                     \
-            k_l2p<real, PP, false><<<ncell, L2P_BS, 0, st>>>(C, depth, g.periodic, P.leaf_start, \
+            k_l2p<real, PP, false><<<(ncell + L2P_LPC - 1) / L2P_LPC, L2P_BS, 0, st>>>(C, depth, g.periodic, ncell, P.leaf_start, \
                                                             P.s_pt, loc_leaf, P.react, W.cap,   \
                                                             P.out_pt);                          \
         break;
