@@ -19,6 +19,13 @@ fmm_oracle.c:
   5. near field over the 27 neighbouring cells,
   +  combination of the split charges back into their particles.
 
+`fmm(..., shift_free=True)` takes App. A.2 instead of steps 2-4: every
+cell's grid charges and functional are taken with respect to the box, the
+upward pass sums children, the interaction lists apply the shift-free
+bilinear forms BB_{C~,C} (target and source shifted from the box,
+shift_{S->C} the inverse of shift_{C->S}), and the downward pass is the
+identity.
+
 The energy is E = 1/2 sum_i q_i phi_i, phi_i the potential at particle i from
 every other particle (steps 4 and 5 each count every pair from both sides).
 
@@ -70,6 +77,16 @@ def lib():
         L.orc_m2m.argtypes = [i32, i32, i32, P]
         L.orc_downward.argtypes = [i32, i32, i32, P, P, P, P]
         L.orc_evaluate.argtypes = [i32, i32, i32, i64, P, P, P, P, P, P, P, P, P, P]
+        L.orc_sf_shift_to_box.argtypes = [i32, i32, i32, P]
+        L.orc_sf_shift_from_box.argtypes = [i32, i32, i32, P]
+        L.orc_sf_shift_from_box.restype = i32
+        L.orc_sf_p2m.argtypes = [i32, i32, P, P, P, P, P]
+        L.orc_sf_upward.argtypes = [i32, i32, i32, P]
+        L.orc_sf_bilinear.argtypes = [i32, i32, P, P, P, P]
+        L.orc_sf_bilinear.restype = i32
+        L.orc_sf_downward.argtypes = [i32, i32, i32, P, P, P, P]
+        L.orc_sf_downward.restype = i32
+        L.orc_sf_evaluate.argtypes = [i32, i32, i32, i64, P, P, P, P, P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -136,6 +153,36 @@ def lattice_kernel(n):
 
 def lattice_psi(r):
     return lib().orc_lattice_psi(float(r[0]), float(r[1]), float(r[2]))
+
+
+def sf_shift_to_box(n, l, c):
+    """App. A.2: shift_{C->S} along one axis for the level-l cell at
+    coordinate c, G[b, i] = g_b((c + a_i) / 2^l)."""
+    G = np.empty((n, n))
+    lib().orc_sf_shift_to_box(n, l, c, _p(G))
+    return G
+
+
+def sf_shift_from_box(n, l, c):
+    """App. A.2: shift_{S->C} along one axis (the inverse of sf_shift_to_box,
+    by elimination), H[i, b]."""
+    H = np.empty((n, n))
+    if lib().orc_sf_shift_from_box(n, l, c, _p(H)):
+        raise ArithmeticError("singular shift")
+    return H
+
+
+def sf_bilinear(n, l, ct, cs, o):
+    """App. A.2: the matrix of BB_{C~,C} (target cell ct, source cell cs,
+    offset o before wrapping, level l, unit-box units), box-node indices
+    [target, source]."""
+    n3 = n ** 3
+    B = np.empty((n3, n3))
+    a = lambda v: np.ascontiguousarray(v, dtype=np.int32)
+    ct, cs, o = a(ct), a(cs), a(o)
+    if lib().orc_sf_bilinear(n, l, _p(ct), _p(cs), _p(o), _p(B)):
+        raise ArithmeticError("singular shift")
+    return B
 
 
 def replace(n, t, q):
@@ -207,22 +254,24 @@ def level_offset(n, l):
 
 
 def fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sample=None,
-        keep=True, grid_scale=1.0):
+        keep=True, grid_scale=1.0, shift_free=False):
     """Runs the oracle FMM; grid_scale < 1 takes the reduced arrangement of the
-    n-division points (§4.1: spacing times grid_scale about the cell centre).
-    See _fmm for the other arguments."""
+    n-division points (§4.1: spacing times grid_scale about the cell centre);
+    shift_free takes the bilinear forms without shifts of App. A.2 (grid
+    charges and functionals of every cell with respect to the box).  See _fmm
+    for the other arguments."""
     if continuous and grid_scale != 1.0:
         raise ValueError("the reduced arrangement is defined for the plain form")
     L_ = lib()
     L_.orc_set_grid_scale(float(grid_scale))
     try:
-        return _fmm(pos, q, box, depth, n, periodic, continuous, dt, sample, keep)
+        return _fmm(pos, q, box, depth, n, periodic, continuous, dt, sample, keep, shift_free)
     finally:
         L_.orc_set_grid_scale(1.0)
 
 
 def _fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sample=None,
-         keep=True):
+         keep=True, shift_free=False):
     """Runs the oracle FMM.
 
     pos: (N,3) float32 positions, q: (N,) float32 charges, box = (x0,y0,z0,L).
@@ -231,6 +280,9 @@ def _fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sampl
     sample: optional particle indices; then only the outputs of those
         particles are computed (upward pass in full, downward pass and
         evaluation only where those particles need them) and E is None.
+
+    shift_free: App. A.2; Phi and L of the result are then the box-basis
+        vectors Phi^S and L^S of every cell.
 
     Returns a dict with phi (potential per unit charge), F (adjoint force),
     F_paper, E (physical units), and the intermediates when keep=True.
@@ -285,9 +337,13 @@ def _fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sampl
 
     # step 2: upward pass
     Phi = np.zeros(level_offset(n, depth + 1))
-    L_.orc_p2m(n, depth, _p(st), _p(sq), _p(start), _p(Phi))
     lmin = 0 if periodic else 2
-    L_.orc_m2m(n, depth, lmin, _p(Phi))
+    if shift_free:
+        L_.orc_sf_p2m(n, depth, _p(st), _p(scell), _p(sq), _p(start), _p(Phi))
+        L_.orc_sf_upward(n, depth, lmin, _p(Phi))
+    else:
+        L_.orc_p2m(n, depth, _p(st), _p(sq), _p(start), _p(Phi))
+        L_.orc_m2m(n, depth, lmin, _p(Phi))
 
     # step 3: downward pass
     Klat = lattice_kernel(n) if periodic else None
@@ -308,16 +364,22 @@ def _fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sampl
         ptr_t = ctypes.c_void_p * (depth + 1)
         need_ptrs = ptr_t(*[a.ctypes.data for a in need_arrays])
     Lv = np.zeros_like(Phi)
-    L_.orc_downward(n, depth, int(periodic), _p(Phi), _p(Lv),
-                    ctypes.cast(need_ptrs, ctypes.c_void_p) if need_ptrs is not None else None,
-                    _p(Klat) if Klat is not None else None)
+    need_arg = ctypes.cast(need_ptrs, ctypes.c_void_p) if need_ptrs is not None else None
+    if shift_free:
+        if L_.orc_sf_downward(n, depth, int(periodic), _p(Phi), _p(Lv), need_arg,
+                              _p(Klat) if Klat is not None else None):
+            raise ArithmeticError("singular shift")
+    else:
+        L_.orc_downward(n, depth, int(periodic), _p(Phi), _p(Lv), need_arg,
+                        _p(Klat) if Klat is not None else None)
 
     # steps 4-5 at every charge
     phi_pt = np.zeros(npts)
     F_pt = np.zeros((npts, 3))
     ncoinc = ctypes.c_int64(0)
-    L_.orc_evaluate(n, depth, int(periodic), npts, _p(st), _p(scell), _p(sq), _p(sorigin),
-                    _p(start), _p(Lv), _p(mask), _p(phi_pt), _p(F_pt), ctypes.byref(ncoinc))
+    evaluate = L_.orc_sf_evaluate if shift_free else L_.orc_evaluate
+    evaluate(n, depth, int(periodic), npts, _p(st), _p(scell), _p(sq), _p(sorigin),
+             _p(start), _p(Lv), _p(mask), _p(phi_pt), _p(F_pt), ctypes.byref(ncoinc))
 
     # split charges back into their particles
     inv = np.empty(npts, np.int64)

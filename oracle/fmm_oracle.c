@@ -715,6 +715,56 @@ void orc_downward(int n, int depth, int periodic, const double *Phi, double *L,
 /* field over the cell itself and its 26 neighbours                          */
 /* ------------------------------------------------------------------------ */
 
+/* Step 5 at sorted charge s: the direct sum over the charges of its cell and
+ * of the 26 neighbours (no second neighbours, §1), skipping charges of the
+ * same original particle (the split charges of one particle do not interact
+ * with each other).  Coincident charges of different particles contribute
+ * nothing and are counted in *coinc.  out = (phi per unit charge, F). */
+static void near_field(int depth, int periodic, int64_t s, const double *st, const int32_t *scell,
+                       const double *sq, const int64_t *sorigin, const int64_t *start,
+                       double out[4], int64_t *coinc)
+{
+    const int S = 1 << depth;
+    const double w = 1.0 / (double)S;
+    int cx = scell[3 * s], cy = scell[3 * s + 1], cz = scell[3 * s + 2];
+    double pn = 0.0, nfx = 0.0, nfy = 0.0, nfz = 0.0;
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                int nx = cx + dx, ny = cy + dy, nz = cz + dz;
+                if (periodic) {
+                    nx = (nx + S) % S;
+                    ny = (ny + S) % S;
+                    nz = (nz + S) % S;
+                } else if (nx < 0 || ny < 0 || nz < 0 || nx >= S || ny >= S || nz >= S) {
+                    continue;
+                }
+                uint32_t key = morton3(nx, ny, nz, depth);
+                for (int64_t r = start[key]; r < start[key + 1]; r++) {
+                    if (sorigin[r] == sorigin[s]) continue;
+                    /* separation in unit-box units, neighbour cell at offset (dx,dy,dz) */
+                    double rx = (st[3 * s] - st[3 * r] - dx) * w;
+                    double ry = (st[3 * s + 1] - st[3 * r + 1] - dy) * w;
+                    double rz = (st[3 * s + 2] - st[3 * r + 2] - dz) * w;
+                    double r2 = rx * rx + ry * ry + rz * rz;
+                    if (r2 == 0.0) {
+                        (*coinc)++;
+                        continue;
+                    }
+                    double rr = sqrt(r2);
+                    pn += sq[r] / rr;
+                    double c = sq[s] * sq[r] / (r2 * rr);
+                    nfx += c * rx;
+                    nfy += c * ry;
+                    nfz += c * rz;
+                }
+            }
+    out[0] = pn;
+    out[1] = nfx;
+    out[2] = nfy;
+    out[3] = nfz;
+}
+
 /* For every sorted charge s (or those with mask[s] set):
  *   far:  phi_far = Psi_leaf(g(x_s)) = sum_ijk g_ijk(x_s) L_leaf[ijk]
  *         (step 4 per unit charge), and the force Psi_leaf(v'_a) with
@@ -731,7 +781,6 @@ void orc_evaluate(int n, int depth, int periodic, int64_t npts, const double *st
                   double *F, int64_t *ncoinc)
 {
     const int n3 = n * n * n, S = 1 << depth;
-    const double w = 1.0 / (double)S;
     const double *Ll = L + level_offset(n, depth);
     int64_t coinc = 0;
 #pragma omp parallel for schedule(dynamic, 256) reduction(+ : coinc)
@@ -759,42 +808,316 @@ void orc_evaluate(int n, int depth, int periodic, int64_t npts, const double *st
                 }
         /* d/du = 2^depth d/dt */
         double fx = -sq[s] * gfx * S, fy = -sq[s] * gfy * S, fz = -sq[s] * gfz * S;
-        double pn = 0.0, nfx = 0.0, nfy = 0.0, nfz = 0.0;
-        for (int dz = -1; dz <= 1; dz++)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++) {
-                    int nx = cx + dx, ny = cy + dy, nz = cz + dz;
-                    if (periodic) {
-                        nx = (nx + S) % S;
-                        ny = (ny + S) % S;
-                        nz = (nz + S) % S;
-                    } else if (nx < 0 || ny < 0 || nz < 0 || nx >= S || ny >= S || nz >= S) {
-                        continue;
-                    }
-                    uint32_t key = morton3(nx, ny, nz, depth);
-                    for (int64_t r = start[key]; r < start[key + 1]; r++) {
-                        if (sorigin[r] == sorigin[s]) continue;
-                        /* separation in unit-box units, neighbour cell at offset (dx,dy,dz) */
-                        double rx = (st[3 * s] - st[3 * r] - dx) * w;
-                        double ry = (st[3 * s + 1] - st[3 * r + 1] - dy) * w;
-                        double rz = (st[3 * s + 2] - st[3 * r + 2] - dz) * w;
-                        double r2 = rx * rx + ry * ry + rz * rz;
-                        if (r2 == 0.0) {
-                            coinc++;
-                            continue;
-                        }
-                        double rr = sqrt(r2);
-                        pn += sq[r] / rr;
-                        double c = sq[s] * sq[r] / (r2 * rr);
-                        nfx += c * rx;
-                        nfy += c * ry;
-                        nfz += c * rz;
-                    }
-                }
+        double nf[4];
+        near_field(depth, periodic, s, st, scell, sq, sorigin, start, nf, &coinc);
+        double pn = nf[0], nfx = nf[1], nfy = nf[2], nfz = nf[3];
         phi[s] = pf + pn;
         F[3 * s] = fx + nfx;
         F[3 * s + 1] = fy + nfy;
         F[3 * s + 2] = fz + nfz;
+    }
+    if (ncoinc) *ncoinc = coinc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* App. A.2: bilinear forms without shifts                                   */
+/* ------------------------------------------------------------------------ */
+/*
+ * Every cell C's grid charges are taken with respect to the whole box S,
+ * Phi^S_C = shift_{C->S}(Phi_C): the same vector as replacing C's point
+ * charges directly with respect to S.  So the upward pass is a sum of the
+ * children's vectors, and with
+ *     BB_{C,C~}(v, w) = B_{C,C~}(shift_{S->C}(v), shift_{S->C~}(w))
+ * the far field is a sum of BB over the interaction lists; the functional of
+ * a cell, also taken with respect to S, passes to the children unchanged
+ * (the downward pass is the identity).  shift_{S->C} is the inverse of
+ * shift_{C->S}; it extrapolates from C to S and grows like 2^{l(n-1)}.
+ */
+
+/* shift_{C->S} along one axis for the cell of level l at coordinate c: C's
+ * node a_i lies at (c + a_i)/2^l in box coordinates, and replacing a charge
+ * there with respect to S gives the box weights g_b((c + a_i)/2^l).
+ * G[b*n + i]. */
+void orc_sf_shift_to_box(int n, int l, int c, double *G)
+{
+    double g[ORC_MAXN];
+    const double h = ldexp(1.0, -l);
+    for (int i = 0; i < n; i++) {
+        orc_lagrange(n, h * ((double)c + tau(n, i)), g);
+        for (int b = 0; b < n; b++) G[b * n + i] = g[b];
+    }
+}
+
+/* Inverse of the n x n matrix A by Gauss-Jordan elimination with partial
+ * pivoting; returns 0, or 1 if a pivot is zero. */
+static int invert(int n, const double *A, double *X)
+{
+    double M[ORC_MAXN][2 * ORC_MAXN];
+    for (int r = 0; r < n; r++)
+        for (int c = 0; c < n; c++) {
+            M[r][c] = A[r * n + c];
+            M[r][n + c] = (r == c) ? 1.0 : 0.0;
+        }
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++)
+            if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+        if (M[piv][c] == 0.0) return 1;
+        if (piv != c)
+            for (int k = 0; k < 2 * n; k++) {
+                double t = M[c][k];
+                M[c][k] = M[piv][k];
+                M[piv][k] = t;
+            }
+        double d = M[c][c];
+        for (int k = 0; k < 2 * n; k++) M[c][k] /= d;
+        for (int r = 0; r < n; r++) {
+            if (r == c) continue;
+            double f = M[r][c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < 2 * n; k++) M[r][k] -= f * M[c][k];
+        }
+    }
+    for (int r = 0; r < n; r++)
+        for (int c = 0; c < n; c++) X[r * n + c] = M[r][n + c];
+    return 0;
+}
+
+/* shift_{S->C} along one axis: the inverse of orc_sf_shift_to_box,
+ * H[i*n + b] (cell node i, box node b).  Returns 0 or 1 (singular). */
+int orc_sf_shift_from_box(int n, int l, int c, double *H)
+{
+    double G[ORC_MAXN * ORC_MAXN];
+    orc_sf_shift_to_box(n, l, c, G);
+    return invert(n, G, H);
+}
+
+/* Replacement of the charges of every finest cell directly with respect to
+ * the box: Phi^S_leaf[i,j,k] = sum_l q_l g_i(X_l) g_j(Y_l) g_k(Z_l), X the
+ * box coordinate (c + t)/2^depth of a charge at cell-local t.  Writes level
+ * `depth` of PhiS (natural cell order). */
+void orc_sf_p2m(int n, int depth, const double *st, const int32_t *scell, const double *sq,
+                const int64_t *start, double *PhiS)
+{
+    const int64_t ncell = (int64_t)1 << (3 * depth);
+    const int n3 = n * n * n, S = 1 << depth;
+    const double h = 1.0 / (double)S;
+    double *P = PhiS + level_offset(n, depth);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t key = 0; key < ncell; key++) {
+        int cx, cy, cz;
+        demorton3((uint32_t)key, depth, &cx, &cy, &cz);
+        double *v = P + (((int64_t)cz * S + cy) * S + cx) * n3;
+        for (int a = 0; a < n3; a++) v[a] = 0.0;
+        for (int64_t s = start[key]; s < start[key + 1]; s++) {
+            double gx[ORC_MAXN], gy[ORC_MAXN], gz[ORC_MAXN];
+            orc_lagrange(n, h * ((double)scell[3 * s] + st[3 * s]), gx);
+            orc_lagrange(n, h * ((double)scell[3 * s + 1] + st[3 * s + 1]), gy);
+            orc_lagrange(n, h * ((double)scell[3 * s + 2] + st[3 * s + 2]), gz);
+            for (int k = 0; k < n; k++)
+                for (int j = 0; j < n; j++)
+                    for (int i = 0; i < n; i++)
+                        v[(k * n + j) * n + i] += sq[s] * gx[i] * gy[j] * gz[k];
+        }
+    }
+}
+
+/* Upward pass of App. A.2: Phi^S_parent = sum of the eight children's Phi^S,
+ * from level `depth` up to level `lmin`. */
+void orc_sf_upward(int n, int depth, int lmin, double *PhiS)
+{
+    const int n3 = n * n * n;
+    for (int l = depth; l > lmin; l--) {
+        const int S = 1 << l, Sp = S >> 1;
+        const double *C = PhiS + level_offset(n, l);
+        double *P = PhiS + level_offset(n, l - 1);
+#pragma omp parallel for schedule(static)
+        for (int64_t pc = 0; pc < (int64_t)Sp * Sp * Sp; pc++) {
+            int px = (int)(pc % Sp), py = (int)((pc / Sp) % Sp), pz = (int)(pc / ((int64_t)Sp * Sp));
+            double *v = P + pc * n3;
+            for (int e = 0; e < n3; e++) v[e] = 0.0;
+            for (int hz = 0; hz < 2; hz++)
+                for (int hy = 0; hy < 2; hy++)
+                    for (int hx = 0; hx < 2; hx++) {
+                        int cx = 2 * px + hx, cy = 2 * py + hy, cz = 2 * pz + hz;
+                        const double *w = C + (((int64_t)cz * S + cy) * S + cx) * n3;
+                        for (int e = 0; e < n3; e++) v[e] += w[e];
+                    }
+        }
+    }
+}
+
+/* out = BB v for the cells C~ (target, coordinates ct) and C (source, cs) of
+ * level l at offset o = C - C~ before any periodic wrap: the box-basis
+ * vector v of C is shifted to C (shift_{S->C}), the bilinear form of the two
+ * unit cells at offset o, scaled by 2^l to unit-box units, is applied, and
+ * the result is taken back to the box basis with the transpose of
+ * shift_{S->C~}.  Hs/Ht: the per-axis shift_{S->C} matrices of source and
+ * target (orc_sf_shift_from_box); K: the unit kernel of offset o. */
+static void sf_apply(int n, int l, const double *const Hs[3], const double *const Ht[3],
+                     const double *K, const double *v, double *out)
+{
+    const int n3 = n * n * n;
+    double a[ORC_MAXN * ORC_MAXN * ORC_MAXN], b[ORC_MAXN * ORC_MAXN * ORC_MAXN];
+    shift_axis(n, Hs[0], 0, v, a);
+    shift_axis(n, Hs[1], 1, a, b);
+    shift_axis(n, Hs[2], 2, b, a);
+    const double scale = ldexp(1.0, l);
+    for (int r = 0; r < n3; r++) {
+        double s = 0.0;
+        for (int c = 0; c < n3; c++) s += K[(int64_t)r * n3 + c] * a[c];
+        b[r] = scale * s;
+    }
+    shift_axis_t(n, Ht[0], 0, b, a);
+    shift_axis_t(n, Ht[1], 1, a, b);
+    shift_axis_t(n, Ht[2], 2, b, out);
+}
+
+/* The matrix of BB for target cell ct, source cell cs (wrapped coordinates)
+ * at offset o, level l: B[r*n^3 + c] = (BB e_c)[r], box-node indices.
+ * Returns 0, or 1 if a shift is singular. */
+int orc_sf_bilinear(int n, int l, const int *ct, const int *cs, const int *o, double *B)
+{
+    const int n3 = n * n * n;
+    double hs[3][ORC_MAXN * ORC_MAXN], ht[3][ORC_MAXN * ORC_MAXN];
+    for (int ax = 0; ax < 3; ax++)
+        if (orc_sf_shift_from_box(n, l, cs[ax], hs[ax]) || orc_sf_shift_from_box(n, l, ct[ax], ht[ax]))
+            return 1;
+    const double *Hs[3] = {hs[0], hs[1], hs[2]}, *Ht[3] = {ht[0], ht[1], ht[2]};
+    double *K = (double *)malloc(sizeof(double) * (size_t)n3 * n3);
+    double *e = (double *)calloc((size_t)n3, sizeof(double));
+    double *col = (double *)malloc(sizeof(double) * (size_t)n3);
+    orc_m2l_kernel(n, o[0], o[1], o[2], K);
+    for (int c = 0; c < n3; c++) {
+        e[c] = 1.0;
+        sf_apply(n, l, Hs, Ht, K, e, col);
+        e[c] = 0.0;
+        for (int r = 0; r < n3; r++) B[(int64_t)r * n3 + c] = col[r];
+    }
+    free(K);
+    free(e);
+    free(col);
+    return 0;
+}
+
+/* Downward pass of App. A.2 on box-basis functionals L^S:
+ *   level 0: zero (open form), or the box against its far images (periodic
+ *            form, §4.2: the box basis is the level-0 cell's basis);
+ *   level l: L^S_C~ = L^S_parent (the identity) + sum over the interaction
+ *            list of BB_{C~,C} Phi^S_C, the same lists as orc_downward.
+ * need[l] as in orc_downward.  Returns 0, or 1 if a shift is singular. */
+int orc_sf_downward(int n, int depth, int periodic, const double *PhiS, double *LS,
+                    const uint8_t *const *need, const double *Klat)
+{
+    const int n3 = n * n * n;
+    if (periodic) {
+        double *L0 = LS + level_offset(n, 0);
+        const double *P0 = PhiS + level_offset(n, 0);
+        for (int a = 0; a < n3; a++) {
+            double s = 0.0;
+            for (int b = 0; b < n3; b++) s += Klat[(int64_t)a * n3 + b] * P0[b];
+            L0[a] = s;
+        }
+    } else {
+        for (int e = 0; e < n3; e++) LS[level_offset(n, 0) + e] = 0.0;
+    }
+    /* unit kernels K_o, |o|_inf <= 3 */
+    double *Kall = (double *)malloc(sizeof(double) * 343 * (size_t)n3 * n3);
+    for (int oi = 0; oi < 343; oi++)
+        orc_m2l_kernel(n, oi % 7 - 3, (oi / 7) % 7 - 3, oi / 49 - 3, Kall + (int64_t)oi * n3 * n3);
+    int bad = 0;
+    for (int l = 1; l <= depth; l++) {
+        const int S = 1 << l, Sp = S >> 1;
+        const double *Pl = PhiS + level_offset(n, l);
+        double *Ll = LS + level_offset(n, l);
+        const double *Lp = LS + level_offset(n, l - 1);
+        const int do_m2l = periodic ? (l >= 1) : (l >= 2);
+        /* shift_{S->C} per axis coordinate of this level */
+        double *H = (double *)malloc(sizeof(double) * (size_t)S * n * n);
+        for (int c = 0; c < S; c++) bad |= orc_sf_shift_from_box(n, l, c, H + (size_t)c * n * n);
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t c = 0; c < (int64_t)S * S * S; c++) {
+            if (need && need[l] && !need[l][c]) continue;
+            int cx = (int)(c % S), cy = (int)((c / S) % S), cz = (int)(c / ((int64_t)S * S));
+            double *v = Ll + c * n3;
+            int px = cx >> 1, py = cy >> 1, pz = cz >> 1;
+            const double *w = Lp + (((int64_t)pz * Sp + py) * Sp + px) * n3;
+            for (int e = 0; e < n3; e++) v[e] = w[e];
+            if (!do_m2l) continue;
+            const double *Ht[3] = {H + (size_t)cx * n * n, H + (size_t)cy * n * n,
+                                   H + (size_t)cz * n * n};
+            double y[ORC_MAXN * ORC_MAXN * ORC_MAXN];
+            for (int sz = 2 * (pz - 1); sz <= 2 * (pz + 1) + 1; sz++)
+                for (int sy = 2 * (py - 1); sy <= 2 * (py + 1) + 1; sy++)
+                    for (int sx = 2 * (px - 1); sx <= 2 * (px + 1) + 1; sx++) {
+                        int ox = sx - cx, oy = sy - cy, oz = sz - cz;
+                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+                        int wx = sx, wy = sy, wz = sz;
+                        if (periodic) {
+                            wx = ((sx % S) + S) % S;
+                            wy = ((sy % S) + S) % S;
+                            wz = ((sz % S) + S) % S;
+                        } else if (sx < 0 || sy < 0 || sz < 0 || sx >= S || sy >= S || sz >= S) {
+                            continue;
+                        }
+                        const double *Hs[3] = {H + (size_t)wx * n * n, H + (size_t)wy * n * n,
+                                               H + (size_t)wz * n * n};
+                        int oi = ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3);
+                        const double *src = Pl + (((int64_t)wz * S + wy) * S + wx) * n3;
+                        sf_apply(n, l, Hs, Ht, Kall + (int64_t)oi * n3 * n3, src, y);
+                        for (int e = 0; e < n3; e++) v[e] += y[e];
+                    }
+        }
+        free(H);
+    }
+    free(Kall);
+    return bad;
+}
+
+/* Steps 4-5 with box-basis functionals: the far field at a charge is
+ * L^S_leaf . g(X) with the box weights at its box coordinate X = (c + t)/2^depth,
+ * and the far force -q dg/dX (box coordinates are unit-box units); the near
+ * field as orc_evaluate. */
+void orc_sf_evaluate(int n, int depth, int periodic, int64_t npts, const double *st,
+                     const int32_t *scell, const double *sq, const int64_t *sorigin,
+                     const int64_t *start, const double *LS, const uint8_t *mask, double *phi,
+                     double *F, int64_t *ncoinc)
+{
+    const int n3 = n * n * n, S = 1 << depth;
+    const double h = 1.0 / (double)S;
+    const double *Ll = LS + level_offset(n, depth);
+    int64_t coinc = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : coinc)
+    for (int64_t s = 0; s < npts; s++) {
+        if (mask && !mask[s]) continue;
+        int cx = scell[3 * s], cy = scell[3 * s + 1], cz = scell[3 * s + 2];
+        const double *v = Ll + (((int64_t)cz * S + cy) * S + cx) * n3;
+        double X = h * ((double)cx + st[3 * s]), Y = h * ((double)cy + st[3 * s + 1]),
+               Z = h * ((double)cz + st[3 * s + 2]);
+        double gx[ORC_MAXN], gy[ORC_MAXN], gz[ORC_MAXN];
+        double dx_[ORC_MAXN], dy_[ORC_MAXN], dz_[ORC_MAXN];
+        orc_lagrange(n, X, gx);
+        orc_lagrange(n, Y, gy);
+        orc_lagrange(n, Z, gz);
+        orc_lagrange_deriv(n, X, dx_);
+        orc_lagrange_deriv(n, Y, dy_);
+        orc_lagrange_deriv(n, Z, dz_);
+        double pf = 0.0, gfx = 0.0, gfy = 0.0, gfz = 0.0;
+        for (int k = 0; k < n; k++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) {
+                    double Lv = v[(k * n + j) * n + i];
+                    pf += gx[i] * gy[j] * gz[k] * Lv;
+                    gfx += dx_[i] * gy[j] * gz[k] * Lv;
+                    gfy += gx[i] * dy_[j] * gz[k] * Lv;
+                    gfz += gx[i] * gy[j] * dz_[k] * Lv;
+                }
+        double nf[4];
+        near_field(depth, periodic, s, st, scell, sq, sorigin, start, nf, &coinc);
+        phi[s] = pf + nf[0];
+        F[3 * s] = -sq[s] * gfx + nf[1];
+        F[3 * s + 1] = -sq[s] * gfy + nf[2];
+        F[3 * s + 2] = -sq[s] * gfz + nf[3];
     }
     if (ncoinc) *ncoinc = coinc;
 }

@@ -419,3 +419,104 @@ def test_reduced_arrangement_is_still_a_replacement():
     assert errs[-1] < 1e-3 and all(errs[k + 1] < errs[k] for k in range(3)), errs
     with pytest.raises(ValueError):
         oracle.fmm(pos, q, box, depth=2, n=4, continuous=True, grid_scale=1 / 1.2)
+
+
+# --- App. A.2: bilinear forms without shifts ------------------------------------
+
+def _box_kron(n, l, cx, cy, cz, mats):
+    """The per-axis matrices of cell (cx, cy, cz) combined on an n^3 vector
+    [k, j, i]: v -> (Mz (x) My (x) Mx) v."""
+    return lambda v: np.einsum("Kk,Jj,Ii,kji->KJI", mats(n, l, cz), mats(n, l, cy),
+                               mats(n, l, cx), v.reshape(n, n, n)).reshape(-1)
+
+
+@pytest.mark.parametrize("n,l", [(3, 2), (4, 3), (5, 2), (4, 1)])
+def test_sf_shift_from_box_closed_form(n, l):
+    """shift_{S->C} inverts shift_{C->S}; since the box basis is exact on
+    polynomials of degree < n, its (i, b) entry is the cell's basis function i
+    at the box node b in cell coordinates, g_i(2^l a_b - c)."""
+    a = oracle.nodes(n)
+    for c in range(1 << l):
+        H = oracle.sf_shift_from_box(n, l, c)
+        closed = oracle.lagrange(n, (1 << l) * a - c).T  # [i, b]
+        np.testing.assert_allclose(H, closed, rtol=1e-9, atol=1e-9 * np.abs(closed).max())
+        np.testing.assert_allclose(oracle.sf_shift_to_box(n, l, c) @ H, np.eye(n), atol=1e-9)
+    np.testing.assert_allclose(oracle.sf_shift_to_box(n, 0, 0), np.eye(n), atol=1e-15)
+
+
+@pytest.mark.parametrize("periodic,continuous", [(False, False), (True, True)])
+def test_sf_upward_equals_shifted_replacement(periodic, continuous):
+    """App. A.2: Phi^S_C = shift_{C->S}(Phi_C) equals replacing C's charges
+    directly with respect to the box, at the leaves and, the box basis being
+    additive over children, at every level of the upward pass."""
+    n, depth = 4, 3
+    pos, q, box = inputs.uniform_cont(1500, 11)
+    std = oracle.fmm(pos, q, box, depth, n, periodic=periodic, continuous=continuous)
+    sf = oracle.fmm(pos, q, box, depth, n, periodic=periodic, continuous=continuous,
+                    shift_free=True)
+    for l in range(0 if periodic else 2, depth + 1):
+        S = 1 << l
+        Pv = oracle.level_view(std["Phi"], n, l)
+        Ps = oracle.level_view(sf["Phi"], n, l)
+        for c in range(8 ** l):
+            cx, cy, cz = c % S, (c // S) % S, c // (S * S)
+            want = _box_kron(n, l, cx, cy, cz, oracle.sf_shift_to_box)(Pv[c])
+            np.testing.assert_allclose(Ps[c], want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
+
+
+@pytest.mark.parametrize("n,depth,periodic,continuous,tol", [
+    (4, 3, False, False, 1e-10),
+    (4, 3, True, True, 1e-10),
+    (5, 2, False, True, 1e-10),
+    (3, 4, True, False, 1e-9),
+])
+def test_sf_fmm_equals_shifted_fmm(n, depth, periodic, continuous, tol):
+    """App. A.2: B_{C,C~}(Phi_C, Phi_C~) = BB_{C,C~}(Phi^S_C, Phi^S_C~) and the
+    downward pass becomes the identity, so the two forms give the same
+    potentials, forces and energy up to the rounding of the extrapolating
+    shift_{S->C} (which grows with depth and order)."""
+    pos, q, box = inputs.uniform_cont(2500, 12)
+    std = oracle.fmm(pos, q, box, depth, n, periodic=periodic, continuous=continuous)
+    sf = oracle.fmm(pos, q, box, depth, n, periodic=periodic, continuous=continuous,
+                    shift_free=True)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(sf["phi"], std["phi"]) < tol
+    assert rel(sf["F"], std["F"]) < tol
+    assert rel(sf["F_paper"], std["F_paper"]) < tol
+    assert abs(sf["E"] - std["E"]) < tol * abs(std["E"])
+
+
+def _rep(n, x):
+    return np.einsum("pk,pj,pi->pkji", oracle.lagrange(n, x[:, 2]), oracle.lagrange(n, x[:, 1]),
+                     oracle.lagrange(n, x[:, 0])).reshape(len(x), -1)
+
+
+def test_sf_bilinear_matrix_and_fp32_conditioning():
+    """The matrix of BB_{C~,C} applied to box-basis charges and read with box
+    weights reproduces the shifted bilinear form of the two cells (§2.1.7),
+    and the far field it represents agrees with the direct 1/r sum to the
+    method's accuracy.  Rounded to FP32, the explicit form loses accuracy
+    with depth (shift_{S->C} extrapolates over 2^l cells): at order 4 about
+    1e-4 at level 2 and several percent at level 3."""
+    rng = np.random.default_rng(7)
+    n = 4
+    err32 = {}
+    for l in (2, 3):
+        S = 1 << l
+        ct, o = np.array([S // 2 - 1, S // 2, S // 2]), np.array([2, 1, 0])
+        cs = ct + o
+        B = oracle.sf_bilinear(n, l, ct, cs, o)
+        ts, tt = rng.random((40, 3)), rng.random((200, 3))
+        qs = rng.uniform(-1, 1, 40)
+        shifted = _rep(n, tt) @ (S * oracle.m2l_kernel(n, o) @ (qs @ _rep(n, ts)))
+        Wt, PhiS = _rep(n, (ct + tt) / S), qs @ _rep(n, (cs + ts) / S)
+        f64 = Wt @ (B @ PhiS)
+        f32 = (Wt.astype(np.float32) @ (B.astype(np.float32) @ PhiS.astype(np.float32)))
+        nr = np.linalg.norm(shifted)
+        assert np.linalg.norm(f64 - shifted) / nr < 1e-8
+        err32[l] = np.linalg.norm(f32.astype(np.float64) - shifted) / nr
+        d = np.linalg.norm((ct + tt)[:, None, :] - (cs + ts)[None, :, :], axis=2) / S
+        direct = (qs[None, :] / d).sum(1)
+        assert np.linalg.norm(f64 - direct) / np.linalg.norm(direct) < 5e-3
+    assert err32[2] < 1e-3
+    assert err32[3] > 1e-2
