@@ -35,6 +35,7 @@ METRIC = "FMM energy+forces Mparticles/s"
 UNIT = "Mparticles/s"
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 P2P_FLOPS_PER_PAIR = 20
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
 
 
 def _peaks():
@@ -648,6 +649,7 @@ def main():
         "clocks": clocks,
         "m2l_tensor": m2l_tc,
         "plain_fp32": plain,
+        "shift_free": shift_free_line(args.steps, dev, flush, stream) if world == 1 else None,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"], res["error_vs_fp64_oracle"] = cpu_baseline(args.workload, gpu_outputs)
@@ -657,6 +659,75 @@ def main():
     plan_e2e.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def shift_free_line(steps, dev, flush, stream):
+    """App. A.2 (bilinear forms without shifts) beside the shifted form, both
+    FP64, on 23,040 uniform +-1 charges (open, plain, depth 3, p 4: the size
+    of §3.1's runs and the depth the paper keeps the forms for).  The
+    dominant kernel, k_sf_m2l, streams one p^6 FP64 right part per cell pair
+    of the interaction lists: its roofline is that read against HBM, and its
+    FP64 multiply-adds against the nominal FP64 rate."""
+    import torch
+    from paper_2212_13080_gb300 import FMM, inputs
+    w = inputs.workload("uniform23k")
+    n, p = len(w["q"]), w["p"]
+    pos = torch.from_numpy(w["pos"]).to(dev)
+    q = torch.from_numpy(w["q"]).to(dev)
+    res, outs = {}, {}
+    for sf in (True, False):
+        t0 = time.perf_counter()
+        plan = FMM(w["box"], w["depth"], p, precision="fp64", shift_free=sf, max_n=n, sync=False)
+        torch.cuda.synchronize()
+        create_ms = (time.perf_counter() - t0) * 1e3
+        ws = plan.workspace(n)
+        out = {"potential": torch.empty(n, dtype=torch.float64, device=dev),
+               "energy": torch.empty(1, dtype=torch.float64, device=dev),
+               "forces": torch.empty((n, 3), dtype=torch.float64, device=dev)}
+        for _ in range(3):
+            plan.eval(pos, q, workspace=ws, out=out)
+        t = []
+        for _ in range(max(5, steps // 2)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.eval(pos, q, workspace=ws, out=out)
+            b.record(stream)
+            b.synchronize()
+            t.append(a.elapsed_time(b))
+        if plan_status(plan, ws):
+            raise SystemExit("shift-free line: evaluation failed")
+        plan.set_timing(True, serial=True)
+        iso, k = {}, 5
+        for _ in range(k):
+            flush.zero_()
+            plan.eval(pos, q, workspace=ws, out=out)
+            for s_, v in plan.stats()["stage_ms"].items():
+                iso[s_] = iso.get(s_, 0.0) + v / k
+        torch.cuda.synchronize()
+        outs[sf] = (out["potential"].cpu().numpy(), out["forces"].cpu().numpy())
+        res["shift_free" if sf else "shifted"] = {
+            "ms_per_step": statistics.mean(t), "value": n / (statistics.mean(t) * 1e-3) / 1e6,
+            "unit": UNIT, "plan_create_ms": create_ms, "stage_ms_isolated": iso}
+        plan.close()
+    import numpy as np
+    pairs = m2l_cell_pairs(w["depth"], False)
+    tab_bytes = pairs * p ** 6 * 8
+    m2l_ms = res["shift_free"]["stage_ms_isolated"]["m2l"]
+    hbm, _, _, peak_kind = _peaks()
+    gbs = tab_bytes / (m2l_ms * 1e-3) / 1e9
+    fp64 = 2.0 * p ** 6 * pairs / (m2l_ms * 1e-3) / 1e12
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    res.update({
+        "workload": "uniform23k: 23,040 uniform +-1, open, plain, depth 3, p 4, fp64",
+        "kernel": "k_sf_m2l", "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+        "frac": gbs / hbm, "peak_source": peak_kind,
+        "algorithmic": "%d cell pairs x p^6 FP64 right parts (%d bytes per step)" % (pairs, tab_bytes),
+        "fp64_tflops": fp64, "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
+        "fp64_frac_of_nominal": fp64 / FP64_NOMINAL_TFLOPS,
+        "rel_diff_vs_shifted": {"potential": rel(outs[True][0], outs[False][0]),
+                                "forces": rel(outs[True][1], outs[False][1])}})
+    return res
 
 
 def plan_status(plan, ws):

@@ -90,10 +90,21 @@ typedef struct {
                               "reduced" arrangement, e.g. 1/1.2); (0, 1]; <= 0 selects 1;
                               plain form only (continuous with a scale != 1:
                               FMM_ERR_UNSUPPORTED) */
+    int shift_free;        /* 1: App. A.2, bilinear forms without shifts.  Every cell's grid
+                              charges and functional are taken with respect to the box (the
+                              upward pass sums children, the downward pass is the identity),
+                              and the plan precomputes, on the device in FP64, one matrix
+                              BB = shift_{S->C~}^T K_o shift_{S->C} per (cell, interaction-list
+                              offset) of every level: 8 p^6 bytes each, plan-owned.
+                              shift_{S->C} extrapolates over 2^l cells, so the forms lose
+                              about 2(p-1) bits per level: FMM_PREC_FP64 only, p <= 5, and
+                              tables of at most 32 GiB (else FMM_ERR_UNSUPPORTED); the
+                              reduced arrangement and batched plans are not supported.
+                              0 (default): the shifted form of §2.2. */
 } fmm_opts_t;
 
 /* Fills *opts with the defaults (continuous 0, split_ratio 1/256, split_capacity 0
- * (automatic), precision FP32, adjoint forces, sync 1). */
+ * (automatic), precision FP32, adjoint forces, sync 1, grid_scale 1, shift_free 0). */
 void fmm_opts_default(fmm_opts_t *opts);
 
 /*
@@ -109,7 +120,10 @@ void fmm_opts_default(fmm_opts_t *opts);
  * bilinear-form kernels 1/|a - (o + b)| for |o|_inf <= 3 (eq. bilinear), and
  * (periodic) the Ewald lattice kernel of the box's far images; uploads them to
  * the current device.  The plan owns those tables (device memory freed by
- * fmm_plan_destroy).  Errors: FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA.
+ * fmm_plan_destroy).  With opts.shift_free it also builds the per-axis
+ * shift_{S->C} matrices and computes the App. A.2 forms on the device (FP64,
+ * synchronous).  Errors: FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA,
+ * FMM_ERR_UNSUPPORTED.
  */
 int fmm_plan_create(fmm_plan_t *plan, const double box[4], int depth, int p, int periodic,
                     const fmm_opts_t *opts, int64_t max_n);

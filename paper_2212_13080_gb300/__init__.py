@@ -42,13 +42,16 @@ class FMM:
     for precision="fp64".  Host tensors are copied to the device and the
     results back (the end-to-end path); host results are views of pinned
     buffers the plan keeps and overwrites on its next host call (clone to keep).
-    precision: "fp32" (SIMT contraction), "fp64", "tf32x3" (contraction of
-    levels >= 4 on the tcgen05 tensor cores, 3-pass split TF32; p = 4).
+    precision: "fp32" (SIMT contraction), "fp64", "tf32x3" / "tf32x1" /
+    "bf16x3" (bilinear forms of every level on the tcgen05 tensor cores).
+    grid_scale < 1: the reduced arrangement of the p-division points (§4.1).
+    shift_free: App. A.2, precomputed bilinear forms on box-basis grid charges
+    (precision "fp64", p <= 5).
     """
 
     def __init__(self, box, depth, p, periodic=False, continuous=False, split_ratio=None,
                  precision="fp32", force_mode="adjoint", max_n=1 << 20, split_capacity=None,
-                 sync=True, device=None, grid_scale=1.0):
+                 sync=True, device=None, grid_scale=1.0, shift_free=False):
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         self.box = tuple(float(x) for x in box)
@@ -69,6 +72,8 @@ class FMM:
         self.sync = bool(sync)
         o.sync = 0
         o.grid_scale = float(grid_scale)
+        o.shift_free = int(bool(shift_free))
+        self.shift_free = bool(shift_free)
         with torch.cuda.device(self.device):
             self._h = B.fmm_plan_create(self.box, self.depth, self.p, self.periodic, o, self.max_n)
         self.out_dtype = torch.float64 if precision == "fp64" else torch.float32

@@ -61,7 +61,7 @@ class fmm_opts_t(ctypes.Structure):
     _fields_ = [("continuous", ctypes.c_int), ("split_ratio", ctypes.c_double),
                 ("split_capacity", ctypes.c_double), ("precision", ctypes.c_int),
                 ("force_mode", ctypes.c_int), ("sync", ctypes.c_int),
-                ("grid_scale", ctypes.c_double)]
+                ("grid_scale", ctypes.c_double), ("shift_free", ctypes.c_int)]
 
 
 class fmm_stats_t(ctypes.Structure):

@@ -33,6 +33,10 @@ struct fmm_plan_s {
     int tc_mode;            // FMM_TC_*: split TF32 x3, TF32 x1, split BF16 x3
     int inject;             // FMM_INJECT_* for the next evaluation (test hook)
     bool shared;            // tables belong to another plan (batched systems)
+    void *sf_tab;           // App. A.2 forms of every level (shift-free plans), FP64
+    int64_t sf_base[FMM_MAXDEPTH + 2];  // first pair of every level in sf_tab
+    void *sf_H;             // per-axis shift_{S->C} of every level
+    int64_t sf_hoff[FMM_MAXDEPTH + 2];
     Coef<float> cf;
     Coef<double> cd;
     Geom geom;
@@ -459,6 +463,10 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     T.tc_khi_map = P->khi_map;
     T.tc_klo_map = P->klo_map;
     T.tc_kbar = (const float *)P->Kbar_tc;
+    T.sf_tab = (const double *)P->sf_tab;
+    T.sf_base = P->sf_base;
+    T.sf_H = (const double *)P->sf_H;
+    T.sf_hoff = P->sf_hoff;
     int rc = launch_downward<real>(g, C, ptr, W, T, F, tr);
     if (rc) return rc;
     if (S.far) {
@@ -514,6 +522,7 @@ void fmm_opts_default(fmm_opts_t *o) {
     o->force_mode = FMM_FORCE_ADJOINT;
     o->sync = 1;
     o->grid_scale = 1.0;
+    o->shift_free = 0;
 }
 
 const char *fmm_strerror(int s) {
@@ -559,6 +568,13 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     if (o.precision != FMM_PREC_FP32 && o.precision != FMM_PREC_FP64 && !tc_prec)
         return FMM_ERR_UNSUPPORTED;
     if (tc_prec && (p < 3 || p > 6)) return FMM_ERR_UNSUPPORTED;
+    // App. A.2 forms: FP64 (they extrapolate over 2^l cells), p <= 5, <= 32 GiB
+    if (o.shift_free) {
+        int64_t base[FMM_MAXDEPTH + 2];
+        if (o.precision != FMM_PREC_FP64 || p > 5 || o.grid_scale != 1.0 ||
+            fmm::sf_table_bytes(p, depth, periodic ? 1 : 0, base) > ((size_t)32 << 30))
+            return FMM_ERR_UNSUPPORTED;
+    }
     fmm_plan_s *P = new (std::nothrow) fmm_plan_s();
     if (!P) return FMM_ERR_OOM;
     P->depth = depth;
@@ -582,6 +598,7 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     g.periodic = P->periodic;
     g.continuous = o.continuous ? 1 : 0;
     g.force_mode = o.force_mode;
+    g.shift_free = o.shift_free ? 1 : 0;
     g.S = 1 << depth;
     for (int a = 0; a < 3; a++) g.x0[a] = (float)box[a];
     g.Lf = (float)box[3];
@@ -610,6 +627,8 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     }
     fmm::far_set_attributes();
     int rc = P->fp64 ? upload_tables<double>(P) : upload_tables<float>(P);
+    if (rc == FMM_OK && o.shift_free) rc = fmm::sf_build(p, depth, P->periodic, P->cd, &P->sf_tab, P->sf_base, &P->sf_H,
+                                                   P->sf_hoff);
     if (rc != FMM_OK) {
         fmm_plan_destroy(P);
         return rc;
@@ -640,6 +659,8 @@ void fmm_plan_destroy(fmm_plan_t P) {
     if (P->Ktc_hi) cudaFree(P->Ktc_hi);
     if (P->Ktc_lo) cudaFree(P->Ktc_lo);
     if (P->Kbar_tc) cudaFree(P->Kbar_tc);
+    if (P->sf_tab) cudaFree(P->sf_tab);
+    if (P->sf_H) cudaFree(P->sf_H);
     if (P->h_hdr) cudaFreeHost(P->h_hdr);
     delete P;
 }
@@ -980,6 +1001,10 @@ int fmm_batch_create(fmm_batch_t *out, int nsys, const double *boxes, const int 
     B->periodic = periodic ? 1 : 0;
     fmm_opts_default(&B->opts);
     if (opts) B->opts = *opts;
+    if (B->opts.shift_free) {  // the App. A.2 tables are per plan: single systems only
+        delete B;
+        return FMM_ERR_UNSUPPORTED;
+    }
     B->max_n.assign(max_n, max_n + nsys);
     B->masters.assign(FMM_MAXDEPTH + 1, nullptr);
     int rc = FMM_OK;

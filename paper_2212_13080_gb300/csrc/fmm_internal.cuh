@@ -32,6 +32,7 @@ struct Coef {
 // Per-evaluation scalars.
 struct Geom {
     int p, p3, depth, periodic, continuous, force_mode;
+    int shift_free;   // App. A.2: grid charges and functionals with respect to the box
     int S;            // 2^depth
     float x0[3];      // float32 box corner
     float Lf;         // float32 box edge
@@ -208,6 +209,13 @@ struct DevTables {
     int tc_inject;                        // FMM_INJECT_* test hook for this evaluation
     const void *tc_khi_map, *tc_klo_map;  // CUtensorMap of the split unit-cell kernels
     const float *tc_kbar;                 // [343][p3 padded to 32] row means
+    // App. A.2 forms (shift-free plans), FP64: right parts K_o shift_{S->C},
+    // [level pairs from sf_base[l]][n][m]; per-axis shift_{S->C} of every level
+    // from sf_hoff[l], [c][i][b]
+    const double *sf_tab;
+    const int64_t *sf_base;
+    const double *sf_H;
+    const int64_t *sf_hoff;
 };
 
 // Offset groups of the SIMT contraction at level l: the 189 offsets of a
@@ -262,6 +270,21 @@ int tc_encode_kernel_map(void *map, const void *base, int p3s, int pk, int mode)
 int tc_padded(int p3);            // p^3 rounded up to 32 (MMA N, fp32 K)
 int tc_padded_k(int p3, int mode);  // K extent of a cell vector: 32 (fp32) or 64 (bf16) multiple
 size_t tc_map_bytes();
+
+// bilinear forms without shifts (shift_free.cu, App. A.2; double-precision plans)
+// table bytes and the first pair of every level (base[0..depth+1])
+size_t sf_table_bytes(int p, int depth, int periodic, int64_t *base);
+// allocates and computes the forms of every level (synchronous); also keeps
+// the per-axis shift_{S->C} matrices of every level (hmat, offsets hoff)
+int sf_build(int p, int depth, int periodic, const Coef<double> &C, void **tab, int64_t *base,
+             void **hmat, int64_t *hoff);
+// upward pass after the leaves' box-basis replacement: sums of children
+void launch_sf_upward(const Geom &g, const Ptrs<double> &P, const WsLayout &W, cudaStream_t st,
+                      Tracer &tr);
+// interaction lists of every level plus the identity downward pass
+void launch_sf_downward(const Geom &g, const Ptrs<double> &P, const WsLayout &W, const double *tab,
+                        const int64_t *base, const double *hmat, const int64_t *hoff,
+                        cudaStream_t st, Tracer &tr);
 
 // near field + far-field evaluation at the charges (kernels_p2p.cu)
 // near field: writes out_pt (assigns); far field at the charges: adds to it

@@ -100,14 +100,16 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(Coef<real> C, int depth, const i
 }
 
 // Warp-per-cell form for p^3 <= 128: four finest cells per CTA, one warp each,
-// no block barriers.  Lane t computes the weights of the chunk's t-th charge
+// no block barriers.  sf: the weights are taken at the box coordinate
+// (c + t)/2^depth instead of the cell-local t (App. A.2, replacement with
+// respect to the box).  Lane t computes the weights of the chunk's t-th charge
 // into the warp's shared-memory rows; every lane then accumulates its grid
 // nodes (lane, lane + 32, ...) over the chunk.  The cell's total charge: a warp
 // tree per chunk, chunks added with compensation.
 #define P2M_WARPS 4
 
 template <typename real, int P>
-__global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_warp(Coef<real> C, int depth, int ncell,
+__global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_warp(Coef<real> C, int depth, int ncell, int sf,
                                                             const int *__restrict__ leaf_start,
                                                             const typename Vec4<real>::T *__restrict__ s_pt,
                                                             real *__restrict__ phi_leaf,
@@ -121,6 +123,9 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_warp(Coef<real> C, int d
     int cx, cy, cz;
     morton_decode((uint32_t)key, cx, cy, cz);
     const int s0 = leaf_start[key], s1 = leaf_start[key + 1];
+    // coordinate of the weights: o + h t (cell-local: o = 0, h = 1)
+    const real h = sf ? real(1) / (real)(1 << depth) : real(1);
+    const real ox = sf ? h * cx : real(0), oy = sf ? h * cy : real(0), oz = sf ? h * cz : real(0);
     real (*ws)[3 * P + 1] = w[warp];
     real acc[NO];
 #pragma unroll
@@ -132,13 +137,13 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_warp(Coef<real> C, int d
         if (lane < m) {
             typename Vec4<real>::T v = s_pt[c0 + lane];
             real g[FMM_MAXP];
-            lag_weights(C, P, v.x, g);
+            lag_weights(C, P, ox + h * v.x, g);
 #pragma unroll
             for (int i = 0; i < P; i++) ws[lane][i] = v.w * g[i];
-            lag_weights(C, P, v.y, g);
+            lag_weights(C, P, oy + h * v.y, g);
 #pragma unroll
             for (int i = 0; i < P; i++) ws[lane][P + i] = g[i];
-            lag_weights(C, P, v.z, g);
+            lag_weights(C, P, oz + h * v.z, g);
 #pragma unroll
             for (int i = 0; i < P; i++) ws[lane][2 * P + i] = g[i];
             qv = v.w;
@@ -548,7 +553,8 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
 #define WCASE(PP)                                                                                \
     case PP:                                                                                     \
         k_p2m_warp<real, PP><<<(ncell + P2M_WARPS - 1) / P2M_WARPS, 32 * P2M_WARPS, 0, st>>>(     \
-            C, depth, ncell, P.leaf_start, P.s_pt, phi_leaf, P.qlev + W.q_level[depth]);          \
+            C, depth, ncell, g.shift_free, P.leaf_start, P.s_pt, phi_leaf,                        \
+            P.qlev + W.q_level[depth]);                                                           \
         break;
 #define CASE(PP)                                                                                 \
     case PP:                                                                                     \
@@ -561,6 +567,10 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
     }
     tr.count();
     tr.end();
+    if (g.shift_free) {  // App. A.2: the box basis is additive over children
+        if constexpr (std::is_same<real, double>::value) launch_sf_upward(g, P, W, st, tr);
+        return;
+    }
     tr.begin(FMM_STAGE_M2M, st);
     const int lmin = g.periodic ? 0 : 2;
     for (int l = depth; l >= 1; l--) {
@@ -600,6 +610,11 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
                                            P.qlev + W.q_level[0], P.loc + W.loc_level[0]);
         tr.count();
         tr.end();
+    }
+    if (g.shift_free) {  // App. A.2: precomputed forms, identity downward pass
+        if constexpr (std::is_same<real, double>::value)
+            launch_sf_downward(g, P, W, T.sf_tab, T.sf_base, T.sf_H, T.sf_hoff, st, tr);
+        return FMM_OK;
     }
     int lsimt_end = depth;
     if (T.tc_lmin > 0 && depth >= T.tc_lmin) lsimt_end = T.tc_lmin - 1;

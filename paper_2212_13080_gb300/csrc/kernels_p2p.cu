@@ -53,7 +53,7 @@ __device__ __forceinline__ int64_t nf_cell(int cx, int cy, int cz, int dx, int d
 #define L2P_LPC 4  // finest cells per CTA (consecutive keys: one contiguous charge range)
 
 template <typename real, int P, bool FORCES>
-__global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int periodic, int ncell,
+__global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int periodic, int ncell, int sf,
                                                 const int *__restrict__ leaf_start,
                                                 const typename Vec4<real>::T *__restrict__ s_pt,
                                                 const real *__restrict__ loc_leaf,
@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
     __shared__ real Ls[L2P_LPC][P3];
     __shared__ int slot_ok[L2P_LPC][NF_SEGS - 1];
     __shared__ int lst[L2P_LPC + 1];
+    __shared__ real org[L2P_LPC][3];  // coordinate of the weights: org + h t
     const int k0 = blockIdx.x * L2P_LPC;
     const int nleaf = min(L2P_LPC, ncell - k0);
     if (threadIdx.x <= L2P_LPC) lst[threadIdx.x] = leaf_start[min(k0 + (int)threadIdx.x, ncell)];
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
         int cx, cy, cz;
         morton_decode((uint32_t)(k0 + j), cx, cy, cz);
         Ls[j][o] = loc_leaf[loc_cell(depth, cx, cy, cz) * P3 + o];
+        if (o < 3) org[j][o] = sf ? (real)(o == 0 ? cx : o == 1 ? cy : cz) / (real)(1 << depth) : real(0);
     }
     // slot d - 1 of a cell's charges was written by the cell (that cell -
     // delta_d), d = 1..13, if it exists and holds charges
@@ -86,21 +88,25 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
     }
     __syncthreads();
     const real S = (real)(1 << depth);
+    // cell-local weights (t) or, shift-free, box weights at (c + t)/2^depth;
+    // the force is -q times the gradient in unit-box coordinates
+    const real h = sf ? real(1) / S : real(1), FS = sf ? real(1) : S;
     for (int s = lst[0] + threadIdx.x; s < lst[nleaf]; s += blockDim.x) {
         int lf = 0;  // which of the CTA's cells holds charge s
         while (s >= lst[lf + 1]) lf++;
         const real *Lc = Ls[lf];
         const int *okc = slot_ok[lf];
         typename Vec4<real>::T v = s_pt[s];
+        const real X = org[lf][0] + h * v.x, Y = org[lf][1] + h * v.y, Z = org[lf][2] + h * v.z;
         real gx[FMM_MAXP], gy[FMM_MAXP], gz[FMM_MAXP], dx[FMM_MAXP], dy[FMM_MAXP], dz[FMM_MAXP];
         if (FORCES) {
-            lag_weights_deriv(C, P, v.x, gx, dx);
-            lag_weights_deriv(C, P, v.y, gy, dy);
-            lag_weights_deriv(C, P, v.z, gz, dz);
+            lag_weights_deriv(C, P, X, gx, dx);
+            lag_weights_deriv(C, P, Y, gy, dy);
+            lag_weights_deriv(C, P, Z, gz, dz);
         } else {
-            lag_weights(C, P, v.x, gx);
-            lag_weights(C, P, v.y, gy);
-            lag_weights(C, P, v.z, gz);
+            lag_weights(C, P, X, gx);
+            lag_weights(C, P, Y, gy);
+            lag_weights(C, P, Z, gz);
         }
         real phi = 0, fx = 0, fy = 0, fz = 0;
 #pragma unroll 1
@@ -141,9 +147,9 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
             o.w += r.w;
         }
         o.x += phi;
-        o.y += -v.w * S * fx;
-        o.z += -v.w * S * fy;
-        o.w += -v.w * S * fz;
+        o.y += -v.w * FS * fx;
+        o.z += -v.w * FS * fy;
+        o.w += -v.w * FS * fz;
         out_pt[s] = o;
     }
 }
@@ -482,11 +488,11 @@ void launch_l2p(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const W
 #define CASE(PP)                                                                                 \
     case PP:                                                                                     \
         if (forces)                                                                              \
-            k_l2p<real, PP, true><<<(ncell + L2P_LPC - 1) / L2P_LPC, L2P_BS, 0, st>>>(C, depth, g.periodic, ncell, P.leaf_start,  \
+            k_l2p<real, PP, true><<<(ncell + L2P_LPC - 1) / L2P_LPC, L2P_BS, 0, st>>>(C, depth, g.periodic, ncell, g.shift_free, P.leaf_start,  \
                                                            P.s_pt, loc_leaf, P.react, W.cap,    \
                                                            P.out_pt);                           \
         else                                                                                     \
-            k_l2p<real, PP, false><<<(ncell + L2P_LPC - 1) / L2P_LPC, L2P_BS, 0, st>>>(C, depth, g.periodic, ncell, P.leaf_start, \
+            k_l2p<real, PP, false><<<(ncell + L2P_LPC - 1) / L2P_LPC, L2P_BS, 0, st>>>(C, depth, g.periodic, ncell, g.shift_free, P.leaf_start, \
                                                             P.s_pt, loc_leaf, P.react, W.cap,   \
                                                             P.out_pt);                          \
         break;

@@ -127,6 +127,9 @@ def workload(name, seed=None, n=None):
     if name == "uniform4k":  # 4096 uniform +-1, open, plain, depth 3, p 4
         pos, q, box = uniform_pm1(4096 if n is None else n, 1 if seed is None else seed)
         return dict(pos=pos, q=q, box=box, depth=3, p=4, periodic=False, continuous=False)
+    if name == "uniform23k":  # 23,040 uniform +-1 (the size of §3.1's runs), open, plain, depth 3, p 4
+        pos, q, box = uniform_pm1(23040 if n is None else n, 7 if seed is None else seed)
+        return dict(pos=pos, q=q, box=box, depth=3, p=4, periodic=False, continuous=False)
     if name == "uniform1m":  # 1,048,576 uniform, open, continuous, depth 5, p 4
         pos, q, box = uniform_cont(1 << 20 if n is None else n, 2 if seed is None else seed)
         return dict(pos=pos, q=q, box=box, depth=5, p=4, periodic=False, continuous=True)

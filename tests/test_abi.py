@@ -58,3 +58,29 @@ def test_plan_argument_checks():
     o.split_ratio = 0.6
     assert L.fmm_plan_create(ctypes.byref(h), box, 3, 4, 0, ctypes.byref(o), 10) == B.FMM_ERR_ARG
     assert L.fmm_eval(None, 1, None, None, None, None, None, None, 0, None) == B.FMM_ERR_ARG
+
+
+def test_shift_free_options_rejected_before_any_device_call():
+    """App. A.2 plans: FP64 only (the forms extrapolate over 2^l cells), p <= 5,
+    the standard arrangement, tables of at most 32 GiB, single systems; the
+    checks come before the plan touches the device."""
+    import pytest
+    from paper_2212_13080_gb300 import _binding as B
+    box = (0.0, 0.0, 0.0, 1.0)
+
+    def opts(**kw):
+        o = B.fmm_opts_default()
+        o.precision = B.FMM_PREC_FP64
+        o.shift_free = 1
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    for depth, p, o in [(3, 4, opts(precision=B.FMM_PREC_FP32)),
+                        (3, 4, opts(precision=B.FMM_PREC_TF32X3)),
+                        (2, 6, opts()),
+                        (3, 4, opts(grid_scale=1 / 1.2)),
+                        (4, 5, opts())]:  # 110 GB of forms
+        with pytest.raises(B.FmmError) as e:
+            B.fmm_plan_create(box, depth, p, False, o, 1000)
+        assert e.value.code == B.FMM_ERR_UNSUPPORTED, (depth, p)
