@@ -28,7 +28,7 @@
 namespace fmm {
 
 #define SF_TBS 256  // threads of the table kernel
-#define SF_BS 256   // threads of the contraction kernel
+#define SF_BS 512   // threads of the contraction kernel
 #define SF_NOFF 189
 
 // cell (cx, cy, cz) of level l >= 1 from its index in the L layout
@@ -171,10 +171,12 @@ __global__ void k_sf_up(int l, int p3, const double *__restrict__ phi_c, double 
 // ---------------------------------------------------------------------------
 // Interaction lists of level l:
 //     L^S_C~ = L^S_parent + shift_{S->C~}^T sum_o A_{C~,o} Phi^S_{C~+o}.
-// One CTA per target cell; NG groups of GS threads take every NG-th offset,
-// thread m of a group one node of the target cell (its table column is
-// contiguous over m); the groups' sums are added in group order, then the
-// left factor is applied by three in-place passes of p-point transforms.
+// One CTA per target cell, 16 warps; warp w takes the offsets w, w + 16, ...
+// and lane t the target nodes t, t + 32, ... (its table columns are
+// contiguous over the warp).  The source vector sits in the lanes' registers
+// and is broadcast by shuffles; even and odd source nodes go to two
+// accumulators.  The warps' sums are added in warp order, then the left
+// factor is applied by three in-place passes of p-point transforms.
 // ---------------------------------------------------------------------------
 template <int P>
 __global__ void __launch_bounds__(SF_BS) k_sf_m2l(int l, int periodic, int add_parent,
@@ -185,10 +187,10 @@ __global__ void __launch_bounds__(SF_BS) k_sf_m2l(int l, int periodic, int add_p
                                                   double *__restrict__ loc_l) {
     constexpr int P3 = P * P * P, PP = P * P;
     constexpr int64_t P6 = (int64_t)P3 * P3;
-    constexpr int GS = (P3 + 31) / 32 * 32;
-    constexpr int NG = SF_BS / GS;
+    constexpr int MR = (P3 + 31) / 32;  // target nodes per lane
+    constexpr int NW = SF_BS / 32;
     __shared__ int64_t src[SF_NOFF];
-    __shared__ double part[NG][GS];
+    __shared__ double part[NW][MR * 32];
     __shared__ double y[P3];
     __shared__ double Ht[3][PP];
     const int64_t cl = blockIdx.x;
@@ -205,26 +207,38 @@ __global__ void __launch_bounds__(SF_BS) k_sf_m2l(int l, int periodic, int add_p
         Ht[e / PP][e % PP] = H[(int64_t)c * PP + e % PP];
     }
     __syncthreads();
-    const int g = threadIdx.x / GS, m = threadIdx.x % GS;
-    double acc = 0.0;
-    if (m < P3) {
-        for (int oi = g; oi < SF_NOFF; oi += NG) {
-            const int64_t sc = src[oi];
-            if (sc < 0) continue;
-            const double *B = tab_l + (cl * SF_NOFF + oi) * P6 + m;
-            const double *ph = phi_l + sc * P3;
-            double s = 0.0;
-#pragma unroll 8
-            for (int n = 0; n < P3; n++) s += B[(int64_t)n * P3] * ph[n];
-            acc += s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double a0[MR], a1[MR];
+#pragma unroll
+    for (int k = 0; k < MR; k++) a0[k] = a1[k] = 0.0;
+    for (int oi = warp; oi < SF_NOFF; oi += NW) {
+        const int64_t sc = src[oi];  // uniform over the warp
+        if (sc < 0) continue;
+        const double *B = tab_l + (cl * SF_NOFF + oi) * P6 + lane;
+        const double *ph = phi_l + sc * P3;
+        double f[MR];
+#pragma unroll
+        for (int k = 0; k < MR; k++) f[k] = (lane + 32 * k < P3) ? ph[lane + 32 * k] : 0.0;
+#pragma unroll
+        for (int n = 0; n < P3; n++) {
+            const double v = __shfl_sync(0xffffffffu, f[n >> 5], n & 31);
+#pragma unroll
+            for (int k = 0; k < MR; k++) {
+                if (32 * k + 32 <= P3 || lane + 32 * k < P3) {
+                    const double b = B[(int64_t)n * P3 + 32 * k];
+                    if (n & 1) a1[k] += b * v;
+                    else a0[k] += b * v;
+                }
+            }
         }
     }
-    part[g][m] = acc;
+#pragma unroll
+    for (int k = 0; k < MR; k++) part[warp][lane + 32 * k] = a0[k] + a1[k];
     __syncthreads();
     if (threadIdx.x < P3) {
         double t = part[0][threadIdx.x];
 #pragma unroll
-        for (int k = 1; k < NG; k++) t += part[k][threadIdx.x];
+        for (int w = 1; w < NW; w++) t += part[w][threadIdx.x];
         y[threadIdx.x] = t;
     }
     __syncthreads();
