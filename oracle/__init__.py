@@ -26,6 +26,12 @@ bilinear forms BB_{C~,C} (target and source shifted from the box,
 shift_{S->C} the inverse of shift_{C->S}), and the downward pass is the
 identity.
 
+`fmm(..., force_kernel=True)` takes the far forces from the force kernels
+(x - x~)/|P - P~|^3 (§4.1's remark on other kernels): three more functionals
+per cell from the same interaction lists (the periodic lattice term from the
+gradient of the Ewald lattice potential), read with the plain weights; a
+particle's force is the sum of the forces on its charges.
+
 The energy is E = 1/2 sum_i q_i phi_i, phi_i the potential at particle i from
 every other particle (steps 4 and 5 each count every pair from both sides).
 
@@ -87,6 +93,10 @@ def lib():
         L.orc_sf_downward.argtypes = [i32, i32, i32, P, P, P, P]
         L.orc_sf_downward.restype = i32
         L.orc_sf_evaluate.argtypes = [i32, i32, i32, i64, P, P, P, P, P, P, P, P, P, P]
+        L.orc_set_kernel.argtypes = [i32]
+        L.orc_lattice_grad.argtypes = [d, d, d, P]
+        L.orc_evaluate_kernel.argtypes = [i32, i32, i32, i64, P, P, P, P, P, P, P, P, P, P, P, P,
+                                          P]
         _lib = L
     return _lib
 
@@ -136,23 +146,41 @@ def shift_matrix(n, h):
     return G
 
 
-def m2l_kernel(n, o):
-    """§2.1.7 eq. (bilinear): K[a, b] = 1/|a - (o + b)| for unit cells."""
+def m2l_kernel(n, o, comp=0):
+    """§2.1.7 eq. (bilinear): K[a, b] = 1/|a - (o + b)| for unit cells; comp
+    1..3 the x, y, z component of the force kernel r/|r|^3 at r = a - (o + b)."""
     n3 = n ** 3
     K = np.empty((n3, n3))
-    lib().orc_m2l_kernel(n, int(o[0]), int(o[1]), int(o[2]), _p(K))
+    L = lib()
+    L.orc_set_kernel(int(comp))
+    try:
+        L.orc_m2l_kernel(n, int(o[0]), int(o[1]), int(o[2]), _p(K))
+    finally:
+        L.orc_set_kernel(0)
     return K
 
 
-def lattice_kernel(n):
+def lattice_kernel(n, comp=0):
+    """Level-0 lattice kernel psi(a - b) (§4.2); comp 1..3: -d psi/d r_c."""
     n3 = n ** 3
     K = np.empty((n3, n3))
-    lib().orc_lattice_kernel(n, _p(K))
+    L = lib()
+    L.orc_set_kernel(int(comp))
+    try:
+        L.orc_lattice_kernel(n, _p(K))
+    finally:
+        L.orc_set_kernel(0)
     return K
 
 
 def lattice_psi(r):
     return lib().orc_lattice_psi(float(r[0]), float(r[1]), float(r[2]))
+
+
+def lattice_grad(r):
+    g = np.empty(3)
+    lib().orc_lattice_grad(float(r[0]), float(r[1]), float(r[2]), _p(g))
+    return g
 
 
 def sf_shift_to_box(n, l, c):
@@ -254,24 +282,30 @@ def level_offset(n, l):
 
 
 def fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sample=None,
-        keep=True, grid_scale=1.0, shift_free=False):
+        keep=True, grid_scale=1.0, shift_free=False, force_kernel=False):
     """Runs the oracle FMM; grid_scale < 1 takes the reduced arrangement of the
     n-division points (§4.1: spacing times grid_scale about the cell centre);
     shift_free takes the bilinear forms without shifts of App. A.2 (grid
     charges and functionals of every cell with respect to the box).  See _fmm
-    for the other arguments."""
+    for the other arguments.  force_kernel takes the far forces from the force
+    kernels (x - x~)/|P - P~|^3 (§4.1) instead of the derivative of the weights;
+    "F" is then the sum of the forces on a particle's charges."""
     if continuous and grid_scale != 1.0:
         raise ValueError("the reduced arrangement is defined for the plain form")
+    if shift_free and force_kernel:
+        raise ValueError("the shift-free forms are built for the potential kernel")
     L_ = lib()
     L_.orc_set_grid_scale(float(grid_scale))
     try:
-        return _fmm(pos, q, box, depth, n, periodic, continuous, dt, sample, keep, shift_free)
+        return _fmm(pos, q, box, depth, n, periodic, continuous, dt, sample, keep, shift_free,
+                    force_kernel)
     finally:
         L_.orc_set_grid_scale(1.0)
+        L_.orc_set_kernel(0)
 
 
 def _fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sample=None,
-         keep=True, shift_free=False):
+         keep=True, shift_free=False, force_kernel=False):
     """Runs the oracle FMM.
 
     pos: (N,3) float32 positions, q: (N,) float32 charges, box = (x0,y0,z0,L).
@@ -373,13 +407,29 @@ def _fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sampl
         L_.orc_downward(n, depth, int(periodic), _p(Phi), _p(Lv), need_arg,
                         _p(Klat) if Klat is not None else None)
 
+    LF = []
+    if force_kernel:  # the functionals of the three force kernels, same lists
+        for c in (1, 2, 3):
+            L_.orc_set_kernel(c)
+            Kc = lattice_kernel(n, c) if periodic else None
+            L_.orc_set_kernel(c)
+            LF.append(np.zeros_like(Phi))
+            L_.orc_downward(n, depth, int(periodic), _p(Phi), _p(LF[-1]), need_arg,
+                            _p(Kc) if Kc is not None else None)
+        L_.orc_set_kernel(0)
+
     # steps 4-5 at every charge
     phi_pt = np.zeros(npts)
     F_pt = np.zeros((npts, 3))
     ncoinc = ctypes.c_int64(0)
-    evaluate = L_.orc_sf_evaluate if shift_free else L_.orc_evaluate
-    evaluate(n, depth, int(periodic), npts, _p(st), _p(scell), _p(sq), _p(sorigin),
-             _p(start), _p(Lv), _p(mask), _p(phi_pt), _p(F_pt), ctypes.byref(ncoinc))
+    if force_kernel:
+        L_.orc_evaluate_kernel(n, depth, int(periodic), npts, _p(st), _p(scell), _p(sq),
+                               _p(sorigin), _p(start), _p(Lv), _p(LF[0]), _p(LF[1]), _p(LF[2]),
+                               _p(mask), _p(phi_pt), _p(F_pt), ctypes.byref(ncoinc))
+    else:
+        evaluate = L_.orc_sf_evaluate if shift_free else L_.orc_evaluate
+        evaluate(n, depth, int(periodic), npts, _p(st), _p(scell), _p(sq), _p(sorigin),
+                 _p(start), _p(Lv), _p(mask), _p(phi_pt), _p(F_pt), ctypes.byref(ncoinc))
 
     # split charges back into their particles
     inv = np.empty(npts, np.int64)
@@ -392,7 +442,7 @@ def _fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sampl
     F_norm = np.stack([-qf.astype(np.float64) *
                        np.bincount(pt_origin, weights=pt_dw[:, a] * phi_e, minlength=N)
                        for a in range(3)], axis=1)
-    F_adj = np.where(axes.astype(bool), F_norm, F_paper)
+    F_adj = F_paper if force_kernel else np.where(axes.astype(bool), F_norm, F_paper)
 
     Lb = float(box[3])
     out = {
@@ -411,7 +461,7 @@ def _fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sampl
         out.update(dict(u=u, t=t, cell=cell, key=key, count=count, axes=axes, offset=offset,
                         pt_t=pt_t, pt_cell=pt_cell, pt_key=pt_key, pt_q=pt_q, pt_w=pt_w,
                         pt_dw=pt_dw, pt_origin=pt_origin, perm=perm, start=start, Phi=Phi,
-                        L=Lv, phi_pt=phi_pt, F_pt=F_pt))
+                        L=Lv, LF=LF, phi_pt=phi_pt, F_pt=F_pt))
     return out
 
 

@@ -95,9 +95,28 @@ void orc_shift_matrix(int n, int h, double *G)
     }
 }
 
+/* The function F of the bilinear forms.  §2.1.7 takes F(P, P~) = 1/|P - P~|;
+ * the discussion of other kernels (§4.1) notes that the same replacement
+ * gives the forces directly with F = (x - x~)/|P - P~|^3 (and its y, z
+ * components) instead of differentiating the replaced charges' weights.
+ * g_kernel: 0 = 1/r, 1..3 = the x, y, z component of r/|r|^3.  At level l,
+ * unit-cell distances are 2^l times unit-box distances, so the forms scale
+ * by 2^l (potential) or 4^l (force components). */
+static int g_kernel = 0;
+void orc_set_kernel(int c) { g_kernel = c; }
+static double kernel_value(double dx, double dy, double dz)
+{
+    double r2 = dx * dx + dy * dy + dz * dz, r = sqrt(r2);
+    if (g_kernel == 0) return 1.0 / r;
+    double d = g_kernel == 1 ? dx : g_kernel == 2 ? dy : dz;
+    return d / (r2 * r);
+}
+static double level_scale(int l) { return ldexp(1.0, g_kernel == 0 ? l : 2 * l); }
+
 /* §2.1.7, eqs. (newer), (bilinear): F(P(a), P(a~)) = 1/|a - a~| between the
  * n-division points a of the unit cell at the origin and a~ of the unit cell
- * displaced by the integer vector o.  K[a*n^3 + b]. */
+ * displaced by the integer vector o (or the force component selected by
+ * orc_set_kernel).  K[a*n^3 + b]. */
 void orc_m2l_kernel(int n, int ox, int oy, int oz, double *K)
 {
     int n3 = n * n * n;
@@ -106,8 +125,7 @@ void orc_m2l_kernel(int n, int ox, int oy, int oz, double *K)
         for (int b = 0; b < n3; b++) {
             double bx = ox + tau(n, b % n), by = oy + tau(n, (b / n) % n),
                    bz = oz + tau(n, b / (n * n));
-            double dx = ax - bx, dy = ay - by, dz = az - bz;
-            K[(int64_t)a * n3 + b] = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+            K[(int64_t)a * n3 + b] = kernel_value(ax - bx, ay - by, az - bz);
         }
     }
 }
@@ -160,7 +178,42 @@ double orc_lattice_psi(double rx, double ry, double rz)
     return s;
 }
 
-/* K_lat[a*n^3 + b] = psi(a - b) for the n-division points of the unit box.
+/* Gradient of psi: term by term, d/dr [erfc(al d)/d] and d/dr [-erf(al d)/d]
+ * along r + m, and -2 A h sin(2 pi h.r) for the reciprocal terms; the
+ * nearest-image term is even and smooth at d = 0, where its gradient is 0. */
+void orc_lattice_grad(double rx, double ry, double rz, double *g)
+{
+    const double al = EW_ALPHA;
+    g[0] = g[1] = g[2] = 0.0;
+    for (int mz = -EW_RMAX; mz <= EW_RMAX; mz++)
+        for (int my = -EW_RMAX; my <= EW_RMAX; my++)
+            for (int mx = -EW_RMAX; mx <= EW_RMAX; mx++) {
+                double dx = rx + mx, dy = ry + my, dz = rz + mz;
+                double d = sqrt(dx * dx + dy * dy + dz * dz);
+                int nearest = (abs(mx) <= 1 && abs(my) <= 1 && abs(mz) <= 1);
+                if (d == 0.0) continue;
+                double gauss = 2.0 * al / sqrt(M_PI) * exp(-al * al * d * d) / d;
+                double dd = nearest ? -gauss + erf(al * d) / (d * d)      /* d/dd of -erf/d */
+                                    : -gauss - erfc(al * d) / (d * d);    /* d/dd of erfc/d */
+                g[0] += dd * dx / d;
+                g[1] += dd * dy / d;
+                g[2] += dd * dz / d;
+            }
+    for (int hz = -EW_KMAX; hz <= EW_KMAX; hz++)
+        for (int hy = -EW_KMAX; hy <= EW_KMAX; hy++)
+            for (int hx = -EW_KMAX; hx <= EW_KMAX; hx++) {
+                if (hx == 0 && hy == 0 && hz == 0) continue;
+                double h2 = (double)(hx * hx + hy * hy + hz * hz);
+                double A = exp(-M_PI * M_PI * h2 / (al * al)) / h2;
+                double sn = sin(2.0 * M_PI * (hx * rx + hy * ry + hz * rz));
+                g[0] -= 2.0 * A * hx * sn;
+                g[1] -= 2.0 * A * hy * sn;
+                g[2] -= 2.0 * A * hz * sn;
+            }
+}
+
+/* K_lat[a*n^3 + b] = psi(a - b) for the n-division points of the unit box
+ * (force component c of orc_set_kernel: -d psi / d r_c at a - b).
  * psi depends on a - b only, which takes (2n-1)^3 distinct values; each is
  * evaluated once. */
 void orc_lattice_kernel(int n, double *K)
@@ -173,7 +226,13 @@ void orc_lattice_kernel(int n, double *K)
         double rx = tau(n, dx > 0 ? dx : 0) - tau(n, dx < 0 ? -dx : 0);
         double ry = tau(n, dy > 0 ? dy : 0) - tau(n, dy < 0 ? -dy : 0);
         double rz = tau(n, dz > 0 ? dz : 0) - tau(n, dz < 0 ? -dz : 0);
-        tab[e] = orc_lattice_psi(rx, ry, rz);
+        if (g_kernel == 0) {
+            tab[e] = orc_lattice_psi(rx, ry, rz);
+        } else {
+            double g[3];
+            orc_lattice_grad(rx, ry, rz, g);
+            tab[e] = -g[g_kernel - 1];
+        }
     }
     for (int a = 0; a < n3; a++)
         for (int b = 0; b < n3; b++) {
@@ -663,7 +722,7 @@ void orc_downward(int n, int depth, int periodic, const double *Phi, double *L,
     }
     for (int l = 1; l <= depth; l++) {
         const int S = 1 << l, Sp = S >> 1;
-        const double scale = (double)S;
+        const double scale = level_scale(l);
         const double *Pl = Phi + level_offset(n, l);
         double *Ll = L + level_offset(n, l);
         const double *Lp = L + level_offset(n, l - 1);
@@ -1118,6 +1177,47 @@ void orc_sf_evaluate(int n, int depth, int periodic, int64_t npts, const double 
         F[3 * s] = -sq[s] * gfx + nf[1];
         F[3 * s + 1] = -sq[s] * gfy + nf[2];
         F[3 * s + 2] = -sq[s] * gfz + nf[3];
+    }
+    if (ncoinc) *ncoinc = coinc;
+}
+
+/* Steps 4-5 with the forces taken from the force kernels (§4.1's remark):
+ * L holds the potential functionals, LF[c] those of the c-th force component
+ * (orc_set_kernel(c + 1) for the downward pass).  Far potential per unit
+ * charge g(x).L_leaf as in orc_evaluate; far force component c is
+ * q g(x).LF[c]_leaf with the plain weights; the near field as orc_evaluate. */
+void orc_evaluate_kernel(int n, int depth, int periodic, int64_t npts, const double *st,
+                         const int32_t *scell, const double *sq, const int64_t *sorigin,
+                         const int64_t *start, const double *L, const double *LFx,
+                         const double *LFy, const double *LFz, const uint8_t *mask, double *phi,
+                         double *F, int64_t *ncoinc)
+{
+    const int n3 = n * n * n, S = 1 << depth;
+    const int64_t off = level_offset(n, depth);
+    const double *LF[3] = {LFx + off, LFy + off, LFz + off};
+    int64_t coinc = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : coinc)
+    for (int64_t s = 0; s < npts; s++) {
+        if (mask && !mask[s]) continue;
+        int cx = scell[3 * s], cy = scell[3 * s + 1], cz = scell[3 * s + 2];
+        const int64_t cell = (((int64_t)cz * S + cy) * S + cx) * n3;
+        double gx[ORC_MAXN], gy[ORC_MAXN], gz[ORC_MAXN];
+        orc_lagrange(n, st[3 * s], gx);
+        orc_lagrange(n, st[3 * s + 1], gy);
+        orc_lagrange(n, st[3 * s + 2], gz);
+        double pf = 0.0, f[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < n; k++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) {
+                    int a = (k * n + j) * n + i;
+                    double w = gx[i] * gy[j] * gz[k];
+                    pf += w * L[off + cell + a];
+                    for (int c = 0; c < 3; c++) f[c] += w * LF[c][cell + a];
+                }
+        double nf[4];
+        near_field(depth, periodic, s, st, scell, sq, sorigin, start, nf, &coinc);
+        phi[s] = pf + nf[0];
+        for (int c = 0; c < 3; c++) F[3 * s + c] = sq[s] * f[c] + nf[1 + c];
     }
     if (ncoinc) *ncoinc = coinc;
 }

@@ -520,3 +520,78 @@ def test_sf_bilinear_matrix_and_fp32_conditioning():
         assert np.linalg.norm(f64 - direct) / np.linalg.norm(direct) < 5e-3
     assert err32[2] < 1e-3
     assert err32[3] > 1e-2
+
+
+# --- §4.1: forces from the force kernels ------------------------------------------
+
+def test_lattice_gradient_matches_central_differences():
+    """The periodic force kernel -grad psi (§4.2 lattice term, force component)
+    against central differences of the lattice potential psi."""
+    rng = np.random.default_rng(21)
+    for r in [np.array([0.3, -0.2, 0.55]), np.zeros(3), *rng.uniform(-1, 1, (4, 3))]:
+        g = oracle.lattice_grad(r)
+        h = 1e-5
+        fd = np.array([(oracle.lattice_psi(r + h * e) - oracle.lattice_psi(r - h * e)) / (2 * h)
+                       for e in np.eye(3)])
+        np.testing.assert_allclose(g, fd, rtol=1e-8, atol=1e-8)
+    np.testing.assert_allclose(oracle.lattice_grad(np.zeros(3)), 0.0, atol=1e-12)
+
+
+def test_force_kernel_tables_are_minus_gradient_of_potential_kernel():
+    """K^c_o[a, b] = (a - o - b)_c / |a - o - b|^3 = -d/da_c (1/|a - o - b|),
+    entry by entry from the node coordinates, next to the potential table;
+    and the sign by hand: like charges repel, so the force on a target at the
+    origin from a source at +2 in x points to -x."""
+    n = 3
+    a = oracle.nodes(n)
+    o = (2, -3, 1)
+    K = oracle.m2l_kernel(n, o)
+    for c in (1, 2, 3):
+        Kc = oracle.m2l_kernel(n, o, comp=c)
+        for ia in range(n ** 3):
+            ta = np.array([a[ia % n], a[(ia // n) % n], a[ia // (n * n)]])
+            for ib in range(n ** 3):
+                tb = np.array(o) + np.array([a[ib % n], a[(ib // n) % n], a[ib // (n * n)]])
+                r = ta - tb
+                assert abs(Kc[ia, ib] - r[c - 1] / np.linalg.norm(r) ** 3) < 1e-15
+                assert abs(K[ia, ib] - 1 / np.linalg.norm(r)) < 1e-15
+    # target node 0 at the origin, source cell at +2 in x: force points to -x
+    assert oracle.m2l_kernel(n, (2, 0, 0), comp=1)[0, 0] < 0
+
+
+@pytest.mark.parametrize("periodic,continuous", [(False, False), (True, True)])
+def test_force_kernel_forces_conserve_momentum(periodic, continuous):
+    """With the force kernels every far term is antisymmetric: the charges of
+    cell C feel sum_i q_i g(x_i) . K^c Phi_C~ = Phi_C . K^c Phi_C~ (the
+    replacement, eq. ex66), and the charges of C~ feel Phi_C~ . K^c' Phi_C
+    with K^c'[b, a] = -K^c[a, b]; the lattice gradient is odd; the near field
+    is pairwise.  So the total force vanishes to rounding -- which the
+    derivative (adjoint) forces of the interpolated energy do not satisfy."""
+    pos, q, box = inputs.uniform_cont(3000, 3)
+    a = oracle.fmm(pos, q, box, 3, 4, periodic=periodic, continuous=continuous, force_kernel=True)
+    b = oracle.fmm(pos, q, box, 3, 4, periodic=periodic, continuous=continuous)
+    scale = np.abs(a["F"]).sum()
+    assert np.abs(a["F"].sum(axis=0)).max() < 1e-13 * scale
+    assert np.abs(b["F"].sum(axis=0)).max() > 1e-7 * scale
+    # the potentials and the energy do not depend on how the forces are taken
+    np.testing.assert_array_equal(a["phi"], b["phi"])
+    assert a["E"] == b["E"]
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_force_kernel_forces_converge_to_direct_sum(periodic):
+    """§4.1: forces computed directly with the force kernels approach the
+    exact (direct / Ewald) forces as the order grows, and at each order are
+    closer than the derivative of the interpolated potential."""
+    pos, q, box = inputs.uniform_pm1(3000, 4)
+    tg = np.arange(0, 3000, 10)  # 300 targets (the Ewald reference is O(N) per target)
+    _, F_ref = oracle.direct(pos, q, box, periodic=periodic, targets=tg)
+    rel = lambda x: np.linalg.norm(x[tg] - F_ref) / np.linalg.norm(F_ref)
+    errs = []
+    for n in (3, 4, 5, 6):
+        ek = rel(oracle.fmm(pos, q, box, 3, n, periodic=periodic, force_kernel=True)["F"])
+        ea = rel(oracle.fmm(pos, q, box, 3, n, periodic=periodic)["F"])
+        assert ek < ea, (n, ek, ea)
+        errs.append(ek)
+    assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-4
