@@ -70,6 +70,12 @@ extern "C" {
 /* ---- flags of fmm_eval ---------------------------------------------------- */
 #define FMM_FORCE_ADJOINT 0 /* forces = -dE/dx of the FMM energy (default) */
 #define FMM_FORCE_PAPER 1   /* split axes: sum of the forces the split charges feel (§2.3) */
+#define FMM_FORCE_KERNEL 2  /* far forces from the force kernels r/|r|^3 (§4.1, other
+                               kernels): three more functionals per cell through the same
+                               interaction lists (periodic: the gradient of the lattice term),
+                               read with the plain weights; a particle's force is the sum of
+                               its charges' forces.  Conserves total momentum exactly; the
+                               backward pass stays the adjoint -dE/dx.  Not with shift_free. */
 
 typedef struct fmm_plan_s *fmm_plan_t;
 
@@ -81,7 +87,7 @@ typedef struct {
                               <= 0 selects max(2, 1.5 (1 + 2 (d/w)(m-1))^3), m = p
                               (even p) or p+1 (odd p): 1.5x the uniform-density mean */
     int precision;         /* FMM_PREC_* */
-    int force_mode;        /* FMM_FORCE_ADJOINT or FMM_FORCE_PAPER */
+    int force_mode;        /* FMM_FORCE_ADJOINT, FMM_FORCE_PAPER or FMM_FORCE_KERNEL */
     int sync;              /* 1 (default when opts is NULL): fmm_eval waits for the device
                               and returns device-side errors; 0: fmm_eval returns after
                               queueing, fmm_status() reports them later */

@@ -22,7 +22,7 @@ __all__ = ["FMM", "FMMBatch", "FmmError", "fmm_energy"]
 
 _PREC = {"fp32": B.FMM_PREC_FP32, "fp64": B.FMM_PREC_FP64, "tf32x3": B.FMM_PREC_TF32X3,
          "tf32x1": B.FMM_PREC_TF32X1, "bf16x3": B.FMM_PREC_BF16X3}
-_FORCE = {"adjoint": B.FMM_FORCE_ADJOINT, "paper": B.FMM_FORCE_PAPER}
+_FORCE = {"adjoint": B.FMM_FORCE_ADJOINT, "paper": B.FMM_FORCE_PAPER, "kernel": B.FMM_FORCE_KERNEL}
 
 
 def _ptr(t):

@@ -30,6 +30,7 @@ FMM_PREC_BF16X3 = 4
 
 FMM_FORCE_ADJOINT = 0
 FMM_FORCE_PAPER = 1
+FMM_FORCE_KERNEL = 2
 
 FMM_DUMP_COUNTS = 0
 FMM_DUMP_KEYS = 1

@@ -22,13 +22,16 @@ struct fmm_plan_s {
     int64_t max_n;
     int device;
     bool fp64;
-    void *Kunit;  // [343][p^3][p^3] Kt_o transposed ([o][b][a]), plan real type
-    void *Kbar;   // [343][p^3] row means of the unit-cell kernels
-    void *Klat;   // [p^3][p^3] lattice kernel minus its row mean (periodic form)
-    void *Klbar;  // [p^3] row means of the lattice kernel
-    void *Ktc_hi, *Ktc_lo;  // [343][a][b] TF32 split of Kt, padded to 32 (TF32X3 plans)
-    void *Kbar_tc;          // [343][a] row means, padded to 32
-    alignas(64) unsigned char khi_map[128], klo_map[128];  // their TMA tensor maps
+    // every table has ncomp blocks: the potential kernel 1/r and, with
+    // FMM_FORCE_KERNEL, the three components of the force kernel r/|r|^3
+    int ncomp;
+    void *Kunit;  // [comp][343][p^3][p^3] Kt_o transposed ([o][b][a]), plan real type
+    void *Kbar;   // [comp][343][p^3] row means of the unit-cell kernels
+    void *Klat;   // [comp][p^3][p^3] lattice kernel minus its row mean (periodic form)
+    void *Klbar;  // [comp][p^3] row means of the lattice kernel
+    void *Ktc_hi, *Ktc_lo;  // [comp][343][a][b] split of Kt, padded (tensor-core plans)
+    void *Kbar_tc;          // [comp][343][a] row means, padded to 32
+    alignas(64) unsigned char khi_map[4][128], klo_map[4][128];  // their TMA tensor maps
     bool tc;                // bilinear forms of every level on tensor cores
     int tc_mode;            // FMM_TC_*: split TF32 x3, TF32 x1, split BF16 x3
     int inject;             // FMM_INJECT_* for the next evaluation (test hook)
@@ -75,6 +78,51 @@ double lagrange(int p, double gs, int i, double x) {
 // 1/|r + m| for r in [-1,1]^3 (unit cubic box, tin-foil boundary, neutralising
 // background constant -pi/alpha^2): the Ewald pair potential of the unit box
 // minus its 27 nearest image terms (§4.2, periodic form, level 0).
+double far_image_sum(double rx, double ry, double rz);
+
+// Its gradient, term by term (the force kernel of the lattice term is minus
+// this): radial derivatives of -erf(a s)/s and erfc(a s)/s times (r + m)/s,
+// and -4 pi w h sin(2 pi h.r) for each reciprocal pair.
+void far_image_grad(double rx, double ry, double rz, double g[3]) {
+    const double alpha = 2.0;
+    const int RM = 7, HM = 7;
+    const double c2 = 2.0 * alpha / std::sqrt(M_PI);
+    g[0] = g[1] = g[2] = 0.0;
+    for (int mz = -RM; mz <= RM; mz++)
+        for (int my = -RM; my <= RM; my++)
+            for (int mx = -RM; mx <= RM; mx++) {
+                double x = rx + mx, y = ry + my, z = rz + mz;
+                double s = std::sqrt(x * x + y * y + z * z);
+                if (s == 0.0) continue;  // the near term is even and smooth at 0
+                bool near = std::abs(mx) <= 1 && std::abs(my) <= 1 && std::abs(mz) <= 1;
+                double e = c2 * std::exp(-alpha * alpha * s * s) / s;
+                double d = near ? -e + std::erf(alpha * s) / (s * s) : -e - std::erfc(alpha * s) / (s * s);
+                g[0] += d * x / s;
+                g[1] += d * y / s;
+                g[2] += d * z / s;
+            }
+    for (int hz = 0; hz <= HM; hz++)
+        for (int hy = -HM; hy <= HM; hy++)
+            for (int hx = -HM; hx <= HM; hx++) {
+                if (hz == 0 && (hy < 0 || (hy == 0 && hx <= 0))) continue;
+                double h2 = (double)(hx * hx + hy * hy + hz * hz);
+                double w = std::exp(-M_PI * M_PI * h2 / (alpha * alpha)) / (M_PI * h2);
+                double sn = std::sin(2.0 * M_PI * (hx * rx + hy * ry + hz * rz));
+                g[0] -= 4.0 * M_PI * w * hx * sn;
+                g[1] -= 4.0 * M_PI * w * hy * sn;
+                g[2] -= 4.0 * M_PI * w * hz * sn;
+            }
+}
+
+// The function of the bilinear forms between unit cells at separation
+// (dx, dy, dz) = a - (o + b): comp 0 is 1/r (§2.1.7), comps 1..3 the x, y, z
+// components of r/|r|^3 (§4.1: the forces directly from the kernel).
+double kernel_value(int comp, double dx, double dy, double dz) {
+    const double r2 = dx * dx + dy * dy + dz * dz, r = std::sqrt(r2);
+    if (comp == 0) return 1.0 / r;
+    return (comp == 1 ? dx : comp == 2 ? dy : dz) / (r2 * r);
+}
+
 double far_image_sum(double rx, double ry, double rz) {
     const double alpha = 2.0;
     const int RM = 7, HM = 7;
@@ -146,35 +194,36 @@ static float bf16_value(uint16_t h) {
 }
 
 // Unit-cell kernels of eq. (bilinear), K_o[a,b] = 1/|a - (o + b)| for the 316
-// offsets 2 <= |o|_inf <= 3, split into row mean and remainder (FP64, then
-// rounded to the plan's type).
+// offsets 2 <= |o|_inf <= 3 (and, with FMM_FORCE_KERNEL, the three force
+// kernels), split into row mean and remainder (FP64, then rounded to the
+// plan's type).
 template <typename real>
 int upload_tables(fmm_plan_t P) {
-    const int p = P->p, p3 = p * p * p;
+    const int p = P->p, p3 = p * p * p, nc = P->ncomp;
     const double gs = P->opts.grid_scale;
     const size_t nk = (size_t)343 * p3 * p3;
-    std::vector<real> KtT(nk, (real)0), Kbar((size_t)343 * p3, (real)0);
+    std::vector<real> KtT(nc * nk, (real)0), Kbar((size_t)nc * 343 * p3, (real)0);
     std::vector<double> row(p3);
-    for (int oz = -3; oz <= 3; oz++)
-        for (int oy = -3; oy <= 3; oy++)
-            for (int ox = -3; ox <= 3; ox++) {
-                if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
-                size_t oi = (size_t)(((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3));
-                for (int a = 0; a < p3; a++) {
-                    double ax = node(p, gs, a % p), ay = node(p, gs, (a / p) % p), az = node(p, gs, a / (p * p));
-                    double mean = 0.0;
-                    for (int b = 0; b < p3; b++) {
-                        double dx = ax - (ox + node(p, gs, b % p));
-                        double dy = ay - (oy + node(p, gs, (b / p) % p));
-                        double dz = az - (oz + node(p, gs, b / (p * p)));
-                        row[b] = 1.0 / std::sqrt(dx * dx + dy * dy + dz * dz);
-                        mean += row[b];
+    for (int c = 0; c < nc; c++)
+        for (int oz = -3; oz <= 3; oz++)
+            for (int oy = -3; oy <= 3; oy++)
+                for (int ox = -3; ox <= 3; ox++) {
+                    if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
+                    size_t oi = (size_t)c * 343 + (size_t)(((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3));
+                    for (int a = 0; a < p3; a++) {
+                        double ax = node(p, gs, a % p), ay = node(p, gs, (a / p) % p), az = node(p, gs, a / (p * p));
+                        double mean = 0.0;
+                        for (int b = 0; b < p3; b++) {
+                            row[b] = kernel_value(c, ax - (ox + node(p, gs, b % p)),
+                                                  ay - (oy + node(p, gs, (b / p) % p)),
+                                                  az - (oz + node(p, gs, b / (p * p))));
+                            mean += row[b];
+                        }
+                        mean /= p3;
+                        Kbar[oi * p3 + a] = (real)mean;
+                        for (int b = 0; b < p3; b++) KtT[(oi * p3 + b) * p3 + a] = (real)(row[b] - mean);
                     }
-                    mean /= p3;
-                    Kbar[oi * p3 + a] = (real)mean;
-                    for (int b = 0; b < p3; b++) KtT[(oi * p3 + b) * p3 + a] = (real)(row[b] - mean);
                 }
-            }
     int rc = upload(&P->Kunit, KtT);
     if (!rc) rc = upload(&P->Kbar, Kbar);
     if (rc) return rc;
@@ -187,26 +236,25 @@ int upload_tables(fmm_plan_t P) {
         const int p3s = tc_padded(p3), pk = tc_padded_k(p3, P->tc_mode);
         const bool bf16 = P->tc_mode == FMM_TC_BF16X3;
         const size_t nt = (size_t)343 * p3s * pk;
-        std::vector<float> Khi(nt, 0.0f), Klo(nt, 0.0f), Kb((size_t)343 * p3s, 0.0f);
-        std::vector<uint16_t> Khi16(bf16 ? nt : 0, 0), Klo16(bf16 ? nt : 0, 0);
-        for (int oi = 0; oi < 343; oi++) {
+        std::vector<float> Khi(nc * nt, 0.0f), Klo(nc * nt, 0.0f), Kb((size_t)nc * 343 * p3s, 0.0f);
+        std::vector<uint16_t> Khi16(bf16 ? nc * nt : 0, 0), Klo16(bf16 ? nc * nt : 0, 0);
+        for (int oc = 0; oc < 343 * nc; oc++) {
+            const int c = oc / 343, oi = oc % 343;
             int ox = oi % 7 - 3, oy = (oi / 7) % 7 - 3, oz = oi / 49 - 3;
             if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
             for (int a = 0; a < p3; a++) {
                 double ax = node(p, gs, a % p), ay = node(p, gs, (a / p) % p), az = node(p, gs, a / (p * p));
                 double mean = 0.0;
                 for (int b = 0; b < p3; b++) {
-                    double dx = ax - (ox + node(p, gs, b % p));
-                    double dy = ay - (oy + node(p, gs, (b / p) % p));
-                    double dz = az - (oz + node(p, gs, b / (p * p)));
-                    row[b] = 1.0 / std::sqrt(dx * dx + dy * dy + dz * dz);
+                    row[b] = kernel_value(c, ax - (ox + node(p, gs, b % p)), ay - (oy + node(p, gs, (b / p) % p)),
+                                          az - (oz + node(p, gs, b / (p * p))));
                     mean += row[b];
                 }
                 mean /= p3;
-                Kb[(size_t)oi * p3s + a] = (float)mean;
+                Kb[(size_t)oc * p3s + a] = (float)mean;
                 for (int b = 0; b < p3; b++) {
                     double k = row[b] - mean;
-                    size_t idx = ((size_t)oi * p3s + a) * pk + b;
+                    size_t idx = ((size_t)oc * p3s + a) * pk + b;
                     if (bf16) {
                         uint16_t h = bf16_rne((float)k);
                         Khi16[idx] = h;
@@ -228,33 +276,46 @@ int upload_tables(fmm_plan_t P) {
         rc = bf16 ? upload(&P->Ktc_hi, Khi16) : upload(&P->Ktc_hi, Khi);
         if (!rc) rc = bf16 ? upload(&P->Ktc_lo, Klo16) : upload(&P->Ktc_lo, Klo);
         if (!rc) rc = upload(&P->Kbar_tc, Kb);
-        if (!rc) rc = tc_encode_kernel_map(P->khi_map, P->Ktc_hi, p3s, pk, P->tc_mode);
-        if (!rc) rc = tc_encode_kernel_map(P->klo_map, P->Ktc_lo, p3s, pk, P->tc_mode);
+        const size_t cb = nt * (bf16 ? 2 : 4);  // bytes of one component's table
+        for (int c = 0; c < nc && !rc; c++) {
+            rc = tc_encode_kernel_map(P->khi_map[c], (const char *)P->Ktc_hi + c * cb, p3s, pk, P->tc_mode);
+            if (!rc) rc = tc_encode_kernel_map(P->klo_map[c], (const char *)P->Ktc_lo + c * cb, p3s, pk, P->tc_mode);
+        }
         if (rc) return rc;
     }
     if (P->periodic) {
-        // psi depends on a - b only: (2p-1)^3 distinct arguments
+        // psi depends on a - b only: (2p-1)^3 distinct arguments; the force
+        // components take -grad psi
         const int m = 2 * p - 1;
-        std::vector<double> tab((size_t)m * m * m);
+        std::vector<double> tab((size_t)nc * m * m * m);
         for (int dz = 0; dz < m; dz++)
             for (int dy = 0; dy < m; dy++)
-                for (int dx = 0; dx < m; dx++)
-                    tab[((size_t)dz * m + dy) * m + dx] =
-                        far_image_sum(gs * (dx - (p - 1)) / (double)(p - 1), gs * (dy - (p - 1)) / (double)(p - 1),
-                                      gs * (dz - (p - 1)) / (double)(p - 1));
-        std::vector<real> Kl((size_t)p3 * p3), Klb(p3);
-        for (int a = 0; a < p3; a++) {
-            double mean = 0.0;
-            for (int b = 0; b < p3; b++) {
-                int dx = a % p - b % p + p - 1, dy = (a / p) % p - (b / p) % p + p - 1,
-                    dz = a / (p * p) - b / (p * p) + p - 1;
-                row[b] = tab[((size_t)dz * m + dy) * m + dx];
-                mean += row[b];
+                for (int dx = 0; dx < m; dx++) {
+                    const double rx = gs * (dx - (p - 1)) / (double)(p - 1),
+                                 ry = gs * (dy - (p - 1)) / (double)(p - 1),
+                                 rz = gs * (dz - (p - 1)) / (double)(p - 1);
+                    const size_t e = ((size_t)dz * m + dy) * m + dx;
+                    tab[e] = far_image_sum(rx, ry, rz);
+                    if (nc > 1) {
+                        double gr[3];
+                        far_image_grad(rx, ry, rz, gr);
+                        for (int c = 1; c < nc; c++) tab[(size_t)c * m * m * m + e] = -gr[c - 1];
+                    }
+                }
+        std::vector<real> Kl((size_t)nc * p3 * p3), Klb((size_t)nc * p3);
+        for (int c = 0; c < nc; c++)
+            for (int a = 0; a < p3; a++) {
+                double mean = 0.0;
+                for (int b = 0; b < p3; b++) {
+                    int dx = a % p - b % p + p - 1, dy = (a / p) % p - (b / p) % p + p - 1,
+                        dz = a / (p * p) - b / (p * p) + p - 1;
+                    row[b] = tab[(size_t)c * m * m * m + ((size_t)dz * m + dy) * m + dx];
+                    mean += row[b];
+                }
+                mean /= p3;
+                Klb[(size_t)c * p3 + a] = (real)mean;
+                for (int b = 0; b < p3; b++) Kl[((size_t)c * p3 + a) * p3 + b] = (real)(row[b] - mean);
             }
-            mean /= p3;
-            Klb[a] = (real)mean;
-            for (int b = 0; b < p3; b++) Kl[(size_t)a * p3 + b] = (real)(row[b] - mean);
-        }
         rc = upload(&P->Klat, Kl);
         if (!rc) rc = upload(&P->Klbar, Klb);
         if (rc) return rc;
@@ -319,7 +380,8 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     W.phi_level[P->depth + 1] = ph * p3;
     W.loc_level[P->depth + 1] = lc * p3;
     W.phi = take((size_t)ph * p3 * rs);
-    W.loc = take((size_t)lc * p3 * rs);
+    W.loc_comp = lc * p3;  // functionals of one kernel component
+    W.loc = take((size_t)lc * p3 * rs * P->ncomp);
     int64_t qc = 0;
     for (int l = 0; l <= P->depth; l++) {
         W.q_level[l] = qc;
@@ -452,17 +514,21 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     }
     launch_upward<real>(g, C, ptr, W, F.main, tr);
     DevTables<real> T;
-    T.KtT = (const real *)P->Kunit;
-    T.Kbar = (const real *)P->Kbar;
-    T.Klt = (const real *)P->Klat;
-    T.Klbar = (const real *)P->Klbar;
+    const int p3 = g.p3;
+    T.ncomp = P->ncomp;
+    for (int c = 0; c < P->ncomp; c++) {
+        T.KtT[c] = (const real *)P->Kunit + (size_t)c * 343 * p3 * p3;
+        T.Kbar[c] = (const real *)P->Kbar + (size_t)c * 343 * p3;
+        T.Klt[c] = P->Klat ? (const real *)P->Klat + (size_t)c * p3 * p3 : nullptr;
+        T.Klbar[c] = P->Klbar ? (const real *)P->Klbar + (size_t)c * p3 : nullptr;
+        T.tc_khi_map[c] = P->khi_map[c];
+        T.tc_klo_map[c] = P->klo_map[c];
+        T.tc_kbar[c] = P->Kbar_tc ? (const float *)P->Kbar_tc + (size_t)c * 343 * tc_padded(p3) : nullptr;
+    }
     T.tc_lmin = P->tc ? (P->periodic ? 1 : 2) : 0;  // every level on the tensor cores
     T.tc_mode = P->tc_mode;
     T.tc_inject = P->inject;
     P->inject = FMM_INJECT_NONE;  // one evaluation only
-    T.tc_khi_map = P->khi_map;
-    T.tc_klo_map = P->klo_map;
-    T.tc_kbar = (const float *)P->Kbar_tc;
     T.sf_tab = (const double *)P->sf_tab;
     T.sf_base = P->sf_base;
     T.sf_H = (const double *)P->sf_H;
@@ -491,6 +557,8 @@ int backward_impl(fmm_plan_t P, int64_t n, const float *q, const double *gE, rea
                                                                         : (const void *)&P->cf);
     Geom g = P->geom;
     if (n == 0) return FMM_OK;
+    // the gradient of the energy: adjoint forces whatever the forward mode
+    if (g.force_mode == FMM_FORCE_KERNEL) g.force_mode = FMM_FORCE_ADJOINT;
     launch_p2p<real>(g, ptr, W, true, st, tr);
     launch_l2p<real>(g, C, ptr, W, true, st, tr);
     launch_unsplit<real>(g, ptr, W, (int)n, q, nullptr, nullptr, grad_pos, gE, grad_q, true, st, tr);
@@ -563,6 +631,10 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     // nodes: the reduced arrangement is for the plain form
     if (o.continuous && o.grid_scale != 1.0) return FMM_ERR_UNSUPPORTED;
     if (o.continuous && !(o.split_ratio < 0.5)) return FMM_ERR_ARG;
+    if (o.force_mode != FMM_FORCE_ADJOINT && o.force_mode != FMM_FORCE_PAPER &&
+        o.force_mode != FMM_FORCE_KERNEL)
+        return FMM_ERR_ARG;
+    if (o.force_mode == FMM_FORCE_KERNEL && o.shift_free) return FMM_ERR_UNSUPPORTED;
     const bool tc_prec = o.precision == FMM_PREC_TF32X3 || o.precision == FMM_PREC_TF32X1 ||
                          o.precision == FMM_PREC_BF16X3;
     if (o.precision != FMM_PREC_FP32 && o.precision != FMM_PREC_FP64 && !tc_prec)
@@ -581,6 +653,7 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     P->p = p;
     P->periodic = periodic ? 1 : 0;
     P->opts = o;
+    P->ncomp = o.force_mode == FMM_FORCE_KERNEL ? 4 : 1;
     memcpy(P->box, box, sizeof(double) * 4);
     P->max_n = max_n;
     P->fp64 = o.precision == FMM_PREC_FP64;

@@ -67,7 +67,7 @@ struct WsLayout {
     size_t tmp, perm, inv;
     size_t s_pt, s_origin, out_pt;
     size_t react;  // [13][cap] near-field reactions per forward direction (mutual near field)
-    size_t phi, loc;                      // all levels
+    size_t phi, loc;                      // all levels (loc: ncomp blocks of loc_comp)
     size_t qlev;                          // total charge of every cell, padded Phi layout
     size_t phihi, philo;                  // TF32 split of Phi (tensor-core plans)
     size_t m2l_part;                      // per-offset-group partials of the SIMT contraction
@@ -77,6 +77,7 @@ struct WsLayout {
     int64_t ncell;                        // 8^depth
     int64_t phi_level[FMM_MAXDEPTH + 2];  // element offset of each level in Phi
     int64_t loc_level[FMM_MAXDEPTH + 2];  // element offset of each level in L
+    int64_t loc_comp;                     // elements of one kernel component's L
     int64_t q_level[FMM_MAXDEPTH + 2];    // cell offset of each level in qlev
     int scan_blocks;
 };
@@ -197,18 +198,22 @@ struct Ptrs {
 // as sum_b Kt_o[a,b] Phi[b] + Kbar_o[a] Q with Q = sum_b Phi[b] the cell's total
 // charge (replacement conserves charge), which removes the cancellation of the
 // nearly constant kernel against grid charges of both signs.
+// Component c of every table: c = 0 the potential kernel 1/r, c = 1..3 the
+// force kernel r/|r|^3 (FMM_FORCE_KERNEL plans, ncomp = 4), whose forms scale
+// by 4^l instead of 2^l at level l.
 template <typename real>
 struct DevTables {
-    const real *KtT;    // [343][b][a] = Kt_o[a,b] (transposed, SIMT contraction)
-    const real *Kbar;   // [343][a]
-    const real *Klt;    // [a][b] lattice kernel minus its row mean (periodic form)
-    const real *Klbar;  // [a]
+    int ncomp;
+    const real *KtT[4];    // [343][b][a] = Kt_o[a,b] (transposed, SIMT contraction)
+    const real *Kbar[4];   // [343][a]
+    const real *Klt[4];    // [a][b] lattice kernel minus its row mean (periodic form)
+    const real *Klbar[4];  // [a]
     // tensor-core contraction (TF32X3 / TF32X1 / BF16X3 plans): levels >= tc_lmin, 0 = none
     int tc_lmin;
     int tc_mode;                          // FMM_TC_*
     int tc_inject;                        // FMM_INJECT_* test hook for this evaluation
-    const void *tc_khi_map, *tc_klo_map;  // CUtensorMap of the split unit-cell kernels
-    const float *tc_kbar;                 // [343][p3 padded to 32] row means
+    const void *tc_khi_map[4], *tc_klo_map[4];  // CUtensorMap of the split unit-cell kernels
+    const float *tc_kbar[4];                    // [343][p3 padded to 32] row means
     // App. A.2 forms (shift-free plans), FP64: right parts K_o shift_{S->C},
     // [level pairs from sf_base[l]][n][m]; per-axis shift_{S->C} of every level
     // from sf_hoff[l], [c][i][b]
@@ -262,9 +267,12 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
 #define FMM_TC_TF32X3 0  // 3-pass split TF32
 #define FMM_TC_TF32X1 1  // 1-pass TF32
 #define FMM_TC_BF16X3 2  // 3-pass split BF16
+// loc: the functionals to write (one kernel component); spow: forms scale by
+// 2^(l spow) at level l; split: also split the grid charges into the operand
+// copies (once per evaluation)
 int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
                   const void *k_lo_map, const float *kbar, int lmin, int mode, int inject,
-                  cudaStream_t st, Tracer &tr);
+                  float *loc, int spow, bool split, cudaStream_t st, Tracer &tr);
 // map of a [343][p3s][pk] kernel table: fp32 (pk = p3s) or bf16 (pk = tc_padded_k)
 int tc_encode_kernel_map(void *map, const void *base, int p3s, int pk, int mode);
 int tc_padded(int p3);            // p^3 rounded up to 32 (MMA N, fp32 K)

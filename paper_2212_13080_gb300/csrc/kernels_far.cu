@@ -331,7 +331,8 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
                                                      const real *__restrict__ q_l,
                                                      real *__restrict__ loc_l,
                                                      const real *__restrict__ KtT,
-                                                     const real *__restrict__ Kbar, int ngroups) {
+                                                     const real *__restrict__ Kbar, int ngroups,
+                                                     int spow) {
     typedef typename Vec4<real>::T real4;
     extern __shared__ __align__(16) unsigned char smraw[];
     real *Ps = reinterpret_cast<real *>(smraw);  // [64 b][64 cells]
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(M2L_BS) k_m2l_simt(int p, int l, const real *_
                     }
             }
     // ngroups > 1: loc_l is the partial buffer of this group (level layout)
-    const real scale = (real)(1 << l);
+    const real scale = (real)(1 << (l * spow));  // unit cells -> unit box: 2^l (1/r), 4^l (r/|r|^3)
     real *dst = loc_l + (int64_t)grp * ((int64_t)1 << (3 * l)) * p3;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -601,14 +602,19 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
     const int p = g.p, p3 = g.p3, depth = g.depth;
     const int achunks = (p3 + M2L_T - 1) / M2L_T;
     const size_t sm_m2l = sizeof(real) * (2 * M2L_T * M2L_T + 2 * M2L_T);
-    // 1. every level's own interaction-list contributions (they only need Phi):
-    //    L_0 = lattice term (periodic), L_l = sum over the interaction list
+    // 1. every level's own interaction-list contributions (they only need Phi),
+    //    for every kernel component c (its own L block, forms scaled by
+    //    2^(l spow)): L_0 = lattice term (periodic), L_l = sum over the
+    //    interaction list
     const int lstart = g.periodic ? 1 : 2;
     if (g.periodic) {
         tr.begin(FMM_STAGE_M2L, st);
-        k_lattice<real><<<1, 256, 0, st>>>(p3, T.Klt, T.Klbar, P.phi + W.phi_level[0],
-                                           P.qlev + W.q_level[0], P.loc + W.loc_level[0]);
-        tr.count();
+        for (int c = 0; c < T.ncomp; c++) {
+            k_lattice<real><<<1, 256, 0, st>>>(p3, T.Klt[c], T.Klbar[c], P.phi + W.phi_level[0],
+                                               P.qlev + W.q_level[0],
+                                               P.loc + c * W.loc_comp + W.loc_level[0]);
+            tr.count();
+        }
         tr.end();
     }
     if (g.shift_free) {  // App. A.2: precomputed forms, identity downward pass
@@ -621,51 +627,62 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
     // the SIMT levels run on the coarse stream, beside the tensor-core levels
     cudaEventRecord(S.fork, st);
     cudaStreamWaitEvent(S.coarse, S.fork, 0);
-    for (int l = lstart; l <= lsimt_end; l++) {
-        const int H = 1 << (l - 1);
-        const int Tt = H < 4 ? H : 4;
-        const int ntiles = (H / Tt) * (H / Tt) * (H / Tt);
-        const int G = m2l_groups(l, p3);
-        dim3 grid(ntiles, 8, achunks * G);
-        real *dst = G > 1 ? P.m2l_part : P.loc + W.loc_level[l];
-        tr.begin(FMM_STAGE_M2L, S.coarse);
-        k_m2l_simt<real><<<grid, M2L_BS, sm_m2l, S.coarse>>>(p, l, P.phi + W.phi_level[l],
-                                                             P.qlev + W.q_level[l], dst, T.KtT,
-                                                             T.Kbar, G);
-        tr.count();
-        if (G > 1) {
-            const int64_t n = ((int64_t)1 << (3 * l)) * p3;
-            int nb = (int)((n + 255) / 256);
-            if (nb > 152 * 16) nb = 152 * 16;
-            k_m2l_reduce<real><<<nb, 256, 0, S.coarse>>>(G, n, P.m2l_part, P.loc + W.loc_level[l]);
+    for (int c = 0; c < T.ncomp; c++) {
+        real *loc_c = P.loc + c * W.loc_comp;
+        const int spow = c == 0 ? 1 : 2;
+        for (int l = lstart; l <= lsimt_end; l++) {
+            const int H = 1 << (l - 1);
+            const int Tt = H < 4 ? H : 4;
+            const int ntiles = (H / Tt) * (H / Tt) * (H / Tt);
+            const int G = m2l_groups(l, p3);
+            dim3 grid(ntiles, 8, achunks * G);
+            real *dst = G > 1 ? P.m2l_part : loc_c + W.loc_level[l];
+            tr.begin(FMM_STAGE_M2L, S.coarse);
+            k_m2l_simt<real><<<grid, M2L_BS, sm_m2l, S.coarse>>>(p, l, P.phi + W.phi_level[l],
+                                                                 P.qlev + W.q_level[l], dst, T.KtT[c],
+                                                                 T.Kbar[c], G, spow);
             tr.count();
+            if (G > 1) {
+                const int64_t n = ((int64_t)1 << (3 * l)) * p3;
+                int nb = (int)((n + 255) / 256);
+                if (nb > 152 * 16) nb = 152 * 16;
+                k_m2l_reduce<real><<<nb, 256, 0, S.coarse>>>(G, n, P.m2l_part, loc_c + W.loc_level[l]);
+                tr.count();
+            }
+            tr.end();
         }
-        tr.end();
     }
     cudaEventRecord(S.coarse_done, S.coarse);
     if constexpr (std::is_same<real, float>::value) {
         if (T.tc_lmin > 0 && depth >= T.tc_lmin) {
-            int rc = launch_m2l_tc(g, P, W, T.tc_khi_map, T.tc_klo_map, T.tc_kbar, T.tc_lmin,
-                                   T.tc_mode, T.tc_inject, st, tr);
-            if (rc) return rc;
+            for (int c = 0; c < T.ncomp; c++) {
+                int rc = launch_m2l_tc(g, P, W, T.tc_khi_map[c], T.tc_klo_map[c], T.tc_kbar[c], T.tc_lmin,
+                                       T.tc_mode, T.tc_inject, P.loc + c * W.loc_comp, c == 0 ? 1 : 2,
+                                       c == 0, st, tr);
+                if (rc) return rc;
+            }
         }
     }
     cudaStreamWaitEvent(st, S.coarse_done, 0);
-    // 2. downward: Psi_child = Psi_parent o shift, added level by level
-    for (int l = g.periodic ? 1 : 3; l <= depth; l++) {
-        int nparent = 1 << (3 * (l - 1));
-        tr.begin(FMM_STAGE_L2L, st);
-        switch (p) {
+    // 2. downward: Psi_child = Psi_parent o shift, added level by level (the
+    //    shift acts on functionals whatever their kernel)
+    for (int c = 0; c < T.ncomp; c++) {
+        real *loc_c = P.loc + c * W.loc_comp;
+        for (int l = g.periodic ? 1 : 3; l <= depth; l++) {
+            int nparent = 1 << (3 * (l - 1));
+            tr.begin(FMM_STAGE_L2L, st);
+            switch (p) {
 #define CASE(PP)                                                                                   \
     case PP:                                                                                       \
         k_l2l<real, PP><<<nparent, M2M_BS, l2l_smem<real, PP>(), st>>>(                            \
-            C, l, P.loc + W.loc_level[l - 1], P.loc + W.loc_level[l]);                             \
+            C, l, loc_c + W.loc_level[l - 1], loc_c + W.loc_level[l]);                             \
         break;
-            CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+                CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
+            }
+            tr.count();
+            tr.end();
         }
-        tr.count();
-        tr.end();
     }
     return FMM_OK;
 }

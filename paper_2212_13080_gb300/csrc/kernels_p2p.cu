@@ -45,36 +45,46 @@ __device__ __forceinline__ int64_t nf_cell(int cx, int cy, int cz, int dx, int d
 
 // ---------------------------------------------------------------------------
 // far field: phi_far = sum_ijk g_i(t_x) g_j(t_y) g_k(t_z) L_leaf[ijk] and
-// F_far = -q * 2^depth * grad_t phi_far.  One CTA per four consecutive finest
-// cells (their charges are one contiguous range), L_leaf in shared memory, one
-// thread per charge.
+// F_far = -q * 2^depth * grad_t phi_far.  KF (force kernels, §4.1): the far
+// force is q times the plain weights against the three force functionals,
+// F_far,c = q g(t) . L^c_leaf.  One CTA per four consecutive finest cells
+// (their charges are one contiguous range; one cell when the four cells'
+// functionals would not fit the static shared memory), L_leaf in shared
+// memory, one thread per charge.
 // ---------------------------------------------------------------------------
 #define L2P_BS 128
 #define L2P_LPC 4  // finest cells per CTA (consecutive keys: one contiguous charge range)
 
-template <typename real, int P, bool FORCES>
+template <typename real, int P, bool KF>
+constexpr int l2p_lpc() {
+    return (KF && (size_t)L2P_LPC * 4 * P * P * P * sizeof(real) > 24576) ? 1 : L2P_LPC;
+}
+
+template <typename real, int P, bool FORCES, bool KF>
 __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int periodic, int ncell, int sf,
                                                 const int *__restrict__ leaf_start,
                                                 const typename Vec4<real>::T *__restrict__ s_pt,
-                                                const real *__restrict__ loc_leaf,
+                                                const real *__restrict__ loc_leaf, int64_t loc_comp,
                                                 const typename Vec4<real>::T *__restrict__ react,
                                                 int64_t rstride,
                                                 typename Vec4<real>::T *__restrict__ out_pt) {
     typedef typename Vec4<real>::T real4;
     constexpr int P3 = P * P * P;
-    __shared__ real Ls[L2P_LPC][P3];
-    __shared__ int slot_ok[L2P_LPC][NF_SEGS - 1];
-    __shared__ int lst[L2P_LPC + 1];
-    __shared__ real org[L2P_LPC][3];  // coordinate of the weights: org + h t
-    const int k0 = blockIdx.x * L2P_LPC;
-    const int nleaf = min(L2P_LPC, ncell - k0);
-    if (threadIdx.x <= L2P_LPC) lst[threadIdx.x] = leaf_start[min(k0 + (int)threadIdx.x, ncell)];
-    for (int e = threadIdx.x; e < nleaf * P3; e += blockDim.x) {
-        const int j = e / P3, o = e % P3;
+    constexpr int LPC = l2p_lpc<real, P, KF>();
+    constexpr int NCL = KF ? 4 : 1;  // functionals per cell: potential (+ 3 force components)
+    __shared__ real Ls[LPC][NCL][P3];
+    __shared__ int slot_ok[LPC][NF_SEGS - 1];
+    __shared__ int lst[LPC + 1];
+    __shared__ real org[LPC][3];  // coordinate of the weights: org + h t
+    const int k0 = blockIdx.x * LPC;
+    const int nleaf = min(LPC, ncell - k0);
+    if (threadIdx.x <= LPC) lst[threadIdx.x] = leaf_start[min(k0 + (int)threadIdx.x, ncell)];
+    for (int e = threadIdx.x; e < nleaf * NCL * P3; e += blockDim.x) {
+        const int j = e / (NCL * P3), c = (e / P3) % NCL, o = e % P3;
         int cx, cy, cz;
         morton_decode((uint32_t)(k0 + j), cx, cy, cz);
-        Ls[j][o] = loc_leaf[loc_cell(depth, cx, cy, cz) * P3 + o];
-        if (o < 3) org[j][o] = sf ? (real)(o == 0 ? cx : o == 1 ? cy : cz) / (real)(1 << depth) : real(0);
+        Ls[j][c][o] = loc_leaf[c * loc_comp + loc_cell(depth, cx, cy, cz) * P3 + o];
+        if (c == 0 && o < 3) org[j][o] = sf ? (real)(o == 0 ? cx : o == 1 ? cy : cz) / (real)(1 << depth) : real(0);
     }
     // slot d - 1 of a cell's charges was written by the cell (that cell -
     // delta_d), d = 1..13, if it exists and holds charges
@@ -94,12 +104,11 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
     for (int s = lst[0] + threadIdx.x; s < lst[nleaf]; s += blockDim.x) {
         int lf = 0;  // which of the CTA's cells holds charge s
         while (s >= lst[lf + 1]) lf++;
-        const real *Lc = Ls[lf];
         const int *okc = slot_ok[lf];
         typename Vec4<real>::T v = s_pt[s];
         const real X = org[lf][0] + h * v.x, Y = org[lf][1] + h * v.y, Z = org[lf][2] + h * v.z;
         real gx[FMM_MAXP], gy[FMM_MAXP], gz[FMM_MAXP], dx[FMM_MAXP], dy[FMM_MAXP], dz[FMM_MAXP];
-        if (FORCES) {
+        if (FORCES && !KF) {
             lag_weights_deriv(C, P, X, gx, dx);
             lag_weights_deriv(C, P, Y, gy, dy);
             lag_weights_deriv(C, P, Z, gz, dz);
@@ -109,30 +118,60 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
             lag_weights(C, P, Z, gz);
         }
         real phi = 0, fx = 0, fy = 0, fz = 0;
+        if (KF) {
+            const real *L0 = Ls[lf][0], *L1 = Ls[lf][NCL > 1 ? 1 : 0], *L2 = Ls[lf][NCL > 2 ? 2 : 0],
+                       *L3 = Ls[lf][NCL > 3 ? 3 : 0];
 #pragma unroll 1
-        for (int k = 0; k < P; k++) {
-            real ax = 0, ay = 0, az = 0, aw = 0;
+            for (int k = 0; k < P; k++) {
+                real a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll
-            for (int j = 0; j < P; j++) {
-                real rx = 0, rdx = 0;
+                for (int j = 0; j < P; j++) {
+                    real r0 = 0, r1 = 0, r2 = 0, r3 = 0;
 #pragma unroll
-                for (int i = 0; i < P; i++) {
-                    real Lv = Lc[(k * P + j) * P + i];
-                    rx += gx[i] * Lv;
-                    if (FORCES) rdx += dx[i] * Lv;
+                    for (int i = 0; i < P; i++) {
+                        const int o = (k * P + j) * P + i;
+                        r0 += gx[i] * L0[o];
+                        r1 += gx[i] * L1[o];
+                        r2 += gx[i] * L2[o];
+                        r3 += gx[i] * L3[o];
+                    }
+                    a0 += gy[j] * r0;
+                    a1 += gy[j] * r1;
+                    a2 += gy[j] * r2;
+                    a3 += gy[j] * r3;
                 }
-                ax += gy[j] * rx;
-                if (FORCES) {
-                    ay += gy[j] * rdx;
-                    az += dy[j] * rx;
-                    aw += gy[j] * rx;
-                }
+                phi += gz[k] * a0;
+                fx += gz[k] * a1;
+                fy += gz[k] * a2;
+                fz += gz[k] * a3;
             }
-            phi += gz[k] * ax;
-            if (FORCES) {
-                fx += gz[k] * ay;
-                fy += gz[k] * az;
-                fz += dz[k] * aw;
+        } else {
+            const real *Lc = Ls[lf][0];
+#pragma unroll 1
+            for (int k = 0; k < P; k++) {
+                real ax = 0, ay = 0, az = 0, aw = 0;
+#pragma unroll
+                for (int j = 0; j < P; j++) {
+                    real rx = 0, rdx = 0;
+#pragma unroll
+                    for (int i = 0; i < P; i++) {
+                        real Lv = Lc[(k * P + j) * P + i];
+                        rx += gx[i] * Lv;
+                        if (FORCES) rdx += dx[i] * Lv;
+                    }
+                    ax += gy[j] * rx;
+                    if (FORCES) {
+                        ay += gy[j] * rdx;
+                        az += dy[j] * rx;
+                        aw += gy[j] * rx;
+                    }
+                }
+                phi += gz[k] * ax;
+                if (FORCES) {
+                    fx += gz[k] * ay;
+                    fy += gz[k] * az;
+                    fz += dz[k] * aw;
+                }
             }
         }
         // near field: own sums, then the reactions of the 13 slots in order
@@ -147,9 +186,15 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
             o.w += r.w;
         }
         o.x += phi;
-        o.y += -v.w * FS * fx;
-        o.z += -v.w * FS * fy;
-        o.w += -v.w * FS * fz;
+        if (KF) {  // the force functionals are in unit-box units already
+            o.y += v.w * fx;
+            o.z += v.w * fy;
+            o.w += v.w * fz;
+        } else {
+            o.y += -v.w * FS * fx;
+            o.z += -v.w * FS * fy;
+            o.w += -v.w * FS * fz;
+        }
         out_pt[s] = o;
     }
 }
@@ -483,21 +528,22 @@ void launch_l2p(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const W
                 bool forces, cudaStream_t st, Tracer &tr) {
     const int ncell = (int)W.ncell, depth = g.depth;
     const real *loc_leaf = P.loc + W.loc_level[depth];
+    const bool kf = forces && g.force_mode == FMM_FORCE_KERNEL;
     tr.begin(FMM_STAGE_L2P, st);
+#define L2P(PP, F, K)                                                                              \
+    k_l2p<real, PP, F, K><<<(ncell + l2p_lpc<real, PP, K>() - 1) / l2p_lpc<real, PP, K>(), L2P_BS, 0, st>>>( \
+        C, depth, g.periodic, ncell, g.shift_free, P.leaf_start, P.s_pt, loc_leaf, W.loc_comp,      \
+        P.react, W.cap, P.out_pt)
     switch (g.p) {
 #define CASE(PP)                                                                                 \
     case PP:                                                                                     \
-        if (forces)                                                                              \
-            k_l2p<real, PP, true><<<(ncell + L2P_LPC - 1) / L2P_LPC, L2P_BS, 0, st>>>(C, depth, g.periodic, ncell, g.shift_free, P.leaf_start,  \
-                                                           P.s_pt, loc_leaf, P.react, W.cap,    \
-                                                           P.out_pt);                           \
-        else                                                                                     \
-            k_l2p<real, PP, false><<<(ncell + L2P_LPC - 1) / L2P_LPC, L2P_BS, 0, st>>>(C, depth, g.periodic, ncell, g.shift_free, P.leaf_start, \
-                                                            P.s_pt, loc_leaf, P.react, W.cap,   \
-                                                            P.out_pt);                          \
+        if (kf) L2P(PP, true, true);                                                             \
+        else if (forces) L2P(PP, true, false);                                                   \
+        else L2P(PP, false, false);                                                              \
         break;
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
+#undef L2P
     }
     tr.count();
     tr.end();

@@ -494,7 +494,8 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
                 Ny += d.z * o.x;
                 Nz += d.w * o.x;
             }
-            unsigned ax = g.force_mode == FMM_FORCE_PAPER ? 0u : axes[i];
+            // paper and force-kernel forces: the sum of the split charges' forces
+            unsigned ax = g.force_mode != FMM_FORCE_ADJOINT ? 0u : axes[i];
             real qi = (real)q[i];
             Fx = (ax & 1) ? -qi * Nx : Sx;
             Fy = (ax & 2) ? -qi * Ny : Sy;

@@ -56,6 +56,7 @@ struct TcParams {
     CUtensorMap k_hi, k_lo;
     int first_block[FMM_MAXDEPTH + 2];
     int lmin, lmax, p3;
+    int spow;  // the forms of level l scale by 2^(l spow): 1 for 1/r, 2 for r/|r|^3
     long long loc_off[FMM_MAXDEPTH + 1];
     long long q_off[FMM_MAXDEPTH + 1];
     float *loc;
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
         const int cx = 2 * (X0 + tx) + bx, cy = 2 * (Y0 + ty) + by, cz = 2 * (Z0 + tz) + bz;
         const int p3 = prm.p3;
         float *out = prm.loc + prm.loc_off[l] + (valid ? loc_cell(l, cx, cy, cz) : 0) * p3 + c0;
-        const float scale = (float)(1 << l);
+        const float scale = (float)(1 << (l * prm.spow));
         if (ok) {
             if (valid) {
 #pragma unroll
@@ -475,7 +476,7 @@ static int launch_tc_mode(int p3s, const TcParams &prm, int blocks, cudaStream_t
 
 int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
                   const void *k_lo_map, const float *kbar, int lmin, int mode, int inject,
-                  cudaStream_t st, Tracer &tr) {
+                  float *loc, int spow, bool split, cudaStream_t st, Tracer &tr) {
     const int depth = g.depth, p3 = g.p3, p3s = tc_padded(p3), pk = tc_padded_k(p3, mode);
     const bool bf16 = mode == FMM_TC_BF16X3;
     // the grid charges of levels lmin..depth in the operand layout, split into
@@ -491,11 +492,13 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
     tr.begin(FMM_STAGE_M2L, st);
     __nv_bfloat16 *hi16 = reinterpret_cast<__nv_bfloat16 *>(P.phihi);
     __nv_bfloat16 *lo16 = reinterpret_cast<__nv_bfloat16 *>(P.philo);
-    if (bf16)
-        k_split_bf16<<<152 * 8, 256, 0, st>>>(P.phi, SL, hi16, lo16, p3, pk);
-    else
-        k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi, SL, P.phihi, P.philo, p3, p3s, mode == FMM_TC_TF32X1);
-    tr.count();
+    if (split) {
+        if (bf16)
+            k_split_bf16<<<152 * 8, 256, 0, st>>>(P.phi, SL, hi16, lo16, p3, pk);
+        else
+            k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi, SL, P.phihi, P.philo, p3, p3s, mode == FMM_TC_TF32X1);
+        tr.count();
+    }
     TcParams prm;
     memset(&prm, 0, sizeof(prm));
     int blocks = 0;
@@ -518,7 +521,8 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
     prm.lmin = lmin;
     prm.lmax = depth;
     prm.p3 = p3;
-    prm.loc = P.loc;
+    prm.spow = spow;
+    prm.loc = loc;
     prm.qlev = P.qlev;
     prm.kbar = kbar;
     prm.status = &P.hdr->status;

@@ -84,3 +84,21 @@ def test_shift_free_options_rejected_before_any_device_call():
         with pytest.raises(B.FmmError) as e:
             B.fmm_plan_create(box, depth, p, False, o, 1000)
         assert e.value.code == B.FMM_ERR_UNSUPPORTED, (depth, p)
+
+
+def test_force_mode_validated_before_any_device_call():
+    import pytest
+    from paper_2212_13080_gb300 import _binding as B
+    box = (0.0, 0.0, 0.0, 1.0)
+    o = B.fmm_opts_default()
+    o.force_mode = 7
+    with pytest.raises(B.FmmError) as e:
+        B.fmm_plan_create(box, 3, 4, False, o, 1000)
+    assert e.value.code == B.FMM_ERR_ARG
+    o = B.fmm_opts_default()
+    o.force_mode = B.FMM_FORCE_KERNEL
+    o.precision = B.FMM_PREC_FP64
+    o.shift_free = 1
+    with pytest.raises(B.FmmError) as e:
+        B.fmm_plan_create(box, 3, 4, False, o, 1000)
+    assert e.value.code == B.FMM_ERR_UNSUPPORTED
