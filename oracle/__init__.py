@@ -94,6 +94,7 @@ def lib():
         L.orc_sf_downward.restype = i32
         L.orc_sf_evaluate.argtypes = [i32, i32, i32, i64, P, P, P, P, P, P, P, P, P, P]
         L.orc_set_kernel.argtypes = [i32]
+        L.orc_set_power.argtypes = [i32]
         L.orc_lattice_grad.argtypes = [d, d, d, P]
         L.orc_evaluate_kernel.argtypes = [i32, i32, i32, i64, P, P, P, P, P, P, P, P, P, P, P, P,
                                           P]
@@ -240,10 +241,21 @@ def unit_coords(pos, box, periodic):
     return u.astype(np.float64), err
 
 
-def direct(pos, q, box, periodic=False, targets=None):
+def direct(pos, q, box, periodic=False, targets=None, power=1):
     """O(N^2) Coulomb sum (open) or Ewald sum with tin-foil boundary
     (periodic) on the canonical coordinates.  Returns (phi, F) at targets,
-    physical units."""
+    physical units.  power=2: the 1/r^2 sum (open only)."""
+    if power != 1:
+        if periodic:
+            raise ValueError("the lattice sum of 1/r^2 diverges")
+        L_ = lib()
+        L_.orc_set_power(int(power))
+        try:
+            phi, F = direct(pos, q, box, False, targets)
+        finally:
+            L_.orc_set_power(1)
+        Lb = float(np.asarray(box, np.float64)[3])
+        return phi * Lb / Lb ** power, F * Lb ** 2 / Lb ** (power + 1)
     u, err = unit_coords(pos, box, periodic)
     if err:
         raise ValueError("oracle: input outside the box or not finite (flags %d)" % err)
@@ -282,26 +294,41 @@ def level_offset(n, l):
 
 
 def fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sample=None,
-        keep=True, grid_scale=1.0, shift_free=False, force_kernel=False):
+        keep=True, grid_scale=1.0, shift_free=False, force_kernel=False, power=1):
     """Runs the oracle FMM; grid_scale < 1 takes the reduced arrangement of the
     n-division points (§4.1: spacing times grid_scale about the cell centre);
     shift_free takes the bilinear forms without shifts of App. A.2 (grid
     charges and functionals of every cell with respect to the box).  See _fmm
     for the other arguments.  force_kernel takes the far forces from the force
     kernels (x - x~)/|P - P~|^3 (§4.1) instead of the derivative of the weights;
-    "F" is then the sum of the forces on a particle's charges."""
+    "F" is then the sum of the forces on a particle's charges.  power=2 takes
+    F(P, P~) = 1/|P - P~|^2 (the other function §4.1 names) for the far forms
+    and the near field alike (open boundary: its lattice sum diverges)."""
     if continuous and grid_scale != 1.0:
         raise ValueError("the reduced arrangement is defined for the plain form")
     if shift_free and force_kernel:
         raise ValueError("the shift-free forms are built for the potential kernel")
+    if power != 1 and (periodic or shift_free):
+        raise ValueError("1/r^2: open boundary, shifted forms only")
     L_ = lib()
     L_.orc_set_grid_scale(float(grid_scale))
+    L_.orc_set_power(int(power))
     try:
-        return _fmm(pos, q, box, depth, n, periodic, continuous, dt, sample, keep, shift_free,
-                    force_kernel)
+        out = _fmm(pos, q, box, depth, n, periodic, continuous, dt, sample, keep, shift_free,
+                   force_kernel)
     finally:
         L_.orc_set_grid_scale(1.0)
         L_.orc_set_kernel(0)
+        L_.orc_set_power(1)
+    if power != 1:  # unit-box results scale as L^-power (potential), L^-(power+1) (forces)
+        Lb = float(np.asarray(box, np.float64)[3])
+        f_phi, f_F = Lb / Lb ** power, Lb ** 2 / Lb ** (power + 1)
+        for k in ("phi", "E"):
+            if out.get(k) is not None:
+                out[k] = out[k] * f_phi
+        for k in ("F", "F_paper"):
+            out[k] = out[k] * f_F
+    return out
 
 
 def _fmm(pos, q, box, depth, n, periodic=False, continuous=False, dt=None, sample=None,

@@ -104,14 +104,25 @@ void orc_shift_matrix(int n, int h, double *G)
  * by 2^l (potential) or 4^l (force components). */
 static int g_kernel = 0;
 void orc_set_kernel(int c) { g_kernel = c; }
+/* The same remark names 1/|P - P~|^2 as another function the replacement
+ * applies to.  g_power = 1: F = 1/r (default); g_power = 2: F = 1/r^2, whose
+ * force components are 2 (x - x~)/r^4.  Forms scale by 2^(l g_power) and
+ * 2^(l (g_power + 1)) at level l. */
+static int g_power = 1;
+void orc_set_power(int k) { g_power = k; }
 static double kernel_value(double dx, double dy, double dz)
 {
     double r2 = dx * dx + dy * dy + dz * dz, r = sqrt(r2);
+    if (g_power == 2) {
+        if (g_kernel == 0) return 1.0 / r2;
+        double d = g_kernel == 1 ? dx : g_kernel == 2 ? dy : dz;
+        return 2.0 * d / (r2 * r2);
+    }
     if (g_kernel == 0) return 1.0 / r;
     double d = g_kernel == 1 ? dx : g_kernel == 2 ? dy : dz;
     return d / (r2 * r);
 }
-static double level_scale(int l) { return ldexp(1.0, g_kernel == 0 ? l : 2 * l); }
+static double level_scale(int l) { return ldexp(1.0, g_kernel == 0 ? g_power * l : (g_power + 1) * l); }
 
 /* §2.1.7, eqs. (newer), (bilinear): F(P(a), P(a~)) = 1/|a - a~| between the
  * n-division points a of the unit cell at the origin and a~ of the unit cell
@@ -310,7 +321,8 @@ void orc_ewald_direct(int64_t N, const double *x, const double *q, int64_t nt,
     }
 }
 
-/* Plain O(N^2) Coulomb sum, open boundary: phi_i = sum_{j != i} q_j/|x_i - x_j|
+/* Plain O(N^2) Coulomb sum (or the 1/r^2 sum, orc_set_power(2)), open boundary:
+ * phi_i = sum_{j != i} q_j/|x_i - x_j|
  * and F_i = q_i sum_{j != i} q_j (x_i - x_j)/|x_i - x_j|^3, at particles tgt[].
  * Coincident pairs are skipped. */
 void orc_direct_open(int64_t N, const double *x, const double *q, int64_t nt,
@@ -327,8 +339,9 @@ void orc_direct_open(int64_t N, const double *x, const double *q, int64_t nt,
             double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 == 0.0) continue;
             double r = sqrt(r2);
-            p += q[j] / r;
-            double c = q[j] / (r2 * r);
+            /* 1/r, or 1/r^2 (orc_set_power(2)) with force 2 q q' r/r^4 */
+            p += g_power == 2 ? q[j] / r2 : q[j] / r;
+            double c = g_power == 2 ? 2.0 * q[j] / (r2 * r2) : q[j] / (r2 * r);
             fx += c * dx;
             fy += c * dy;
             fz += c * dz;
@@ -811,8 +824,10 @@ static void near_field(int depth, int periodic, int64_t s, const double *st, con
                         continue;
                     }
                     double rr = sqrt(r2);
-                    pn += sq[r] / rr;
-                    double c = sq[s] * sq[r] / (r2 * rr);
+                    /* pair potential q/r^g_power; force -q_s q_r grad_s (1/r^g_power) */
+                    pn += g_power == 2 ? sq[r] / r2 : sq[r] / rr;
+                    double c = g_power == 2 ? 2.0 * sq[s] * sq[r] / (r2 * r2)
+                                            : sq[s] * sq[r] / (r2 * rr);
                     nfx += c * rx;
                     nfy += c * ry;
                     nfz += c * rz;

@@ -595,3 +595,54 @@ def test_force_kernel_forces_converge_to_direct_sum(periodic):
         errs.append(ek)
     assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:])), errs
     assert errs[-1] < 1e-4
+
+
+# --- §4.1: the 1/r^2 kernel ------------------------------------------------------
+
+def test_inverse_square_tables_closed_form():
+    """F = 1/r^2: table entries 1/|a - o - b|^2 and force components
+    2 (a - o - b)_c / |a - o - b|^4 (= -d/da_c of 1/r^2)."""
+    n = 3
+    a = oracle.nodes(n)
+    o = (-2, 3, 0)
+    lib = oracle.lib()
+    lib.orc_set_power(2)
+    try:
+        tabs = [oracle.m2l_kernel(n, o, comp=c) for c in range(4)]
+    finally:
+        lib.orc_set_power(1)
+    for ia in range(n ** 3):
+        ta = np.array([a[ia % n], a[(ia // n) % n], a[ia // (n * n)]])
+        for ib in range(n ** 3):
+            r = ta - np.array(o) - np.array([a[ib % n], a[(ib // n) % n], a[ib // (n * n)]])
+            r2 = r @ r
+            assert abs(tabs[0][ia, ib] - 1 / r2) < 1e-15
+            for c in range(3):
+                assert abs(tabs[c + 1][ia, ib] - 2 * r[c] / r2 ** 2) < 1e-15
+
+
+def test_inverse_square_converges_and_scales():
+    """The replacement FMM of 1/r^2 (§4.1) converges to the direct 1/r^2 sum
+    as the order grows, for the potentials, the derivative forces and the
+    kernel forces (which conserve momentum); and it is homogeneous: the same
+    charges in a box twice as large have 1/4 the potentials and 1/8 the
+    forces."""
+    pos, q, box = inputs.uniform_pm1(3000, 4)
+    phi_d, F_d = oracle.direct(pos, q, box, power=2)
+    rel = lambda x, y: np.linalg.norm(x - y) / np.linalg.norm(y)
+    prev = None
+    for n in (3, 4, 5, 6):
+        a = oracle.fmm(pos, q, box, 3, n, power=2, keep=False)
+        b = oracle.fmm(pos, q, box, 3, n, power=2, force_kernel=True, keep=False)
+        e = (rel(a["phi"], phi_d), rel(a["F"], F_d), rel(b["F"], F_d))
+        if prev is not None:
+            assert all(x < y for x, y in zip(e, prev)), (n, e, prev)
+        prev = e
+        assert np.abs(b["F"].sum(axis=0)).max() < 1e-13 * np.abs(b["F"]).sum()
+    assert max(prev) < 1e-5
+    pos2 = (pos.astype(np.float64) * 2).astype(np.float32)
+    a1 = oracle.fmm(pos, q, box, 3, 4, power=2, keep=False)
+    a2 = oracle.fmm(pos2, q, (0.0, 0.0, 0.0, 2.0), 3, 4, power=2, keep=False)
+    np.testing.assert_allclose(4 * a2["phi"], a1["phi"], rtol=1e-14)
+    np.testing.assert_allclose(8 * a2["F"], a1["F"], rtol=1e-14, atol=1e-14 * np.abs(a1["F"]).max())
+    assert abs(4 * a2["E"] - a1["E"]) < 1e-14 * abs(a1["E"])
