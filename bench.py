@@ -238,11 +238,13 @@ def _oracle_targets(n):
     return np.sort(np.random.default_rng(12345).choice(n, ORACLE_SAMPLE, replace=False))
 
 
-def cpu_baseline(workload, gpu_outputs=None):
+def cpu_baseline(workload, gpu_outputs=None, kernel_outputs=None):
     """The FP64 oracle on the host cores (whole workload up to 2M particles, else the
     outputs of 512 sampled particles) and, from the same run, the relative L2 error of
     the GPU results against it; for the open form also the method's own error (the
-    oracle against the direct O(N) sum at the sampled particles)."""
+    oracle against the direct O(N) sum at the sampled particles).  kernel_outputs:
+    the GPU results of a force-kernel plan (§4.1), checked against the oracle's
+    force-kernel run on the same particles (and against the direct sum)."""
     import numpy as np
     import oracle
     from paper_2212_13080_gb300 import inputs
@@ -289,6 +291,21 @@ def cpu_baseline(workload, gpu_outputs=None):
             err["method_error_vs_direct"] = {"particles": int(len(tg)),
                                              "potential_rel_l2": rel(phi_m, phi_d),
                                              "forces_rel_l2": rel(F_m, F_d)}
+        if kernel_outputs is not None:
+            rk = oracle.fmm(w["pos"], w["q"], w["box"], depth=w["depth"], n=w["p"],
+                            periodic=w["periodic"], continuous=w["continuous"], sample=idx,
+                            keep=False, force_kernel=True)
+            Fk = np.asarray(rk["F"], np.float64).reshape(-1, 3)
+            if idx is not None and Fk.shape[0] == n:
+                Fk = Fk[idx]
+            _, F_g, _ = kernel_outputs
+            ek = {"forces_rel_l2": rel(F_g[sel].astype(np.float64), Fk)}
+            if not w["periodic"]:
+                Fm = np.asarray(rk["F"], np.float64).reshape(-1, 3)
+                if Fm.shape[0] == n:
+                    Fm = Fm[tg]
+                ek["oracle_forces_vs_direct_rel_l2"] = rel(Fm, F_d)
+            err["force_kernel"] = ek
     return base, err
 
 
@@ -563,6 +580,46 @@ def main():
                  "value": n / (statistics.mean(t32) * 1e-3) / 1e6, "unit": UNIT}
         plan32.close()
 
+    # far forces from the force kernels (§4.1), same workload and precision
+    force_kernel, fk_host = None, None
+    if not args.shift_free:
+        fk_plan = FMM(box, w["depth"], w["p"], sync=False, **dict(mk, force_mode="kernel"))
+        fk_ws = fk_plan.workspace(n)
+        fk_out = {"potential": torch.empty(n, dtype=plan.out_dtype, device=dev),
+                  "energy": torch.empty(1, dtype=torch.float64, device=dev),
+                  "forces": torch.empty((n, 3), dtype=plan.out_dtype, device=dev)}
+        for _ in range(3):
+            fk_plan.eval(pos, q, workspace=fk_ws, out=fk_out)
+        tk = []
+        for _ in range(max(5, args.steps // 2)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fk_plan.eval(pos, q, workspace=fk_ws, out=fk_out)
+            b.record(stream)
+            b.synchronize()
+            tk.append(a.elapsed_time(b))
+        if plan_status(fk_plan, fk_ws):
+            raise SystemExit("force-kernel plan: evaluation failed")
+        fk_plan.set_timing(True, serial=True)
+        fk_iso = {}
+        for _ in range(5):
+            flush.zero_()
+            fk_plan.eval(pos, q, workspace=fk_ws, out=fk_out)
+            for k_, v in fk_plan.stats()["stage_ms"].items():
+                fk_iso[k_] = fk_iso.get(k_, 0.0) + v / 5
+        torch.cuda.synchronize()
+        fk_host = (fk_out["potential"].cpu().numpy(), fk_out["forces"].cpu().numpy(),
+                   float(fk_out["energy"].item()))
+        force_kernel = {"force_mode": "kernel", "precision": args.precision,
+                        "ms_per_step": statistics.mean(tk),
+                        "value": world * n / (statistics.mean(tk) * 1e-3) / 1e6, "unit": UNIT,
+                        "stage_ms_isolated": fk_iso,
+                        "m2l_tflops_algorithmic": 4 * m2l_flops / (fk_iso["m2l"] * 1e-3) / 1e12,
+                        "note": "four contractions (1/r and the x, y, z force kernels), plain-weight "
+                                "far-field evaluation"}
+        fk_plan.close()
+
     # end to end through the public API with host buffers (pinned)
     plan_e2e = FMM(box, w["depth"], w["p"], sync=True, **mk)
     pos_p = torch.from_numpy(pos_h).pin_memory()
@@ -656,10 +713,12 @@ def main():
         "clocks": clocks,
         "m2l_tensor": m2l_tc,
         "plain_fp32": plain,
+        "force_kernel": force_kernel,
         "shift_free": shift_free_line(args.steps, dev, flush, stream) if world == 1 else None,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"], res["error_vs_fp64_oracle"] = cpu_baseline(args.workload, gpu_outputs)
+        res["cpu_baseline"], res["error_vs_fp64_oracle"] = cpu_baseline(args.workload, gpu_outputs,
+                                                                        fk_host)
     if rank == 0:
         print(json.dumps(res), flush=True)
     plan.close()

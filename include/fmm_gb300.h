@@ -70,6 +70,8 @@ extern "C" {
 /* ---- flags of fmm_eval ---------------------------------------------------- */
 #define FMM_FORCE_ADJOINT 0 /* forces = -dE/dx of the FMM energy (default) */
 #define FMM_FORCE_PAPER 1   /* split axes: sum of the forces the split charges feel (§2.3) */
+#define FMM_KERNEL_COULOMB 0
+#define FMM_KERNEL_INV_SQUARE 1
 #define FMM_FORCE_KERNEL 2  /* far forces from the force kernels r/|r|^3 (§4.1, other
                                kernels): three more functionals per cell through the same
                                interaction lists (periodic: the gradient of the lattice term),
@@ -107,10 +109,17 @@ typedef struct {
                               tables of at most 32 GiB (else FMM_ERR_UNSUPPORTED); the
                               reduced arrangement and batched plans are not supported.
                               0 (default): the shifted form of §2.2. */
+    int kernel;            /* FMM_KERNEL_COULOMB (default): F(P, P~) = 1/|P - P~|;
+                              FMM_KERNEL_INV_SQUARE: 1/|P - P~|^2, the other function §4.1
+                              names, for the far forms and the near field alike (potential
+                              sum_j q_j/r^2, force 2 q_i q_j r/r^4).  Open boundary only (its
+                              lattice sum diverges) and not with shift_free
+                              (FMM_ERR_UNSUPPORTED). */
 } fmm_opts_t;
 
 /* Fills *opts with the defaults (continuous 0, split_ratio 1/256, split_capacity 0
- * (automatic), precision FP32, adjoint forces, sync 1, grid_scale 1, shift_free 0). */
+ * (automatic), precision FP32, adjoint forces, sync 1, grid_scale 1, shift_free 0,
+ * kernel FMM_KERNEL_COULOMB). */
 void fmm_opts_default(fmm_opts_t *opts);
 
 /*

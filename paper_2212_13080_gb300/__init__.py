@@ -23,6 +23,7 @@ __all__ = ["FMM", "FMMBatch", "FmmError", "fmm_energy"]
 _PREC = {"fp32": B.FMM_PREC_FP32, "fp64": B.FMM_PREC_FP64, "tf32x3": B.FMM_PREC_TF32X3,
          "tf32x1": B.FMM_PREC_TF32X1, "bf16x3": B.FMM_PREC_BF16X3}
 _FORCE = {"adjoint": B.FMM_FORCE_ADJOINT, "paper": B.FMM_FORCE_PAPER, "kernel": B.FMM_FORCE_KERNEL}
+_KERNEL = {"coulomb": B.FMM_KERNEL_COULOMB, "inverse_square": B.FMM_KERNEL_INV_SQUARE}
 
 
 def _ptr(t):
@@ -47,11 +48,14 @@ class FMM:
     grid_scale < 1: the reduced arrangement of the p-division points (§4.1).
     shift_free: App. A.2, precomputed bilinear forms on box-basis grid charges
     (precision "fp64", p <= 5).
+    force_mode: "adjoint" (-dE/dx), "paper" (split charges' forces summed) or
+    "kernel" (far forces from the force kernels, §4.1).
+    kernel: "coulomb" (1/r) or "inverse_square" (1/r^2, open boundary).
     """
 
     def __init__(self, box, depth, p, periodic=False, continuous=False, split_ratio=None,
                  precision="fp32", force_mode="adjoint", max_n=1 << 20, split_capacity=None,
-                 sync=True, device=None, grid_scale=1.0, shift_free=False):
+                 sync=True, device=None, grid_scale=1.0, shift_free=False, kernel="coulomb"):
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         self.box = tuple(float(x) for x in box)
@@ -73,6 +77,7 @@ class FMM:
         o.sync = 0
         o.grid_scale = float(grid_scale)
         o.shift_free = int(bool(shift_free))
+        o.kernel = _KERNEL[kernel]
         self.shift_free = bool(shift_free)
         with torch.cuda.device(self.device):
             self._h = B.fmm_plan_create(self.box, self.depth, self.p, self.periodic, o, self.max_n)

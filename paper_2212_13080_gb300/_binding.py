@@ -31,6 +31,8 @@ FMM_PREC_BF16X3 = 4
 FMM_FORCE_ADJOINT = 0
 FMM_FORCE_PAPER = 1
 FMM_FORCE_KERNEL = 2
+FMM_KERNEL_COULOMB = 0
+FMM_KERNEL_INV_SQUARE = 1
 
 FMM_DUMP_COUNTS = 0
 FMM_DUMP_KEYS = 1
@@ -62,7 +64,8 @@ class fmm_opts_t(ctypes.Structure):
     _fields_ = [("continuous", ctypes.c_int), ("split_ratio", ctypes.c_double),
                 ("split_capacity", ctypes.c_double), ("precision", ctypes.c_int),
                 ("force_mode", ctypes.c_int), ("sync", ctypes.c_int),
-                ("grid_scale", ctypes.c_double), ("shift_free", ctypes.c_int)]
+                ("grid_scale", ctypes.c_double), ("shift_free", ctypes.c_int),
+                ("kernel", ctypes.c_int)]
 
 
 class fmm_stats_t(ctypes.Structure):

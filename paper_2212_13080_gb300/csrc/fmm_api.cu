@@ -117,10 +117,13 @@ void far_image_grad(double rx, double ry, double rz, double g[3]) {
 // The function of the bilinear forms between unit cells at separation
 // (dx, dy, dz) = a - (o + b): comp 0 is 1/r (§2.1.7), comps 1..3 the x, y, z
 // components of r/|r|^3 (§4.1: the forces directly from the kernel).
-double kernel_value(int comp, double dx, double dy, double dz) {
+// power 2: 1/r^2 and the components of its force kernel 2 r/r^4 (§4.1 names
+// 1/r^2 as another function the replacement applies to).
+double kernel_value(int comp, int power, double dx, double dy, double dz) {
     const double r2 = dx * dx + dy * dy + dz * dz, r = std::sqrt(r2);
-    if (comp == 0) return 1.0 / r;
-    return (comp == 1 ? dx : comp == 2 ? dy : dz) / (r2 * r);
+    const double d = comp == 1 ? dx : comp == 2 ? dy : dz;
+    if (power == 2) return comp == 0 ? 1.0 / r2 : 2.0 * d / (r2 * r2);
+    return comp == 0 ? 1.0 / r : d / (r2 * r);
 }
 
 double far_image_sum(double rx, double ry, double rz) {
@@ -199,7 +202,7 @@ static float bf16_value(uint16_t h) {
 // plan's type).
 template <typename real>
 int upload_tables(fmm_plan_t P) {
-    const int p = P->p, p3 = p * p * p, nc = P->ncomp;
+    const int p = P->p, p3 = p * p * p, nc = P->ncomp, pw = P->geom.power;
     const double gs = P->opts.grid_scale;
     const size_t nk = (size_t)343 * p3 * p3;
     std::vector<real> KtT(nc * nk, (real)0), Kbar((size_t)nc * 343 * p3, (real)0);
@@ -214,7 +217,7 @@ int upload_tables(fmm_plan_t P) {
                         double ax = node(p, gs, a % p), ay = node(p, gs, (a / p) % p), az = node(p, gs, a / (p * p));
                         double mean = 0.0;
                         for (int b = 0; b < p3; b++) {
-                            row[b] = kernel_value(c, ax - (ox + node(p, gs, b % p)),
+                            row[b] = kernel_value(c, pw, ax - (ox + node(p, gs, b % p)),
                                                   ay - (oy + node(p, gs, (b / p) % p)),
                                                   az - (oz + node(p, gs, b / (p * p))));
                             mean += row[b];
@@ -246,7 +249,7 @@ int upload_tables(fmm_plan_t P) {
                 double ax = node(p, gs, a % p), ay = node(p, gs, (a / p) % p), az = node(p, gs, a / (p * p));
                 double mean = 0.0;
                 for (int b = 0; b < p3; b++) {
-                    row[b] = kernel_value(c, ax - (ox + node(p, gs, b % p)), ay - (oy + node(p, gs, (b / p) % p)),
+                    row[b] = kernel_value(c, pw, ax - (ox + node(p, gs, b % p)), ay - (oy + node(p, gs, (b / p) % p)),
                                           az - (oz + node(p, gs, b / (p * p))));
                     mean += row[b];
                 }
@@ -591,6 +594,7 @@ void fmm_opts_default(fmm_opts_t *o) {
     o->sync = 1;
     o->grid_scale = 1.0;
     o->shift_free = 0;
+    o->kernel = FMM_KERNEL_COULOMB;
 }
 
 const char *fmm_strerror(int s) {
@@ -635,6 +639,9 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
         o.force_mode != FMM_FORCE_KERNEL)
         return FMM_ERR_ARG;
     if (o.force_mode == FMM_FORCE_KERNEL && o.shift_free) return FMM_ERR_UNSUPPORTED;
+    if (o.kernel != FMM_KERNEL_COULOMB && o.kernel != FMM_KERNEL_INV_SQUARE) return FMM_ERR_ARG;
+    // the lattice sum of 1/r^2 diverges; the shift-free forms are built for 1/r
+    if (o.kernel == FMM_KERNEL_INV_SQUARE && (periodic || o.shift_free)) return FMM_ERR_UNSUPPORTED;
     const bool tc_prec = o.precision == FMM_PREC_TF32X3 || o.precision == FMM_PREC_TF32X1 ||
                          o.precision == FMM_PREC_BF16X3;
     if (o.precision != FMM_PREC_FP32 && o.precision != FMM_PREC_FP64 && !tc_prec)
@@ -672,6 +679,7 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     g.continuous = o.continuous ? 1 : 0;
     g.force_mode = o.force_mode;
     g.shift_free = o.shift_free ? 1 : 0;
+    g.power = o.kernel == FMM_KERNEL_INV_SQUARE ? 2 : 1;
     g.S = 1 << depth;
     for (int a = 0; a < 3; a++) g.x0[a] = (float)box[a];
     g.Lf = (float)box[3];

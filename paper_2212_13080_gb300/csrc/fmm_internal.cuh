@@ -33,6 +33,7 @@ struct Coef {
 struct Geom {
     int p, p3, depth, periodic, continuous, force_mode;
     int shift_free;   // App. A.2: grid charges and functionals with respect to the box
+    int power;        // F(P, P~) = 1/r^power: 1 (Coulomb) or 2
     int S;            // 2^depth
     float x0[3];      // float32 box corner
     float Lf;         // float32 box edge

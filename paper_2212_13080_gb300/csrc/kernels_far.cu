@@ -629,7 +629,7 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
     cudaStreamWaitEvent(S.coarse, S.fork, 0);
     for (int c = 0; c < T.ncomp; c++) {
         real *loc_c = P.loc + c * W.loc_comp;
-        const int spow = c == 0 ? 1 : 2;
+        const int spow = c == 0 ? g.power : g.power + 1;  // 1/r^k: 2^(lk); its force: 2^(l(k+1))
         for (int l = lstart; l <= lsimt_end; l++) {
             const int H = 1 << (l - 1);
             const int Tt = H < 4 ? H : 4;
@@ -657,7 +657,8 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
         if (T.tc_lmin > 0 && depth >= T.tc_lmin) {
             for (int c = 0; c < T.ncomp; c++) {
                 int rc = launch_m2l_tc(g, P, W, T.tc_khi_map[c], T.tc_klo_map[c], T.tc_kbar[c], T.tc_lmin,
-                                       T.tc_mode, T.tc_inject, P.loc + c * W.loc_comp, c == 0 ? 1 : 2,
+                                       T.tc_mode, T.tc_inject, P.loc + c * W.loc_comp,
+                                       c == 0 ? g.power : g.power + 1,
                                        c == 0, st, tr);
                 if (rc) return rc;
             }

@@ -240,18 +240,20 @@ template <> __device__ __forceinline__ float rsqrt_pair<float>(float x) {
 template <> __device__ __forceinline__ double rsqrt_pair<double>(double x) { return 1.0 / sqrt(x); }
 
 // One (target, source) pair of the forward phase: target sums (p, x, y, z) in
-// a, the source's reaction in r.  FIRST assigns a instead of adding.
-template <typename real, bool FORCES, bool GUARD, bool FIRST>
+// a, the source's reaction in r.  FIRST assigns a instead of adding.  POW: the
+// pair function 1/r (1) or 1/r^2 (2), whose force is 2 r/r^4.
+template <typename real, bool FORCES, bool GUARD, bool FIRST, int POW>
 __device__ __forceinline__ void nf_pair(const typename Vec4<real>::T &tv, int to, real sx, real sy, real sz,
                                         real sq, int so, real *a, real &rp, real &rx, real &ry, real &rz) {
     const real dx = tv.x - sx, dy = tv.y - sy, dz = tv.z - sz;
     const real r2 = dx * dx + dy * dy + dz * dz;
     real ri = rsqrt_pair<real>(r2);
     ri = (so != to && (!GUARD || r2 > real(0))) ? ri : real(0);
-    if (FIRST) a[0] = sq * ri; else a[0] += sq * ri;
-    rp += tv.w * ri;
+    const real pf = POW == 2 ? ri * ri : ri;  // the pair function
+    if (FIRST) a[0] = sq * pf; else a[0] += sq * pf;
+    rp += tv.w * pf;
     if (FORCES) {
-        const real ri3 = ri * ri * ri;
+        const real ri3 = POW == 2 ? real(2) * pf * pf : ri * ri * ri;  // |force| / (q q' r)
         const real as = sq * ri3, bt = tv.w * ri3;
         if (FIRST) {
             a[1] = as * dx;
@@ -268,7 +270,7 @@ __device__ __forceinline__ void nf_pair(const typename Vec4<real>::T &tv, int to
     }
 }
 
-template <typename real, bool FORCES, bool GUARD>
+template <typename real, bool FORCES, bool GUARD, int POW>
 __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const int *__restrict__ leaf_start,
                                                const typename Vec4<real>::T *__restrict__ s_pt,
                                                const int *__restrict__ s_origin,
@@ -317,6 +319,7 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
     const int npass = (Ns + NF_BS * NF_KS - 1) / (NF_BS * NF_KS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const real Sr = (real)S;
+    const real Sp = POW == 2 ? Sr * Sr : Sr;  // unit-box scale of the pair function
     real *tb_w = tbuf[warp];
 
     // ---- forward phase (mutual) ----
@@ -375,11 +378,11 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
                 for (int u = 0; u < TG; u++) {
                     const real4 tv = tpos[g0 + u];
                     const int to = tori[g0 + u];
-                    nf_pair<real, FORCES, GUARD, true>(tv, to, sx[0], sy[0], sz[0], sq[0], so[0], acc + u * NC,
+                    nf_pair<real, FORCES, GUARD, true, POW>(tv, to, sx[0], sy[0], sz[0], sq[0], so[0], acc + u * NC,
                                                        rp[0], rx[0], ry[0], rz[0]);
 #pragma unroll
                     for (int k = 1; k < NF_KS; k++)
-                        nf_pair<real, FORCES, GUARD, false>(tv, to, sx[k], sy[k], sz[k], sq[k], so[k],
+                        nf_pair<real, FORCES, GUARD, false, POW>(tv, to, sx[k], sy[k], sz[k], sq[k], so[k],
                                                             acc + u * NC, rp[k], rx[k], ry[k], rz[k]);
                 }
                 // transpose through shared memory: lane l sums value l over the lanes in order
@@ -399,11 +402,11 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
                 for (int u = 0; u < TR; u++) {
                     const real4 tv = tpos[g0 + u];
                     const int to = tori[g0 + u];
-                    nf_pair<real, FORCES, GUARD, true>(tv, to, sx[0], sy[0], sz[0], sq[0], so[0], acc + u * NC,
+                    nf_pair<real, FORCES, GUARD, true, POW>(tv, to, sx[0], sy[0], sz[0], sq[0], so[0], acc + u * NC,
                                                        rp[0], rx[0], ry[0], rz[0]);
 #pragma unroll
                     for (int k = 1; k < NF_KS; k++)
-                        nf_pair<real, FORCES, GUARD, false>(tv, to, sx[k], sy[k], sz[k], sq[k], so[k],
+                        nf_pair<real, FORCES, GUARD, false, POW>(tv, to, sx[k], sy[k], sz[k], sq[k], so[k],
                                                             acc + u * NC, rp[k], rx[k], ry[k], rz[k]);
                 }
                 __syncwarp();
@@ -440,12 +443,12 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
             }
         }
         // reactions of this pass's sources, complete after all target blocks;
-        // unit-box units: 1/r_u = S/r_t, (x/r^3)_u = S^2 (x/r^3)_t
+        // unit-box units: 1/r_u^k = S^k/r_t^k, forces S^(k+1) times
 #pragma unroll
         for (int k = 0; k < NF_KS; k++) {
             if (sidx[k] >= 0) {
-                const real qs = sq[k] * Sr * Sr;
-                react[sseg[k] * rstride + sidx[k]] = make_vec4(Sr * rp[k], qs * rx[k], qs * ry[k], qs * rz[k]);
+                const real qs = sq[k] * Sp * Sr;
+                react[sseg[k] * rstride + sidx[k]] = make_vec4(Sp * rp[k], qs * rx[k], qs * ry[k], qs * rz[k]);
             }
         }
     }
@@ -483,9 +486,10 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
                     const real r2 = dx * dx + dy * dy + dz * dz;
                     real ri = rsqrt_pair<real>(r2);
                     ri = (r2 > real(0) && sori[j] != to) ? ri : real(0);
-                    pa += sv.w * ri;
+                    const real pf = POW == 2 ? ri * ri : ri;
+                    pa += sv.w * pf;
                     if (FORCES) {
-                        const real q3 = sv.w * ri * ri * ri;
+                        const real q3 = sv.w * (POW == 2 ? real(2) * pf * pf : ri * ri * ri);
                         xa += q3 * dx;
                         ya += q3 * dy;
                         za += q3 * dz;
@@ -516,8 +520,8 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
                 v[2] += prev.z;
                 v[3] += prev.w;
             }
-            const real qs = tv.w * Sr * Sr;
-            o = make_vec4(Sr * v[0], qs * v[1], qs * v[2], qs * v[3]);
+            const real qs = tv.w * Sp * Sr;
+            o = make_vec4(Sp * v[0], qs * v[1], qs * v[2], qs * v[3]);
         }
         __syncthreads();
     }
@@ -557,8 +561,14 @@ void launch_p2p(const Geom &g, const Ptrs<real> &P, const WsLayout &W, bool forc
     // charges of different cells can coincide only on split planes with odd p
     const bool guard = g.continuous && (g.p & 1);
 #define LAUNCH(F, G)                                                                               \
-    k_p2p<real, F, G><<<ncell, NF_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt, P.s_origin, \
-                                               P.out_pt, P.react, W.cap)
+    do {                                                                                           \
+        if (g.power == 2)                                                                          \
+            k_p2p<real, F, G, 2><<<ncell, NF_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt, \
+                                                          P.s_origin, P.out_pt, P.react, W.cap);  \
+        else                                                                                       \
+            k_p2p<real, F, G, 1><<<ncell, NF_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt, \
+                                                          P.s_origin, P.out_pt, P.react, W.cap);  \
+    } while (0)
     if (forces) {
         if (guard) LAUNCH(true, true);
         else LAUNCH(true, false);

@@ -574,10 +574,12 @@ void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n
     }
     int nb = (n + UNSPLIT_BS - 1) / UNSPLIT_BS;
     double *ep = (!backward && energy) ? P.epart : nullptr;
+    // unit box -> box of edge L: potentials of 1/r^k scale by L^-k, forces by L^-(k+1)
+    const double iL = 1.0 / g.L, sphi = g.power == 2 ? iL * iL : iL;
     k_unsplit<real><<<nb, UNSPLIT_BS, 0, st>>>(
         g, P.hdr, n, q, g.continuous ? P.offset : nullptr, P.count, P.axes, P.inv,
         g.continuous ? P.e_wd : nullptr, P.out_pt, potential, forces, ep, grad_energy, grad_q,
-        backward ? 1 : 0, (real)(1.0 / g.L), (real)((1.0 / g.L) * (1.0 / g.L)));
+        backward ? 1 : 0, (real)sphi, (real)(sphi * iL));
     tr.count();
     if (ep) {
         k_energy_final<<<1, 1024, 0, st>>>(P.epart, nb, energy);

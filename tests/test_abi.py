@@ -102,3 +102,26 @@ def test_force_mode_validated_before_any_device_call():
     with pytest.raises(B.FmmError) as e:
         B.fmm_plan_create(box, 3, 4, False, o, 1000)
     assert e.value.code == B.FMM_ERR_UNSUPPORTED
+
+
+def test_inverse_square_kernel_options():
+    """1/r^2: open boundary only (its lattice sum diverges), not shift-free."""
+    import pytest
+    from paper_2212_13080_gb300 import _binding as B
+    box = (0.0, 0.0, 0.0, 1.0)
+    o = B.fmm_opts_default()
+    assert o.kernel == B.FMM_KERNEL_COULOMB
+    o.kernel = B.FMM_KERNEL_INV_SQUARE
+    with pytest.raises(B.FmmError) as e:
+        B.fmm_plan_create(box, 3, 4, True, o, 1000)
+    assert e.value.code == B.FMM_ERR_UNSUPPORTED
+    o.precision = B.FMM_PREC_FP64
+    o.shift_free = 1
+    with pytest.raises(B.FmmError) as e:
+        B.fmm_plan_create(box, 3, 4, False, o, 1000)
+    assert e.value.code == B.FMM_ERR_UNSUPPORTED
+    o = B.fmm_opts_default()
+    o.kernel = 5
+    with pytest.raises(B.FmmError) as e:
+        B.fmm_plan_create(box, 3, 4, False, o, 1000)
+    assert e.value.code == B.FMM_ERR_ARG

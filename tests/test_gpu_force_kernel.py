@@ -68,3 +68,36 @@ def test_force_kernel_backward_is_the_adjoint():
     assert _rel(P.grad.cpu().numpy().astype(np.float64), -ref["F"]) < 2e-7
     assert _rel(Q.grad.cpu().numpy().astype(np.float64), ref["phi"]) < 2e-7
     plan.close()
+
+
+# --- the 1/r^2 kernel (§4.1, other functions) -------------------------------------
+
+R2_CASES = [
+    ("uniform4k-open-plain-d3-p4", lambda: inputs.uniform_pm1(4096, 1), 3, 4, False, None),
+    ("uniform20k-open-cont-d4-p5", lambda: inputs.uniform_cont(20000, 5), 4, 5, True, 1 / 32),
+]
+
+
+@pytest.mark.parametrize("force_mode", ["adjoint", "kernel"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("case", R2_CASES, ids=[c[0] for c in R2_CASES])
+def test_parity_inverse_square(case, precision, force_mode):
+    """F(P, P~) = 1/|P - P~|^2 for the far forms and the near field: the GPU
+    path (tables, level scales 4^l / 8^l, near-field pair function 1/r^2 with
+    force 2 r/r^4, output scaling L^-2 / L^-3) against the oracle's."""
+    name, gen, depth, p, cont, dt = case
+    pos, q, box = gen()
+    box = (0.0, 0.0, 0.0, 2.5)  # a box edge != 1 checks the output scaling
+    pos = (pos.astype(np.float64) * 2.5).astype(np.float32)
+    ref = oracle.fmm(pos, q, box, depth=depth, n=p, continuous=cont, dt=dt, power=2,
+                     force_kernel=force_mode == "kernel", keep=False)
+    plan = FMM(box, depth, p, continuous=cont, split_ratio=dt, precision=precision,
+               max_n=len(q), force_mode=force_mode, kernel="inverse_square")
+    r = plan.eval(torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda())
+    tol = TOL[precision]
+    if precision != "fp64" and cont and force_mode == "adjoint":
+        tol = 1e-5  # adjoint forces of split charges in FP32 (as for 1/r)
+    assert _rel(r["potential"].cpu().numpy().astype(np.float64), ref["phi"]) < TOL[precision]
+    assert _rel(r["forces"].cpu().numpy().astype(np.float64), ref["F"]) < tol
+    assert abs(r["energy"].item() - ref["E"]) < TOL[precision] * abs(ref["E"])
+    plan.close()
