@@ -36,6 +36,11 @@ UNIT = "Mparticles/s"
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 P2P_FLOPS_PER_PAIR = 20
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
+# DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
+# capture of the current kernels on these workloads (profiles/k_p2p_uniform1m.md,
+# profiles/k_m2l_tc_uniform1m.md); reported as the roofline's traffic
+PROFILED_TRAFFIC = {("uniform1m", "tf32x3", "k_p2p"): 201449216,
+                    ("uniform1m", "tf32x3", "k_m2l_tc"): 42046976}
 
 
 def _peaks():
@@ -688,6 +693,9 @@ def main():
                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
                     "achieved_isolated": ach_iso,
                     "frac_isolated": ach_iso / FP32_ALU_PEAK_TFLOPS}
+    roof["traffic"] = PROFILED_TRAFFIC.get((args.workload, args.precision, roof["kernel"]))
+    if roof["traffic"] is not None:
+        roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     roof["hbm_peak_gbs"] = hbm
     roof["hbm_peak_source"] = peak_kind
 
