@@ -288,7 +288,9 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
     constexpr int WP = NF_TB * NC > 128 ? NF_TB * NC : 128;  // the own phase uses 128 per warp
     __shared__ real wpart[NW][WP];
     __shared__ __align__(16) real tbuf[NW][32 * NF_TP];
-    __shared__ int seg_start[NF_SEGS], seg_off[NF_SEGS];
+    // seg_off: prefix of the 13 forward segments' sizes, then sentinels up to
+    // index 16 for the 4-step search of a slot's segment
+    __shared__ int seg_start[NF_SEGS], seg_off[NF_SEGS + 3];
 
     const uint32_t key = blockIdx.x;
     const int t0 = leaf_start[key], T = leaf_start[key + 1] - t0;
@@ -296,23 +298,28 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
     const int S = 1 << depth;
     int cx, cy, cz;
     morton_decode(key, cx, cy, cz);
-    // forward segments d = 1..13 at [d - 1]
-    if (threadIdx.x < NF_SEGS - 1) {
-        int dx, dy, dz;
-        nf_delta(threadIdx.x + 1, dx, dy, dz);
-        const int64_t b = nf_cell(cx, cy, cz, dx, dy, dz, S, periodic);
+    // forward segments d = 1..13 at [d - 1]: warp 0, sizes summed by a shuffle scan
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
         int st = 0, cnt = 0;
-        if (b >= 0) {
-            st = leaf_start[b];
-            cnt = leaf_start[b + 1] - st;
+        if (l < NF_SEGS - 1) {
+            int dx, dy, dz;
+            nf_delta(l + 1, dx, dy, dz);
+            const int64_t b = nf_cell(cx, cy, cz, dx, dy, dz, S, periodic);
+            if (b >= 0) {
+                st = leaf_start[b];
+                cnt = leaf_start[b + 1] - st;
+            }
+            seg_start[l] = st;
         }
-        seg_start[threadIdx.x] = st;
-        seg_off[threadIdx.x + 1] = cnt;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        seg_off[0] = 0;
-        for (int d = 0; d < NF_SEGS - 1; d++) seg_off[d + 1] += seg_off[d];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, cnt, o);
+            if (l >= o) cnt += v;
+        }
+        if (l == 0) seg_off[0] = 0;
+        if (l < NF_SEGS - 1) seg_off[l + 1] = cnt;
+        else if (l < NF_SEGS + 2) seg_off[l + 1] = 0x7fffffff;
     }
     __syncthreads();
     const int Ns = seg_off[NF_SEGS - 1];
@@ -338,8 +345,12 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
             sseg[k] = 0;
             rp[k] = rx[k] = ry[k] = rz[k] = 0;
             if (f < Ns) {
+                // the last segment starting at or before f (seg_off is non-decreasing)
                 int d = 0;
-                while (f >= seg_off[d + 1]) d++;
+                if (seg_off[d + 8] <= f) d += 8;
+                if (seg_off[d + 4] <= f) d += 4;
+                if (seg_off[d + 2] <= f) d += 2;
+                if (seg_off[d + 1] <= f) d += 1;
                 const int j = seg_start[d] + (f - seg_off[d]);
                 int dx, dy, dz;
                 nf_delta(d + 1, dx, dy, dz);
