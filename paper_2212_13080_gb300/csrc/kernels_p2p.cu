@@ -298,6 +298,24 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
     const int S = 1 << depth;
     int cx, cy, cz;
     morton_decode(key, cx, cy, cz);
+    // a cell whose charges fit one target block stages them once, here, so that
+    // their loads overlap the segment lookups (padded to a whole remainder
+    // group with inert targets: far from every source, no charge, an origin no
+    // source has)
+    const bool one_block = T <= NF_TB;
+    if (one_block) {
+        const int ntp = (T + TR - 1) / TR * TR;
+        for (int i = threadIdx.x; i < ntp; i += NF_BS) {
+            if (i < T) {
+                tpos[i] = s_pt[t0 + i];
+                tori[i] = s_origin[t0 + i];
+            } else {
+                const real far = -(real)(4 * S + 16);
+                tpos[i] = make_vec4(far, far, far, real(0));
+                tori[i] = -2;
+            }
+        }
+    }
     // forward segments d = 1..13 at [d - 1]: warp 0, sizes summed by a shuffle scan
     if (threadIdx.x < 32) {
         const int l = threadIdx.x;
@@ -366,22 +384,26 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
         }
         for (int tb = 0; tb < T; tb += NF_TB) {
             const int nt = min(NF_TB, T - tb);
-            __syncthreads();  // previous block's shared data consumed
-            // targets padded to a whole group with inert ones: far from every
-            // source, no charge, an origin no source has
-            // whole groups of TG, then the rest in groups of TR: pad to TR only
-            const int ntp = (nt + TR - 1) / TR * TR;
-            for (int i = threadIdx.x; i < ntp; i += NF_BS) {
-                if (i < nt) {
-                    tpos[i] = s_pt[t0 + tb + i];
-                    tori[i] = s_origin[t0 + tb + i];
-                } else {
-                    const real far = -(real)(4 * S + 16);
-                    tpos[i] = make_vec4(far, far, far, real(0));
-                    tori[i] = -2;
+            if (!one_block) {
+                __syncthreads();  // previous block's shared data consumed
+                // targets padded to a whole group with inert ones: far from every
+                // source, no charge, an origin no source has
+                // whole groups of TG, then the rest in groups of TR: pad to TR only
+                const int ntp = (nt + TR - 1) / TR * TR;
+                for (int i = threadIdx.x; i < ntp; i += NF_BS) {
+                    if (i < nt) {
+                        tpos[i] = s_pt[t0 + tb + i];
+                        tori[i] = s_origin[t0 + tb + i];
+                    } else {
+                        const real far = -(real)(4 * S + 16);
+                        tpos[i] = make_vec4(far, far, far, real(0));
+                        tori[i] = -2;
+                    }
                 }
             }
-            __syncthreads();
+            // targets visible (staged before the prologue's barrier for one
+            // block); the previous pass's reads of wpart done
+            if (!one_block || pass > 0) __syncthreads();
             int g0 = 0;
             for (; g0 + TG <= nt; g0 += TG) {
                 real acc[32];
@@ -432,7 +454,18 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
                 }
             }
             __syncthreads();
-            // target sums: the warps in order, then accumulated over passes
+            // target sums: the warps in order, then accumulated over passes; with
+            // forces one thread per (target, component), all threads busy
+            if (NC == 4) {
+                real *ob = reinterpret_cast<real *>(out_pt + t0 + tb);
+                for (int e = threadIdx.x; e < nt * 4; e += NF_BS) {
+                    real t = wpart[0][e];
+#pragma unroll
+                    for (int w = 1; w < NW; w++) t += wpart[w][e];
+                    if (pass > 0) t += ob[e];
+                    ob[e] = t;
+                }
+            } else
             for (int i = threadIdx.x; i < nt; i += NF_BS) {
                 real v[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -466,22 +499,24 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
 
     // ---- own phase: pairs inside A, one-sided; a lane per target (chunks of
     // 32), the warps take every fourth source; warp partials summed in order ----
-    real4 *spos = reinterpret_cast<real4 *>(&tbuf[0][0]);  // free after the forward phase
+    // (one block: the cell's charges are still staged in tpos / tori and serve
+    // as targets and sources; else sources are staged block by block in tbuf)
+    real4 *spos = one_block ? tpos : reinterpret_cast<real4 *>(&tbuf[0][0]);
     int *sori = reinterpret_cast<int *>(&tori[0]);
-    const bool once = T <= NF_TB;
+    if (one_block) __syncthreads();  // the forward phase's reads of wpart done
     for (int c0 = 0; c0 < T; c0 += 32) {
         const int ti = c0 + lane;
         const bool act = ti < T;
         real4 tv = make_vec4(real(0), real(0), real(0), real(0));
         int to = -3;
         if (act) {
-            tv = s_pt[t0 + ti];
-            to = s_origin[t0 + ti];
+            tv = one_block ? tpos[ti] : s_pt[t0 + ti];
+            to = one_block ? tori[ti] : s_origin[t0 + ti];
         }
         real pa = 0, xa = 0, ya = 0, za = 0;
         for (int sb = 0; sb < T; sb += NF_TB) {
             const int ns = min(NF_TB, T - sb);
-            if (!(once && c0 > 0)) {
+            if (!one_block) {
                 __syncthreads();
                 for (int i = threadIdx.x; i < ns; i += NF_BS) {
                     spos[i] = s_pt[t0 + sb + i];
