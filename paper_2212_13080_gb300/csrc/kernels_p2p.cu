@@ -226,6 +226,9 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
 // ---------------------------------------------------------------------------
 #define NF_BS 128
 #define NF_KS 4
+#ifndef NF_MINB
+#define NF_MINB 4  // single precision: CTAs per SM the register allocation must allow
+#endif
 #define NF_TP 36  // row stride (words) of the per-warp transpose buffer
 
 // 1/sqrt(r2): single precision uses the SFU reciprocal square root directly
@@ -270,8 +273,99 @@ __device__ __forceinline__ void nf_pair(const typename Vec4<real>::T &tv, int to
     }
 }
 
+// Single precision, two targets at once: the pair (target 2q, source) in the
+// low lane and (target 2q + 1, source) in the high lane of the packed FP32x2
+// instructions (one issue slot for two pair evaluations).  ns*: the source
+// position negated (d = t + ns = t - s); ntw: the targets' charges negated.
+// The source's reaction accumulates as two partial sums, one per lane, with
+// the sign of ntw (the potential's is flipped back at the end of the pass).
+template <bool FORCES, bool GUARD, bool FIRST, int POW>
+__device__ __forceinline__ void nf_pair2(float2 tx, float2 ty, float2 tz, float2 ntw, int to0, int to1,
+                                         float2 nsx, float2 nsy, float2 nsz, float2 sq, int so,
+                                         float2 *a, float2 &rp, float2 &rx, float2 &ry, float2 &rz) {
+    const float2 dx = __fadd2_rn(tx, nsx), dy = __fadd2_rn(ty, nsy), dz = __fadd2_rn(tz, nsz);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    float2 ri = make_float2(rsqrt_pair<float>(r2.x), rsqrt_pair<float>(r2.y));
+    ri.x = (so != to0 && (!GUARD || r2.x > 0.0f)) ? ri.x : 0.0f;
+    ri.y = (so != to1 && (!GUARD || r2.y > 0.0f)) ? ri.y : 0.0f;
+    const float2 pf = POW == 2 ? __fmul2_rn(ri, ri) : ri;  // the pair function
+    if (FIRST) a[0] = __fmul2_rn(sq, pf); else a[0] = __ffma2_rn(sq, pf, a[0]);
+    rp = __ffma2_rn(ntw, pf, rp);  // minus the reaction potential
+    if (FORCES) {
+        const float2 ri3 = POW == 2 ? __fmul2_rn(__fadd2_rn(pf, pf), pf) : __fmul2_rn(__fmul2_rn(ri, ri), ri);
+        const float2 as = __fmul2_rn(sq, ri3), nbt = __fmul2_rn(ntw, ri3);
+        if (FIRST) {
+            a[1] = __fmul2_rn(as, dx);
+            a[2] = __fmul2_rn(as, dy);
+            a[3] = __fmul2_rn(as, dz);
+        } else {
+            a[1] = __ffma2_rn(as, dx, a[1]);
+            a[2] = __ffma2_rn(as, dy, a[2]);
+            a[3] = __ffma2_rn(as, dz, a[3]);
+        }
+        rx = __ffma2_rn(nbt, dx, rx);
+        ry = __ffma2_rn(nbt, dy, ry);
+        rz = __ffma2_rn(nbt, dz, rz);
+    }
+}
+
+// target i of a block into the pair layout: component h = i % 2 of pair i / 2
+__device__ __forceinline__ void nf_stage_pair(float4 *tpa, float4 *tpb, int2 *tpo, int i, float4 v, int o) {
+    float *a = reinterpret_cast<float *>(tpa + i / 2), *b = reinterpret_cast<float *>(tpb + i / 2);
+    const int h = i & 1;
+    a[h] = v.x;
+    a[2 + h] = v.y;
+    b[h] = v.z;
+    b[2 + h] = -v.w;
+    reinterpret_cast<int *>(tpo + i / 2)[h] = o;
+}
+__device__ __forceinline__ void nf_stage_pair(double4 *, double4 *, int2 *, int, double4, int) {}
+
+// NT targets from g0 (an even count) against this thread's KS sources, packed
+// by target pairs; the sums are transposed through shared memory in
+// pair-major order (value (q, c, h) at q*2*NC + 2c + h, target 2q + h, component
+// c) and summed over the warp's lanes in order into wp.
+template <bool FORCES, bool GUARD, int POW, int NT, int KS>
+__device__ __forceinline__ void nf_targets2(const float4 *tpa, const float4 *tpb, const int2 *tpo, int g0, int nt,
+                                            const float2 (&nsx)[KS], const float2 (&nsy)[KS],
+                                            const float2 (&nsz)[KS], const float2 (&sq)[KS], const int (&so)[KS],
+                                            float2 (&rp)[KS], float2 (&rx)[KS], float2 (&ry)[KS],
+                                            float2 (&rz)[KS], float *tb_w, float *wp, int lane) {
+    constexpr int NC = FORCES ? 4 : 1;
+    float2 acc[NT / 2 * NC];
+#pragma unroll
+    for (int q = 0; q < NT / 2; q++) {
+        // target pair (g0 + 2q, g0 + 2q + 1): (x0, x1, y0, y1), (z0, z1, -w0, -w1)
+        const float4 A = tpa[g0 / 2 + q], Bv = tpb[g0 / 2 + q];
+        const int2 O = tpo[g0 / 2 + q];
+        const float2 tx = make_float2(A.x, A.y), ty = make_float2(A.z, A.w), tz = make_float2(Bv.x, Bv.y);
+        const float2 ntw = make_float2(Bv.z, Bv.w);
+        nf_pair2<FORCES, GUARD, true, POW>(tx, ty, tz, ntw, O.x, O.y, nsx[0], nsy[0], nsz[0], sq[0], so[0],
+                                           acc + q * NC, rp[0], rx[0], ry[0], rz[0]);
+#pragma unroll
+        for (int k = 1; k < KS; k++)
+            nf_pair2<FORCES, GUARD, false, POW>(tx, ty, tz, ntw, O.x, O.y, nsx[k], nsy[k], nsz[k], sq[k], so[k],
+                                                acc + q * NC, rp[k], rx[k], ry[k], rz[k]);
+    }
+    constexpr int NV = NT * NC;  // values per lane
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < NV / 2; v += 2)
+        *reinterpret_cast<float4 *>(tb_w + lane * NF_TP + 2 * v) =
+            make_float4(acc[v].x, acc[v].y, acc[v + 1].x, acc[v + 1].y);
+    __syncwarp();
+    if (lane < NV) {
+        float tot = tb_w[lane];
+#pragma unroll
+        for (int r = 1; r < 32; r++) tot += tb_w[r * NF_TP + lane];
+        const int q = lane / (2 * NC), c = (lane / 2) % NC, h = lane % 2;
+        const int u = 2 * q + h;
+        if (g0 + u < nt) wp[(g0 + u) * NC + c] = tot;
+    }
+}
+
 template <typename real, bool FORCES, bool GUARD, int POW>
-__global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const int *__restrict__ leaf_start,
+__global__ void __launch_bounds__(NF_BS, sizeof(real) == 4 ? NF_MINB : 1) k_p2p(int depth, int periodic, const int *__restrict__ leaf_start,
                                                const typename Vec4<real>::T *__restrict__ s_pt,
                                                const int *__restrict__ s_origin,
                                                typename Vec4<real>::T *__restrict__ out_pt,
@@ -285,6 +379,11 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
     constexpr int NF_TB = sizeof(real) == 8 ? 64 : 256;
     __shared__ real4 tpos[NF_TB];
     __shared__ int tori[NF_TB];
+    // single precision: the targets again by pairs, (x0, x1, y0, y1),
+    // (z0, z1, -w0, -w1) and the two origins (the packed pair evaluations)
+    constexpr int NPR = sizeof(real) == 4 ? NF_TB / 2 : 1;
+    __shared__ float4 tpa[NPR], tpb[NPR];
+    __shared__ int2 tpo[NPR];
     constexpr int WP = NF_TB * NC > 128 ? NF_TB * NC : 128;  // the own phase uses 128 per warp
     __shared__ real wpart[NW][WP];
     __shared__ __align__(16) real tbuf[NW][32 * NF_TP];
@@ -306,14 +405,19 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
     if (one_block) {
         const int ntp = (T + TR - 1) / TR * TR;
         for (int i = threadIdx.x; i < ntp; i += NF_BS) {
+            real4 v;
+            int o;
             if (i < T) {
-                tpos[i] = s_pt[t0 + i];
-                tori[i] = s_origin[t0 + i];
+                v = s_pt[t0 + i];
+                o = s_origin[t0 + i];
             } else {
                 const real far = -(real)(4 * S + 16);
-                tpos[i] = make_vec4(far, far, far, real(0));
-                tori[i] = -2;
+                v = make_vec4(far, far, far, real(0));
+                o = -2;
             }
+            tpos[i] = v;
+            tori[i] = o;
+            if constexpr (sizeof(real) == 4) nf_stage_pair(tpa, tpb, tpo, i, v, o);
         }
     }
     // forward segments d = 1..13 at [d - 1]: warp 0, sizes summed by a shuffle scan
@@ -382,6 +486,20 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
                 sseg[k] = d;
             }
         }
+        // single precision: the sources broadcast to both lanes of the packed
+        // pair evaluations, positions negated; reactions as two partial sums
+        float2 nsx2[NF_KS], nsy2[NF_KS], nsz2[NF_KS], sq2[NF_KS];
+        float2 rp2[NF_KS], rx2[NF_KS], ry2[NF_KS], rz2[NF_KS];
+        if constexpr (sizeof(real) == 4) {
+#pragma unroll
+            for (int k = 0; k < NF_KS; k++) {
+                nsx2[k] = make_float2(-sx[k], -sx[k]);
+                nsy2[k] = make_float2(-sy[k], -sy[k]);
+                nsz2[k] = make_float2(-sz[k], -sz[k]);
+                sq2[k] = make_float2(sq[k], sq[k]);
+                rp2[k] = rx2[k] = ry2[k] = rz2[k] = make_float2(0.0f, 0.0f);
+            }
+        }
         for (int tb = 0; tb < T; tb += NF_TB) {
             const int nt = min(NF_TB, T - tb);
             if (!one_block) {
@@ -391,20 +509,33 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
                 // whole groups of TG, then the rest in groups of TR: pad to TR only
                 const int ntp = (nt + TR - 1) / TR * TR;
                 for (int i = threadIdx.x; i < ntp; i += NF_BS) {
+                    real4 v;
+                    int o;
                     if (i < nt) {
-                        tpos[i] = s_pt[t0 + tb + i];
-                        tori[i] = s_origin[t0 + tb + i];
+                        v = s_pt[t0 + tb + i];
+                        o = s_origin[t0 + tb + i];
                     } else {
                         const real far = -(real)(4 * S + 16);
-                        tpos[i] = make_vec4(far, far, far, real(0));
-                        tori[i] = -2;
+                        v = make_vec4(far, far, far, real(0));
+                        o = -2;
                     }
+                    tpos[i] = v;
+                    tori[i] = o;
+                    if constexpr (sizeof(real) == 4) nf_stage_pair(tpa, tpb, tpo, i, v, o);
                 }
             }
             // targets visible (staged before the prologue's barrier for one
             // block); the previous pass's reads of wpart done
             if (!one_block || pass > 0) __syncthreads();
             int g0 = 0;
+            if constexpr (sizeof(real) == 4) {
+                for (; g0 + TG <= nt; g0 += TG)
+                    nf_targets2<FORCES, GUARD, POW, TG, NF_KS>(tpa, tpb, tpo, g0, nt, nsx2, nsy2, nsz2, sq2, so, rp2,
+                                                               rx2, ry2, rz2, tb_w, wpart[warp], lane);
+                for (; g0 < nt; g0 += TR)
+                    nf_targets2<FORCES, GUARD, POW, TR, NF_KS>(tpa, tpb, tpo, g0, nt, nsx2, nsy2, nsz2, sq2, so, rp2,
+                                                               rx2, ry2, rz2, tb_w, wpart[warp], lane);
+            }
             for (; g0 + TG <= nt; g0 += TG) {
                 real acc[32];
 #pragma unroll
@@ -484,6 +615,15 @@ __global__ void __launch_bounds__(NF_BS) k_p2p(int depth, int periodic, const in
                     v[3] += prev.w;
                 }
                 o = make_vec4(v[0], v[1], v[2], v[3]);
+            }
+        }
+        if constexpr (sizeof(real) == 4) {
+#pragma unroll
+            for (int k = 0; k < NF_KS; k++) {
+                rp[k] = -(rp2[k].x + rp2[k].y);
+                rx[k] = rx2[k].x + rx2[k].y;
+                ry[k] = ry2[k].x + ry2[k].y;
+                rz[k] = rz2[k].x + rz2[k].y;
             }
         }
         // reactions of this pass's sources, complete after all target blocks;
