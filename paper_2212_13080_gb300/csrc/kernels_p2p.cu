@@ -10,6 +10,10 @@
 #include "fmm_internal.cuh"
 #include "lagrange.cuh"
 
+#ifndef NF_QUNROLL
+#define NF_QUNROLL 16  // unroll of the target-pair loop of the packed evaluation
+#endif
+
 namespace fmm {
 
 __device__ __forceinline__ float4 make_vec4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
@@ -333,7 +337,8 @@ __device__ __forceinline__ void nf_targets2(const float4 *tpa, const float4 *tpb
                                             float2 (&rz)[KS], float *tb_w, float *wp, int lane) {
     constexpr int NC = FORCES ? 4 : 1;
     float2 acc[NT / 2 * NC];
-#pragma unroll
+    constexpr int QU = NF_QUNROLL;
+#pragma unroll QU
     for (int q = 0; q < NT / 2; q++) {
         // target pair (g0 + 2q, g0 + 2q + 1): (x0, x1, y0, y1), (z0, z1, -w0, -w1)
         const float4 A = tpa[g0 / 2 + q], Bv = tpb[g0 / 2 + q];
