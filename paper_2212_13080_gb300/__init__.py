@@ -241,7 +241,7 @@ class FMMBatch:
 
     def __init__(self, boxes, depths, p, periodic=False, continuous=False, split_ratio=None,
                  precision="fp32", force_mode="adjoint", max_n=None, split_capacity=None,
-                 sync=True, device=None):
+                 sync=True, device=None, kernel="coulomb"):
         import numpy as np
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
@@ -254,6 +254,7 @@ class FMMBatch:
             o.split_capacity = float(split_capacity)
         o.precision = _PREC[precision]
         o.force_mode = _FORCE[force_mode]
+        o.kernel = _KERNEL[kernel]
         o.sync = int(bool(sync))
         self.out_dtype = torch.float64 if precision == "fp64" else torch.float32
         with torch.cuda.device(self.device):

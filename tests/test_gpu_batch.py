@@ -56,3 +56,29 @@ def test_batch_against_oracle():
         assert np.linalg.norm(phi - ref["phi"]) < 1e-11 * np.linalg.norm(ref["phi"])
         assert abs(r["energy"][i].item() - ref["E"]) < 1e-11 * abs(ref["E"])
     bt.close()
+
+
+@pytest.mark.parametrize("periodic,kernel,force_mode", [(True, "coulomb", "kernel"),
+                                                         (False, "inverse_square", "adjoint")])
+def test_batch_other_kernels_match_single_system(periodic, kernel, force_mode):
+    """Force-kernel forces (§4.1) and the 1/r^2 kernel through the batched
+    path: each system equals its own single-system evaluation bit for bit
+    (the batched systems share their depth's tables, four kernel components
+    for force-kernel plans)."""
+    pos, q, offs, boxes, counts = inputs.batch_systems(6, 17, lo=1024, hi=12000)
+    depths = _depths(counts)
+    bt = FMMBatch(boxes, depths, 4, periodic=periodic, continuous=True, precision="fp32",
+                  max_n=counts, kernel=kernel, force_mode=force_mode)
+    P, Q = torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda()
+    r = bt.eval(P, Q, offs)
+    torch.cuda.synchronize()
+    for i in range(len(counts)):
+        a, b = offs[i], offs[i + 1]
+        plan = FMM(boxes[i], int(depths[i]), 4, periodic=periodic, continuous=True, precision="fp32",
+                   max_n=int(counts[i]), kernel=kernel, force_mode=force_mode)
+        s = plan.eval(P[a:b].contiguous(), Q[a:b].contiguous())
+        assert torch.equal(r["potential"][a:b], s["potential"]), i
+        assert torch.equal(r["forces"][a:b], s["forces"]), i
+        assert r["energy"][i].item() == s["energy"].item(), i
+        plan.close()
+    bt.close()
