@@ -158,8 +158,12 @@ class FMM:
                 h = hb[k][: v.numel()].view(v.shape)
                 h.copy_(v, non_blocking=True)
                 out_h[k] = h
+            # the device status word travels with the outputs; only a nonzero
+            # word needs the library's decoding (a second, short read)
+            hb["status"].copy_(ws[:4].view(torch.int32), non_blocking=True)
             stream_t.synchronize()
-            self._check_status(ws, stream)  # the stream is idle: a short read
+            if int(hb["status"][0]) != 0:
+                self._check_status(ws, stream)
             res = out_h
         return res
 
@@ -174,7 +178,8 @@ class FMM:
             hb = {"n": n,
                   "potential": torch.empty(n, dtype=self.out_dtype).pin_memory(),
                   "energy": torch.empty(1, dtype=torch.float64).pin_memory(),
-                  "forces": torch.empty(3 * n, dtype=self.out_dtype).pin_memory()}
+                  "forces": torch.empty(3 * n, dtype=self.out_dtype).pin_memory(),
+                  "status": torch.zeros(1, dtype=torch.int32).pin_memory()}
             self._hbuf = hb
         return hb
 
