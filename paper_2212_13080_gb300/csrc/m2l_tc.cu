@@ -34,7 +34,7 @@
 namespace fmm {
 
 #define TC_M 128
-#define TC_STAGES 2
+#define TC_STAGES_MAX 3  // stages of the TMA ring (per tile shape, see TcShape::STAGES)
 #define TC_ABYTES (TC_M * 128)      // 128 rows x 32 fp32 (one K chunk)
 #define TC_WAIT_CYCLES (4LL << 30)  // about 2 s of SM clock
 #define TC_NOFF 189
@@ -108,7 +108,10 @@ struct TcShape {
     static constexpr bool LO = MODE != TC_TF32X1;       // lo parts loaded and used
     static constexpr int BBYTES = N * 128;
     static constexpr int STAGE = 2 * TC_ABYTES + 2 * BBYTES;
-    static constexpr int SMEM = TC_STAGES * STAGE + 1024 + 128;
+    // ring depth: three 64 KB stages for N = 128 (one CTA per SM, 193 KB);
+    // two otherwise (N = 64: two CTAs per SM of 2 x 48 KB; N = 224: 2 x 88 KB)
+    static constexpr int STAGES = N == 128 ? 3 : 2;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 128;
     static constexpr int TCOLS = 2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : (2 * N <= 256 ? 256 : 512));
     static constexpr int MINB = N <= 64 ? 2 : 1;
     static constexpr int COLS = N / CH;                 // columns per epilogue thread
@@ -121,10 +124,13 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
     extern __shared__ unsigned char smraw[];
     const uint32_t raw = tc::smem_u32(smraw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
-    const uint32_t bars = sbase + TC_STAGES * Sh::STAGE;
-    const uint32_t full0 = bars, empty0 = bars + 16, rfull0 = bars + 32, rfree0 = bars + 48;
-    const uint32_t done = bars + 64;  // every MMA of this CTA has completed
-    const uint32_t tslot = bars + 72;
+    // barriers: full / empty per stage, rfull / rfree per TMEM region (two),
+    // done, then the TMEM address slot (16 * STAGES + 40 <= 128 bytes)
+    const uint32_t bars = sbase + Sh::STAGES * Sh::STAGE;
+    const uint32_t full0 = bars, empty0 = bars + 8 * Sh::STAGES, rfull0 = bars + 16 * Sh::STAGES;
+    const uint32_t rfree0 = rfull0 + 16;
+    const uint32_t done = rfree0 + 16;  // every MMA of this CTA has completed
+    const uint32_t tslot = done + 8;
     volatile uint32_t *tslot_ptr = reinterpret_cast<volatile uint32_t *>(smraw + (tslot - raw));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -143,11 +149,13 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
     const int bx = par & 1, by = (par >> 1) & 1, bz = par >> 2;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < Sh::STAGES; s++) {
             tc::mbar_init(full0 + 8 * s, 1);
             tc::mbar_init(empty0 + 8 * s, 1);
-            tc::mbar_init(rfull0 + 8 * s, 1);
-            tc::mbar_init(rfree0 + 8 * s, 32 * Sh::EPI);
+        }
+        for (int r = 0; r < 2; r++) {
+            tc::mbar_init(rfull0 + 8 * r, 1);
+            tc::mbar_init(rfree0 + 8 * r, 32 * Sh::EPI);
         }
         tc::mbar_init(done, 1);
         tc::fence_barrier_init();
@@ -161,14 +169,15 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
     if (warp == Sh::EPI && lane == 0) {
         // ---- TMA producer: (offset, K chunk) stages ----
         bool failed = false;
-        int last_phase[TC_STAGES] = {-1, -1};
+        int last_phase[TC_STAGES_MAX];
+        for (int s = 0; s < TC_STAGES_MAX; s++) last_phase[s] = -1;
         int ox = -2 - bx - 1, oy = -2 - by, oz = -2 - bz, it = 0;
         while (!failed && next_offset(bx, by, bz, ox, oy, oz)) {
             const Off f = make_off(bx, by, bz, ox, oy, oz);
             const int cX = X0 + 1 + f.dX, cY = Y0 + 1 + f.dY, cZ = Z0 + 1 + f.dZ;
             for (int kc = 0; kc < Sh::KC; kc++, it++) {
-                const int s = it % TC_STAGES;
-                const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+                const int s = it % Sh::STAGES;
+                const uint32_t ph = (uint32_t)(it / Sh::STAGES) & 1u;
                 if (!tc::mbar_wait(empty0 + 8 * s, ph ^ 1u, TC_WAIT_CYCLES)) {
                     tc_wait_failed(prm.status, 1, l, it);
                     failed = true;
@@ -191,7 +200,7 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
         if (failed) {
             atomicOr(prm.status, ST_TIMEOUT);
             // let the copies already issued land before the CTA can exit
-            for (int s = 0; s < TC_STAGES; s++)
+            for (int s = 0; s < Sh::STAGES; s++)
                 if (last_phase[s] >= 0) tc::mbar_wait(full0 + 8 * s, (uint32_t)last_phase[s], TC_WAIT_CYCLES);
         }
     } else if (warp == Sh::EPI + 1 && lane == 0) {
@@ -209,8 +218,8 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
             const uint32_t d = tmem + (uint32_t)(r * N);
             for (int kc = 0; kc < Sh::KC; kc++) {
                 const int it = Sh::KC * i + kc;
-                const int s = it % TC_STAGES;
-                const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+                const int s = it % Sh::STAGES;
+                const uint32_t ph = (uint32_t)(it / Sh::STAGES) & 1u;
                 if (!tc::mbar_wait(full0 + 8 * s, ph, TC_WAIT_CYCLES)) {
                     tc_wait_failed(prm.status, 3, l, it);
                     failed = true;
