@@ -39,8 +39,8 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
 # DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
 # capture of the current kernels on these workloads (profiles/k_p2p_uniform1m.md,
 # profiles/k_m2l_tc_uniform1m.md); reported as the roofline's traffic
-PROFILED_TRAFFIC = {("uniform1m", "tf32x3", "k_p2p"): 201832448,
-                    ("uniform1m", "tf32x3", "k_m2l_tc"): 42046976}
+PROFILED_TRAFFIC = {("uniform1m", "tf32x3", "k_p2p"): 201362688,
+                    ("uniform1m", "tf32x3", "k_m2l_tc"): 42223360}
 
 
 def _peaks():
