@@ -337,7 +337,9 @@ __device__ __forceinline__ void nf_targets2(const float4 *tpa, const float4 *tpb
                                             float2 (&rz)[KS], float *tb_w, float *wp, int lane) {
     constexpr int NC = FORCES ? 4 : 1;
     float2 acc[NT / 2 * NC];
-    constexpr int QU = NF_QUNROLL;
+    // with forces 4 target pairs, unrolled whole; potential only 16, unrolled
+    // by 4 (whole, they spill)
+    constexpr int QU = FORCES ? NF_QUNROLL : (NF_QUNROLL < 4 ? NF_QUNROLL : 4);
 #pragma unroll QU
     for (int q = 0; q < NT / 2; q++) {
         // target pair (g0 + 2q, g0 + 2q + 1): (x0, x1, y0, y1), (z0, z1, -w0, -w1)
