@@ -56,3 +56,27 @@ def test_reference_arm_runs_on_rank_zero_only():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.run_reference(None, "uniform1m", 2, 1) is None  # returns before any work
+
+
+def test_reference_arm_json_contract():
+    """The reference arm (the oracle on the host cores) prints one JSON line
+    with the contract's keys: impl, the metric of the main arm, its
+    cpu_baseline description and an e2e object without host copies."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "uniform4k", "--steps", "1", "--warmup", "3"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["steps"] == 1 and line["warmup"] >= 3 and line["value"] > 0
+    assert line["config"]["workload"] == "uniform4k"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    e = line["e2e"]
+    assert e["value"] == line["value"] and e["unit"] == line["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
