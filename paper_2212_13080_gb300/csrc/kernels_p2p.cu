@@ -218,6 +218,8 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
 // coordinate 1 below it, 0 above); otherwise the frame coordinates differ by
 // at least one ulp along an axis of delta_d.  So the pairs to skip are charges
 // of the same particle (split charges) and, with GUARD, coincident charges.
+// Single precision evaluates two targets per packed FP32x2 instruction
+// (nf_targets2), the targets staged a second time by pairs.
 //
 // Own phase: the pairs inside A, one-sided (each target against all of A's
 // charges), skipping charges of the same particle and coincident charges.
