@@ -526,3 +526,39 @@ def test_parity_reduced_arrangement(precision, periodic, p):
     with pytest.raises(FmmError) as e:
         FMM(box, 4, p, continuous=True, max_n=len(q), grid_scale=s)
     assert e.value.code == B.FMM_ERR_UNSUPPORTED
+
+
+def test_water_autograd_forces_central_differences():
+    """The periodic continuous water-like configuration (p = 5): forces from the
+    adjoint pass (autograd through fmm_energy) against central differences of
+    the GPU's own FP64 energy, h = 1e-4 (as represented in float32), on 64
+    seeded particles away from the split-band edges.  A reduced system (10,000
+    triples, depth 3): at full size the FP64 energy takes seconds per
+    evaluation and FP32 energy differences are below the rounding."""
+    pos, q, box = inputs.water(10000, 3)
+    plan = FMM(box, 3, 5, periodic=True, continuous=True, precision="fp64", max_n=len(q))
+    P = torch.from_numpy(pos).cuda().requires_grad_(True)
+    Q = torch.from_numpy(q).cuda()
+    from paper_2212_13080_gb300 import fmm_energy
+    E = fmm_energy(plan, P, Q)
+    E.backward()
+    F = -P.grad.double().cpu().numpy()
+    L, S = box[3], 8
+    ref = oracle.fmm(pos, q, box, depth=3, n=5, periodic=True, continuous=True, keep=True)
+    t, dt = ref["t"].astype(np.float64), 1.0 / 256
+    h = 1e-4
+    edge = np.minimum(np.abs(t - dt), np.abs(1 - t - dt)).min(axis=1) * (L / S)  # physical units
+    rng = np.random.default_rng(3)
+    idx = rng.choice(np.where(edge > 4 * h)[0], 64, replace=False)
+    Fmax = np.abs(F).max()
+    for i in idx:
+        for a in range(3):
+            Es, xs = [], []
+            for s in (1, -1):
+                pp = pos.copy()
+                pp[i, a] = np.float32(pos[i, a] + s * h)
+                xs.append(float(pp[i, a]))
+                Es.append(plan.eval(torch.from_numpy(pp).cuda(), Q, forces=False)["energy"].item())
+            fd = -(Es[0] - Es[1]) / (xs[0] - xs[1])
+            assert abs(fd - F[i, a]) < 1e-4 * Fmax, (i, a, fd, F[i, a])
+    plan.close()
