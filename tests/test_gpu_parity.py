@@ -562,3 +562,30 @@ def test_water_autograd_forces_central_differences():
             fd = -(Es[0] - Es[1]) / (xs[0] - xs[1])
             assert abs(fd - F[i, a]) < 1e-4 * Fmax, (i, a, fd, F[i, a])
     plan.close()
+
+
+def test_continuity_through_the_periodic_wall_fp64():
+    """§4.2: a particle moved from just below the wall x = 1 of the periodic box
+    to x = 0 (the same physical place) changes the continuous periodic form's
+    energy by about |F| dx and its force by nearly nothing; the plain periodic
+    form jumps (its near-field partition changes at the wall)."""
+    pos, q, box = inputs.uniform_pm1(1500, 71)
+    Q = torch.from_numpy(q).cuda()
+    below = np.nextafter(np.float32(1.0), np.float32(0))
+    dx = 1.0 - float(below)
+    for cont in (True, False):
+        plan = FMM(box, 3, 4, periodic=True, continuous=cont, precision="fp64", max_n=len(q))
+        out = []
+        for x in (below, np.float32(0.0)):
+            p = pos.copy()
+            p[0, 0] = x
+            r = plan.eval(torch.from_numpy(p).cuda(), Q)
+            out.append((r["energy"].item(), r["forces"][0].cpu().numpy()))
+        (E0, F0), (E1, F1) = out
+        Fm = np.abs(F0).max()
+        if cont:
+            assert abs(E1 - E0) < 3 * Fm * dx + 1e-12 * abs(E0), (E1 - E0, Fm * dx)
+            assert np.abs(F1 - F0).max() < 1e-4 * Fm, (F0, F1)
+        else:
+            assert abs(E1 - E0) > 20 * Fm * dx, (E1 - E0, Fm * dx)
+        plan.close()
