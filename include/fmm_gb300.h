@@ -209,8 +209,11 @@ int fmm_status(fmm_plan_t plan, const void *workspace, void *stream);
  *   FMM_DUMP_POINTS   real [n_eff][4]: (t_x, t_y, t_z, q_eff) per sorted slot,
  *                     t in finest-cell units (real = float, double for FP64 plans)
  *   FMM_DUMP_PHI      real [level][8^level][p^3]: grid charges, natural cell
- *                     order (cz*S + cy)*S + cx, levels 0..depth
- *   FMM_DUMP_LOCAL    real, same layout: functionals L (Psi_C(v) = L_C . v)
+ *                     order (cz*S + cy)*S + cx, levels 0..depth (shift-free plans:
+ *                     the box-basis charges Phi^S of App. A.2)
+ *   FMM_DUMP_LOCAL    real, same layout: functionals L (Psi_C(v) = L_C . v) of
+ *                     the potential kernel (force-kernel plans keep three more
+ *                     blocks, not dumped; shift-free plans: box-basis L^S)
  *   FMM_DUMP_OUT      real [n_eff][4]: (phi, F_x, F_y, F_z) per sorted charge in
  *                     unit-box units (phi per unit charge, F with the charge)
  * Errors: FMM_ERR_ARG (unknown item or dst too small).
