@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(Coef<real> C, int depth, const i
 // into the warp's shared-memory rows; every lane then accumulates its grid
 // nodes (lane, lane + 32, ...) over the chunk.  The cell's total charge: a warp
 // tree per chunk, chunks added with compensation.
+#ifndef P2M_WARPS
 #define P2M_WARPS 4
+#endif
 
 template <typename real, int P>
 __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_warp(Coef<real> C, int depth, int ncell, int sf,

@@ -57,7 +57,9 @@ __device__ __forceinline__ int64_t nf_cell(int cx, int cy, int cz, int dx, int d
 // memory, one thread per charge.
 // ---------------------------------------------------------------------------
 #define L2P_BS 128
+#ifndef L2P_LPC
 #define L2P_LPC 4  // finest cells per CTA (consecutive keys: one contiguous charge range)
+#endif
 
 template <typename real, int P, bool KF>
 constexpr int l2p_lpc() {
