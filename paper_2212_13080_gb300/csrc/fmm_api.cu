@@ -363,12 +363,11 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     W.e_pt = take(W.cap * 4 * rs);
     W.e_wd = take(cont ? W.cap * 4 * rs : 0);
     W.e_origin = take(W.cap * 4);
+    W.e_rank = take(W.cap * 4);
     W.leaf_count = take(W.ncell * 4);
     W.leaf_start = take((W.ncell + 1) * 4);
-    W.cursor = take(W.ncell * 4);
     W.tmp = take(W.cap * 4);
     W.perm = take(W.cap * 4);
-    W.inv = take(W.cap * 4);
     W.s_pt = take(W.cap * 4 * rs);
     W.s_origin = take(W.cap * 4);
     W.out_pt = take(W.cap * 4 * rs);
@@ -431,15 +430,15 @@ Ptrs<real> make_ptrs(const WsLayout &W, void *ws) {
     P.e_pt = (R4 *)(b + W.e_pt);
     P.e_wd = (R4 *)(b + W.e_wd);
     P.e_origin = (int *)(b + W.e_origin);
+    P.e_rank = (int *)(b + W.e_rank);
     P.leaf_count = (int *)(b + W.leaf_count);
     P.leaf_start = (int *)(b + W.leaf_start);
-    P.cursor = (int *)(b + W.cursor);
     P.tmp = (int *)(b + W.tmp);
     P.perm = (int *)(b + W.perm);
-    P.inv = (int *)(b + W.inv);
     P.s_pt = (R4 *)(b + W.s_pt);
     P.s_origin = (int *)(b + W.s_origin);
     P.out_pt = (R4 *)(b + W.out_pt);
+    P.out_e = P.e_pt;  // e_pt is dead once the sort has gathered it
     P.react = (R4 *)(b + W.react);
     P.phi = (real *)(b + W.phi);
     P.loc = (real *)(b + W.loc);
@@ -499,7 +498,6 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
         return FMM_OK;
     }
     cudaMemsetAsync(ptr.leaf_count, 0, W.ncell * 4, st);
-    cudaMemsetAsync(ptr.cursor, 0, W.ncell * 4, st);
     launch_bin_emit<real>(g, C, ptr, W, (int)n, pos, q, st, tr);
     launch_sort<real>(g, ptr, W, (int)n, st, tr);
     // the near field needs only the sorted charges: it runs on its own stream
@@ -910,7 +908,19 @@ int fmm_debug_dump(fmm_plan_t P, int what, const void *workspace, void *dst, siz
     case FMM_DUMP_PERM: return copy(W.perm, need);
     case FMM_DUMP_START: return copy(W.leaf_start, need);
     case FMM_DUMP_POINTS: return copy(W.s_pt, need);
-    case FMM_DUMP_OUT: return copy(W.out_pt, need);
+    case FMM_DUMP_OUT: {
+        // results are kept by emitted index: back to sorted order through perm
+        std::vector<char> e(need);
+        std::vector<int32_t> pm((size_t)h.n_eff);
+        if (cudaMemcpyAsync(e.data(), b + W.e_pt, need, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(pm.data(), b + W.perm, pm.size() * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        const size_t row = 4 * rs;
+        for (size_t s = 0; s < pm.size(); s++)
+            memcpy((char *)dst + s * row, e.data() + (size_t)pm[s] * row, row);
+        return FMM_OK;
+    }
     case FMM_DUMP_WAIT: {
         int32_t c[4] = {h.wait_site, h.wait_block, h.wait_level, h.wait_iter};
         memcpy(dst, c, 16);

@@ -63,9 +63,10 @@ struct WsHeader {
 struct WsLayout {
     size_t hdr;
     size_t count, offset, axes;           // per particle (continuous form)
-    size_t e_key, e_pt, e_wd, e_origin;   // per emitted charge
-    size_t leaf_count, leaf_start, cursor;
-    size_t tmp, perm, inv;
+    size_t e_key, e_pt, e_wd, e_origin;   // per emitted charge (e_pt: results after the sort)
+    size_t e_rank;                        // arrival rank of each emitted charge in its cell
+    size_t leaf_count, leaf_start;
+    size_t tmp, perm;
     size_t s_pt, s_origin, out_pt;
     size_t react;  // [13][cap] near-field reactions per forward direction (mutual near field)
     size_t phi, loc;                      // all levels (loc: ncomp blocks of loc_comp)
@@ -179,9 +180,12 @@ struct Ptrs {
     unsigned char *axes;
     uint32_t *e_key;
     typename Vec4<real>::T *e_pt, *e_wd;
-    int *e_origin;
-    int *leaf_count, *leaf_start, *cursor;
-    int *tmp, *perm, *inv;
+    int *e_origin, *e_rank;
+    int *leaf_count, *leaf_start;
+    int *tmp, *perm;
+    // per emitted charge, once the sort has consumed e_pt: (phi, F) of every
+    // charge in unit-box units, written by the far field at the charges
+    typename Vec4<real>::T *out_e;
     typename Vec4<real>::T *s_pt;
     int *s_origin;
     typename Vec4<real>::T *out_pt;
@@ -296,7 +300,8 @@ void launch_sf_downward(const Geom &g, const Ptrs<double> &P, const WsLayout &W,
                         cudaStream_t st, Tracer &tr);
 
 // near field + far-field evaluation at the charges (kernels_p2p.cu)
-// near field: writes out_pt (assigns); far field at the charges: adds to it
+// near field: writes out_pt (assigns) and the reaction slots; far field at the
+// charges: adds them and the far field, stores the totals to out_e[perm[slot]]
 template <typename real>
 void launch_p2p(const Geom &g, const Ptrs<real> &P, const WsLayout &W, bool forces,
                 cudaStream_t st, Tracer &tr);

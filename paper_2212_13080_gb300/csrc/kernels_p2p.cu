@@ -1,12 +1,14 @@
 // Evaluation at the charges: near field (step 5: direct sum over the finest
 // cell and its 26 neighbours) and far field (§2.2 step 4 and the far-field force
-// at the end of §2.2).  Results per sorted charge, unit-box units:
-//   out_pt[slot] = (phi, F_x, F_y, F_z), phi per unit charge, F with the charge.
+// at the end of §2.2).  Results in unit-box units, (phi, F_x, F_y, F_z) with phi
+// per unit charge and F with the charge.
 // The near-field kernel evaluates every pair of neighbouring cells once for
-// both partners (mutual form): it writes the target cell's own sums to out_pt
-// and the partners' reactions to one slot per direction; the far-field kernel
-// adds the slots in a fixed order and the far field.  The near field needs only
-// the sorted charges and runs beside the far field.
+// both partners (mutual form): it writes the target cell's own sums to
+// out_pt[slot] (sorted order) and the partners' reactions to one slot per
+// direction; the far-field kernel adds the slots in a fixed order and the far
+// field, and stores the total by emitted index, out_e[perm[slot]], where the
+// recombination reads each particle's charges in a row.  The near field needs
+// only the sorted charges and runs beside the far field.
 #include "fmm_internal.cuh"
 #include "lagrange.cuh"
 
@@ -73,7 +75,9 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
                                                 const real *__restrict__ loc_leaf, int64_t loc_comp,
                                                 const typename Vec4<real>::T *__restrict__ react,
                                                 int64_t rstride,
-                                                typename Vec4<real>::T *__restrict__ out_pt) {
+                                                const typename Vec4<real>::T *__restrict__ out_pt,
+                                                const int *__restrict__ perm,
+                                                typename Vec4<real>::T *__restrict__ out_e) {
     typedef typename Vec4<real>::T real4;
     constexpr int P3 = P * P * P;
     constexpr int LPC = l2p_lpc<real, P, KF>();
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
             o.z += -v.w * FS * fy;
             o.w += -v.w * FS * fz;
         }
-        out_pt[s] = o;
+        out_e[perm[s]] = o;
     }
 }
 
@@ -734,7 +738,7 @@ void launch_l2p(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const W
 #define L2P(PP, F, K)                                                                              \
     k_l2p<real, PP, F, K><<<(ncell + l2p_lpc<real, PP, K>() - 1) / l2p_lpc<real, PP, K>(), L2P_BS, 0, st>>>( \
         C, depth, g.periodic, ncell, g.shift_free, P.leaf_start, P.s_pt, loc_leaf, W.loc_comp,      \
-        P.react, W.cap, P.out_pt)
+        P.react, W.cap, P.out_pt, P.perm, P.out_e)
     switch (g.p) {
 #define CASE(PP)                                                                                 \
     case PP:                                                                                     \

@@ -122,52 +122,39 @@ __device__ __forceinline__ void split_entry(const Geom &g, const Coef<real> &C, 
     cell = side ? A.cu : A.cl;
 }
 
-// number of charges per particle (continuous form only)
-__global__ void k_split_count(Geom g, int n, const float *__restrict__ pos, int *__restrict__ count,
-                              unsigned char *__restrict__ axes, WsHeader *hdr) {
-    int st = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int m = 1;
-        unsigned char ax = 0;
-        for (int a = 0; a < 3; a++) {
-            float t;
-            int c;
-            bin_axis(g, pos[3 * i + a], a, t, c, st);
-            AxisInfo A = split_axis_info(g, c, t);
-            m *= A.m;
-            if (A.mode) ax |= (unsigned char)(1 << a);
-        }
-        count[i] = m;
-        axes[i] = ax;
+// Charges of particle i (continuous form) and its split axes (bit a: axis a).
+__device__ __forceinline__ int split_count_one(const Geom &g, const float *__restrict__ pos, int i,
+                                               unsigned char &ax, int &st) {
+    int m = 1;
+    ax = 0;
+    for (int a = 0; a < 3; a++) {
+        float t;
+        int c;
+        bin_axis(g, pos[3 * i + a], a, t, c, st);
+        AxisInfo A = split_axis_info(g, c, t);
+        m *= A.m;
+        if (A.mode) ax |= (unsigned char)(1 << a);
     }
-    if (st) atomicOr(&hdr->status, st);
-}
-
-// Marks every charge of a fully emitted particle with the particle's index
-// (continuous form).  The charges of particle i are [offset[i], offset[i] +
-// count[i]); the emitted particles are the prefix with offset[i+1] <= n_eff.
-__global__ void k_mark(int n, const int *__restrict__ offset, const int *__restrict__ count,
-                       const WsHeader *hdr, int *__restrict__ e_origin) {
-    const int ne = hdr->n_eff;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int e0 = offset[i], m = count[i];
-        if (e0 + m > ne) continue;
-        for (int k = 0; k < m; k++) e_origin[e0 + k] = i;
-    }
+    return m;
 }
 
 // Emits the charges, one thread per charge (no divergence on split
 // particles): charge e is entry k = e - offset[i] of particle i, the tensor
 // product of its axes with x fastest.  Writes the Morton key, (t, q_eff),
-// (W, dW/du) and origin, and counts the charges of every finest cell.
+// (W, dW/du) and origin, and counts the charges of every finest cell; the
+// count before this charge's increment is its rank among the cell's charges
+// in arrival order (e_rank), the slot the sort scatters it to.  The plain form
+// emits every particle (n_eff = n); the continuous form's n_eff was set by the
+// scan of the charge counts.
 template <typename real>
 __global__ void k_emit(Geom g, Coef<real> C, int n, const float *__restrict__ pos,
                        const float *__restrict__ q, const int *__restrict__ offset,
                        uint32_t *__restrict__ e_key, typename Vec4<real>::T *__restrict__ e_pt,
                        typename Vec4<real>::T *__restrict__ e_wd, int *__restrict__ e_origin,
-                       int *__restrict__ leaf_count, WsHeader *hdr) {
+                       int *__restrict__ e_rank, int *__restrict__ leaf_count, WsHeader *hdr) {
     int st = 0;
     const int ne = offset ? hdr->n_eff : n;
+    if (!offset && blockIdx.x == 0 && threadIdx.x == 0) hdr->n_eff = n;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
         const int i = offset ? e_origin[e] : e;
         int k = offset ? e - offset[i] : 0;
@@ -204,39 +191,25 @@ __global__ void k_emit(Geom g, Coef<real> C, int n, const float *__restrict__ po
             e_wd[e] = d;
         }
         if (!offset) e_origin[e] = i;
-        atomicAdd(&leaf_count[key], 1);
+        e_rank[e] = atomicAdd(&leaf_count[key], 1);
     }
     if (st) atomicOr(&hdr->status, st);
 }
 
-// n_eff = charges of the particles that were emitted in full: the particles
-// with offset[i+1] <= cap form a prefix (offsets increase), found by bisection.
-__global__ void k_set_neff(const int *offset, int n, WsHeader *hdr, int cap) {
-    if (!offset) {
-        hdr->n_eff = n;
-        return;
-    }
-    if (offset[n] <= cap) {
-        hdr->n_eff = offset[n];
-        return;
-    }
-    int lo = 0, hi = n;  // number of particles fully emitted is in [lo, hi)
-    while (hi - lo > 1) {
-        int mid = (lo + hi) / 2;
-        if (offset[mid] <= cap) lo = mid; else hi = mid;
-    }
-    // offset[lo] <= cap < offset[lo+1]: particle lo was not emitted
-    hdr->n_eff = offset[lo];
-    atomicOr(&hdr->status, ST_SPLIT_OVERFLOW);
-}
-
 // ---------------------------------------------------------------------------
 // exclusive scan of int32 (three passes: block sums, scan of block sums,
-// block-local scan plus prefix); out has m+1 entries, out[m] = total.
+// block-local scan plus prefix); out has m+1 entries, out[m] = total.  The
+// continuous form's charge counts are computed by the first pass itself, and
+// its last pass also marks the particle of every emitted charge.  Up to
+// SCAN1_MAX entries (the finest cells to depth 5) are scanned by one CTA in
+// one launch.
 // ---------------------------------------------------------------------------
 #define SCAN_BS 256
 #define SCAN_IPT 8
 #define SCAN_TILE (SCAN_BS * SCAN_IPT)
+#define SCAN1_BS 1024
+#define SCAN1_IPT 32
+#define SCAN1_MAX (SCAN1_BS * SCAN1_IPT)
 
 __device__ __forceinline__ int block_excl_scan(int v, int *sh, int &total) {
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -277,6 +250,30 @@ __global__ void k_scan_reduce(const int *__restrict__ in, int m, int *__restrict
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
+// first pass over the particles (continuous form): charges per particle and
+// split axes (§2.3), written out and summed per block
+__global__ void k_split_count_reduce(Geom g, int n, const float *__restrict__ pos, int *__restrict__ count,
+                                     unsigned char *__restrict__ axes, int *__restrict__ bsum,
+                                     WsHeader *hdr) {
+    __shared__ int sh[32];
+    const int base = blockIdx.x * SCAN_TILE;
+    int s = 0, st = 0;
+    for (int k = 0; k < SCAN_IPT; k++) {
+        const int i = base + k * SCAN_BS + threadIdx.x;
+        if (i < n) {
+            unsigned char ax;
+            const int m = split_count_one(g, pos, i, ax, st);
+            count[i] = m;
+            axes[i] = ax;
+            s += m;
+        }
+    }
+    int tot;
+    block_excl_scan(s, sh, tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+    if (st) atomicOr(&hdr->status, st);
+}
+
 __global__ void k_scan_blocks(int *bsum, int nb) {
     __shared__ int sh[32];
     int carry = 0;
@@ -291,8 +288,14 @@ __global__ void k_scan_blocks(int *bsum, int nb) {
     if (threadIdx.x == 0) bsum[nb] = carry;
 }
 
+// MARK (charges per particle): the emitted charges are those of the particles
+// whose charges end at or before cap, a prefix since the offsets increase; the
+// particle of each of them goes to e_origin, and n_eff (their number) to the
+// header, by the particle where the prefix ends (with the overflow status) or,
+// when every particle fits, by the last block.
+template <bool MARK>
 __global__ void k_scan_apply(const int *__restrict__ in, int m, const int *__restrict__ bsum,
-                             int *__restrict__ out) {
+                             int *__restrict__ out, int cap, int *__restrict__ e_origin, WsHeader *hdr) {
     __shared__ int sh[32];
     int base = blockIdx.x * SCAN_TILE;
     int vals[SCAN_IPT];
@@ -307,74 +310,130 @@ __global__ void k_scan_apply(const int *__restrict__ in, int m, const int *__res
     int pre = block_excl_scan(s, sh, tot) + bsum[blockIdx.x];
     for (int k = 0; k < SCAN_IPT; k++) {
         int i = base + threadIdx.x * SCAN_IPT + k;
-        if (i < m) out[i] = pre;
+        if (i < m) {
+            out[i] = pre;
+            if (MARK) {
+                const int end = pre + vals[k];
+                if (end <= cap) {
+                    for (int j = pre; j < end; j++) e_origin[j] = i;
+                } else if (pre <= cap) {
+                    hdr->n_eff = pre;
+                    atomicOr(&hdr->status, ST_SPLIT_OVERFLOW);
+                }
+            }
+        }
         pre += vals[k];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[m] = bsum[gridDim.x];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        const int total = bsum[gridDim.x];
+        out[m] = total;
+        if (MARK && total <= cap) hdr->n_eff = total;
+    }
+}
+
+// m <= SCAN1_MAX: thread t owns entries [32 t, 32 t + 32), read and written as
+// int4 where the run is whole (m is a multiple of 64 from depth 2 on)
+__global__ void __launch_bounds__(SCAN1_BS) k_scan_one(const int *__restrict__ in, int m, int *__restrict__ out) {
+    __shared__ int sh[32];
+    const int b = threadIdx.x * SCAN1_IPT;
+    const bool whole = b + SCAN1_IPT <= m;
+    int v[SCAN1_IPT];
+    int s = 0;
+    if (whole) {
+#pragma unroll
+        for (int k = 0; k < SCAN1_IPT; k += 4) {
+            const int4 w = *reinterpret_cast<const int4 *>(in + b + k);
+            v[k] = w.x;
+            v[k + 1] = w.y;
+            v[k + 2] = w.z;
+            v[k + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN1_IPT; k++) v[k] = b + k < m ? in[b + k] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < SCAN1_IPT; k++) s += v[k];
+    int tot;
+    int pre = block_excl_scan(s, sh, tot);
+#pragma unroll
+    for (int k = 0; k < SCAN1_IPT; k++) {
+        const int x = v[k];
+        v[k] = pre;
+        pre += x;
+    }
+    if (whole) {
+#pragma unroll
+        for (int k = 0; k < SCAN1_IPT; k += 4)
+            *reinterpret_cast<int4 *>(out + b + k) = make_int4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN1_IPT; k++)
+            if (b + k < m) out[b + k] = v[k];
+    }
+    if (threadIdx.x == 0) out[m] = tot;
 }
 
 int launch_scan(const int *in, int *out, int m, int *tmp, cudaStream_t st) {
+    if (m <= SCAN1_MAX) {
+        k_scan_one<<<1, SCAN1_BS, 0, st>>>(in, m, out);
+        return 1;
+    }
     int nb = (m + SCAN_TILE - 1) / SCAN_TILE;
-    if (nb == 0) nb = 1;
     k_scan_reduce<<<nb, SCAN_BS, 0, st>>>(in, m, tmp);
     k_scan_blocks<<<1, 1024, 0, st>>>(tmp, nb);
-    k_scan_apply<<<nb, SCAN_BS, 0, st>>>(in, m, tmp, out);
+    k_scan_apply<false><<<nb, SCAN_BS, 0, st>>>(in, m, tmp, out, 0, nullptr, nullptr);
     return 3;
 }
 
 template <typename real>
 void launch_bin_emit(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, const WsLayout &W,
                      int n, const float *pos, const float *q, cudaStream_t st, Tracer &tr) {
-    int nb = (n + 255) / 256;
-    if (nb < 1) nb = 1;
-    if (nb > 152 * 64) nb = 152 * 64;
     const int *offset = nullptr;
     tr.begin(FMM_STAGE_BIN, st);
     if (g.continuous) {
-        k_split_count<<<nb, 256, 0, st>>>(g, n, pos, P.count, P.axes, P.hdr);
-        tr.count(1 + launch_scan(P.count, P.offset, n, P.scan_tmp, st));
+        // charges per particle, their offsets, the particle of every emitted charge
+        const int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+        k_split_count_reduce<<<nb, SCAN_BS, 0, st>>>(g, n, pos, P.count, P.axes, P.scan_tmp, P.hdr);
+        k_scan_blocks<<<1, 1024, 0, st>>>(P.scan_tmp, nb);
+        k_scan_apply<true><<<nb, SCAN_BS, 0, st>>>(P.count, n, P.scan_tmp, P.offset, (int)W.cap, P.e_origin,
+                                                   P.hdr);
+        tr.count(3);
         offset = P.offset;
-    }
-    k_set_neff<<<1, 1, 0, st>>>(offset, n, P.hdr, (int)W.cap);
-    tr.count();
-    if (offset) {
-        k_mark<<<nb, 256, 0, st>>>(n, offset, P.count, P.hdr, P.e_origin);
-        tr.count();
     }
     int64_t ne_max = offset ? W.cap : n;
     int nbe = (int)((ne_max + 255) / 256);
     if (nbe < 1) nbe = 1;
     if (nbe > 152 * 64) nbe = 152 * 64;
     k_emit<real><<<nbe, 256, 0, st>>>(g, C, n, pos, q, offset, P.e_key, P.e_pt,
-                                      g.continuous ? P.e_wd : nullptr, P.e_origin, P.leaf_count,
-                                      P.hdr);
+                                      g.continuous ? P.e_wd : nullptr, P.e_origin, P.e_rank,
+                                      P.leaf_count, P.hdr);
     tr.count();
     tr.end();
 }
 
 // ---------------------------------------------------------------------------
-// stable counting sort by finest cell: scatter with per-cell cursors, then
-// order each cell's segment by emitted index (= particle order), then gather.
+// stable counting sort by finest cell: scatter to the slot of each charge's
+// arrival rank in its cell, then order each cell's segment by emitted index
+// (= particle order), then gather.
 // ---------------------------------------------------------------------------
 __global__ void k_scatter(const WsHeader *hdr, const uint32_t *__restrict__ e_key,
-                          const int *__restrict__ leaf_start, int *__restrict__ cursor,
+                          const int *__restrict__ e_rank, const int *__restrict__ leaf_start,
                           int *__restrict__ tmp) {
     int ne = hdr->n_eff;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-        uint32_t k = e_key[e];
-        int slot = leaf_start[k] + atomicAdd(&cursor[k], 1);
-        tmp[slot] = e;
-    }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x)
+        tmp[leaf_start[e_key[e]] + e_rank[e]] = e;
 }
 
 // one warp per finest cell: rank every element of the cell's segment among
 // the segment (emission indices, all distinct), and move it to its sorted
-// slot: charge, origin, perm (slot -> emitted index) and inv (emitted -> slot)
+// slot: charge, origin and perm (slot -> emitted index).  Up to 64 elements
+// are ranked in registers (two per lane, compared through shuffles).
 template <typename real>
 __global__ void k_leaf_gather(int ncell, const int *__restrict__ leaf_start, const int *__restrict__ tmp,
                               const typename Vec4<real>::T *__restrict__ e_pt,
                               const int *__restrict__ e_origin, typename Vec4<real>::T *__restrict__ s_pt,
-                              int *__restrict__ s_origin, int *__restrict__ perm, int *__restrict__ inv) {
+                              int *__restrict__ s_origin, int *__restrict__ perm) {
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -382,19 +441,32 @@ __global__ void k_leaf_gather(int ncell, const int *__restrict__ leaf_start, con
         int s0 = leaf_start[c], s1 = leaf_start[c + 1];
         int cnt = s1 - s0;
         if (cnt == 0) continue;
-        if (cnt <= 32) {
-            int v = lane < cnt ? tmp[s0 + lane] : 0x7fffffff;
-            int r = 0;
-            for (int j = 0; j < cnt; j++) {
-                int w = __shfl_sync(0xffffffffu, v, j);
-                r += (w < v);
+        if (cnt <= 64) {
+            const int v0 = lane < cnt ? tmp[s0 + lane] : 0x7fffffff;
+            const int v1 = lane + 32 < cnt ? tmp[s0 + 32 + lane] : 0x7fffffff;
+            int r0 = 0, r1 = 0;
+            const int c0 = cnt < 32 ? cnt : 32;
+            for (int j = 0; j < c0; j++) {
+                const int w = __shfl_sync(0xffffffffu, v0, j);
+                r0 += (w < v0);
+                r1 += (w < v1);
+            }
+            for (int j = 0; j < cnt - 32; j++) {
+                const int w = __shfl_sync(0xffffffffu, v1, j);
+                r0 += (w < v0);
+                r1 += (w < v1);
             }
             if (lane < cnt) {
-                const int slot = s0 + r;
-                perm[slot] = v;
-                inv[v] = slot;
-                s_pt[slot] = e_pt[v];
-                s_origin[slot] = e_origin[v];
+                const int slot = s0 + r0;
+                perm[slot] = v0;
+                s_pt[slot] = e_pt[v0];
+                s_origin[slot] = e_origin[v0];
+            }
+            if (lane + 32 < cnt) {
+                const int slot = s0 + r1;
+                perm[slot] = v1;
+                s_pt[slot] = e_pt[v1];
+                s_origin[slot] = e_origin[v1];
             }
         } else {
             for (int i = lane; i < cnt; i += 32) {
@@ -403,7 +475,6 @@ __global__ void k_leaf_gather(int ncell, const int *__restrict__ leaf_start, con
                 for (int j = 0; j < cnt; j++) r += (tmp[s0 + j] < v);
                 const int slot = s0 + r;
                 perm[slot] = v;
-                inv[v] = slot;
                 s_pt[slot] = e_pt[v];
                 s_origin[slot] = e_origin[v];
             }
@@ -420,11 +491,11 @@ void launch_sort(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, c
     int nbp = (int)((W.cap + 255) / 256);
     if (nbp < 1) nbp = 1;
     if (nbp > 152 * 64) nbp = 152 * 64;
-    k_scatter<<<nbp, 256, 0, st>>>(P.hdr, P.e_key, P.leaf_start, P.cursor, P.tmp);
+    k_scatter<<<nbp, 256, 0, st>>>(P.hdr, P.e_key, P.e_rank, P.leaf_start, P.tmp);
     int nbl = (ncell * 32 + 255) / 256;
     if (nbl > 152 * 64) nbl = 152 * 64;
     k_leaf_gather<real><<<nbl, 256, 0, st>>>(ncell, P.leaf_start, P.tmp, P.e_pt, P.e_origin, P.s_pt,
-                                             P.s_origin, P.perm, P.inv);
+                                             P.s_origin, P.perm);
     tr.count(2);
     tr.end();
 }
@@ -435,7 +506,9 @@ void launch_sort(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, c
 //   phi_i = sum_k W_k phi(s_k)
 //   adjoint force, axis not split: sum_k F(s_k); split axis: -q_i sum_k dW_k/du phi(s_k)
 //   paper force: sum_k F(s_k) on every axis
-// out_pt holds (phi, F) per sorted charge in unit-box units.
+// out_e holds (phi, F) per emitted charge in unit-box units: the charges of
+// particle i are read in a row, [offset[i], offset[i+1]) (i itself in the
+// plain form).
 // backward: grad_pos = -F * gE, grad_q = phi * gE.
 // ---------------------------------------------------------------------------
 #define UNSPLIT_BS 256
@@ -460,8 +533,8 @@ template <typename real>
 __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__restrict__ q,
                           const int *__restrict__ offset,
                           const int *__restrict__ count, const unsigned char *__restrict__ axes,
-                          const int *__restrict__ inv, const typename Vec4<real>::T *__restrict__ e_wd,
-                          const typename Vec4<real>::T *__restrict__ out_pt, real *__restrict__ potential,
+                          const typename Vec4<real>::T *__restrict__ e_wd,
+                          const typename Vec4<real>::T *__restrict__ out_e, real *__restrict__ potential,
                           real *__restrict__ forces, double *__restrict__ epart,
                           const double *__restrict__ grad_energy, real *__restrict__ grad_q,
                           int backward, real sphi, real sF) {
@@ -473,7 +546,7 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
     if (i < n) {
         real phi, Fx, Fy, Fz;
         if (!offset) {
-            typename Vec4<real>::T o = out_pt[inv[i]];
+            typename Vec4<real>::T o = out_e[i];
             phi = o.x;
             Fx = o.y;
             Fy = o.z;
@@ -484,7 +557,7 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
             phi = 0;
             real Sx = 0, Sy = 0, Sz = 0, Nx = 0, Ny = 0, Nz = 0;
             for (int e = e0; e < e0 + m; e++) {
-                typename Vec4<real>::T o = out_pt[inv[e]];
+                typename Vec4<real>::T o = out_e[e];
                 typename Vec4<real>::T d = e_wd[e];
                 phi += d.x * o.x;
                 Sx += o.y;
@@ -577,8 +650,8 @@ void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n
     // unit box -> box of edge L: potentials of 1/r^k scale by L^-k, forces by L^-(k+1)
     const double iL = 1.0 / g.L, sphi = g.power == 2 ? iL * iL : iL;
     k_unsplit<real><<<nb, UNSPLIT_BS, 0, st>>>(
-        g, P.hdr, n, q, g.continuous ? P.offset : nullptr, P.count, P.axes, P.inv,
-        g.continuous ? P.e_wd : nullptr, P.out_pt, potential, forces, ep, grad_energy, grad_q,
+        g, P.hdr, n, q, g.continuous ? P.offset : nullptr, P.count, P.axes,
+        g.continuous ? P.e_wd : nullptr, P.out_e, potential, forces, ep, grad_energy, grad_q,
         backward ? 1 : 0, (real)sphi, (real)(sphi * iL));
     tr.count();
     if (ep) {
