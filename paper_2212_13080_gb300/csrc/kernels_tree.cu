@@ -202,7 +202,8 @@ __global__ void k_emit(Geom g, Coef<real> C, int n, const float *__restrict__ po
 // continuous form's charge counts are computed by the first pass itself, and
 // its last pass also marks the particle of every emitted charge.  Up to
 // SCAN1_MAX entries (the finest cells to depth 5) are scanned by one CTA in
-// one launch.
+// one launch.  The last pass and the one-CTA scan read and write a warp's
+// entries 128 at a time (int4 per lane).
 // ---------------------------------------------------------------------------
 #define SCAN_BS 256
 #define SCAN_IPT 8
@@ -288,41 +289,98 @@ __global__ void k_scan_blocks(int *bsum, int nb) {
     if (threadIdx.x == 0) bsum[nb] = carry;
 }
 
+// Exclusive scan of a CTA's tile of 128 * IT entries per warp from base: warp
+// w owns [base + 128 IT w, base + 128 IT (w + 1)), read 128 entries at a time
+// (one int4 per lane: coalesced).  v[it] gets the lane's four entries of chunk
+// it, pre[it] the exclusive prefix (within the tile) of the first of them;
+// total the tile's sum.
+template <int IT>
+__device__ __forceinline__ void tile_scan(const int *__restrict__ in, int base, int m, int4 (&v)[IT],
+                                          int (&pre)[IT], int *sh, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int run = 0;
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int i = base + (warp * IT + it) * 128 + 4 * lane;
+        int4 x;
+        if (i + 4 <= m) {
+            x = *reinterpret_cast<const int4 *>(in + i);
+        } else {
+            x.x = i < m ? in[i] : 0;
+            x.y = i + 1 < m ? in[i + 1] : 0;
+            x.z = i + 2 < m ? in[i + 2] : 0;
+            x.w = i + 3 < m ? in[i + 3] : 0;
+        }
+        v[it] = x;
+        const int s = x.x + x.y + x.z + x.w;
+        int inc = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        pre[it] = run + inc - s;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    // the warps' totals: only lane 31 contributes, so every lane of warp w
+    // receives the sum over the warps before w
+    const int wpre = block_excl_scan(lane == 31 ? run : 0, sh, total);
+#pragma unroll
+    for (int it = 0; it < IT; it++) pre[it] += wpre;
+}
+
+// writes the exclusive prefixes of the lane's four entries of chunk it
+__device__ __forceinline__ void tile_store(int *__restrict__ out, int i, int m, int p, int4 x) {
+    const int4 r = make_int4(p, p + x.x, p + x.x + x.y, p + x.x + x.y + x.z);
+    if (i + 4 <= m) {
+        *reinterpret_cast<int4 *>(out + i) = r;
+    } else {
+        if (i < m) out[i] = r.x;
+        if (i + 1 < m) out[i + 1] = r.y;
+        if (i + 2 < m) out[i + 2] = r.z;
+    }
+}
+
 // MARK (charges per particle): the emitted charges are those of the particles
 // whose charges end at or before cap, a prefix since the offsets increase; the
 // particle of each of them goes to e_origin, and n_eff (their number) to the
 // header, by the particle where the prefix ends (with the overflow status) or,
 // when every particle fits, by the last block.
 template <bool MARK>
-__global__ void k_scan_apply(const int *__restrict__ in, int m, const int *__restrict__ bsum,
-                             int *__restrict__ out, int cap, int *__restrict__ e_origin, WsHeader *hdr) {
-    __shared__ int sh[32];
-    int base = blockIdx.x * SCAN_TILE;
-    int vals[SCAN_IPT];
-    int s = 0;
-    // thread owns SCAN_IPT consecutive elements
-    for (int k = 0; k < SCAN_IPT; k++) {
-        int i = base + threadIdx.x * SCAN_IPT + k;
-        vals[k] = i < m ? in[i] : 0;
-        s += vals[k];
+__device__ __forceinline__ void mark_one(int i, int m, int pre, int cnt, int cap, int *__restrict__ e_origin,
+                                         WsHeader *hdr) {
+    if (!MARK || i >= m) return;
+    const int end = pre + cnt;
+    if (end <= cap) {
+        for (int j = pre; j < end; j++) e_origin[j] = i;
+    } else if (pre <= cap) {
+        hdr->n_eff = pre;
+        atomicOr(&hdr->status, ST_SPLIT_OVERFLOW);
     }
+}
+
+template <bool MARK>
+__global__ void __launch_bounds__(SCAN_BS) k_scan_apply(const int *__restrict__ in, int m, const int *__restrict__ bsum,
+                                                        int *__restrict__ out, int cap, int *__restrict__ e_origin,
+                                                        WsHeader *hdr) {
+    __shared__ int sh[32];
+    constexpr int IT = SCAN_TILE / SCAN_BS / 4;
+    const int base = blockIdx.x * SCAN_TILE;
+    int4 v[IT];
+    int pre[IT];
     int tot;
-    int pre = block_excl_scan(s, sh, tot) + bsum[blockIdx.x];
-    for (int k = 0; k < SCAN_IPT; k++) {
-        int i = base + threadIdx.x * SCAN_IPT + k;
-        if (i < m) {
-            out[i] = pre;
-            if (MARK) {
-                const int end = pre + vals[k];
-                if (end <= cap) {
-                    for (int j = pre; j < end; j++) e_origin[j] = i;
-                } else if (pre <= cap) {
-                    hdr->n_eff = pre;
-                    atomicOr(&hdr->status, ST_SPLIT_OVERFLOW);
-                }
-            }
-        }
-        pre += vals[k];
+    tile_scan<IT>(in, base, m, v, pre, sh, tot);
+    const int carry = bsum[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int i = base + (warp * IT + it) * 128 + 4 * lane;
+        const int p = pre[it] + carry;
+        tile_store(out, i, m, p, v[it]);
+        mark_one<MARK>(i, m, p, v[it].x, cap, e_origin, hdr);
+        mark_one<MARK>(i + 1, m, p + v[it].x, v[it].y, cap, e_origin, hdr);
+        mark_one<MARK>(i + 2, m, p + v[it].x + v[it].y, v[it].z, cap, e_origin, hdr);
+        mark_one<MARK>(i + 3, m, p + v[it].x + v[it].y + v[it].z, v[it].w, cap, e_origin, hdr);
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         const int total = bsum[gridDim.x];
@@ -331,46 +389,17 @@ __global__ void k_scan_apply(const int *__restrict__ in, int m, const int *__res
     }
 }
 
-// m <= SCAN1_MAX: thread t owns entries [32 t, 32 t + 32), read and written as
-// int4 where the run is whole (m is a multiple of 64 from depth 2 on)
+// m <= SCAN1_MAX: the whole array is one tile of the CTA
 __global__ void __launch_bounds__(SCAN1_BS) k_scan_one(const int *__restrict__ in, int m, int *__restrict__ out) {
     __shared__ int sh[32];
-    const int b = threadIdx.x * SCAN1_IPT;
-    const bool whole = b + SCAN1_IPT <= m;
-    int v[SCAN1_IPT];
-    int s = 0;
-    if (whole) {
-#pragma unroll
-        for (int k = 0; k < SCAN1_IPT; k += 4) {
-            const int4 w = *reinterpret_cast<const int4 *>(in + b + k);
-            v[k] = w.x;
-            v[k + 1] = w.y;
-            v[k + 2] = w.z;
-            v[k + 3] = w.w;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < SCAN1_IPT; k++) v[k] = b + k < m ? in[b + k] : 0;
-    }
-#pragma unroll
-    for (int k = 0; k < SCAN1_IPT; k++) s += v[k];
+    constexpr int IT = SCAN1_MAX / SCAN1_BS / 4;
+    int4 v[IT];
+    int pre[IT];
     int tot;
-    int pre = block_excl_scan(s, sh, tot);
+    tile_scan<IT>(in, 0, m, v, pre, sh, tot);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < SCAN1_IPT; k++) {
-        const int x = v[k];
-        v[k] = pre;
-        pre += x;
-    }
-    if (whole) {
-#pragma unroll
-        for (int k = 0; k < SCAN1_IPT; k += 4)
-            *reinterpret_cast<int4 *>(out + b + k) = make_int4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < SCAN1_IPT; k++)
-            if (b + k < m) out[b + k] = v[k];
-    }
+    for (int it = 0; it < IT; it++) tile_store(out, (warp * IT + it) * 128 + 4 * lane, m, pre[it], v[it]);
     if (threadIdx.x == 0) out[m] = tot;
 }
 
