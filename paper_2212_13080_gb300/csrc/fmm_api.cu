@@ -412,7 +412,7 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     int64_t mx = n > W.ncell ? n : W.ncell;
     W.scan_blocks = (int)(mx / 2048 + 2);
     W.scan_tmp = take((size_t)(W.scan_blocks + 1) * 4);
-    W.epart = take((size_t)((n + 255) / 256 + 1) * 8);
+    W.epart = take((size_t)((n + 255) / 256 + 1) * 16);  // (hi, lo) per block, real <= 8 B
     W.total = o;
     return W;
 }

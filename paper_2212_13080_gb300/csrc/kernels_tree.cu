@@ -564,11 +564,11 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
                           const int *__restrict__ count, const unsigned char *__restrict__ axes,
                           const typename Vec4<real>::T *__restrict__ e_wd,
                           const typename Vec4<real>::T *__restrict__ out_e, real *__restrict__ potential,
-                          real *__restrict__ forces, double *__restrict__ epart,
+                          real *__restrict__ forces, real *__restrict__ epart,
                           const double *__restrict__ grad_energy, real *__restrict__ grad_q,
                           int backward, real sphi, real sF) {
     // sphi = 1/L and sF = 1/L^2 come from the host: no FP64 arithmetic per thread
-    __shared__ double sh[UNSPLIT_BS / 32];
+    __shared__ real sh[UNSPLIT_BS / 32][2];
     double gE = backward ? *grad_energy : 0.0;
     real ehi = 0, elo = 0;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -627,35 +627,51 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
     }
     if (epart) {
         // deterministic block reduction of sum q phi: exact products, then
-        // compensated pair sums over the warp (no FP64 arithmetic per particle)
+        // compensated pair sums over the warp and over the warps in order; the
+        // block's sum stays a (hi, lo) pair of the working precision: no FP64
+        // arithmetic here (a slow pipe on this part, which the per-block
+        // conversions and adds kept busy)
         for (int o = 16; o > 0; o >>= 1) {
             const real bh = __shfl_down_sync(0xffffffffu, ehi, o);
             const real bl = __shfl_down_sync(0xffffffffu, elo, o);
             pair_add(ehi, elo, bh, bl);
         }
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)ehi + (double)elo;
+        if ((threadIdx.x & 31) == 0) {
+            sh[threadIdx.x >> 5][0] = ehi;
+            sh[threadIdx.x >> 5][1] = elo;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double s = 0;
-            for (int w = 0; w < UNSPLIT_BS / 32; w++) s += sh[w];
-            epart[blockIdx.x] = 0.5 * s;
+            real h = sh[0][0], l = sh[0][1];
+            for (int w = 1; w < UNSPLIT_BS / 32; w++) pair_add(h, l, sh[w][0], sh[w][1]);
+            epart[2 * blockIdx.x] = h;
+            epart[2 * blockIdx.x + 1] = l;
         }
     }
 }
 
-// total energy from the block partials: strided per-thread sums, warp trees,
-// then the warps' sums in order (fixed order: deterministic)
-__global__ void k_energy_final(const double *__restrict__ epart, int nb, double *energy) {
-    __shared__ double sh[32];
-    double s = 0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += epart[b];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+// total energy from the blocks' (hi, lo) pairs: strided per-thread pair sums,
+// warp trees, then the warps' pairs in order (fixed order: deterministic);
+// E = (hi + lo) / 2 in FP64 once
+template <typename real>
+__global__ void k_energy_final(const real *__restrict__ epart, int nb, double *energy) {
+    __shared__ real sh[32][2];
+    real h = 0, l = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) pair_add(h, l, epart[2 * b], epart[2 * b + 1]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const real bh = __shfl_down_sync(0xffffffffu, h, o);
+        const real bl = __shfl_down_sync(0xffffffffu, l, o);
+        pair_add(h, l, bh, bl);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[threadIdx.x >> 5][0] = h;
+        sh[threadIdx.x >> 5][1] = l;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
-        *energy = t;
+        real th = sh[0][0], tl = sh[0][1];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) pair_add(th, tl, sh[w][0], sh[w][1]);
+        *energy = 0.5 * ((double)th + (double)tl);
     }
 }
 
@@ -675,7 +691,7 @@ void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n
         return;
     }
     int nb = (n + UNSPLIT_BS - 1) / UNSPLIT_BS;
-    double *ep = (!backward && energy) ? P.epart : nullptr;
+    real *ep = (!backward && energy) ? reinterpret_cast<real *>(P.epart) : nullptr;  // [nb][2]
     // unit box -> box of edge L: potentials of 1/r^k scale by L^-k, forces by L^-(k+1)
     const double iL = 1.0 / g.L, sphi = g.power == 2 ? iL * iL : iL;
     k_unsplit<real><<<nb, UNSPLIT_BS, 0, st>>>(
@@ -684,7 +700,7 @@ void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n
         backward ? 1 : 0, (real)sphi, (real)(sphi * iL));
     tr.count();
     if (ep) {
-        k_energy_final<<<1, 1024, 0, st>>>(P.epart, nb, energy);
+        k_energy_final<real><<<1, 1024, 0, st>>>(ep, nb, energy);
         tr.count();
     }
     tr.end();
