@@ -213,7 +213,10 @@ int fmm_status(fmm_plan_t plan, const void *workspace, void *stream);
  *                     the box-basis charges Phi^S of App. A.2)
  *   FMM_DUMP_LOCAL    real, same layout: functionals L (Psi_C(v) = L_C . v) of
  *                     the potential kernel (force-kernel plans keep three more
- *                     blocks, not dumped; shift-free plans: box-basis L^S)
+ *                     blocks, not dumped; shift-free plans: box-basis L^S).
+ *                     They are formed only at cells that hold charges (step 4
+ *                     reads no other) on the levels of the downward pass (open
+ *                     form: levels >= 2); every other entry reads as zero.
  *   FMM_DUMP_OUT      real [n_eff][4]: (phi, F_x, F_y, F_z) per sorted charge in
  *                     unit-box units (phi per unit charge, F with the charge)
  * Errors: FMM_ERR_ARG (unknown item or dst too small).

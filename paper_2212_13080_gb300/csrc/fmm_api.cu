@@ -409,6 +409,7 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     const size_t pht = (size_t)tc_level_first(P->depth + 1);  // cells of the operand layout
     W.phihi = take(P->tc ? pht * p3s * rs : 0);
     W.philo = take(P->tc ? pht * p3s * rs : 0);
+    W.occ = take(P->tc ? (size_t)occ_ints(P->depth, P->periodic ? 1 : 2) * 4 : 0);
     int64_t mx = n > W.ncell ? n : W.ncell;
     W.scan_blocks = (int)(mx / 2048 + 2);
     W.scan_tmp = take((size_t)(W.scan_blocks + 1) * 4);
@@ -446,6 +447,7 @@ Ptrs<real> make_ptrs(const WsLayout &W, void *ws) {
     P.m2l_part = (real *)(b + W.m2l_part);
     P.phihi = (real *)(b + W.phihi);
     P.philo = (real *)(b + W.philo);
+    P.occ = (int *)(b + W.occ);
     P.scan_tmp = (int *)(b + W.scan_tmp);
     P.epart = (double *)(b + W.epart);
     return P;
@@ -935,16 +937,37 @@ int fmm_debug_dump(fmm_plan_t P, int what, const void *workspace, void *dst, siz
         if (cudaMemcpyAsync(raw.data(), b + off, raw.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return FMM_ERR_CUDA;
+        // functionals are formed at the cells that hold charges, on the
+        // levels of the downward pass (open form: from level 2); the others
+        // are reported as zero
+        std::vector<int32_t> start;
+        if (!isphi) {
+            start.resize((size_t)W.ncell + 1);
+            if (cudaMemcpyAsync(start.data(), b + W.leaf_start, start.size() * 4, cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return FMM_ERR_CUDA;
+        }
+        const int lform = P->periodic ? 0 : 2;
         char *d = (char *)dst;
         size_t o = 0;
         for (int l = 0; l <= P->depth; l++) {
             int S = 1 << l;
             int64_t lvl = isphi ? W.phi_level[l] : W.loc_level[l];
+            const int sh = 3 * (P->depth - l);
             for (int cz = 0; cz < S; cz++)
                 for (int cy = 0; cy < S; cy++)
                     for (int cx = 0; cx < S; cx++) {
                         int64_t c = isphi ? phi_cell(l, cx, cy, cz) : loc_cell(l, cx, cy, cz);
-                        memcpy(d + o, raw.data() + (size_t)(lvl + c * p3) * rs, (size_t)p3 * rs);
+                        bool formed = true;
+                        if (!isphi) {
+                            const int64_t k = morton_encode(cx, cy, cz);
+                            formed = l >= lform && start[(size_t)((k + 1) << sh)] > start[(size_t)(k << sh)];
+                        }
+                        if (formed)
+                            memcpy(d + o, raw.data() + (size_t)(lvl + c * p3) * rs, (size_t)p3 * rs);
+                        else
+                            memset(d + o, 0, (size_t)p3 * rs);
                         o += (size_t)p3 * rs;
                     }
         }

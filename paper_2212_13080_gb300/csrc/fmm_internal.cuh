@@ -73,6 +73,7 @@ struct WsLayout {
     size_t qlev;                          // total charge of every cell, padded Phi layout
     size_t phihi, philo;                  // TF32 split of Phi (tensor-core plans)
     size_t m2l_part;                      // per-offset-group partials of the SIMT contraction
+    size_t occ;                           // occupied-cell lists of the contraction (tensor-core plans)
     size_t scan_tmp, epart;
     size_t total;
     int64_t cap;                          // charge capacity
@@ -144,6 +145,43 @@ __host__ __device__ inline int64_t loc_cell(int l, int cx, int cy, int cz) {
 }
 __host__ __device__ inline int64_t loc_level_cells(int l) { return (int64_t)1 << (3 * l); }
 
+// A cell of level l with Morton key k holds charges iff its finest cells
+// [k 8^(depth-l), (k+1) 8^(depth-l)) hold any: their sorted ranges do not
+// all start at the same slot.
+__device__ __forceinline__ bool cell_occupied(const int *leaf_start, int depth, int l, int64_t key) {
+    const int sh = 3 * (depth - l);
+    return leaf_start[(key + 1) << sh] > leaf_start[key << sh];
+}
+
+// Occupied-cell lists of the tensor-core contraction: one segment per (level
+// l >= lmin, target parity), s = 8 (l - lmin) + parity, holding the occupied
+// cells of that parity in coarse Morton order; the lists are built in blocks
+// of OCC_BLOCK coarse cells.  Ints in the workspace region `occ`:
+//   [0, nblk)                     occupied cells per block (then their prefix)
+//   [nblk, nblk + nseg)           occupied cells per segment
+//   [.., + nseg + 1)              prefix of the segments' 128-row tiles
+//   [occ_list_offset, ..)         the lists, segment s from the number of
+//                                 cells of the segments before it
+#define OCC_BLOCK 1024
+__host__ __device__ inline int occ_nseg(int depth, int lmin) { return 8 * (depth - lmin + 1); }
+__host__ __device__ inline int64_t occ_seg_cells(int lmin, int s) { return (int64_t)1 << (3 * (lmin + s / 8 - 1)); }
+__host__ __device__ inline int64_t occ_seg_first(int lmin, int s) {  // first list entry of segment s
+    int64_t b = 0;
+    for (int k = 0; k < s; k++) b += occ_seg_cells(lmin, k);
+    return b;
+}
+__host__ __device__ inline int occ_nblk(int depth, int lmin) {
+    int nb = 0;
+    for (int s = 0; s < occ_nseg(depth, lmin); s++) nb += (int)((occ_seg_cells(lmin, s) + OCC_BLOCK - 1) / OCC_BLOCK);
+    return nb;
+}
+__host__ __device__ inline int64_t occ_list_offset(int depth, int lmin) {
+    return ((int64_t)occ_nblk(depth, lmin) + 2 * occ_nseg(depth, lmin) + 1 + 63) / 64 * 64;
+}
+__host__ __device__ inline int64_t occ_ints(int depth, int lmin) {
+    return occ_list_offset(depth, lmin) + occ_seg_first(lmin, occ_nseg(depth, lmin));
+}
+
 template <typename real> struct Vec4;
 template <> struct Vec4<float> { typedef float4 T; };
 template <> struct Vec4<double> { typedef double4 T; };
@@ -194,6 +232,7 @@ struct Ptrs {
     real *qlev;
     real *phihi, *philo;
     real *m2l_part;
+    int *occ;
     int *scan_tmp;
     double *epart;
 };

@@ -488,10 +488,13 @@ __global__ void k_lattice(int p3, const real *__restrict__ Klt, const real *__re
 // §2.2 step 3: Psi_child(v) = Psi_parent(shift_{child->parent}(v)), i.e.
 // L_child_h += (G_hx (x) G_hy (x) G_hz)^T L_parent, as three passes (z, y, x).
 // One CTA per parent of level l-1; adds to the 8 children of level l (which
-// already hold their own interaction-list contributions).
+// already hold their own interaction-list contributions).  Only cells that
+// hold charges are formed: step 4 reads no other functional, and the children
+// of a cell without charges hold none either.
 // ---------------------------------------------------------------------------
 template <typename real, int P>
-__global__ void __launch_bounds__(M2M_BS) k_l2l(Coef<real> C, int l, const real *__restrict__ loc_parent,
+__global__ void __launch_bounds__(M2M_BS) k_l2l(Coef<real> C, int l, int depth, const int *__restrict__ leaf_start,
+                                                const real *__restrict__ loc_parent,
                                                 real *__restrict__ loc_child) {
     constexpr int P3 = P * P * P, PP = P * P;
     extern __shared__ unsigned char smraw[];
@@ -499,9 +502,17 @@ __global__ void __launch_bounds__(M2M_BS) k_l2l(Coef<real> C, int l, const real 
     real *A = Lp + P3;                           // [hz][k][J][I]       2 p^3
     real *B = A + 2 * P3;                        // [hz][hy][k][j][I]   4 p^3
     real *Gs = B + 4 * P3;                       // [h][J][i]           2 p^2
+    __shared__ unsigned occ_child;               // bit h: child h holds charges
     const int Hp = 1 << (l - 1);  // parents per axis (level l-1)
     const int pid = blockIdx.x;
     const int px = pid % Hp, py = (pid / Hp) % Hp, pz = pid / (Hp * Hp);
+    const int64_t pkey = morton_encode(px, py, pz);
+    if (!cell_occupied(leaf_start, depth, l - 1, pkey)) return;
+    if (threadIdx.x < 32) {
+        const bool o = threadIdx.x < 8 && cell_occupied(leaf_start, depth, l, pkey * 8 + threadIdx.x);
+        const unsigned m = __ballot_sync(0xffffffffu, o);
+        if (threadIdx.x == 0) occ_child = m;
+    }
     const real *src = loc_parent + loc_cell(l - 1, px, py, pz) * P3;
     for (int e = threadIdx.x; e < 2 * PP; e += M2M_BS) Gs[e] = C.G[e / PP][e % PP];
     for (int o = threadIdx.x; o < P3; o += M2M_BS) Lp[o] = src[o];
@@ -535,7 +546,7 @@ __global__ void __launch_bounds__(M2M_BS) k_l2l(Coef<real> C, int l, const real 
 #pragma unroll
         for (int I = 0; I < P; I++) s += g[I * P] * b[I];
         const int cx = 2 * px + hx, cy = 2 * py + hy, cz = 2 * pz + hz;
-        loc_child[loc_cell(l, cx, cy, cz) * P3 + o] += s;
+        if (occ_child & (1u << h)) loc_child[loc_cell(l, cx, cy, cz) * P3 + o] += s;
     }
 }
 
@@ -678,7 +689,7 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
 #define CASE(PP)                                                                                   \
     case PP:                                                                                       \
         k_l2l<real, PP><<<nparent, M2M_BS, l2l_smem<real, PP>(), st>>>(                            \
-            C, l, loc_c + W.loc_level[l - 1], loc_c + W.loc_level[l]);                             \
+            C, l, depth, P.leaf_start, loc_c + W.loc_level[l - 1], loc_c + W.loc_level[l]);        \
         break;
                 CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE

@@ -318,6 +318,489 @@ __global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::M
     }
 }
 
+// ---------------------------------------------------------------------------
+// Occupied cells.  Only the functionals of cells that hold a charge are read
+// (step 4 evaluates a cell's functional at its own charges, and a cell with
+// charges has a parent with charges), so the contraction forms those alone:
+// its 128-row tiles are cut from a list of the occupied cells of each (level,
+// target parity) segment, in coarse Morton order, built after the sort.
+// ---------------------------------------------------------------------------
+struct OccParams {
+    const int *leaf_start;
+    int *occ;  // the workspace region (layout in fmm_internal.cuh)
+    int depth, lmin, nseg, nblk;
+    int bfirst[8 * (FMM_MAXDEPTH + 1) + 1];  // first block of each segment
+};
+
+// block -> segment, level, parity and its first coarse cell
+__device__ __forceinline__ int occ_block_segment(const OccParams &op, int &l, int &par, int64_t &c0) {
+    int s = 0;
+    while (s + 1 < op.nseg && (int)blockIdx.x >= op.bfirst[s + 1]) s++;
+    l = op.lmin + s / 8;
+    par = s & 7;
+    c0 = (int64_t)(blockIdx.x - op.bfirst[s]) * OCC_BLOCK;
+    return s;
+}
+
+// Occupancy of the four consecutive coarse cells of this thread (bit k: cell
+// c0 + 4 threadIdx.x + k) and the block's exclusive prefix of their count.
+__device__ __forceinline__ unsigned occ_flags(const OccParams &op, int l, int par, int64_t c0, int &pre,
+                                              int &total) {
+    __shared__ int wsum[OCC_BLOCK / 4 / 32];
+    const int64_t ncs = occ_seg_cells(op.lmin, 8 * (l - op.lmin));
+    unsigned f = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int64_t kc = c0 + 4 * threadIdx.x + k;
+        if (kc < ncs && cell_occupied(op.leaf_start, op.depth, l, kc * 8 + par)) f |= 1u << k;
+    }
+    const int v = __popc(f), lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    int before = 0;
+    total = 0;
+#pragma unroll
+    for (int w = 0; w < OCC_BLOCK / 4 / 32; w++) {
+        before += w < warp ? wsum[w] : 0;
+        total += wsum[w];
+    }
+    pre = before + inc - v;
+    return f;
+}
+
+__global__ void __launch_bounds__(OCC_BLOCK / 4) k_occ_count(const __grid_constant__ OccParams op) {
+    int l, par, pre, total;
+    int64_t c0;
+    occ_block_segment(op, l, par, c0);
+    occ_flags(op, l, par, c0, pre, total);
+    if (threadIdx.x == 0) op.occ[blockIdx.x] = total;
+}
+
+// per segment (one warp each): the blocks' exclusive prefix and the segment's count
+__global__ void k_occ_offsets(const __grid_constant__ OccParams op) {
+    int *bcnt = op.occ, *cnt = op.occ + op.nblk;
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (s >= op.nseg) return;
+    int run = 0;
+    for (int b0 = op.bfirst[s]; b0 < op.bfirst[s + 1]; b0 += 32) {
+        const int b = b0 + lane;
+        const int c = b < op.bfirst[s + 1] ? bcnt[b] : 0;
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (b < op.bfirst[s + 1]) bcnt[b] = run + inc - c;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) cnt[s] = run;
+}
+
+// the list entries: coarse coordinates X | Y << 10 | Z << 20 of each occupied
+// cell; block 0 also writes the prefix of the segments' 128-row tiles
+__global__ void __launch_bounds__(OCC_BLOCK / 4) k_occ_scatter(const __grid_constant__ OccParams op) {
+    int l, par, pre, total;
+    int64_t c0;
+    const int s = occ_block_segment(op, l, par, c0);
+    unsigned f = occ_flags(op, l, par, c0, pre, total);
+    int *dst = op.occ + occ_list_offset(op.depth, op.lmin) + occ_seg_first(op.lmin, s) + op.occ[blockIdx.x] + pre;
+    for (int k = 0; k < 4; k++) {
+        if (f & (1u << k)) {
+            int X, Y, Z;
+            morton_decode((uint32_t)(c0 + 4 * threadIdx.x + k), X, Y, Z);
+            *dst++ = X | (Y << 10) | (Z << 20);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int *cnt = op.occ + op.nblk;
+        int *tiles = op.occ + op.nblk + op.nseg;
+        int t = 0;
+        for (int k = 0; k < op.nseg; k++) {
+            tiles[k] = t;
+            t += (cnt[k] + 127) / 128;
+        }
+        tiles[op.nseg] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The contraction over the occupied-cell lists.  One CTA per 128-row tile of a
+// segment (level l, target parity b): row r is the tile's r-th occupied
+// target cell; for offset o its A operand row is the source cell (target + o)
+// of the operand layout, gathered by the producer warps with 16-byte
+// cp.async copies straight into the 128-byte-swizzled K-major layout (the
+// 16-byte chunk j of row r lands at chunk j ^ (r mod 8)); the kernel matrix B
+// arrives by TMA as in the box form.  The copies of a stage are complete and
+// fenced for the async proxy before the producers arrive on its barrier.  MMA
+// issue, TMEM regions and the epilogue are those of the box form, so every
+// row is summed over the offsets in the same order: a row's functional is the
+// box form's bit for bit.
+// ---------------------------------------------------------------------------
+struct TcgParams {
+    CUtensorMap k_hi, k_lo;
+    CUtensorMap phi_hi[FMM_MAXDEPTH + 1], phi_lo[FMM_MAXDEPTH + 1];  // box maps of the operand layout
+    const char *op_hi, *op_lo;  // operand copies of the grid charges (every level)
+    int row_bytes;              // bytes of one cell vector in the operand layout
+    int lmin, depth, p3, spow, nseg;
+    const int *occ;             // occupied-cell lists
+    long long op_cell0[FMM_MAXDEPTH + 2];  // first operand cell of each level
+    long long loc_off[FMM_MAXDEPTH + 1];
+    long long q_off[FMM_MAXDEPTH + 1];
+    float *loc;
+    const float *qlev;
+    const float *kbar;  // [343][N], zero padded
+    int *status;
+    int inject_stall;   // test hook: the first stage's kernel copies are withheld
+};
+
+// Ring depths per tile shape.  N >= 128: the gathered A stages (32 KB each)
+// and the kernel-matrix B stages (2 N 128 bytes) are separate rings with their
+// own producers, so the gather keeps G = SA - 1 stages of copies in flight per
+// producer thread; one CTA per SM (N = 224: 3 A + 2 B stages, 208 KB; N = 128:
+// 4 + 2, 192 KB).  N <= 64 (UNI): one ring whose stages hold A and B, one
+// producer warp whose first lane also issues the B copies, six warps and two
+// CTAs per SM (each CTA's barrier round trips and epilogue hide under the
+// other's MMAs).
+template <int N, int MODE>
+struct TcgShape {
+    typedef TcShape<N, MODE> B;
+    static constexpr bool UNI = N <= 64;
+    static constexpr int PW = UNI ? 1 : 2;  // producer (gather) warps
+    static constexpr int NPROD = 32 * PW;
+    static constexpr int SA = UNI ? 2 : (N == 224 ? 3 : 4);
+    static constexpr int SB = 2;
+    static constexpr int G = SA - 1;                 // copy groups in flight per producer thread
+    static constexpr int ASTAGE = 2 * TC_ABYTES;     // hi, lo
+    static constexpr int BSTAGE = 2 * B::BBYTES;     // hi, lo
+    static constexpr int WB = B::EPI + PW;           // kernel-matrix TMA warp (split rings)
+    static constexpr int WM = UNI ? WB : WB + 1;     // MMA warp
+    static constexpr int THREADS = 32 * (WM + 1);
+    static constexpr int MINB = UNI ? 2 : 1;
+    static constexpr int SMEM = 1024 + SA * ASTAGE + SB * BSTAGE + 256 + 3 * TC_M * 4;
+};
+
+template <int G>
+__device__ __forceinline__ void cp_async_wait_pending() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(G) : "memory");
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>::MINB) k_m2l_tcg(const __grid_constant__ TcgParams prm) {
+    typedef TcShape<N, MODE> Sh;
+    typedef TcgShape<N, MODE> Gh;
+    const int nblk = occ_nblk(prm.depth, prm.lmin);
+    const int *cnt_seg = prm.occ + nblk, *tiles = cnt_seg + prm.nseg;
+    if ((int)blockIdx.x >= tiles[prm.nseg]) return;  // past the last occupied tile
+    int sg = 0;
+    while (sg + 1 < prm.nseg && (int)blockIdx.x >= tiles[sg + 1]) sg++;
+    const int l = prm.lmin + sg / 8, par = sg & 7;
+    const int bx = par & 1, by = (par >> 1) & 1, bz = par >> 2;
+    const int H = 1 << (l - 1), P = H + 2, Pt = (int)tc_level_extent(l);
+    const int count = cnt_seg[sg];
+    const int r0 = ((int)blockIdx.x - tiles[sg]) * TC_M;  // first list entry of the tile
+    const int *lst = prm.occ + occ_list_offset(prm.depth, prm.lmin) + occ_seg_first(prm.lmin, sg);
+
+    extern __shared__ unsigned char smraw[];
+    const uint32_t raw = tc::smem_u32(smraw);
+    const uint32_t abase = (raw + 1023u) & ~1023u;           // A ring
+    const uint32_t bbase = abase + Gh::SA * Gh::ASTAGE;       // B ring
+    const uint32_t bars = bbase + Gh::SB * Gh::BSTAGE;
+    const uint32_t afull0 = bars, aempty0 = afull0 + 8 * Gh::SA;
+    const uint32_t bfull0 = aempty0 + 8 * Gh::SA, bempty0 = bfull0 + 8 * Gh::SB;
+    const uint32_t rfull0 = bempty0 + 8 * Gh::SB, rfree0 = rfull0 + 16;
+    const uint32_t done = rfree0 + 16;
+    const uint32_t tslot = done + 8;
+    volatile uint32_t *tslot_ptr = reinterpret_cast<volatile uint32_t *>(smraw + (tslot - raw));
+    // per row: source-cell base in the operand layout, cell in the padded
+    // Phi layout (charges Q), target cell in the L layout (-1: past the list)
+    int *rowA = reinterpret_cast<int *>(smraw + (bars - raw) + 256);
+    int *rowQ = rowA + TC_M, *rowL = rowQ + TC_M;
+
+    // Box tiles: when every cell of the segment holds charges the tile's 128
+    // consecutive Morton cells form one 8 x 4 x 4 box, and each offset's A
+    // operand is one TMA box copy (row r = x + 8 y + 32 z of the box) instead
+    // of 128 gathered rows.  Levels with fewer than 8 coarse cells per axis
+    // take one box at the origin, partly outside the grid (the operand layout
+    // holds zeros there; those rows are not stored), whatever their occupancy.
+    const bool box = H < 8 || count == (1 << (3 * (l - 1)));
+    int X0 = 0, Y0 = 0, Z0 = 0;
+    if (box) morton_decode((uint32_t)r0, X0, Y0, Z0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < TC_M) {
+        const int r = threadIdx.x;
+        int X, Y, Z;
+        bool in;
+        if (box) {
+            X = X0 + (r & 7);
+            Y = Y0 + ((r >> 3) & 3);
+            Z = Z0 + (r >> 5);
+            in = X < H && Y < H && Z < H;
+        } else {
+            in = r0 + r < count;
+            const int pk = lst[in ? r0 + r : r0];  // rows past the list repeat the tile's first cell
+            X = pk & 1023;
+            Y = (pk >> 10) & 1023;
+            Z = pk >> 20;
+        }
+        rowA[r] = ((Z + 1) * Pt + Y + 1) * Pt + X + 1;
+        rowQ[r] = ((Z + 1) * P + Y + 1) * P + X + 1;
+        rowL[r] = in ? ((par * H + Z) * H + Y) * H + X : -1;
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Gh::SA; s++) {
+            // arrivals: the box copies' issuer, or every gather thread (plus the
+            // issuer of the B copies when they share the ring)
+            tc::mbar_init(afull0 + 8 * s, box ? 1 : Gh::NPROD + (Gh::UNI ? 1 : 0));
+            tc::mbar_init(aempty0 + 8 * s, 1);
+        }
+        for (int s = 0; s < Gh::SB; s++) {
+            tc::mbar_init(bfull0 + 8 * s, 1);
+            tc::mbar_init(bempty0 + 8 * s, 1);
+        }
+        for (int r = 0; r < 2; r++) {
+            tc::mbar_init(rfull0 + 8 * r, 1);
+            tc::mbar_init(rfree0 + 8 * r, 32 * Sh::EPI);
+        }
+        tc::mbar_init(done, 1);
+        tc::fence_barrier_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, Sh::TCOLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot_ptr;
+
+    if (warp >= Sh::EPI && warp < Sh::EPI + Gh::PW && (!box || (warp == Sh::EPI && lane == 0))) {
+        // ---- A producers.  Box tiles: the first lane issues one TMA box (hi,
+        //      lo) per stage.  Otherwise the gather: lane = (row within a group
+        //      of four) * 8 + 16-byte chunk, warp pw takes rows 4 (pw + PW i) +
+        //      lane / 8; a stage is signalled once its copies are complete and
+        //      fenced for the async proxy, G - 1 stages later (G stages of copies
+        //      in flight).  With one ring (UNI) the first lane also issues the
+        //      stage's B copies. ----
+        const int pw = warp - Sh::EPI;
+        const bool lead = pw == 0 && lane == 0;
+        const int j = lane & 7, rsub = lane >> 3;
+        constexpr uint32_t ABYTES = Sh::LO ? 2 * TC_ABYTES : TC_ABYTES;
+        constexpr uint32_t BBYTES = Sh::LO ? 2 * Sh::BBYTES : Sh::BBYTES;
+        bool failed = false;
+        int last_phase[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+        int sig = 0;  // next gathered stage to signal
+        const int64_t lvl0 = prm.op_cell0[l];
+        const int64_t pt3 = (int64_t)Pt * Pt * Pt;
+        int ox = -2 - bx - 1, oy = -2 - by, oz = -2 - bz, it = 0;
+        while (!failed && next_offset(bx, by, bz, ox, oy, oz)) {
+            const Off f = make_off(bx, by, bz, ox, oy, oz);
+            const int64_t delta = lvl0 + f.spar * pt3 + ((int64_t)f.dZ * Pt + f.dY) * Pt + f.dX;
+            const int cX = X0 + 1 + f.dX, cY = Y0 + 1 + f.dY, cZ = Z0 + 1 + f.dZ;
+            for (int kc = 0; kc < Sh::KC; kc++, it++) {
+                const int s = it % Gh::SA;
+                const uint32_t ph = (uint32_t)(it / Gh::SA) & 1u;
+                if (!tc::mbar_wait(aempty0 + 8 * s, ph ^ 1u, TC_WAIT_CYCLES)) {
+                    if (lane == 0) tc_wait_failed(prm.status, 1, l, it);
+                    failed = true;
+                    break;
+                }
+                const uint32_t st = abase + s * Gh::ASTAGE;
+                const uint32_t fb = afull0 + 8 * s;
+                // TMA bytes of this stage (an arrival of its own; none when the
+                // lead only gathers)
+                const uint32_t tx = (box ? ABYTES : 0u) + (Gh::UNI ? BBYTES : 0u);
+                if (lead && tx) {
+                    tc::mbar_expect_tx(fb, tx);
+                    last_phase[s] = (int)ph;
+                    if (box) {
+                        tc::tma_load_5d(st, &prm.phi_hi[l], fb, kc * Sh::KE, cX, cY, cZ, f.spar);
+                        if (Sh::LO) tc::tma_load_5d(st + TC_ABYTES, &prm.phi_lo[l], fb, kc * Sh::KE, cX, cY, cZ, f.spar);
+                    }
+                    if (Gh::UNI && !(prm.inject_stall && it == 0)) {  // inject: armed, never filled
+                        const uint32_t stb = bbase + s * Gh::BSTAGE;
+                        tc::tma_load_3d(stb, &prm.k_hi, fb, kc * Sh::KE, 0, f.oi);
+                        if (Sh::LO) tc::tma_load_3d(stb + Sh::BBYTES, &prm.k_lo, fb, kc * Sh::KE, 0, f.oi);
+                    }
+                }
+                if (box) continue;
+                const int64_t cb = (int64_t)kc * 128 + j * 16;
+#pragma unroll 4
+                for (int i = 0; i < 32 / Gh::PW; i++) {
+                    const int r = 4 * (pw + Gh::PW * i) + rsub;
+                    const int64_t src = (delta + rowA[r]) * prm.row_bytes + cb;
+                    const uint32_t d = st + r * 128 + ((j ^ (r & 7)) << 4);
+                    tc::cp_async16(d, prm.op_hi + src);
+                    if (Sh::LO) tc::cp_async16(d + TC_ABYTES, prm.op_lo + src);
+                }
+                tc::cp_async_commit();
+                cp_async_wait_pending<Gh::G - 1>();  // stages <= it - G + 1 have landed
+                if (it - Gh::G + 1 >= sig) {
+                    tc::fence_proxy_async_smem();
+                    for (; sig <= it - Gh::G + 1; sig++) tc::mbar_arrive(afull0 + 8 * (sig % Gh::SA));
+                }
+            }
+        }
+        if (!box) {
+            tc::cp_async_wait_all();  // no copy outlives the CTA
+            if (!failed) {
+                tc::fence_proxy_async_smem();
+                for (; sig < it; sig++) tc::mbar_arrive(afull0 + 8 * (sig % Gh::SA));
+            }
+        }
+        if (failed) {
+            if (lane == 0) atomicOr(prm.status, ST_TIMEOUT);
+            if (lead)  // the TMA copies already issued land before the CTA can exit
+                for (int s = 0; s < Gh::SA; s++)
+                    if (last_phase[s] >= 0) tc::mbar_wait(afull0 + 8 * s, (uint32_t)last_phase[s], TC_WAIT_CYCLES);
+        }
+    } else if (!Gh::UNI && warp == Gh::WB && lane == 0) {
+        // ---- kernel-matrix producer (split rings): K chunk kc of K_o by TMA ----
+        bool failed = false;
+        int last_phase[4] = {-1, -1, -1, -1};
+        int ox = -2 - bx - 1, oy = -2 - by, oz = -2 - bz, it = 0;
+        while (!failed && next_offset(bx, by, bz, ox, oy, oz)) {
+            const Off f = make_off(bx, by, bz, ox, oy, oz);
+            for (int kc = 0; kc < Sh::KC; kc++, it++) {
+                const int s = it % Gh::SB;
+                const uint32_t ph = (uint32_t)(it / Gh::SB) & 1u;
+                if (!tc::mbar_wait(bempty0 + 8 * s, ph ^ 1u, TC_WAIT_CYCLES)) {
+                    tc_wait_failed(prm.status, 1, l, it);
+                    failed = true;
+                    break;
+                }
+                const uint32_t st = bbase + s * Gh::BSTAGE;
+                const uint32_t fb = bfull0 + 8 * s;
+                tc::mbar_expect_tx(fb, Sh::LO ? 2 * Sh::BBYTES : Sh::BBYTES);
+                last_phase[s] = (int)ph;
+                if (prm.inject_stall && it == 0) continue;  // armed, never filled (test hook)
+                tc::tma_load_3d(st, &prm.k_hi, fb, kc * Sh::KE, 0, f.oi);
+                if (Sh::LO) tc::tma_load_3d(st + Sh::BBYTES, &prm.k_lo, fb, kc * Sh::KE, 0, f.oi);
+            }
+        }
+        if (failed) {
+            atomicOr(prm.status, ST_TIMEOUT);
+            // the copies already issued land before the CTA can exit
+            for (int s = 0; s < Gh::SB; s++)
+                if (last_phase[s] >= 0) tc::mbar_wait(bfull0 + 8 * s, (uint32_t)last_phase[s], TC_WAIT_CYCLES);
+        }
+    } else if (warp == Gh::WM && lane == 0) {
+        // ---- MMA issuer: offset i accumulates into TMEM region i & 1 ----
+        const uint32_t idesc = MODE == TC_BF16X3 ? tc::idesc_bf16(TC_M, N) : tc::idesc_tf32(TC_M, N);
+        bool failed = false;
+        for (int i = 0; i < TC_NOFF && !failed; i++) {
+            const int r = i & 1;
+            const uint32_t u = (uint32_t)(i >> 1) & 1u;
+            if (!tc::mbar_wait(rfree0 + 8 * r, u ^ 1u, TC_WAIT_CYCLES)) {
+                tc_wait_failed(prm.status, 2, l, i);
+                failed = true;
+                break;
+            }
+            const uint32_t d = tmem + (uint32_t)(r * N);
+            for (int kc = 0; kc < Sh::KC; kc++) {
+                const int it = Sh::KC * i + kc;
+                const int sa = it % Gh::SA, sb = it % Gh::SB;
+                if (!tc::mbar_wait(afull0 + 8 * sa, (uint32_t)(it / Gh::SA) & 1u, TC_WAIT_CYCLES) ||
+                    (!Gh::UNI && !tc::mbar_wait(bfull0 + 8 * sb, (uint32_t)(it / Gh::SB) & 1u, TC_WAIT_CYCLES))) {
+                    tc_wait_failed(prm.status, 3, l, it);
+                    failed = true;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t sta = abase + sa * Gh::ASTAGE, stb = bbase + sb * Gh::BSTAGE;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {  // 32 bytes of K per MMA (8 tf32 or 16 bf16)
+                    const uint64_t ah = tc::desc_sw128(sta + 32 * k);
+                    const uint64_t al = tc::desc_sw128(sta + TC_ABYTES + 32 * k);
+                    const uint64_t bh = tc::desc_sw128(stb + 32 * k);
+                    const uint64_t bl = tc::desc_sw128(stb + Sh::BBYTES + 32 * k);
+                    if (MODE == TC_BF16X3) {
+                        tc::mma_bf16(d, ah, bh, idesc, (kc | k) != 0);
+                        tc::mma_bf16(d, ah, bl, idesc, 1u);
+                        tc::mma_bf16(d, al, bh, idesc, 1u);
+                    } else {
+                        tc::mma_tf32(d, ah, bh, idesc, (kc | k) != 0);
+                        if (MODE == TC_TF32X3) {
+                            tc::mma_tf32(d, ah, bl, idesc, 1u);
+                            tc::mma_tf32(d, al, bh, idesc, 1u);
+                        }
+                    }
+                }
+                tc::mma_commit(aempty0 + 8 * sa);
+                if (!Gh::UNI) tc::mma_commit(bempty0 + 8 * sb);
+            }
+            if (!failed) tc::mma_commit(rfull0 + 8 * r);
+        }
+        if (failed) atomicOr(prm.status, ST_TIMEOUT);
+        tc::mma_commit(done);  // always: the deallocation waits on it
+    } else if (warp < Sh::EPI) {
+        // ---- epilogue: TMEM lane = row; columns [c0, c0 + COLS) ----
+        const int sub = warp & 3, cgrp = warp >> 2;
+        const int c0 = cgrp * Sh::COLS;
+        const int row = sub * 32 + lane;
+        const int lrow = rowL[row];
+        const bool valid = lrow >= 0;
+        const float *q = prm.qlev + prm.q_off[l] + rowQ[row];
+        const int64_t pp3 = (int64_t)P * P * P;
+        float tot[Sh::COLS];
+#pragma unroll
+        for (int j = 0; j < Sh::COLS; j++) tot[j] = 0.0f;
+        bool ok = true;
+        int ox = -2 - bx - 1, oy = -2 - by, oz = -2 - bz;
+        for (int i = 0; i < TC_NOFF; i++) {
+            next_offset(bx, by, bz, ox, oy, oz);
+            const Off f = make_off(bx, by, bz, ox, oy, oz);
+            const float Qs = valid ? q[f.spar * pp3 + ((int64_t)f.dZ * P + f.dY) * P + f.dX] : 0.0f;
+            const float4 *kb = reinterpret_cast<const float4 *>(prm.kbar + (int64_t)f.oi * N + c0);
+            const int r = i & 1;
+            const uint32_t u = (uint32_t)(i >> 1) & 1u;
+            if (ok && !tc::mbar_wait(rfull0 + 8 * r, u, TC_WAIT_CYCLES)) {
+                if (lane == 0) tc_wait_failed(prm.status, 4, l, i);
+                ok = false;
+            }
+            tc::fence_after_sync();
+            const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(r * N + c0);
+#pragma unroll
+            for (int c = 0; c < Sh::COLS / 16; c++) {
+                uint32_t v[16];
+                tc::tmem_ld16(taddr + c * 16, v);
+#pragma unroll
+                for (int j = 0; j < 16; j += 4) {
+                    const float4 m = kb[(c * 16 + j) >> 2];
+                    tot[c * 16 + j] += __uint_as_float(v[j]) + m.x * Qs;
+                    tot[c * 16 + j + 1] += __uint_as_float(v[j + 1]) + m.y * Qs;
+                    tot[c * 16 + j + 2] += __uint_as_float(v[j + 2]) + m.z * Qs;
+                    tot[c * 16 + j + 3] += __uint_as_float(v[j + 3]) + m.w * Qs;
+                }
+            }
+            tc::fence_before_sync();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rfree0 + 8 * r) : "memory");
+        }
+        const int p3 = prm.p3;
+        float *out = prm.loc + prm.loc_off[l] + (int64_t)(valid ? lrow : 0) * p3 + c0;
+        const float scale = (float)(1 << (l * prm.spow));
+        if (ok) {
+            if (valid) {
+#pragma unroll
+                for (int j = 0; j < Sh::COLS; j++)
+                    if (c0 + j < p3) out[j] = scale * tot[j];
+            }
+        } else if (lane == 0) {
+            atomicOr(prm.status, ST_TIMEOUT);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::mbar_wait(done, 0, TC_WAIT_CYCLES);
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, Sh::TCOLS);
+    }
+}
+
 // Levels lmin..lmax of the grid charges, remapped from the padded layout (P =
 // H + 2 per axis) into the operand layout (tc_level_extent per axis, zeros
 // outside) and split into hi / lo parts.  One element = one (cell, b) of the
@@ -483,6 +966,31 @@ static int launch_tc_mode(int p3s, const TcParams &prm, int blocks, cudaStream_t
     }
 }
 
+template <int N, int MODE>
+static int launch_tcg_kernel(const TcgParams &prm, int blocks, cudaStream_t st) {
+    typedef TcgShape<N, MODE> Gh;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_m2l_tcg<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Gh::SMEM) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        attr = true;
+    }
+    k_m2l_tcg<N, MODE><<<blocks, Gh::THREADS, Gh::SMEM, st>>>(prm);
+    return FMM_OK;
+}
+
+template <int MODE>
+static int launch_tcg_mode(int p3s, const TcgParams &prm, int blocks, cudaStream_t st) {
+    switch (p3s) {
+    case 32: return launch_tcg_kernel<32, MODE>(prm, blocks, st);
+    case 64: return launch_tcg_kernel<64, MODE>(prm, blocks, st);
+    case 128: return launch_tcg_kernel<128, MODE>(prm, blocks, st);
+    case 224: return launch_tcg_kernel<224, MODE>(prm, blocks, st);
+    default: return FMM_ERR_UNSUPPORTED;
+    }
+}
+
 int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
                   const void *k_lo_map, const float *kbar, int lmin, int mode, int inject,
                   float *loc, int spow, bool split, cudaStream_t st, Tracer &tr) {
@@ -508,6 +1016,65 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
             k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi, SL, P.phihi, P.philo, p3, p3s, mode == FMM_TC_TF32X1);
         tr.count();
     }
+#ifndef FMM_TC_DENSE
+    // the occupied cells of every (level, parity) segment, once per evaluation
+    OccParams op;
+    memset(&op, 0, sizeof(op));
+    op.leaf_start = P.leaf_start;
+    op.occ = P.occ;
+    op.depth = depth;
+    op.lmin = lmin;
+    op.nseg = occ_nseg(depth, lmin);
+    int nb = 0, blocks = 0;
+    for (int s = 0; s < op.nseg; s++) {
+        op.bfirst[s] = nb;
+        nb += (int)((occ_seg_cells(lmin, s) + OCC_BLOCK - 1) / OCC_BLOCK);
+        blocks += (int)((occ_seg_cells(lmin, s) + TC_M - 1) / TC_M);  // tiles if every cell holds charges
+    }
+    op.bfirst[op.nseg] = nb;
+    op.nblk = nb;
+    if (split) {
+        k_occ_count<<<nb, OCC_BLOCK / 4, 0, st>>>(op);
+        k_occ_offsets<<<(op.nseg + 7) / 8, 256, 0, st>>>(op);
+        k_occ_scatter<<<nb, OCC_BLOCK / 4, 0, st>>>(op);
+        tr.count(3);
+    }
+    TcgParams prm;
+    memset(&prm, 0, sizeof(prm));
+    memcpy(&prm.k_hi, k_hi_map, sizeof(CUtensorMap));
+    memcpy(&prm.k_lo, k_lo_map, sizeof(CUtensorMap));
+    const size_t es = bf16 ? 2 : 4;
+    prm.op_hi = reinterpret_cast<const char *>(P.phihi);
+    prm.op_lo = reinterpret_cast<const char *>(P.philo);
+    prm.row_bytes = (int)((bf16 ? pk : p3s) * es);
+    prm.lmin = lmin;
+    prm.depth = depth;
+    prm.p3 = p3;
+    prm.spow = spow;
+    prm.nseg = op.nseg;
+    prm.occ = P.occ;
+    for (int l = 0; l <= depth + 1; l++) prm.op_cell0[l] = tc_level_first(l);
+    for (int l = lmin; l <= depth; l++) {
+        prm.loc_off[l] = W.loc_level[l];
+        prm.q_off[l] = W.q_level[l];
+        {  // box maps of the operand layout
+            const int64_t cl = tc_level_first(l);
+            const void *bh = bf16 ? (const void *)(hi16 + cl * pk) : (const void *)(P.phihi + cl * p3s);
+            const void *bl = bf16 ? (const void *)(lo16 + cl * pk) : (const void *)(P.philo + cl * p3s);
+            int rc = encode_phi_map(&prm.phi_hi[l], bh, l, pk, bf16);
+            if (!rc) rc = encode_phi_map(&prm.phi_lo[l], bl, l, pk, bf16);
+            if (rc) return rc;
+        }
+    }
+    prm.loc = loc;
+    prm.qlev = P.qlev;
+    prm.kbar = kbar;
+    prm.status = &P.hdr->status;
+    prm.inject_stall = inject == FMM_INJECT_TC_STALL;
+    int rc = mode == FMM_TC_BF16X3   ? launch_tcg_mode<TC_BF16X3>(p3s, prm, blocks, st)
+             : mode == FMM_TC_TF32X1 ? launch_tcg_mode<TC_TF32X1>(p3s, prm, blocks, st)
+                                     : launch_tcg_mode<TC_TF32X3>(p3s, prm, blocks, st);
+#else
     TcParams prm;
     memset(&prm, 0, sizeof(prm));
     int blocks = 0;
@@ -539,6 +1106,7 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
     int rc = mode == FMM_TC_BF16X3   ? launch_tc_mode<TC_BF16X3>(p3s, prm, blocks, st)
              : mode == FMM_TC_TF32X1 ? launch_tc_mode<TC_TF32X1>(p3s, prm, blocks, st)
                                      : launch_tc_mode<TC_TF32X3>(p3s, prm, blocks, st);
+#endif
     tr.count();
     tr.end();
     return rc;
