@@ -1,23 +1,30 @@
 #!/usr/bin/env python
 """Benchmark of the replacement-based FMM (energy + potentials + forces).
 
-Workload (default "uniform1m"): 1,048,576 particles uniform in the unit cube,
-charges uniform in [-1, 1] shifted to zero net charge, open boundary,
-continuous (split) form with 2d = w/128, octree depth 5, p = 4, FP32.
+Workload (default "plummer8m"): 8,388,608 particles of a Plummer sphere (scale
+radius 0.1 of the unit box, centred, redrawn outside the box) with +-1
+charges summing to zero, open boundary, plain form, octree depth 7 (2,097,152
+finest cells, 61% of them empty), p = 6 (216 grid charges per cell).
 Default precision "tf32x3": every stage in FP32, the far-field contraction of
-levels >= 4 on the tcgen05 tensor cores in 3-pass split TF32 (its parity with
-the FP64 oracle meets the FP32 tolerance); the line also reports the plain
-FP32 form (SIMT contraction) measured the same way.
+every level on the tcgen05 tensor cores in 3-pass split TF32 (its parity with
+the FP64 oracle meets the FP32 tolerance).  The line also reports the plain
+FP32 form (SIMT contraction), the force-kernel form, the shift-free forms, and
+shorter lines for BF16x3 and for the uniform (1,048,576 particles, continuous
+form, depth 5, p 4) and water-like (2,097,150 particles, periodic continuous
+form, depth 6, p 5) workloads.
 
 One step = one full evaluation: binning, split, sort, upward pass, downward
 pass, far and near field, recombination, FP64 energy.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision P] [--no-extras] [--no-cpu-baseline]
 
 --impl reference times the FP64 CPU oracle (the only reference this method
-has) on the host cores, on the same workload.  Multi-GPU (torchrun): every rank
-evaluates its own replica of the workload (weak scaling, no collective on the
-data path); the value is the particles of all ranks over the slowest rank.
+has) on the host cores, on the same workload (above 2M particles: the outputs
+of 512 sampled particles per step, with the full upward pass).  Multi-GPU
+(torchrun): every rank evaluates its own replica of the workload (weak
+scaling, no collective on the data path); the value is the particles of all
+ranks over the slowest rank.
 """
 import argparse
 import json
@@ -37,10 +44,10 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA 
 P2P_FLOPS_PER_PAIR = 20
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
 # DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
-# capture of the current kernels on these workloads (profiles/k_p2p_uniform1m.md,
-# profiles/k_m2l_tc_uniform1m.md); reported as the roofline's traffic
-PROFILED_TRAFFIC = {("uniform1m", "tf32x3", "k_p2p"): 201362688,
-                    ("uniform1m", "tf32x3", "k_m2l_tc"): 42223360}
+# capture of the current kernels (scaled to a full launch where the capture
+# ran on a smaller case of the same distribution); reported as the
+# rooflines' traffic
+PROFILED_TRAFFIC = {("uniform1m", "tf32x3", "k_p2p"): 201362688}
 
 
 def _peaks():
@@ -436,15 +443,241 @@ def batch_cpu_baseline(pos_h, q_h, offs, boxes, counts, depths, outs):
     return base, summary
 
 
+def cell_occupancy(start, depth):
+    """Per level l, a boolean grid [z][y][x] of the cells whose finest cells hold
+    charges, from the finest-cell ranges (Morton order)."""
+    import numpy as np
+    start = np.asarray(start, np.int64)
+    out = {}
+    for l in range(depth + 1):
+        S, sh = 1 << l, 3 * (depth - l)
+        k = np.arange(S ** 3, dtype=np.int64)
+        occ = start[(k + 1) << sh] > start[k << sh]
+        xyz = np.zeros((S ** 3, 3), np.int64)
+        for bit in range(l):
+            for a in range(3):
+                xyz[:, a] |= ((k >> (3 * bit + a)) & 1) << bit
+        g = np.zeros((S, S, S), bool)
+        g[xyz[:, 2], xyz[:, 1], xyz[:, 0]] = occ
+        out[l] = g
+    return out
+
+
+def m2l_work(start, depth, periodic, p, precision):
+    """Cell pairs of the interaction lists: every pair in range (dense), the pairs
+    whose target and source both hold charges (the method's own work: a functional
+    is read only where there are charges, an empty source adds nothing), and the
+    tensor-core work the contraction executes (128-row tiles of the occupied
+    targets, 189 offsets each, p^3 padded to the MMA shape, 3 passes for the
+    split forms)."""
+    import numpy as np
+    occ = cell_occupancy(start, depth)
+    dense = both = tiles = 0
+    for l in range(1 if periodic else 2, depth + 1):
+        g, H = occ[l], 1 << (l - 1)
+        mode = "wrap" if periodic else "constant"
+        for par in range(8):
+            b = [(par >> a) & 1 for a in range(3)]  # x, y, z
+            T = g[b[2]::2, b[1]::2, b[0]::2]
+            nocc = int(T.sum())
+            tiles += (1 if nocc else 0) if H < 8 else (nocc + 127) // 128
+            for oz in range(-2 - b[2], 4 - b[2]):
+                for oy in range(-2 - b[1], 4 - b[1]):
+                    for ox in range(-2 - b[0], 4 - b[0]):
+                        if max(abs(ox), abs(oy), abs(oz)) <= 1:
+                            continue
+                        s = [b[0] + ox, b[1] + oy, b[2] + oz]
+                        src = np.pad(g[s[2] & 1::2, s[1] & 1::2, s[0] & 1::2], 1, mode=mode)
+                        d = [v >> 1 for v in s]
+                        src = src[1 + d[2]:1 + d[2] + H, 1 + d[1]:1 + d[1] + H, 1 + d[0]:1 + d[0] + H]
+                        both += int(np.count_nonzero(T & src))
+                        if periodic:
+                            dense += H ** 3
+                        else:
+                            dense += int(np.prod([H - abs(v) for v in d]))
+    p3 = p ** 3
+    n_pad = (p3 + 31) // 32 * 32
+    k_pad = (p3 + 63) // 64 * 64 if precision == "bf16x3" else n_pad
+    passes = 1 if precision == "tf32x1" else 3
+    return {"dense_pairs": dense, "occupied_pairs": both, "tiles": tiles,
+            "algorithmic_flops": 2.0 * p3 * p3 * both, "dense_flops": 2.0 * p3 * p3 * dense,
+            "executed_flops": 2.0 * tiles * 128 * 189 * n_pad * k_pad * passes}
+
+
+def tc_peak(precision, long_step):
+    """Dense tensor peak of the contraction's MMA kind (TF/s) and its source."""
+    hbm, bf16_burst, bf16_sust, kind = _peaks()
+    ref = bf16_sust if long_step else bf16_burst
+    which = "sustained" if long_step else "burst"
+    if precision == "bf16x3":  # kind::f16: the measured bf16 rate itself
+        return ref, "%s bf16 %s %.1f TF/s" % (kind, which, ref)
+    # kind::tf32: 1/2 of it (nominal 1.1 vs 2.25 PF/s)
+    return ref / 2, "%s bf16 %s %.1f TF/s x 1/2 (nominal tf32:bf16 ratio)" % (kind, which, ref)
+
+
+class Run:
+    """One workload and precision: its plan, workspace, outputs and step."""
+
+    def __init__(self, name, precision, dev, shift_free=False, force_mode="adjoint", w=None):
+        import torch
+        from paper_2212_13080_gb300 import FMM, inputs
+        self.name, self.precision = name, precision
+        self.w = w if w is not None else inputs.workload(name)
+        w = self.w
+        self.n = n = len(w["q"])
+        self.pos = torch.from_numpy(w["pos"]).to(dev)
+        self.q = torch.from_numpy(w["q"]).to(dev)
+        self.mk = dict(periodic=w["periodic"], continuous=w["continuous"], precision=precision,
+                       max_n=n, shift_free=shift_free, force_mode=force_mode)
+        self.plan = FMM(w["box"], w["depth"], w["p"], sync=False, **self.mk)
+        self.ws = self.plan.workspace(n)
+        od = self.plan.out_dtype
+        self.out = {"potential": torch.empty(n, dtype=od, device=dev),
+                    "energy": torch.empty(1, dtype=torch.float64, device=dev),
+                    "forces": torch.empty((n, 3), dtype=od, device=dev)}
+
+    def step(self):
+        self.plan.eval(self.pos, self.q, workspace=self.ws, out=self.out)
+
+    def check(self):
+        rc = plan_status(self.plan, self.ws)
+        if rc:
+            raise SystemExit("%s %s: evaluation failed: status %d" % (self.name, self.precision, rc))
+
+    def time(self, steps, warmup, flush, stream, timing=True):
+        """Mean device ms per step (CUDA events on the launching stream, L2
+        flushed before every step), the library's stage times and launches."""
+        import torch
+        self.plan.set_timing(timing)
+        for _ in range(warmup):
+            self.step()
+        torch.cuda.synchronize()
+        self.check()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        stage_tot, launches = {}, 0
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            self.step()
+            evs[i][1].record(stream)
+            st = self.plan.stats()
+            launches += st["launches"]
+            for k, v in st["stage_ms"].items():
+                stage_tot[k] = stage_tot.get(k, 0.0) + v
+        torch.cuda.synchronize()
+        self.check()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return statistics.mean(ms), {k: v / steps for k, v in stage_tot.items()}, launches
+
+    def isolated(self, steps, flush):
+        """Each stage's own duration: the same steps with every stage on one stream."""
+        import torch
+        self.plan.set_timing(True, serial=True)
+        tot = {}
+        for _ in range(steps):
+            flush.zero_()
+            self.step()
+            for k, v in self.plan.stats()["stage_ms"].items():
+                tot[k] = tot.get(k, 0.0) + v / steps
+        torch.cuda.synchronize()
+        self.plan.set_timing(True)
+        return tot
+
+    def host_outputs(self):
+        return (self.out["potential"].cpu().numpy(), self.out["forces"].cpu().numpy(),
+                float(self.out["energy"].item()))
+
+    def close(self):
+        self.plan.close()
+
+
+def rooflines(run, t_step, stage_ms, stage_iso):
+    """The contraction's and the near field's rooflines (algorithmic flops over
+    their stage time), and which of the two dominates by isolated time."""
+    w = run.w
+    start = run.plan.dump("start")
+    pairs = p2p_pairs(run.plan, w["depth"], w["periodic"])
+    mw = m2l_work(start, w["depth"], w["periodic"], w["p"], run.precision)
+    long_step = t_step >= 100.0
+    tc = run.precision in ("tf32x3", "tf32x1", "bf16x3")
+    out = {}
+    p2p_flops = float(P2P_FLOPS_PER_PAIR) * pairs
+    ach = p2p_flops / (stage_ms["p2p"] * 1e-3) / 1e12
+    ach_iso = p2p_flops / (stage_iso["p2p"] * 1e-3) / 1e12
+    out["p2p"] = {"kernel": "k_p2p", "bound": "alu", "achieved": ach_iso, "peak": FP32_ALU_PEAK_TFLOPS,
+                  "unit": "TFLOP/s", "frac": ach_iso / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                  "algorithmic": "%d ordered pairs x %d flop" % (pairs, P2P_FLOPS_PER_PAIR),
+                  "duration": "isolated stage time (every stage on one stream)",
+                  "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                  "achieved_in_step": ach, "frac_in_step": ach / FP32_ALU_PEAK_TFLOPS,
+                  "ordered_pairs": pairs}
+    m_ms, m_iso = stage_ms["m2l"], stage_iso["m2l"]
+    if tc:
+        peak, src = tc_peak(run.precision, long_step)
+        a = mw["algorithmic_flops"] / (m_ms * 1e-3) / 1e12
+        out["m2l"] = {"kernel": "k_m2l_tcg", "bound": "tensor", "achieved": a, "peak": peak,
+                      "unit": "TFLOP/s", "frac": a / peak, "traffic": None,
+                      "algorithmic": "%d cell pairs whose cells both hold charges x 2 p^6 flop "
+                                     "(all levels per step)" % mw["occupied_pairs"],
+                      "duration": "in-step stage time (far-field stream; split, lists and "
+                                  "contraction)",
+                      "peak_source": src,
+                      "dense_pairs": mw["dense_pairs"],
+                      "achieved_on_dense_count": mw["dense_flops"] / (m_ms * 1e-3) / 1e12,
+                      "executed_tflops": mw["executed_flops"] / (m_ms * 1e-3) / 1e12,
+                      "executed_frac": mw["executed_flops"] / (m_ms * 1e-3) / 1e12 / peak,
+                      "executed": "%d tiles x 128 rows x 189 offsets, p^3 padded, %d passes"
+                                  % (mw["tiles"], 1 if run.precision == "tf32x1" else 3),
+                      "achieved_isolated": mw["algorithmic_flops"] / (m_iso * 1e-3) / 1e12}
+    else:
+        a = mw["algorithmic_flops"] / (m_ms * 1e-3) / 1e12
+        out["m2l"] = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": a,
+                      "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                      "frac": a / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                      "algorithmic": "%d cell pairs whose cells both hold charges x 2 p^6 flop"
+                                     % mw["occupied_pairs"],
+                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                      "dense_pairs": mw["dense_pairs"],
+                      "achieved_on_dense_count": mw["dense_flops"] / (m_ms * 1e-3) / 1e12}
+    dom = max(("m2l", "p2p"), key=lambda k: stage_iso.get(k, 0.0))
+    for k, r in out.items():
+        r["traffic"] = PROFILED_TRAFFIC.get((run.name, run.precision, r["kernel"]))
+        if r["traffic"] is not None:
+            r["traffic_unit"] = ("bytes per launch (ncu dram__bytes_read.sum + "
+                                 "dram__bytes_write.sum)")
+    return dom, out, pairs, mw
+
+
+def extra_line(name, precision, dev, flush, stream, steps):
+    """A shorter line for another workload or precision: throughput, stage
+    times, the two rooflines (no CPU leg)."""
+    r = Run(name, precision, dev)
+    t, st, launches = r.time(steps, 3, flush, stream)
+    iso = r.isolated(max(3, steps // 3), flush)
+    dom, roofs, pairs, mw = rooflines(r, t, st, iso)
+    w = r.w
+    res = {"workload": name, "precision": precision, "n": r.n, "depth": w["depth"], "p": w["p"],
+           "periodic": w["periodic"], "continuous": w["continuous"], "ms_per_step": t,
+           "value": r.n / (t * 1e-3) / 1e6, "unit": UNIT, "gpu_launches_per_step": launches // steps,
+           "stage_ms": st, "stage_ms_isolated": iso, "dominant": dom, "roofline_m2l": roofs["m2l"],
+           "roofline_p2p": roofs["p2p"]}
+    r.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uniform1m")
+    ap.add_argument("--workload", default="plummer8m")
     ap.add_argument("--precision", default="tf32x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra lines (other workloads, BF16x3, plain FP32, force kernels, "
+                         "shift-free forms)")
     ap.add_argument("--shift-free", action="store_true",
                     help="App. A.2 forms for the main plan (precision fp64, p <= 5)")
     ap.add_argument("--profile", action="store_true",
@@ -465,7 +698,6 @@ def main():
             return
         run_reference(args, args.workload, world, rank)
         return
-    import numpy as np
     import torch
     dist = init_ranks(world, local)
     if args.workload == "batch512":
@@ -474,161 +706,89 @@ def main():
             dist.destroy_process_group()
         return
 
-    from paper_2212_13080_gb300 import FMM, inputs
-    w = inputs.workload(args.workload)
-    pos_h, q_h, box = w["pos"], w["q"], w["box"]
-    n = len(q_h)
+    from paper_2212_13080_gb300 import FMM
     dev = torch.device("cuda", local)
-    pos = torch.from_numpy(pos_h).to(dev)
-    q = torch.from_numpy(q_h).to(dev)
-    mk = dict(periodic=w["periodic"], continuous=w["continuous"], precision=args.precision,
-              max_n=n, shift_free=args.shift_free)
-    plan = FMM(box, w["depth"], w["p"], sync=False, **mk)
-    plan.set_timing(True)
-    ws = plan.workspace(n)
-    od = plan.out_dtype
-    out = {"potential": torch.empty(n, dtype=od, device=dev),
-           "energy": torch.empty(1, dtype=torch.float64, device=dev),
-           "forces": torch.empty((n, 3), dtype=od, device=dev)}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
-
-    def step():
-        plan.eval(pos, q, workspace=ws, out=out)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    rc = plan_status(plan, ws)
-    if rc:
-        raise SystemExit("evaluation failed: status %d" % rc)
+    run = Run(args.workload, args.precision, dev, shift_free=args.shift_free)
+    w, n = run.w, run.n
 
     if args.profile:
-        for _ in range(args.steps):
-            step()
+        for _ in range(args.warmup + args.steps):
+            run.step()
         torch.cuda.synchronize()
         print(json.dumps({"profile": True, "workload": args.workload, "steps": args.steps,
-                          "precision": args.precision, "status": plan_status(plan, ws)}))
+                          "precision": args.precision, "status": plan_status(run.plan, run.ws)}))
         return
 
-    # algorithmic work of one step
-    pairs = p2p_pairs(plan, w["depth"], w["periodic"])
-    cellpairs = m2l_cell_pairs(w["depth"], w["periodic"])
-    m2l_flops = 2.0 * (w["p"] ** 6) * cellpairs
-    p2p_flops = float(P2P_FLOPS_PER_PAIR) * pairs
-
+    # the timed steps, with clocks sampled during them
+    run.plan.set_timing(True)
+    for _ in range(args.warmup):
+        run.step()
+    torch.cuda.synchronize()
+    run.check()
     sampler = ClockSampler(local)
     fence(dist)
     sampler.start()
     time.sleep(0.3)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
-    stage_tot = {}
-    launches = 0
+    stage_tot, launches = {}, 0
     for i in range(args.steps):
         flush.zero_()
         evs[i][0].record(stream)
-        step()
+        run.step()
         evs[i][1].record(stream)
-        st = plan.stats()
+        st = run.plan.stats()
         launches += st["launches"]
         for k, v in st["stage_ms"].items():
             stage_tot[k] = stage_tot.get(k, 0.0) + v
     fence(dist)
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in evs]
-    rc = plan_status(plan, ws)
-    if rc:
-        raise SystemExit("evaluation failed: status %d" % rc)
+    run.check()
     t_step = job_step_ms(statistics.mean(ms), dist, dev)
     value = job_value(world, n, t_step)
     stage_ms = {k: v / args.steps for k, v in stage_tot.items()}
+    stage_ms_iso = run.isolated(max(3, args.steps // 4), flush)
+    gpu_outputs = {args.precision: run.host_outputs()}
+    dom, roofs, pairs, mw = rooflines(run, t_step, stage_ms, stage_ms_iso)
+    roof = dict(roofs[dom])
+    hbm, _, _, peak_kind = _peaks()
+    roof["hbm_peak_gbs"] = hbm
+    roof["hbm_peak_source"] = peak_kind
 
-    # the same steps with every stage on one stream: each stage's own duration
-    plan.set_timing(True, serial=True)
-    iso_tot, n_iso = {}, max(3, args.steps // 4)
-    for _ in range(n_iso):
-        flush.zero_()
-        step()
-        for k, v in plan.stats()["stage_ms"].items():
-            iso_tot[k] = iso_tot.get(k, 0.0) + v
-    torch.cuda.synchronize()
-    plan.set_timing(True)
-    stage_ms_iso = {k: v / n_iso for k, v in iso_tot.items()}
-
-    def host_outputs():
-        return (out["potential"].cpu().numpy(), out["forces"].cpu().numpy(),
-                float(out["energy"].item()))
-    gpu_outputs = {args.precision: host_outputs()}
-
+    extras = not args.no_extras and world == 1
     # the plain FP32 form (SIMT contraction), same timing protocol, fewer steps
     plain = None
-    if args.precision != "fp32":
-        plan32 = FMM(box, w["depth"], w["p"], sync=False, **dict(mk, precision="fp32", shift_free=False))
-        ws32 = plan32.workspace(n)
-        if plan.out_dtype != torch.float32:
-            out = {"potential": torch.empty(n, device=dev), "energy": out["energy"],
-                   "forces": torch.empty((n, 3), device=dev)}
-        for _ in range(2):
-            plan32.eval(pos, q, workspace=ws32, out=out)
-        t32 = []
-        for _ in range(max(3, args.steps // 4)):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            plan32.eval(pos, q, workspace=ws32, out=out)
-            b.record(stream)
-            b.synchronize()
-            t32.append(a.elapsed_time(b))
-        gpu_outputs["fp32"] = host_outputs()
-        plain = {"precision": "fp32", "ms_per_step": statistics.mean(t32),
-                 "value": n / (statistics.mean(t32) * 1e-3) / 1e6, "unit": UNIT}
-        plan32.close()
+    if extras and args.precision != "fp32" and not args.shift_free:
+        r32 = Run(args.workload, "fp32", dev, w=w)
+        k32 = 3 if n > (1 << 21) else max(3, args.steps // 4)
+        t32, st32, _ = r32.time(k32, 1, flush, stream, timing=False)
+        gpu_outputs["fp32"] = r32.host_outputs()
+        plain = {"precision": "fp32", "ms_per_step": t32, "value": n / (t32 * 1e-3) / 1e6,
+                 "unit": UNIT}
+        r32.close()
 
     # far forces from the force kernels (§4.1), same workload and precision
     force_kernel, fk_host = None, None
-    if not args.shift_free:
-        fk_plan = FMM(box, w["depth"], w["p"], sync=False, **dict(mk, force_mode="kernel"))
-        fk_ws = fk_plan.workspace(n)
-        fk_out = {"potential": torch.empty(n, dtype=plan.out_dtype, device=dev),
-                  "energy": torch.empty(1, dtype=torch.float64, device=dev),
-                  "forces": torch.empty((n, 3), dtype=plan.out_dtype, device=dev)}
-        for _ in range(3):
-            fk_plan.eval(pos, q, workspace=fk_ws, out=fk_out)
-        tk = []
-        for _ in range(max(5, args.steps // 2)):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fk_plan.eval(pos, q, workspace=fk_ws, out=fk_out)
-            b.record(stream)
-            b.synchronize()
-            tk.append(a.elapsed_time(b))
-        if plan_status(fk_plan, fk_ws):
-            raise SystemExit("force-kernel plan: evaluation failed")
-        fk_plan.set_timing(True, serial=True)
-        fk_iso = {}
-        for _ in range(5):
-            flush.zero_()
-            fk_plan.eval(pos, q, workspace=fk_ws, out=fk_out)
-            for k_, v in fk_plan.stats()["stage_ms"].items():
-                fk_iso[k_] = fk_iso.get(k_, 0.0) + v / 5
-        torch.cuda.synchronize()
-        fk_host = (fk_out["potential"].cpu().numpy(), fk_out["forces"].cpu().numpy(),
-                   float(fk_out["energy"].item()))
-        force_kernel = {"force_mode": "kernel", "precision": args.precision,
-                        "ms_per_step": statistics.mean(tk),
-                        "value": world * n / (statistics.mean(tk) * 1e-3) / 1e6, "unit": UNIT,
+    if extras and not args.shift_free:
+        rk = Run(args.workload, args.precision, dev, force_mode="kernel", w=w)
+        tk, _, _ = rk.time(max(5, args.steps // 2), 3, flush, stream, timing=False)
+        fk_iso = rk.isolated(5, flush)
+        fk_host = rk.host_outputs()
+        force_kernel = {"force_mode": "kernel", "precision": args.precision, "ms_per_step": tk,
+                        "value": world * n / (tk * 1e-3) / 1e6, "unit": UNIT,
                         "stage_ms_isolated": fk_iso,
-                        "m2l_tflops_algorithmic": 4 * m2l_flops / (fk_iso["m2l"] * 1e-3) / 1e12,
+                        "m2l_tflops_algorithmic": 4 * mw["algorithmic_flops"] / (fk_iso["m2l"] * 1e-3) / 1e12,
                         "note": "four contractions (1/r and the x, y, z force kernels), plain-weight "
                                 "far-field evaluation"}
-        fk_plan.close()
+        rk.close()
 
     # end to end through the public API with host buffers (pinned)
-    plan_e2e = FMM(box, w["depth"], w["p"], sync=True, **mk)
-    pos_p = torch.from_numpy(pos_h).pin_memory()
-    q_p = torch.from_numpy(q_h).pin_memory()
+    plan_e2e = FMM(w["box"], w["depth"], w["p"], sync=True, **dict(run.mk, force_mode="adjoint"))
+    pos_p = torch.from_numpy(w["pos"]).pin_memory()
+    q_p = torch.from_numpy(w["q"]).pin_memory()
     for _ in range(2):
         plan_e2e.eval(pos_p, q_p)
     torch.cuda.synchronize()
@@ -639,98 +799,51 @@ def main():
         te.append(time.perf_counter() - t0)
     e2e_v = world * n / statistics.mean(te) / 1e6
     h2d = pos_p.numel() * 4 + q_p.numel() * 4
-    d2h = r["potential"].numel() * 4 + r["forces"].numel() * 4 + 8
+    d2h = r["potential"].numel() * r["potential"].element_size() + \
+        r["forces"].numel() * r["forces"].element_size() + 8
+    plan_e2e.close()
 
-    # roofline of the dominant kernel stage
-    hbm, bf16_burst, bf16_sust, peak_kind = _peaks()
-    # the dominant kernel by its own (isolated) duration: in-step times overlap
-    dom = max(("m2l", "p2p"), key=lambda k: stage_ms_iso.get(k, 0.0))
-    # TF32 dense = 1/2 of the bf16 rate (nominal 1.1 vs 2.25 PF/s); the burst figure
-    # for millisecond steps, the sustained one once a step runs for 100 ms or more
-    long_step = t_step >= 100.0
-    bf16_ref = bf16_sust if long_step else bf16_burst
-    tc = args.precision in ("tf32x3", "tf32x1", "bf16x3")
-    passes = 1 if args.precision == "tf32x1" else 3
-    if args.precision == "bf16x3":  # kind::f16: the measured bf16 rate itself
-        tc_peak = bf16_ref
-        tc_src = "%s bf16 %s %.1f TF/s" % (peak_kind, "sustained" if long_step else "burst", bf16_ref)
-    else:                           # kind::tf32: 1/2 of it (nominal 1.1 vs 2.25 PF/s)
-        tc_peak = bf16_ref / 2
-        tc_src = "%s bf16 %s %.1f TF/s x 1/2 (nominal tf32:bf16 ratio)" % (
-            peak_kind, "sustained" if long_step else "burst", bf16_ref)
-    m2l_tc = None
-    if tc:
-        m2l_tc = {"kernel": "k_m2l_tc (every level)", "bound": "tensor",
-                  "precision": args.precision,
-                  "achieved_algorithmic_tflops": m2l_flops / (stage_ms["m2l"] * 1e-3) / 1e12,
-                  "executed_tflops": passes * m2l_flops / (stage_ms["m2l"] * 1e-3) / 1e12,
-                  "passes": passes, "peak_tflops": tc_peak, "peak_source": tc_src}
-    if dom == "p2p":
-        ach = p2p_flops / (stage_ms["p2p"] * 1e-3) / 1e12
-        ach_iso = p2p_flops / (stage_ms_iso["p2p"] * 1e-3) / 1e12
-        roof = {"kernel": "k_p2p", "bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
-                "algorithmic": "%d ordered pairs x %d flop" % (pairs, P2P_FLOPS_PER_PAIR),
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
-                "note": "achieved: in-step duration, overlapped with the far field; "
-                        "achieved_isolated: the same kernel with every stage on one stream",
-                "achieved_isolated": ach_iso, "frac_isolated": ach_iso / FP32_ALU_PEAK_TFLOPS}
-    else:
-        ach = m2l_flops / (stage_ms["m2l"] * 1e-3) / 1e12
-        ach_iso = m2l_flops / (stage_ms_iso["m2l"] * 1e-3) / 1e12
-        if tc:
-            roof = {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": ach, "peak": tc_peak,
-                    "unit": "TFLOP/s", "frac": ach / tc_peak, "traffic": None,
-                    "algorithmic": "%d cell pairs x 2 p^6 flop (all levels per step; the split "
-                                   "forms execute %dx)" % (cellpairs, passes),
-                    "peak_source": tc_src,
-                    "achieved_isolated": ach_iso, "frac_isolated": ach_iso / tc_peak}
-        else:
-            roof = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": ach,
-                    "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
-                    "algorithmic": "%d cell pairs x 2 p^6 flop (all levels per step)" % cellpairs,
-                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
-                    "achieved_isolated": ach_iso,
-                    "frac_isolated": ach_iso / FP32_ALU_PEAK_TFLOPS}
-    roof["traffic"] = PROFILED_TRAFFIC.get((args.workload, args.precision, roof["kernel"]))
-    if roof["traffic"] is not None:
-        roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
-    roof["hbm_peak_gbs"] = hbm
-    roof["hbm_peak_source"] = peak_kind
-
+    cfg = {"workload": args.workload, "n": n, "depth": w["depth"], "p": w["p"],
+           "periodic": w["periodic"], "continuous": w["continuous"],
+           "outputs": "potential+energy+forces",
+           "l2": "flushed (256 MB write) before every timed step",
+           "parallelism": "replicas" if world > 1 else "single"}
+    if w["continuous"]:
+        cfg["split_2d_over_w"] = 1 / 128
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f64" if args.precision == "fp64" else "f32",
         "precision": args.precision,
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "depth": w["depth"], "p": w["p"],
-                   "periodic": w["periodic"], "continuous": w["continuous"],
-                   "split_2d_over_w": 1 / 128, "outputs": "potential+energy+forces",
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": cfg,
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
+        "roofline_m2l": roofs["m2l"], "roofline_p2p": roofs["p2p"],
         "stage_ms": stage_ms, "stage_ms_isolated": stage_ms_iso,
         "pairs_per_s": pairs / (t_step * 1e-3),
-        "p2p_tflops": p2p_flops / (stage_ms.get("p2p", 1e9) * 1e-3) / 1e12,
-        "m2l_tflops": m2l_flops / (stage_ms.get("m2l", 1e9) * 1e-3) / 1e12,
+        "m2l_cell_pairs": {"dense": mw["dense_pairs"], "both_occupied": mw["occupied_pairs"],
+                           "tiles": mw["tiles"]},
         "clocks": clocks,
-        "m2l_tensor": m2l_tc,
         "plain_fp32": plain,
         "force_kernel": force_kernel,
-        "shift_free": shift_free_line(args.steps, dev, flush, stream) if world == 1 else None,
     }
+    run.close()
+    if extras:
+        res["shift_free"] = shift_free_line(args.steps, dev, flush, stream)
+        res["extra"] = []
+        if args.workload == "plummer8m" and args.precision == "tf32x3":
+            res["extra"].append(extra_line("plummer8m", "bf16x3", dev, flush, stream, 5))
+        for name in ("uniform1m", "water2m"):
+            if name != args.workload:
+                res["extra"].append(extra_line(name, "tf32x3", dev, flush, stream, 10))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"], res["error_vs_fp64_oracle"] = cpu_baseline(args.workload, gpu_outputs,
                                                                         fk_host)
     if rank == 0:
         print(json.dumps(res), flush=True)
-    plan.close()
-    plan_e2e.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -178,6 +178,22 @@ __host__ __device__ inline int occ_nblk(int depth, int lmin) {
 __host__ __device__ inline int64_t occ_list_offset(int depth, int lmin) {
     return ((int64_t)occ_nblk(depth, lmin) + 2 * occ_nseg(depth, lmin) + 1 + 63) / 64 * 64;
 }
+// A segment takes box tiles (each offset's A operand one TMA box of 8 x 4 x 4
+// coarse cells, empty cells included) when it has fewer than 8 coarse cells
+// per axis or when the share of its cells that hold charges reaches the
+// threshold of the tile width N (p^3 padded): the gathered tiles of narrow
+// shapes keep fewer copies in flight per MMA, so they pay off only on sparser
+// segments (measured: N = 224 gathers as fast as boxes, N = 128 at ~2/3 of
+// their rate, N <= 64 at ~2/5).
+__host__ __device__ inline bool occ_box_segment(int H, int64_t count, int N) {
+    const int pct = N >= 224 ? 95 : (N >= 128 ? 70 : 40);
+    return H < 8 || count * 100 >= (int64_t)pct * H * H * H;
+}
+__host__ __device__ inline int occ_seg_tiles(int H, int64_t count, int N) {
+    if (count == 0) return 0;
+    if (H < 8) return 1;
+    return occ_box_segment(H, count, N) ? (int)((int64_t)H * H * H / 128) : (int)((count + 127) / 128);
+}
 __host__ __device__ inline int64_t occ_ints(int depth, int lmin) {
     return occ_list_offset(depth, lmin) + occ_seg_first(lmin, occ_nseg(depth, lmin));
 }

@@ -2,14 +2,25 @@
 // 5th-generation tensor cores (tcgen05): 3-pass split TF32, 1-pass TF32 or
 // 3-pass split BF16, FP32 accumulation.
 //
-// For one level, one target parity and one box of 8x4x4 coarse cells (128
-// target cells = the MMA's M; the coarsest levels take one box partly outside
-// the grid), every one of the 189 interaction-list offsets o
-// contributes L[cell][a] += sum_b Phi[cell + o][b] K_o[a][b]: a 128 x N x K
-// GEMM (N = K = p^3 padded to a multiple of 32) whose A operand (the 128
-// source vectors) is one rectangular box of the padded parity-major grid-charge
-// layout and whose B operand is the unit-cell kernel.  Both arrive by TMA, in
-// 128-byte K chunks, into a 2-stage ring; one thread issues the MMAs.
+// Only cells that hold charges get a functional (step 4 reads no other).
+// After the sort, a list of the occupied cells of every (level, target
+// parity) segment is built in coarse Morton order; one CTA takes 128 of them
+// (the MMA's M).  For each of the 189 interaction-list offsets o, the tile's
+// contribution L[cell][a] += sum_b Phi[cell + o][b] K_o[a][b] is a
+// 128 x N x K GEMM (N = K = p^3 padded to a multiple of 32): A holds the
+// tile's 128 source vectors, B the unit-cell kernel K_o, both in 128-byte K
+// chunks staged in shared memory with the 128-byte swizzle; one thread issues
+// the MMAs into tensor memory.  A arrives in one of two ways:
+//   - box tiles (a segment whose cells mostly hold charges, or a level with
+//     fewer than 8 coarse cells per axis): the tile is 128 consecutive
+//     Morton cells, an 8 x 4 x 4 box of the padded parity-major layout, and
+//     each stage's A is one TMA box copy; one thread issues A and B into the
+//     same ring stage;
+//   - gathered tiles (sparser segments): producer warps copy each row's 128
+//     bytes with 16-byte cp.async straight into the swizzled layout, complete
+//     and fence them for the async proxy before arriving on the stage; B has
+//     its own TMA producer and ring (tile widths N >= 128), so several stages
+//     of gathered copies stay in flight.
 //
 // Accuracy.  Split precision: x = hi + lo with hi = x with its 13 low mantissa
 // bits cleared (exact in TF32); D = Ahi Bhi + Ahi Blo + Alo Bhi.  The BF16
@@ -23,7 +34,9 @@
 // the epilogue warps read it out and add the 189 partials in FP32 registers,
 // so no FP32 accumulator in TMEM sees more than 3 * K / 8 MMAs (the tensor
 // cores' accumulation is not round-to-nearest; over 1512 MMAs it drifted by
-// ~1e-4).  For N > 64 the epilogue splits the columns over two warp groups.
+// ~1e-4).  A row's functional depends on its own A rows only, so it is the
+// same, bit for bit, whichever tile form computes it.  For N > 64 the
+// epilogue splits the columns over two warp groups.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -34,12 +47,10 @@
 namespace fmm {
 
 #define TC_M 128
-#define TC_STAGES_MAX 3  // stages of the TMA ring (per tile shape, see TcShape::STAGES)
 #define TC_ABYTES (TC_M * 128)      // 128 rows x 32 fp32 (one K chunk)
 #define TC_WAIT_CYCLES (4LL << 30)  // about 2 s of SM clock
 #define TC_NOFF 189
 
-struct TcParams;
 // records the first wait of the launch that gave up (diagnostics in the header)
 __device__ __forceinline__ void tc_wait_failed(int *status, int site, int level, int iter) {
     WsHeader *h = reinterpret_cast<WsHeader *>(status);
@@ -49,22 +60,6 @@ __device__ __forceinline__ void tc_wait_failed(int *status, int site, int level,
         h->wait_iter = iter;
     }
 }
-
-struct TcParams {
-    CUtensorMap phi_hi[FMM_MAXDEPTH + 1];
-    CUtensorMap phi_lo[FMM_MAXDEPTH + 1];
-    CUtensorMap k_hi, k_lo;
-    int first_block[FMM_MAXDEPTH + 2];
-    int lmin, lmax, p3;
-    int spow;  // the forms of level l scale by 2^(l spow): 1 for 1/r, 2 for r/|r|^3
-    long long loc_off[FMM_MAXDEPTH + 1];
-    long long q_off[FMM_MAXDEPTH + 1];
-    float *loc;
-    const float *qlev;
-    const float *kbar;  // [343][N], zero padded
-    int *status;
-    int inject_stall;   // test hook: the first stage's copies are withheld
-};
 
 // The i-th offset of the interaction list of parity (bx, by, bz), in the
 // order shared by the producer and the epilogue.
@@ -102,221 +97,13 @@ template <int N, int MODE>
 struct TcShape {
     static constexpr int CH = N > 64 ? 2 : 1;           // epilogue column groups
     static constexpr int EPI = 4 * CH;                  // epilogue warps
-    static constexpr int THREADS = 32 * (EPI + 2);      // + producer + MMA issuer
     static constexpr int KE = MODE == TC_BF16X3 ? 64 : 32;  // K elements per 128-byte chunk
     static constexpr int KC = (N + KE - 1) / KE;        // 128-byte K chunks
     static constexpr bool LO = MODE != TC_TF32X1;       // lo parts loaded and used
-    static constexpr int BBYTES = N * 128;
-    static constexpr int STAGE = 2 * TC_ABYTES + 2 * BBYTES;
-    // ring depth: three 64 KB stages for N = 128 (one CTA per SM, 193 KB);
-    // two otherwise (N = 64: two CTAs per SM of 2 x 48 KB; N = 224: 2 x 88 KB)
-    static constexpr int STAGES = N == 128 ? 3 : 2;
-    static constexpr int SMEM = STAGES * STAGE + 1024 + 128;
+    static constexpr int BBYTES = N * 128;              // one K chunk of K_o (hi or lo)
     static constexpr int TCOLS = 2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : (2 * N <= 256 ? 256 : 512));
-    static constexpr int MINB = N <= 64 ? 2 : 1;
     static constexpr int COLS = N / CH;                 // columns per epilogue thread
 };
-
-template <int N, int MODE>
-__global__ void __launch_bounds__(TcShape<N, MODE>::THREADS, TcShape<N, MODE>::MINB)
-    k_m2l_tc(const __grid_constant__ TcParams prm) {
-    typedef TcShape<N, MODE> Sh;
-    extern __shared__ unsigned char smraw[];
-    const uint32_t raw = tc::smem_u32(smraw);
-    const uint32_t sbase = (raw + 1023u) & ~1023u;
-    // barriers: full / empty per stage, rfull / rfree per TMEM region (two),
-    // done, then the TMEM address slot (16 * STAGES + 40 <= 128 bytes)
-    const uint32_t bars = sbase + Sh::STAGES * Sh::STAGE;
-    const uint32_t full0 = bars, empty0 = bars + 8 * Sh::STAGES, rfull0 = bars + 16 * Sh::STAGES;
-    const uint32_t rfree0 = rfull0 + 16;
-    const uint32_t done = rfree0 + 16;  // every MMA of this CTA has completed
-    const uint32_t tslot = done + 8;
-    volatile uint32_t *tslot_ptr = reinterpret_cast<volatile uint32_t *>(smraw + (tslot - raw));
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    // block -> level, target parity, tile of 8x4x4 coarse cells
-    int l = prm.lmin;
-    while (l < prm.lmax && (int)blockIdx.x >= prm.first_block[l + 1]) l++;
-    const int rel = blockIdx.x - prm.first_block[l];
-    const int H = 1 << (l - 1), P = H + 2;
-    // levels with fewer than 8 x 4 x 4 coarse cells per parity take one tile,
-    // partly outside the grid (those rows read the TMA fill and are not stored)
-    const int ntx = (H + 7) / 8, nty = (H + 3) / 4, ntz = (H + 3) / 4;
-    const int ntiles = ntx * nty * ntz;
-    const int par = rel / ntiles, tile = rel % ntiles;
-    const int X0 = (tile % ntx) * 8, Y0 = ((tile / ntx) % nty) * 4, Z0 = (tile / (ntx * nty)) * 4;
-    const int bx = par & 1, by = (par >> 1) & 1, bz = par >> 2;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < Sh::STAGES; s++) {
-            tc::mbar_init(full0 + 8 * s, 1);
-            tc::mbar_init(empty0 + 8 * s, 1);
-        }
-        for (int r = 0; r < 2; r++) {
-            tc::mbar_init(rfull0 + 8 * r, 1);
-            tc::mbar_init(rfree0 + 8 * r, 32 * Sh::EPI);
-        }
-        tc::mbar_init(done, 1);
-        tc::fence_barrier_init();
-    }
-    if (warp == 0) tc::tmem_alloc(tslot, Sh::TCOLS);
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = *tslot_ptr;
-
-    if (warp == Sh::EPI && lane == 0) {
-        // ---- TMA producer: (offset, K chunk) stages ----
-        bool failed = false;
-        int last_phase[TC_STAGES_MAX];
-        for (int s = 0; s < TC_STAGES_MAX; s++) last_phase[s] = -1;
-        int ox = -2 - bx - 1, oy = -2 - by, oz = -2 - bz, it = 0;
-        while (!failed && next_offset(bx, by, bz, ox, oy, oz)) {
-            const Off f = make_off(bx, by, bz, ox, oy, oz);
-            const int cX = X0 + 1 + f.dX, cY = Y0 + 1 + f.dY, cZ = Z0 + 1 + f.dZ;
-            for (int kc = 0; kc < Sh::KC; kc++, it++) {
-                const int s = it % Sh::STAGES;
-                const uint32_t ph = (uint32_t)(it / Sh::STAGES) & 1u;
-                if (!tc::mbar_wait(empty0 + 8 * s, ph ^ 1u, TC_WAIT_CYCLES)) {
-                    tc_wait_failed(prm.status, 1, l, it);
-                    failed = true;
-                    break;
-                }
-                const uint32_t st = sbase + s * Sh::STAGE;
-                const uint32_t fb = full0 + 8 * s;
-                const int kx = kc * Sh::KE;
-                tc::mbar_expect_tx(fb, Sh::LO ? Sh::STAGE : TC_ABYTES + Sh::BBYTES);
-                if (prm.inject_stall && it == 0) continue;  // armed, never filled (test hook)
-                tc::tma_load_5d(st, &prm.phi_hi[l], fb, kx, cX, cY, cZ, f.spar);
-                tc::tma_load_3d(st + 2 * TC_ABYTES, &prm.k_hi, fb, kx, 0, f.oi);
-                if (Sh::LO) {
-                    tc::tma_load_5d(st + TC_ABYTES, &prm.phi_lo[l], fb, kx, cX, cY, cZ, f.spar);
-                    tc::tma_load_3d(st + 2 * TC_ABYTES + Sh::BBYTES, &prm.k_lo, fb, kx, 0, f.oi);
-                }
-                last_phase[s] = (int)ph;
-            }
-        }
-        if (failed) {
-            atomicOr(prm.status, ST_TIMEOUT);
-            // let the copies already issued land before the CTA can exit
-            for (int s = 0; s < Sh::STAGES; s++)
-                if (last_phase[s] >= 0) tc::mbar_wait(full0 + 8 * s, (uint32_t)last_phase[s], TC_WAIT_CYCLES);
-        }
-    } else if (warp == Sh::EPI + 1 && lane == 0) {
-        // ---- MMA issuer: offset i accumulates into TMEM region i & 1 ----
-        const uint32_t idesc = MODE == TC_BF16X3 ? tc::idesc_bf16(TC_M, N) : tc::idesc_tf32(TC_M, N);
-        bool failed = false;
-        for (int i = 0; i < TC_NOFF && !failed; i++) {
-            const int r = i & 1;
-            const uint32_t u = (uint32_t)(i >> 1) & 1u;
-            if (!tc::mbar_wait(rfree0 + 8 * r, u ^ 1u, TC_WAIT_CYCLES)) {
-                tc_wait_failed(prm.status, 2, l, i);
-                failed = true;
-                break;
-            }
-            const uint32_t d = tmem + (uint32_t)(r * N);
-            for (int kc = 0; kc < Sh::KC; kc++) {
-                const int it = Sh::KC * i + kc;
-                const int s = it % Sh::STAGES;
-                const uint32_t ph = (uint32_t)(it / Sh::STAGES) & 1u;
-                if (!tc::mbar_wait(full0 + 8 * s, ph, TC_WAIT_CYCLES)) {
-                    tc_wait_failed(prm.status, 3, l, it);
-                    failed = true;
-                    break;
-                }
-                tc::fence_after_sync();
-                const uint32_t st = sbase + s * Sh::STAGE;
-#pragma unroll
-                for (int k = 0; k < 4; k++) {  // 32 bytes of K per MMA (8 tf32 or 16 bf16)
-                    const uint64_t ah = tc::desc_sw128(st + 32 * k);
-                    const uint64_t al = tc::desc_sw128(st + TC_ABYTES + 32 * k);
-                    const uint64_t bh = tc::desc_sw128(st + 2 * TC_ABYTES + 32 * k);
-                    const uint64_t bl = tc::desc_sw128(st + 2 * TC_ABYTES + Sh::BBYTES + 32 * k);
-                    if (MODE == TC_BF16X3) {
-                        tc::mma_bf16(d, ah, bh, idesc, (kc | k) != 0);
-                        tc::mma_bf16(d, ah, bl, idesc, 1u);
-                        tc::mma_bf16(d, al, bh, idesc, 1u);
-                    } else {
-                        tc::mma_tf32(d, ah, bh, idesc, (kc | k) != 0);
-                        if (MODE == TC_TF32X3) {
-                            tc::mma_tf32(d, ah, bl, idesc, 1u);
-                            tc::mma_tf32(d, al, bh, idesc, 1u);
-                        }
-                    }
-                }
-                tc::mma_commit(empty0 + 8 * s);
-            }
-            if (!failed) tc::mma_commit(rfull0 + 8 * r);
-        }
-        if (failed) atomicOr(prm.status, ST_TIMEOUT);
-        tc::mma_commit(done);  // always: the deallocation waits on it
-    } else if (warp < Sh::EPI) {
-        // ---- epilogue: TMEM lane = target cell; columns [c0, c0 + COLS) ----
-        const int sub = warp & 3, cgrp = warp >> 2;
-        const int c0 = cgrp * Sh::COLS;
-        const int row = sub * 32 + lane;
-        const int tx = row & 7, ty = (row >> 3) & 3, tz = row >> 5;
-        const bool valid = X0 + tx < H && Y0 + ty < H && Z0 + tz < H;
-        const float *q = prm.qlev + prm.q_off[l];
-        float tot[Sh::COLS];
-#pragma unroll
-        for (int j = 0; j < Sh::COLS; j++) tot[j] = 0.0f;
-        bool ok = true;
-        int ox = -2 - bx - 1, oy = -2 - by, oz = -2 - bz;
-        for (int i = 0; i < TC_NOFF; i++) {
-            next_offset(bx, by, bz, ox, oy, oz);
-            const Off f = make_off(bx, by, bz, ox, oy, oz);
-            const float Qs = valid ? q[(((int64_t)f.spar * P + Z0 + tz + 1 + f.dZ) * P + Y0 + ty + 1 + f.dY) * P +
-                                       X0 + tx + 1 + f.dX]
-                                   : 0.0f;
-            const float4 *kb = reinterpret_cast<const float4 *>(prm.kbar + (int64_t)f.oi * N + c0);
-            const int r = i & 1;
-            const uint32_t u = (uint32_t)(i >> 1) & 1u;
-            if (ok && !tc::mbar_wait(rfull0 + 8 * r, u, TC_WAIT_CYCLES)) {
-                if (lane == 0) tc_wait_failed(prm.status, 4, l, i);
-                ok = false;
-            }
-            tc::fence_after_sync();
-            const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(r * N + c0);
-#pragma unroll
-            for (int c = 0; c < Sh::COLS / 16; c++) {
-                uint32_t v[16];
-                tc::tmem_ld16(taddr + c * 16, v);
-#pragma unroll
-                for (int j = 0; j < 16; j += 4) {
-                    const float4 m = kb[(c * 16 + j) >> 2];
-                    tot[c * 16 + j] += __uint_as_float(v[j]) + m.x * Qs;
-                    tot[c * 16 + j + 1] += __uint_as_float(v[j + 1]) + m.y * Qs;
-                    tot[c * 16 + j + 2] += __uint_as_float(v[j + 2]) + m.z * Qs;
-                    tot[c * 16 + j + 3] += __uint_as_float(v[j + 3]) + m.w * Qs;
-                }
-            }
-            tc::fence_before_sync();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rfree0 + 8 * r) : "memory");
-        }
-        const int cx = 2 * (X0 + tx) + bx, cy = 2 * (Y0 + ty) + by, cz = 2 * (Z0 + tz) + bz;
-        const int p3 = prm.p3;
-        float *out = prm.loc + prm.loc_off[l] + (valid ? loc_cell(l, cx, cy, cz) : 0) * p3 + c0;
-        const float scale = (float)(1 << (l * prm.spow));
-        if (ok) {
-            if (valid) {
-#pragma unroll
-                for (int j = 0; j < Sh::COLS; j++)
-                    if (c0 + j < p3) out[j] = scale * tot[j];
-            }
-        } else if (lane == 0) {
-            atomicOr(prm.status, ST_TIMEOUT);
-        }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) {
-        tc::mbar_wait(done, 0, TC_WAIT_CYCLES);
-        tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, Sh::TCOLS);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Occupied cells.  Only the functionals of cells that hold a charge are read
@@ -329,6 +116,7 @@ struct OccParams {
     const int *leaf_start;
     int *occ;  // the workspace region (layout in fmm_internal.cuh)
     int depth, lmin, nseg, nblk;
+    int N;     // tile width of the contraction (box or gathered tiles per segment)
     int bfirst[8 * (FMM_MAXDEPTH + 1) + 1];  // first block of each segment
 };
 
@@ -424,7 +212,7 @@ __global__ void __launch_bounds__(OCC_BLOCK / 4) k_occ_scatter(const __grid_cons
         int t = 0;
         for (int k = 0; k < op.nseg; k++) {
             tiles[k] = t;
-            t += (cnt[k] + 127) / 128;
+            t += occ_seg_tiles(1 << (op.lmin + k / 8 - 1), cnt[k], op.N);
         }
         tiles[op.nseg] = t;
     }
@@ -464,7 +252,7 @@ struct TcgParams {
 // and the kernel-matrix B stages (2 N 128 bytes) are separate rings with their
 // own producers, so the gather keeps G = SA - 1 stages of copies in flight per
 // producer thread; one CTA per SM (N = 224: 3 A + 2 B stages, 208 KB; N = 128:
-// 4 + 2, 192 KB).  N <= 64 (UNI): one ring whose stages hold A and B, one
+// 3 + 3, 192 KB).  Dynamic plus static shared memory stays below 227 KB.  N <= 64 (UNI): one ring whose stages hold A and B, one
 // producer warp whose first lane also issues the B copies, six warps and two
 // CTAs per SM (each CTA's barrier round trips and epilogue hide under the
 // other's MMAs).
@@ -474,8 +262,8 @@ struct TcgShape {
     static constexpr bool UNI = N <= 64;
     static constexpr int PW = UNI ? 1 : 2;  // producer (gather) warps
     static constexpr int NPROD = 32 * PW;
-    static constexpr int SA = UNI ? 2 : (N == 224 ? 3 : 4);
-    static constexpr int SB = 2;
+    static constexpr int SA = UNI ? 2 : 3;
+    static constexpr int SB = N == 128 ? 3 : 2;
     static constexpr int G = SA - 1;                 // copy groups in flight per producer thread
     static constexpr int ASTAGE = 2 * TC_ABYTES;     // hi, lo
     static constexpr int BSTAGE = 2 * B::BBYTES;     // hi, lo
@@ -484,6 +272,7 @@ struct TcgShape {
     static constexpr int THREADS = 32 * (WM + 1);
     static constexpr int MINB = UNI ? 2 : 1;
     static constexpr int SMEM = 1024 + SA * ASTAGE + SB * BSTAGE + 256 + 3 * TC_M * 4;
+    static_assert(SMEM + 1024 <= 227 * 1024, "shared memory of one CTA");
 };
 
 template <int G>
@@ -495,16 +284,22 @@ template <int N, int MODE>
 __global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>::MINB) k_m2l_tcg(const __grid_constant__ TcgParams prm) {
     typedef TcShape<N, MODE> Sh;
     typedef TcgShape<N, MODE> Gh;
-    const int nblk = occ_nblk(prm.depth, prm.lmin);
-    const int *cnt_seg = prm.occ + nblk, *tiles = cnt_seg + prm.nseg;
-    if ((int)blockIdx.x >= tiles[prm.nseg]) return;  // past the last occupied tile
+    // the segments' counts and tile prefix, read once into shared memory
+    __shared__ int seg_cnt[8 * (FMM_MAXDEPTH + 1)], seg_tiles[8 * (FMM_MAXDEPTH + 1) + 1];
+    {
+        const int *cnt_g = prm.occ + occ_nblk(prm.depth, prm.lmin), *tiles_g = cnt_g + prm.nseg;
+        if ((int)threadIdx.x <= prm.nseg) seg_tiles[threadIdx.x] = tiles_g[threadIdx.x];
+        if ((int)threadIdx.x < prm.nseg) seg_cnt[threadIdx.x] = cnt_g[threadIdx.x];
+        __syncthreads();
+    }
+    if ((int)blockIdx.x >= seg_tiles[prm.nseg]) return;  // past the last occupied tile
     int sg = 0;
-    while (sg + 1 < prm.nseg && (int)blockIdx.x >= tiles[sg + 1]) sg++;
+    while (sg + 1 < prm.nseg && (int)blockIdx.x >= seg_tiles[sg + 1]) sg++;
     const int l = prm.lmin + sg / 8, par = sg & 7;
     const int bx = par & 1, by = (par >> 1) & 1, bz = par >> 2;
     const int H = 1 << (l - 1), P = H + 2, Pt = (int)tc_level_extent(l);
-    const int count = cnt_seg[sg];
-    const int r0 = ((int)blockIdx.x - tiles[sg]) * TC_M;  // first list entry of the tile
+    const int count = seg_cnt[sg];
+    const int r0 = ((int)blockIdx.x - seg_tiles[sg]) * TC_M;  // first list entry of the tile
     const int *lst = prm.occ + occ_list_offset(prm.depth, prm.lmin) + occ_seg_first(prm.lmin, sg);
 
     extern __shared__ unsigned char smraw[];
@@ -523,13 +318,19 @@ __global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>:
     int *rowA = reinterpret_cast<int *>(smraw + (bars - raw) + 256);
     int *rowQ = rowA + TC_M, *rowL = rowQ + TC_M;
 
-    // Box tiles: when every cell of the segment holds charges the tile's 128
-    // consecutive Morton cells form one 8 x 4 x 4 box, and each offset's A
-    // operand is one TMA box copy (row r = x + 8 y + 32 z of the box) instead
-    // of 128 gathered rows.  Levels with fewer than 8 coarse cells per axis
-    // take one box at the origin, partly outside the grid (the operand layout
-    // holds zeros there; those rows are not stored), whatever their occupancy.
-    const bool box = H < 8 || count == (1 << (3 * (l - 1)));
+    // Box tiles (occ_box_segment: a level with fewer than 8 coarse cells per
+    // axis, or a segment whose cells mostly hold charges): tile t is the 128
+    // consecutive Morton cells [128 t, 128 t + 128), one 8 x 4 x 4 box, and
+    // each offset's A operand is one TMA box copy (row r = x + 8 y + 32 z of
+    // the box) instead of 128 gathered rows.  A level with fewer than 8 coarse
+    // cells per axis takes one box at the origin, partly outside the grid (the
+    // operand layout holds zeros there; those rows are not stored).
+    const bool box = occ_box_segment(H, count, N);
+    // one ring whose stages hold A and B, filled by one thread (box tiles, and
+    // every tile of the narrow shapes), or split rings (gathered tiles of N >= 128)
+    const bool uni = Gh::UNI || box;
+    const int SU = Gh::SA < Gh::SB ? Gh::SA : Gh::SB;
+    const int ra = uni ? SU : Gh::SA, rb = uni ? SU : Gh::SB;  // ring depths of A and B
     int X0 = 0, Y0 = 0, Z0 = 0;
     if (box) morton_decode((uint32_t)r0, X0, Y0, Z0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -557,7 +358,7 @@ __global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>:
         for (int s = 0; s < Gh::SA; s++) {
             // arrivals: the box copies' issuer, or every gather thread (plus the
             // issuer of the B copies when they share the ring)
-            tc::mbar_init(afull0 + 8 * s, box ? 1 : Gh::NPROD + (Gh::UNI ? 1 : 0));
+            tc::mbar_init(afull0 + 8 * s, box ? 1 : Gh::NPROD + (uni ? 1 : 0));
             tc::mbar_init(aempty0 + 8 * s, 1);
         }
         for (int s = 0; s < Gh::SB; s++) {
@@ -601,8 +402,8 @@ __global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>:
             const int64_t delta = lvl0 + f.spar * pt3 + ((int64_t)f.dZ * Pt + f.dY) * Pt + f.dX;
             const int cX = X0 + 1 + f.dX, cY = Y0 + 1 + f.dY, cZ = Z0 + 1 + f.dZ;
             for (int kc = 0; kc < Sh::KC; kc++, it++) {
-                const int s = it % Gh::SA;
-                const uint32_t ph = (uint32_t)(it / Gh::SA) & 1u;
+                const int s = it % ra;
+                const uint32_t ph = (uint32_t)(it / ra) & 1u;
                 if (!tc::mbar_wait(aempty0 + 8 * s, ph ^ 1u, TC_WAIT_CYCLES)) {
                     if (lane == 0) tc_wait_failed(prm.status, 1, l, it);
                     failed = true;
@@ -612,7 +413,7 @@ __global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>:
                 const uint32_t fb = afull0 + 8 * s;
                 // TMA bytes of this stage (an arrival of its own; none when the
                 // lead only gathers)
-                const uint32_t tx = (box ? ABYTES : 0u) + (Gh::UNI ? BBYTES : 0u);
+                const uint32_t tx = (box ? ABYTES : 0u) + (uni ? BBYTES : 0u);
                 if (lead && tx) {
                     tc::mbar_expect_tx(fb, tx);
                     last_phase[s] = (int)ph;
@@ -620,7 +421,7 @@ __global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>:
                         tc::tma_load_5d(st, &prm.phi_hi[l], fb, kc * Sh::KE, cX, cY, cZ, f.spar);
                         if (Sh::LO) tc::tma_load_5d(st + TC_ABYTES, &prm.phi_lo[l], fb, kc * Sh::KE, cX, cY, cZ, f.spar);
                     }
-                    if (Gh::UNI && !(prm.inject_stall && it == 0)) {  // inject: armed, never filled
+                    if (uni && !(prm.inject_stall && it == 0)) {  // inject: armed, never filled
                         const uint32_t stb = bbase + s * Gh::BSTAGE;
                         tc::tma_load_3d(stb, &prm.k_hi, fb, kc * Sh::KE, 0, f.oi);
                         if (Sh::LO) tc::tma_load_3d(stb + Sh::BBYTES, &prm.k_lo, fb, kc * Sh::KE, 0, f.oi);
@@ -640,7 +441,7 @@ __global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>:
                 cp_async_wait_pending<Gh::G - 1>();  // stages <= it - G + 1 have landed
                 if (it - Gh::G + 1 >= sig) {
                     tc::fence_proxy_async_smem();
-                    for (; sig <= it - Gh::G + 1; sig++) tc::mbar_arrive(afull0 + 8 * (sig % Gh::SA));
+                    for (; sig <= it - Gh::G + 1; sig++) tc::mbar_arrive(afull0 + 8 * (sig % ra));
                 }
             }
         }
@@ -648,16 +449,16 @@ __global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>:
             tc::cp_async_wait_all();  // no copy outlives the CTA
             if (!failed) {
                 tc::fence_proxy_async_smem();
-                for (; sig < it; sig++) tc::mbar_arrive(afull0 + 8 * (sig % Gh::SA));
+                for (; sig < it; sig++) tc::mbar_arrive(afull0 + 8 * (sig % ra));
             }
         }
         if (failed) {
             if (lane == 0) atomicOr(prm.status, ST_TIMEOUT);
             if (lead)  // the TMA copies already issued land before the CTA can exit
-                for (int s = 0; s < Gh::SA; s++)
+                for (int s = 0; s < ra; s++)
                     if (last_phase[s] >= 0) tc::mbar_wait(afull0 + 8 * s, (uint32_t)last_phase[s], TC_WAIT_CYCLES);
         }
-    } else if (!Gh::UNI && warp == Gh::WB && lane == 0) {
+    } else if (!uni && warp == Gh::WB && lane == 0) {
         // ---- kernel-matrix producer (split rings): K chunk kc of K_o by TMA ----
         bool failed = false;
         int last_phase[4] = {-1, -1, -1, -1};
@@ -702,9 +503,9 @@ __global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>:
             const uint32_t d = tmem + (uint32_t)(r * N);
             for (int kc = 0; kc < Sh::KC; kc++) {
                 const int it = Sh::KC * i + kc;
-                const int sa = it % Gh::SA, sb = it % Gh::SB;
-                if (!tc::mbar_wait(afull0 + 8 * sa, (uint32_t)(it / Gh::SA) & 1u, TC_WAIT_CYCLES) ||
-                    (!Gh::UNI && !tc::mbar_wait(bfull0 + 8 * sb, (uint32_t)(it / Gh::SB) & 1u, TC_WAIT_CYCLES))) {
+                const int sa = it % ra, sb = it % rb;
+                if (!tc::mbar_wait(afull0 + 8 * sa, (uint32_t)(it / ra) & 1u, TC_WAIT_CYCLES) ||
+                    (!uni && !tc::mbar_wait(bfull0 + 8 * sb, (uint32_t)(it / rb) & 1u, TC_WAIT_CYCLES))) {
                     tc_wait_failed(prm.status, 3, l, it);
                     failed = true;
                     break;
@@ -730,7 +531,7 @@ __global__ void __launch_bounds__(TcgShape<N, MODE>::THREADS, TcgShape<N, MODE>:
                     }
                 }
                 tc::mma_commit(aempty0 + 8 * sa);
-                if (!Gh::UNI) tc::mma_commit(bempty0 + 8 * sb);
+                if (!uni) tc::mma_commit(bempty0 + 8 * sb);
             }
             if (!failed) tc::mma_commit(rfull0 + 8 * r);
         }
@@ -942,31 +743,6 @@ int tc_encode_kernel_map(void *map, const void *base, int p3s, int pk, int mode)
 size_t tc_map_bytes() { return sizeof(CUtensorMap); }
 
 template <int N, int MODE>
-static int launch_tc_kernel(const TcParams &prm, int blocks, cudaStream_t st) {
-    typedef TcShape<N, MODE> Sh;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_m2l_tc<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 Sh::SMEM) != cudaSuccess)
-            return FMM_ERR_CUDA;
-        attr = true;
-    }
-    k_m2l_tc<N, MODE><<<blocks, Sh::THREADS, Sh::SMEM, st>>>(prm);
-    return FMM_OK;
-}
-
-template <int MODE>
-static int launch_tc_mode(int p3s, const TcParams &prm, int blocks, cudaStream_t st) {
-    switch (p3s) {
-    case 32: return launch_tc_kernel<32, MODE>(prm, blocks, st);
-    case 64: return launch_tc_kernel<64, MODE>(prm, blocks, st);
-    case 128: return launch_tc_kernel<128, MODE>(prm, blocks, st);
-    case 224: return launch_tc_kernel<224, MODE>(prm, blocks, st);
-    default: return FMM_ERR_UNSUPPORTED;
-    }
-}
-
-template <int N, int MODE>
 static int launch_tcg_kernel(const TcgParams &prm, int blocks, cudaStream_t st) {
     typedef TcgShape<N, MODE> Gh;
     static bool attr = false;
@@ -1016,7 +792,6 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
             k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi, SL, P.phihi, P.philo, p3, p3s, mode == FMM_TC_TF32X1);
         tr.count();
     }
-#ifndef FMM_TC_DENSE
     // the occupied cells of every (level, parity) segment, once per evaluation
     OccParams op;
     memset(&op, 0, sizeof(op));
@@ -1025,6 +800,7 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
     op.depth = depth;
     op.lmin = lmin;
     op.nseg = occ_nseg(depth, lmin);
+    op.N = p3s;
     int nb = 0, blocks = 0;
     for (int s = 0; s < op.nseg; s++) {
         op.bfirst[s] = nb;
@@ -1074,39 +850,6 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
     int rc = mode == FMM_TC_BF16X3   ? launch_tcg_mode<TC_BF16X3>(p3s, prm, blocks, st)
              : mode == FMM_TC_TF32X1 ? launch_tcg_mode<TC_TF32X1>(p3s, prm, blocks, st)
                                      : launch_tcg_mode<TC_TF32X3>(p3s, prm, blocks, st);
-#else
-    TcParams prm;
-    memset(&prm, 0, sizeof(prm));
-    int blocks = 0;
-    for (int l = lmin; l <= depth; l++) {
-        const int64_t cl = tc_level_first(l);  // first cell of level l (operand layout)
-        const void *bh = bf16 ? (const void *)(hi16 + cl * pk) : (const void *)(P.phihi + cl * p3s);
-        const void *bl = bf16 ? (const void *)(lo16 + cl * pk) : (const void *)(P.philo + cl * p3s);
-        int rc = encode_phi_map(&prm.phi_hi[l], bh, l, pk, bf16);
-        if (!rc) rc = encode_phi_map(&prm.phi_lo[l], bl, l, pk, bf16);
-        if (rc) return rc;
-        prm.first_block[l] = blocks;
-        const int H = 1 << (l - 1);
-        blocks += 8 * ((H + 7) / 8) * ((H + 3) / 4) * ((H + 3) / 4);
-        prm.loc_off[l] = W.loc_level[l];
-        prm.q_off[l] = W.q_level[l];
-    }
-    prm.first_block[depth + 1] = blocks;
-    memcpy(&prm.k_hi, k_hi_map, sizeof(CUtensorMap));
-    memcpy(&prm.k_lo, k_lo_map, sizeof(CUtensorMap));
-    prm.lmin = lmin;
-    prm.lmax = depth;
-    prm.p3 = p3;
-    prm.spow = spow;
-    prm.loc = loc;
-    prm.qlev = P.qlev;
-    prm.kbar = kbar;
-    prm.status = &P.hdr->status;
-    prm.inject_stall = inject == FMM_INJECT_TC_STALL;
-    int rc = mode == FMM_TC_BF16X3   ? launch_tc_mode<TC_BF16X3>(p3s, prm, blocks, st)
-             : mode == FMM_TC_TF32X1 ? launch_tc_mode<TC_TF32X1>(p3s, prm, blocks, st)
-                                     : launch_tc_mode<TC_TF32X3>(p3s, prm, blocks, st);
-#endif
     tr.count();
     tr.end();
     return rc;

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_main_arm_json_contract():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "uniform4k",
-                          "--steps", "3", "--warmup", "3", "--no-cpu-baseline"],
+                          "--steps", "3", "--warmup", "3", "--no-cpu-baseline", "--no-extras"],
                          capture_output=True, text=True, timeout=900, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-3000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
