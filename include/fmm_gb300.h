@@ -184,7 +184,12 @@ int fmm_eval(fmm_plan_t plan, int64_t n, const float *pos, const float *q, void 
  *   grad_pos     device, (n,3) float32 (float64 for FP64 plans), nullable.
  *   grad_q       device, (n) float32 (float64 for FP64 plans), nullable.
  * pos and q must be the arrays the last fmm_eval was given.  Errors:
- * FMM_ERR_STATE if the workspace holds no evaluation of this plan and n.
+ * FMM_ERR_STATE if the workspace holds no evaluation of this plan and n: the
+ * host checks that this plan's last fmm_eval used this workspace and n, and
+ * the device checks the tag (plan, n) that every evaluation leaves in the
+ * workspace header, so an evaluation of another plan into the same workspace
+ * since then is caught too (returned with opts.sync = 1, else by fmm_status;
+ * the gradients are then undefined).
  */
 int fmm_backward(fmm_plan_t plan, int64_t n, const float *pos, const float *q,
                  const double *grad_energy, void *grad_pos, void *grad_q, void *workspace,
@@ -192,7 +197,8 @@ int fmm_backward(fmm_plan_t plan, int64_t n, const float *pos, const float *q,
 
 /*
  * fmm_status — device-side status of the last fmm_eval/fmm_backward on this
- * workspace (waits on `stream`).  For opts.sync = 0.
+ * workspace (waits on `stream`).  For opts.sync = 0.  workspace NULL: the
+ * scratch array of fmm_eval_static on the current device.
  */
 int fmm_status(fmm_plan_t plan, const void *workspace, void *stream);
 
@@ -337,18 +343,22 @@ int fmm_batch_get_stats(fmm_batch_t batch, fmm_batch_stats_t *stats);
 /*
  * fmm_eval_static — fmm_eval without a workspace argument.  The paper has no
  * counterpart: this entry point is for callers that cannot allocate device
- * memory at the time they evaluate (code running inside another framework's
- * stream capture, real-time time-step loops that forbid allocation, hosts
- * whose device memory is all owned by a pool they cannot draw from).
+ * memory at the time they evaluate (a plugin inside a host application whose
+ * device memory is all owned by the host's allocator or pool, real-time
+ * time-step loops that must not allocate, deployments that fix their device
+ * memory at start-up).
  *   Scratch: a static device array of FMM_STATIC_WORKSPACE_BYTES (32 MiB),
  *   which every GPU that loads the library holds until the process exits.
  *   Limit: (plan, n) whose fmm_workspace_size exceeds it are rejected with
  *   FMM_ERR_WORKSPACE before any device work.
  *   Allocation: none (no cudaMalloc/cudaFree, no allocating library call);
  *   the plan, created beforehand, owns its tables.
+ *   Device: the current device must be the one the plan was created on, else
+ *   FMM_ERR_ARG.
  *   Set-up: the first call on a device, with that device current, looks up
- *   the array's device address (cudaGetSymbolAddress); make that first call
- *   before any stream capture.
+ *   the array's device address (cudaGetSymbolAddress).
+ *   Status: with opts.sync = 1 the call waits and returns the device status;
+ *   with opts.sync = 0, fmm_status(plan, NULL, stream) reads it later.
  *   Sharing: every call uses the same array and leaves the last call's
  *   contents in it (the call clears what must start at zero itself); calls
  *   that overlap on the GPU (other streams, other host threads) race and

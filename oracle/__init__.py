@@ -98,6 +98,8 @@ def lib():
         L.orc_lattice_grad.argtypes = [d, d, d, P]
         L.orc_evaluate_kernel.argtypes = [i32, i32, i32, i64, P, P, P, P, P, P, P, P, P, P, P, P,
                                           P]
+        L.orc_interaction_list.argtypes = [i32, i32, i32, i32, i32, P, P]
+        L.orc_interaction_list.restype = i32
         _lib = L
     return _lib
 
@@ -287,6 +289,17 @@ def ewald_unit(x, q, targets=None):
 # ---------------------------------------------------------------------------
 
 DEFAULT_SPLIT_RATIO = 1.0 / 256.0  # d / (leaf width), i.e. 2d = w/128
+
+
+def interaction_list(l, periodic, cx, cy, cz):
+    """§2.2 step 3: the interaction list of cell (cx, cy, cz) of level l, the list
+    the downward pass iterates over: (source cells in natural order (z S + y) S +
+    x, offset indices ((oz + 3) 7 + oy + 3) 7 + ox + 3), in (z, y, x) order of
+    the source; open form: sources inside the box only; periodic: wrapped."""
+    src = np.zeros(189, np.int64)
+    oi = np.zeros(189, np.int32)
+    m = lib().orc_interaction_list(int(l), int(periodic), int(cx), int(cy), int(cz), _p(src), _p(oi))
+    return src[:m].copy(), oi[:m].copy()
 
 
 def level_offset(n, l):

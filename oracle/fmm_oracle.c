@@ -682,6 +682,43 @@ static void shift_axis_t(int n, const double *G, int axis, const double *in, dou
             }
 }
 
+/* The interaction list of cell (cx, cy, cz) of a level with S cells per axis
+ * (§2.2 step 3): the children of the parent cell and of its 26 neighbours
+ * that are not adjacent to the cell (no offset with |o|_inf <= 1), in
+ * (z, y, x) order of the source.  Open form: only sources inside the box;
+ * periodic form: the source index wrapped, the offset kept.  Writes the
+ * source cell (natural order (z S + y) S + x) and the offset's index
+ * ((oz + 3) 7 + oy + 3) 7 + ox + 3 of every entry; returns their number. */
+static int interaction_list(int S, int periodic, int cx, int cy, int cz, int64_t *src, int *oidx)
+{
+    const int px = cx >> 1, py = cy >> 1, pz = cz >> 1;
+    int m = 0;
+    for (int sz = 2 * (pz - 1); sz <= 2 * (pz + 1) + 1; sz++)
+        for (int sy = 2 * (py - 1); sy <= 2 * (py + 1) + 1; sy++)
+            for (int sx = 2 * (px - 1); sx <= 2 * (px + 1) + 1; sx++) {
+                int ox = sx - cx, oy = sy - cy, oz = sz - cz;
+                if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+                int wx = sx, wy = sy, wz = sz;
+                if (periodic) {
+                    wx = ((sx % S) + S) % S;
+                    wy = ((sy % S) + S) % S;
+                    wz = ((sz % S) + S) % S;
+                } else if (sx < 0 || sy < 0 || sz < 0 || sx >= S || sy >= S || sz >= S) {
+                    continue;
+                }
+                src[m] = ((int64_t)wz * S + wy) * S + wx;
+                oidx[m] = ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3);
+                m++;
+            }
+    return m;
+}
+
+/* The list above for cell (cx, cy, cz) of level l (at most 189 entries). */
+int orc_interaction_list(int l, int periodic, int cx, int cy, int cz, int64_t *src, int *oidx)
+{
+    return interaction_list(1 << l, periodic, cx, cy, cz, src, oidx);
+}
+
 /* The linear functional Psi_C(v) of §2.2 step 3 is stored as the vector L_C
  * with Psi_C(v) = L_C . v.
  *
@@ -755,28 +792,18 @@ void orc_downward(int n, int depth, int periodic, const double *Phi, double *L,
             for (int e = 0; e < n3; e++) v[e] = a[e];
             if (!do_m2l) continue;
             /* interaction list */
-            for (int sz = 2 * (pz - 1); sz <= 2 * (pz + 1) + 1; sz++)
-                for (int sy = 2 * (py - 1); sy <= 2 * (py + 1) + 1; sy++)
-                    for (int sx = 2 * (px - 1); sx <= 2 * (px + 1) + 1; sx++) {
-                        int ox = sx - cx, oy = sy - cy, oz = sz - cz;
-                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                        int wx = sx, wy = sy, wz = sz;
-                        if (periodic) {
-                            wx = ((sx % S) + S) % S;
-                            wy = ((sy % S) + S) % S;
-                            wz = ((sz % S) + S) % S;
-                        } else if (sx < 0 || sy < 0 || sz < 0 || sx >= S || sy >= S || sz >= S) {
-                            continue;
-                        }
-                        int oi = ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3);
-                        const double *kt = KT + (int64_t)oi * n3 * n3;
-                        const double *src = Pl + (((int64_t)wz * S + wy) * S + wx) * n3;
-                        for (int bb = 0; bb < n3; bb++) {
-                            double f = scale * src[bb];
-                            const double *row = kt + (int64_t)bb * n3;
-                            for (int aa = 0; aa < n3; aa++) v[aa] += row[aa] * f;
-                        }
-                    }
+            int64_t il_src[189];
+            int il_o[189];
+            const int m = interaction_list(S, periodic, cx, cy, cz, il_src, il_o);
+            for (int e = 0; e < m; e++) {
+                const double *kt = KT + (int64_t)il_o[e] * n3 * n3;
+                const double *src = Pl + il_src[e] * n3;
+                for (int bb = 0; bb < n3; bb++) {
+                    double f = scale * src[bb];
+                    const double *row = kt + (int64_t)bb * n3;
+                    for (int aa = 0; aa < n3; aa++) v[aa] += row[aa] * f;
+                }
+            }
         }
     }
     free(KT);
@@ -1121,24 +1148,16 @@ int orc_sf_downward(int n, int depth, int periodic, const double *PhiS, double *
             const double *Ht[3] = {H + (size_t)cx * n * n, H + (size_t)cy * n * n,
                                    H + (size_t)cz * n * n};
             double y[ORC_MAXN * ORC_MAXN * ORC_MAXN];
-            for (int sz = 2 * (pz - 1); sz <= 2 * (pz + 1) + 1; sz++)
-                for (int sy = 2 * (py - 1); sy <= 2 * (py + 1) + 1; sy++)
-                    for (int sx = 2 * (px - 1); sx <= 2 * (px + 1) + 1; sx++) {
-                        int ox = sx - cx, oy = sy - cy, oz = sz - cz;
-                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                        int wx = sx, wy = sy, wz = sz;
-                        if (periodic) {
-                            wx = ((sx % S) + S) % S;
-                            wy = ((sy % S) + S) % S;
-                            wz = ((sz % S) + S) % S;
-                        } else if (sx < 0 || sy < 0 || sz < 0 || sx >= S || sy >= S || sz >= S) {
-                            continue;
-                        }
+            int64_t il_src[189];
+            int il_o[189];
+            const int m = interaction_list(S, periodic, cx, cy, cz, il_src, il_o);
+            for (int k = 0; k < m; k++) {
+                        const int wx = (int)(il_src[k] % S), wy = (int)((il_src[k] / S) % S),
+                                  wz = (int)(il_src[k] / ((int64_t)S * S));
                         const double *Hs[3] = {H + (size_t)wx * n * n, H + (size_t)wy * n * n,
                                                H + (size_t)wz * n * n};
-                        int oi = ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3);
-                        const double *src = Pl + (((int64_t)wz * S + wy) * S + wx) * n3;
-                        sf_apply(n, l, Hs, Ht, Kall + (int64_t)oi * n3 * n3, src, y);
+                        const double *src = Pl + il_src[k] * n3;
+                        sf_apply(n, l, Hs, Ht, Kall + (int64_t)il_o[k] * n3 * n3, src, y);
                         for (int e = 0; e < n3; e++) v[e] += y[e];
                     }
         }

@@ -167,10 +167,10 @@ class FMM:
             res = out_h
         return res
 
-    def _check_status(self, ws, stream):
+    def _check_status(self, ws, stream, where="fmm_eval"):
         rc = B.fmm_status(self._h, _ptr(ws), _stream(stream))
         if rc:
-            raise FmmError(rc, "fmm_eval")
+            raise FmmError(rc, where)
 
     def _host_out(self, n):
         hb = getattr(self, "_hbuf", None)
@@ -193,6 +193,8 @@ class FMM:
         gq = torch.empty(n, dtype=self.out_dtype, device=self.device)
         B.fmm_backward(self._h, n, _ptr(pos_d), _ptr(q_d), _ptr(gE), _ptr(gpos), _ptr(gq),
                        _ptr(ws), ws.numel(), _stream(stream))
+        if self.sync:  # the device-side checks, among them the workspace's evaluation tag
+            self._check_status(ws, stream, "fmm_backward")
         return gpos, gq
 
     def inject(self, what="tc_stall"):

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -16,6 +17,7 @@ void far_set_attributes();
 using namespace fmm;
 
 struct fmm_plan_s {
+    long long id;  // distinct per plan (batched systems included): tags the workspace
     int depth, p, periodic;
     fmm_opts_t opts;
     double box[4];
@@ -55,7 +57,14 @@ struct fmm_plan_s {
     Tracer last;  // launches and stage events of the last call
 };
 
-static int g_plan_counter = 0;
+static std::atomic<long long> g_plan_counter{0};
+
+namespace fmm {
+int plan_device(const fmm_plan_s *P) { return P->device; }
+}  // namespace fmm
+
+// Tag of an evaluation in the workspace header: plan id and n.
+static long long eval_tag(const fmm_plan_s *P, int64_t n) { return (P->id << 32) | (long long)n; }
 
 // ---------------------------------------------------------------------------
 // FP64 tables (host)
@@ -454,6 +463,7 @@ Ptrs<real> make_ptrs(const WsLayout &W, void *ws) {
 }
 
 int status_to_error(int st) {
+    if (st & ST_STATE) return FMM_ERR_STATE;
     if (st & ST_TIMEOUT) return FMM_ERR_TIMEOUT;
     if (st & ST_NONFINITE) return FMM_ERR_NONFINITE;
     if (st & ST_OUT_OF_BOX) return FMM_ERR_OUT_OF_BOX;
@@ -464,6 +474,12 @@ int status_to_error(int st) {
 __global__ void k_mark_valid(WsHeader *hdr, long long tag) {
     hdr->valid = 1;
     hdr->tag = tag;
+}
+
+// the backward pass reuses the state of the last evaluation on the workspace:
+// it must be this plan's, for this n
+__global__ void k_check_state(WsHeader *hdr, long long tag) {
+    if (!hdr->valid || hdr->tag != tag) atomicOr(&hdr->status, ST_STATE);
 }
 
 int check_ws(const fmm_plan_t P, int64_t n, const void *ws, size_t bytes) {
@@ -546,7 +562,7 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     launch_l2p<real>(g, C, ptr, W, forces != nullptr, st, tr);
     launch_unsplit<real>(g, ptr, W, (int)n, q, potential, energy, forces, nullptr, nullptr, false,
                          st, tr);
-    k_mark_valid<<<1, 1, 0, st>>>(ptr.hdr, (long long)n);
+    k_mark_valid<<<1, 1, 0, st>>>(ptr.hdr, eval_tag(P, n));
     tr.count();
     return FMM_OK;
 }
@@ -560,6 +576,8 @@ int backward_impl(fmm_plan_t P, int64_t n, const float *q, const double *gE, rea
                                                                         : (const void *)&P->cf);
     Geom g = P->geom;
     if (n == 0) return FMM_OK;
+    k_check_state<<<1, 1, 0, st>>>(ptr.hdr, eval_tag(P, n));
+    tr.count();
     // the gradient of the energy: adjoint forces whatever the forward mode
     if (g.force_mode == FMM_FORCE_KERNEL) g.force_mode = FMM_FORCE_ADJOINT;
     launch_p2p<real>(g, ptr, W, true, st, tr);
@@ -656,6 +674,7 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     }
     fmm_plan_s *P = new (std::nothrow) fmm_plan_s();
     if (!P) return FMM_ERR_OOM;
+    P->id = ++g_plan_counter;
     P->depth = depth;
     P->p = p;
     P->periodic = periodic ? 1 : 0;
@@ -830,7 +849,13 @@ int fmm_get_stats(fmm_plan_t P, fmm_stats_t *out) {
 }
 
 int fmm_status(fmm_plan_t P, const void *workspace, void *stream) {
-    if (!P || !workspace) return FMM_ERR_ARG;
+    if (!P) return FMM_ERR_ARG;
+    if (!workspace) {  // the scratch array of fmm_eval_static on the current device
+        void *ws = nullptr;
+        const int rc = fmm::static_workspace_address(&ws);
+        if (rc != FMM_OK) return rc;
+        workspace = ws;
+    }
     return finish(P, (const WsHeader *)((const char *)workspace), (cudaStream_t)stream, true);
 }
 
@@ -1035,6 +1060,7 @@ namespace {
 fmm_plan_t clone_plan(const fmm_plan_s *m, const double *box, int64_t max_n) {
     fmm_plan_s *P = new (std::nothrow) fmm_plan_s(*m);
     if (!P) return nullptr;
+    P->id = ++g_plan_counter;
     P->shared = true;
     P->s_near = P->s_coarse = P->s_far = nullptr;
     P->e_sorted = P->e_near = P->e_fork = P->e_coarse = P->e_far = nullptr;

@@ -58,6 +58,7 @@ struct WsHeader {
 #define ST_NONFINITE 2
 #define ST_SPLIT_OVERFLOW 4
 #define ST_TIMEOUT 8
+#define ST_STATE 16  // backward on a workspace whose last evaluation was another plan's or n's
 
 // Workspace carving (byte offsets), computed on the host for (plan, n).
 struct WsLayout {
@@ -353,6 +354,11 @@ void launch_sf_upward(const Geom &g, const Ptrs<double> &P, const WsLayout &W, c
 void launch_sf_downward(const Geom &g, const Ptrs<double> &P, const WsLayout &W, const double *tab,
                         const int64_t *base, const double *hmat, const int64_t *hoff,
                         cudaStream_t st, Tracer &tr);
+
+// the device a plan was created on (fmm_api.cu); the scratch array of
+// fmm_eval_static on the current device, looked up once per device (fmm_static.cu)
+int plan_device(const fmm_plan_s *plan);
+int static_workspace_address(void **out);
 
 // near field + far-field evaluation at the charges (kernels_p2p.cu)
 // near field: writes out_pt (assigns) and the reaction slots; far field at the

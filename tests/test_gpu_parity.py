@@ -139,15 +139,22 @@ TF32_CASES = [
     ("uniform60k-d4-p6-open", lambda: inputs.uniform_pm1(60000, 34), 4, 6, False, False),
     ("uniform30k-d4-p3-open", lambda: inputs.uniform_pm1(30000, 35), 4, 3, False, False),
     ("uniform200k-d5-p3-periodic", lambda: inputs.uniform_pm1(200000, 36), 5, 3, True, False),
+    # sparse (Plummer) inputs: segments below the box threshold take gathered
+    # tiles, for every tile width (N = 64, 128, 224), with and without split
+    ("plummer20k-d5-p4-open", lambda: inputs.plummer(20000, 37), 5, 4, False, False),
+    ("plummer60k-d5-p5-open-cont", lambda: inputs.plummer(60000, 38), 5, 5, False, True),
+    ("plummer100k-d5-p6-open", lambda: inputs.plummer(100000, 39), 5, 6, False, False),
+    ("plummer30k-d4-p5-periodic", lambda: inputs.plummer(30000, 40), 4, 5, True, False),
 ]
 
 
 @pytest.mark.parametrize("case", TF32_CASES, ids=[c[0] for c in TF32_CASES])
 def test_parity_tf32x3(case):
-    """Far-field contraction of levels >= 4 on the tcgen05 tensor cores (3-pass
-    split TF32, per-offset accumulators, p^3 padded to a multiple of 32);
-    potentials, energy and forces within the reduced-precision tolerance of
-    the FP64 oracle (sampled outputs)."""
+    """Far-field contraction of every level on the tcgen05 tensor cores (3-pass
+    split TF32, per-offset accumulators, p^3 padded to a multiple of 32; box
+    and gathered tiles); potentials and forces within the reduced-precision
+    tolerance of the FP64 oracle (sampled outputs), functionals of every level
+    at the cells that hold charges."""
     name, gen, depth, p, periodic, cont = case
     pos, q, box = gen()
     n = len(q)
@@ -155,6 +162,9 @@ def test_parity_tf32x3(case):
     ref = oracle.fmm(pos, q, box, depth=depth, n=p, periodic=periodic, continuous=cont, sample=s)
     plan, out = _gpu(pos, q, box, depth, p, periodic, cont, None, "tf32x3")
     _check_integer_work(plan, ref)
+    full = oracle.fmm(pos, q, box, depth=depth, n=p, periodic=periodic, continuous=cont) if n <= 100000 else None
+    if full is not None:
+        _check_levels(plan, full, p, depth, periodic, TOL_LEVELS_FP32)
     assert _rel_l2(out["potential"][s], ref["phi"]) < TOL_TF32X3
     assert _rel_l2(out["forces"][s], ref["F"]) < TOL_TF32X3
     plan.close()
@@ -349,6 +359,32 @@ def test_backward_matches_forces_and_potential(precision):
     plan.close()
 
 
+def test_backward_rejects_a_workspace_another_plan_wrote():
+    """fmm_backward reuses the state the last evaluation left in the workspace;
+    once another plan has evaluated into the same workspace it fails with
+    FMM_ERR_STATE instead of returning gradients of the other system."""
+    pos, q, box = inputs.uniform_cont(3000, 41)
+    pos2, q2, _ = inputs.uniform_cont(3000, 42)
+    a = FMM(box, 3, 4, continuous=True, split_ratio=1 / 16, max_n=len(q))
+    b = FMM(box, 3, 4, continuous=True, split_ratio=1 / 16, max_n=len(q))
+    ws = a.workspace(len(q))
+    gE = torch.ones(1, dtype=torch.float64, device="cuda")
+    a.eval(torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda(), workspace=ws)
+    gpos, gq = a.backward(gE)
+    ref = oracle.fmm(pos, q, box, depth=3, n=4, continuous=True, dt=1 / 16)
+    assert _rel_l2(gq.cpu().numpy().astype(np.float64), ref["phi"]) < TOL_FP32
+    b.eval(torch.from_numpy(pos2).cuda(), torch.from_numpy(q2).cuda(), workspace=ws)
+    with pytest.raises(FmmError) as e:
+        a.backward(gE)
+    assert e.value.code == B.FMM_ERR_STATE
+    # a new evaluation of the first plan makes the workspace its own again
+    a.eval(torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda(), workspace=ws)
+    gpos, gq = a.backward(gE)
+    assert _rel_l2(gq.cpu().numpy().astype(np.float64), ref["phi"]) < TOL_FP32
+    a.close()
+    b.close()
+
+
 def test_forces_central_differences_fp64():
     """Forces are -dE/dx of the GPU's own energy (central differences, h = 2^-14,
     particles away from the split-band edges)."""
@@ -375,11 +411,13 @@ def test_forces_central_differences_fp64():
     plan.close()
 
 
-@pytest.mark.parametrize("name,sample,precision", [("uniform1m", None, "fp32"), ("water2m", 256, "fp32"),
+@pytest.mark.parametrize("name,sample,precision", [("uniform1m", None, "fp32"), ("water2m", 2048, "fp32"),
                                                     ("uniform1m", None, "tf32x3"),
-                                                    ("water2m", 256, "tf32x3"),
-                                                    ("plummer8m", 256, "tf32x3"),
-                                                    ("plummer8m", 256, "bf16x3")])
+                                                    ("water2m", 2048, "tf32x3"),
+                                                    ("water2m", 2048, "bf16x3"),
+                                                    ("plummer8m", 2048, "fp32"),
+                                                    ("plummer8m", 2048, "tf32x3"),
+                                                    ("plummer8m", 2048, "bf16x3")])
 def test_parity_full_size_sampled(name, sample, precision):
     """Full-size workloads in the benchmark's launch configuration: integer work
     on every charge; outputs on every particle (uniform1m: the oracle runs the
