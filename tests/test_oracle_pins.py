@@ -646,3 +646,104 @@ def test_inverse_square_converges_and_scales():
     np.testing.assert_allclose(4 * a2["phi"], a1["phi"], rtol=1e-14)
     np.testing.assert_allclose(8 * a2["F"], a1["F"], rtol=1e-14, atol=1e-14 * np.abs(a1["F"]).max())
     assert abs(4 * a2["E"] - a1["E"]) < 1e-14 * abs(a1["E"])
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_split_forces_closed_form_when_every_pair_is_near(n):
+    """§2.3 forces in closed form.  Depth 2, open box: every particle lies
+    inside the 2 x 2 x 2 block of cells around the box centre, more than d from
+    its outer planes, so every pair of charges is in the near field of the
+    other and every interaction list holds only empty cells: the method's
+    potential, energy and forces are then direct sums over the split charges.
+    The split charges are built here from §2.3's definition alone: across a
+    plane b (here the centre planes 1/2) a coordinate x with |x - b| < d becomes
+    n charges at s_k = b + d (-1 + 2 k / (n - 1)) with the one-dimensional
+    Lagrange weights w_k(x) on those nodes (the tensor product over split
+    axes; the middle charge of odd n on the plane counts once in full).  The
+    paper force sums the forces on a particle's charges; the adjoint force
+    along a split axis a is -q sum_k (dW_k/dx_a) phi(s_k)."""
+    rng = np.random.default_rng(100 + n)
+    w, dt = 0.25, 1.0 / 8
+    d = w * dt
+    lo, hi = 0.25 + d + 1e-3, 0.75 - d - 1e-3
+    npart = 48
+    pos = rng.uniform(lo, hi, (npart, 3))
+    # a third of the particles within d of a centre plane on one axis, a sixth
+    # on two axes, one on all three (particles split on all three axes would
+    # share the same n^3 charge positions: coincident charges of different
+    # particles contribute nothing, and so does such a pair below)
+    for i in range(npart):
+        k = 1 if i % 3 == 0 else (2 if i % 6 == 1 else (3 if i == 2 else 0))
+        for a in rng.permutation(3)[:k]:
+            pos[i, a] = 0.5 + rng.uniform(-0.95, 0.95) * d
+    pos = pos.astype(np.float32)
+    q = rng.choice([-1.0, 1.0], npart).astype(np.float32)
+    q[-1] = -np.sum(q[:-1]) if abs(np.sum(q[:-1])) <= 1 else q[-1]
+    r = oracle.fmm(pos, q, (0, 0, 0, 1), depth=2, n=n, continuous=True, dt=dt)
+    assert r["n_points"] > npart  # the configuration splits
+
+    nodes = 0.5 + d * (-1.0 + 2.0 * np.arange(n) / (n - 1))
+
+    def w1(x):
+        g = np.ones(n)
+        dg = np.zeros(n)
+        for k in range(n):
+            for m in range(n):
+                if m == k:
+                    continue
+                f = (x - nodes[m]) / (nodes[k] - nodes[m])
+                dg[k] = dg[k] * f + g[k] / (nodes[k] - nodes[m])
+                g[k] *= f
+        return g, dg
+
+    X = pos.astype(np.float64)
+    charges = []  # per particle: positions (m, 3), weights (m,), d weights / dx (m, 3)
+    for i in range(npart):
+        axes = []
+        for a in range(3):
+            if abs(X[i, a] - 0.5) < d:
+                g, dg = w1(X[i, a])
+                axes.append((nodes, g, dg))
+            else:
+                axes.append((np.array([X[i, a]]), np.ones(1), np.zeros(1)))
+        S, W, DW = [], [], []
+        for kz in range(len(axes[2][0])):
+            for ky in range(len(axes[1][0])):
+                for kx in range(len(axes[0][0])):
+                    ks = (kx, ky, kz)
+                    S.append([axes[a][0][ks[a]] for a in range(3)])
+                    W.append(np.prod([axes[a][1][ks[a]] for a in range(3)]))
+                    DW.append([axes[a][2][ks[a]] * np.prod([axes[b][1][ks[b]] for b in range(3) if b != a])
+                               for a in range(3)])
+        charges.append((np.array(S), np.array(W), np.array(DW)))
+    phi = np.zeros(npart)
+    Fp = np.zeros((npart, 3))
+    Fa = np.zeros((npart, 3))
+    for i in range(npart):
+        Si, Wi, DWi = charges[i]
+        phik = np.zeros(len(Wi))
+        fk = np.zeros((len(Wi), 3))
+        for j in range(npart):
+            if j == i:
+                continue
+            Sj, Wj, _ = charges[j]
+            dv = Si[:, None, :] - Sj[None, :, :]
+            rr = np.sqrt(np.sum(dv * dv, axis=2))
+            inv = np.divide(1.0, rr, out=np.zeros_like(rr), where=rr > 0)
+            phik += np.sum(q[j] * Wj[None, :] * inv, axis=1)
+            fk += np.sum((q[j] * Wj[None, :] * inv ** 3)[:, :, None] * dv, axis=1)
+        phi[i] = np.dot(Wi, phik)
+        Fp[i] = q[i] * np.sum(Wi[:, None] * fk, axis=0)
+        for a in range(3):
+            split = abs(X[i, a] - 0.5) < d
+            Fa[i, a] = -q[i] * np.dot(DWi[:, a], phik) if split else Fp[i, a]
+    E = 0.5 * np.dot(q.astype(np.float64), phi)
+    tol = 1e-12
+    assert np.max(np.abs(r["phi"] - phi)) < tol * np.max(np.abs(phi))
+    assert abs(r["E"] - E) < tol * abs(E)
+    assert np.max(np.abs(r["F_paper"] - Fp)) < tol * np.max(np.abs(Fp))
+    assert np.max(np.abs(r["F"] - Fa)) < tol * np.max(np.abs(Fa))
+    # the two forms differ on split axes only
+    split = np.abs(X - 0.5) < d
+    assert np.max(np.abs(Fa - Fp)[~split]) == 0.0
+    assert np.max(np.abs(Fa - Fp)[split]) > 1e-6 * np.max(np.abs(Fp))
