@@ -6,6 +6,7 @@
 #include <cstring>
 #include <atomic>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "fmm_internal.cuh"
@@ -419,6 +420,7 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     W.phihi = take(P->tc ? pht * p3s * rs : 0);
     W.philo = take(P->tc ? pht * p3s * rs : 0);
     W.occ = take(P->tc ? (size_t)occ_ints(P->depth, P->periodic ? 1 : 2) * 4 : 0);
+    W.delta = take(cont && !P->fp64 ? (size_t)W.cap * 4 : 0);
     int64_t mx = n > W.ncell ? n : W.ncell;
     W.scan_blocks = (int)(mx / 2048 + 2);
     W.scan_tmp = take((size_t)(W.scan_blocks + 1) * 4);
@@ -457,6 +459,7 @@ Ptrs<real> make_ptrs(const WsLayout &W, void *ws) {
     P.phihi = (real *)(b + W.phihi);
     P.philo = (real *)(b + W.philo);
     P.occ = (int *)(b + W.occ);
+    P.delta = (float *)(b + W.delta);
     P.scan_tmp = (int *)(b + W.scan_tmp);
     P.epart = (double *)(b + W.epart);
     return P;
@@ -554,6 +557,9 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     T.sf_hoff = P->sf_hoff;
     int rc = launch_downward<real>(g, C, ptr, W, T, F, tr);
     if (rc) return rc;
+    if constexpr (std::is_same<real, float>::value)
+        if (g.continuous && forces && g.force_mode == FMM_FORCE_ADJOINT)
+            launch_split_delta(g, P->cd, ptr, W, (int)n, pos, F.main, tr);
     if (S.far) {
         cudaEventRecord(S.far_done, S.far);
         cudaStreamWaitEvent(st, S.far_done, 0);
@@ -568,7 +574,7 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
 }
 
 template <typename real>
-int backward_impl(fmm_plan_t P, int64_t n, const float *q, const double *gE, real *grad_pos,
+int backward_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, const double *gE, real *grad_pos,
                   real *grad_q, void *ws, cudaStream_t st, Tracer &tr) {
     WsLayout W = make_layout(P, n);
     Ptrs<real> ptr = make_ptrs<real>(W, ws);
@@ -582,6 +588,9 @@ int backward_impl(fmm_plan_t P, int64_t n, const float *q, const double *gE, rea
     if (g.force_mode == FMM_FORCE_KERNEL) g.force_mode = FMM_FORCE_ADJOINT;
     launch_p2p<real>(g, ptr, W, true, st, tr);
     launch_l2p<real>(g, C, ptr, W, true, st, tr);
+    if constexpr (std::is_same<real, float>::value)
+        if (g.continuous && g.force_mode == FMM_FORCE_ADJOINT)
+            launch_split_delta(g, P->cd, ptr, W, (int)n, pos, st, tr);
     launch_unsplit<real>(g, ptr, W, (int)n, q, nullptr, nullptr, grad_pos, gE, grad_q, true, st, tr);
     return FMM_OK;
 }
@@ -798,9 +807,8 @@ int fmm_eval(fmm_plan_t P, int64_t n, const float *pos, const float *q, void *po
 int fmm_backward(fmm_plan_t P, int64_t n, const float *pos, const float *q,
                  const double *grad_energy, void *grad_pos, void *grad_q, void *workspace,
                  size_t workspace_bytes, void *stream) {
-    (void)pos;
     if (!P || n < 0 || n > P->max_n || !grad_energy) return FMM_ERR_ARG;
-    if (n > 0 && !q) return FMM_ERR_ARG;
+    if (n > 0 && (!q || !pos)) return FMM_ERR_ARG;
     int rc = check_ws(P, n, workspace, workspace_bytes);
     if (rc) return rc;
     if (P->last_ws != workspace || P->last_n != n) return FMM_ERR_STATE;
@@ -808,9 +816,9 @@ int fmm_backward(fmm_plan_t P, int64_t n, const float *pos, const float *q,
     cudaGetLastError();
     Tracer tr = make_tracer(P, st);
     if (P->fp64)
-        rc = backward_impl<double>(P, n, q, grad_energy, (double *)grad_pos, (double *)grad_q, workspace, st, tr);
+        rc = backward_impl<double>(P, n, pos, q, grad_energy, (double *)grad_pos, (double *)grad_q, workspace, st, tr);
     else
-        rc = backward_impl<float>(P, n, q, grad_energy, (float *)grad_pos, (float *)grad_q, workspace, st, tr);
+        rc = backward_impl<float>(P, n, pos, q, grad_energy, (float *)grad_pos, (float *)grad_q, workspace, st, tr);
     P->last = tr;
     if (rc) return rc;
     WsLayout W = make_layout(P, n);

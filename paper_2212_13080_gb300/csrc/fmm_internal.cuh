@@ -75,6 +75,7 @@ struct WsLayout {
     size_t phihi, philo;                  // TF32 split of Phi (tensor-core plans)
     size_t m2l_part;                      // per-offset-group partials of the SIMT contraction
     size_t occ;                           // occupied-cell lists of the contraction (tensor-core plans)
+    size_t delta;                         // per emitted charge of a split particle: phi(s_k) - phi(r)
     size_t scan_tmp, epart;
     size_t total;
     int64_t cap;                          // charge capacity
@@ -250,6 +251,7 @@ struct Ptrs {
     real *phihi, *philo;
     real *m2l_part;
     int *occ;
+    float *delta;  // single-precision plans of the continuous form (adjoint split forces)
     int *scan_tmp;
     double *epart;
 };
@@ -305,6 +307,10 @@ template <typename real>
 void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, const float *q,
                     real *potential, double *energy, real *forces, const double *grad_energy,
                     real *grad_q, bool backward, cudaStream_t st, Tracer &tr);
+// single-precision plans, continuous form, adjoint forces: the potential
+// differences between each split particle's charges (kernels_tree.cu)
+void launch_split_delta(const Geom &g, const Coef<double> &Cd, const Ptrs<float> &P, const WsLayout &W, int n,
+                        const float *pos, cudaStream_t st, Tracer &tr);
 int launch_scan(const int *in, int *out, int m, int *tmp, cudaStream_t st);
 
 // far field (kernels_far.cu)

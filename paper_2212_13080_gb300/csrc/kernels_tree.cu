@@ -1,5 +1,7 @@
 // Binning, split, stable sort by finest cell, recombination of split charges
 // and the FP64 energy reduction.
+#include <type_traits>
+
 #include "fmm_internal.cuh"
 #include "lagrange.cuh"
 
@@ -530,6 +532,245 @@ void launch_sort(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, c
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint forces of split particles, difference form (§2.3).  Along a split
+// axis the adjoint force is -q sum_k (dW_k/dx) phi(s_k); the weights sum to
+// one, so their derivatives sum to zero and the same force is
+// -q sum_k (dW_k/dx) D_k with D_k = phi(s_k) - phi(r) for any reference point
+// r.  dW/dx ~ 1/(2d) amplifies independent errors of the phi(s_k): FP32
+// rounding of each charge's near- and far-field sums, and (for even p) the
+// single-precision rounding of the charges' positions (the nodes plane +
+// d(-1 + 2k/(p-1)) are not binary fractions).  This kernel forms the D_k
+// directly, for split particles only: r is the particle's first charge (the
+// node plane - d of every split axis, exact in single precision), s_k the
+// exact node (double precision); the near-field part sums, over the sources
+// both points see, q (1/|s_k - x| - 1/|r - x|) = -q n / (r0 rk (r0 + rk)) with
+// n = |s_k - x|^2 - |r - x|^2 = delta . (delta - 2 (x - r)), delta = s_k - r
+// (a small number with a small relative error), and the plain terms of the
+// sources only one of them sees (cells adjacent to one of the two cells the
+// segment crosses); the far-field part is the difference of the two points'
+// functionals g(t) . L of their own cells, each evaluated in double precision.
+// Same-particle and coincident charges are skipped as in the near field.
+// One warp per split particle; each warp takes 32 consecutive particles.
+// POW: the pair function 1/r (1) or 1/r^2 (2).
+// ---------------------------------------------------------------------------
+
+// exact node of entry e of split axis A: the side (0 lower, 1 upper cell of
+// the plane; 0 for an axis that is not split) and the cell-local coordinate
+__device__ __forceinline__ void split_entry_exact(const Geom &g, const AxisInfo &A, int e, int &side,
+                                                  double &t, float &tf) {
+    if (A.mode == 0) {
+        side = 0;
+        t = (double)A.t;
+        tf = A.t;
+        return;
+    }
+    const int p = g.p;
+    int k;
+    bool half = false;
+    if (p & 1) {
+        const int mid = (p - 1) / 2;
+        if (e < mid) {
+            k = e;
+            side = 0;
+        } else if (e == mid) {
+            k = mid;
+            side = 0;
+            half = true;
+        } else if (e == mid + 1) {
+            k = mid;
+            side = 1;
+            half = true;
+        } else {
+            k = e - 1;
+            side = 1;
+        }
+    } else {
+        k = e;
+        side = (2 * k < p - 1) ? 0 : 1;
+    }
+    const double dt = (double)g.dtf, s = (double)(2 * k) / (double)(p - 1) - 1.0;
+    t = half ? (side ? 0.0 : 1.0) : (side ? s * dt : 1.0 + s * dt);
+    // the emitted charge's single-precision coordinate: the expression of split_entry
+    const float sf = (float)(2 * k) / (float)(p - 1) - 1.0f, dtf = g.dtf;
+    tf = half ? (side ? 0.0f : 1.0f) : (side ? sf * dtf : 1.0f + sf * dtf);
+}
+
+// x - s along one axis, the source x at coordinate v of a cell `shift` cells
+// from the charge's cell, the charge at t = th + tl of its own cell: each case
+// subtracts in the frame where the nearby operands are exact (Sterbenz)
+__device__ __forceinline__ float sd_axis_diff(float v, int shift, float th, float tl) {
+    const float d = shift == 1 ? v - (th - 1.0f) : (shift == -1 ? (v - 1.0f) - th : (v + (float)shift) - th);
+    return d - tl;
+}
+
+#define SD_WARPS 8  // warps per CTA
+
+template <int POW, int CH>
+__global__ void __launch_bounds__(32 * SD_WARPS) k_split_delta(Geom g, Coef<double> Cd, int n, const float *__restrict__ pos,
+                                                           const int *__restrict__ count, const int *__restrict__ offset,
+                                                           const int *__restrict__ leaf_start,
+                                                           const float4 *__restrict__ s_pt, const int *__restrict__ s_origin,
+                                                           const float *__restrict__ loc_leaf, float *__restrict__ delta,
+                                                           const WsHeader *hdr) {
+    // double-precision weights of every distinct coordinate of the particle's
+    // charges: axis a, entry e (the reference point is entry 0 of every axis)
+    __shared__ double wsm[SD_WARPS][3][FMM_MAXP + 1][FMM_MAXP];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int i0 = (blockIdx.x * SD_WARPS + wl) * 32;
+    if (i0 >= n) return;
+    const int S = g.S, p = g.p, p3 = g.p3;
+    const int n_eff = hdr->n_eff;
+    const int mine = i0 + lane < n && count[i0 + lane] > 1 && offset[i0 + lane] + count[i0 + lane] <= n_eff;
+    unsigned todo = __ballot_sync(0xffffffffu, mine);
+    double (*W)[FMM_MAXP + 1][FMM_MAXP] = wsm[wl];
+    while (todo) {
+        const int i = i0 + __ffs(todo) - 1;
+        todo &= todo - 1;
+        // the particle's axes: binned cell, split geometry, base = the lower cell
+        // of each split axis (unwrapped), the binned cell otherwise
+        AxisInfo A[3];
+        int base[3], sp[3];
+        float R[3];  // the reference point (first charge) in the base frame
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            int st = 0, c;
+            float t;
+            bin_axis(g, pos[3 * i + a], a, t, c, st);
+            A[a] = split_axis_info(g, c, t);
+            sp[a] = A[a].mode != 0;
+            base[a] = A[a].mode == 1 ? c - 1 : c;
+            R[a] = sp[a] ? 1.0f - g.dtf : t;  // node plane - d: exact in single precision
+        }
+        const int m = A[0].m * A[1].m * A[2].m, e0 = offset[i];
+        // weights: lane = a * 8 + e computes entry e of axis a
+        {
+            const int a = lane >> 3, e = lane & 7;
+            if (a < 3 && e < A[a].m) {
+                int side;
+                double t;
+                float tfl;
+                split_entry_exact(g, A[a], e, side, t, tfl);
+                double w[FMM_MAXP];
+                lag_weights<double>(Cd, p, t, w);
+#pragma unroll
+                for (int k = 0; k < FMM_MAXP; k++) W[a][e][k] = w[k];
+            }
+        }
+        __syncwarp();
+        double far0 = 0.0;  // far field at the reference point (entry 0 of every axis)
+        {
+            const int64_t cr = loc_cell(g.depth, (base[0] + S) % S, (base[1] + S) % S, (base[2] + S) % S);
+            for (int o = lane; o < p3; o += 32)
+                far0 += W[0][0][o % p] * W[1][0][(o / p) % p] * W[2][0][o / (p * p)] * (double)loc_leaf[cr * p3 + o];
+        }
+        for (int c0 = 0; c0 < m; c0 += CH) {
+            // the chunk's charges: entries, sides (bit a: upper cell of axis a),
+            // offset from the reference point, far-field difference
+            float dl[CH][3], th[CH][3], tl[CH][3], tf[CH][3];
+            int sd[CH];
+            double fd[CH];
+#pragma unroll
+            for (int k = 0; k < CH; k++) {
+                int le = min(c0 + k, m - 1);
+                const int ex = le % A[0].m;
+                le /= A[0].m;
+                const int e3[3] = {ex, le % A[1].m, le / A[1].m};
+                int side[3];
+                double tk[3];
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    split_entry_exact(g, A[a], e3[a], side[a], tk[a], tf[k][a]);
+                    dl[k][a] = (float)(((double)side[a] + tk[a]) - (double)R[a]);
+                    th[k][a] = (float)tk[a];
+                    tl[k][a] = (float)(tk[a] - (double)th[k][a]);
+                }
+                sd[k] = side[0] | (side[1] << 1) | (side[2] << 2);
+                const int64_t ck = loc_cell(g.depth, (base[0] + side[0] + S) % S, (base[1] + side[1] + S) % S,
+                                            (base[2] + side[2] + S) % S);
+                double f = 0.0;
+                for (int o = lane; o < p3; o += 32)
+                    f += W[0][e3[0]][o % p] * W[1][e3[1]][(o / p) % p] * W[2][e3[2]][o / (p * p)] *
+                         (double)loc_leaf[ck * p3 + o];
+                fd[k] = f - far0;
+            }
+            // near field: the cells adjacent to any of the particle's cells
+            float acc[CH], cmp[CH];
+#pragma unroll
+            for (int k = 0; k < CH; k++) acc[k] = cmp[k] = 0.0f;
+            for (int uz = -1; uz <= 1 + sp[2]; uz++)
+                for (int uy = -1; uy <= 1 + sp[1]; uy++)
+                    for (int ux = -1; ux <= 1 + sp[0]; ux++) {
+                        int gx = base[0] + ux, gy = base[1] + uy, gz = base[2] + uz;
+                        if (g.periodic) {
+                            gx = (gx + S) % S;
+                            gy = (gy + S) % S;
+                            gz = (gz + S) % S;
+                        } else if (gx < 0 || gy < 0 || gz < 0 || gx >= S || gy >= S || gz >= S) {
+                            continue;
+                        }
+                        const uint32_t key = morton_encode(gx, gy, gz);
+                        const int ja = leaf_start[key], jb = leaf_start[key + 1];
+                        const bool inR = ux <= 1 && uy <= 1 && uz <= 1;
+                        for (int j = ja + lane; j < jb; j += 32) {
+                            if (s_origin[j] == i) continue;
+                            const float4 v = s_pt[j];
+                            // x - r (the reference is exact in single precision, side 0)
+                            const float d0x = sd_axis_diff(v.x, ux, R[0], 0.0f), d0y = sd_axis_diff(v.y, uy, R[1], 0.0f),
+                                        d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
+                            const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
+#pragma unroll
+                            for (int k = 0; k < CH; k++) {
+                                const int sx = sd[k] & 1, sy = (sd[k] >> 1) & 1, sz = sd[k] >> 2;
+                                const bool inK = ux >= sx - 1 && ux <= sx + 1 && uy >= sy - 1 && uy <= sy + 1 &&
+                                                 uz >= sz - 1 && uz <= sz + 1;
+                                // x - s_k directly, accurate also when x is close to s_k
+                                const float dkx = sd_axis_diff(v.x, ux - sx, th[k][0], tl[k][0]),
+                                            dky = sd_axis_diff(v.y, uy - sy, th[k][1], tl[k][1]),
+                                            dkz = sd_axis_diff(v.z, uz - sz, th[k][2], tl[k][2]);
+                                // coincident with the emitted charge (the single-precision
+                                // positions the near field compares): skipped as there
+                                const bool zk = sd_axis_diff(v.x, ux - sx, tf[k][0], 0.0f) == 0.0f &&
+                                                sd_axis_diff(v.y, uy - sy, tf[k][1], 0.0f) == 0.0f &&
+                                                sd_axis_diff(v.z, uz - sz, tf[k][2], 0.0f) == 0.0f;
+                                // |s_k - x|^2 - |r - x|^2 = delta . (delta - 2 (x - r))
+                                const float nm = dl[k][0] * (dl[k][0] - 2.0f * d0x) + dl[k][1] * (dl[k][1] - 2.0f * d0y) +
+                                                 dl[k][2] * (dl[k][2] - 2.0f * d0z);
+                                const float rk2 = dkx * dkx + dky * dky + dkz * dkz;
+                                float term = 0.0f;
+                                if (inK && inR && !zk && r02 > 0.0f && rk2 > 0.0f) {
+                                    if (POW == 2) {
+                                        term = -v.w * nm / (r02 * rk2);
+                                    } else {
+                                        const float r0 = sqrtf(r02), rk = sqrtf(rk2);
+                                        term = -v.w * nm / (r0 * rk * (r0 + rk));
+                                    }
+                                } else {
+                                    if (inK && !zk && rk2 > 0.0f) term += POW == 2 ? v.w / rk2 : v.w / sqrtf(rk2);
+                                    if (inR && r02 > 0.0f) term -= POW == 2 ? v.w / r02 : v.w / sqrtf(r02);
+                                }
+                                const float y = term - cmp[k], tt = acc[k] + y;  // compensated sum
+                                cmp[k] = (tt - acc[k]) - y;
+                                acc[k] = tt;
+                            }
+                        }
+                    }
+            const double Sp = POW == 2 ? (double)S * S : (double)S;
+#pragma unroll
+            for (int k = 0; k < CH; k++) {
+                double v = (double)acc[k] - (double)cmp[k];
+                double f = fd[k];
+                for (int o = 16; o > 0; o >>= 1) {
+                    v += __shfl_xor_sync(0xffffffffu, v, o);
+                    f += __shfl_xor_sync(0xffffffffu, f, o);
+                }
+                if (lane == 0 && c0 + k < m) delta[e0 + c0 + k] = (float)(Sp * v + f);
+            }
+        }
+        __syncwarp();  // the weights table is rewritten for the next particle
+    }
+}
+
+// ---------------------------------------------------------------------------
 // recombination of the split charges into their particles (§2.3), scaling to
 // physical units, and the FP64 energy E = 1/2 sum_i q_i phi_i.
 //   phi_i = sum_k W_k phi(s_k)
@@ -563,8 +804,8 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
                           const int *__restrict__ offset,
                           const int *__restrict__ count, const unsigned char *__restrict__ axes,
                           const typename Vec4<real>::T *__restrict__ e_wd,
-                          const typename Vec4<real>::T *__restrict__ out_e, real *__restrict__ potential,
-                          real *__restrict__ forces, real *__restrict__ epart,
+                          const typename Vec4<real>::T *__restrict__ out_e, const float *__restrict__ delta,
+                          real *__restrict__ potential, real *__restrict__ forces, real *__restrict__ epart,
                           const double *__restrict__ grad_energy, real *__restrict__ grad_q,
                           int backward, real sphi, real sF) {
     // sphi = 1/L and sF = 1/L^2 come from the host: no FP64 arithmetic per thread
@@ -592,9 +833,12 @@ __global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__res
                 Sx += o.y;
                 Sy += o.z;
                 Sz += o.w;
-                Nx += d.y * o.x;
-                Ny += d.z * o.x;
-                Nz += d.w * o.x;
+                // split axes: the weights' derivatives against phi(s_k), or
+                // against the differences phi(s_k) - phi(r) where they were formed
+                const real D = (delta && m > 1) ? (real)delta[e] : o.x;
+                Nx += d.y * D;
+                Ny += d.z * D;
+                Nz += d.w * D;
             }
             // paper and force-kernel forces: the sum of the split charges' forces
             unsigned ax = g.force_mode != FMM_FORCE_ADJOINT ? 0u : axes[i];
@@ -696,13 +940,36 @@ void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n
     const double iL = 1.0 / g.L, sphi = g.power == 2 ? iL * iL : iL;
     k_unsplit<real><<<nb, UNSPLIT_BS, 0, st>>>(
         g, P.hdr, n, q, g.continuous ? P.offset : nullptr, P.count, P.axes,
-        g.continuous ? P.e_wd : nullptr, P.out_e, potential, forces, ep, grad_energy, grad_q,
+        g.continuous ? P.e_wd : nullptr, P.out_e,
+        (std::is_same<real, float>::value && g.continuous && g.force_mode == FMM_FORCE_ADJOINT) ? P.delta : nullptr,
+        potential, forces, ep, grad_energy, grad_q,
         backward ? 1 : 0, (real)sphi, (real)(sphi * iL));
     tr.count();
     if (ep) {
         k_energy_final<real><<<1, 1024, 0, st>>>(ep, nb, energy);
         tr.count();
     }
+    tr.end();
+}
+
+void launch_split_delta(const Geom &g, const Coef<double> &Cd, const Ptrs<float> &P, const WsLayout &W, int n,
+                        const float *pos, cudaStream_t st, Tracer &tr) {
+    if (n <= 0) return;
+    tr.begin(FMM_STAGE_UNSPLIT, st);
+    const int nb = (n + 32 * SD_WARPS - 1) / (32 * SD_WARPS);  // 32 particles per warp
+    const float *leaf = reinterpret_cast<const float *>(P.loc) + W.loc_level[g.depth];
+    // charges per pass: the charges of a particle split along one axis
+    const int ch = g.p <= 4 ? 4 : (g.p <= 6 ? 6 : 8);
+#define SD_LAUNCH(POW, CH)                                                                                  \
+    k_split_delta<POW, CH><<<nb, 32 * SD_WARPS, 0, st>>>(g, Cd, n, pos, P.count, P.offset, P.leaf_start, P.s_pt, \
+                                                        P.s_origin, leaf, P.delta, P.hdr)
+    if (g.power == 2) {
+        if (ch == 4) SD_LAUNCH(2, 4); else if (ch == 6) SD_LAUNCH(2, 6); else SD_LAUNCH(2, 8);
+    } else {
+        if (ch == 4) SD_LAUNCH(1, 4); else if (ch == 6) SD_LAUNCH(1, 6); else SD_LAUNCH(1, 8);
+    }
+#undef SD_LAUNCH
+    tr.count();
     tr.end();
 }
 

@@ -95,8 +95,6 @@ def test_parity_inverse_square(case, precision, force_mode):
                max_n=len(q), force_mode=force_mode, kernel="inverse_square")
     r = plan.eval(torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda())
     tol = TOL[precision]
-    if precision != "fp64" and cont and force_mode == "adjoint":
-        tol = 1e-5  # adjoint forces of split charges in FP32 (as for 1/r)
     assert _rel(r["potential"].cpu().numpy().astype(np.float64), ref["phi"]) < TOL[precision]
     assert _rel(r["forces"].cpu().numpy().astype(np.float64), ref["F"]) < tol
     assert abs(r["energy"].item() - ref["E"]) < TOL[precision] * abs(ref["E"])
