@@ -76,6 +76,7 @@ struct WsLayout {
     size_t m2l_part;                      // per-offset-group partials of the SIMT contraction
     size_t occ;                           // occupied-cell lists of the contraction (tensor-core plans)
     size_t delta;                         // per emitted charge of a split particle: phi(s_k) - phi(r)
+    size_t slist;                         // the split particles (count, then indices)
     size_t scan_tmp, epart;
     size_t total;
     int64_t cap;                          // charge capacity
@@ -252,6 +253,7 @@ struct Ptrs {
     real *m2l_part;
     int *occ;
     float *delta;  // single-precision plans of the continuous form (adjoint split forces)
+    int *slist;
     int *scan_tmp;
     double *epart;
 };

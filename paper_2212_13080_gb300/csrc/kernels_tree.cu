@@ -540,28 +540,48 @@ void launch_sort(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, c
 // rounding of each charge's near- and far-field sums, and (for even p) the
 // single-precision rounding of the charges' positions (the nodes plane +
 // d(-1 + 2k/(p-1)) are not binary fractions).  This kernel forms the D_k
-// directly, for split particles only: r is the particle's first charge (the
+// directly, for split particles only, r = the particle's first charge (the
 // node plane - d of every split axis, exact in single precision), s_k the
-// exact node (double precision); the near-field part sums, over the sources
-// both points see, q (1/|s_k - x| - 1/|r - x|) = -q n / (r0 rk (r0 + rk)) with
-// n = |s_k - x|^2 - |r - x|^2 = delta . (delta - 2 (x - r)), delta = s_k - r
-// (a small number with a small relative error), and the plain terms of the
-// sources only one of them sees (cells adjacent to one of the two cells the
-// segment crosses); the far-field part is the difference of the two points'
-// functionals g(t) . L of their own cells, each evaluated in double precision.
+// exact node (a single-precision pair).
+//
+// One split axis a (nearly every split particle): the charges differ from r
+// by delta_k along a only.  The neighbour cells form three slabs along a:
+// u = -1 (seen by r and the charges below the plane), u = 0..1 (seen by all),
+// u = 2 (seen by the charges above).  For a source farther than 16 max|delta|
+// from r, 1/|s_k - x| = sum_n delta_k^n c_n(mu) / rho^(n+1) (Legendre; for
+// 1/r^2 the Chebyshev U_n and one more power), rho = |x - r|, mu its cosine
+// with the axis, so every slab reduces to seven moments M_n = sum q c_n /
+// rho^(n+1), n = 0..6, independent of the charges (h^7 < 4e-9 is dropped);
+// the few sources closer than that to r take direct terms per charge.  Then
+// D_k = sum_{n>=1} delta_k^n (M_n(middle) + M_n(the other slab its side sees))
+// + direct terms, and above the plane + M_0(u = 2) - M_0(u = -1).  Far field:
+// g(s_k) . L - g(r) . L = (W_a(s_k) - W_a(r)) W_b W_c . L of the lower cell
+// (below), or (W_a(s_k) - e_0) W_b W_c . L_upper + X with X = g(plane) .
+// L_upper - g(r) . L_lower (above): the weight differences are small and
+// exact to their own rounding, so these sums run in single precision, and
+// only X (with the two M_0, which cancel against it) in double precision.
+// Several split axes (a fraction of a percent): direct terms, chunks of CH
+// charges per task, near-field part q (1/|s_k - x| - 1/|r - x|) = -q n /
+// (r0 rk (r0 + rk)) with n = delta . (delta - 2 (x - r)) where both see the
+// source, plain terms where one does, far field in double precision.
 // Same-particle and coincident charges are skipped as in the near field.
-// One warp per split particle; each warp takes 32 consecutive particles.
+// Persistent warps take one task each: the chunks of the several-axis
+// particles first (the longest), then one task per one-axis particle.
 // POW: the pair function 1/r (1) or 1/r^2 (2).
 // ---------------------------------------------------------------------------
 
-// exact node of entry e of split axis A: the side (0 lower, 1 upper cell of
-// the plane; 0 for an axis that is not split) and the cell-local coordinate
-__device__ __forceinline__ void split_entry_exact(const Geom &g, const AxisInfo &A, int e, int &side,
-                                                  double &t, float &tf) {
+// Entry e of split axis A: the side (0 lower, 1 upper cell of the plane; 0
+// for an axis that is not split), the exact node as a single-precision pair
+// t = th + tl (error-free transformations: the quotient 2k/(p-1) with its
+// remainder, TwoSum for the shifts; dt is a power of two), and the
+// single-precision coordinate the emission computed (the expression of
+// split_entry), which the near field compares for coincidence.
+__device__ __forceinline__ void split_entry_df(const Geom &g, const AxisInfo &A, int e, int &side, float &th,
+                                               float &tl, float &tf) {
     if (A.mode == 0) {
         side = 0;
-        t = (double)A.t;
-        tf = A.t;
+        th = tf = A.t;
+        tl = 0.0f;
         return;
     }
     const int p = g.p;
@@ -588,11 +608,28 @@ __device__ __forceinline__ void split_entry_exact(const Geom &g, const AxisInfo 
         k = e;
         side = (2 * k < p - 1) ? 0 : 1;
     }
-    const double dt = (double)g.dtf, s = (double)(2 * k) / (double)(p - 1) - 1.0;
-    t = half ? (side ? 0.0 : 1.0) : (side ? s * dt : 1.0 + s * dt);
-    // the emitted charge's single-precision coordinate: the expression of split_entry
-    const float sf = (float)(2 * k) / (float)(p - 1) - 1.0f, dtf = g.dtf;
+    const float dtf = g.dtf;
+    const float sf = (float)(2 * k) / (float)(p - 1) - 1.0f;
     tf = half ? (side ? 0.0f : 1.0f) : (side ? sf * dtf : 1.0f + sf * dtf);
+    if (half) {
+        th = side ? 0.0f : 1.0f;
+        tl = 0.0f;
+        return;
+    }
+    const float num = (float)(2 * k), den = (float)(p - 1);
+    const float qh = __fdiv_rn(num, den), ql = __fdiv_rn(fmaf(-qh, den, num), den);  // 2k/(p-1)
+    const float sh = __fsub_rn(qh, 1.0f), bb = __fsub_rn(sh, qh);                      // s = q - 1
+    const float sl = __fadd_rn(__fadd_rn(__fsub_rn(qh, __fsub_rn(sh, bb)), __fsub_rn(-1.0f, bb)), ql);
+    const float ah = __fmul_rn(sh, dtf), al = __fmul_rn(sl, dtf);                    // s dt (exact)
+    if (side) {
+        th = __fadd_rn(ah, al);
+        tl = __fsub_rn(al, __fsub_rn(th, ah));
+    } else {  // 1 + s dt
+        const float t1 = __fadd_rn(1.0f, ah), b2 = __fsub_rn(t1, 1.0f);
+        const float e2 = __fadd_rn(__fadd_rn(__fsub_rn(1.0f, __fsub_rn(t1, b2)), __fsub_rn(ah, b2)), al);
+        th = __fadd_rn(t1, e2);
+        tl = __fsub_rn(e2, __fsub_rn(th, t1));
+    }
 }
 
 // x - s along one axis, the source x at coordinate v of a cell `shift` cells
@@ -603,29 +640,155 @@ __device__ __forceinline__ float sd_axis_diff(float v, int shift, float th, floa
     return d - tl;
 }
 
-#define SD_WARPS 8  // warps per CTA
+#define SD_WARPS 4  // warps per CTA
+
+// The split particles as tasks.  slist[0] = the number split along one axis,
+// listed from slist[2] up; slist[1] = the number split along two or three,
+// listed from slist[n + 1] down (each particle is one or the other, so the
+// two never meet).  m1 = the charges of a particle split along one axis.
+__global__ void k_split_list(int n, int m1, const int *__restrict__ count, const int *__restrict__ offset,
+                             const WsHeader *hdr, int *__restrict__ slist) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    const bool mine = i < n && count[i] > 1 && offset[i] + count[i] <= hdr->n_eff;
+    const bool one = mine && count[i] <= m1;
+    const unsigned b1 = __ballot_sync(0xffffffffu, one), bm = __ballot_sync(0xffffffffu, mine && !one);
+    int base1 = 0, basem = 0;
+    if (lane == 0 && b1) base1 = atomicAdd(&slist[0], __popc(b1));
+    if (lane == 0 && bm) basem = atomicAdd(&slist[1], __popc(bm));
+    base1 = __shfl_sync(0xffffffffu, base1, 0);
+    basem = __shfl_sync(0xffffffffu, basem, 0);
+    const unsigned below = (1u << lane) - 1u;
+    if (one)
+        slist[2 + base1 + __popc(b1 & below)] = i;
+    else if (mine)
+        slist[n + 1 - (basem + __popc(bm & below))] = i;
+}
+
+#define SD_NM 7                 // series terms n = 0..6
+#define SD_NMOM (3 * SD_NM)     // moments of the three slabs
+
+// (h, l) += (bh, bl) in single-precision pair arithmetic (TwoSum of the high
+// parts, the low parts and the error added to the low part)
+__device__ __forceinline__ void sd_two_sum(float &h, float &l, float bh, float bl) {
+    const float s = h + bh, v = s - h, e = (h - (s - v)) + (bh - v), t = e + l + bl;
+    h = s + t;
+    l = t - (h - s);
+}
+#define SD_KMAX (FMM_MAXP + 1)  // charges of a particle split along one axis, at most
+
+// q (1/|s_k - x|^POW - 1/|r - x|^POW) for a source x seen by r (inR) and/or by
+// the charge s_k (its cells: side bits sdk); d0 = x - r, r02 = |d0|^2, ri0 =
+// 1/|d0| (0 where x = r).  kk: s_k - r (3), s_k as th (3) + tl (3), and the
+// single-precision coordinate the emission computed (3).
+template <int POW>
+__device__ __forceinline__ float sd_pair_term(const float4 &v, int ux, int uy, int uz, float d0x, float d0y,
+                                              float d0z, float r02, float ri0, bool inR, const float *kk,
+                                              int sdk) {
+    const int sx = sdk & 1, sy = (sdk >> 1) & 1, sz = sdk >> 2;
+    const bool inK = ux >= sx - 1 && ux <= sx + 1 && uy >= sy - 1 && uy <= sy + 1 && uz >= sz - 1 && uz <= sz + 1;
+    // x - s_k directly, accurate also when x is close to s_k
+    const float dkx = sd_axis_diff(v.x, ux - sx, kk[3], kk[6]), dky = sd_axis_diff(v.y, uy - sy, kk[4], kk[7]),
+                dkz = sd_axis_diff(v.z, uz - sz, kk[5], kk[8]);
+    const float rk2 = dkx * dkx + dky * dky + dkz * dkz;
+    // coincident with the emitted charge (the single-precision positions the
+    // near field compares): skipped as there.  Only a charge within a few ulps
+    // of s_k can be.
+    bool zk = false;
+    if (rk2 < 1e-12f)
+        zk = sd_axis_diff(v.x, ux - sx, kk[9], 0.0f) == 0.0f && sd_axis_diff(v.y, uy - sy, kk[10], 0.0f) == 0.0f &&
+             sd_axis_diff(v.z, uz - sz, kk[11], 0.0f) == 0.0f;
+    const float rik = (rk2 > 0.0f && !zk) ? rsqrtf(rk2) : 0.0f;
+    float term = 0.0f;
+    if (inK && inR && rik > 0.0f && ri0 > 0.0f) {
+        // |s_k - x|^2 - |r - x|^2 = delta . (delta - 2 (x - r)): a small number
+        // with a small relative error
+        const float nm = kk[0] * (kk[0] - 2.0f * d0x) + kk[1] * (kk[1] - 2.0f * d0y) + kk[2] * (kk[2] - 2.0f * d0z);
+        if (POW == 2)
+            term = -v.w * nm * (ri0 * ri0) * (rik * rik);
+        else
+            term = -v.w * nm * ri0 * rik * __fdividef(1.0f, r02 * ri0 + rk2 * rik);
+    } else {
+        if (inK) term += POW == 2 ? v.w * rik * rik : v.w * rik;
+        if (inR) term -= POW == 2 ? v.w * ri0 * ri0 : v.w * ri0;
+    }
+    return term;
+}
+
+// The direct terms of one source x of the middle slab (seen by r and every
+// charge) close to r, added to gs[k] for the m charges: rare, kept out of line.
+template <int POW>
+__device__ __noinline__ void sd_direct_terms(const float4 v, int ux, int uy, int uz, float d0x, float d0y, float d0z,
+                                             float r02, float ri0, int m, const float *kq, const int *ks, float *gs) {
+    for (int k = 0; k < m; k++)
+        atomicAdd(&gs[k], sd_pair_term<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, true, kq + 12 * k, ks[k]));
+}
+
+// Series terms of one source for a point s = r + h |x - r| e_a on the split
+// axis a: 1/|s - x|^POW = sum_n h^n c_n(mu) / |x - r|^POW, mu = (x - r)_a /
+// |x - r| (the generating functions of the Legendre polynomials P_n for 1/r
+// and of the Chebyshev polynomials U_n of the second kind for 1/r^2).  With h
+// = delta / rho: t_n = q c_n(mu) / rho^(n + POW), and 1/|s - x|^POW = sum_n
+// delta^n t_n / q.  da = (x - r)_a, ri = 1/rho.
+template <int POW>
+__device__ __forceinline__ void sd_series_terms(float q, float da, float ri, float (&t)[SD_NM]) {
+    const float mu = da * ri;
+    float c[SD_NM];
+    c[0] = 1.0f;
+    c[1] = POW == 2 ? 2.0f * mu : mu;
+#pragma unroll
+    for (int k = 2; k < SD_NM; k++)
+        c[k] = POW == 2 ? fmaf(2.0f * mu, c[k - 1], -c[k - 2])
+                        : fmaf((float)(2 * k - 1) / (float)k * mu, c[k - 1], -(float)(k - 1) / (float)k * c[k - 2]);
+    float gq = POW == 2 ? q * ri * ri : q * ri;
+#pragma unroll
+    for (int k = 0; k < SD_NM; k++) {
+        t[k] = gq * c[k];
+        gq *= ri;
+    }
+}
+
+// The offset u (each in -1..2) of cell c of the neighbour table whose axis o2
+// varies slowest, then o1, then o0 (extents n0, n1).
+__device__ __forceinline__ void sd_cell_offset(int c, int o0, int o1, int n0, int n1, int &ux, int &uy, int &uz) {
+    const int a = c % n0 - 1, b = (c / n0) % n1 - 1, d = c / (n0 * n1) - 1;
+    ux = o0 == 0 ? a : (o1 == 0 ? b : d);
+    uy = o0 == 1 ? a : (o1 == 1 ? b : d);
+    uz = o0 == 2 ? a : (o1 == 2 ? b : d);
+}
 
 template <int POW, int CH>
-__global__ void __launch_bounds__(32 * SD_WARPS) k_split_delta(Geom g, Coef<double> Cd, int n, const float *__restrict__ pos,
-                                                           const int *__restrict__ count, const int *__restrict__ offset,
-                                                           const int *__restrict__ leaf_start,
-                                                           const float4 *__restrict__ s_pt, const int *__restrict__ s_origin,
-                                                           const float *__restrict__ loc_leaf, float *__restrict__ delta,
-                                                           const WsHeader *hdr) {
-    // double-precision weights of every distinct coordinate of the particle's
-    // charges: axis a, entry e (the reference point is entry 0 of every axis)
+__global__ void __launch_bounds__(32 * SD_WARPS, 5)
+    k_split_delta(Geom g, Coef<double> Cd, int n, const float *__restrict__ pos, const int *__restrict__ count,
+                  const int *__restrict__ offset, const int *__restrict__ leaf_start, const float4 *__restrict__ s_pt,
+                  const int *__restrict__ s_origin, const float *__restrict__ loc_leaf, float *__restrict__ delta,
+                  const int *__restrict__ slist) {
+    // double-precision weights: every distinct coordinate of the particle's
+    // charges (axis a, entry e) for a particle split along several axes; the
+    // per-axis rows and weight differences for one split axis (carved below)
     __shared__ double wsm[SD_WARPS][3][FMM_MAXP + 1][FMM_MAXP];
+    __shared__ int csm[SD_WARPS][64 + 65 + 64];        // neighbour cells: first slot, count prefix, offset
+    __shared__ float ksm[SD_WARPS][SD_KMAX * 12];      // the charges (one split axis) or one chunk of them
+    __shared__ int ssm[SD_WARPS][SD_KMAX];             // their sides (bit a: the upper cell of axis a)
+    __shared__ float gsm[SD_WARPS][SD_KMAX];           // near-source terms per charge (one split axis)
+    __shared__ float msm[SD_WARPS][2][SD_NMOM];        // the moments (high, low) per slab and order
+    __shared__ float csum[SD_WARPS][2][CH][32];        // per-lane compensated sums per charge (several axes)
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int i0 = (blockIdx.x * SD_WARPS + wl) * 32;
-    if (i0 >= n) return;
     const int S = g.S, p = g.p, p3 = g.p3;
-    const int n_eff = hdr->n_eff;
-    const int mine = i0 + lane < n && count[i0 + lane] > 1 && offset[i0 + lane] + count[i0 + lane] <= n_eff;
-    unsigned todo = __ballot_sync(0xffffffffu, mine);
-    double (*W)[FMM_MAXP + 1][FMM_MAXP] = wsm[wl];
-    while (todo) {
-        const int i = i0 + __ffs(todo) - 1;
-        todo &= todo - 1;
+    const int n1 = slist[0], nmul = slist[1];
+    const int m1 = p + (p & 1);
+    const int nchm = (m1 * m1 * m1 + CH - 1) / CH;  // chunks of a particle split along several axes, at most
+    const long long ntask = (long long)nmul * nchm + n1;
+    // persistent warps over the tasks: the chunks of the particles split along
+    // several axes (the longest) first, then one task per particle split along one
+    for (long long tk = blockIdx.x * SD_WARPS + wl; tk < ntask; tk += (long long)gridDim.x * SD_WARPS) {
+        int i, c0 = 0;
+        if (tk < (long long)nmul * nchm) {
+            i = slist[n + 1 - (int)(tk / nchm)];
+            c0 = (int)(tk % nchm) * CH;
+            if (c0 >= count[i]) continue;  // warp-uniform: past this particle's charges
+        } else {
+            i = slist[2 + (int)(tk - (long long)nmul * nchm)];
+        }
         // the particle's axes: binned cell, split geometry, base = the lower cell
         // of each split axis (unwrapped), the binned cell otherwise
         AxisInfo A[3];
@@ -642,131 +805,373 @@ __global__ void __launch_bounds__(32 * SD_WARPS) k_split_delta(Geom g, Coef<doub
             R[a] = sp[a] ? 1.0f - g.dtf : t;  // node plane - d: exact in single precision
         }
         const int m = A[0].m * A[1].m * A[2].m, e0 = offset[i];
-        // weights: lane = a * 8 + e computes entry e of axis a
+        const int a1 = sp[0] + sp[1] + sp[2] == 1 ? (sp[0] ? 0 : (sp[1] ? 1 : 2)) : -1;  // the one split axis
+        // the neighbour table: the cells adjacent to any of the particle's cells,
+        // resolved once by all lanes (first sorted slot, prefix of the charge
+        // counts, offset u from the base cell packed 3 x 4 bits); with one split
+        // axis it varies slowest, so that its slabs u = -1, 0..1, 2 are
+        // contiguous (cells 0..8, 9..26, 27..35)
+        int o0 = 0, o1 = 1;
+        if (a1 == 0) {
+            o0 = 1;
+            o1 = 2;
+        } else if (a1 == 1) {
+            o1 = 2;
+        }
+        const int nd0 = 3 + sp[o0], nd1 = 3 + sp[o1];
+        const int nc = (3 + sp[0]) * (3 + sp[1]) * (3 + sp[2]);
+        int *cst = csm[wl], *cpre = cst + 64, *cpk = cpre + 65;
         {
-            const int a = lane >> 3, e = lane & 7;
-            if (a < 3 && e < A[a].m) {
-                int side;
-                double t;
-                float tfl;
-                split_entry_exact(g, A[a], e, side, t, tfl);
-                double w[FMM_MAXP];
-                lag_weights<double>(Cd, p, t, w);
+            int cnt_lane[2] = {0, 0};
 #pragma unroll
-                for (int k = 0; k < FMM_MAXP; k++) W[a][e][k] = w[k];
+            for (int h = 0; h < 2; h++) {
+                const int c = lane + 32 * h;
+                if (c < nc) {
+                    int ux, uy, uz;
+                    sd_cell_offset(c, o0, o1, nd0, nd1, ux, uy, uz);
+                    int gx = base[0] + ux, gy = base[1] + uy, gz = base[2] + uz;
+                    bool in = true;
+                    if (g.periodic) {
+                        gx = (gx + S) % S;
+                        gy = (gy + S) % S;
+                        gz = (gz + S) % S;
+                    } else {
+                        in = gx >= 0 && gy >= 0 && gz >= 0 && gx < S && gy < S && gz < S;
+                    }
+                    int a0 = 0, cc = 0;
+                    if (in) {
+                        const uint32_t key = morton_encode(gx, gy, gz);
+                        a0 = leaf_start[key];
+                        cc = leaf_start[key + 1] - a0;
+                    }
+                    cst[c] = a0;
+                    cpk[c] = (ux + 1) | ((uy + 1) << 4) | ((uz + 1) << 8);
+                    cnt_lane[h] = cc;
+                }
             }
-        }
-        __syncwarp();
-        double far0 = 0.0;  // far field at the reference point (entry 0 of every axis)
-        {
-            const int64_t cr = loc_cell(g.depth, (base[0] + S) % S, (base[1] + S) % S, (base[2] + S) % S);
-            for (int o = lane; o < p3; o += 32)
-                far0 += W[0][0][o % p] * W[1][0][(o / p) % p] * W[2][0][o / (p * p)] * (double)loc_leaf[cr * p3 + o];
-        }
-        for (int c0 = 0; c0 < m; c0 += CH) {
-            // the chunk's charges: entries, sides (bit a: upper cell of axis a),
-            // offset from the reference point, far-field difference
-            float dl[CH][3], th[CH][3], tl[CH][3], tf[CH][3];
-            int sd[CH];
-            double fd[CH];
+            // prefix of the counts over the (up to 64) cells
+            int inc0 = cnt_lane[0], inc1 = cnt_lane[1];
 #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y0 = __shfl_up_sync(0xffffffffu, inc0, o), y1 = __shfl_up_sync(0xffffffffu, inc1, o);
+                if (lane >= o) {
+                    inc0 += y0;
+                    inc1 += y1;
+                }
+            }
+            const int tot0 = __shfl_sync(0xffffffffu, inc0, 31);
+            if (lane < nc) cpre[lane + 1] = inc0;
+            if (lane + 32 < nc) cpre[lane + 33] = tot0 + inc1;
+            if (lane == 0) cpre[0] = 0;
+        }
+        const float Sp = POW == 2 ? (float)S * (float)S : (float)S;  // cell units to unit-box units
+        if (a1 >= 0) {
+            // ---- one split axis a1: the m <= SD_KMAX charges in one pass ----
+            const int ob = o0, oc = o1;  // the other two axes
+            // W_a1 at r (lower cell), W_ob and W_oc at the particle; per charge
+            // W_a1(s_k) - W_a1 at its cell's point: r below the plane, the plane
+            // itself above (t = 0 of the upper cell, the first node: weights e_0)
+            double *wr = &wsm[wl][0][0][0];
+            double *wb = wr + FMM_MAXP, *wc = wb + FMM_MAXP;
+            float *dw = reinterpret_cast<float *>(wc + FMM_MAXP);
+            float *kq = ksm[wl], *gs = gsm[wl];
+            int *ks = ssm[wl];
+            int sidek = 0;
+            double t = 0.0;  // lane k < m: charge k along a1; 16: r along a1; 17, 18: the other axes
+            if (lane < m) {  // charge k = lane: entry k of a1, entry 0 of the other axes
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    int side;
+                    float th, tl, tfk;
+                    split_entry_df(g, A[a], a == a1 ? lane : 0, side, th, tl, tfk);
+                    // s_k - r: th - r exact (Sterbenz) below the plane, r = 1 - dt
+                    const float dd = !sp[a] ? 0.0f : (side ? __fadd_rn(th, g.dtf) : __fsub_rn(th, R[a]));
+                    kq[lane * 12 + a] = dd + tl;
+                    kq[lane * 12 + 3 + a] = th;
+                    kq[lane * 12 + 6 + a] = tl;
+                    kq[lane * 12 + 9 + a] = tfk;
+                    sidek |= side << a;
+                    if (a == a1) t = (double)th + (double)tl;
+                }
+                ks[lane] = sidek;
+                gs[lane] = 0.0f;
+            } else if (lane >= 16 && lane < 19) {
+                const int a = lane == 17 ? ob : (lane == 18 ? oc : a1);
+                int side;
+                float th, tl, tfk;
+                split_entry_df(g, A[a], 0, side, th, tl, tfk);
+                t = (double)th + (double)tl;
+            }
+            {
+                double w[FMM_MAXP];
+                lag_weights<double>(Cd, p, t, w);  // one pass for all lanes
+                if (lane >= 16 && lane < 19) {
+                    double *dst = lane == 16 ? wr : (lane == 17 ? wb : wc);
+#pragma unroll
+                    for (int k = 0; k < FMM_MAXP; k++)
+                        if (k < p) dst[k] = w[k];
+                }
+                __syncwarp();
+                if (lane < m) {
+                    const bool upk = (sidek >> a1) & 1;
+#pragma unroll
+                    for (int k = 0; k < FMM_MAXP; k++)
+                        if (k < p) dw[lane * FMM_MAXP + k] = (float)(w[k] - (upk ? (k == 0 ? 1.0 : 0.0) : wr[k]));
+                }
+            }
+            __syncwarp();
+            // far field along the lines of a1 (one per node pair of ob, oc):
+            // charge k: (W_a1(s_k) - W_a1(its cell's point)) W_ob W_oc . L of its
+            // cell in single precision (the difference is small and carries its
+            // own rounding only); X = g(plane) . L_upper - g(r) . L_lower in
+            // double precision, the same for every upper charge (g(plane) is
+            // e_0 along a1)
+            const int sa = a1 == 0 ? 1 : (a1 == 1 ? p : p * p);
+            const int sb = ob == 0 ? 1 : (ob == 1 ? p : p * p), sc = oc == 0 ? 1 : (oc == 1 ? p : p * p);
+            const int64_t cl = loc_cell(g.depth, (base[0] + S) % S, (base[1] + S) % S, (base[2] + S) % S);
+            const int64_t cu = loc_cell(g.depth, (base[0] + (a1 == 0) + S) % S, (base[1] + (a1 == 1) + S) % S,
+                                        (base[2] + (a1 == 2) + S) % S);
+            float fk[SD_KMAX];
+#pragma unroll
+            for (int k = 0; k < SD_KMAX; k++) fk[k] = 0.0f;
+            double X = 0.0;
+            for (int ln = lane; ln < p * p; ln += 32) {
+                const int jb = ln % p, jc = ln / p;
+                const float *Ll = loc_leaf + cl * p3 + jb * sb + jc * sc, *Lu = loc_leaf + cu * p3 + jb * sb + jc * sc;
+                float L0[FMM_MAXP], L1[FMM_MAXP];
+                double xs = 0.0;
+#pragma unroll
+                for (int a = 0; a < FMM_MAXP; a++) {
+                    L0[a] = a < p ? Ll[a * sa] : 0.0f;
+                    L1[a] = a < p ? Lu[a * sa] : 0.0f;
+                    if (a < p) xs -= wr[a] * (double)L0[a];
+                }
+                const double wbc = wb[jb] * wc[jc];
+                X += wbc * (xs + (double)L1[0]);
+                const float fbc = (float)wbc;
+#pragma unroll
+                for (int k = 0; k < SD_KMAX; k++) {
+                    if (k < m) {
+                        const bool upk = (ks[k] >> a1) & 1;
+                        const float *d = dw + k * FMM_MAXP;
+                        float s = 0.0f;
+#pragma unroll
+                        for (int a = 0; a < FMM_MAXP; a++)
+                            if (a < p) s = fmaf(d[a], upk ? L1[a] : L0[a], s);
+                        fk[k] = fmaf(fbc, s, fk[k]);
+                    }
+                }
+            }
+            float myf = 0.0f;
+#pragma unroll
+            for (int k = 0; k < SD_KMAX; k++) {
+                if (k < m) {
+                    float v = fk[k];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == k) myf = v;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) X += __shfl_xor_sync(0xffffffffu, X, o);
+            // near field, three slabs of the table along a1: u = -1 (seen by r and
+            // the lower charges), 0..1 (seen by all), 2 (seen by the upper
+            // charges).  Sources of the middle slab closer to r than 16 max|delta|:
+            // direct terms per charge (gs); all others: series moments, which
+            // truncated after h^6 leave h^7 < 4e-9 of each term (8 h^7 for 1/r^2)
+            float far2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < SD_KMAX; k++)
+                if (k < m) far2 = fmaxf(far2, 256.0f * kq[k * 12 + a1] * kq[k * 12 + a1]);
+#pragma unroll 1
+            for (int set = 0; set < 3; set++) {
+                const int cb = set == 0 ? 0 : (set == 1 ? 9 : 27), ce = set == 0 ? 9 : (set == 1 ? 27 : 36);
+                const int fe = cpre[ce];
+                // one source: its series terms t (zero where it is skipped or taken directly)
+                auto source = [&](const float4 &v, int pk, bool ok, float(&t)[SD_NM]) {
+                    const int ux = (pk & 15) - 1, uy = ((pk >> 4) & 15) - 1, uz = (pk >> 8) - 1;
+                    // x - r (the reference is exact in single precision, side 0)
+                    const float d0x = sd_axis_diff(v.x, ux, R[0], 0.0f), d0y = sd_axis_diff(v.y, uy, R[1], 0.0f),
+                                d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
+                    const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
+                    const float ri0 = r02 > 0.0f ? rsqrtf(r02) : 0.0f;
+                    const bool direct = set == 1 && r02 <= far2;
+                    if (ok && direct) sd_direct_terms<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, m, kq, ks, gs);
+                    sd_series_terms<POW>(ok && !direct ? v.w : 0.0f, a1 == 0 ? d0x : (a1 == 1 ? d0y : d0z), ri0, t);
+                };
+                float acc[SD_NM], cmp[SD_NM];
+#pragma unroll
+                for (int k = 0; k < SD_NM; k++) acc[k] = cmp[k] = 0.0f;
+                // two sources per lane and step (f and f + 32), loaded together
+                int c = cb, c2 = cb;
+                for (int f = cpre[cb] + lane; f < fe; f += 64) {
+                    while (cpre[c + 1] <= f) c++;
+                    const int f2 = f + 32;
+                    const bool ok2 = f2 < fe;
+                    if (ok2) {
+                        c2 = max(c2, c);
+                        while (cpre[c2 + 1] <= f2) c2++;
+                    }
+                    const int j = cst[c] + (f - cpre[c]);
+                    const int j2 = ok2 ? cst[c2] + (f2 - cpre[c2]) : j;
+                    const int og1 = s_origin[j], og2 = s_origin[j2];
+                    const float4 v1 = s_pt[j], v2 = s_pt[j2];
+                    float t1[SD_NM], t2[SD_NM];
+                    source(v1, cpk[c], og1 != i, t1);
+                    source(v2, cpk[c2], ok2 && og2 != i, t2);
+#pragma unroll
+                    for (int k = 0; k < SD_NM; k++) {  // compensated sums
+                        const float y = (t1[k] + t2[k]) - cmp[k], tt = acc[k] + y;
+                        cmp[k] = (tt - acc[k]) - y;
+                        acc[k] = tt;
+                    }
+                }
+                // over the lanes: the moments n >= 1 in single precision (each lane's
+                // compensated sum rounded once); n = 0 (used where the two points see
+                // different slabs, and cancelling there) as pairs
+                float h0 = acc[0], l0 = -cmp[0];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    sd_two_sum(h0, l0, __shfl_xor_sync(0xffffffffu, h0, o), __shfl_xor_sync(0xffffffffu, l0, o));
+#pragma unroll
+                for (int k = 1; k < SD_NM; k++) {
+                    float v = acc[k] - cmp[k];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    acc[k] = v;
+                }
+                if (lane == 0) {
+                    msm[wl][0][set * SD_NM] = h0;
+                    msm[wl][1][set * SD_NM] = l0;
+#pragma unroll
+                    for (int k = 1; k < SD_NM; k++) {
+                        msm[wl][0][set * SD_NM + k] = acc[k];
+                        msm[wl][1][set * SD_NM + k] = 0.0f;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane < m) {
+                // D_k = sum_{n>=1} delta^n (M_n of the middle slab + of the slab only
+                // this side sees besides it) + direct terms + far difference; an upper
+                // charge adds M_0(u = 2) - M_0(u = -1) + X, which cancel to a small
+                // number: that sum in double precision
+                const float dk = kq[lane * 12 + a1];
+                const bool up = (sidek >> a1) & 1;
+                const float *MH = msm[wl][0], *ML = msm[wl][1];
+                const int o = up ? 2 * SD_NM : 0;  // the other slab: u = 2 above the plane, u = -1 below
+                float s = 0.0f;
+#pragma unroll
+                for (int k = SD_NM - 1; k >= 1; k--)
+                    s = (s + ((MH[SD_NM + k] + ML[SD_NM + k]) + (MH[o + k] + ML[o + k]))) * dk;
+                const double zs = up ? (double)Sp * (((double)MH[2 * SD_NM] + (double)ML[2 * SD_NM]) -
+                                                     ((double)MH[0] + (double)ML[0])) + X
+                                     : 0.0;
+                delta[e0 + lane] = (float)((double)(Sp * (s + gs[lane]) + myf) + zs);
+            }
+        } else {
+            // ---- several split axes: charges c0 .. c0 + CH - 1, direct terms ----
+            double(*W)[FMM_MAXP + 1][FMM_MAXP] = wsm[wl];
+            {  // weights: lane = a * 8 + e computes entry e of axis a
+                const int a = lane >> 3, e = lane & 7;
+                if (a < 3 && e < A[a].m) {
+                    int side;
+                    float th, tl, tfl;
+                    split_entry_df(g, A[a], e, side, th, tl, tfl);
+                    double w[FMM_MAXP];
+                    lag_weights<double>(Cd, p, (double)th + (double)tl, w);
+#pragma unroll
+                    for (int k = 0; k < FMM_MAXP; k++)
+                        if (k < p) W[a][e][k] = w[k];
+                }
+            }
+            __syncwarp();
+            double far0 = 0.0;  // far field at the reference point (entry 0 of every axis)
+            {
+                const int64_t cr = loc_cell(g.depth, (base[0] + S) % S, (base[1] + S) % S, (base[2] + S) % S);
+                for (int o = lane; o < p3; o += 32)
+                    far0 += W[0][0][o % p] * W[1][0][(o / p) % p] * W[2][0][o / (p * p)] * (double)loc_leaf[cr * p3 + o];
+            }
+            for (int o = 16; o > 0; o >>= 1) far0 += __shfl_xor_sync(0xffffffffu, far0, o);
+            float *kq = ksm[wl];  // per charge of the chunk: s_k - r (3), th (3), tl (3), tf (3)
+            int *ks = ssm[wl];    // and its sides
+            double fdk = 0.0;     // lane k: the far-field difference of charge c0 + k
+#pragma unroll 1
             for (int k = 0; k < CH; k++) {
                 int le = min(c0 + k, m - 1);
                 const int ex = le % A[0].m;
                 le /= A[0].m;
                 const int e3[3] = {ex, le % A[1].m, le / A[1].m};
                 int side[3];
-                double tk[3];
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    split_entry_exact(g, A[a], e3[a], side[a], tk[a], tf[k][a]);
-                    dl[k][a] = (float)(((double)side[a] + tk[a]) - (double)R[a]);
-                    th[k][a] = (float)tk[a];
-                    tl[k][a] = (float)(tk[a] - (double)th[k][a]);
+                    float th, tl, tfk;
+                    split_entry_df(g, A[a], e3[a], side[a], th, tl, tfk);
+                    if (lane == k) {
+                        const float dd = !sp[a] ? 0.0f : (side[a] ? __fadd_rn(th, g.dtf) : __fsub_rn(th, R[a]));
+                        kq[k * 12 + a] = dd + tl;
+                        kq[k * 12 + 3 + a] = th;
+                        kq[k * 12 + 6 + a] = tl;
+                        kq[k * 12 + 9 + a] = tfk;
+                        ks[k] = side[0] | (side[1] << 1) | (side[2] << 2);
+                    }
                 }
-                sd[k] = side[0] | (side[1] << 1) | (side[2] << 2);
                 const int64_t ck = loc_cell(g.depth, (base[0] + side[0] + S) % S, (base[1] + side[1] + S) % S,
                                             (base[2] + side[2] + S) % S);
                 double f = 0.0;
                 for (int o = lane; o < p3; o += 32)
                     f += W[0][e3[0]][o % p] * W[1][e3[1]][(o / p) % p] * W[2][e3[2]][o / (p * p)] *
                          (double)loc_leaf[ck * p3 + o];
-                fd[k] = f - far0;
+                for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+                if (lane == k) fdk = f - far0;
+                csum[wl][0][k][lane] = 0.0f;  // this lane's compensated sums for the charge
+                csum[wl][1][k][lane] = 0.0f;
             }
-            // near field: the cells adjacent to any of the particle's cells
-            float acc[CH], cmp[CH];
-#pragma unroll
-            for (int k = 0; k < CH; k++) acc[k] = cmp[k] = 0.0f;
-            for (int uz = -1; uz <= 1 + sp[2]; uz++)
-                for (int uy = -1; uy <= 1 + sp[1]; uy++)
-                    for (int ux = -1; ux <= 1 + sp[0]; ux++) {
-                        int gx = base[0] + ux, gy = base[1] + uy, gz = base[2] + uz;
-                        if (g.periodic) {
-                            gx = (gx + S) % S;
-                            gy = (gy + S) % S;
-                            gz = (gz + S) % S;
-                        } else if (gx < 0 || gy < 0 || gz < 0 || gx >= S || gy >= S || gz >= S) {
-                            continue;
-                        }
-                        const uint32_t key = morton_encode(gx, gy, gz);
-                        const int ja = leaf_start[key], jb = leaf_start[key + 1];
-                        const bool inR = ux <= 1 && uy <= 1 && uz <= 1;
-                        for (int j = ja + lane; j < jb; j += 32) {
-                            if (s_origin[j] == i) continue;
-                            const float4 v = s_pt[j];
-                            // x - r (the reference is exact in single precision, side 0)
-                            const float d0x = sd_axis_diff(v.x, ux, R[0], 0.0f), d0y = sd_axis_diff(v.y, uy, R[1], 0.0f),
-                                        d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
-                            const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
-#pragma unroll
-                            for (int k = 0; k < CH; k++) {
-                                const int sx = sd[k] & 1, sy = (sd[k] >> 1) & 1, sz = sd[k] >> 2;
-                                const bool inK = ux >= sx - 1 && ux <= sx + 1 && uy >= sy - 1 && uy <= sy + 1 &&
-                                                 uz >= sz - 1 && uz <= sz + 1;
-                                // x - s_k directly, accurate also when x is close to s_k
-                                const float dkx = sd_axis_diff(v.x, ux - sx, th[k][0], tl[k][0]),
-                                            dky = sd_axis_diff(v.y, uy - sy, th[k][1], tl[k][1]),
-                                            dkz = sd_axis_diff(v.z, uz - sz, th[k][2], tl[k][2]);
-                                // coincident with the emitted charge (the single-precision
-                                // positions the near field compares): skipped as there
-                                const bool zk = sd_axis_diff(v.x, ux - sx, tf[k][0], 0.0f) == 0.0f &&
-                                                sd_axis_diff(v.y, uy - sy, tf[k][1], 0.0f) == 0.0f &&
-                                                sd_axis_diff(v.z, uz - sz, tf[k][2], 0.0f) == 0.0f;
-                                // |s_k - x|^2 - |r - x|^2 = delta . (delta - 2 (x - r))
-                                const float nm = dl[k][0] * (dl[k][0] - 2.0f * d0x) + dl[k][1] * (dl[k][1] - 2.0f * d0y) +
-                                                 dl[k][2] * (dl[k][2] - 2.0f * d0z);
-                                const float rk2 = dkx * dkx + dky * dky + dkz * dkz;
-                                float term = 0.0f;
-                                if (inK && inR && !zk && r02 > 0.0f && rk2 > 0.0f) {
-                                    if (POW == 2) {
-                                        term = -v.w * nm / (r02 * rk2);
-                                    } else {
-                                        const float r0 = sqrtf(r02), rk = sqrtf(rk2);
-                                        term = -v.w * nm / (r0 * rk * (r0 + rk));
-                                    }
-                                } else {
-                                    if (inK && !zk && rk2 > 0.0f) term += POW == 2 ? v.w / rk2 : v.w / sqrtf(rk2);
-                                    if (inR && r02 > 0.0f) term -= POW == 2 ? v.w / r02 : v.w / sqrtf(r02);
-                                }
-                                const float y = term - cmp[k], tt = acc[k] + y;  // compensated sum
-                                cmp[k] = (tt - acc[k]) - y;
-                                acc[k] = tt;
-                            }
-                        }
-                    }
-            const double Sp = POW == 2 ? (double)S * S : (double)S;
-#pragma unroll
-            for (int k = 0; k < CH; k++) {
-                double v = (double)acc[k] - (double)cmp[k];
-                double f = fd[k];
-                for (int o = 16; o > 0; o >>= 1) {
-                    v += __shfl_xor_sync(0xffffffffu, v, o);
-                    f += __shfl_xor_sync(0xffffffffu, f, o);
+            __syncwarp();
+            // two sources per lane and step (f and f + 32), loaded together
+            const int nsrc = cpre[nc];
+            int c = 0, c2 = 0;
+            for (int f = lane; f < nsrc; f += 64) {
+                while (cpre[c + 1] <= f) c++;
+                const int f2 = f + 32;
+                const bool ok2 = f2 < nsrc;
+                if (ok2) {
+                    c2 = max(c2, c);
+                    while (cpre[c2 + 1] <= f2) c2++;
                 }
-                if (lane == 0 && c0 + k < m) delta[e0 + c0 + k] = (float)(Sp * v + f);
+                const int j = cst[c] + (f - cpre[c]);
+                const int j2 = ok2 ? cst[c2] + (f2 - cpre[c2]) : j;
+                const int og1 = s_origin[j], og2 = s_origin[j2];
+                const float4 v1 = s_pt[j], v2 = s_pt[j2];
+#pragma unroll 1
+                for (int h = 0; h < 2; h++) {
+                    if (h == 0 ? og1 == i : (!ok2 || og2 == i)) continue;
+                    const float4 v = h == 0 ? v1 : v2;
+                    const int pk = cpk[h == 0 ? c : c2], ux = (pk & 15) - 1, uy = ((pk >> 4) & 15) - 1,
+                              uz = (pk >> 8) - 1;
+                    const bool inR = ux <= 1 && uy <= 1 && uz <= 1;
+                    const float d0x = sd_axis_diff(v.x, ux, R[0], 0.0f), d0y = sd_axis_diff(v.y, uy, R[1], 0.0f),
+                                d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
+                    const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
+                    const float ri0 = r02 > 0.0f ? rsqrtf(r02) : 0.0f;
+#pragma unroll 1
+                    for (int k = 0; k < CH; k++) {
+                        const float term = sd_pair_term<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, inR, kq + k * 12, ks[k]);
+                        const float ak = csum[wl][0][k][lane], ck = csum[wl][1][k][lane];
+                        const float y = term - ck, tt = ak + y;  // compensated sum
+                        csum[wl][1][k][lane] = (tt - ak) - y;
+                        csum[wl][0][k][lane] = tt;
+                    }
+                }
             }
+            double vk = 0.0;
+#pragma unroll 1
+            for (int k = 0; k < CH; k++) {
+                double v = (double)csum[wl][0][k][lane] - (double)csum[wl][1][k][lane];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == k) vk = v;
+            }
+            if (lane < CH && c0 + lane < m) delta[e0 + c0 + lane] = (float)((double)Sp * vk + fdk);
         }
-        __syncwarp();  // the weights table is rewritten for the next particle
+        __syncwarp();  // the tables are rewritten by the next task
     }
 }
 
@@ -956,13 +1361,16 @@ void launch_split_delta(const Geom &g, const Coef<double> &Cd, const Ptrs<float>
                         const float *pos, cudaStream_t st, Tracer &tr) {
     if (n <= 0) return;
     tr.begin(FMM_STAGE_UNSPLIT, st);
-    const int nb = (n + 32 * SD_WARPS - 1) / (32 * SD_WARPS);  // 32 particles per warp
+    cudaMemsetAsync(P.slist, 0, 8, st);
+    k_split_list<<<(n + 255) / 256, 256, 0, st>>>(n, g.p + (g.p & 1), P.count, P.offset, P.hdr, P.slist);
+    tr.count();
+    const int nb = 152 * 5;  // persistent: five CTAs per SM
     const float *leaf = reinterpret_cast<const float *>(P.loc) + W.loc_level[g.depth];
-    // charges per pass: the charges of a particle split along one axis
+    // charges per pass of a particle split along several axes
     const int ch = g.p <= 4 ? 4 : (g.p <= 6 ? 6 : 8);
 #define SD_LAUNCH(POW, CH)                                                                                  \
     k_split_delta<POW, CH><<<nb, 32 * SD_WARPS, 0, st>>>(g, Cd, n, pos, P.count, P.offset, P.leaf_start, P.s_pt, \
-                                                        P.s_origin, leaf, P.delta, P.hdr)
+                                                        P.s_origin, leaf, P.delta, P.slist)
     if (g.power == 2) {
         if (ch == 4) SD_LAUNCH(2, 4); else if (ch == 6) SD_LAUNCH(2, 6); else SD_LAUNCH(2, 8);
     } else {

@@ -139,4 +139,7 @@ def workload(name, seed=None, n=None):
     if name == "plummer8m":  # 8,388,608 Plummer, open, plain, depth 7, p 6
         pos, q, box = plummer(1 << 23 if n is None else n, 4 if seed is None else seed)
         return dict(pos=pos, q=q, box=box, depth=7, p=6, periodic=False, continuous=False)
+    if name == "plummer1m":  # 1,048,576 Plummer, open, plain, depth 6, p 6 (a small case of plummer8m)
+        pos, q, box = plummer(1 << 20 if n is None else n, 4 if seed is None else seed)
+        return dict(pos=pos, q=q, box=box, depth=6, p=6, periodic=False, continuous=False)
     raise KeyError(name)
