@@ -47,7 +47,9 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
 # capture of the current kernels (scaled to a full launch where the capture
 # ran on a smaller case of the same distribution); reported as the
 # rooflines' traffic
-PROFILED_TRAFFIC = {("uniform1m", "tf32x3", "k_p2p"): 201362688}
+PROFILED_TRAFFIC = {("uniform1m", "tf32x3", "k_p2p"): 201362688,
+                    ("plummer8m", "tf32x3", "k_m2l_tcg"): 344989364736 + 960240896,
+                    ("plummer8m", "tf32x3", "k_p2p"): 288133376 + 1771937792}
 
 
 def _peaks():

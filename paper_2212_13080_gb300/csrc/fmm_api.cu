@@ -422,6 +422,7 @@ WsLayout make_layout(const fmm_plan_t P, int64_t n) {
     W.occ = take(P->tc ? (size_t)occ_ints(P->depth, P->periodic ? 1 : 2) * 4 : 0);
     W.delta = take(cont && !P->fp64 ? (size_t)W.cap * 4 : 0);
     W.slist = take(cont && !P->fp64 ? (size_t)(n + 2) * 4 : 0);
+    W.pord = take((size_t)(W.ncell + 16) * 4);
     int64_t mx = n > W.ncell ? n : W.ncell;
     W.scan_blocks = (int)(mx / 2048 + 2);
     W.scan_tmp = take((size_t)(W.scan_blocks + 1) * 4);
@@ -462,6 +463,7 @@ Ptrs<real> make_ptrs(const WsLayout &W, void *ws) {
     P.occ = (int *)(b + W.occ);
     P.delta = (float *)(b + W.delta);
     P.slist = (int *)(b + W.slist);
+    P.pord = (int *)(b + W.pord);
     P.scan_tmp = (int *)(b + W.scan_tmp);
     P.epart = (double *)(b + W.epart);
     return P;

@@ -77,6 +77,7 @@ struct WsLayout {
     size_t occ;                           // occupied-cell lists of the contraction (tensor-core plans)
     size_t delta;                         // per emitted charge of a split particle: phi(s_k) - phi(r)
     size_t slist;                         // the split particles (count, then indices)
+    size_t pord;                          // near-field launch order: class counts, fill, cells
     size_t scan_tmp, epart;
     size_t total;
     int64_t cap;                          // charge capacity
@@ -254,6 +255,7 @@ struct Ptrs {
     int *occ;
     float *delta;  // single-precision plans of the continuous form (adjoint split forces)
     int *slist;
+    int *pord;
     int *scan_tmp;
     double *epart;
 };

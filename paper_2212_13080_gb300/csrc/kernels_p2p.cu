@@ -243,6 +243,47 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
 #endif
 #define NF_TP 36  // row stride (words) of the per-warp transpose buffer
 
+// Launch order of the near field: the occupied cells, heaviest first.  A
+// cell's work grows with its charge count T (T times its own and its 13
+// forward neighbours' charges), so the cells go in seven classes by T, the
+// largest first, and within a class in the order the atomics hand out (a
+// cell's sums do not depend on when its CTA runs: the results are the same
+// bit for bit).  Clustered inputs put a few hundred cells with up to ~1000
+// charges each among many light ones; launched in cell order they would
+// start late and run alone at the end.  pord[0..6]: class sizes; pord[8..14]:
+// fill counters; pord[16..]: the cells (zeroed before the count).
+#define NF_NCLS 7
+__device__ __forceinline__ int nf_class(int T) {
+    return T >= 512 ? 0 : T >= 256 ? 1 : T >= 128 ? 2 : T >= 64 ? 3 : T >= 32 ? 4 : T >= 16 ? 5 : T > 0 ? 6 : -1;
+}
+
+__global__ void k_nf_order_count(int64_t ncell, const int *__restrict__ leaf_start, int *__restrict__ pord) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int cls = c < ncell ? nf_class(leaf_start[c + 1] - leaf_start[c]) : -1;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NF_NCLS; k++) {
+        const unsigned b = __ballot_sync(0xffffffffu, cls == k);
+        if (lane == 0 && b) atomicAdd(&pord[k], __popc(b));
+    }
+}
+
+__global__ void k_nf_order_fill(int64_t ncell, const int *__restrict__ leaf_start, int *__restrict__ pord) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int cls = c < ncell ? nf_class(leaf_start[c + 1] - leaf_start[c]) : -1;
+    const int lane = threadIdx.x & 31;
+    int first = 0;  // the first slot of class k
+#pragma unroll
+    for (int k = 0; k < NF_NCLS; k++) {
+        const unsigned b = __ballot_sync(0xffffffffu, cls == k);
+        int base = 0;
+        if (lane == 0 && b) base = atomicAdd(&pord[8 + k], __popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (cls == k) pord[16 + first + base + __popc(b & ((1u << lane) - 1u))] = (int)c;
+        first += pord[k];
+    }
+}
+
 // 1/sqrt(r2): single precision uses the SFU reciprocal square root directly
 // (r2 is never subnormal here: it is 0 or a squared distance of FP32 charges
 // inside a few cells); double precision the correctly rounded form.
@@ -385,7 +426,7 @@ __global__ void __launch_bounds__(NF_BS, sizeof(real) == 4 ? NF_MINB : 1) k_p2p(
                                                const int *__restrict__ s_origin,
                                                typename Vec4<real>::T *__restrict__ out_pt,
                                                typename Vec4<real>::T *__restrict__ react,
-                                               int64_t rstride) {
+                                               int64_t rstride, const int *__restrict__ pord) {
     typedef typename Vec4<real>::T real4;
     constexpr int NC = FORCES ? 4 : 1;     // components per target
     constexpr int TG = 32 / NC;            // targets per transposed group
@@ -406,7 +447,16 @@ __global__ void __launch_bounds__(NF_BS, sizeof(real) == 4 ? NF_MINB : 1) k_p2p(
     // index 16 for the 4-step search of a slot's segment
     __shared__ int seg_start[NF_SEGS], seg_off[NF_SEGS + 3];
 
-    const uint32_t key = blockIdx.x;
+    // the cell of this CTA: the launch order's entry (occupied cells, heaviest
+    // first), or the block index where there is no order (small grids)
+    uint32_t key = blockIdx.x;
+    if (pord) {
+        int nocc = 0;
+#pragma unroll
+        for (int k = 0; k < NF_NCLS; k++) nocc += pord[k];
+        if ((int)blockIdx.x >= nocc) return;
+        key = (uint32_t)pord[16 + blockIdx.x];
+    }
     const int t0 = leaf_start[key], T = leaf_start[key + 1] - t0;
     if (T == 0) return;
     const int S = 1 << depth;
@@ -761,14 +811,25 @@ void launch_p2p(const Geom &g, const Ptrs<real> &P, const WsLayout &W, bool forc
     tr.begin(FMM_STAGE_P2P, st);
     // charges of different cells can coincide only on split planes with odd p
     const bool guard = g.continuous && (g.p & 1);
+    // the launch order pays off where a few heavy cells could start late
+    // among many light ones; grids of fewer than 32,768 cells go in cell order
+    const int *pord = W.ncell >= 32768 ? P.pord : nullptr;
+    if (pord) {
+        cudaMemsetAsync(P.pord, 0, 16 * sizeof(int), st);
+        const int nb = (int)((W.ncell + 255) / 256);
+        k_nf_order_count<<<nb, 256, 0, st>>>(W.ncell, P.leaf_start, P.pord);
+        tr.count();
+        k_nf_order_fill<<<nb, 256, 0, st>>>(W.ncell, P.leaf_start, P.pord);
+        tr.count();
+    }
 #define LAUNCH(F, G)                                                                               \
     do {                                                                                           \
         if (g.power == 2)                                                                          \
             k_p2p<real, F, G, 2><<<ncell, NF_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt, \
-                                                          P.s_origin, P.out_pt, P.react, W.cap);  \
+                                                          P.s_origin, P.out_pt, P.react, W.cap, pord);   \
         else                                                                                       \
             k_p2p<real, F, G, 1><<<ncell, NF_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt, \
-                                                          P.s_origin, P.out_pt, P.react, W.cap);  \
+                                                          P.s_origin, P.out_pt, P.react, W.cap, pord);   \
     } while (0)
     if (forces) {
         if (guard) LAUNCH(true, true);

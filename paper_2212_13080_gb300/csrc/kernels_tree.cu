@@ -1,5 +1,6 @@
 // Binning, split, stable sort by finest cell, recombination of split charges
 // and the FP64 energy reduction.
+#include <algorithm>
 #include <type_traits>
 
 #include "fmm_internal.cuh"
@@ -747,6 +748,34 @@ __device__ __forceinline__ void sd_series_terms(float q, float da, float ri, flo
     }
 }
 
+// Direct terms of a source of an outer slab closer to r than the series
+// allows (only with split widths well above the default): u = -1 (set 0): the
+// charges below the plane see it with r, a difference term each (r's plain
+// term stays in the slab's M_0); u = 2 (set 2): the charges above the plane
+// alone see it, a plain term each, in double precision.
+template <int POW>
+__device__ __noinline__ void sd_direct_outer(const float4 v, int ux, int uy, int uz, float d0x, float d0y, float d0z,
+                                             float r02, float ri0, int set, int a1, int m, const float *kq,
+                                             const int *ks, float *gs, double *gsd) {
+    for (int k = 0; k < m; k++) {
+        const int sk = ks[k];
+        const bool upk = (sk >> a1) & 1;
+        if (set == 0 && !upk) {
+            atomicAdd(&gs[k], sd_pair_term<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, true, kq + 12 * k, sk));
+        } else if (set == 2 && upk) {
+            const float *kk = kq + 12 * k;
+            const int sh[3] = {ux - (sk & 1), uy - ((sk >> 1) & 1), uz - (sk >> 2)};
+            const float vv[3] = {v.x, v.y, v.z};
+            double r2 = 0.0;
+            for (int a = 0; a < 3; a++) {
+                const double d = ((double)vv[a] + (double)sh[a]) - ((double)kk[3 + a] + (double)kk[6 + a]);
+                r2 += d * d;
+            }
+            if (r2 > 0.0) atomicAdd(&gsd[k], POW == 2 ? (double)v.w / r2 : (double)v.w / sqrt(r2));
+        }
+    }
+}
+
 // The offset u (each in -1..2) of cell c of the neighbour table whose axis o2
 // varies slowest, then o1, then o0 (extents n0, n1).
 __device__ __forceinline__ void sd_cell_offset(int c, int o0, int o1, int n0, int n1, int &ux, int &uy, int &uz) {
@@ -770,6 +799,7 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
     __shared__ float ksm[SD_WARPS][SD_KMAX * 12];      // the charges (one split axis) or one chunk of them
     __shared__ int ssm[SD_WARPS][SD_KMAX];             // their sides (bit a: the upper cell of axis a)
     __shared__ float gsm[SD_WARPS][SD_KMAX];           // near-source terms per charge (one split axis)
+    __shared__ double gsd[SD_WARPS][SD_KMAX];          // plain near-source terms per charge (outer slab)
     __shared__ float msm[SD_WARPS][2][SD_NMOM];        // the moments (high, low) per slab and order
     __shared__ float csum[SD_WARPS][2][CH][32];        // per-lane compensated sums per charge (several axes)
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -895,6 +925,7 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
                 }
                 ks[lane] = sidek;
                 gs[lane] = 0.0f;
+                gsd[wl][lane] = 0.0;
             } else if (lane >= 16 && lane < 19) {
                 const int a = lane == 17 ? ob : (lane == 18 ? oc : a1);
                 int side;
@@ -974,18 +1005,23 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
             for (int o = 16; o > 0; o >>= 1) X += __shfl_xor_sync(0xffffffffu, X, o);
             // near field, three slabs of the table along a1: u = -1 (seen by r and
             // the lower charges), 0..1 (seen by all), 2 (seen by the upper
-            // charges).  Sources of the middle slab closer to r than 16 max|delta|:
-            // direct terms per charge (gs); all others: series moments, which
-            // truncated after h^6 leave h^7 < 4e-9 of each term (8 h^7 for 1/r^2)
+            // charges).  Sources closer to r than 16 max|delta|: direct terms per
+            // charge (gs; with the default split width only middle-slab sources
+            // are that close); all others: series moments, which truncated after
+            // h^6 leave h^7 < 4e-9 of each term (8 h^7 for 1/r^2)
             float far2 = 0.0f;
 #pragma unroll
             for (int k = 0; k < SD_KMAX; k++)
                 if (k < m) far2 = fmaxf(far2, 256.0f * kq[k * 12 + a1] * kq[k * 12 + a1]);
+            bool outer_direct = false;
 #pragma unroll 1
             for (int set = 0; set < 3; set++) {
                 const int cb = set == 0 ? 0 : (set == 1 ? 9 : 27), ce = set == 0 ? 9 : (set == 1 ? 27 : 36);
                 const int fe = cpre[ce];
-                // one source: its series terms t (zero where it is skipped or taken directly)
+                // one source: its series terms t (zero where it is skipped or taken
+                // directly; r's plain term of the slab u = -1 is kept in its M_0 for
+                // every source; direct sources of the outer slabs are taken after
+                // the three slabs)
                 auto source = [&](const float4 &v, int pk, bool ok, float(&t)[SD_NM]) {
                     const int ux = (pk & 15) - 1, uy = ((pk >> 4) & 15) - 1, uz = (pk >> 8) - 1;
                     // x - r (the reference is exact in single precision, side 0)
@@ -993,9 +1029,15 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
                                 d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
                     const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
                     const float ri0 = r02 > 0.0f ? rsqrtf(r02) : 0.0f;
-                    const bool direct = set == 1 && r02 <= far2;
-                    if (ok && direct) sd_direct_terms<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, m, kq, ks, gs);
+                    const bool direct = r02 <= far2;
+                    if (ok && direct) {
+                        if (set == 1)
+                            sd_direct_terms<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, m, kq, ks, gs);
+                        else
+                            outer_direct = true;  // taken after the slabs
+                    }
                     sd_series_terms<POW>(ok && !direct ? v.w : 0.0f, a1 == 0 ? d0x : (a1 == 1 ? d0y : d0z), ri0, t);
+                    if (set == 0 && ok && direct) t[0] = POW == 2 ? v.w * ri0 * ri0 : v.w * ri0;
                 };
                 float acc[SD_NM], cmp[SD_NM];
 #pragma unroll
@@ -1048,6 +1090,27 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
                     }
                 }
             }
+            if (__any_sync(0xffffffffu, outer_direct)) {
+                // sources of the outer slabs closer to r than the series allows (split
+                // widths well above the default): their direct terms
+                for (int set = 0; set < 3; set += 2) {
+                    const int fb = cpre[set == 0 ? 0 : 27], fe = cpre[set == 0 ? 9 : 36];
+                    int c = set == 0 ? 0 : 27;
+                    for (int f = fb + lane; f < fe; f += 32) {
+                        while (cpre[c + 1] <= f) c++;
+                        const int j = cst[c] + (f - cpre[c]);
+                        if (s_origin[j] == i) continue;
+                        const float4 v = s_pt[j];
+                        const int pk = cpk[c], ux = (pk & 15) - 1, uy = ((pk >> 4) & 15) - 1, uz = (pk >> 8) - 1;
+                        const float d0x = sd_axis_diff(v.x, ux, R[0], 0.0f), d0y = sd_axis_diff(v.y, uy, R[1], 0.0f),
+                                    d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
+                        const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
+                        if (r02 > far2) continue;
+                        const float ri0 = r02 > 0.0f ? rsqrtf(r02) : 0.0f;
+                        sd_direct_outer<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, set, a1, m, kq, ks, gs, gsd[wl]);
+                    }
+                }
+            }
             __syncwarp();
             if (lane < m) {
                 // D_k = sum_{n>=1} delta^n (M_n of the middle slab + of the slab only
@@ -1062,9 +1125,10 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
 #pragma unroll
                 for (int k = SD_NM - 1; k >= 1; k--)
                     s = (s + ((MH[SD_NM + k] + ML[SD_NM + k]) + (MH[o + k] + ML[o + k]))) * dk;
-                const double zs = up ? (double)Sp * (((double)MH[2 * SD_NM] + (double)ML[2 * SD_NM]) -
-                                                     ((double)MH[0] + (double)ML[0])) + X
-                                     : 0.0;
+                const double zs = (up ? (double)Sp * (((double)MH[2 * SD_NM] + (double)ML[2 * SD_NM]) -
+                                                      ((double)MH[0] + (double)ML[0])) + X
+                                      : 0.0) +
+                                  (double)Sp * gsd[wl][lane];
                 delta[e0 + lane] = (float)((double)(Sp * (s + gs[lane]) + myf) + zs);
             }
         } else {
@@ -1364,7 +1428,9 @@ void launch_split_delta(const Geom &g, const Coef<double> &Cd, const Ptrs<float>
     cudaMemsetAsync(P.slist, 0, 8, st);
     k_split_list<<<(n + 255) / 256, 256, 0, st>>>(n, g.p + (g.p & 1), P.count, P.offset, P.hdr, P.slist);
     tr.count();
-    const int nb = 152 * 5;  // persistent: five CTAs per SM
+    // persistent: five CTAs per SM, fewer for small systems (a few percent of
+    // the particles are split; the loop takes any number of tasks)
+    const int nb = (int)std::min<int64_t>(152 * 5, std::max<int64_t>(1, ((int64_t)n + 63) / 64));
     const float *leaf = reinterpret_cast<const float *>(P.loc) + W.loc_level[g.depth];
     // charges per pass of a particle split along several axes
     const int ch = g.p <= 4 ? 4 : (g.p <= 6 ? 6 : 8);

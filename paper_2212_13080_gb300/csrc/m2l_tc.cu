@@ -37,6 +37,7 @@
 // ~1e-4).  A row's functional depends on its own A rows only, so it is the
 // same, bit for bit, whichever tile form computes it.  For N > 64 the
 // epilogue splits the columns over two warp groups.
+#include <algorithm>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -786,10 +787,14 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
     __nv_bfloat16 *hi16 = reinterpret_cast<__nv_bfloat16 *>(P.phihi);
     __nv_bfloat16 *lo16 = reinterpret_cast<__nv_bfloat16 *>(P.philo);
     if (split) {
+        // grid-stride over the levels' (cell, 4 values); small systems take a
+        // small grid, so that other work keeps the SMs
+        const int64_t units = (SL.dst[depth + 1] - SL.dst[lmin]) * ((bf16 ? pk : p3s) / 4);
+        const int nbs = (int)std::min<int64_t>(152 * 8, std::max<int64_t>(1, (units + 255) / 256));
         if (bf16)
-            k_split_bf16<<<152 * 8, 256, 0, st>>>(P.phi, SL, hi16, lo16, p3, pk);
+            k_split_bf16<<<nbs, 256, 0, st>>>(P.phi, SL, hi16, lo16, p3, pk);
         else
-            k_split_tf32<<<152 * 8, 256, 0, st>>>(P.phi, SL, P.phihi, P.philo, p3, p3s, mode == FMM_TC_TF32X1);
+            k_split_tf32<<<nbs, 256, 0, st>>>(P.phi, SL, P.phihi, P.philo, p3, p3s, mode == FMM_TC_TF32X1);
         tr.count();
     }
     // the occupied cells of every (level, parity) segment, once per evaluation
