@@ -223,9 +223,13 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
 // with odd p, whose middle split charges sit on the cell plane (local
 // coordinate 1 below it, 0 above); otherwise the frame coordinates differ by
 // at least one ulp along an axis of delta_d.  So the pairs to skip are charges
-// of the same particle (split charges) and, with GUARD, coincident charges.
+// of the same particle (split charges) and, with odd p, coincident charges:
+// CK = 0 (plain form: every charge is a particle of its own, none to skip),
+// 1 (continuous form: charges of the same particle), 2 (and coincident ones).
 // Single precision evaluates two targets per packed FP32x2 instruction
-// (nf_targets2), the targets staged a second time by pairs.
+// (nf_targets2), the targets staged a second time by pairs.  (Skipping a
+// warp's source slots past the last source, with the slots assigned warp by
+// warp and a warp-uniform count of the active ones, was measured slower.)
 //
 // Own phase: the pairs inside A, one-sided (each target against all of A's
 // charges), skipping charges of the same particle and coincident charges.
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(Coef<real> C, int depth, int per
 // blocks of TB (256 in single precision, 64 in double: static shared memory).
 // ---------------------------------------------------------------------------
 #define NF_BS 128
-#define NF_KS 4
+#define NF_KS 4  // source slots per thread
 #ifndef NF_MINB
 #define NF_MINB 4  // single precision: CTAs per SM the register allocation must allow
 #endif
@@ -298,13 +302,13 @@ template <> __device__ __forceinline__ double rsqrt_pair<double>(double x) { ret
 // One (target, source) pair of the forward phase: target sums (p, x, y, z) in
 // a, the source's reaction in r.  FIRST assigns a instead of adding.  POW: the
 // pair function 1/r (1) or 1/r^2 (2), whose force is 2 r/r^4.
-template <typename real, bool FORCES, bool GUARD, bool FIRST, int POW>
+template <typename real, bool FORCES, int CK, bool FIRST, int POW>
 __device__ __forceinline__ void nf_pair(const typename Vec4<real>::T &tv, int to, real sx, real sy, real sz,
                                         real sq, int so, real *a, real &rp, real &rx, real &ry, real &rz) {
     const real dx = tv.x - sx, dy = tv.y - sy, dz = tv.z - sz;
     const real r2 = dx * dx + dy * dy + dz * dz;
     real ri = rsqrt_pair<real>(r2);
-    ri = (so != to && (!GUARD || r2 > real(0))) ? ri : real(0);
+    if (CK >= 1) ri = (so != to && (CK < 2 || r2 > real(0))) ? ri : real(0);
     const real pf = POW == 2 ? ri * ri : ri;  // the pair function
     if (FIRST) a[0] = sq * pf; else a[0] += sq * pf;
     rp += tv.w * pf;
@@ -332,15 +336,17 @@ __device__ __forceinline__ void nf_pair(const typename Vec4<real>::T &tv, int to
 // position negated (d = t + ns = t - s); ntw: the targets' charges negated.
 // The source's reaction accumulates as two partial sums, one per lane, with
 // the sign of ntw (the potential's is flipped back at the end of the pass).
-template <bool FORCES, bool GUARD, bool FIRST, int POW>
+template <bool FORCES, int CK, bool FIRST, int POW>
 __device__ __forceinline__ void nf_pair2(float2 tx, float2 ty, float2 tz, float2 ntw, int to0, int to1,
                                          float2 nsx, float2 nsy, float2 nsz, float2 sq, int so,
                                          float2 *a, float2 &rp, float2 &rx, float2 &ry, float2 &rz) {
     const float2 dx = __fadd2_rn(tx, nsx), dy = __fadd2_rn(ty, nsy), dz = __fadd2_rn(tz, nsz);
     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
     float2 ri = make_float2(rsqrt_pair<float>(r2.x), rsqrt_pair<float>(r2.y));
-    ri.x = (so != to0 && (!GUARD || r2.x > 0.0f)) ? ri.x : 0.0f;
-    ri.y = (so != to1 && (!GUARD || r2.y > 0.0f)) ? ri.y : 0.0f;
+    if (CK >= 1) {
+        ri.x = (so != to0 && (CK < 2 || r2.x > 0.0f)) ? ri.x : 0.0f;
+        ri.y = (so != to1 && (CK < 2 || r2.y > 0.0f)) ? ri.y : 0.0f;
+    }
     const float2 pf = POW == 2 ? __fmul2_rn(ri, ri) : ri;  // the pair function
     if (FIRST) a[0] = __fmul2_rn(sq, pf); else a[0] = __ffma2_rn(sq, pf, a[0]);
     rp = __ffma2_rn(ntw, pf, rp);  // minus the reaction potential
@@ -378,7 +384,7 @@ __device__ __forceinline__ void nf_stage_pair(double4 *, double4 *, int2 *, int,
 // by target pairs; the sums are transposed through shared memory in
 // pair-major order (value (q, c, h) at q*2*NC + 2c + h, target 2q + h, component
 // c) and summed over the warp's lanes in order into wp.
-template <bool FORCES, bool GUARD, int POW, int NT, int KS>
+template <bool FORCES, int CK, int POW, int NT, int KS>
 __device__ __forceinline__ void nf_targets2(const float4 *tpa, const float4 *tpb, const int2 *tpo, int g0, int nt,
                                             const float2 (&nsx)[KS], const float2 (&nsy)[KS],
                                             const float2 (&nsz)[KS], const float2 (&sq)[KS], const int (&so)[KS],
@@ -396,12 +402,12 @@ __device__ __forceinline__ void nf_targets2(const float4 *tpa, const float4 *tpb
         const int2 O = tpo[g0 / 2 + q];
         const float2 tx = make_float2(A.x, A.y), ty = make_float2(A.z, A.w), tz = make_float2(Bv.x, Bv.y);
         const float2 ntw = make_float2(Bv.z, Bv.w);
-        nf_pair2<FORCES, GUARD, true, POW>(tx, ty, tz, ntw, O.x, O.y, nsx[0], nsy[0], nsz[0], sq[0], so[0],
-                                           acc + q * NC, rp[0], rx[0], ry[0], rz[0]);
+        nf_pair2<FORCES, CK, true, POW>(tx, ty, tz, ntw, O.x, O.y, nsx[0], nsy[0], nsz[0], sq[0], so[0],
+                                        acc + q * NC, rp[0], rx[0], ry[0], rz[0]);
 #pragma unroll
         for (int k = 1; k < KS; k++)
-            nf_pair2<FORCES, GUARD, false, POW>(tx, ty, tz, ntw, O.x, O.y, nsx[k], nsy[k], nsz[k], sq[k], so[k],
-                                                acc + q * NC, rp[k], rx[k], ry[k], rz[k]);
+            nf_pair2<FORCES, CK, false, POW>(tx, ty, tz, ntw, O.x, O.y, nsx[k], nsy[k], nsz[k], sq[k], so[k],
+                                             acc + q * NC, rp[k], rx[k], ry[k], rz[k]);
     }
     constexpr int NV = NT * NC;  // values per lane
     __syncwarp();
@@ -420,7 +426,7 @@ __device__ __forceinline__ void nf_targets2(const float4 *tpa, const float4 *tpb
     }
 }
 
-template <typename real, bool FORCES, bool GUARD, int POW>
+template <typename real, bool FORCES, int CK, int POW>
 __global__ void __launch_bounds__(NF_BS, sizeof(real) == 4 ? NF_MINB : 1) k_p2p(int depth, int periodic, const int *__restrict__ leaf_start,
                                                const typename Vec4<real>::T *__restrict__ s_pt,
                                                const int *__restrict__ s_origin,
@@ -595,11 +601,11 @@ __global__ void __launch_bounds__(NF_BS, sizeof(real) == 4 ? NF_MINB : 1) k_p2p(
             int g0 = 0;
             if constexpr (sizeof(real) == 4) {
                 for (; g0 + TG <= nt; g0 += TG)
-                    nf_targets2<FORCES, GUARD, POW, TG, NF_KS>(tpa, tpb, tpo, g0, nt, nsx2, nsy2, nsz2, sq2, so, rp2,
-                                                               rx2, ry2, rz2, tb_w, wpart[warp], lane);
+                    nf_targets2<FORCES, CK, POW, TG, NF_KS>(tpa, tpb, tpo, g0, nt, nsx2, nsy2, nsz2, sq2, so, rp2,
+                                                            rx2, ry2, rz2, tb_w, wpart[warp], lane);
                 for (; g0 < nt; g0 += TR)
-                    nf_targets2<FORCES, GUARD, POW, TR, NF_KS>(tpa, tpb, tpo, g0, nt, nsx2, nsy2, nsz2, sq2, so, rp2,
-                                                               rx2, ry2, rz2, tb_w, wpart[warp], lane);
+                    nf_targets2<FORCES, CK, POW, TR, NF_KS>(tpa, tpb, tpo, g0, nt, nsx2, nsy2, nsz2, sq2, so, rp2,
+                                                            rx2, ry2, rz2, tb_w, wpart[warp], lane);
             }
             for (; g0 + TG <= nt; g0 += TG) {
                 real acc[32];
@@ -607,11 +613,11 @@ __global__ void __launch_bounds__(NF_BS, sizeof(real) == 4 ? NF_MINB : 1) k_p2p(
                 for (int u = 0; u < TG; u++) {
                     const real4 tv = tpos[g0 + u];
                     const int to = tori[g0 + u];
-                    nf_pair<real, FORCES, GUARD, true, POW>(tv, to, sx[0], sy[0], sz[0], sq[0], so[0], acc + u * NC,
+                    nf_pair<real, FORCES, CK, true, POW>(tv, to, sx[0], sy[0], sz[0], sq[0], so[0], acc + u * NC,
                                                        rp[0], rx[0], ry[0], rz[0]);
 #pragma unroll
                     for (int k = 1; k < NF_KS; k++)
-                        nf_pair<real, FORCES, GUARD, false, POW>(tv, to, sx[k], sy[k], sz[k], sq[k], so[k],
+                        nf_pair<real, FORCES, CK, false, POW>(tv, to, sx[k], sy[k], sz[k], sq[k], so[k],
                                                             acc + u * NC, rp[k], rx[k], ry[k], rz[k]);
                 }
                 // transpose through shared memory: lane l sums value l over the lanes in order
@@ -631,11 +637,11 @@ __global__ void __launch_bounds__(NF_BS, sizeof(real) == 4 ? NF_MINB : 1) k_p2p(
                 for (int u = 0; u < TR; u++) {
                     const real4 tv = tpos[g0 + u];
                     const int to = tori[g0 + u];
-                    nf_pair<real, FORCES, GUARD, true, POW>(tv, to, sx[0], sy[0], sz[0], sq[0], so[0], acc + u * NC,
+                    nf_pair<real, FORCES, CK, true, POW>(tv, to, sx[0], sy[0], sz[0], sq[0], so[0], acc + u * NC,
                                                        rp[0], rx[0], ry[0], rz[0]);
 #pragma unroll
                     for (int k = 1; k < NF_KS; k++)
-                        nf_pair<real, FORCES, GUARD, false, POW>(tv, to, sx[k], sy[k], sz[k], sq[k], so[k],
+                        nf_pair<real, FORCES, CK, false, POW>(tv, to, sx[k], sy[k], sz[k], sq[k], so[k],
                                                             acc + u * NC, rp[k], rx[k], ry[k], rz[k]);
                 }
                 __syncwarp();
@@ -809,8 +815,10 @@ void launch_p2p(const Geom &g, const Ptrs<real> &P, const WsLayout &W, bool forc
                 cudaStream_t st, Tracer &tr) {
     const int ncell = (int)W.ncell, depth = g.depth;
     tr.begin(FMM_STAGE_P2P, st);
-    // charges of different cells can coincide only on split planes with odd p
-    const bool guard = g.continuous && (g.p & 1);
+    // pairs to skip (see k_p2p): none in the plain form; charges of the same
+    // particle in the continuous form; also coincident charges there with odd p
+    // (split charges on the cell plane)
+    const int ck = !g.continuous ? 0 : ((g.p & 1) ? 2 : 1);
     // the launch order pays off where a few heavy cells could start late
     // among many light ones; grids of fewer than 32,768 cells go in cell order
     const int *pord = W.ncell >= 32768 ? P.pord : nullptr;
@@ -822,21 +830,23 @@ void launch_p2p(const Geom &g, const Ptrs<real> &P, const WsLayout &W, bool forc
         k_nf_order_fill<<<nb, 256, 0, st>>>(W.ncell, P.leaf_start, P.pord);
         tr.count();
     }
-#define LAUNCH(F, G)                                                                               \
+#define LAUNCH(F, CK)                                                                              \
     do {                                                                                           \
         if (g.power == 2)                                                                          \
-            k_p2p<real, F, G, 2><<<ncell, NF_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt, \
+            k_p2p<real, F, CK, 2><<<ncell, NF_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt, \
                                                           P.s_origin, P.out_pt, P.react, W.cap, pord);   \
         else                                                                                       \
-            k_p2p<real, F, G, 1><<<ncell, NF_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt, \
+            k_p2p<real, F, CK, 1><<<ncell, NF_BS, 0, st>>>(depth, g.periodic, P.leaf_start, P.s_pt, \
                                                           P.s_origin, P.out_pt, P.react, W.cap, pord);   \
     } while (0)
     if (forces) {
-        if (guard) LAUNCH(true, true);
-        else LAUNCH(true, false);
+        if (ck == 2) LAUNCH(true, 2);
+        else if (ck == 1) LAUNCH(true, 1);
+        else LAUNCH(true, 0);
     } else {
-        if (guard) LAUNCH(false, true);
-        else LAUNCH(false, false);
+        if (ck == 2) LAUNCH(false, 2);
+        else if (ck == 1) LAUNCH(false, 1);
+        else LAUNCH(false, 0);
     }
 #undef LAUNCH
     tr.count();

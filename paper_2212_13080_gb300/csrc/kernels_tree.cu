@@ -804,6 +804,7 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
     __shared__ float csum[SD_WARPS][2][CH][32];        // per-lane compensated sums per charge (several axes)
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int S = g.S, p = g.p, p3 = g.p3;
+    constexpr int PM = CH;  // p <= PM: the launch picks CH = 4, 6 or 8 by p
     const int n1 = slist[0], nmul = slist[1];
     const int m1 = p + (p & 1);
     const int nchm = (m1 * m1 * m1 + CH - 1) / CH;  // chunks of a particle split along several axes, at most
@@ -934,19 +935,19 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
                 t = (double)th + (double)tl;
             }
             {
-                double w[FMM_MAXP];
-                lag_weights<double>(Cd, p, t, w);  // one pass for all lanes
+                double w[PM];
+                lag_weights<double, PM>(Cd, p, t, w);  // one pass for all lanes
                 if (lane >= 16 && lane < 19) {
                     double *dst = lane == 16 ? wr : (lane == 17 ? wb : wc);
 #pragma unroll
-                    for (int k = 0; k < FMM_MAXP; k++)
+                    for (int k = 0; k < PM; k++)
                         if (k < p) dst[k] = w[k];
                 }
                 __syncwarp();
                 if (lane < m) {
                     const bool upk = (sidek >> a1) & 1;
 #pragma unroll
-                    for (int k = 0; k < FMM_MAXP; k++)
+                    for (int k = 0; k < PM; k++)
                         if (k < p) dw[lane * FMM_MAXP + k] = (float)(w[k] - (upk ? (k == 0 ? 1.0 : 0.0) : wr[k]));
                 }
             }
@@ -962,17 +963,17 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
             const int64_t cl = loc_cell(g.depth, (base[0] + S) % S, (base[1] + S) % S, (base[2] + S) % S);
             const int64_t cu = loc_cell(g.depth, (base[0] + (a1 == 0) + S) % S, (base[1] + (a1 == 1) + S) % S,
                                         (base[2] + (a1 == 2) + S) % S);
-            float fk[SD_KMAX];
+            float fk[PM];  // m <= p + (p & 1) <= PM charges
 #pragma unroll
-            for (int k = 0; k < SD_KMAX; k++) fk[k] = 0.0f;
+            for (int k = 0; k < PM; k++) fk[k] = 0.0f;
             double X = 0.0;
             for (int ln = lane; ln < p * p; ln += 32) {
                 const int jb = ln % p, jc = ln / p;
                 const float *Ll = loc_leaf + cl * p3 + jb * sb + jc * sc, *Lu = loc_leaf + cu * p3 + jb * sb + jc * sc;
-                float L0[FMM_MAXP], L1[FMM_MAXP];
+                float L0[PM], L1[PM];
                 double xs = 0.0;
 #pragma unroll
-                for (int a = 0; a < FMM_MAXP; a++) {
+                for (int a = 0; a < PM; a++) {
                     L0[a] = a < p ? Ll[a * sa] : 0.0f;
                     L1[a] = a < p ? Lu[a * sa] : 0.0f;
                     if (a < p) xs -= wr[a] * (double)L0[a];
@@ -981,13 +982,13 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
                 X += wbc * (xs + (double)L1[0]);
                 const float fbc = (float)wbc;
 #pragma unroll
-                for (int k = 0; k < SD_KMAX; k++) {
+                for (int k = 0; k < PM; k++) {
                     if (k < m) {
                         const bool upk = (ks[k] >> a1) & 1;
                         const float *d = dw + k * FMM_MAXP;
                         float s = 0.0f;
 #pragma unroll
-                        for (int a = 0; a < FMM_MAXP; a++)
+                        for (int a = 0; a < PM; a++)
                             if (a < p) s = fmaf(d[a], upk ? L1[a] : L0[a], s);
                         fk[k] = fmaf(fbc, s, fk[k]);
                     }
@@ -995,7 +996,7 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
             }
             float myf = 0.0f;
 #pragma unroll
-            for (int k = 0; k < SD_KMAX; k++) {
+            for (int k = 0; k < PM; k++) {
                 if (k < m) {
                     float v = fk[k];
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1011,7 +1012,7 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
             // h^6 leave h^7 < 4e-9 of each term (8 h^7 for 1/r^2)
             float far2 = 0.0f;
 #pragma unroll
-            for (int k = 0; k < SD_KMAX; k++)
+            for (int k = 0; k < PM; k++)
                 if (k < m) far2 = fmaxf(far2, 256.0f * kq[k * 12 + a1] * kq[k * 12 + a1]);
             bool outer_direct = false;
 #pragma unroll 1
@@ -1140,10 +1141,10 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
                     int side;
                     float th, tl, tfl;
                     split_entry_df(g, A[a], e, side, th, tl, tfl);
-                    double w[FMM_MAXP];
-                    lag_weights<double>(Cd, p, (double)th + (double)tl, w);
+                    double w[PM];
+                    lag_weights<double, PM>(Cd, p, (double)th + (double)tl, w);
 #pragma unroll
-                    for (int k = 0; k < FMM_MAXP; k++)
+                    for (int k = 0; k < PM; k++)
                         if (k < p) W[a][e][k] = w[k];
                 }
             }

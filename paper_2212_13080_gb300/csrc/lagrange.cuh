@@ -5,21 +5,21 @@
 
 namespace fmm {
 
-// all p weights g_i(t), by prefix/suffix products
-template <typename real>
+// all p weights g_i(t), by prefix/suffix products; p <= NMAX, g holds NMAX
+template <typename real, int NMAX = FMM_MAXP>
 __device__ __forceinline__ void lag_weights(const Coef<real> &C, int p, real t, real *g) {
-    real d[FMM_MAXP];
+    real d[NMAX];
 #pragma unroll
-    for (int k = 0; k < FMM_MAXP; k++) d[k] = (k < p) ? t - C.tau[k] : real(1);
+    for (int k = 0; k < NMAX; k++) d[k] = (k < p) ? t - C.tau[k] : real(1);
     real pre = 1;
 #pragma unroll
-    for (int i = 0; i < FMM_MAXP; i++) {
+    for (int i = 0; i < NMAX; i++) {
         g[i] = pre;
         pre *= d[i];
     }
     real suf = 1;
 #pragma unroll
-    for (int i = FMM_MAXP - 1; i >= 0; i--) {
+    for (int i = NMAX - 1; i >= 0; i--) {
         if (i < p) {
             g[i] *= suf * C.cinv[i];
             suf *= d[i];
