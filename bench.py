@@ -385,7 +385,7 @@ def run_batch(args, world, rank, local, dist=None):
         outs["fp32"] = {k: v.cpu().numpy() for k, v in out.items()}
         plain = {"precision": "fp32", "ms_per_step": statistics.mean(t32),
                  "value": world * n / (statistics.mean(t32) * 1e-3) / 1e6, "unit": UNIT,
-                 "lanes": b32.stats()["lanes"]}
+                 "merged": b32.stats()["merged"], "schedule": b32.stats()["schedule"]}
         b32.close()
     res = None
     if rank == 0:
@@ -401,7 +401,8 @@ def run_batch(args, world, rank, local, dist=None):
                        "outputs": "potential+energy+forces per system",
                        "l2": "flushed (256 MB write) before every timed step"},
             "gpu_launches": st["launches"] * args.steps, "graph_launches_per_step": 1,
-            "lanes": st["lanes"], "tune_ms": st["tune_ms"], "clocks": clocks,
+            "merged": st["merged"], "schedule": st["schedule"], "lanes": st["lanes"],
+            "tune_ms": st["tune_ms"], "clocks": clocks,
             "plain_fp32": plain}
         if world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"], res["error_vs_fp64_oracle"] = batch_cpu_baseline(

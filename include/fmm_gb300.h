@@ -318,25 +318,37 @@ int fmm_batch_workspace_size(fmm_batch_t batch, const int64_t *n, size_t *bytes)
  * fmm_batch_eval — evaluates every system.  Particles of system i are rows
  * offsets[i] .. offsets[i+1]-1 (offsets: host, nsys + 1, CSR) of pos (device,
  * float32 (N,3)), q, potential and forces (as fmm_eval); energy: device,
- * nsys doubles (nullable).  The systems are spread over several stream lanes
- * forked from and joined back to `stream`; the whole launch sequence is
- * captured once into a CUDA graph and replayed by later calls with the same
- * pointers and counts (one graph launch per call).  The number of lanes is
- * chosen by timing candidates on the first call (fmm_batch_get_stats reports
- * it).  Returns the first device-side error of any system (opts.sync = 1).
+ * nsys doubles (nullable).  Every kernel launch site of an evaluation runs
+ * once for all systems: each system's launch parameters are recorded, and
+ * one launch of the site covers every system's blocks (a block finds its
+ * system from the prefix of the systems' block counts), so each system's
+ * results equal its single-system evaluation bit for bit.  The merged
+ * launches are captured once into a CUDA graph and replayed by later calls
+ * with the same pointers and counts (one graph launch per call); the first
+ * call times the schedules (one stream, or the near field on a second stream)
+ * and keeps the faster (fmm_batch_get_stats reports it).  Batches whose
+ * systems' launch sequences do not merge (FP64 plans) run as per-system
+ * pipelines spread over stream lanes instead, their count chosen the same
+ * way.  Returns the first device-side error of any system (opts.sync = 1).
  */
 int fmm_batch_eval(fmm_batch_t batch, const int64_t *offsets, const float *pos, const float *q,
                    void *potential, double *energy, void *forces, void *workspace,
                    size_t workspace_bytes, void *stream);
 
 /* launches: kernels launched by the last fmm_batch_eval (inside its graph);
- * lanes: stream lanes chosen by the autotuner; graph: 1 if the last call
- * replayed a captured graph. */
+ * merged: 1 if every call site ran as one launch for all systems; schedule:
+ * the merged form's schedule chosen by the autotuner (0: one stream, 1: the
+ * near field on a second stream beside the rest); lanes: stream lanes of the
+ * per-system form (0 when merged); graph: 1 if the last call replayed a
+ * captured graph. */
 typedef struct {
     int launches;
     int lanes;
     int graph;
-    double tune_ms[8];  /* measured ms per call of lanes = 2, 4, 8, 16, 32 (first call) */
+    double tune_ms[8];  /* ms per call measured on the first call: lanes = 2, 4, 8, 16, 32
+                           (per-system form) at [0..4], schedules 0 and 1 (merged) at [5], [6] */
+    int merged;
+    int schedule;
 } fmm_batch_stats_t;
 int fmm_batch_get_stats(fmm_batch_t batch, fmm_batch_stats_t *stats);
 

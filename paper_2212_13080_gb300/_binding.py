@@ -75,7 +75,7 @@ class fmm_stats_t(ctypes.Structure):
 
 class fmm_batch_stats_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int), ("lanes", ctypes.c_int), ("graph", ctypes.c_int),
-                ("tune_ms", ctypes.c_double * 8)]
+                ("tune_ms", ctypes.c_double * 8), ("merged", ctypes.c_int), ("schedule", ctypes.c_int)]
 
 
 class FmmError(RuntimeError):
@@ -241,5 +241,8 @@ def fmm_batch_eval(h, offsets, pos, q, potential, energy, forces, workspace, ws_
 def fmm_batch_get_stats(h):
     st = fmm_batch_stats_t()
     _check(lib().fmm_batch_get_stats(h, ctypes.byref(st)), "fmm_batch_get_stats")
-    return {"launches": st.launches, "lanes": st.lanes, "graph": bool(st.graph),
-            "tune_ms": dict(zip([2, 4, 8, 16, 32], list(st.tune_ms)[:5]))}
+    tm = list(st.tune_ms)
+    return {"launches": st.launches, "lanes": st.lanes, "graph": bool(st.graph), "merged": bool(st.merged),
+            "schedule": st.schedule,
+            "tune_ms": ({"one_stream": tm[5], "near_stream": tm[6]} if st.merged
+                        else dict(zip([2, 4, 8, 16, 32], tm[:5])))}

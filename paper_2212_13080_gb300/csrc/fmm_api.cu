@@ -10,9 +10,24 @@
 #include <vector>
 
 #include "fmm_internal.cuh"
+#include "launch.cuh"
 
 namespace fmm {
 void far_set_attributes();
+
+__global__ void __launch_bounds__(KZero::BS, KZero::MINB) k_zero_words(const __grid_constant__ KZero k) {
+    k.run(blockIdx.x, gridDim.x);
+}
+
+void zero_words(Tracer &tr, int tag, void *p, size_t bytes, cudaStream_t st) {
+    if (!tr.rec) {
+        cudaMemsetAsync(p, 0, bytes, st);
+        return;
+    }
+    const int64_t nw = (int64_t)(bytes / 4);
+    const int blocks = (int)std::min<int64_t>(152 * 8, std::max<int64_t>(1, (nw + 4 * KZero::BS - 1) / (4 * KZero::BS)));
+    launch_k(tr, tag, k_zero_words, KZero{reinterpret_cast<int *>(p), nw}, blocks, KZero::BS, 0, st);
+}
 }
 
 using namespace fmm;
@@ -478,9 +493,19 @@ int status_to_error(int st) {
     return FMM_OK;
 }
 
-__global__ void k_mark_valid(WsHeader *hdr, long long tag) {
-    hdr->valid = 1;
-    hdr->tag = tag;
+struct KMarkValid {
+    static constexpr int BS = 32, MINB = 1;
+    WsHeader *hdr;
+    long long tag;
+    __device__ void run(int, int) const {
+        if (threadIdx.x == 0) {
+            hdr->valid = 1;
+            hdr->tag = tag;
+        }
+    }
+};
+__global__ void __launch_bounds__(KMarkValid::BS, KMarkValid::MINB) k_mark_valid(const __grid_constant__ KMarkValid k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
 // the backward pass reuses the state of the last evaluation on the workspace:
@@ -516,25 +541,30 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     const Coef<real> &C = *reinterpret_cast<const Coef<real> *>(P->fp64 ? (const void *)&P->cd
                                                                         : (const void *)&P->cf);
     Geom g = P->geom;
-    cudaMemsetAsync(ptr.hdr, 0, 256, st);
+    zero_words(tr, FMM_TAG(S_ZERO_HDR, 0), ptr.hdr, 256, st);
     if (n == 0) {
         launch_unsplit<real>(g, ptr, W, 0, q, potential, energy, forces, nullptr, nullptr, false, st,
                              tr);
         return FMM_OK;
     }
-    cudaMemsetAsync(ptr.leaf_count, 0, W.ncell * 4, st);
+    zero_words(tr, FMM_TAG(S_ZERO_LEAF, 0), ptr.leaf_count, W.ncell * 4, st);
     launch_bin_emit<real>(g, C, ptr, W, (int)n, pos, q, st, tr);
     launch_sort<real>(g, ptr, W, (int)n, st, tr);
     // the near field needs only the sorted charges: it runs on its own stream
     // beside the whole far field and joins before the far field is added
-    cudaEventRecord(S.sorted, st);
-    cudaStreamWaitEvent(S.near, S.sorted, 0);
+    // (recorded launches: the near stream's are marked, the join is a marker)
+    if (!tr.rec) {
+        cudaEventRecord(S.sorted, st);
+        cudaStreamWaitEvent(S.near, S.sorted, 0);
+    }
+    tr.near = S.near;
     launch_p2p<real>(g, ptr, W, forces != nullptr, S.near, tr);
-    cudaEventRecord(S.near_done, S.near);
+    tr.near = nullptr;
+    if (!tr.rec) cudaEventRecord(S.near_done, S.near);
     // the far field runs on a high-priority stream when one is given, so that
     // its CTAs are dispatched ahead of the near field's as SMs free up
     Streams F = S;
-    if (S.far) {
+    if (S.far && !tr.rec) {
         cudaStreamWaitEvent(S.far, S.sorted, 0);
         F.main = S.far;
     }
@@ -564,15 +594,17 @@ int eval_impl(fmm_plan_t P, int64_t n, const float *pos, const float *q, real *p
     if constexpr (std::is_same<real, float>::value)
         if (g.continuous && forces && g.force_mode == FMM_FORCE_ADJOINT)
             launch_split_delta(g, P->cd, ptr, W, (int)n, pos, F.main, tr);
-    if (S.far) {
+    if (S.far && !tr.rec) {
         cudaEventRecord(S.far_done, S.far);
         cudaStreamWaitEvent(st, S.far_done, 0);
     }
-    cudaStreamWaitEvent(st, S.near_done, 0);
+    if (!tr.rec) cudaStreamWaitEvent(st, S.near_done, 0);
+    else record_marker(tr, FMM_TAG(S_JOIN_NEAR, 0));
     launch_l2p<real>(g, C, ptr, W, forces != nullptr, st, tr);
     launch_unsplit<real>(g, ptr, W, (int)n, q, potential, energy, forces, nullptr, nullptr, false,
                          st, tr);
-    k_mark_valid<<<1, 1, 0, st>>>(ptr.hdr, eval_tag(P, n));
+    launch_k(tr, FMM_TAG(S_MARK_VALID, 0), k_mark_valid, KMarkValid{ptr.hdr, eval_tag(P, n)}, 1, KMarkValid::BS, 0,
+             st);
     tr.count();
     return FMM_OK;
 }
@@ -1065,6 +1097,18 @@ struct fmm_batch_s {
     double tune_ms[8];
     int launches;
     bool last_graph;
+    // merged form: one launch per call site for all systems (schedule 1: the
+    // near-field launches on a forked stream beside the rest, 0: one stream;
+    // -1: not yet chosen; merged = false: the systems' sequences do not merge
+    // and the stream lanes are used)
+    bool merged;
+    int schedule;
+    cudaStream_t near;
+    cudaEvent_t near_fork, near_join;
+    char *d_tab;      // per merged launch: the systems' functors and block prefix
+    size_t tab_bytes;
+    void *d_x;        // cross-system contraction tiles: lists and the systems' table
+    size_t x_bytes;
 };
 
 namespace {
@@ -1087,6 +1131,238 @@ fmm_plan_t clone_plan(const fmm_plan_s *m, const double *box, int64_t max_n) {
     P->geom.Lf = (float)box[3];
     P->geom.L = box[3];
     return P;
+}
+
+// One launch of the merged form: the call site's functor type (its launcher),
+// its block size and shared memory, and where its functor array and block
+// prefix lie in the batch's table.
+struct MergedLaunch {
+    int tag;
+    int near;
+    void (*many)(const void *, const int *, int, int, int, size_t, cudaStream_t);
+    void (*set_smem)(size_t);
+    int threads, total;
+    size_t smem;
+    size_t ks_off, first_off;
+};
+
+// Records every system's launch sequence and merges them: equal tags become
+// one launch; the order of the merged launches is a topological order of the
+// systems' sequences (ties: first appearance).  Fails (FMM_ERR_UNSUPPORTED)
+// where the sequences do not merge: an order that conflicts, or one tag with
+// different kernels or launch shapes.  The table (functors, prefixes) is
+// uploaded to the device before the call returns.
+int record_merged(fmm_batch_t B, const std::vector<int64_t> &n, const std::vector<int64_t> &pofs,
+                  const std::vector<size_t> &wofs, const float *pos, const float *q, void *potential,
+                  double *energy, void *forces, char *ws, std::vector<MergedLaunch> &out) {
+    const int ns = B->nsys;
+    if (B->opts.precision == FMM_PREC_FP64) return FMM_ERR_UNSUPPORTED;
+    fmm_plan_t M0 = nullptr;  // the tables (shared by every master: same p, kernel and options)
+    for (fmm_plan_t m : B->masters)
+        if (m && !M0) M0 = m;
+    // tensor-core plans: the levels with fewer than 8 coarse cells per axis
+    // (l <= 3) of every system run as cross-system tiles, full rows; each
+    // system's own contraction takes levels 4 and up
+    const int tc_lmin = M0->tc ? (B->periodic ? 1 : 2) : 0;
+    const int x_lmax = 3;
+    std::vector<std::vector<LaunchRec>> recs(ns);
+    const Lane &L = B->lane[0];
+    Streams S = {L.main, L.near, L.coarse, L.sorted, L.near_done, L.fork, L.coarse_done, nullptr, nullptr};
+    for (int i = 0; i < ns; i++) {
+        Tracer tr;
+        tr.rec = &recs[i];
+        tr.tc_lbig = tc_lmin ? x_lmax + 1 : 0;
+        fmm_plan_t P = B->sys[i];
+        const int64_t o = pofs[i];
+        char *pot = potential ? (char *)potential + o * 4 : nullptr;
+        char *frc = forces ? (char *)forces + 3 * o * 4 : nullptr;
+        double *en = energy ? energy + i : nullptr;
+        int rc = eval_impl<float>(P, n[i], pos + 3 * o, q + o, (float *)pot, en, (float *)frc, ws + wofs[i], S, tr);
+        if (rc) return rc;
+    }
+    if (tc_lmin) {
+        // the cross-system tiles, one launch per kernel component, right after
+        // the operand split of the first system that has one (merged, that
+        // split is every system's)
+        std::vector<TcXSys> xs((size_t)M0->ncomp * ns);
+        std::vector<int> dep(ns);
+        WsLayout W0;
+        for (int i = 0; i < ns; i++) {
+            WsLayout W = make_layout(B->sys[i], n[i]);
+            Ptrs<float> Pi = make_ptrs<float>(W, ws + wofs[i]);
+            if (i == 0) W0 = W;
+            dep[i] = n[i] > 0 ? B->sys[i]->depth : 0;
+            for (int c = 0; c < M0->ncomp; c++)
+                xs[(size_t)c * ns + i] = TcXSys{reinterpret_cast<const char *>(Pi.phihi),
+                                               reinterpret_cast<const char *>(Pi.philo), Pi.qlev,
+                                               Pi.loc + c * W.loc_comp};
+        }
+        const void *khi[4], *klo[4];
+        const float *kb[4];
+        for (int c = 0; c < M0->ncomp; c++) {
+            khi[c] = M0->khi_map[c];
+            klo[c] = M0->klo_map[c];
+            kb[c] = (const float *)M0->Kbar_tc + (size_t)c * 343 * tc_padded(M0->geom.p3);
+        }
+        int *status = &reinterpret_cast<WsHeader *>(ws + wofs[0])->status;
+        std::vector<LaunchRec> xr;
+        int rc = tc_cross_records(xs, dep, M0->ncomp, tc_lmin, x_lmax, M0->geom.p3, M0->tc_mode, M0->geom.power, khi,
+                                  klo, kb, W0, status, &B->d_x, &B->x_bytes, xr);
+        if (rc) return rc;
+        bool placed = false;
+        for (int i = 0; i < ns && !placed; i++)
+            for (size_t k = 0; k < recs[i].size() && !placed; k++)
+                if (recs[i][k].tag == FMM_TAG(S_SPLIT_TC, 0)) {
+                    recs[i].insert(recs[i].begin() + k + 1, xr.begin(), xr.end());
+                    placed = true;
+                }
+    }
+    // tags, their first appearance and the edges between consecutive launches
+    std::vector<int> tags;
+    std::vector<int> first_seen;
+    auto index_of = [&](int tag) {
+        for (size_t k = 0; k < tags.size(); k++)
+            if (tags[k] == tag) return (int)k;
+        tags.push_back(tag);
+        return (int)tags.size() - 1;
+    };
+    std::vector<std::vector<int>> seq(ns);
+    for (int i = 0; i < ns; i++)
+        for (const LaunchRec &r : recs[i]) seq[i].push_back(index_of(r.tag));
+    const int nt = (int)tags.size();
+    std::vector<std::vector<char>> edge(nt, std::vector<char>(nt, 0));
+    std::vector<int> indeg(nt, 0);
+    for (int i = 0; i < ns; i++) {
+        std::vector<char> seen(nt, 0);
+        for (size_t k = 0; k < seq[i].size(); k++) {
+            if (seen[seq[i][k]]) return FMM_ERR_UNSUPPORTED;  // one site twice in a system
+            seen[seq[i][k]] = 1;
+            if (k > 0 && !edge[seq[i][k - 1]][seq[i][k]]) {
+                edge[seq[i][k - 1]][seq[i][k]] = 1;
+                indeg[seq[i][k]]++;
+            }
+        }
+    }
+    std::vector<int> order;
+    std::vector<char> done(nt, 0);
+    for (int it = 0; it < nt; it++) {
+        int pick = -1;
+        for (int t = 0; t < nt && pick < 0; t++)
+            if (!done[t] && indeg[t] == 0) pick = t;
+        if (pick < 0) return FMM_ERR_UNSUPPORTED;  // the orders conflict
+        done[pick] = 1;
+        order.push_back(pick);
+        for (int t = 0; t < nt; t++)
+            if (edge[pick][t]) indeg[t]--;
+    }
+    // per merged launch: the systems' functors and the prefix of their blocks
+    std::vector<const LaunchRec *> by(ns);
+    std::vector<unsigned char> host;
+    auto place = [&](size_t bytes, size_t align) {
+        size_t o = (host.size() + align - 1) / align * align;
+        host.resize(o + bytes, 0);
+        return o;
+    };
+    out.clear();
+    for (int t : order) {
+        const LaunchRec *ref = nullptr;
+        for (int i = 0; i < ns; i++) {
+            by[i] = nullptr;
+            for (size_t k = 0; k < recs[i].size(); k++)
+                if (seq[i][k] == t) by[i] = &recs[i][k];
+            if (!by[i]) continue;
+            if (!ref) ref = by[i];
+            else if (by[i]->many != ref->many || by[i]->threads != ref->threads || by[i]->smem != ref->smem ||
+                     by[i]->ksize != ref->ksize || by[i]->near != ref->near)
+                return FMM_ERR_UNSUPPORTED;
+        }
+        MergedLaunch m;
+        m.tag = tags[t];
+        m.near = ref->near;
+        m.many = ref->many;
+        m.set_smem = ref->set_smem;
+        m.threads = ref->threads;
+        m.smem = ref->smem;
+        m.total = 0;
+        m.ks_off = m.first_off = 0;
+        if (ref->many) {
+            const size_t al = ref->kalign < 16 ? 16 : ref->kalign;
+            m.ks_off = place(ref->ksize * ns, al < 128 ? 128 : al);
+            for (int i = 0; i < ns; i++)
+                if (by[i]) memcpy(host.data() + m.ks_off + i * ref->ksize, by[i]->k.data(), ref->ksize);
+            m.first_off = place(sizeof(int) * (ns + 1), 16);
+            int *first = reinterpret_cast<int *>(host.data() + m.first_off);
+            int64_t tot = 0;
+            for (int i = 0; i < ns; i++) {
+                first[i] = (int)tot;
+                tot += by[i] ? by[i]->blocks : 0;
+            }
+            if (tot > INT32_MAX) return FMM_ERR_UNSUPPORTED;
+            first[ns] = (int)tot;
+            m.total = (int)tot;
+        }
+        out.push_back(m);
+    }
+    if (host.size() > B->tab_bytes) {
+        if (B->d_tab) cudaFree(B->d_tab);
+        B->d_tab = nullptr;
+        B->tab_bytes = 0;
+        if (cudaMalloc(&B->d_tab, host.size()) != cudaSuccess) return FMM_ERR_OOM;
+        B->tab_bytes = host.size();
+    }
+    if (!host.empty() && cudaMemcpy(B->d_tab, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    for (const MergedLaunch &m : out)
+        if (m.set_smem && m.smem > 48 * 1024) m.set_smem(m.smem);
+    return FMM_OK;
+}
+
+// Captures the merged launches: schedule 0 on one stream; schedule 1 with
+// the near-field launches on a stream forked before the first of them and
+// joined back at the marker.
+int capture_merged(fmm_batch_t B, const std::vector<MergedLaunch> &ml, int schedule, const char *ws,
+                   cudaStream_t st, cudaGraphExec_t *out, int *launches) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return FMM_ERR_CUDA;
+    int total = 0;
+    bool forked = false;
+    for (const MergedLaunch &m : ml) {
+        cudaStream_t s = st;
+        if (schedule == 1 && m.near) {
+            if (!forked) {
+                cudaEventRecord(B->near_fork, st);
+                cudaStreamWaitEvent(B->near, B->near_fork, 0);
+                forked = true;
+            }
+            s = B->near;
+        }
+        if (!m.many) {  // the join marker
+            if (forked) {
+                cudaEventRecord(B->near_join, B->near);
+                cudaStreamWaitEvent(st, B->near_join, 0);
+                forked = false;
+            }
+            continue;
+        }
+        if (m.total <= 0) continue;
+        m.many(B->d_tab + m.ks_off, reinterpret_cast<const int *>(B->d_tab + m.first_off), B->nsys, m.total,
+               m.threads, m.smem, s);
+        total++;
+    }
+    if (forked) {
+        cudaEventRecord(B->near_join, B->near);
+        cudaStreamWaitEvent(st, B->near_join, 0);
+    }
+    k_batch_status<<<1, 256, 0, st>>>(ws, B->d_off, B->nsys, B->d_status);
+    total++;
+    cudaMemcpyAsync(B->h_status, B->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (e != cudaSuccess || !graph) return FMM_ERR_CUDA;
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return FMM_ERR_CUDA;
+    *launches = total;
+    return FMM_OK;
 }
 
 int capture_batch(fmm_batch_t B, int lanes, const std::vector<int64_t> &n,
@@ -1211,6 +1487,16 @@ int fmm_batch_create(fmm_batch_t *out, int nsys, const double *boxes, const int 
             cudaMalloc(&B->d_off, sizeof(long long) * nsys) != cudaSuccess)
             rc = FMM_ERR_OOM;
     }
+    B->merged = true;
+    B->schedule = -1;
+    if (rc == FMM_OK) {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&B->near, cudaStreamNonBlocking, lo) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->near_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->near_join, cudaEventDisableTiming) != cudaSuccess)
+            rc = FMM_ERR_CUDA;
+    }
     if (rc != FMM_OK) {
         fmm_batch_destroy(B);
         return rc;
@@ -1243,6 +1529,11 @@ void fmm_batch_destroy(fmm_batch_t B) {
     if (B->d_status) cudaFree(B->d_status);
     if (B->h_status) cudaFreeHost(B->h_status);
     if (B->d_off) cudaFree(B->d_off);
+    if (B->d_tab) cudaFree(B->d_tab);
+    if (B->d_x) cudaFree(B->d_x);
+    if (B->near) cudaStreamDestroy(B->near);
+    if (B->near_fork) cudaEventDestroy(B->near_fork);
+    if (B->near_join) cudaEventDestroy(B->near_join);
     delete B;
 }
 
@@ -1295,7 +1586,10 @@ int fmm_batch_eval(fmm_batch_t B, const int64_t *offsets, const float *pos, cons
     key.insert(key.end(), n.begin(), n.end());
     cudaGetLastError();
     B->last_graph = true;
-    if (!B->gexec || key != B->key || (B->lanes && B->glanes != B->lanes)) {
+    std::vector<MergedLaunch> ml;
+    if (!B->gexec || key != B->key || (!B->merged && B->lanes && B->glanes != B->lanes)) {
+        // the table and offsets are rewritten: nothing of an earlier call may still read them
+        if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_ERR_CUDA;
         std::vector<long long> off(B->nsys);
         for (int i = 0; i < B->nsys; i++) off[i] = (long long)wofs[i];
         if (cudaMemcpy(B->d_off, off.data(), sizeof(long long) * B->nsys, cudaMemcpyHostToDevice) !=
@@ -1305,6 +1599,49 @@ int fmm_batch_eval(fmm_batch_t B, const int64_t *offsets, const float *pos, cons
             cudaGraphExecDestroy(B->gexec);
             B->gexec = nullptr;
         }
+        // the merged form where the systems' sequences merge, else stream lanes
+        rc = B->merged ? record_merged(B, n, pofs, wofs, pos, q, potential, energy, forces, ws, ml)
+                       : FMM_ERR_UNSUPPORTED;
+        if (rc != FMM_OK && rc != FMM_ERR_UNSUPPORTED) return rc;
+        B->merged = rc == FMM_OK;
+    }
+    if (!B->gexec && B->merged) {
+        if (B->schedule < 0) {
+            // autotune the schedule: time each candidate's graph
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            double best = 1e30;
+            int best_s = 0;
+            for (int c = 0; c < 2 && rc == FMM_OK; c++) {
+                cudaGraphExec_t ex = nullptr;
+                int launches = 0;
+                rc = capture_merged(B, ml, c, ws, st, &ex, &launches);
+                if (rc) break;
+                cudaGraphLaunch(ex, st);  // warm-up
+                cudaEventRecord(a, st);
+                for (int r = 0; r < 3; r++) cudaGraphLaunch(ex, st);
+                cudaEventRecord(b, st);
+                cudaEventSynchronize(b);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, b);
+                B->tune_ms[5 + c] = ms / 3.0;
+                if (ms < best) {
+                    best = ms;
+                    best_s = c;
+                }
+                cudaGraphExecDestroy(ex);
+            }
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            if (rc) return rc;
+            B->schedule = best_s;
+        }
+        rc = capture_merged(B, ml, B->schedule, ws, st, &B->gexec, &B->launches);
+        if (rc) return rc;
+        B->key = key;
+    }
+    if (!B->gexec) {
         if (!B->lanes) {
             // autotune the number of stream lanes: time each candidate's graph
             cudaEvent_t a, b;
@@ -1358,9 +1695,11 @@ int fmm_batch_get_stats(fmm_batch_t B, fmm_batch_stats_t *out) {
     if (!B || !out) return FMM_ERR_ARG;
     memset(out, 0, sizeof(*out));
     out->launches = B->launches;
-    out->lanes = B->lanes;
+    out->lanes = B->merged ? 0 : B->lanes;
     out->graph = B->last_graph ? 1 : 0;
-    for (int c = 0; c < 5; c++) out->tune_ms[c] = B->tune_ms[c];
+    for (int c = 0; c < 8; c++) out->tune_ms[c] = B->tune_ms[c];
+    out->merged = B->merged ? 1 : 0;
+    out->schedule = B->merged ? B->schedule : -1;
     return FMM_OK;
 }
 

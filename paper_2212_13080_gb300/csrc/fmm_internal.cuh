@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/fmm_gb300.h"
 
 #define FMM_MAXP 8
@@ -206,9 +208,19 @@ template <typename real> struct Vec4;
 template <> struct Vec4<float> { typedef float4 T; };
 template <> struct Vec4<double> { typedef double4 T; };
 
+struct LaunchRec;  // launch.cuh
+
 // Stage tracer: counts kernel launches and, when on, brackets each stage's
-// kernels with CUDA events on the stream (FMM_STAGE_* ids).
+// kernels with CUDA events on the stream (FMM_STAGE_* ids).  rec: the
+// launches are recorded there instead of issued (batched evaluations merge
+// them across systems; nothing but launches of functor kernels may be issued
+// then: no memset, copy or event).
 struct Tracer {
+    std::vector<LaunchRec> *rec = nullptr;
+    cudaStream_t near = nullptr;  // while recording: the near-field stream
+    // while recording a batch whose small levels run as cross-system tiles:
+    // the first level of a system's own tensor-core contraction
+    int tc_lbig = 0;
     bool on = false;
     cudaStream_t st = 0;
     int launches = 0;
@@ -315,7 +327,7 @@ void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n
 // differences between each split particle's charges (kernels_tree.cu)
 void launch_split_delta(const Geom &g, const Coef<double> &Cd, const Ptrs<float> &P, const WsLayout &W, int n,
                         const float *pos, cudaStream_t st, Tracer &tr);
-int launch_scan(const int *in, int *out, int m, int *tmp, cudaStream_t st);
+int launch_scan(const int *in, int *out, int m, int *tmp, cudaStream_t st, Tracer &tr);
 
 // far field (kernels_far.cu)
 template <typename real>
@@ -341,9 +353,23 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
 // loc: the functionals to write (one kernel component); spow: forms scale by
 // 2^(l spow) at level l; split: also split the grid charges into the operand
 // copies (once per evaluation)
+// one system of a batched evaluation's cross-system contraction tiles
+struct TcXSys {
+    const char *op_hi, *op_lo;  // operand copies (hi, lo) of its grid charges
+    const float *qlev;          // its cell charges
+    float *loc;                 // its functionals (one kernel component)
+};
+// The launches (one per kernel component) of the cross-system tiles of a
+// batch: levels lmin..lmax of every system, all cells.  sys: ncomp x nsys
+// (component-major); depth: per system.  The lists and the per-system table
+// are written to the device buffer *dx (grown as needed, owned by the caller).
+int tc_cross_records(const std::vector<TcXSys> &sys, const std::vector<int> &depth, int ncomp, int lmin,
+                     int lmax, int p3, int mode, int spow0, const void *const *k_hi_maps,
+                     const void *const *k_lo_maps, const float *const *kbars, const WsLayout &W, int *status,
+                     void **dx, size_t *dx_bytes, std::vector<LaunchRec> &out);
 int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const void *k_hi_map,
                   const void *k_lo_map, const float *kbar, int lmin, int mode, int inject,
-                  float *loc, int spow, bool split, cudaStream_t st, Tracer &tr);
+                  float *loc, int spow, bool split, int comp, cudaStream_t st, Tracer &tr);
 // map of a [343][p3s][pk] kernel table: fp32 (pk = p3s) or bf16 (pk = tc_padded_k)
 int tc_encode_kernel_map(void *map, const void *base, int p3s, int pk, int mode);
 int tc_padded(int p3);            // p^3 rounded up to 32 (MMA N, fp32 K)

@@ -4,6 +4,7 @@
 #include <type_traits>
 
 #include "fmm_internal.cuh"
+#include "launch.cuh"
 #include "lagrange.cuh"
 
 namespace fmm {
@@ -150,53 +151,69 @@ __device__ __forceinline__ int split_count_one(const Geom &g, const float *__res
 // emits every particle (n_eff = n); the continuous form's n_eff was set by the
 // scan of the charge counts.
 template <typename real>
-__global__ void k_emit(Geom g, Coef<real> C, int n, const float *__restrict__ pos,
-                       const float *__restrict__ q, const int *__restrict__ offset,
-                       uint32_t *__restrict__ e_key, typename Vec4<real>::T *__restrict__ e_pt,
-                       typename Vec4<real>::T *__restrict__ e_wd, int *__restrict__ e_origin,
-                       int *__restrict__ e_rank, int *__restrict__ leaf_count, WsHeader *hdr) {
-    int st = 0;
-    const int ne = offset ? hdr->n_eff : n;
-    if (!offset && blockIdx.x == 0 && threadIdx.x == 0) hdr->n_eff = n;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-        const int i = offset ? e_origin[e] : e;
-        int k = offset ? e - offset[i] : 0;
-        AxisInfo A[3];
-        for (int a = 0; a < 3; a++) {
-            float t;
-            int c;
-            bin_axis(g, pos[3 * i + a], a, t, c, st);
-            A[a] = split_axis_info(g, c, t);
+struct KEmit {
+    static constexpr int BS = 0, MINB = 0;
+    Geom g;
+    Coef<real> C;
+    int n;
+    const float *__restrict__ pos;
+    const float *__restrict__ q;
+    const int *__restrict__ offset;
+    uint32_t *__restrict__ e_key;
+    typename Vec4<real>::T *__restrict__ e_pt;
+    typename Vec4<real>::T *__restrict__ e_wd;
+    int *__restrict__ e_origin;
+    int *__restrict__ e_rank;
+    int *__restrict__ leaf_count;
+    WsHeader *hdr;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        int st = 0;
+        const int ne = offset ? hdr->n_eff : n;
+        if (!offset && bid_ == 0 && threadIdx.x == 0) hdr->n_eff = n;
+        for (int e = bid_ * blockDim.x + threadIdx.x; e < ne; e += nblk_ * blockDim.x) {
+            const int i = offset ? e_origin[e] : e;
+            int k = offset ? e - offset[i] : 0;
+            AxisInfo A[3];
+            for (int a = 0; a < 3; a++) {
+                float t;
+                int c;
+                bin_axis(g, pos[3 * i + a], a, t, c, st);
+                A[a] = split_axis_info(g, c, t);
+            }
+            const int ex = k % A[0].m;
+            k /= A[0].m;
+            const int ey = k % A[1].m, ez = k / A[1].m;
+            int cx, cy, cz;
+            real tx, ty, tz, wx, wy, wz, dwx, dwy, dwz;
+            split_entry(g, C, A[0], ex, cx, tx, wx, dwx);
+            split_entry(g, C, A[1], ey, cy, ty, wy, dwy);
+            split_entry(g, C, A[2], ez, cz, tz, wz, dwz);
+            const real W = wx * wy * wz;
+            const uint32_t key = morton_encode(cx, cy, cz);
+            e_key[e] = key;
+            typename Vec4<real>::T v;
+            v.x = tx;
+            v.y = ty;
+            v.z = tz;
+            v.w = (real)q[i] * W;
+            e_pt[e] = v;
+            if (e_wd) {
+                typename Vec4<real>::T d;
+                d.x = W;
+                d.y = dwx * wy * wz;
+                d.z = wx * dwy * wz;
+                d.w = wx * wy * dwz;
+                e_wd[e] = d;
+            }
+            if (!offset) e_origin[e] = i;
+            e_rank[e] = atomicAdd(&leaf_count[key], 1);
         }
-        const int ex = k % A[0].m;
-        k /= A[0].m;
-        const int ey = k % A[1].m, ez = k / A[1].m;
-        int cx, cy, cz;
-        real tx, ty, tz, wx, wy, wz, dwx, dwy, dwz;
-        split_entry(g, C, A[0], ex, cx, tx, wx, dwx);
-        split_entry(g, C, A[1], ey, cy, ty, wy, dwy);
-        split_entry(g, C, A[2], ez, cz, tz, wz, dwz);
-        const real W = wx * wy * wz;
-        const uint32_t key = morton_encode(cx, cy, cz);
-        e_key[e] = key;
-        typename Vec4<real>::T v;
-        v.x = tx;
-        v.y = ty;
-        v.z = tz;
-        v.w = (real)q[i] * W;
-        e_pt[e] = v;
-        if (e_wd) {
-            typename Vec4<real>::T d;
-            d.x = W;
-            d.y = dwx * wy * wz;
-            d.z = wx * dwy * wz;
-            d.w = wx * wy * dwz;
-            e_wd[e] = d;
-        }
-        if (!offset) e_origin[e] = i;
-        e_rank[e] = atomicAdd(&leaf_count[key], 1);
+        if (st) atomicOr(&hdr->status, st);
     }
-    if (st) atomicOr(&hdr->status, st);
+};
+template <typename real>
+__global__ void k_emit(const __grid_constant__ KEmit<real> k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -241,55 +258,83 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sh, int &total) {
     return pre;
 }
 
-__global__ void k_scan_reduce(const int *__restrict__ in, int m, int *__restrict__ bsum) {
-    __shared__ int sh[32];
-    int base = blockIdx.x * SCAN_TILE;
-    int s = 0;
-    for (int k = 0; k < SCAN_IPT; k++) {
-        int i = base + k * SCAN_BS + threadIdx.x;
-        if (i < m) s += in[i];
+struct KScanReduce {
+    static constexpr int BS = 0, MINB = 0;
+    const int *__restrict__ in;
+    int m;
+    int *__restrict__ bsum;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        __shared__ int sh[32];
+        int base = bid_ * SCAN_TILE;
+        int s = 0;
+        for (int k = 0; k < SCAN_IPT; k++) {
+            int i = base + k * SCAN_BS + threadIdx.x;
+            if (i < m) s += in[i];
+        }
+        int tot;
+        block_excl_scan(s, sh, tot);
+        if (threadIdx.x == 0) bsum[bid_] = tot;
     }
-    int tot;
-    block_excl_scan(s, sh, tot);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+};
+__global__ void k_scan_reduce(const __grid_constant__ KScanReduce k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
 // first pass over the particles (continuous form): charges per particle and
 // split axes (§2.3), written out and summed per block
-__global__ void k_split_count_reduce(Geom g, int n, const float *__restrict__ pos, int *__restrict__ count,
-                                     unsigned char *__restrict__ axes, int *__restrict__ bsum,
-                                     WsHeader *hdr) {
-    __shared__ int sh[32];
-    const int base = blockIdx.x * SCAN_TILE;
-    int s = 0, st = 0;
-    for (int k = 0; k < SCAN_IPT; k++) {
-        const int i = base + k * SCAN_BS + threadIdx.x;
-        if (i < n) {
-            unsigned char ax;
-            const int m = split_count_one(g, pos, i, ax, st);
-            count[i] = m;
-            axes[i] = ax;
-            s += m;
+struct KSplitCount {
+    static constexpr int BS = 0, MINB = 0;
+    Geom g;
+    int n;
+    const float *__restrict__ pos;
+    int *__restrict__ count;
+    unsigned char *__restrict__ axes;
+    int *__restrict__ bsum;
+    WsHeader *hdr;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        __shared__ int sh[32];
+        const int base = bid_ * SCAN_TILE;
+        int s = 0, st = 0;
+        for (int k = 0; k < SCAN_IPT; k++) {
+            const int i = base + k * SCAN_BS + threadIdx.x;
+            if (i < n) {
+                unsigned char ax;
+                const int m = split_count_one(g, pos, i, ax, st);
+                count[i] = m;
+                axes[i] = ax;
+                s += m;
+            }
         }
+        int tot;
+        block_excl_scan(s, sh, tot);
+        if (threadIdx.x == 0) bsum[bid_] = tot;
+        if (st) atomicOr(&hdr->status, st);
     }
-    int tot;
-    block_excl_scan(s, sh, tot);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
-    if (st) atomicOr(&hdr->status, st);
+};
+__global__ void k_split_count_reduce(const __grid_constant__ KSplitCount k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
-__global__ void k_scan_blocks(int *bsum, int nb) {
-    __shared__ int sh[32];
-    int carry = 0;
-    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
-        int i = b0 + threadIdx.x;
-        int v = i < nb ? bsum[i] : 0;
-        int tot;
-        int pre = block_excl_scan(v, sh, tot);
-        if (i < nb) bsum[i] = carry + pre;
-        carry += tot;
+struct KScanBlocks {
+    static constexpr int BS = 0, MINB = 0;
+    int *bsum;
+    int nb;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        __shared__ int sh[32];
+        int carry = 0;
+        for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+            int i = b0 + threadIdx.x;
+            int v = i < nb ? bsum[i] : 0;
+            int tot;
+            int pre = block_excl_scan(v, sh, tot);
+            if (i < nb) bsum[i] = carry + pre;
+            carry += tot;
+        }
+        if (threadIdx.x == 0) bsum[nb] = carry;
     }
-    if (threadIdx.x == 0) bsum[nb] = carry;
+};
+__global__ void k_scan_blocks(const __grid_constant__ KScanBlocks k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
 // Exclusive scan of a CTA's tile of 128 * IT entries per warp from base: warp
@@ -363,58 +408,80 @@ __device__ __forceinline__ void mark_one(int i, int m, int pre, int cnt, int cap
 }
 
 template <bool MARK>
-__global__ void __launch_bounds__(SCAN_BS) k_scan_apply(const int *__restrict__ in, int m, const int *__restrict__ bsum,
-                                                        int *__restrict__ out, int cap, int *__restrict__ e_origin,
-                                                        WsHeader *hdr) {
-    __shared__ int sh[32];
-    constexpr int IT = SCAN_TILE / SCAN_BS / 4;
-    const int base = blockIdx.x * SCAN_TILE;
-    int4 v[IT];
-    int pre[IT];
-    int tot;
-    tile_scan<IT>(in, base, m, v, pre, sh, tot);
-    const int carry = bsum[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+struct KScanApply {
+    static constexpr int BS = SCAN_BS, MINB = 0;  // bounds on the block size only
+    const int *__restrict__ in;
+    int m;
+    const int *__restrict__ bsum;
+    int *__restrict__ out;
+    int cap;
+    int *__restrict__ e_origin;
+    WsHeader *hdr;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        __shared__ int sh[32];
+        constexpr int IT = SCAN_TILE / SCAN_BS / 4;
+        const int base = bid_ * SCAN_TILE;
+        int4 v[IT];
+        int pre[IT];
+        int tot;
+        tile_scan<IT>(in, base, m, v, pre, sh, tot);
+        const int carry = bsum[bid_];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int it = 0; it < IT; it++) {
-        const int i = base + (warp * IT + it) * 128 + 4 * lane;
-        const int p = pre[it] + carry;
-        tile_store(out, i, m, p, v[it]);
-        mark_one<MARK>(i, m, p, v[it].x, cap, e_origin, hdr);
-        mark_one<MARK>(i + 1, m, p + v[it].x, v[it].y, cap, e_origin, hdr);
-        mark_one<MARK>(i + 2, m, p + v[it].x + v[it].y, v[it].z, cap, e_origin, hdr);
-        mark_one<MARK>(i + 3, m, p + v[it].x + v[it].y + v[it].z, v[it].w, cap, e_origin, hdr);
+        for (int it = 0; it < IT; it++) {
+            const int i = base + (warp * IT + it) * 128 + 4 * lane;
+            const int p = pre[it] + carry;
+            tile_store(out, i, m, p, v[it]);
+            mark_one<MARK>(i, m, p, v[it].x, cap, e_origin, hdr);
+            mark_one<MARK>(i + 1, m, p + v[it].x, v[it].y, cap, e_origin, hdr);
+            mark_one<MARK>(i + 2, m, p + v[it].x + v[it].y, v[it].z, cap, e_origin, hdr);
+            mark_one<MARK>(i + 3, m, p + v[it].x + v[it].y + v[it].z, v[it].w, cap, e_origin, hdr);
+        }
+        if (bid_ == nblk_ - 1 && threadIdx.x == 0) {
+            const int total = bsum[nblk_];
+            out[m] = total;
+            if (MARK && total <= cap) hdr->n_eff = total;
+        }
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        const int total = bsum[gridDim.x];
-        out[m] = total;
-        if (MARK && total <= cap) hdr->n_eff = total;
-    }
+};
+template <bool MARK>
+__global__ void __launch_bounds__(KScanApply<MARK>::BS) k_scan_apply(const __grid_constant__ KScanApply<MARK> k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
 // m <= SCAN1_MAX: the whole array is one tile of the CTA
-__global__ void __launch_bounds__(SCAN1_BS) k_scan_one(const int *__restrict__ in, int m, int *__restrict__ out) {
-    __shared__ int sh[32];
-    constexpr int IT = SCAN1_MAX / SCAN1_BS / 4;
-    int4 v[IT];
-    int pre[IT];
-    int tot;
-    tile_scan<IT>(in, 0, m, v, pre, sh, tot);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+struct KScanOne {
+    static constexpr int BS = SCAN1_BS, MINB = 0;  // bounds on the block size only
+    const int *__restrict__ in;
+    int m;
+    int *__restrict__ out;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        __shared__ int sh[32];
+        constexpr int IT = SCAN1_MAX / SCAN1_BS / 4;
+        int4 v[IT];
+        int pre[IT];
+        int tot;
+        tile_scan<IT>(in, 0, m, v, pre, sh, tot);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int it = 0; it < IT; it++) tile_store(out, (warp * IT + it) * 128 + 4 * lane, m, pre[it], v[it]);
-    if (threadIdx.x == 0) out[m] = tot;
+        for (int it = 0; it < IT; it++) tile_store(out, (warp * IT + it) * 128 + 4 * lane, m, pre[it], v[it]);
+        if (threadIdx.x == 0) out[m] = tot;
+    }
+};
+__global__ void __launch_bounds__(KScanOne::BS) k_scan_one(const __grid_constant__ KScanOne k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
-int launch_scan(const int *in, int *out, int m, int *tmp, cudaStream_t st) {
+int launch_scan(const int *in, int *out, int m, int *tmp, cudaStream_t st, Tracer &tr) {
     if (m <= SCAN1_MAX) {
-        k_scan_one<<<1, SCAN1_BS, 0, st>>>(in, m, out);
+        launch_k(tr, FMM_TAG(S_SCAN_ONE, 0), k_scan_one, KScanOne{in, m, out}, 1, SCAN1_BS, 0, st);
         return 1;
     }
     int nb = (m + SCAN_TILE - 1) / SCAN_TILE;
-    k_scan_reduce<<<nb, SCAN_BS, 0, st>>>(in, m, tmp);
-    k_scan_blocks<<<1, 1024, 0, st>>>(tmp, nb);
-    k_scan_apply<false><<<nb, SCAN_BS, 0, st>>>(in, m, tmp, out, 0, nullptr, nullptr);
+    launch_k(tr, FMM_TAG(S_SCAN_REDUCE, 0), k_scan_reduce, KScanReduce{in, m, tmp}, nb, SCAN_BS, 0, st);
+    launch_k(tr, FMM_TAG(S_SCAN_BLOCKS, 0), k_scan_blocks, KScanBlocks{tmp, nb}, 1, 1024, 0, st);
+    launch_k(tr, FMM_TAG(S_SCAN_APPLY, 0), k_scan_apply<false>,
+             KScanApply<false>{in, m, tmp, out, 0, nullptr, nullptr}, nb, SCAN_BS, 0, st);
     return 3;
 }
 
@@ -426,10 +493,12 @@ void launch_bin_emit(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, co
     if (g.continuous) {
         // charges per particle, their offsets, the particle of every emitted charge
         const int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-        k_split_count_reduce<<<nb, SCAN_BS, 0, st>>>(g, n, pos, P.count, P.axes, P.scan_tmp, P.hdr);
-        k_scan_blocks<<<1, 1024, 0, st>>>(P.scan_tmp, nb);
-        k_scan_apply<true><<<nb, SCAN_BS, 0, st>>>(P.count, n, P.scan_tmp, P.offset, (int)W.cap, P.e_origin,
-                                                   P.hdr);
+        launch_k(tr, FMM_TAG(S_SPLIT_COUNT, 0), k_split_count_reduce,
+                 KSplitCount{g, n, pos, P.count, P.axes, P.scan_tmp, P.hdr}, nb, SCAN_BS, 0, st);
+        launch_k(tr, FMM_TAG(S_SCAN_BLOCKS_E, 0), k_scan_blocks, KScanBlocks{P.scan_tmp, nb}, 1, 1024, 0, st);
+        launch_k(tr, FMM_TAG(S_SCAN_APPLY_E, 0), k_scan_apply<true>,
+                 KScanApply<true>{P.count, n, P.scan_tmp, P.offset, (int)W.cap, P.e_origin, P.hdr}, nb, SCAN_BS, 0,
+                 st);
         tr.count(3);
         offset = P.offset;
     }
@@ -437,9 +506,10 @@ void launch_bin_emit(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, co
     int nbe = (int)((ne_max + 255) / 256);
     if (nbe < 1) nbe = 1;
     if (nbe > 152 * 64) nbe = 152 * 64;
-    k_emit<real><<<nbe, 256, 0, st>>>(g, C, n, pos, q, offset, P.e_key, P.e_pt,
-                                      g.continuous ? P.e_wd : nullptr, P.e_origin, P.e_rank,
-                                      P.leaf_count, P.hdr);
+    launch_k(tr, FMM_TAG(S_EMIT, 0), k_emit<real>,
+             KEmit<real>{g, C, n, pos, q, offset, P.e_key, P.e_pt, g.continuous ? P.e_wd : nullptr, P.e_origin,
+                         P.e_rank, P.leaf_count, P.hdr},
+             nbe, 256, 0, st);
     tr.count();
     tr.end();
 }
@@ -449,12 +519,21 @@ void launch_bin_emit(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, co
 // arrival rank in its cell, then order each cell's segment by emitted index
 // (= particle order), then gather.
 // ---------------------------------------------------------------------------
-__global__ void k_scatter(const WsHeader *hdr, const uint32_t *__restrict__ e_key,
-                          const int *__restrict__ e_rank, const int *__restrict__ leaf_start,
-                          int *__restrict__ tmp) {
-    int ne = hdr->n_eff;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x)
-        tmp[leaf_start[e_key[e]] + e_rank[e]] = e;
+struct KScatter {
+    static constexpr int BS = 0, MINB = 0;
+    const WsHeader *hdr;
+    const uint32_t *__restrict__ e_key;
+    const int *__restrict__ e_rank;
+    const int *__restrict__ leaf_start;
+    int *__restrict__ tmp;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        int ne = hdr->n_eff;
+        for (int e = bid_ * blockDim.x + threadIdx.x; e < ne; e += nblk_ * blockDim.x)
+            tmp[leaf_start[e_key[e]] + e_rank[e]] = e;
+    }
+};
+__global__ void k_scatter(const __grid_constant__ KScatter k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
 // one warp per finest cell: rank every element of the cell's segment among
@@ -462,56 +541,68 @@ __global__ void k_scatter(const WsHeader *hdr, const uint32_t *__restrict__ e_ke
 // slot: charge, origin and perm (slot -> emitted index).  Up to 64 elements
 // are ranked in registers (two per lane, compared through shuffles).
 template <typename real>
-__global__ void k_leaf_gather(int ncell, const int *__restrict__ leaf_start, const int *__restrict__ tmp,
-                              const typename Vec4<real>::T *__restrict__ e_pt,
-                              const int *__restrict__ e_origin, typename Vec4<real>::T *__restrict__ s_pt,
-                              int *__restrict__ s_origin, int *__restrict__ perm) {
-    int lane = threadIdx.x & 31;
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int c = warp; c < ncell; c += nwarps) {
-        int s0 = leaf_start[c], s1 = leaf_start[c + 1];
-        int cnt = s1 - s0;
-        if (cnt == 0) continue;
-        if (cnt <= 64) {
-            const int v0 = lane < cnt ? tmp[s0 + lane] : 0x7fffffff;
-            const int v1 = lane + 32 < cnt ? tmp[s0 + 32 + lane] : 0x7fffffff;
-            int r0 = 0, r1 = 0;
-            const int c0 = cnt < 32 ? cnt : 32;
-            for (int j = 0; j < c0; j++) {
-                const int w = __shfl_sync(0xffffffffu, v0, j);
-                r0 += (w < v0);
-                r1 += (w < v1);
-            }
-            for (int j = 0; j < cnt - 32; j++) {
-                const int w = __shfl_sync(0xffffffffu, v1, j);
-                r0 += (w < v0);
-                r1 += (w < v1);
-            }
-            if (lane < cnt) {
-                const int slot = s0 + r0;
-                perm[slot] = v0;
-                s_pt[slot] = e_pt[v0];
-                s_origin[slot] = e_origin[v0];
-            }
-            if (lane + 32 < cnt) {
-                const int slot = s0 + r1;
-                perm[slot] = v1;
-                s_pt[slot] = e_pt[v1];
-                s_origin[slot] = e_origin[v1];
-            }
-        } else {
-            for (int i = lane; i < cnt; i += 32) {
-                int v = tmp[s0 + i];
-                int r = 0;
-                for (int j = 0; j < cnt; j++) r += (tmp[s0 + j] < v);
-                const int slot = s0 + r;
-                perm[slot] = v;
-                s_pt[slot] = e_pt[v];
-                s_origin[slot] = e_origin[v];
+struct KLeafGather {
+    static constexpr int BS = 0, MINB = 0;
+    int ncell;
+    const int *__restrict__ leaf_start;
+    const int *__restrict__ tmp;
+    const typename Vec4<real>::T *__restrict__ e_pt;
+    const int *__restrict__ e_origin;
+    typename Vec4<real>::T *__restrict__ s_pt;
+    int *__restrict__ s_origin;
+    int *__restrict__ perm;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        int lane = threadIdx.x & 31;
+        int warp = (bid_ * blockDim.x + threadIdx.x) >> 5;
+        int nwarps = (nblk_ * blockDim.x) >> 5;
+        for (int c = warp; c < ncell; c += nwarps) {
+            int s0 = leaf_start[c], s1 = leaf_start[c + 1];
+            int cnt = s1 - s0;
+            if (cnt == 0) continue;
+            if (cnt <= 64) {
+                const int v0 = lane < cnt ? tmp[s0 + lane] : 0x7fffffff;
+                const int v1 = lane + 32 < cnt ? tmp[s0 + 32 + lane] : 0x7fffffff;
+                int r0 = 0, r1 = 0;
+                const int c0 = cnt < 32 ? cnt : 32;
+                for (int j = 0; j < c0; j++) {
+                    const int w = __shfl_sync(0xffffffffu, v0, j);
+                    r0 += (w < v0);
+                    r1 += (w < v1);
+                }
+                for (int j = 0; j < cnt - 32; j++) {
+                    const int w = __shfl_sync(0xffffffffu, v1, j);
+                    r0 += (w < v0);
+                    r1 += (w < v1);
+                }
+                if (lane < cnt) {
+                    const int slot = s0 + r0;
+                    perm[slot] = v0;
+                    s_pt[slot] = e_pt[v0];
+                    s_origin[slot] = e_origin[v0];
+                }
+                if (lane + 32 < cnt) {
+                    const int slot = s0 + r1;
+                    perm[slot] = v1;
+                    s_pt[slot] = e_pt[v1];
+                    s_origin[slot] = e_origin[v1];
+                }
+            } else {
+                for (int i = lane; i < cnt; i += 32) {
+                    int v = tmp[s0 + i];
+                    int r = 0;
+                    for (int j = 0; j < cnt; j++) r += (tmp[s0 + j] < v);
+                    const int slot = s0 + r;
+                    perm[slot] = v;
+                    s_pt[slot] = e_pt[v];
+                    s_origin[slot] = e_origin[v];
+                }
             }
         }
     }
+};
+template <typename real>
+__global__ void k_leaf_gather(const __grid_constant__ KLeafGather<real> k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
 template <typename real>
@@ -519,15 +610,17 @@ void launch_sort(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, c
                  Tracer &tr) {
     int ncell = (int)W.ncell;
     tr.begin(FMM_STAGE_SORT, st);
-    tr.count(launch_scan(P.leaf_count, P.leaf_start, ncell, P.scan_tmp, st));
+    tr.count(launch_scan(P.leaf_count, P.leaf_start, ncell, P.scan_tmp, st, tr));
     int nbp = (int)((W.cap + 255) / 256);
     if (nbp < 1) nbp = 1;
     if (nbp > 152 * 64) nbp = 152 * 64;
-    k_scatter<<<nbp, 256, 0, st>>>(P.hdr, P.e_key, P.e_rank, P.leaf_start, P.tmp);
+    launch_k(tr, FMM_TAG(S_SCATTER, 0), k_scatter, KScatter{P.hdr, P.e_key, P.e_rank, P.leaf_start, P.tmp}, nbp,
+             256, 0, st);
     int nbl = (ncell * 32 + 255) / 256;
     if (nbl > 152 * 64) nbl = 152 * 64;
-    k_leaf_gather<real><<<nbl, 256, 0, st>>>(ncell, P.leaf_start, P.tmp, P.e_pt, P.e_origin, P.s_pt,
-                                             P.s_origin, P.perm);
+    launch_k(tr, FMM_TAG(S_LEAF_GATHER, 0), k_leaf_gather<real>,
+             KLeafGather<real>{ncell, P.leaf_start, P.tmp, P.e_pt, P.e_origin, P.s_pt, P.s_origin, P.perm}, nbl, 256,
+             0, st);
     tr.count(2);
     tr.end();
 }
@@ -647,22 +740,33 @@ __device__ __forceinline__ float sd_axis_diff(float v, int shift, float th, floa
 // listed from slist[2] up; slist[1] = the number split along two or three,
 // listed from slist[n + 1] down (each particle is one or the other, so the
 // two never meet).  m1 = the charges of a particle split along one axis.
-__global__ void k_split_list(int n, int m1, const int *__restrict__ count, const int *__restrict__ offset,
-                             const WsHeader *hdr, int *__restrict__ slist) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
-    const bool mine = i < n && count[i] > 1 && offset[i] + count[i] <= hdr->n_eff;
-    const bool one = mine && count[i] <= m1;
-    const unsigned b1 = __ballot_sync(0xffffffffu, one), bm = __ballot_sync(0xffffffffu, mine && !one);
-    int base1 = 0, basem = 0;
-    if (lane == 0 && b1) base1 = atomicAdd(&slist[0], __popc(b1));
-    if (lane == 0 && bm) basem = atomicAdd(&slist[1], __popc(bm));
-    base1 = __shfl_sync(0xffffffffu, base1, 0);
-    basem = __shfl_sync(0xffffffffu, basem, 0);
-    const unsigned below = (1u << lane) - 1u;
-    if (one)
-        slist[2 + base1 + __popc(b1 & below)] = i;
-    else if (mine)
-        slist[n + 1 - (basem + __popc(bm & below))] = i;
+struct KSplitList {
+    static constexpr int BS = 0, MINB = 0;
+    int n;
+    int m1;
+    const int *__restrict__ count;
+    const int *__restrict__ offset;
+    const WsHeader *hdr;
+    int *__restrict__ slist;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        const int i = bid_ * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+        const bool mine = i < n && count[i] > 1 && offset[i] + count[i] <= hdr->n_eff;
+        const bool one = mine && count[i] <= m1;
+        const unsigned b1 = __ballot_sync(0xffffffffu, one), bm = __ballot_sync(0xffffffffu, mine && !one);
+        int base1 = 0, basem = 0;
+        if (lane == 0 && b1) base1 = atomicAdd(&slist[0], __popc(b1));
+        if (lane == 0 && bm) basem = atomicAdd(&slist[1], __popc(bm));
+        base1 = __shfl_sync(0xffffffffu, base1, 0);
+        basem = __shfl_sync(0xffffffffu, basem, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (one)
+            slist[2 + base1 + __popc(b1 & below)] = i;
+        else if (mine)
+            slist[n + 1 - (basem + __popc(bm & below))] = i;
+    }
+};
+__global__ void k_split_list(const __grid_constant__ KSplitList k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
 #define SD_NM 7                 // series terms n = 0..6
@@ -786,269 +890,428 @@ __device__ __forceinline__ void sd_cell_offset(int c, int o0, int o1, int n0, in
 }
 
 template <int POW, int CH>
-__global__ void __launch_bounds__(32 * SD_WARPS, 5)
-    k_split_delta(Geom g, Coef<double> Cd, int n, const float *__restrict__ pos, const int *__restrict__ count,
-                  const int *__restrict__ offset, const int *__restrict__ leaf_start, const float4 *__restrict__ s_pt,
-                  const int *__restrict__ s_origin, const float *__restrict__ loc_leaf, float *__restrict__ delta,
-                  const int *__restrict__ slist) {
-    // double-precision weights: every distinct coordinate of the particle's
-    // charges (axis a, entry e) for a particle split along several axes; the
-    // per-axis rows and weight differences for one split axis (carved below)
-    __shared__ double wsm[SD_WARPS][3][FMM_MAXP + 1][FMM_MAXP];
-    __shared__ int csm[SD_WARPS][64 + 65 + 64];        // neighbour cells: first slot, count prefix, offset
-    __shared__ float ksm[SD_WARPS][SD_KMAX * 12];      // the charges (one split axis) or one chunk of them
-    __shared__ int ssm[SD_WARPS][SD_KMAX];             // their sides (bit a: the upper cell of axis a)
-    __shared__ float gsm[SD_WARPS][SD_KMAX];           // near-source terms per charge (one split axis)
-    __shared__ double gsd[SD_WARPS][SD_KMAX];          // plain near-source terms per charge (outer slab)
-    __shared__ float msm[SD_WARPS][2][SD_NMOM];        // the moments (high, low) per slab and order
-    __shared__ float csum[SD_WARPS][2][CH][32];        // per-lane compensated sums per charge (several axes)
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int S = g.S, p = g.p, p3 = g.p3;
-    constexpr int PM = CH;  // p <= PM: the launch picks CH = 4, 6 or 8 by p
-    const int n1 = slist[0], nmul = slist[1];
-    const int m1 = p + (p & 1);
-    const int nchm = (m1 * m1 * m1 + CH - 1) / CH;  // chunks of a particle split along several axes, at most
-    const long long ntask = (long long)nmul * nchm + n1;
-    // persistent warps over the tasks: the chunks of the particles split along
-    // several axes (the longest) first, then one task per particle split along one
-    for (long long tk = blockIdx.x * SD_WARPS + wl; tk < ntask; tk += (long long)gridDim.x * SD_WARPS) {
-        int i, c0 = 0;
-        if (tk < (long long)nmul * nchm) {
-            i = slist[n + 1 - (int)(tk / nchm)];
-            c0 = (int)(tk % nchm) * CH;
-            if (c0 >= count[i]) continue;  // warp-uniform: past this particle's charges
-        } else {
-            i = slist[2 + (int)(tk - (long long)nmul * nchm)];
-        }
-        // the particle's axes: binned cell, split geometry, base = the lower cell
-        // of each split axis (unwrapped), the binned cell otherwise
-        AxisInfo A[3];
-        int base[3], sp[3];
-        float R[3];  // the reference point (first charge) in the base frame
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            int st = 0, c;
-            float t;
-            bin_axis(g, pos[3 * i + a], a, t, c, st);
-            A[a] = split_axis_info(g, c, t);
-            sp[a] = A[a].mode != 0;
-            base[a] = A[a].mode == 1 ? c - 1 : c;
-            R[a] = sp[a] ? 1.0f - g.dtf : t;  // node plane - d: exact in single precision
-        }
-        const int m = A[0].m * A[1].m * A[2].m, e0 = offset[i];
-        const int a1 = sp[0] + sp[1] + sp[2] == 1 ? (sp[0] ? 0 : (sp[1] ? 1 : 2)) : -1;  // the one split axis
-        // the neighbour table: the cells adjacent to any of the particle's cells,
-        // resolved once by all lanes (first sorted slot, prefix of the charge
-        // counts, offset u from the base cell packed 3 x 4 bits); with one split
-        // axis it varies slowest, so that its slabs u = -1, 0..1, 2 are
-        // contiguous (cells 0..8, 9..26, 27..35)
-        int o0 = 0, o1 = 1;
-        if (a1 == 0) {
-            o0 = 1;
-            o1 = 2;
-        } else if (a1 == 1) {
-            o1 = 2;
-        }
-        const int nd0 = 3 + sp[o0], nd1 = 3 + sp[o1];
-        const int nc = (3 + sp[0]) * (3 + sp[1]) * (3 + sp[2]);
-        int *cst = csm[wl], *cpre = cst + 64, *cpk = cpre + 65;
-        {
-            int cnt_lane[2] = {0, 0};
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int c = lane + 32 * h;
-                if (c < nc) {
-                    int ux, uy, uz;
-                    sd_cell_offset(c, o0, o1, nd0, nd1, ux, uy, uz);
-                    int gx = base[0] + ux, gy = base[1] + uy, gz = base[2] + uz;
-                    bool in = true;
-                    if (g.periodic) {
-                        gx = (gx + S) % S;
-                        gy = (gy + S) % S;
-                        gz = (gz + S) % S;
-                    } else {
-                        in = gx >= 0 && gy >= 0 && gz >= 0 && gx < S && gy < S && gz < S;
-                    }
-                    int a0 = 0, cc = 0;
-                    if (in) {
-                        const uint32_t key = morton_encode(gx, gy, gz);
-                        a0 = leaf_start[key];
-                        cc = leaf_start[key + 1] - a0;
-                    }
-                    cst[c] = a0;
-                    cpk[c] = (ux + 1) | ((uy + 1) << 4) | ((uz + 1) << 8);
-                    cnt_lane[h] = cc;
-                }
+struct KSplitDelta {
+    static constexpr int BS = 32 * SD_WARPS, MINB = 5;
+    Geom g;
+    Coef<double> Cd;
+    int n;
+    const float *__restrict__ pos;
+    const int *__restrict__ count;
+    const int *__restrict__ offset;
+    const int *__restrict__ leaf_start;
+    const float4 *__restrict__ s_pt;
+    const int *__restrict__ s_origin;
+    const float *__restrict__ loc_leaf;
+    float *__restrict__ delta;
+    const int *__restrict__ slist;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        // double-precision weights: every distinct coordinate of the particle's
+        // charges (axis a, entry e) for a particle split along several axes; the
+        // per-axis rows and weight differences for one split axis (carved below)
+        __shared__ double wsm[SD_WARPS][3][FMM_MAXP + 1][FMM_MAXP];
+        __shared__ int csm[SD_WARPS][64 + 65 + 64];        // neighbour cells: first slot, count prefix, offset
+        __shared__ float ksm[SD_WARPS][SD_KMAX * 12];      // the charges (one split axis) or one chunk of them
+        __shared__ int ssm[SD_WARPS][SD_KMAX];             // their sides (bit a: the upper cell of axis a)
+        __shared__ float gsm[SD_WARPS][SD_KMAX];           // near-source terms per charge (one split axis)
+        __shared__ double gsd[SD_WARPS][SD_KMAX];          // plain near-source terms per charge (outer slab)
+        __shared__ float msm[SD_WARPS][2][SD_NMOM];        // the moments (high, low) per slab and order
+        __shared__ float csum[SD_WARPS][2][CH][32];        // per-lane compensated sums per charge (several axes)
+        const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+        const int S = g.S, p = g.p, p3 = g.p3;
+        constexpr int PM = CH;  // p <= PM: the launch picks CH = 4, 6 or 8 by p
+        const int n1 = slist[0], nmul = slist[1];
+        const int m1 = p + (p & 1);
+        const int nchm = (m1 * m1 * m1 + CH - 1) / CH;  // chunks of a particle split along several axes, at most
+        const long long ntask = (long long)nmul * nchm + n1;
+        // persistent warps over the tasks: the chunks of the particles split along
+        // several axes (the longest) first, then one task per particle split along one
+        for (long long tk = bid_ * SD_WARPS + wl; tk < ntask; tk += (long long)nblk_ * SD_WARPS) {
+            int i, c0 = 0;
+            if (tk < (long long)nmul * nchm) {
+                i = slist[n + 1 - (int)(tk / nchm)];
+                c0 = (int)(tk % nchm) * CH;
+                if (c0 >= count[i]) continue;  // warp-uniform: past this particle's charges
+            } else {
+                i = slist[2 + (int)(tk - (long long)nmul * nchm)];
             }
-            // prefix of the counts over the (up to 64) cells
-            int inc0 = cnt_lane[0], inc1 = cnt_lane[1];
+            // the particle's axes: binned cell, split geometry, base = the lower cell
+            // of each split axis (unwrapped), the binned cell otherwise
+            AxisInfo A[3];
+            int base[3], sp[3];
+            float R[3];  // the reference point (first charge) in the base frame
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y0 = __shfl_up_sync(0xffffffffu, inc0, o), y1 = __shfl_up_sync(0xffffffffu, inc1, o);
-                if (lane >= o) {
-                    inc0 += y0;
-                    inc1 += y1;
-                }
+            for (int a = 0; a < 3; a++) {
+                int st = 0, c;
+                float t;
+                bin_axis(g, pos[3 * i + a], a, t, c, st);
+                A[a] = split_axis_info(g, c, t);
+                sp[a] = A[a].mode != 0;
+                base[a] = A[a].mode == 1 ? c - 1 : c;
+                R[a] = sp[a] ? 1.0f - g.dtf : t;  // node plane - d: exact in single precision
             }
-            const int tot0 = __shfl_sync(0xffffffffu, inc0, 31);
-            if (lane < nc) cpre[lane + 1] = inc0;
-            if (lane + 32 < nc) cpre[lane + 33] = tot0 + inc1;
-            if (lane == 0) cpre[0] = 0;
-        }
-        const float Sp = POW == 2 ? (float)S * (float)S : (float)S;  // cell units to unit-box units
-        if (a1 >= 0) {
-            // ---- one split axis a1: the m <= SD_KMAX charges in one pass ----
-            const int ob = o0, oc = o1;  // the other two axes
-            // W_a1 at r (lower cell), W_ob and W_oc at the particle; per charge
-            // W_a1(s_k) - W_a1 at its cell's point: r below the plane, the plane
-            // itself above (t = 0 of the upper cell, the first node: weights e_0)
-            double *wr = &wsm[wl][0][0][0];
-            double *wb = wr + FMM_MAXP, *wc = wb + FMM_MAXP;
-            float *dw = reinterpret_cast<float *>(wc + FMM_MAXP);
-            float *kq = ksm[wl], *gs = gsm[wl];
-            int *ks = ssm[wl];
-            int sidek = 0;
-            double t = 0.0;  // lane k < m: charge k along a1; 16: r along a1; 17, 18: the other axes
-            if (lane < m) {  // charge k = lane: entry k of a1, entry 0 of the other axes
+            const int m = A[0].m * A[1].m * A[2].m, e0 = offset[i];
+            const int a1 = sp[0] + sp[1] + sp[2] == 1 ? (sp[0] ? 0 : (sp[1] ? 1 : 2)) : -1;  // the one split axis
+            // the neighbour table: the cells adjacent to any of the particle's cells,
+            // resolved once by all lanes (first sorted slot, prefix of the charge
+            // counts, offset u from the base cell packed 3 x 4 bits); with one split
+            // axis it varies slowest, so that its slabs u = -1, 0..1, 2 are
+            // contiguous (cells 0..8, 9..26, 27..35)
+            int o0 = 0, o1 = 1;
+            if (a1 == 0) {
+                o0 = 1;
+                o1 = 2;
+            } else if (a1 == 1) {
+                o1 = 2;
+            }
+            const int nd0 = 3 + sp[o0], nd1 = 3 + sp[o1];
+            const int nc = (3 + sp[0]) * (3 + sp[1]) * (3 + sp[2]);
+            int *cst = csm[wl], *cpre = cst + 64, *cpk = cpre + 65;
+            {
+                int cnt_lane[2] = {0, 0};
 #pragma unroll
-                for (int a = 0; a < 3; a++) {
+                for (int h = 0; h < 2; h++) {
+                    const int c = lane + 32 * h;
+                    if (c < nc) {
+                        int ux, uy, uz;
+                        sd_cell_offset(c, o0, o1, nd0, nd1, ux, uy, uz);
+                        int gx = base[0] + ux, gy = base[1] + uy, gz = base[2] + uz;
+                        bool in = true;
+                        if (g.periodic) {
+                            gx = (gx + S) % S;
+                            gy = (gy + S) % S;
+                            gz = (gz + S) % S;
+                        } else {
+                            in = gx >= 0 && gy >= 0 && gz >= 0 && gx < S && gy < S && gz < S;
+                        }
+                        int a0 = 0, cc = 0;
+                        if (in) {
+                            const uint32_t key = morton_encode(gx, gy, gz);
+                            a0 = leaf_start[key];
+                            cc = leaf_start[key + 1] - a0;
+                        }
+                        cst[c] = a0;
+                        cpk[c] = (ux + 1) | ((uy + 1) << 4) | ((uz + 1) << 8);
+                        cnt_lane[h] = cc;
+                    }
+                }
+                // prefix of the counts over the (up to 64) cells
+                int inc0 = cnt_lane[0], inc1 = cnt_lane[1];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y0 = __shfl_up_sync(0xffffffffu, inc0, o), y1 = __shfl_up_sync(0xffffffffu, inc1, o);
+                    if (lane >= o) {
+                        inc0 += y0;
+                        inc1 += y1;
+                    }
+                }
+                const int tot0 = __shfl_sync(0xffffffffu, inc0, 31);
+                if (lane < nc) cpre[lane + 1] = inc0;
+                if (lane + 32 < nc) cpre[lane + 33] = tot0 + inc1;
+                if (lane == 0) cpre[0] = 0;
+            }
+            const float Sp = POW == 2 ? (float)S * (float)S : (float)S;  // cell units to unit-box units
+            if (a1 >= 0) {
+                // ---- one split axis a1: the m <= SD_KMAX charges in one pass ----
+                const int ob = o0, oc = o1;  // the other two axes
+                // W_a1 at r (lower cell), W_ob and W_oc at the particle; per charge
+                // W_a1(s_k) - W_a1 at its cell's point: r below the plane, the plane
+                // itself above (t = 0 of the upper cell, the first node: weights e_0)
+                double *wr = &wsm[wl][0][0][0];
+                double *wb = wr + FMM_MAXP, *wc = wb + FMM_MAXP;
+                float *dw = reinterpret_cast<float *>(wc + FMM_MAXP);
+                float *kq = ksm[wl], *gs = gsm[wl];
+                int *ks = ssm[wl];
+                int sidek = 0;
+                double t = 0.0;  // lane k < m: charge k along a1; 16: r along a1; 17, 18: the other axes
+                if (lane < m) {  // charge k = lane: entry k of a1, entry 0 of the other axes
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        int side;
+                        float th, tl, tfk;
+                        split_entry_df(g, A[a], a == a1 ? lane : 0, side, th, tl, tfk);
+                        // s_k - r: th - r exact (Sterbenz) below the plane, r = 1 - dt
+                        const float dd = !sp[a] ? 0.0f : (side ? __fadd_rn(th, g.dtf) : __fsub_rn(th, R[a]));
+                        kq[lane * 12 + a] = dd + tl;
+                        kq[lane * 12 + 3 + a] = th;
+                        kq[lane * 12 + 6 + a] = tl;
+                        kq[lane * 12 + 9 + a] = tfk;
+                        sidek |= side << a;
+                        if (a == a1) t = (double)th + (double)tl;
+                    }
+                    ks[lane] = sidek;
+                    gs[lane] = 0.0f;
+                    gsd[wl][lane] = 0.0;
+                } else if (lane >= 16 && lane < 19) {
+                    const int a = lane == 17 ? ob : (lane == 18 ? oc : a1);
                     int side;
                     float th, tl, tfk;
-                    split_entry_df(g, A[a], a == a1 ? lane : 0, side, th, tl, tfk);
-                    // s_k - r: th - r exact (Sterbenz) below the plane, r = 1 - dt
-                    const float dd = !sp[a] ? 0.0f : (side ? __fadd_rn(th, g.dtf) : __fsub_rn(th, R[a]));
-                    kq[lane * 12 + a] = dd + tl;
-                    kq[lane * 12 + 3 + a] = th;
-                    kq[lane * 12 + 6 + a] = tl;
-                    kq[lane * 12 + 9 + a] = tfk;
-                    sidek |= side << a;
-                    if (a == a1) t = (double)th + (double)tl;
+                    split_entry_df(g, A[a], 0, side, th, tl, tfk);
+                    t = (double)th + (double)tl;
                 }
-                ks[lane] = sidek;
-                gs[lane] = 0.0f;
-                gsd[wl][lane] = 0.0;
-            } else if (lane >= 16 && lane < 19) {
-                const int a = lane == 17 ? ob : (lane == 18 ? oc : a1);
-                int side;
-                float th, tl, tfk;
-                split_entry_df(g, A[a], 0, side, th, tl, tfk);
-                t = (double)th + (double)tl;
-            }
-            {
-                double w[PM];
-                lag_weights<double, PM>(Cd, p, t, w);  // one pass for all lanes
-                if (lane >= 16 && lane < 19) {
-                    double *dst = lane == 16 ? wr : (lane == 17 ? wb : wc);
+                {
+                    double w[PM];
+                    lag_weights<double, PM>(Cd, p, t, w);  // one pass for all lanes
+                    if (lane >= 16 && lane < 19) {
+                        double *dst = lane == 16 ? wr : (lane == 17 ? wb : wc);
 #pragma unroll
-                    for (int k = 0; k < PM; k++)
-                        if (k < p) dst[k] = w[k];
+                        for (int k = 0; k < PM; k++)
+                            if (k < p) dst[k] = w[k];
+                    }
+                    __syncwarp();
+                    if (lane < m) {
+                        const bool upk = (sidek >> a1) & 1;
+#pragma unroll
+                        for (int k = 0; k < PM; k++)
+                            if (k < p) dw[lane * FMM_MAXP + k] = (float)(w[k] - (upk ? (k == 0 ? 1.0 : 0.0) : wr[k]));
+                    }
                 }
                 __syncwarp();
-                if (lane < m) {
-                    const bool upk = (sidek >> a1) & 1;
+                // far field along the lines of a1 (one per node pair of ob, oc):
+                // charge k: (W_a1(s_k) - W_a1(its cell's point)) W_ob W_oc . L of its
+                // cell in single precision (the difference is small and carries its
+                // own rounding only); X = g(plane) . L_upper - g(r) . L_lower in
+                // double precision, the same for every upper charge (g(plane) is
+                // e_0 along a1)
+                const int sa = a1 == 0 ? 1 : (a1 == 1 ? p : p * p);
+                const int sb = ob == 0 ? 1 : (ob == 1 ? p : p * p), sc = oc == 0 ? 1 : (oc == 1 ? p : p * p);
+                const int64_t cl = loc_cell(g.depth, (base[0] + S) % S, (base[1] + S) % S, (base[2] + S) % S);
+                const int64_t cu = loc_cell(g.depth, (base[0] + (a1 == 0) + S) % S, (base[1] + (a1 == 1) + S) % S,
+                                            (base[2] + (a1 == 2) + S) % S);
+                float fk[PM];  // m <= p + (p & 1) <= PM charges
 #pragma unroll
-                    for (int k = 0; k < PM; k++)
-                        if (k < p) dw[lane * FMM_MAXP + k] = (float)(w[k] - (upk ? (k == 0 ? 1.0 : 0.0) : wr[k]));
+                for (int k = 0; k < PM; k++) fk[k] = 0.0f;
+                double X = 0.0;
+                for (int ln = lane; ln < p * p; ln += 32) {
+                    const int jb = ln % p, jc = ln / p;
+                    const float *Ll = loc_leaf + cl * p3 + jb * sb + jc * sc, *Lu = loc_leaf + cu * p3 + jb * sb + jc * sc;
+                    float L0[PM], L1[PM];
+                    double xs = 0.0;
+#pragma unroll
+                    for (int a = 0; a < PM; a++) {
+                        L0[a] = a < p ? Ll[a * sa] : 0.0f;
+                        L1[a] = a < p ? Lu[a * sa] : 0.0f;
+                        if (a < p) xs -= wr[a] * (double)L0[a];
+                    }
+                    const double wbc = wb[jb] * wc[jc];
+                    X += wbc * (xs + (double)L1[0]);
+                    const float fbc = (float)wbc;
+#pragma unroll
+                    for (int k = 0; k < PM; k++) {
+                        if (k < m) {
+                            const bool upk = (ks[k] >> a1) & 1;
+                            const float *d = dw + k * FMM_MAXP;
+                            float s = 0.0f;
+#pragma unroll
+                            for (int a = 0; a < PM; a++)
+                                if (a < p) s = fmaf(d[a], upk ? L1[a] : L0[a], s);
+                            fk[k] = fmaf(fbc, s, fk[k]);
+                        }
+                    }
                 }
-            }
-            __syncwarp();
-            // far field along the lines of a1 (one per node pair of ob, oc):
-            // charge k: (W_a1(s_k) - W_a1(its cell's point)) W_ob W_oc . L of its
-            // cell in single precision (the difference is small and carries its
-            // own rounding only); X = g(plane) . L_upper - g(r) . L_lower in
-            // double precision, the same for every upper charge (g(plane) is
-            // e_0 along a1)
-            const int sa = a1 == 0 ? 1 : (a1 == 1 ? p : p * p);
-            const int sb = ob == 0 ? 1 : (ob == 1 ? p : p * p), sc = oc == 0 ? 1 : (oc == 1 ? p : p * p);
-            const int64_t cl = loc_cell(g.depth, (base[0] + S) % S, (base[1] + S) % S, (base[2] + S) % S);
-            const int64_t cu = loc_cell(g.depth, (base[0] + (a1 == 0) + S) % S, (base[1] + (a1 == 1) + S) % S,
-                                        (base[2] + (a1 == 2) + S) % S);
-            float fk[PM];  // m <= p + (p & 1) <= PM charges
-#pragma unroll
-            for (int k = 0; k < PM; k++) fk[k] = 0.0f;
-            double X = 0.0;
-            for (int ln = lane; ln < p * p; ln += 32) {
-                const int jb = ln % p, jc = ln / p;
-                const float *Ll = loc_leaf + cl * p3 + jb * sb + jc * sc, *Lu = loc_leaf + cu * p3 + jb * sb + jc * sc;
-                float L0[PM], L1[PM];
-                double xs = 0.0;
-#pragma unroll
-                for (int a = 0; a < PM; a++) {
-                    L0[a] = a < p ? Ll[a * sa] : 0.0f;
-                    L1[a] = a < p ? Lu[a * sa] : 0.0f;
-                    if (a < p) xs -= wr[a] * (double)L0[a];
-                }
-                const double wbc = wb[jb] * wc[jc];
-                X += wbc * (xs + (double)L1[0]);
-                const float fbc = (float)wbc;
+                float myf = 0.0f;
 #pragma unroll
                 for (int k = 0; k < PM; k++) {
                     if (k < m) {
-                        const bool upk = (ks[k] >> a1) & 1;
-                        const float *d = dw + k * FMM_MAXP;
-                        float s = 0.0f;
-#pragma unroll
-                        for (int a = 0; a < PM; a++)
-                            if (a < p) s = fmaf(d[a], upk ? L1[a] : L0[a], s);
-                        fk[k] = fmaf(fbc, s, fk[k]);
+                        float v = fk[k];
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == k) myf = v;
                     }
                 }
-            }
-            float myf = 0.0f;
+                for (int o = 16; o > 0; o >>= 1) X += __shfl_xor_sync(0xffffffffu, X, o);
+                // near field, three slabs of the table along a1: u = -1 (seen by r and
+                // the lower charges), 0..1 (seen by all), 2 (seen by the upper
+                // charges).  Sources closer to r than 16 max|delta|: direct terms per
+                // charge (gs; with the default split width only middle-slab sources
+                // are that close); all others: series moments, which truncated after
+                // h^6 leave h^7 < 4e-9 of each term (8 h^7 for 1/r^2)
+                float far2 = 0.0f;
 #pragma unroll
-            for (int k = 0; k < PM; k++) {
-                if (k < m) {
-                    float v = fk[k];
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == k) myf = v;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) X += __shfl_xor_sync(0xffffffffu, X, o);
-            // near field, three slabs of the table along a1: u = -1 (seen by r and
-            // the lower charges), 0..1 (seen by all), 2 (seen by the upper
-            // charges).  Sources closer to r than 16 max|delta|: direct terms per
-            // charge (gs; with the default split width only middle-slab sources
-            // are that close); all others: series moments, which truncated after
-            // h^6 leave h^7 < 4e-9 of each term (8 h^7 for 1/r^2)
-            float far2 = 0.0f;
-#pragma unroll
-            for (int k = 0; k < PM; k++)
-                if (k < m) far2 = fmaxf(far2, 256.0f * kq[k * 12 + a1] * kq[k * 12 + a1]);
-            bool outer_direct = false;
+                for (int k = 0; k < PM; k++)
+                    if (k < m) far2 = fmaxf(far2, 256.0f * kq[k * 12 + a1] * kq[k * 12 + a1]);
+                bool outer_direct = false;
 #pragma unroll 1
-            for (int set = 0; set < 3; set++) {
-                const int cb = set == 0 ? 0 : (set == 1 ? 9 : 27), ce = set == 0 ? 9 : (set == 1 ? 27 : 36);
-                const int fe = cpre[ce];
-                // one source: its series terms t (zero where it is skipped or taken
-                // directly; r's plain term of the slab u = -1 is kept in its M_0 for
-                // every source; direct sources of the outer slabs are taken after
-                // the three slabs)
-                auto source = [&](const float4 &v, int pk, bool ok, float(&t)[SD_NM]) {
-                    const int ux = (pk & 15) - 1, uy = ((pk >> 4) & 15) - 1, uz = (pk >> 8) - 1;
-                    // x - r (the reference is exact in single precision, side 0)
-                    const float d0x = sd_axis_diff(v.x, ux, R[0], 0.0f), d0y = sd_axis_diff(v.y, uy, R[1], 0.0f),
-                                d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
-                    const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
-                    const float ri0 = r02 > 0.0f ? rsqrtf(r02) : 0.0f;
-                    const bool direct = r02 <= far2;
-                    if (ok && direct) {
-                        if (set == 1)
-                            sd_direct_terms<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, m, kq, ks, gs);
-                        else
-                            outer_direct = true;  // taken after the slabs
-                    }
-                    sd_series_terms<POW>(ok && !direct ? v.w : 0.0f, a1 == 0 ? d0x : (a1 == 1 ? d0y : d0z), ri0, t);
-                    if (set == 0 && ok && direct) t[0] = POW == 2 ? v.w * ri0 * ri0 : v.w * ri0;
-                };
-                float acc[SD_NM], cmp[SD_NM];
+                for (int set = 0; set < 3; set++) {
+                    const int cb = set == 0 ? 0 : (set == 1 ? 9 : 27), ce = set == 0 ? 9 : (set == 1 ? 27 : 36);
+                    const int fe = cpre[ce];
+                    // one source: its series terms t (zero where it is skipped or taken
+                    // directly; r's plain term of the slab u = -1 is kept in its M_0 for
+                    // every source; direct sources of the outer slabs are taken after
+                    // the three slabs)
+                    auto source = [&](const float4 &v, int pk, bool ok, float(&t)[SD_NM]) {
+                        const int ux = (pk & 15) - 1, uy = ((pk >> 4) & 15) - 1, uz = (pk >> 8) - 1;
+                        // x - r (the reference is exact in single precision, side 0)
+                        const float d0x = sd_axis_diff(v.x, ux, R[0], 0.0f), d0y = sd_axis_diff(v.y, uy, R[1], 0.0f),
+                                    d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
+                        const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
+                        const float ri0 = r02 > 0.0f ? rsqrtf(r02) : 0.0f;
+                        const bool direct = r02 <= far2;
+                        if (ok && direct) {
+                            if (set == 1)
+                                sd_direct_terms<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, m, kq, ks, gs);
+                            else
+                                outer_direct = true;  // taken after the slabs
+                        }
+                        sd_series_terms<POW>(ok && !direct ? v.w : 0.0f, a1 == 0 ? d0x : (a1 == 1 ? d0y : d0z), ri0, t);
+                        if (set == 0 && ok && direct) t[0] = POW == 2 ? v.w * ri0 * ri0 : v.w * ri0;
+                    };
+                    float acc[SD_NM], cmp[SD_NM];
 #pragma unroll
-                for (int k = 0; k < SD_NM; k++) acc[k] = cmp[k] = 0.0f;
+                    for (int k = 0; k < SD_NM; k++) acc[k] = cmp[k] = 0.0f;
+                    // two sources per lane and step (f and f + 32), loaded together
+                    int c = cb, c2 = cb;
+                    for (int f = cpre[cb] + lane; f < fe; f += 64) {
+                        while (cpre[c + 1] <= f) c++;
+                        const int f2 = f + 32;
+                        const bool ok2 = f2 < fe;
+                        if (ok2) {
+                            c2 = max(c2, c);
+                            while (cpre[c2 + 1] <= f2) c2++;
+                        }
+                        const int j = cst[c] + (f - cpre[c]);
+                        const int j2 = ok2 ? cst[c2] + (f2 - cpre[c2]) : j;
+                        const int og1 = s_origin[j], og2 = s_origin[j2];
+                        const float4 v1 = s_pt[j], v2 = s_pt[j2];
+                        float t1[SD_NM], t2[SD_NM];
+                        source(v1, cpk[c], og1 != i, t1);
+                        source(v2, cpk[c2], ok2 && og2 != i, t2);
+#pragma unroll
+                        for (int k = 0; k < SD_NM; k++) {  // compensated sums
+                            const float y = (t1[k] + t2[k]) - cmp[k], tt = acc[k] + y;
+                            cmp[k] = (tt - acc[k]) - y;
+                            acc[k] = tt;
+                        }
+                    }
+                    // over the lanes: the moments n >= 1 in single precision (each lane's
+                    // compensated sum rounded once); n = 0 (used where the two points see
+                    // different slabs, and cancelling there) as pairs
+                    float h0 = acc[0], l0 = -cmp[0];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+                        sd_two_sum(h0, l0, __shfl_xor_sync(0xffffffffu, h0, o), __shfl_xor_sync(0xffffffffu, l0, o));
+#pragma unroll
+                    for (int k = 1; k < SD_NM; k++) {
+                        float v = acc[k] - cmp[k];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        acc[k] = v;
+                    }
+                    if (lane == 0) {
+                        msm[wl][0][set * SD_NM] = h0;
+                        msm[wl][1][set * SD_NM] = l0;
+#pragma unroll
+                        for (int k = 1; k < SD_NM; k++) {
+                            msm[wl][0][set * SD_NM + k] = acc[k];
+                            msm[wl][1][set * SD_NM + k] = 0.0f;
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, outer_direct)) {
+                    // sources of the outer slabs closer to r than the series allows (split
+                    // widths well above the default): their direct terms
+                    for (int set = 0; set < 3; set += 2) {
+                        const int fb = cpre[set == 0 ? 0 : 27], fe = cpre[set == 0 ? 9 : 36];
+                        int c = set == 0 ? 0 : 27;
+                        for (int f = fb + lane; f < fe; f += 32) {
+                            while (cpre[c + 1] <= f) c++;
+                            const int j = cst[c] + (f - cpre[c]);
+                            if (s_origin[j] == i) continue;
+                            const float4 v = s_pt[j];
+                            const int pk = cpk[c], ux = (pk & 15) - 1, uy = ((pk >> 4) & 15) - 1, uz = (pk >> 8) - 1;
+                            const float d0x = sd_axis_diff(v.x, ux, R[0], 0.0f), d0y = sd_axis_diff(v.y, uy, R[1], 0.0f),
+                                        d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
+                            const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
+                            if (r02 > far2) continue;
+                            const float ri0 = r02 > 0.0f ? rsqrtf(r02) : 0.0f;
+                            sd_direct_outer<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, set, a1, m, kq, ks, gs, gsd[wl]);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane < m) {
+                    // D_k = sum_{n>=1} delta^n (M_n of the middle slab + of the slab only
+                    // this side sees besides it) + direct terms + far difference; an upper
+                    // charge adds M_0(u = 2) - M_0(u = -1) + X, which cancel to a small
+                    // number: that sum in double precision
+                    const float dk = kq[lane * 12 + a1];
+                    const bool up = (sidek >> a1) & 1;
+                    const float *MH = msm[wl][0], *ML = msm[wl][1];
+                    const int o = up ? 2 * SD_NM : 0;  // the other slab: u = 2 above the plane, u = -1 below
+                    float s = 0.0f;
+#pragma unroll
+                    for (int k = SD_NM - 1; k >= 1; k--)
+                        s = (s + ((MH[SD_NM + k] + ML[SD_NM + k]) + (MH[o + k] + ML[o + k]))) * dk;
+                    const double zs = (up ? (double)Sp * (((double)MH[2 * SD_NM] + (double)ML[2 * SD_NM]) -
+                                                          ((double)MH[0] + (double)ML[0])) + X
+                                          : 0.0) +
+                                      (double)Sp * gsd[wl][lane];
+                    delta[e0 + lane] = (float)((double)(Sp * (s + gs[lane]) + myf) + zs);
+                }
+            } else {
+                // ---- several split axes: charges c0 .. c0 + CH - 1, direct terms ----
+                double(*W)[FMM_MAXP + 1][FMM_MAXP] = wsm[wl];
+                {  // weights: lane = a * 8 + e computes entry e of axis a
+                    const int a = lane >> 3, e = lane & 7;
+                    if (a < 3 && e < A[a].m) {
+                        int side;
+                        float th, tl, tfl;
+                        split_entry_df(g, A[a], e, side, th, tl, tfl);
+                        double w[PM];
+                        lag_weights<double, PM>(Cd, p, (double)th + (double)tl, w);
+#pragma unroll
+                        for (int k = 0; k < PM; k++)
+                            if (k < p) W[a][e][k] = w[k];
+                    }
+                }
+                __syncwarp();
+                double far0 = 0.0;  // far field at the reference point (entry 0 of every axis)
+                {
+                    const int64_t cr = loc_cell(g.depth, (base[0] + S) % S, (base[1] + S) % S, (base[2] + S) % S);
+                    for (int o = lane; o < p3; o += 32)
+                        far0 += W[0][0][o % p] * W[1][0][(o / p) % p] * W[2][0][o / (p * p)] * (double)loc_leaf[cr * p3 + o];
+                }
+                for (int o = 16; o > 0; o >>= 1) far0 += __shfl_xor_sync(0xffffffffu, far0, o);
+                float *kq = ksm[wl];  // per charge of the chunk: s_k - r (3), th (3), tl (3), tf (3)
+                int *ks = ssm[wl];    // and its sides
+                double fdk = 0.0;     // lane k: the far-field difference of charge c0 + k
+#pragma unroll 1
+                for (int k = 0; k < CH; k++) {
+                    int le = min(c0 + k, m - 1);
+                    const int ex = le % A[0].m;
+                    le /= A[0].m;
+                    const int e3[3] = {ex, le % A[1].m, le / A[1].m};
+                    int side[3];
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        float th, tl, tfk;
+                        split_entry_df(g, A[a], e3[a], side[a], th, tl, tfk);
+                        if (lane == k) {
+                            const float dd = !sp[a] ? 0.0f : (side[a] ? __fadd_rn(th, g.dtf) : __fsub_rn(th, R[a]));
+                            kq[k * 12 + a] = dd + tl;
+                            kq[k * 12 + 3 + a] = th;
+                            kq[k * 12 + 6 + a] = tl;
+                            kq[k * 12 + 9 + a] = tfk;
+                            ks[k] = side[0] | (side[1] << 1) | (side[2] << 2);
+                        }
+                    }
+                    const int64_t ck = loc_cell(g.depth, (base[0] + side[0] + S) % S, (base[1] + side[1] + S) % S,
+                                                (base[2] + side[2] + S) % S);
+                    double f = 0.0;
+                    for (int o = lane; o < p3; o += 32)
+                        f += W[0][e3[0]][o % p] * W[1][e3[1]][(o / p) % p] * W[2][e3[2]][o / (p * p)] *
+                             (double)loc_leaf[ck * p3 + o];
+                    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+                    if (lane == k) fdk = f - far0;
+                    csum[wl][0][k][lane] = 0.0f;  // this lane's compensated sums for the charge
+                    csum[wl][1][k][lane] = 0.0f;
+                }
+                __syncwarp();
                 // two sources per lane and step (f and f + 32), loaded together
-                int c = cb, c2 = cb;
-                for (int f = cpre[cb] + lane; f < fe; f += 64) {
+                const int nsrc = cpre[nc];
+                int c = 0, c2 = 0;
+                for (int f = lane; f < nsrc; f += 64) {
                     while (cpre[c + 1] <= f) c++;
                     const int f2 = f + 32;
-                    const bool ok2 = f2 < fe;
+                    const bool ok2 = f2 < nsrc;
                     if (ok2) {
                         c2 = max(c2, c);
                         while (cpre[c2 + 1] <= f2) c2++;
@@ -1057,187 +1320,43 @@ __global__ void __launch_bounds__(32 * SD_WARPS, 5)
                     const int j2 = ok2 ? cst[c2] + (f2 - cpre[c2]) : j;
                     const int og1 = s_origin[j], og2 = s_origin[j2];
                     const float4 v1 = s_pt[j], v2 = s_pt[j2];
-                    float t1[SD_NM], t2[SD_NM];
-                    source(v1, cpk[c], og1 != i, t1);
-                    source(v2, cpk[c2], ok2 && og2 != i, t2);
-#pragma unroll
-                    for (int k = 0; k < SD_NM; k++) {  // compensated sums
-                        const float y = (t1[k] + t2[k]) - cmp[k], tt = acc[k] + y;
-                        cmp[k] = (tt - acc[k]) - y;
-                        acc[k] = tt;
-                    }
-                }
-                // over the lanes: the moments n >= 1 in single precision (each lane's
-                // compensated sum rounded once); n = 0 (used where the two points see
-                // different slabs, and cancelling there) as pairs
-                float h0 = acc[0], l0 = -cmp[0];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-                    sd_two_sum(h0, l0, __shfl_xor_sync(0xffffffffu, h0, o), __shfl_xor_sync(0xffffffffu, l0, o));
-#pragma unroll
-                for (int k = 1; k < SD_NM; k++) {
-                    float v = acc[k] - cmp[k];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    acc[k] = v;
-                }
-                if (lane == 0) {
-                    msm[wl][0][set * SD_NM] = h0;
-                    msm[wl][1][set * SD_NM] = l0;
-#pragma unroll
-                    for (int k = 1; k < SD_NM; k++) {
-                        msm[wl][0][set * SD_NM + k] = acc[k];
-                        msm[wl][1][set * SD_NM + k] = 0.0f;
-                    }
-                }
-            }
-            if (__any_sync(0xffffffffu, outer_direct)) {
-                // sources of the outer slabs closer to r than the series allows (split
-                // widths well above the default): their direct terms
-                for (int set = 0; set < 3; set += 2) {
-                    const int fb = cpre[set == 0 ? 0 : 27], fe = cpre[set == 0 ? 9 : 36];
-                    int c = set == 0 ? 0 : 27;
-                    for (int f = fb + lane; f < fe; f += 32) {
-                        while (cpre[c + 1] <= f) c++;
-                        const int j = cst[c] + (f - cpre[c]);
-                        if (s_origin[j] == i) continue;
-                        const float4 v = s_pt[j];
-                        const int pk = cpk[c], ux = (pk & 15) - 1, uy = ((pk >> 4) & 15) - 1, uz = (pk >> 8) - 1;
+#pragma unroll 1
+                    for (int h = 0; h < 2; h++) {
+                        if (h == 0 ? og1 == i : (!ok2 || og2 == i)) continue;
+                        const float4 v = h == 0 ? v1 : v2;
+                        const int pk = cpk[h == 0 ? c : c2], ux = (pk & 15) - 1, uy = ((pk >> 4) & 15) - 1,
+                                  uz = (pk >> 8) - 1;
+                        const bool inR = ux <= 1 && uy <= 1 && uz <= 1;
                         const float d0x = sd_axis_diff(v.x, ux, R[0], 0.0f), d0y = sd_axis_diff(v.y, uy, R[1], 0.0f),
                                     d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
                         const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
-                        if (r02 > far2) continue;
                         const float ri0 = r02 > 0.0f ? rsqrtf(r02) : 0.0f;
-                        sd_direct_outer<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, set, a1, m, kq, ks, gs, gsd[wl]);
+#pragma unroll 1
+                        for (int k = 0; k < CH; k++) {
+                            const float term = sd_pair_term<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, inR, kq + k * 12, ks[k]);
+                            const float ak = csum[wl][0][k][lane], ck = csum[wl][1][k][lane];
+                            const float y = term - ck, tt = ak + y;  // compensated sum
+                            csum[wl][1][k][lane] = (tt - ak) - y;
+                            csum[wl][0][k][lane] = tt;
+                        }
                     }
                 }
-            }
-            __syncwarp();
-            if (lane < m) {
-                // D_k = sum_{n>=1} delta^n (M_n of the middle slab + of the slab only
-                // this side sees besides it) + direct terms + far difference; an upper
-                // charge adds M_0(u = 2) - M_0(u = -1) + X, which cancel to a small
-                // number: that sum in double precision
-                const float dk = kq[lane * 12 + a1];
-                const bool up = (sidek >> a1) & 1;
-                const float *MH = msm[wl][0], *ML = msm[wl][1];
-                const int o = up ? 2 * SD_NM : 0;  // the other slab: u = 2 above the plane, u = -1 below
-                float s = 0.0f;
-#pragma unroll
-                for (int k = SD_NM - 1; k >= 1; k--)
-                    s = (s + ((MH[SD_NM + k] + ML[SD_NM + k]) + (MH[o + k] + ML[o + k]))) * dk;
-                const double zs = (up ? (double)Sp * (((double)MH[2 * SD_NM] + (double)ML[2 * SD_NM]) -
-                                                      ((double)MH[0] + (double)ML[0])) + X
-                                      : 0.0) +
-                                  (double)Sp * gsd[wl][lane];
-                delta[e0 + lane] = (float)((double)(Sp * (s + gs[lane]) + myf) + zs);
-            }
-        } else {
-            // ---- several split axes: charges c0 .. c0 + CH - 1, direct terms ----
-            double(*W)[FMM_MAXP + 1][FMM_MAXP] = wsm[wl];
-            {  // weights: lane = a * 8 + e computes entry e of axis a
-                const int a = lane >> 3, e = lane & 7;
-                if (a < 3 && e < A[a].m) {
-                    int side;
-                    float th, tl, tfl;
-                    split_entry_df(g, A[a], e, side, th, tl, tfl);
-                    double w[PM];
-                    lag_weights<double, PM>(Cd, p, (double)th + (double)tl, w);
-#pragma unroll
-                    for (int k = 0; k < PM; k++)
-                        if (k < p) W[a][e][k] = w[k];
-                }
-            }
-            __syncwarp();
-            double far0 = 0.0;  // far field at the reference point (entry 0 of every axis)
-            {
-                const int64_t cr = loc_cell(g.depth, (base[0] + S) % S, (base[1] + S) % S, (base[2] + S) % S);
-                for (int o = lane; o < p3; o += 32)
-                    far0 += W[0][0][o % p] * W[1][0][(o / p) % p] * W[2][0][o / (p * p)] * (double)loc_leaf[cr * p3 + o];
-            }
-            for (int o = 16; o > 0; o >>= 1) far0 += __shfl_xor_sync(0xffffffffu, far0, o);
-            float *kq = ksm[wl];  // per charge of the chunk: s_k - r (3), th (3), tl (3), tf (3)
-            int *ks = ssm[wl];    // and its sides
-            double fdk = 0.0;     // lane k: the far-field difference of charge c0 + k
+                double vk = 0.0;
 #pragma unroll 1
-            for (int k = 0; k < CH; k++) {
-                int le = min(c0 + k, m - 1);
-                const int ex = le % A[0].m;
-                le /= A[0].m;
-                const int e3[3] = {ex, le % A[1].m, le / A[1].m};
-                int side[3];
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    float th, tl, tfk;
-                    split_entry_df(g, A[a], e3[a], side[a], th, tl, tfk);
-                    if (lane == k) {
-                        const float dd = !sp[a] ? 0.0f : (side[a] ? __fadd_rn(th, g.dtf) : __fsub_rn(th, R[a]));
-                        kq[k * 12 + a] = dd + tl;
-                        kq[k * 12 + 3 + a] = th;
-                        kq[k * 12 + 6 + a] = tl;
-                        kq[k * 12 + 9 + a] = tfk;
-                        ks[k] = side[0] | (side[1] << 1) | (side[2] << 2);
-                    }
+                for (int k = 0; k < CH; k++) {
+                    double v = (double)csum[wl][0][k][lane] - (double)csum[wl][1][k][lane];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == k) vk = v;
                 }
-                const int64_t ck = loc_cell(g.depth, (base[0] + side[0] + S) % S, (base[1] + side[1] + S) % S,
-                                            (base[2] + side[2] + S) % S);
-                double f = 0.0;
-                for (int o = lane; o < p3; o += 32)
-                    f += W[0][e3[0]][o % p] * W[1][e3[1]][(o / p) % p] * W[2][e3[2]][o / (p * p)] *
-                         (double)loc_leaf[ck * p3 + o];
-                for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-                if (lane == k) fdk = f - far0;
-                csum[wl][0][k][lane] = 0.0f;  // this lane's compensated sums for the charge
-                csum[wl][1][k][lane] = 0.0f;
+                if (lane < CH && c0 + lane < m) delta[e0 + c0 + lane] = (float)((double)Sp * vk + fdk);
             }
-            __syncwarp();
-            // two sources per lane and step (f and f + 32), loaded together
-            const int nsrc = cpre[nc];
-            int c = 0, c2 = 0;
-            for (int f = lane; f < nsrc; f += 64) {
-                while (cpre[c + 1] <= f) c++;
-                const int f2 = f + 32;
-                const bool ok2 = f2 < nsrc;
-                if (ok2) {
-                    c2 = max(c2, c);
-                    while (cpre[c2 + 1] <= f2) c2++;
-                }
-                const int j = cst[c] + (f - cpre[c]);
-                const int j2 = ok2 ? cst[c2] + (f2 - cpre[c2]) : j;
-                const int og1 = s_origin[j], og2 = s_origin[j2];
-                const float4 v1 = s_pt[j], v2 = s_pt[j2];
-#pragma unroll 1
-                for (int h = 0; h < 2; h++) {
-                    if (h == 0 ? og1 == i : (!ok2 || og2 == i)) continue;
-                    const float4 v = h == 0 ? v1 : v2;
-                    const int pk = cpk[h == 0 ? c : c2], ux = (pk & 15) - 1, uy = ((pk >> 4) & 15) - 1,
-                              uz = (pk >> 8) - 1;
-                    const bool inR = ux <= 1 && uy <= 1 && uz <= 1;
-                    const float d0x = sd_axis_diff(v.x, ux, R[0], 0.0f), d0y = sd_axis_diff(v.y, uy, R[1], 0.0f),
-                                d0z = sd_axis_diff(v.z, uz, R[2], 0.0f);
-                    const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
-                    const float ri0 = r02 > 0.0f ? rsqrtf(r02) : 0.0f;
-#pragma unroll 1
-                    for (int k = 0; k < CH; k++) {
-                        const float term = sd_pair_term<POW>(v, ux, uy, uz, d0x, d0y, d0z, r02, ri0, inR, kq + k * 12, ks[k]);
-                        const float ak = csum[wl][0][k][lane], ck = csum[wl][1][k][lane];
-                        const float y = term - ck, tt = ak + y;  // compensated sum
-                        csum[wl][1][k][lane] = (tt - ak) - y;
-                        csum[wl][0][k][lane] = tt;
-                    }
-                }
-            }
-            double vk = 0.0;
-#pragma unroll 1
-            for (int k = 0; k < CH; k++) {
-                double v = (double)csum[wl][0][k][lane] - (double)csum[wl][1][k][lane];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == k) vk = v;
-            }
-            if (lane < CH && c0 + lane < m) delta[e0 + c0 + lane] = (float)((double)Sp * vk + fdk);
+            __syncwarp();  // the tables are rewritten by the next task
         }
-        __syncwarp();  // the tables are rewritten by the next task
     }
+};
+template <int POW, int CH>
+__global__ void __launch_bounds__(KSplitDelta<POW, CH>::BS, KSplitDelta<POW, CH>::MINB) k_split_delta(const __grid_constant__ KSplitDelta<POW, CH> k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1270,126 +1389,161 @@ __device__ __forceinline__ void pair_add(real &ah, real &al, real bh, real bl) {
 }
 
 template <typename real>
-__global__ void k_unsplit(Geom g, const WsHeader *hdr, int n, const float *__restrict__ q,
-                          const int *__restrict__ offset,
-                          const int *__restrict__ count, const unsigned char *__restrict__ axes,
-                          const typename Vec4<real>::T *__restrict__ e_wd,
-                          const typename Vec4<real>::T *__restrict__ out_e, const float *__restrict__ delta,
-                          real *__restrict__ potential, real *__restrict__ forces, real *__restrict__ epart,
-                          const double *__restrict__ grad_energy, real *__restrict__ grad_q,
-                          int backward, real sphi, real sF) {
-    // sphi = 1/L and sF = 1/L^2 come from the host: no FP64 arithmetic per thread
-    __shared__ real sh[UNSPLIT_BS / 32][2];
-    double gE = backward ? *grad_energy : 0.0;
-    real ehi = 0, elo = 0;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        real phi, Fx, Fy, Fz;
-        if (!offset) {
-            typename Vec4<real>::T o = out_e[i];
-            phi = o.x;
-            Fx = o.y;
-            Fy = o.z;
-            Fz = o.w;
-        } else {
-            int e0 = offset[i], m = count[i];
-            if (e0 + m > hdr->n_eff) m = 0;  // not emitted (split overflow; status is set)
-            phi = 0;
-            real Sx = 0, Sy = 0, Sz = 0, Nx = 0, Ny = 0, Nz = 0;
-            for (int e = e0; e < e0 + m; e++) {
-                typename Vec4<real>::T o = out_e[e];
-                typename Vec4<real>::T d = e_wd[e];
-                phi += d.x * o.x;
-                Sx += o.y;
-                Sy += o.z;
-                Sz += o.w;
-                // split axes: the weights' derivatives against phi(s_k), or
-                // against the differences phi(s_k) - phi(r) where they were formed
-                const real D = (delta && m > 1) ? (real)delta[e] : o.x;
-                Nx += d.y * D;
-                Ny += d.z * D;
-                Nz += d.w * D;
+struct KUnsplit {
+    static constexpr int BS = 0, MINB = 0;
+    Geom g;
+    const WsHeader *hdr;
+    int n;
+    const float *__restrict__ q;
+    const int *__restrict__ offset;
+    const int *__restrict__ count;
+    const unsigned char *__restrict__ axes;
+    const typename Vec4<real>::T *__restrict__ e_wd;
+    const typename Vec4<real>::T *__restrict__ out_e;
+    const float *__restrict__ delta;
+    real *__restrict__ potential;
+    real *__restrict__ forces;
+    real *__restrict__ epart;
+    const double *__restrict__ grad_energy;
+    real *__restrict__ grad_q;
+    int backward;
+    real sphi;
+    real sF;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        // sphi = 1/L and sF = 1/L^2 come from the host: no FP64 arithmetic per thread
+        __shared__ real sh[UNSPLIT_BS / 32][2];
+        double gE = backward ? *grad_energy : 0.0;
+        real ehi = 0, elo = 0;
+        int i = bid_ * blockDim.x + threadIdx.x;
+        if (i < n) {
+            real phi, Fx, Fy, Fz;
+            if (!offset) {
+                typename Vec4<real>::T o = out_e[i];
+                phi = o.x;
+                Fx = o.y;
+                Fy = o.z;
+                Fz = o.w;
+            } else {
+                int e0 = offset[i], m = count[i];
+                if (e0 + m > hdr->n_eff) m = 0;  // not emitted (split overflow; status is set)
+                phi = 0;
+                real Sx = 0, Sy = 0, Sz = 0, Nx = 0, Ny = 0, Nz = 0;
+                for (int e = e0; e < e0 + m; e++) {
+                    typename Vec4<real>::T o = out_e[e];
+                    typename Vec4<real>::T d = e_wd[e];
+                    phi += d.x * o.x;
+                    Sx += o.y;
+                    Sy += o.z;
+                    Sz += o.w;
+                    // split axes: the weights' derivatives against phi(s_k), or
+                    // against the differences phi(s_k) - phi(r) where they were formed
+                    const real D = (delta && m > 1) ? (real)delta[e] : o.x;
+                    Nx += d.y * D;
+                    Ny += d.z * D;
+                    Nz += d.w * D;
+                }
+                // paper and force-kernel forces: the sum of the split charges' forces
+                unsigned ax = g.force_mode != FMM_FORCE_ADJOINT ? 0u : axes[i];
+                real qi = (real)q[i];
+                Fx = (ax & 1) ? -qi * Nx : Sx;
+                Fy = (ax & 2) ? -qi * Ny : Sy;
+                Fz = (ax & 4) ? -qi * Nz : Sz;
             }
-            // paper and force-kernel forces: the sum of the split charges' forces
-            unsigned ax = g.force_mode != FMM_FORCE_ADJOINT ? 0u : axes[i];
-            real qi = (real)q[i];
-            Fx = (ax & 1) ? -qi * Nx : Sx;
-            Fy = (ax & 2) ? -qi * Ny : Sy;
-            Fz = (ax & 4) ? -qi * Nz : Sz;
+            phi *= sphi;
+            Fx *= sF;
+            Fy *= sF;
+            Fz *= sF;
+            if (!backward) {
+                if (potential) potential[i] = phi;
+                if (forces) {
+                    forces[3 * i] = Fx;
+                    forces[3 * i + 1] = Fy;
+                    forces[3 * i + 2] = Fz;
+                }
+                ehi = (real)q[i] * phi;  // q phi exactly as ehi + elo (single precision)
+                elo = fma_exact_err((real)q[i], phi, ehi);
+            } else {
+                if (forces) {
+                    forces[3 * i] = (real)(-(double)Fx * gE);
+                    forces[3 * i + 1] = (real)(-(double)Fy * gE);
+                    forces[3 * i + 2] = (real)(-(double)Fz * gE);
+                }
+                if (grad_q) grad_q[i] = (real)((double)phi * gE);
+            }
         }
-        phi *= sphi;
-        Fx *= sF;
-        Fy *= sF;
-        Fz *= sF;
-        if (!backward) {
-            if (potential) potential[i] = phi;
-            if (forces) {
-                forces[3 * i] = Fx;
-                forces[3 * i + 1] = Fy;
-                forces[3 * i + 2] = Fz;
+        if (epart) {
+            // deterministic block reduction of sum q phi: exact products, then
+            // compensated pair sums over the warp and over the warps in order; the
+            // block's sum stays a (hi, lo) pair of the working precision: no FP64
+            // arithmetic here (a slow pipe on this part, which the per-block
+            // conversions and adds kept busy)
+            for (int o = 16; o > 0; o >>= 1) {
+                const real bh = __shfl_down_sync(0xffffffffu, ehi, o);
+                const real bl = __shfl_down_sync(0xffffffffu, elo, o);
+                pair_add(ehi, elo, bh, bl);
             }
-            ehi = (real)q[i] * phi;  // q phi exactly as ehi + elo (single precision)
-            elo = fma_exact_err((real)q[i], phi, ehi);
-        } else {
-            if (forces) {
-                forces[3 * i] = (real)(-(double)Fx * gE);
-                forces[3 * i + 1] = (real)(-(double)Fy * gE);
-                forces[3 * i + 2] = (real)(-(double)Fz * gE);
+            if ((threadIdx.x & 31) == 0) {
+                sh[threadIdx.x >> 5][0] = ehi;
+                sh[threadIdx.x >> 5][1] = elo;
             }
-            if (grad_q) grad_q[i] = (real)((double)phi * gE);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                real h = sh[0][0], l = sh[0][1];
+                for (int w = 1; w < UNSPLIT_BS / 32; w++) pair_add(h, l, sh[w][0], sh[w][1]);
+                epart[2 * bid_] = h;
+                epart[2 * bid_ + 1] = l;
+            }
         }
     }
-    if (epart) {
-        // deterministic block reduction of sum q phi: exact products, then
-        // compensated pair sums over the warp and over the warps in order; the
-        // block's sum stays a (hi, lo) pair of the working precision: no FP64
-        // arithmetic here (a slow pipe on this part, which the per-block
-        // conversions and adds kept busy)
-        for (int o = 16; o > 0; o >>= 1) {
-            const real bh = __shfl_down_sync(0xffffffffu, ehi, o);
-            const real bl = __shfl_down_sync(0xffffffffu, elo, o);
-            pair_add(ehi, elo, bh, bl);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            sh[threadIdx.x >> 5][0] = ehi;
-            sh[threadIdx.x >> 5][1] = elo;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            real h = sh[0][0], l = sh[0][1];
-            for (int w = 1; w < UNSPLIT_BS / 32; w++) pair_add(h, l, sh[w][0], sh[w][1]);
-            epart[2 * blockIdx.x] = h;
-            epart[2 * blockIdx.x + 1] = l;
-        }
-    }
+};
+template <typename real>
+__global__ void k_unsplit(const __grid_constant__ KUnsplit<real> k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
 // total energy from the blocks' (hi, lo) pairs: strided per-thread pair sums,
 // warp trees, then the warps' pairs in order (fixed order: deterministic);
 // E = (hi + lo) / 2 in FP64 once
 template <typename real>
-__global__ void k_energy_final(const real *__restrict__ epart, int nb, double *energy) {
-    __shared__ real sh[32][2];
-    real h = 0, l = 0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) pair_add(h, l, epart[2 * b], epart[2 * b + 1]);
-    for (int o = 16; o > 0; o >>= 1) {
-        const real bh = __shfl_down_sync(0xffffffffu, h, o);
-        const real bl = __shfl_down_sync(0xffffffffu, l, o);
-        pair_add(h, l, bh, bl);
+struct KEnergyFinal {
+    static constexpr int BS = 0, MINB = 0;
+    const real *__restrict__ epart;
+    int nb;
+    double *energy;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
+        __shared__ real sh[32][2];
+        real h = 0, l = 0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) pair_add(h, l, epart[2 * b], epart[2 * b + 1]);
+        for (int o = 16; o > 0; o >>= 1) {
+            const real bh = __shfl_down_sync(0xffffffffu, h, o);
+            const real bl = __shfl_down_sync(0xffffffffu, l, o);
+            pair_add(h, l, bh, bl);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sh[threadIdx.x >> 5][0] = h;
+            sh[threadIdx.x >> 5][1] = l;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            real th = sh[0][0], tl = sh[0][1];
+            for (int w = 1; w < (int)(blockDim.x >> 5); w++) pair_add(th, tl, sh[w][0], sh[w][1]);
+            *energy = 0.5 * ((double)th + (double)tl);
+        }
     }
-    if ((threadIdx.x & 31) == 0) {
-        sh[threadIdx.x >> 5][0] = h;
-        sh[threadIdx.x >> 5][1] = l;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        real th = sh[0][0], tl = sh[0][1];
-        for (int w = 1; w < (int)(blockDim.x >> 5); w++) pair_add(th, tl, sh[w][0], sh[w][1]);
-        *energy = 0.5 * ((double)th + (double)tl);
-    }
+};
+template <typename real>
+__global__ void k_energy_final(const __grid_constant__ KEnergyFinal<real> k) {
+    k.run(blockIdx.x, gridDim.x);
 }
 
-__global__ void k_zero_energy(double *energy) { *energy = 0.0; }
+struct KZeroEnergy {
+    static constexpr int BS = 0, MINB = 0;
+    double *energy;
+    __device__ __forceinline__ void run(const int bid_, const int nblk_) const {     *energy = 0.0;     }
+};
+__global__ void k_zero_energy(const __grid_constant__ KZeroEnergy k) {
+    k.run(blockIdx.x, gridDim.x);
+}
 
 template <typename real>
 void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n, const float *q,
@@ -1398,7 +1552,7 @@ void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n
     tr.begin(FMM_STAGE_UNSPLIT, st);
     if (n == 0) {
         if (energy && !backward) {
-            k_zero_energy<<<1, 1, 0, st>>>(energy);
+            launch_k(tr, FMM_TAG(S_ZERO_ENERGY, 0), k_zero_energy, KZeroEnergy{energy}, 1, 1, 0, st);
             tr.count();
         }
         tr.end();
@@ -1408,15 +1562,19 @@ void launch_unsplit(const Geom &g, const Ptrs<real> &P, const WsLayout &W, int n
     real *ep = (!backward && energy) ? reinterpret_cast<real *>(P.epart) : nullptr;  // [nb][2]
     // unit box -> box of edge L: potentials of 1/r^k scale by L^-k, forces by L^-(k+1)
     const double iL = 1.0 / g.L, sphi = g.power == 2 ? iL * iL : iL;
-    k_unsplit<real><<<nb, UNSPLIT_BS, 0, st>>>(
-        g, P.hdr, n, q, g.continuous ? P.offset : nullptr, P.count, P.axes,
-        g.continuous ? P.e_wd : nullptr, P.out_e,
-        (std::is_same<real, float>::value && g.continuous && g.force_mode == FMM_FORCE_ADJOINT) ? P.delta : nullptr,
-        potential, forces, ep, grad_energy, grad_q,
-        backward ? 1 : 0, (real)sphi, (real)(sphi * iL));
+    launch_k(tr, FMM_TAG(S_UNSPLIT, 0), k_unsplit<real>,
+             KUnsplit<real>{g, P.hdr, n, q, g.continuous ? P.offset : nullptr, P.count, P.axes,
+                            g.continuous ? P.e_wd : nullptr, P.out_e,
+                            (std::is_same<real, float>::value && g.continuous && g.force_mode == FMM_FORCE_ADJOINT)
+                                ? P.delta
+                                : nullptr,
+                            potential, forces, ep, grad_energy, grad_q, backward ? 1 : 0, (real)sphi,
+                            (real)(sphi * iL)},
+             nb, UNSPLIT_BS, 0, st);
     tr.count();
     if (ep) {
-        k_energy_final<real><<<1, 1024, 0, st>>>(ep, nb, energy);
+        launch_k(tr, FMM_TAG(S_ENERGY_FINAL, 0), k_energy_final<real>, KEnergyFinal<real>{ep, nb, energy}, 1, 1024,
+                 0, st);
         tr.count();
     }
     tr.end();
@@ -1426,8 +1584,9 @@ void launch_split_delta(const Geom &g, const Coef<double> &Cd, const Ptrs<float>
                         const float *pos, cudaStream_t st, Tracer &tr) {
     if (n <= 0) return;
     tr.begin(FMM_STAGE_UNSPLIT, st);
-    cudaMemsetAsync(P.slist, 0, 8, st);
-    k_split_list<<<(n + 255) / 256, 256, 0, st>>>(n, g.p + (g.p & 1), P.count, P.offset, P.hdr, P.slist);
+    zero_words(tr, FMM_TAG(S_ZERO_SLIST, 0), P.slist, 8, st);
+    launch_k(tr, FMM_TAG(S_SPLIT_LIST, 0), k_split_list,
+             KSplitList{n, g.p + (g.p & 1), P.count, P.offset, P.hdr, P.slist}, (n + 255) / 256, 256, 0, st);
     tr.count();
     // persistent: five CTAs per SM, fewer for small systems (a few percent of
     // the particles are split; the loop takes any number of tasks)
@@ -1436,8 +1595,10 @@ void launch_split_delta(const Geom &g, const Coef<double> &Cd, const Ptrs<float>
     // charges per pass of a particle split along several axes
     const int ch = g.p <= 4 ? 4 : (g.p <= 6 ? 6 : 8);
 #define SD_LAUNCH(POW, CH)                                                                                  \
-    k_split_delta<POW, CH><<<nb, 32 * SD_WARPS, 0, st>>>(g, Cd, n, pos, P.count, P.offset, P.leaf_start, P.s_pt, \
-                                                        P.s_origin, leaf, P.delta, P.slist)
+    launch_k(tr, FMM_TAG(S_SPLIT_DELTA, 0), k_split_delta<POW, CH>,                                             \
+             KSplitDelta<POW, CH>{g, Cd, n, pos, P.count, P.offset, P.leaf_start, P.s_pt, P.s_origin, leaf, P.delta, \
+                                  P.slist},                                                                     \
+             nb, 32 * SD_WARPS, 0, st)
     if (g.power == 2) {
         if (ch == 4) SD_LAUNCH(2, 4); else if (ch == 6) SD_LAUNCH(2, 6); else SD_LAUNCH(2, 8);
     } else {

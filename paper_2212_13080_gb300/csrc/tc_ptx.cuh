@@ -61,7 +61,15 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// ---- TMA (tensor maps in kernel parameter space) ------------------------------
+// ---- TMA (tensor maps in kernel parameter space, or in global memory where a
+// batched launch keeps every system's parameters in a device array) ---------
+// A map in global memory: orders the generic-proxy writes that put it there
+// before this thread's tensor-map-proxy reads of it.
+__device__ __forceinline__ void tensormap_acquire(const void *map) {
+    if (__isGlobal(map))
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                     : "memory");
+}
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
                                             int c0, int c1, int c2) {
     asm volatile(

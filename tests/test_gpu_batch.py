@@ -16,13 +16,18 @@ def _depths(counts):
     return np.clip(np.rint(np.log(counts / 32.0) / np.log(8.0)), 3, 5).astype(int)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "fp64"])
 def test_batch_matches_single_system(precision):
+    """Single-precision plans run every launch site once for all systems
+    (merged form; depths 3, 4 and 5 mixed, so that the systems' level loops
+    and their scan and launch-order variants differ); FP64 plans run as
+    per-system pipelines on stream lanes."""
     pos, q, offs, boxes, counts = inputs.batch_systems(12, 7, lo=1024, hi=20000)
     boxes[3] = (0.25, -1.0, 2.0, 1.5)  # one system in another box
     pos[offs[3]:offs[4]] = (pos[offs[3]:offs[4]] * np.float32(1.5) +
                             np.array([0.25, -1.0, 2.0], np.float32)).astype(np.float32)
     depths = _depths(counts)
+    depths[int(np.argmax(counts))] = 5  # sparse finest cells, 32,768 of them
     bt = FMMBatch(boxes, depths, 4, periodic=True, continuous=True, precision=precision,
                   max_n=counts)
     P, Q = torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda()
@@ -30,7 +35,12 @@ def test_batch_matches_single_system(precision):
         r = bt.eval(P, Q, offs)
         torch.cuda.synchronize()
         st = bt.stats()
-        assert st["lanes"] in (2, 4, 8, 12, 16, 32) and st["launches"] > 12
+        if precision == "fp64":
+            assert not st["merged"] and st["lanes"] in (2, 4, 8, 12, 16, 32) and st["launches"] > 12
+        else:
+            # one launch per call site (levels and variants included) plus the status kernel
+            assert st["merged"] and st["lanes"] == 0 and st["schedule"] in (0, 1)
+            assert 12 < st["launches"] < 80
         for i in range(len(counts)):
             a, b = offs[i], offs[i + 1]
             plan = FMM(boxes[i], int(depths[i]), 4, periodic=True, continuous=True,
@@ -58,23 +68,25 @@ def test_batch_against_oracle():
     bt.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
 @pytest.mark.parametrize("periodic,kernel,force_mode", [(True, "coulomb", "kernel"),
                                                          (False, "inverse_square", "adjoint")])
-def test_batch_other_kernels_match_single_system(periodic, kernel, force_mode):
+def test_batch_other_kernels_match_single_system(periodic, kernel, force_mode, precision):
     """Force-kernel forces (§4.1) and the 1/r^2 kernel through the batched
     path: each system equals its own single-system evaluation bit for bit
     (the batched systems share their depth's tables, four kernel components
-    for force-kernel plans)."""
+    for force-kernel plans; with the tensor cores, the small levels of all
+    systems in shared cross-system tiles, from level 1 periodic or 2 open)."""
     pos, q, offs, boxes, counts = inputs.batch_systems(6, 17, lo=1024, hi=12000)
     depths = _depths(counts)
-    bt = FMMBatch(boxes, depths, 4, periodic=periodic, continuous=True, precision="fp32",
+    bt = FMMBatch(boxes, depths, 4, periodic=periodic, continuous=True, precision=precision,
                   max_n=counts, kernel=kernel, force_mode=force_mode)
     P, Q = torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda()
     r = bt.eval(P, Q, offs)
     torch.cuda.synchronize()
     for i in range(len(counts)):
         a, b = offs[i], offs[i + 1]
-        plan = FMM(boxes[i], int(depths[i]), 4, periodic=periodic, continuous=True, precision="fp32",
+        plan = FMM(boxes[i], int(depths[i]), 4, periodic=periodic, continuous=True, precision=precision,
                    max_n=int(counts[i]), kernel=kernel, force_mode=force_mode)
         s = plan.eval(P[a:b].contiguous(), Q[a:b].contiguous())
         assert torch.equal(r["potential"][a:b], s["potential"]), i
