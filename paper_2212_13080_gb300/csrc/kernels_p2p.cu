@@ -241,9 +241,11 @@ __global__ void __launch_bounds__(KL2P<real, P, FORCES, KF>::BS) k_l2p(const __g
 // CK = 0 (plain form: every charge is a particle of its own, none to skip),
 // 1 (continuous form: charges of the same particle), 2 (and coincident ones).
 // Single precision evaluates two targets per packed FP32x2 instruction
-// (nf_targets2), the targets staged a second time by pairs.  (Skipping a
-// warp's source slots past the last source, with the slots assigned warp by
-// warp and a warp-uniform count of the active ones, was measured slower.)
+// (nf_targets2), the targets staged a second time by pairs.  A pass with at
+// most 128 (256) sources evaluates the first one (two) of each thread's
+// source slots only: slot k of thread t is source 128 k + t, so the count is
+// the same for the whole CTA.  (Skipping empty slots warp by warp, with the
+// slots assigned warp-major, was measured slower.)
 //
 // Own phase: the pairs inside A, one-sided (each target against all of A's
 // charges), skipping charges of the same particle and coincident charges.
@@ -412,11 +414,11 @@ __device__ __forceinline__ void nf_stage_pair(float4 *tpa, float4 *tpb, int2 *tp
 }
 __device__ __forceinline__ void nf_stage_pair(double4 *, double4 *, int2 *, int, double4, int) {}
 
-// NT targets from g0 (an even count) against this thread's KS sources, packed
+// NT targets from g0 (an even count) against this thread's first KV of KS sources, packed
 // by target pairs; the sums are transposed through shared memory in
 // pair-major order (value (q, c, h) at q*2*NC + 2c + h, target 2q + h, component
 // c) and summed over the warp's lanes in order into wp.
-template <bool FORCES, int CK, int POW, int NT, int KS>
+template <bool FORCES, int CK, int POW, int NT, int KS, int KV = KS>
 __device__ __forceinline__ void nf_targets2(const float4 *tpa, const float4 *tpb, const int2 *tpo, int g0, int nt,
                                             const float2 (&nsx)[KS], const float2 (&nsy)[KS],
                                             const float2 (&nsz)[KS], const float2 (&sq)[KS], const int (&so)[KS],
@@ -437,7 +439,7 @@ __device__ __forceinline__ void nf_targets2(const float4 *tpa, const float4 *tpb
         nf_pair2<FORCES, CK, true, POW>(tx, ty, tz, ntw, O.x, O.y, nsx[0], nsy[0], nsz[0], sq[0], so[0],
                                         acc + q * NC, rp[0], rx[0], ry[0], rz[0]);
 #pragma unroll
-        for (int k = 1; k < KS; k++)
+        for (int k = 1; k < KV; k++)
             nf_pair2<FORCES, CK, false, POW>(tx, ty, tz, ntw, O.x, O.y, nsx[k], nsy[k], nsz[k], sq[k], so[k],
                                              acc + q * NC, rp[k], rx[k], ry[k], rz[k]);
     }
@@ -638,12 +640,23 @@ struct KP2P {
                 if (!one_block || pass > 0) __syncthreads();
                 int g0 = 0;
                 if constexpr (sizeof(real) == 4) {
-                    for (; g0 + TG <= nt; g0 += TG)
-                        nf_targets2<FORCES, CK, POW, TG, NF_KS>(tpa, tpb, tpo, g0, nt, nsx2, nsy2, nsz2, sq2, so, rp2,
-                                                                rx2, ry2, rz2, tb_w, wpart[warp], lane);
-                    for (; g0 < nt; g0 += TR)
-                        nf_targets2<FORCES, CK, POW, TR, NF_KS>(tpa, tpb, tpo, g0, nt, nsx2, nsy2, nsz2, sq2, so, rp2,
-                                                                rx2, ry2, rz2, tb_w, wpart[warp], lane);
+                    // the source slots that hold a source in this pass (the same for
+                    // the whole CTA: slot k of thread t is source k NF_BS + t)
+                    const int rem = Ns - pass * NF_BS * NF_KS;
+                    const int kv = rem <= NF_BS ? 1 : (rem <= 2 * NF_BS ? 2 : NF_KS);
+#define NF_GROUPS(KV)                                                                                           \
+    do {                                                                                                        \
+        for (; g0 + TG <= nt; g0 += TG)                                                                         \
+            nf_targets2<FORCES, CK, POW, TG, NF_KS, KV>(tpa, tpb, tpo, g0, nt, nsx2, nsy2, nsz2, sq2, so, rp2, rx2, \
+                                                        ry2, rz2, tb_w, wpart[warp], lane);                     \
+        for (; g0 < nt; g0 += TR)                                                                               \
+            nf_targets2<FORCES, CK, POW, TR, NF_KS, KV>(tpa, tpb, tpo, g0, nt, nsx2, nsy2, nsz2, sq2, so, rp2, rx2, \
+                                                        ry2, rz2, tb_w, wpart[warp], lane);                     \
+    } while (0)
+                    if (kv == 1) NF_GROUPS(1);
+                    else if (kv == 2) NF_GROUPS(2);
+                    else NF_GROUPS(NF_KS);
+#undef NF_GROUPS
                 }
                 for (; g0 + TG <= nt; g0 += TG) {
                     real acc[32];
