@@ -168,7 +168,10 @@ int fmm_workspace_size(fmm_plan_t plan, int64_t n, size_t *bytes);
  *   stream     cudaStream_t as void*.
  * With opts.sync = 1 the call waits for the device and returns the device
  * status (FMM_ERR_OUT_OF_BOX, FMM_ERR_NONFINITE, FMM_ERR_SPLIT_OVERFLOW);
- * outputs are then undefined if the status is not FMM_OK.
+ * outputs are then undefined if the status is not FMM_OK.  A stream being
+ * captured into a CUDA graph cannot be waited on: with opts.sync = 1 the call
+ * then returns FMM_ERR_ARG before any work (plans for captured streams take
+ * opts.sync = 0 and read the status later with fmm_status).
  */
 int fmm_eval(fmm_plan_t plan, int64_t n, const float *pos, const float *q, void *potential,
              double *energy, void *forces, void *workspace, size_t workspace_bytes,

@@ -137,6 +137,10 @@ class FMM:
         F = o.get("forces")
         if forces and F is None:
             F = torch.empty((n, 3), dtype=self.out_dtype, device=self.device)
+        if self.sync and torch.cuda.is_current_stream_capturing():
+            # the status wait after the call would end the capture (as the library's
+            # own opts.sync = 1 refuses it): plans for captured streams take sync=False
+            raise FmmError(B.FMM_ERR_ARG, "fmm_eval (sync plan on a stream being captured)")
         # recorded first: a failed call's workspace still holds its status and wait site
         self._last = (ws, n, pos_d, q_d)
         B.fmm_eval(self._h, n, _ptr(pos_d), _ptr(q_d), _ptr(phi) if potential else None,

@@ -824,6 +824,11 @@ int fmm_eval(fmm_plan_t P, int64_t n, const float *pos, const float *q, void *po
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaGetLastError();
+    if (P->opts.sync) {  // the final wait would end a capture in progress
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FMM_ERR_CUDA;
+        if (cs != cudaStreamCaptureStatusNone) return FMM_ERR_ARG;
+    }
     Tracer tr = make_tracer(P, st);
     Streams S = {st, P->s_near, P->s_coarse, P->e_sorted, P->e_near, P->e_fork, P->e_coarse,
                  P->s_far, P->e_far};

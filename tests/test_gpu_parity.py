@@ -634,3 +634,37 @@ def test_continuity_through_the_periodic_wall_fp64():
         else:
             assert abs(E1 - E0) > 20 * Fm * dx, (E1 - E0, Fm * dx)
         plan.close()
+
+
+def test_sync_plan_refuses_a_stream_being_captured():
+    """Through the C ABI: a plan that waits for the device at the end of the
+    call (opts.sync = 1) returns FMM_ERR_ARG, before any work, when its stream
+    is being captured into a CUDA graph (the wait would end the capture); the
+    capture stays valid, and the same call outside a capture evaluates."""
+    import ctypes
+    from paper_2212_13080_gb300 import _ptr
+    pos, q, box = inputs.uniform_cont(3000, 21)
+    n = len(q)
+    P, Q = torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda()
+    o = B.fmm_opts_default()
+    o.continuous = 1
+    o.sync = 1
+    h = B.fmm_plan_create(box, 3, 4, False, o, n)
+    nb = B.fmm_workspace_size(h, n)
+    ws = FMM._aligned(torch.empty(nb + 256, dtype=torch.uint8, device="cuda"))
+    phi = torch.zeros(n, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(FmmError) as e:
+        with torch.cuda.graph(g):
+            st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            B.fmm_eval(h, n, _ptr(P), _ptr(Q), _ptr(phi), None, None, _ptr(ws), nb, st)
+    assert e.value.code == B.FMM_ERR_ARG
+    torch.cuda.synchronize()
+    assert not torch.any(phi != 0)  # nothing ran
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    B.fmm_eval(h, n, _ptr(P), _ptr(Q), _ptr(phi), None, None, _ptr(ws), nb, st)
+    torch.cuda.synchronize()
+    plan = FMM(box, 3, 4, continuous=True, max_n=n)  # the same plan, its status read by the binding
+    assert torch.equal(phi, plan.eval(P, Q)["potential"])
+    plan.close()
+    B.fmm_plan_destroy(h)
