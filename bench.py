@@ -48,8 +48,8 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
 # ran on a smaller case of the same distribution); reported as the
 # rooflines' traffic
 PROFILED_TRAFFIC = {("uniform1m", "tf32x3", "k_p2p"): 201362688,
-                    ("plummer8m", "tf32x3", "k_m2l_tcg"): 353887522048 + 960099840,
-                    ("plummer8m", "tf32x3", "k_p2p"): 380062976 + 1789159168}
+                    ("plummer8m", "tf32x3", "k_m2l_tcg"): 339113666816 + 960174080,
+                    ("plummer8m", "tf32x3", "k_p2p"): 353114368 + 1788425728}
 
 
 def _peaks():
