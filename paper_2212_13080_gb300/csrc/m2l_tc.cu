@@ -702,6 +702,7 @@ struct SplitLevels {
     int lmin, lmax;
     long long src[FMM_MAXDEPTH + 2];  // first value of level l in the padded layout
     long long dst[FMM_MAXDEPTH + 2];  // first cell of level l in the operand layout
+    long long cst[FMM_MAXDEPTH + 2];  // first visited cell of level l (from lmin; see split_cell)
 };
 __device__ __forceinline__ bool split_source(const SplitLevels &L, int64_t c, int &l, int64_t &src_cell) {
     l = L.lmin;
@@ -722,6 +723,27 @@ __device__ __forceinline__ bool split_source(const SplitLevels &L, int64_t c, in
 // with `nearest` (the 1-pass form, which has no lo term) hi is x rounded to the
 // nearest TF32 value (ties away from zero) instead of truncated.  One thread per
 // 4 consecutive values of a cell (p3s % 32 == 0).
+// Visited cell k -> level l, operand cell c and padded-layout cell src_cell;
+// false: c lies outside the padded layout (written as zeros).  Levels below
+// lpad visit the padded layout's cells only (no box copy reads the rest of
+// their operand layout); the others every operand cell.
+__device__ __forceinline__ bool split_cell(const SplitLevels &L, int lpad, int64_t k, int &l, int64_t &c,
+                                           int64_t &src_cell) {
+    l = L.lmin;
+    while (l < L.lmax && k >= L.cst[l + 1]) l++;
+    const int64_t r = k - L.cst[l];
+    if (l < lpad) {
+        const int Pt = (int)tc_level_extent(l), P = (1 << (l - 1)) + 2;
+        const int x = (int)(r % P), y = (int)((r / P) % P), z = (int)((r / (P * P)) % P), par = (int)(r / (P * P * P));
+        c = L.dst[l] + ((int64_t)(par * Pt + z) * Pt + y) * Pt + x;
+        src_cell = r;
+        return true;
+    }
+    c = L.dst[l] + r;
+    int l2;
+    return split_source(L, c, l2, src_cell);
+}
+
 struct KSplitTf32 {
     static constexpr int BS = 0, MINB = 0;
     const float *__restrict__ phi;
@@ -731,18 +753,16 @@ struct KSplitTf32 {
     int p3;
     int p3s;
     int nearest;
-    int lpad;  // levels below lpad: cells outside the padded layout are left unwritten (no box reads them)
+    int lpad;  // levels below lpad: cells outside the padded layout are not visited (no box reads them)
     __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
         const int q4 = p3s / 4;
-        const int64_t c0 = L.dst[L.lmin], n = (L.dst[L.lmax + 1] - c0) * q4;
+        const int64_t n = L.cst[L.lmax + 1] * q4;
         for (int64_t i = bid_ * (int64_t)blockDim.x + threadIdx.x; i < n;
              i += (int64_t)nblk_ * blockDim.x) {
-            const int64_t c = c0 + i / q4;
             const int b0 = (int)(i % q4) * 4;
             int l;
-            int64_t sc;
-            const bool in = split_source(L, c, l, sc);
-            if (!in && l < lpad) continue;
+            int64_t c, sc;
+            const bool in = split_cell(L, lpad, i / q4, l, c, sc);
             const float *src = phi + L.src[l] + sc * p3;
             float v[4], h[4], w[4];
 #pragma unroll
@@ -774,15 +794,13 @@ struct KSplitBf16 {
     int lpad;  // as KSplitTf32
     __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
         const int q4 = p3k / 4;
-        const int64_t c0 = L.dst[L.lmin], n = (L.dst[L.lmax + 1] - c0) * q4;
+        const int64_t n = L.cst[L.lmax + 1] * q4;
         for (int64_t i = bid_ * (int64_t)blockDim.x + threadIdx.x; i < n;
              i += (int64_t)nblk_ * blockDim.x) {
-            const int64_t c = c0 + i / q4;
             const int b0 = (int)(i % q4) * 4;
             int l;
-            int64_t sc;
-            const bool in = split_source(L, c, l, sc);
-            if (!in && l < lpad) continue;
+            int64_t c, sc;
+            const bool in = split_cell(L, lpad, i / q4, l, c, sc);
             const float *src = phi + L.src[l] + sc * p3;
             __nv_bfloat16 h[4], w[4];
 #pragma unroll
@@ -922,17 +940,22 @@ int launch_m2l_tc(const Geom &g, const Ptrs<float> &P, const WsLayout &W, const 
         SL.src[l] = l <= depth ? W.phi_level[l] : 0;
         SL.dst[l] = tc_level_first(l);
     }
+    // a batch whose small levels run as cross-system (gathered) tiles reads
+    // none of their padding
+    const int lpad = tr.rec ? tr.tc_lbig : 0;
+    SL.cst[lmin] = 0;
+    for (int l = lmin; l <= depth; l++) {
+        const int64_t P = ((int64_t)1 << (l - 1)) + 2;
+        SL.cst[l + 1] = SL.cst[l] + (l < lpad ? 8 * P * P * P : SL.dst[l + 1] - SL.dst[l]);
+    }
     tr.begin(FMM_STAGE_M2L, st);
     __nv_bfloat16 *hi16 = reinterpret_cast<__nv_bfloat16 *>(P.phihi);
     __nv_bfloat16 *lo16 = reinterpret_cast<__nv_bfloat16 *>(P.philo);
     if (split) {
         // grid-stride over the levels' (cell, 4 values); small systems take a
         // small grid, so that other work keeps the SMs
-        const int64_t units = (SL.dst[depth + 1] - SL.dst[lmin]) * ((bf16 ? pk : p3s) / 4);
+        const int64_t units = SL.cst[depth + 1] * ((bf16 ? pk : p3s) / 4);
         const int nbs = (int)std::min<int64_t>(152 * 8, std::max<int64_t>(1, (units + 255) / 256));
-        // a batch whose small levels run as cross-system (gathered) tiles reads
-        // none of their padding
-        const int lpad = tr.rec ? tr.tc_lbig : 0;
         if (bf16)
             launch_k(tr, FMM_TAG(S_SPLIT_TC, 0), k_split_bf16, KSplitBf16{P.phi, SL, hi16, lo16, p3, pk, lpad}, nbs,
                      256, 0, st);
