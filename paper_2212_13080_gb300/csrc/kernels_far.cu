@@ -374,10 +374,11 @@ void launch_halo(int p3, int l, int periodic, real *phi_l, real *q_l, cudaStream
 // ---------------------------------------------------------------------------
 #define M2L_BS 256
 #define M2L_T 64
+#define M2L_PS (M2L_T + 4)  // row stride of the staged source values (keeps rows 16-byte aligned)
 
 template <typename real>
 struct KM2LSimt {
-    static constexpr int BS = M2L_BS, MINB = 0;  // bounds on the block size only
+    static constexpr int BS = M2L_BS, MINB = sizeof(real) == 4 ? 2 : 0;  // FP32: two CTAs per SM
     int p;
     int l;
     const real *__restrict__ phi_l;
@@ -391,8 +392,8 @@ struct KM2LSimt {
     __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
         typedef typename Vec4<real>::T real4;
         extern __shared__ __align__(16) unsigned char smraw[];
-        real *Ps = reinterpret_cast<real *>(smraw);  // [64 b][64 cells]
-        real *Ks = Ps + M2L_T * M2L_T;               // [64 b][64 a]
+        real *Ps = reinterpret_cast<real *>(smraw);  // [64 cells][M2L_PS]: b fastest
+        real *Ks = Ps + M2L_T * M2L_PS;              // [64 b][64 a]
         real *Qs = Ks + M2L_T * M2L_T;               // [64 cells] source total charges
         real *Kb = Qs + M2L_T;                       // [64 a] row means
         const int p3 = p * p * p;
@@ -408,6 +409,11 @@ struct KM2LSimt {
         const int bx = par & 1, by = (par >> 1) & 1, bz = (par >> 2) & 1;
         const int ncell = T * T * T;
         const int cg = threadIdx.x / 16, ag = threadIdx.x % 16;
+        // the cells this thread stages: value b = threadIdx % 64 of cells
+        // c = threadIdx / 64 + 4 it; with T = 4, cell c of the tile is
+        // (c % 4, c / 4 % 4, c / 16): x = threadIdx / 64, y = it % 4, z = it / 4
+        const int c0 = (int)threadIdx.x / M2L_T;
+        const int rb = ((TZ + 1) * P + TY + 1) * P + TX + c0 + 1;
         // per-offset partial sums (64 terms) are added into the totals with Kahan
         // compensation: one FP32 accumulator over all 189 x 64 terms would lose
         // ~sqrt(12096/2) ulps
@@ -450,18 +456,23 @@ struct KM2LSimt {
                         int a = threadIdx.x - M2L_T;
                         Kb[a] = (a0 + a < p3) ? Kbar[(int64_t)oi * p3 + a0 + a] : real(0);
                     }
+                    const int64_t sbase = (int64_t)spar * P * P * P + ((int64_t)dZ * P + dY) * P + dX;
                     for (int b0 = 0; b0 < p3; b0 += M2L_T) {
-                        // stage sources: Ps[b][ci]
-                        for (int e = threadIdx.x; e < M2L_T * M2L_T; e += M2L_BS) {
-                            int ci = e % M2L_T, b = e / M2L_T;
-                            real v = 0;
-                            if (ci < ncell && b0 + b < p3) {
-                                int tx = ci % T, ty = (ci / T) % T, tz = ci / (T * T);
-                                int64_t cell = (((int64_t)spar * P + TZ + tz + 1 + dZ) * P + TY + ty + 1 + dY) * P +
-                                               TX + tx + 1 + dX;
-                                v = phi_l[cell * p3 + b0 + b];
+                        // stage sources: Ps[ci][b], b fastest (coalesced reads of a cell's values)
+                        const int b = threadIdx.x % M2L_T;
+#pragma unroll
+                        for (int it = 0; it < M2L_T * M2L_T / M2L_BS; it++) {
+                            const int ci = c0 + (M2L_BS / M2L_T) * it;
+                            int r;
+                            if (T == 4) {
+                                r = rb + ((it >> 2) * P + (it & 3)) * P;
+                            } else {
+                                const int tx = ci % T, ty = (ci / T) % T, tz = ci / (T * T);
+                                r = ci < ncell ? ((TZ + tz + 1) * P + TY + ty + 1) * P + TX + tx + 1 : -1;
                             }
-                            Ps[b * M2L_T + ci] = v;
+                            real v = 0;
+                            if (r >= 0 && b0 + b < p3) v = phi_l[(sbase + r) * p3 + b0 + b];
+                            Ps[ci * M2L_PS + b] = v;
                         }
                         // stage Kt_o^T: Ks[b][a] = Kt_o[a0+a][b0+b]
                         for (int e = threadIdx.x; e < M2L_T * M2L_T; e += M2L_BS) {
@@ -472,15 +483,36 @@ struct KM2LSimt {
                         }
                         __syncthreads();
                         const int bn = min(M2L_T, p3 - b0);
-                        for (int b = 0; b < bn; b++) {
-                            real4 pv = *reinterpret_cast<const real4 *>(&Ps[b * M2L_T + cg * 4]);
-                            real4 kv = *reinterpret_cast<const real4 *>(&Ks[b * M2L_T + ag * 4]);
-                            real pc[4] = {pv.x, pv.y, pv.z, pv.w};
-                            real kc[4] = {kv.x, kv.y, kv.z, kv.w};
+                        int bb = 0;
+                        for (; bb + 4 <= bn; bb += 4) {  // four values b of four cells per load
+                            real pv[4][4];
 #pragma unroll
-                            for (int i = 0; i < 4; i++)
+                            for (int i = 0; i < 4; i++) {
+                                const real4 v = *reinterpret_cast<const real4 *>(&Ps[(cg * 4 + i) * M2L_PS + bb]);
+                                pv[i][0] = v.x;
+                                pv[i][1] = v.y;
+                                pv[i][2] = v.z;
+                                pv[i][3] = v.w;
+                            }
 #pragma unroll
-                                for (int j = 0; j < 4; j++) acc[i][j] += pc[i] * kc[j];
+                            for (int u = 0; u < 4; u++) {
+                                const real4 kv = *reinterpret_cast<const real4 *>(&Ks[(bb + u) * M2L_T + ag * 4]);
+                                const real kc[4] = {kv.x, kv.y, kv.z, kv.w};
+#pragma unroll
+                                for (int i = 0; i < 4; i++)
+#pragma unroll
+                                    for (int j = 0; j < 4; j++) acc[i][j] += pv[i][u] * kc[j];
+                            }
+                        }
+                        for (; bb < bn; bb++) {
+                            const real4 kv = *reinterpret_cast<const real4 *>(&Ks[bb * M2L_T + ag * 4]);
+                            const real kc[4] = {kv.x, kv.y, kv.z, kv.w};
+#pragma unroll
+                            for (int i = 0; i < 4; i++) {
+                                const real pc = Ps[(cg * 4 + i) * M2L_PS + bb];
+#pragma unroll
+                                for (int j = 0; j < 4; j++) acc[i][j] += pc * kc[j];
+                            }
                         }
                         __syncthreads();
                     }
@@ -514,7 +546,7 @@ struct KM2LSimt {
     }
 };
 template <typename real>
-__global__ void __launch_bounds__(KM2LSimt<real>::BS) k_m2l_simt(const __grid_constant__ KM2LSimt<real> k) {
+__global__ void __launch_bounds__(KM2LSimt<real>::BS, sizeof(real) == 4 ? 2 : 1) k_m2l_simt(const __grid_constant__ KM2LSimt<real> k) {
     k.run(blockIdx.x, gridDim.x);
 }
 
@@ -708,7 +740,7 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
     cudaStream_t st = S.main;
     const int p = g.p, p3 = g.p3, depth = g.depth;
     const int achunks = (p3 + M2L_T - 1) / M2L_T;
-    const size_t sm_m2l = sizeof(real) * (2 * M2L_T * M2L_T + 2 * M2L_T);
+    const size_t sm_m2l = sizeof(real) * (M2L_T * M2L_PS + M2L_T * M2L_T + 2 * M2L_T);
     // 1. every level's own interaction-list contributions (they only need Phi),
     //    for every kernel component c (its own L block, forms scaled by
     //    2^(l spow)): L_0 = lattice term (periodic), L_l = sum over the
@@ -801,8 +833,9 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
 }
 
 void far_set_attributes() {
-    cudaFuncSetAttribute(k_m2l_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 66 * 1024);
-    kb_set_smem<KM2LSimt<double>>(66 * 1024);
+    const int sm_simt_d = (int)(sizeof(double) * (M2L_T * M2L_PS + M2L_T * M2L_T + 2 * M2L_T));
+    cudaFuncSetAttribute(k_m2l_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_simt_d);
+    kb_set_smem<KM2LSimt<double>>(sm_simt_d);
 #define ATTR(real, PP)                                                                             \
     cudaFuncSetAttribute(k_m2m<real, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                          (int)m2m_smem<real, PP>());                                              \
