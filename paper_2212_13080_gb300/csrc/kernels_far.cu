@@ -389,6 +389,8 @@ struct KM2LSimt {
     int ngroups;
     int spow;
     int ntiles;  // grid: tile fastest, then the 8 parities, then a-chunk x group
+    const int *__restrict__ leaf_start;  // target cells' occupancy (finest level depth)
+    int depth;
     __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
         typedef typename Vec4<real>::T real4;
         extern __shared__ __align__(16) unsigned char smraw[];
@@ -408,6 +410,17 @@ struct KM2LSimt {
         const int TX = (tile % ntx) * T, TY = ((tile / ntx) % ntx) * T, TZ = (tile / (ntx * ntx)) * T;
         const int bx = par & 1, by = (par >> 1) & 1, bz = (par >> 2) & 1;
         const int ncell = T * T * T;
+        // a tile none of whose target cells holds a charge forms no functional
+        // that is read (step 4 reads the functionals of occupied cells only)
+        {
+            int occ = 0;
+            if ((int)threadIdx.x < ncell) {
+                const int ci = threadIdx.x, tx = ci % T, ty = (ci / T) % T, tz = ci / (T * T);
+                const uint32_t key = morton_encode(2 * (TX + tx) + bx, 2 * (TY + ty) + by, 2 * (TZ + tz) + bz);
+                occ = cell_occupied(leaf_start, depth, l, key);
+            }
+            if (!__syncthreads_or(occ)) return;
+        }
         const int cg = threadIdx.x / 16, ag = threadIdx.x % 16;
         // the cells this thread stages: value b = threadIdx % 64 of cells
         // c = threadIdx / 64 + 4 it; with T = 4, cell c of the tile is
@@ -781,7 +794,7 @@ int launch_downward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, con
             tr.begin(FMM_STAGE_M2L, S.coarse);
             launch_k(tr, FMM_TAG(S_M2L_SIMT, 4 * l + c), k_m2l_simt<real>,
                      KM2LSimt<real>{p, l, P.phi + W.phi_level[l], P.qlev + W.q_level[l], dst, T.KtT[c], T.Kbar[c],
-                                    G, spow, ntiles},
+                                    G, spow, ntiles, P.leaf_start, depth},
                      ntiles * 8 * achunks * G, M2L_BS, sm_m2l, S.coarse);
             tr.count();
             if (G > 1) {
