@@ -47,7 +47,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
 # capture of the current kernels (scaled to a full launch where the capture
 # ran on a smaller case of the same distribution); reported as the
 # rooflines' traffic
-PROFILED_TRAFFIC = {("uniform1m", "tf32x3", "k_p2p"): 201362688,
+PROFILED_TRAFFIC = {("uniform1m", "tf32x3", "k_p2p"): 48267520 + 187352576,
                     ("plummer8m", "tf32x3", "k_m2l_tcg"): 339113666816 + 960174080,
                     ("plummer8m", "tf32x3", "k_p2p"): 353114368 + 1788425728}
 
