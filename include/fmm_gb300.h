@@ -356,6 +356,15 @@ typedef struct {
 int fmm_batch_get_stats(fmm_batch_t batch, fmm_batch_stats_t *stats);
 
 /*
+ * fmm_batch_set_schedule — fixes the merged form's schedule instead of timing
+ * both on the next capture: 0 one stream, 1 the near field on a second
+ * stream; -1 returns to the autotuner.  The next fmm_batch_eval records and
+ * captures its graph again.  Both schedules give the same results bit for
+ * bit.  Errors: FMM_ERR_ARG (null batch, another value).
+ */
+int fmm_batch_set_schedule(fmm_batch_t batch, int schedule);
+
+/*
  * fmm_eval_static — fmm_eval without a workspace argument.  The paper has no
  * counterpart: this entry point is for callers that cannot allocate device
  * memory at the time they evaluate (a plugin inside a host application whose

@@ -312,6 +312,11 @@ class FMMBatch:
     def stats(self):
         return B.fmm_batch_get_stats(self._h)
 
+    def set_schedule(self, schedule):
+        """Fixes the merged launches' schedule (0: one stream, 1: the near
+        field on a second stream) or returns to the autotuner (-1)."""
+        B.fmm_batch_set_schedule(self._h, schedule)
+
 
 class _Energy(torch.autograd.Function):
     @staticmethod

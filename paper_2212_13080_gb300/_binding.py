@@ -53,7 +53,7 @@ EXPORTED = ["fmm_opts_default", "fmm_plan_create", "fmm_plan_destroy", "fmm_work
             "fmm_set_timing", "fmm_get_stats", "fmm_strerror", "fmm_version",
             "fmm_eval_static", "fmm_batch_create", "fmm_batch_destroy",
             "fmm_batch_workspace_size", "fmm_batch_eval", "fmm_batch_get_stats",
-            "fmm_debug_inject"]
+            "fmm_batch_set_schedule", "fmm_debug_inject"]
 
 FMM_STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -121,6 +121,7 @@ def lib():
         L.fmm_batch_workspace_size.argtypes = [P, P, ctypes.POINTER(sz)]
         L.fmm_batch_eval.argtypes = [P, P, P, P, P, P, P, P, sz, P]
         L.fmm_batch_get_stats.argtypes = [P, ctypes.POINTER(fmm_batch_stats_t)]
+        L.fmm_batch_set_schedule.argtypes = [P, i32]
         _lib = L
     return _lib
 
@@ -236,6 +237,10 @@ def fmm_batch_eval(h, offsets, pos, q, potential, energy, forces, workspace, ws_
     o = np.ascontiguousarray(offsets, dtype=np.int64)
     _check(lib().fmm_batch_eval(h, o.ctypes.data_as(ctypes.c_void_p), pos, q, potential, energy,
                                 forces, workspace, ws_bytes, stream), "fmm_batch_eval")
+
+
+def fmm_batch_set_schedule(h, schedule):
+    _check(lib().fmm_batch_set_schedule(h, int(schedule)), "fmm_batch_set_schedule")
 
 
 def fmm_batch_get_stats(h):

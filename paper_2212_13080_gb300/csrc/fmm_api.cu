@@ -774,6 +774,10 @@ int fmm_plan_create(fmm_plan_t *out, const double box[4], int depth, int p, int 
     int rc = P->fp64 ? upload_tables<double>(P) : upload_tables<float>(P);
     if (rc == FMM_OK && o.shift_free) rc = fmm::sf_build(p, depth, P->periodic, P->cd, &P->sf_tab, P->sf_base, &P->sf_H,
                                                    P->sf_hoff);
+    // the tables went up by cudaMemcpy from pageable memory, which may return
+    // before the transfer lands; an evaluation on a non-blocking stream is not
+    // ordered after it
+    if (rc == FMM_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FMM_ERR_CUDA;
     if (rc != FMM_OK) {
         fmm_plan_destroy(P);
         return rc;
@@ -1323,24 +1327,20 @@ int record_merged(fmm_batch_t B, const std::vector<int64_t> &n, const std::vecto
 }
 
 // Captures the merged launches: schedule 0 on one stream; schedule 1 with
-// the near-field launches on a stream forked before the first of them and
-// joined back at the marker.
+// the near-field launches on a second stream, each after every launch that
+// precedes it in the merged order, joined back at the marker.
 int capture_merged(fmm_batch_t B, const std::vector<MergedLaunch> &ml, int schedule, const char *ws,
                    cudaStream_t st, cudaGraphExec_t *out, int *launches) {
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return FMM_ERR_CUDA;
     int total = 0;
-    bool forked = false;
+    // forked: near-field work not yet joined; main_since: main-stream launches
+    // issued since the near stream last waited for the main stream.  A near
+    // launch waits for every launch before it in the merged order: one system's
+    // near field can follow a main-stream launch (a sort variant of its size)
+    // that the merge placed after another system's first near launch.
+    bool forked = false, main_since = true;
     for (const MergedLaunch &m : ml) {
-        cudaStream_t s = st;
-        if (schedule == 1 && m.near) {
-            if (!forked) {
-                cudaEventRecord(B->near_fork, st);
-                cudaStreamWaitEvent(B->near, B->near_fork, 0);
-                forked = true;
-            }
-            s = B->near;
-        }
         if (!m.many) {  // the join marker
             if (forked) {
                 cudaEventRecord(B->near_join, B->near);
@@ -1350,6 +1350,18 @@ int capture_merged(fmm_batch_t B, const std::vector<MergedLaunch> &ml, int sched
             continue;
         }
         if (m.total <= 0) continue;
+        cudaStream_t s = st;
+        if (schedule == 1 && m.near) {
+            if (main_since) {
+                cudaEventRecord(B->near_fork, st);
+                cudaStreamWaitEvent(B->near, B->near_fork, 0);
+                main_since = false;
+            }
+            forked = true;
+            s = B->near;
+        } else {
+            main_since = true;
+        }
         m.many(B->d_tab + m.ks_off, reinterpret_cast<const int *>(B->d_tab + m.first_off), B->nsys, m.total,
                m.threads, m.smem, s);
         total++;
@@ -1609,6 +1621,10 @@ int fmm_batch_eval(fmm_batch_t B, const int64_t *offsets, const float *pos, cons
                        : FMM_ERR_UNSUPPORTED;
         if (rc != FMM_OK && rc != FMM_ERR_UNSUPPORTED) return rc;
         B->merged = rc == FMM_OK;
+        // the offsets and tables above went up by cudaMemcpy from pageable
+        // memory, which may return before the transfer lands, and the batch's
+        // stream is not ordered after it: wait for it before any launch reads them
+        if (cudaDeviceSynchronize() != cudaSuccess) return FMM_ERR_CUDA;
     }
     if (!B->gexec && B->merged) {
         if (B->schedule < 0) {
@@ -1705,6 +1721,13 @@ int fmm_batch_get_stats(fmm_batch_t B, fmm_batch_stats_t *out) {
     for (int c = 0; c < 8; c++) out->tune_ms[c] = B->tune_ms[c];
     out->merged = B->merged ? 1 : 0;
     out->schedule = B->merged ? B->schedule : -1;
+    return FMM_OK;
+}
+
+int fmm_batch_set_schedule(fmm_batch_t B, int schedule) {
+    if (!B || schedule < -1 || schedule > 1) return FMM_ERR_ARG;
+    B->schedule = schedule;
+    B->key.clear();  // the next call records and captures again
     return FMM_OK;
 }
 

@@ -58,6 +58,7 @@ def test_plan_argument_checks():
     o.split_ratio = 0.6
     assert L.fmm_plan_create(ctypes.byref(h), box, 3, 4, 0, ctypes.byref(o), 10) == B.FMM_ERR_ARG
     assert L.fmm_eval(None, 1, None, None, None, None, None, None, 0, None) == B.FMM_ERR_ARG
+    assert L.fmm_batch_set_schedule(None, 0) == B.FMM_ERR_ARG
 
 
 def test_shift_free_options_rejected_before_any_device_call():

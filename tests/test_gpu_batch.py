@@ -16,12 +16,17 @@ def _depths(counts):
     return np.clip(np.rint(np.log(counts / 32.0) / np.log(8.0)), 3, 5).astype(int)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "fp64"])
-def test_batch_matches_single_system(precision):
+@pytest.mark.parametrize("precision,schedule", [("fp32", -1), ("tf32x3", 0), ("tf32x3", 1), ("fp32", 1),
+                                                 ("fp64", -1)])
+def test_batch_matches_single_system(precision, schedule):
     """Single-precision plans run every launch site once for all systems
     (merged form; depths 3, 4 and 5 mixed, so that the systems' level loops
-    and their scan and launch-order variants differ); FP64 plans run as
-    per-system pipelines on stream lanes."""
+    and their scan and launch-order variants differ), in the schedule the
+    autotuner picks (-1) or a fixed one: one stream (0), or the near field on
+    a second stream (1), where each system's near field must still wait for
+    its own sort although the merged order interleaves the systems' sort
+    variants with the near-field launches; FP64 plans run as per-system
+    pipelines on stream lanes."""
     pos, q, offs, boxes, counts = inputs.batch_systems(12, 7, lo=1024, hi=20000)
     boxes[3] = (0.25, -1.0, 2.0, 1.5)  # one system in another box
     pos[offs[3]:offs[4]] = (pos[offs[3]:offs[4]] * np.float32(1.5) +
@@ -30,6 +35,8 @@ def test_batch_matches_single_system(precision):
     depths[int(np.argmax(counts))] = 5  # sparse finest cells, 32,768 of them
     bt = FMMBatch(boxes, depths, 4, periodic=True, continuous=True, precision=precision,
                   max_n=counts)
+    if schedule >= 0:
+        bt.set_schedule(schedule)
     P, Q = torch.from_numpy(pos).cuda(), torch.from_numpy(q).cuda()
     for call in range(2):  # first call tunes and captures, second replays the graph
         r = bt.eval(P, Q, offs)
@@ -39,7 +46,7 @@ def test_batch_matches_single_system(precision):
             assert not st["merged"] and st["lanes"] in (2, 4, 8, 12, 16, 32) and st["launches"] > 12
         else:
             # one launch per call site (levels and variants included) plus the status kernel
-            assert st["merged"] and st["lanes"] == 0 and st["schedule"] in (0, 1)
+            assert st["merged"] and st["lanes"] == 0 and st["schedule"] in ((0, 1) if schedule < 0 else (schedule,))
             assert 12 < st["launches"] < 80
         for i in range(len(counts)):
             a, b = offs[i], offs[i + 1]
