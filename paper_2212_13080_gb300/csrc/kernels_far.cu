@@ -111,8 +111,9 @@ __global__ void __launch_bounds__(KP2M<real, P>::BS) k_p2m(const __grid_constant
     k.run(blockIdx.x, gridDim.x);
 }
 
-// Warp-per-cell form for p^3 <= 128: four finest cells per CTA, one warp each,
-// no block barriers.  sf: the weights are taken at the box coordinate
+// Warp-per-cell form for p <= 6: four finest cells per CTA, one warp each,
+// no block barriers (most finest cells of a non-uniform system are empty or
+// light: a CTA per cell would spend its time on launch and barriers).  sf: the weights are taken at the box coordinate
 // (c + t)/2^depth instead of the cell-local t (App. A.2, replacement with
 // respect to the box).  Lane t computes the weights of the chunk's t-th charge
 // into the warp's shared-memory rows; every lane then accumulates its grid
@@ -713,7 +714,7 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
                  KP2M<real, PP>{C, depth, P.leaf_start, P.s_pt, phi_leaf, P.qlev + W.q_level[depth]}, \
                  ncell, P2M_BS, 0, st);                                                           \
         break;
-        WCASE(2) WCASE(3) WCASE(4) WCASE(5) CASE(6) CASE(7) CASE(8)
+        WCASE(2) WCASE(3) WCASE(4) WCASE(5) WCASE(6) CASE(7) CASE(8)
 #undef CASE
 #undef WCASE
     }

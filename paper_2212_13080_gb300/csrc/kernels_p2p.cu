@@ -98,8 +98,11 @@ struct KL2P {
         const int k0 = bid_ * LPC;
         const int nleaf = min(LPC, ncell - k0);
         if (threadIdx.x <= LPC) lst[threadIdx.x] = leaf_start[min(k0 + (int)threadIdx.x, ncell)];
+        __syncthreads();
+        if (lst[0] == lst[nleaf]) return;  // no charges in these cells (the whole CTA)
         for (int e = threadIdx.x; e < nleaf * NCL * P3; e += blockDim.x) {
             const int j = e / (NCL * P3), c = (e / P3) % NCL, o = e % P3;
+            if (lst[j + 1] == lst[j]) continue;  // an empty cell: its functionals are not read
             int cx, cy, cz;
             morton_decode((uint32_t)(k0 + j), cx, cy, cz);
             Ls[j][c][o] = loc_leaf[c * loc_comp + loc_cell(depth, cx, cy, cz) * P3 + o];
