@@ -219,7 +219,8 @@ int fmm_status(fmm_plan_t plan, const void *workspace, void *stream);
  *                     t in finest-cell units (real = float, double for FP64 plans)
  *   FMM_DUMP_PHI      real [level][8^level][p^3]: grid charges, natural cell
  *                     order (cz*S + cy)*S + cx, levels 0..depth (shift-free plans:
- *                     the box-basis charges Phi^S of App. A.2)
+ *                     the box-basis charges Phi^S of App. A.2); the open form
+ *                     forms them from level 2, levels 0 and 1 read as zero
  *   FMM_DUMP_LOCAL    real, same layout: functionals L (Psi_C(v) = L_C . v) of
  *                     the potential kernel (force-kernel plans keep three more
  *                     blocks, not dumped; shift-free plans: box-basis L^S).

@@ -1015,9 +1015,9 @@ int fmm_debug_dump(fmm_plan_t P, int what, const void *workspace, void *dst, siz
         if (cudaMemcpyAsync(raw.data(), b + off, raw.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return FMM_ERR_CUDA;
-        // functionals are formed at the cells that hold charges, on the
-        // levels of the downward pass (open form: from level 2); the others
-        // are reported as zero
+        // grid charges are formed on the levels of the upward pass, functionals
+        // at the cells that hold charges on the levels of the downward pass
+        // (open form: both from level 2); the others are reported as zero
         std::vector<int32_t> start;
         if (!isphi) {
             start.resize((size_t)W.ncell + 1);
@@ -1037,7 +1037,7 @@ int fmm_debug_dump(fmm_plan_t P, int what, const void *workspace, void *dst, siz
                 for (int cy = 0; cy < S; cy++)
                     for (int cx = 0; cx < S; cx++) {
                         int64_t c = isphi ? phi_cell(l, cx, cy, cz) : loc_cell(l, cx, cy, cz);
-                        bool formed = true;
+                        bool formed = l >= lform;  // the open form's upward pass stops at level 2
                         if (!isphi) {
                             const int64_t k = morton_encode(cx, cy, cz);
                             formed = l >= lform && start[(size_t)((k + 1) << sh)] > start[(size_t)(k << sh)];

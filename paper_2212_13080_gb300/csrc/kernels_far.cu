@@ -221,6 +221,8 @@ struct KM2M {
     real *__restrict__ phi_parent;
     const real *__restrict__ q_child;
     real *__restrict__ q_parent;
+    int depth;
+    const int *__restrict__ leaf_start;
     __device__ __forceinline__ void run(const int bid_, const int nblk_) const {
         constexpr int P3 = P * P * P, PP = P * P;
         extern __shared__ unsigned char smraw[];
@@ -231,6 +233,14 @@ struct KM2M {
         const int Hp = 1 << (l - 1);                // parents per axis
         const int pid = bid_;
         const int px = pid % Hp, py = (pid / Hp) % Hp, pz = pid / (Hp * Hp);
+        if (!cell_occupied(leaf_start, depth, l - 1, morton_encode(px, py, pz))) {
+            // no charges below this parent: its children's grid charges are all
+            // zero, and so are its own (what the sums below give)
+            real *out = phi_parent + phi_cell(l - 1, px, py, pz) * P3;
+            for (int o = threadIdx.x; o < P3; o += M2M_BS) out[o] = real(0);
+            if (threadIdx.x == 0) q_parent[phi_cell(l - 1, px, py, pz)] = real(0);
+            return;
+        }
         for (int e = threadIdx.x; e < 2 * PP; e += M2M_BS) Gs[e] = C.G[e / PP][e % PP];
         for (int e = threadIdx.x; e < 8 * P3; e += M2M_BS) {
             const int h = e / P3, o = e % P3;
@@ -736,7 +746,7 @@ void launch_upward(const Geom &g, const Coef<real> &C, const Ptrs<real> &P, cons
     case PP:                                                                                       \
         launch_k(tr, FMM_TAG(S_M2M, l), k_m2m<real, PP>,                                          \
                  KM2M<real, PP>{C, l, P.phi + W.phi_level[l], P.phi + W.phi_level[l - 1],          \
-                                P.qlev + W.q_level[l], P.qlev + W.q_level[l - 1]},                 \
+                                P.qlev + W.q_level[l], P.qlev + W.q_level[l - 1], depth, P.leaf_start}, \
                  nparent, M2M_BS, m2m_smem<real, PP>(), st);                                      \
         break;
                 CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
