@@ -1336,9 +1336,10 @@ int capture_merged(fmm_batch_t B, const std::vector<MergedLaunch> &ml, int sched
     int total = 0;
     // forked: near-field work not yet joined; main_since: main-stream launches
     // issued since the near stream last waited for the main stream.  A near
-    // launch waits for every launch before it in the merged order: one system's
-    // near field can follow a main-stream launch (a sort variant of its size)
-    // that the merge placed after another system's first near launch.
+    // launch waits for every launch before it in the merged order, so the
+    // schedule holds for any order the merge gives (a main-stream launch that
+    // one system needs before its near field may come after another system's
+    // first near launch).
     bool forked = false, main_since = true;
     for (const MergedLaunch &m : ml) {
         if (!m.many) {  // the join marker
